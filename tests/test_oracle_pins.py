@@ -1,0 +1,427 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle.
+
+Each test checks one part of the oracle against a closed form, a library
+routine used as a whole step (numpy dense Cholesky / solve / slogdet), brute
+force on tiny inputs, or an invariant, chosen so that a dropped term, a wrong
+sign, a wrong index or a transposed operand in the oracle fails at least one.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2110_12865_gb300 import problems as P
+
+
+def dense_A(p):
+    A = np.zeros((p.m, p.n))
+    for e in range(p.m):
+        s, t = p.rowptr[e], p.rowptr[e + 1]
+        A[e, p.colind[s:t]] = p.aval[s:t]
+    return A
+
+
+def dense_K(p, inst=0):
+    """K written out with numpy dense products (A^T W A + shift I), or the
+    element blocks scattered with np.add.at; fixed DOFs become identity."""
+    if p.kind == P.KIND_ATWA:
+        A = dense_A(p)
+        return A.T @ np.diag(np.asarray(p.vals[inst], np.float64)) @ A + p.shift[inst] * np.eye(p.n)
+    K = np.zeros((p.n, p.n))
+    E = p.vals[inst]
+    d = p.elem_dim
+    for e in range(p.m):
+        full = np.zeros((d, d))
+        ii, jj = np.tril_indices(d)
+        full[ii, jj] = p.elem_K0[e]
+        full[jj, ii] = p.elem_K0[e]
+        dofs = p.elem_dofs[e]
+        keep = dofs >= 0
+        idx = dofs[keep]
+        np.add.at(K, (idx[:, None], idx[None, :]), E[e] * full[np.ix_(keep, keep)])
+    ref = np.zeros(p.n, bool)
+    ref[p.elem_dofs[p.elem_dofs >= 0]] = True
+    K[~ref, ~ref] = 1.0
+    K[ref, ref] += p.shift[inst]
+    return K
+
+
+def permuted(Kd, perm):
+    return Kd[np.ix_(perm, perm)]
+
+
+def col_rel_err(L, Lref):
+    num = np.linalg.norm(L - Lref, axis=0)
+    den = np.linalg.norm(Lref, axis=0)
+    return float(np.max(num / den))
+
+
+# ----------------------------------------------------------------------------
+# assembly
+# ----------------------------------------------------------------------------
+def test_assembly_grid_closed_form():
+    """5-point grid: K_uu = sum_{e ni u} w_e + shift, K_uv = -w_e."""
+    p = P.grid_problem(7, 5, cfg=1)
+    K = O.assemble(p).dense()
+    w = p.vals[0]
+    ref = np.zeros((p.n, p.n))
+    for e, (u, v) in enumerate(p.edges):
+        ref[u, u] += w[e]
+        ref[v, v] += w[e]
+        ref[u, v] = ref[v, u] = -w[e]
+    ref += p.shift[0] * np.eye(p.n)
+    np.testing.assert_allclose(K, ref, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("maker", [lambda: P.grid_problem(16, 12, cfg=1),
+                                   lambda: P.trigrid_problem(9, cfg=3),
+                                   lambda: P.random_spd_pattern(60, 90, np.random.default_rng(3))])
+def test_assembly_matches_dense_product(maker):
+    p = maker()
+    assert p.m <= 4096
+    np.testing.assert_allclose(O.assemble(p).dense(), dense_K(p), rtol=1e-14, atol=1e-13)
+
+
+def test_assembly_elem_matches_dense_scatter():
+    p = P.elasticity_problem(2, cfg=2)
+    p["shift"] = np.array([0.25])
+    np.testing.assert_allclose(O.assemble(p).dense(), dense_K(p), rtol=1e-13, atol=1e-9)
+
+
+def test_element_blocks_rigid_modes():
+    """Each unconstrained K_e^0 is symmetric PSD with the 6 rigid-body modes
+    (3 translations, 3 infinitesimal rotations) in its null space."""
+    p = P.elasticity_problem(2, cfg=2)
+    for e in range(0, p.m, 7):
+        Ke = p.Ke[e]
+        X = p.pos[p.tets[e]]
+        modes = []
+        for c in range(3):
+            t = np.zeros((4, 3))
+            t[:, c] = 1
+            modes.append(t.ravel())
+        for a, b in [(0, 1), (1, 2), (0, 2)]:
+            r = np.zeros((4, 3))
+            r[:, a] = -X[:, b]
+            r[:, b] = X[:, a]
+            modes.append(r.ravel())
+        R = np.array(modes).T
+        assert np.abs(Ke @ R).max() < 1e-10 * np.abs(Ke).max()
+        ev = np.linalg.eigvalsh(Ke)
+        assert ev.min() > -1e-12 * ev.max()
+        assert np.sum(ev > 1e-8 * ev.max()) == 6
+
+
+def test_permute_matches_dense():
+    p = P.random_spd_pattern(40, 60, np.random.default_rng(5))
+    Kp = O.permute(O.assemble(p), p.perm).dense()
+    np.testing.assert_array_equal(Kp, permuted(O.assemble(p).dense(), p.perm))
+
+
+# ----------------------------------------------------------------------------
+# symbolic
+# ----------------------------------------------------------------------------
+def brute_symbolic(Kp_dense_bool):
+    """Dense boolean elimination: returns pattern of L (lower incl. diagonal)."""
+    n = Kp_dense_bool.shape[0]
+    G = np.tril(Kp_dense_bool.copy()) | np.eye(n, dtype=bool)
+    for k in range(n):
+        rows = np.nonzero(G[k + 1:, k])[0] + k + 1
+        for i in rows:
+            G[i, rows[rows <= i]] = True
+    return G
+
+
+def levels_by_definition(parent):
+    n = len(parent)
+    lev = [0] * n
+    for j in range(n):  # children precede parents
+        if parent[j] >= 0:
+            lev[parent[j]] = max(lev[parent[j]], lev[j] + 1)
+    return np.array(lev)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_symbolic_brute_force(seed):
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.integers(20, 300))
+    p = P.random_spd_pattern(n, int(rng.integers(0, 2 * n)), rng)
+    Kp = O.permute(O.assemble(p), p.perm)
+    S = O.Symbolic(Kp)
+    G = brute_symbolic(Kp.dense() != 0)
+    Lpat = np.zeros((n, n), bool)
+    for j in range(n):
+        Lpat[S.Lrowind[S.Lcolptr[j]:S.Lcolptr[j + 1]], j] = True
+    np.testing.assert_array_equal(Lpat, G)
+    parent = np.array([np.nonzero(G[j + 1:, j])[0][0] + j + 1 if G[j + 1:, j].any() else -1
+                       for j in range(n)])
+    np.testing.assert_array_equal(S.parent, parent)
+    np.testing.assert_array_equal(S.colcount, G.sum(0))
+    np.testing.assert_array_equal(S.col_level, levels_by_definition(parent))
+    # fundamental supernodes by definition
+    nchild = np.bincount(parent[parent >= 0], minlength=n)
+    cnt = G.sum(0)
+    first = [j for j in range(n) if not (j > 0 and parent[j - 1] == j and nchild[j] == 1
+                                         and cnt[j] == cnt[j - 1] - 1)]
+    np.testing.assert_array_equal(S.snode_first[:-1], first)
+    # supernodal tree levels by definition
+    col2sn = np.repeat(np.arange(len(first)), np.diff(list(first) + [n]))
+    snp = np.array([col2sn[parent[S.snode_first[k + 1] - 1]] if parent[S.snode_first[k + 1] - 1] >= 0
+                    else -1 for k in range(len(first))])
+    np.testing.assert_array_equal(S.sn_parent, snp)
+    np.testing.assert_array_equal(S.sn_level, levels_by_definition(snp))
+
+
+def test_symbolic_path_natural_order():
+    """Path graph in natural order: zero fill, chain etree, n levels."""
+    n = 50
+    rowptr, colind, aval = P.path_incidence(n)
+    p = P.Problem(kind=0, n=n, m=len(rowptr) - 1, rowptr=rowptr, colind=colind, aval=aval,
+                  perm=np.arange(n, dtype=np.int32), vals=np.ones((1, len(rowptr) - 1)),
+                  shift=np.zeros(1), b=np.ones((1, n)), batch=1)
+    Kp = O.permute(O.assemble(p), p.perm)
+    S = O.Symbolic(Kp)
+    assert S.nnzL == Kp.nnz == 2 * n - 1
+    np.testing.assert_array_equal(S.parent, list(range(1, n)) + [-1])
+    np.testing.assert_array_equal(S.col_level, np.arange(n))
+
+
+def test_symbolic_dense_is_one_supernode():
+    n = 30
+    edges = np.array([(i, j) for i in range(n) for j in range(i + 1, n)])
+    rowptr, colind, aval = P.incidence_csr(edges, n)
+    p = P.Problem(kind=0, n=n, m=len(edges), rowptr=rowptr, colind=colind, aval=aval,
+                  perm=np.random.default_rng(0).permutation(n).astype(np.int32),
+                  vals=np.ones((1, len(edges))), shift=np.ones(1), b=np.ones((1, n)), batch=1)
+    S = O.Symbolic(O.permute(O.assemble(p), p.perm))
+    assert S.n_snodes == 1 and S.nnzL == n * (n + 1) // 2
+
+
+def test_symbolic_tree_leaf_first_zero_fill():
+    """A tree whose vertices are numbered children-before-parent factors with
+    no fill."""
+    rng = np.random.default_rng(7)
+    n = 200
+    par = [int(rng.integers(i + 1, n)) for i in range(n - 1)]  # parent index > child
+    edges = np.array([(i, par[i]) for i in range(n - 1)])
+    rowptr, colind, aval = P.incidence_csr(edges, n)
+    p = P.Problem(kind=0, n=n, m=n - 1, rowptr=rowptr, colind=colind, aval=aval,
+                  perm=np.arange(n, dtype=np.int32), vals=np.ones((1, n - 1)),
+                  shift=np.full(1, 0.5), b=np.ones((1, n)), batch=1)
+    Kp = O.permute(O.assemble(p), p.perm)
+    S = O.Symbolic(Kp)
+    assert S.nnzL == Kp.nnz
+    np.testing.assert_array_equal(S.parent, par + [-1])
+
+
+# ----------------------------------------------------------------------------
+# numeric factorization
+# ----------------------------------------------------------------------------
+def test_tridiagonal_closed_form():
+    """A^T A of the path incidence with single-entry end rows is
+    tridiag(-1, 2, -1); its factor is l_ii = sqrt((i+1)/i),
+    l_{i+1,i} = -sqrt(i/(i+1)) (1-based)."""
+    n = 64
+    rowptr, colind, aval = P.path_incidence(n)
+    p = P.Problem(kind=0, n=n, m=len(rowptr) - 1, rowptr=rowptr, colind=colind, aval=aval,
+                  perm=np.arange(n, dtype=np.int32), vals=np.ones((1, len(rowptr) - 1)),
+                  shift=np.zeros(1), b=np.ones((1, n)), batch=1)
+    r = O.refactor_solve(p)
+    assert r.bad == -1
+    L = r.S.L_dense(r.L)
+    i = np.arange(1, n + 1, dtype=np.float64)
+    np.testing.assert_allclose(np.diag(L), np.sqrt((i + 1) / i), rtol=2e-16 * 8, atol=0)
+    np.testing.assert_allclose(np.diag(L, -1), -np.sqrt(i[:-1] / (i[:-1] + 1)), rtol=2e-16 * 8, atol=0)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_cholesky_matches_numpy_dense(seed):
+    rng = np.random.default_rng(200 + seed)
+    n = int(rng.integers(2, 65))
+    p = P.random_spd_pattern(n, int(rng.integers(0, 3 * n)), rng)
+    r = O.refactor_solve(p)
+    assert r.bad == -1
+    Lref = np.linalg.cholesky(permuted(dense_K(p), p.perm))
+    L = r.S.L_dense(r.L)
+    assert col_rel_err(L, Lref) <= 1e-13
+    assert np.all(np.triu(L, 1) == 0)
+
+
+def own_dense_cholesky(A):
+    """Textbook dense Cholesky-Crout in pure Python loops (a second pin,
+    independent of numpy's LAPACK)."""
+    n = len(A)
+    L = [[0.0] * n for _ in range(n)]
+    for j in range(n):
+        s = A[j][j] - sum(L[j][k] * L[j][k] for k in range(j))
+        L[j][j] = s ** 0.5
+        for i in range(j + 1, n):
+            L[i][j] = (A[i][j] - sum(L[i][k] * L[j][k] for k in range(j))) / L[j][j]
+    return np.array(L)
+
+
+def test_cholesky_matches_own_dense_routine():
+    p = P.grid_problem(5, 4, cfg=1)
+    r = O.refactor_solve(p)
+    Kp = permuted(dense_K(p), p.perm)
+    assert col_rel_err(r.S.L_dense(r.L), own_dense_cholesky(Kp.tolist())) <= 1e-14
+
+
+@pytest.mark.parametrize("maker", [lambda: P.grid_problem(32, 32, cfg=1),
+                                   lambda: P.trigrid_problem(20, cfg=3),
+                                   lambda: P.elasticity_problem(4, cfg=2)])
+def test_reconstruction(maker):
+    p = maker()
+    r = O.refactor_solve(p)
+    Kp = r.Kp.dense()
+    L = r.S.L_dense(r.L)
+    assert np.linalg.norm(L @ L.T - Kp) / np.linalg.norm(Kp) < 1e-14
+
+
+def test_not_spd_reports_first_failing_column():
+    """Pivot j of Cholesky equals det(K~[:j+1,:j+1]) / det(K~[:j,:j]); the
+    oracle must stop at the first j where it is not positive."""
+    rng = np.random.default_rng(11)
+    hits = 0
+    for t in range(40):
+        n = 30
+        p = P.random_spd_pattern(n, 40, rng)
+        p["vals"] = rng.uniform(-0.3, 2.0, (1, p.m))
+        p["shift"] = np.array([-0.05])
+        r = O.refactor_solve(p)
+        Kp = permuted(dense_K(p), p.perm)
+        first = -1
+        prev = 0.0  # log|det| of the empty minor
+        for j in range(n):
+            sgn, ld = np.linalg.slogdet(Kp[: j + 1, : j + 1])
+            if sgn <= 0:
+                first = j
+                break
+        assert r.bad == first
+        hits += first >= 0
+    assert hits > 5
+
+
+# ----------------------------------------------------------------------------
+# solves
+# ----------------------------------------------------------------------------
+def test_solve_matches_numpy_dense():
+    p = P.grid_problem(32, 32, cfg=1)
+    r = O.refactor_solve(p)
+    x = np.linalg.solve(dense_K(p), p.b[0])
+    assert np.linalg.norm(r.x - x) / np.linalg.norm(x) < 1e-13
+
+
+def test_solve_residual_elasticity():
+    p = P.elasticity_problem(5, cfg=2)
+    r = O.refactor_solve(p)
+    res = O.symv(r.K, r.x) - p.b[0]
+    assert np.linalg.norm(res) / np.linalg.norm(p.b[0]) < 1e-12
+    assert np.all(r.x[p.dof_fixed] == 0.0)
+
+
+def test_symv_matches_dense():
+    p = P.trigrid_problem(10, cfg=3)
+    K = O.assemble(p)
+    x = np.random.default_rng(1).standard_normal(p.n)
+    np.testing.assert_allclose(O.symv(K, x), dense_K(p) @ x, rtol=1e-13, atol=1e-12)
+
+
+# ----------------------------------------------------------------------------
+# adjoint
+# ----------------------------------------------------------------------------
+def loss_and_grad(p, inst=0):
+    r = O.refactor_solve(p, inst)
+    xs = p.xstar[inst]
+    xbar = 2.0 * (r.x - xs)
+    vbar, sbar, bbar = O.backward(p, r, xbar, inst)
+    return float(np.sum((r.x - xs) ** 2)), vbar, sbar, bbar
+
+
+def fd_loss(p, vals, shift, b, inst=0):
+    r = O.refactor_solve(p, inst, vals=vals, shift=shift, b=b)
+    return r.x
+
+
+def fd_diff(p, xp, xm, inst=0):
+    """loss(x+) - loss(x-) for loss = ||x - x*||^2, written as
+    sum (x+ - x-)(x+ + x- - 2 x*) so the two large sums do not cancel."""
+    return float(np.sum((xp - xm) * (xp + xm - 2.0 * p.xstar[inst])))
+
+
+@pytest.mark.parametrize("shift", [1.0, 1e-2])
+def test_gradient_central_differences(shift):
+    """|g - g_FD| <= 1e-5 max(|g_FD|, 1e-3 ||g_FD||_inf) + floor, h = 1e-6.
+
+    The central difference itself carries a rounding floor of about
+    kappa(K) * u * ||x||_inf * ||xbar||_1 / h (the two perturbed solves round
+    independently).  With shift 1 (kappa ~ 10) that floor is far below the
+    1e-5 criterion and is set to 0; with shift 1e-2 (kappa ~ 1e3) it is added."""
+    p = P.grid_problem(8, 8, cfg=4, shift=shift)
+    _, vbar, sbar, bbar = loss_and_grad(p)
+    rng = np.random.default_rng(3)
+    h = 1e-6
+    w0, s0, b0 = p.vals[0].astype(np.float64), float(p.shift[0]), p.b[0].copy()
+    edges = rng.choice(p.m, 32, replace=False)
+    g_fd = []
+    for e in edges:
+        wp, wm = w0.copy(), w0.copy()
+        wp[e] += h
+        wm[e] -= h
+        g_fd.append(fd_diff(p, fd_loss(p, wp, s0, b0), fd_loss(p, wm, s0, b0)) / (2 * h))
+    g_fd = np.array(g_fd)
+    r = O.refactor_solve(p)
+    ev = np.linalg.eigvalsh(dense_K(p))
+    floor = 0.0 if shift >= 1.0 else (ev[-1] / ev[0]) * 2.2e-16 * np.abs(r.x).max() * \
+        np.abs(2 * (r.x - p.xstar[0])).sum() / h
+    tol = 1e-5 * np.maximum(np.abs(g_fd), 1e-3 * np.abs(g_fd).max()) + floor
+    assert np.all(np.abs(vbar[edges] - g_fd) <= tol)
+    fd_s = fd_diff(p, fd_loss(p, w0, s0 + h, b0), fd_loss(p, w0, s0 - h, b0)) / (2 * h)
+    assert abs(sbar - fd_s) <= 1e-5 * abs(fd_s) + floor
+    for i in rng.choice(p.n, 8, replace=False):
+        bp, bm = b0.copy(), b0.copy()
+        bp[i] += h
+        bm[i] -= h
+        fd_b = fd_diff(p, fd_loss(p, w0, s0, bp), fd_loss(p, w0, s0, bm)) / (2 * h)
+        assert abs(bbar[i] - fd_b) <= 1e-5 * max(abs(fd_b), 1e-3 * np.abs(bbar).max()) + floor
+
+
+def test_gradient_elasticity_central_differences():
+    p = P.elasticity_problem(2, cfg=2)
+    rng = np.random.default_rng(9)
+    p["xstar"] = rng.standard_normal((1, p.n)) * 1e-4
+    r = O.refactor_solve(p)
+    xbar = 2.0 * (r.x - p.xstar[0])
+    Ebar, _, _ = O.backward(p, r, xbar)
+    E0 = p.vals[0].copy()
+    for e in rng.choice(p.m, 6, replace=False):
+        h = 1e-6 * E0[e]
+        Ep, Em = E0.copy(), E0.copy()
+        Ep[e] += h
+        Em[e] -= h
+        fd = fd_diff(p, fd_loss(p, Ep, 0.0, p.b[0]), fd_loss(p, Em, 0.0, p.b[0])) / (2 * h)
+        assert abs(Ebar[e] - fd) <= 1e-5 * max(abs(fd), 1e-3 * np.abs(Ebar).max())
+
+
+def test_gradient_scalar_closed_form():
+    """n = 1: K = w + s, x = b/(w+s), loss (x - x*)^2:
+    dl/dw = -2 (x - x*) b / (w+s)^2, dl/db = 2 (x - x*)/(w+s)."""
+    w, s, b, xs = 1.7, 0.3, -0.8, 0.25
+    p = P.Problem(kind=0, n=1, m=1, rowptr=np.array([0, 1], np.int64), colind=np.array([0], np.int32),
+                  aval=np.array([1.0]), perm=np.array([0], np.int32), vals=np.array([[w]]),
+                  shift=np.array([s]), b=np.array([[b]]), xstar=np.array([[xs]]), batch=1)
+    _, vbar, sbar, bbar = loss_and_grad(p)
+    x = b / (w + s)
+    assert abs(vbar[0] - (-2 * (x - xs) * b / (w + s) ** 2)) < 1e-15
+    assert abs(sbar - (-2 * (x - xs) * b / (w + s) ** 2)) < 1e-15
+    assert abs(bbar[0] - 2 * (x - xs) / (w + s)) < 1e-15
+
+
+def test_adjoint_symmetry():
+    """<K^-1 u, v> = <u, K^-1 v> for the oracle's solve."""
+    p = P.trigrid_problem(12, cfg=3)
+    r = O.refactor_solve(p)
+    rng = np.random.default_rng(4)
+    u, v = rng.standard_normal(p.n), rng.standard_normal(p.n)
+    a = np.dot(r.S.solve(r.L, p.perm, u), v)
+    b = np.dot(u, r.S.solve(r.L, p.perm, v))
+    assert abs(a - b) <= 1e-12 * max(abs(a), 1.0)
