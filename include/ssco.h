@@ -1,0 +1,233 @@
+/*
+ * ssco.h -- C ABI of the fixed-pattern assemble / refactor / solve / adjoint
+ * library for one GB300 (sm_103a).
+ *
+ * The setting is the paper's "compile once for a fixed structure, evaluate
+ * for many value sets" (Sec. 3.3, requirement 2; Sec. 4.3 grouping of
+ * structurally equal expressions by dependency level; Sec. 4.4 leaf tables
+ * with uniform vs varying constants; Sec. 4.8 index arrays p, constants c,
+ * consecutive outputs, coalesced layouts).  The fixed structure here is the
+ * sparsity pattern of K = A^T diag(w) A + shift*I (or K = sum_e E_e K_e^0,
+ * the tagged element blocks of Sec. 4.2.4); the evaluated program is the
+ * assembly of K, its Cholesky factorization K~ = P K P^T = L L^T and the two
+ * triangular solves, plus their adjoint.
+ *
+ * Conventions shared by every entry point
+ *  - Every call returns an ssco_status; nothing throws across the ABI.
+ *    ssco_last_error(plan) returns a message for the last failing call.
+ *  - The caller owns every array it passes.  ssco_analyze copies what it
+ *    needs; the library owns the host plan until ssco_destroy.
+ *  - ALL device memory is caller-allocated: ssco_plan_info reports the
+ *    sizes of the table buffer and the workspace, ssco_bind attaches them.
+ *    The library never calls cudaMalloc.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default).
+ *    Calls are asynchronous on it except where a comment says otherwise.
+ *  - Batched values are INSTANCE-OUTERMOST: an array "[B][n]" holds value set
+ *    b at offset b*n.  Several patterns in one plan are concatenated: their
+ *    unknowns (and values) follow each other in pattern order.
+ *  - A "system" is one (instance b, pattern k) pair, index b*n_pats + k.
+ *  - A plan and its workspace must not be used on two streams at once.
+ */
+#ifndef SSCO_H
+#define SSCO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SSCO_OK = 0,
+    SSCO_ERR_INVALID_ARG = 1,  /* NULL pointer, bad size, bad enum          */
+    SSCO_ERR_PATTERN = 2,      /* index out of range, bad rowptr, bad perm  */
+    SSCO_ERR_NOT_SPD = 3,      /* a pivot was not > 0 (per system)          */
+    SSCO_ERR_NONFINITE = 4,    /* NaN/Inf in values or right-hand side      */
+    SSCO_ERR_NO_CONVERGE = 5,  /* refinement hit its cap or stagnated       */
+    SSCO_ERR_TIMEOUT = 6,      /* a bounded device wait gave up             */
+    SSCO_ERR_CUDA = 7,         /* a CUDA runtime call failed                */
+    SSCO_ERR_OOM = 8,          /* a caller buffer is smaller than required  */
+    SSCO_ERR_UNSUPPORTED = 9,  /* request outside what this build does      */
+    SSCO_ERR_STATE = 10        /* call order violated (e.g. solve unbound)  */
+} ssco_status;
+
+enum { SSCO_KIND_ATWA = 0, SSCO_KIND_ELEM = 1 };
+enum { SSCO_FP64 = 0, SSCO_FP32_REFINE = 1 };
+enum { SSCO_VALS_F64 = 0, SSCO_VALS_F32 = 1 };
+
+typedef struct ssco_plan_s* ssco_plan;
+
+/* One fixed sparsity structure.
+ * kind = SSCO_KIND_ATWA:  K = A^T diag(w) A + shift*I.  A is m x n in CSR
+ *   (rowptr[m+1] int64, colind[nnz] int32 in [0,n), aval[nnz] constant
+ *   entries, e.g. +-1 for an incidence matrix).  The per-call values are w[m].
+ *   Every diagonal of K receives the shift.
+ * kind = SSCO_KIND_ELEM:  K = sum_e E_e K_e^0 over m elements.  elem_dofs
+ *   [m][elem_dim] lists each element's global DOF (or -1 for a fixed DOF);
+ *   elem_K0 [m][elem_dim*(elem_dim+1)/2] holds K_e^0 as a row-major packed
+ *   lower triangle (i >= j).  The per-call values are E[m].  A DOF that no
+ *   element references becomes an identity row/column (K_ii = 1); every
+ *   referenced DOF's diagonal receives the shift.
+ * perm[n] (perm[new] = old) is the fill-reducing order; NULL = natural.
+ *   It must be a permutation of [0,n) (else SSCO_ERR_PATTERN).          */
+typedef struct {
+    int32_t kind;
+    int32_t n;
+    int32_t m;
+    const int64_t* rowptr;
+    const int32_t* colind;
+    const double* aval;
+    int32_t elem_dim;
+    const int32_t* elem_dofs;
+    const double* elem_K0;
+    const int32_t* perm;
+} ssco_pattern;
+
+/* Options of the numeric phase.
+ * precision: SSCO_FP64 factors and solves in FP64.  SSCO_FP32_REFINE factors
+ *   in FP32 and refines in FP64: r = b - K x with the FP64 K, d = solve32(r),
+ *   x += d, until ||r||_2 <= refine_tol*||b||_2, refine_max_iter iterations,
+ *   or stagnation (||r|| not halved over two iterations).
+ * batch: value sets per pattern (>= 1).
+ * small_front_max: fronts with more rows than this use the multi-CTA dense
+ *   path (0 = default for the precision).
+ * amalgamate: 0 = fundamental supernodes only; > 0 = relaxed amalgamation
+ *   allowing up to that many explicit zeros per merged front column
+ *   (numeric partition only; exported structures stay exact).          */
+typedef struct {
+    int32_t precision;
+    int32_t batch;
+    double refine_tol;
+    int32_t refine_max_iter;
+    int32_t small_front_max;
+    int32_t amalgamate;
+    int32_t reserved[3];
+} ssco_op;
+
+/* Sizes and counts of an analyzed plan (all for the concatenated system). */
+typedef struct {
+    int64_t n;               /* unknowns (sum over patterns)                 */
+    int64_t n_pats;
+    int64_t batch;
+    int64_t n_systems;       /* batch * n_pats                               */
+    int64_t m;               /* values per instance (sum over patterns)      */
+    int64_t nnz_K;           /* lower triangle of K incl. diagonal           */
+    int64_t nnz_L;           /* structural nonzeros of L incl. diagonal      */
+    int64_t n_snodes;        /* fundamental supernodes                       */
+    int64_t n_fronts;        /* supernodes of the numeric partition          */
+    int64_t n_levels;        /* levels of the numeric supernodal forest      */
+    int64_t max_col_level;   /* height of the column elimination forest      */
+    int64_t panel_entries;   /* stored factor entries (per instance)         */
+    int64_t update_entries;  /* stored update-matrix entries (per instance)  */
+    int64_t max_front_rows;
+    int64_t n_assembly_groups;
+    int64_t assembly_terms;  /* total terms in the assembly leaf tables      */
+    int64_t tables_bytes;    /* device table buffer size                     */
+    int64_t workspace_bytes; /* device workspace size                        */
+    double factor_flops;     /* sum_j c_j^2 over the numeric partition       */
+    double factor_flops_exact; /* sum_j c_j^2 over the exact structure       */
+} ssco_info;
+
+/* ssco_plan_export selectors (host copies; sizes in elements).          */
+enum {
+    SSCO_EXPORT_PERM = 0,        /* int32 [n]     concatenated perm (new->old) */
+    SSCO_EXPORT_ETREE = 1,       /* int32 [n]     parent column, -1 = root     */
+    SSCO_EXPORT_COLCOUNT = 2,    /* int32 [n]     nnz of each column of L      */
+    SSCO_EXPORT_L_COLPTR = 3,    /* int64 [n+1]                                */
+    SSCO_EXPORT_L_ROWIND = 4,    /* int32 [nnz_L] rows ascending per column    */
+    SSCO_EXPORT_COL_LEVEL = 5,   /* int32 [n]     height in the column forest  */
+    SSCO_EXPORT_SNODE_FIRST = 6, /* int32 [n_snodes+1] fundamental supernodes  */
+    SSCO_EXPORT_SN_PARENT = 7,   /* int32 [n_snodes]                           */
+    SSCO_EXPORT_SN_LEVEL = 8,    /* int32 [n_snodes] height in the sn forest   */
+    SSCO_EXPORT_K_COLPTR = 9,    /* int64 [n+1]   pattern of K~ (lower, CSC)   */
+    SSCO_EXPORT_K_ROWIND = 10,   /* int32 [nnz_K]                              */
+    SSCO_EXPORT_GROUPS = 11,     /* int64 [n_assembly_groups][4]: members,     */
+                                 /*   terms, coefficient mode (0 varying,      */
+                                 /*   1 uniform), diagonal flag                */
+    SSCO_EXPORT_GROUP_COEF = 12, /* double [n_assembly_groups]: the uniform     */
+                                 /*   constant (0 for varying groups)          */
+    SSCO_EXPORT_FRONT_FIRST = 13,/* int32 [n_fronts+1] numeric partition       */
+    SSCO_EXPORT_FRONT_LEVEL = 14 /* int32 [n_fronts]                           */
+};
+
+/* Symbolic phase (host only, no GPU needed).  Validates every pattern,
+ * builds K~'s pattern and the assembly leaf tables grouped by (term count,
+ * uniform/varying constant, diagonal) [Sec. 4.3, 4.4, App. B], the
+ * elimination forest, column counts, fundamental supernodes, level sets by
+ * height, the numeric front partition and all index tables.
+ * Errors: SSCO_ERR_INVALID_ARG, SSCO_ERR_PATTERN. */
+ssco_status ssco_analyze(const ssco_pattern* const* pats, int32_t n_pats, const ssco_op* op,
+                         ssco_plan* out);
+ssco_status ssco_plan_info(ssco_plan plan, ssco_info* out);
+/* Copies one exported structure into host_buf (bytes must be >= its size,
+ * else SSCO_ERR_OOM). */
+ssco_status ssco_plan_export(ssco_plan plan, int32_t what, void* host_buf, size_t bytes);
+
+/* Attaches caller-allocated device memory: dev_tables (>= tables_bytes,
+ * 256-byte aligned) receives the index tables (copied on `stream`);
+ * dev_workspace (>= workspace_bytes, 256-byte aligned) holds K, the factor,
+ * update matrices, vectors and status words.  Re-binding is allowed. */
+ssco_status ssco_bind(ssco_plan plan, void* dev_tables, size_t tables_bytes, void* dev_workspace,
+                      size_t workspace_bytes, void* stream);
+
+/* Numeric phase: assemble K from vals (device, [B][m], dtype
+ * SSCO_VALS_F64/F32) and shift (device, double [n_systems]), then factor.
+ * Asynchronous.  A non-positive pivot is recorded per system (read it with
+ * ssco_status_get), never branched on. */
+ssco_status ssco_numeric(ssco_plan plan, const void* vals, int32_t vals_dtype, const double* shift,
+                         void* stream);
+
+/* x = K^-1 b for every system (device, double [B][n] each; b and x may not
+ * alias).  In SSCO_FP32_REFINE mode the refinement loop runs on the device;
+ * the host reads one flag per iteration, so this call synchronizes `stream`. */
+ssco_status ssco_solve(ssco_plan plan, const double* b, double* x, void* stream);
+
+/* Adjoint of x = K(vals, shift)^-1 b for a scalar loss with dloss/dx = xbar:
+ * mu = K^-1 xbar (same factor, same refinement), then
+ *   vals_bar_e = -(A mu)_e (A x)_e            (ATWA)
+ *   vals_bar_e = -mu_e^T K_e^0 x_e            (ELEM, free DOFs)
+ *   shift_bar  = -mu^T x over shifted diagonals, per system
+ *   b_bar      = mu.
+ * Device arrays: x, xbar, b_bar [B][n]; vals_bar [B][m]; shift_bar
+ * [n_systems] (may be NULL).  Synchronizes `stream` like ssco_solve. */
+ssco_status ssco_backward(ssco_plan plan, const double* x, const double* xbar, double* vals_bar,
+                          double* shift_bar, double* b_bar, void* stream);
+
+/* Synchronizes `stream`, then copies per-system results to host arrays
+ * (any may be NULL): status (ssco_status codes), iters (refinement
+ * iterations of the last solve), resid (||b - K x||_2 / ||b||_2 of the last
+ * solve, FP64), bad_col (first non-positive pivot in permuted numbering,
+ * -1 if none).  Returns SSCO_OK or the worst system status. */
+ssco_status ssco_status_get(ssco_plan plan, void* stream, int32_t* status, int32_t* iters,
+                            double* resid, int32_t* bad_col);
+
+/* Writes the factor in CSC order of SSCO_EXPORT_L_ROWIND, as double
+ * [B][nnz_L] (device).  Asynchronous. */
+ssco_status ssco_export_L(ssco_plan plan, double* dev_out, void* stream);
+/* Writes K~ values in CSC order of SSCO_EXPORT_K_ROWIND, double [B][nnz_K]
+ * (device).  Asynchronous. */
+ssco_status ssco_export_K(ssco_plan plan, double* dev_out, void* stream);
+
+/* End-to-end call on HOST buffers: copies vals/shift/b to the device
+ * (staging areas inside the workspace), runs numeric + solve, copies x back
+ * and synchronizes.  Host arrays use the same layouts as above. */
+ssco_status ssco_refactor_solve_host(ssco_plan plan, const void* vals, int32_t vals_dtype,
+                                     const double* shift, const double* b, double* x, void* stream);
+
+/* Number of kernel launches the last ssco_numeric / ssco_solve /
+ * ssco_backward / ssco_refactor_solve_host call issued (host counter). */
+int64_t ssco_last_launch_count(ssco_plan plan);
+
+const char* ssco_last_error(ssco_plan plan);
+const char* ssco_status_string(ssco_status s);
+
+/* Versioned binary file of the host plan (no device state). */
+ssco_status ssco_plan_save(ssco_plan plan, const char* path);
+ssco_status ssco_plan_load(const char* path, ssco_plan* out);
+void ssco_destroy(ssco_plan plan);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SSCO_H */

@@ -1,0 +1,205 @@
+// ssco_internal.h -- plan layout shared by the host symbolic phase
+// (ssco_symbolic.cpp), the C ABI (ssco_api.cpp) and the kernels
+// (ssco_kernels.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/ssco.h"
+
+namespace ssco {
+
+// One front of the numeric partition (a fundamental or amalgamated
+// supernode).  Its factor columns [f, f+w) are stored as a dense r x w
+// column-major panel whose rows are rows[rows_off .. rows_off+r) (the first
+// w of them are the front's own columns).  Its update (Schur complement)
+// matrix is (r-w) x (r-w) column-major, lower triangle meaningful.
+struct FrontDesc {
+    int32_t f, w, r, parent;      // first column, width, rows, parent front or -1
+    int32_t nchild, child_off;    // children: child_ids[child_off .. +nchild)
+    int32_t klist_n, sys;         // number of K entries owned; pattern index
+    int64_t klist_off;            // K entries: klist[2*(klist_off+t)] = {kslot, pos}
+    int64_t rows_off;             // into rows[]
+    int64_t panel_off;            // per-instance offset of the r x w panel
+    int64_t upd_off;              // per-instance offset of the (r-w)^2 update
+    int64_t pvec_off;             // per-instance offset of the (r-w) passing vector
+    int64_t relmap_off;           // r-w positions of this front's update rows in
+                                  // the parent's rows (-1 for a root)
+    int64_t inv_off;              // big fronts: [nchild][r] inverse maps (-1 if none)
+};
+
+// Assembly leaf table of one group (Sec. 4.3/4.4): members share a term
+// count, a diagonal flag and (if uniform) the constant of every term.
+// K[slot_base + i] = cadd + sum_t c_t * vals[idx[t*nmem + i]] (+ shift if diag)
+struct AsmGroup {
+    int32_t nmem, nterms, uniform, diag;
+    int32_t sys, pad;
+    double coef;        // uniform constant (uniform == 1)
+    double cadd;        // constant added (1 for identity rows, else 0)
+    int64_t idx_off;    // into asm_idx (term-major, member-innermost)
+    int64_t coef_off;   // into asm_coef (varying groups only)
+    int64_t slot_base;  // first K storage slot of the group
+};
+
+struct AsmChunk {
+    int32_t group, start;
+};
+
+// A batch of fronts handled by one launch.
+struct LaunchList {
+    int32_t level;
+    int32_t cls;        // small-front size class (max rows), or -1 for big fronts
+    int64_t list_off;   // into front_lists
+    int32_t count;
+    int32_t rmax, wmax;
+    int64_t max_lower_tiles;  // big: max tiles of 32x32 over the front's lower triangle
+    int64_t max_syrk_tiles;   // big: max 64x64 lower tiles of the update block
+    int32_t max_klist;        // big: max K entries per front
+};
+
+// Typed device pointers into the bound table buffer.
+struct DevTables {
+    const FrontDesc* fronts;
+    const int32_t* rows;
+    const int32_t* child_ids;
+    const int32_t* relmap;
+    const int32_t* invmap;
+    const int32_t* klist;
+    const int32_t* front_lists;
+    const AsmGroup* groups;
+    const AsmChunk* chunks;
+    const int32_t* asm_idx;
+    const double* asm_coef;
+    const int64_t* sp_rowptr;   // symmetric CSR of K~ over permuted rows
+    const int32_t* sp_col;
+    const int32_t* sp_slot;
+    const int32_t* perm;        // concatenated perm (new -> old)
+    const int32_t* row_sys;     // pattern index of each permuted row
+    const int64_t* sys_n_off;   // [n_pats+1] row ranges of patterns
+    const int64_t* g_rowptr;    // ATWA rows (concatenated), for the adjoint
+    const int32_t* g_colind;    // global (concatenated, original order) columns
+    const double* g_aval;
+    const int32_t* g_row_sys;   // pattern of each ATWA row (values index space)
+    const int32_t* e_dofs;      // ELEM dofs (global, original order, -1 fixed)
+    const double* e_K0;
+    const int32_t* e_sys;       // pattern of each element
+    const int64_t* e_off;       // per element: offset into e_dofs (dim varies per pattern)
+    const int64_t* e_k0off;     // per element: offset into e_K0
+    const int32_t* e_dim;       // per element: local DOF count
+    const uint8_t* shifted;     // per permuted row: receives the shift (1) or not
+    const int32_t* g_rows_all;  // value indices that are ATWA rows
+    const int32_t* e_elems_all; // value indices that are elements
+};
+
+// Byte offsets of every region of the caller's workspace.
+struct WsLayout {
+    size_t K, panel, upd, pvec, vecT, bp, xp, rr, mu, xbar_p;
+    size_t bad_col, sstatus, iters, active, any_active;
+    size_t resid, bnorm, r1, r2, sigma, sbar;
+    size_t st_vals, st_shift, st_b, st_x;
+    size_t total;
+};
+
+struct PatMeta {
+    int32_t kind, n, m, dim;
+    int64_t n_off, m_off;
+};
+
+struct Plan {
+    // options
+    int32_t prec = SSCO_FP64;
+    int32_t B = 1;
+    double tol = 1e-10;
+    int32_t maxit = 30;
+    int32_t small_max = 0;
+    int32_t amalg = 1;
+    size_t tsize = 8;  // bytes of the factor type
+
+    int32_t n_pats = 0;
+    std::vector<PatMeta> pats;
+    int64_t n = 0, m = 0;
+
+    // K~ (concatenated, lower CSC)
+    std::vector<int64_t> Kcolptr;
+    std::vector<int32_t> Krowind;
+    std::vector<int32_t> kslot_of_q;  // CSC position -> storage slot
+    int64_t nnzK = 0;
+
+    // exact symbolic structures
+    std::vector<int32_t> perm, parent, colcount, col_level;
+    std::vector<int32_t> snode_first, sn_parent, sn_level;
+    std::vector<int64_t> sn_rows_off;  // fundamental supernode rows (for exports)
+    std::vector<int32_t> sn_rows;
+    int64_t nnzL = 0;
+    int32_t max_col_level = 0;
+    double flops_exact = 0, flops_numeric = 0;
+
+    // numeric partition
+    std::vector<FrontDesc> fronts;
+    std::vector<int32_t> front_first, front_level;
+    std::vector<int32_t> rows, child_ids, relmap, invmap, klist, front_lists;
+    std::vector<LaunchList> fact_launches;   // per level: small classes + big
+    std::vector<LaunchList> solve_launches;  // per level: all fronts
+    int32_t n_levels = 0;
+    int64_t panel_total = 0, upd_total = 0, pvec_total = 0;
+    int32_t max_rows = 0;
+
+    // assembly
+    std::vector<AsmGroup> groups;
+    std::vector<AsmChunk> chunks;
+    std::vector<int32_t> asm_idx;
+    std::vector<double> asm_coef;
+
+    // SpMV / vectors
+    std::vector<int64_t> sp_rowptr;
+    std::vector<int32_t> sp_col, sp_slot, row_sys;
+    std::vector<int64_t> sys_n_off;
+    std::vector<uint8_t> shifted;
+
+    // adjoint tables
+    std::vector<int64_t> g_rowptr;
+    std::vector<int32_t> g_colind, g_row_sys, g_rows_all;
+    std::vector<double> g_aval;
+    std::vector<int32_t> e_dofs, e_sys, e_dim, e_elems_all;
+    std::vector<int64_t> e_off, e_k0off;
+    std::vector<double> e_K0;
+
+    // device binding
+    std::vector<uint8_t> blob;   // host image of the device tables
+    struct {
+        size_t fronts, rows, child_ids, relmap, invmap, klist, front_lists, groups, chunks,
+            asm_idx, asm_coef, sp_rowptr, sp_col, sp_slot, perm, row_sys, sys_n_off, g_rowptr,
+            g_colind, g_aval, g_row_sys, e_dofs, e_K0, e_sys, e_off, e_k0off, e_dim, shifted,
+            g_rows_all, e_elems_all;
+    } toff{};
+    WsLayout ws{};
+    uint8_t* d_tab = nullptr;
+    uint8_t* d_ws = nullptr;
+    DevTables dt{};
+    bool bound = false;
+    bool factored = false;
+    int32_t* h_flag = nullptr;  // pinned host word for the refinement loop
+
+    std::string last_error;
+    int64_t launches = 0;
+};
+
+// symbolic phase (ssco_symbolic.cpp)
+ssco_status analyze_impl(const ssco_pattern* const* pats, int32_t n_pats, const ssco_op* op,
+                         Plan& P);
+void build_blob(Plan& P);
+void compute_ws_layout(Plan& P);
+void export_L_pattern(const Plan& P, std::vector<int64_t>* colptr, std::vector<int32_t>* rowind);
+
+// kernels (ssco_kernels.cu); each returns cudaError_t as int
+int launch_numeric(Plan& P, const void* vals, int32_t vals_dtype, const double* shift, void* stream);
+int launch_solve(Plan& P, const double* b, double* x, void* stream, bool* synced_ok);
+int launch_backward(Plan& P, const double* x, const double* xbar, double* vals_bar,
+                    double* shift_bar, double* b_bar, void* stream);
+int launch_reset_status(Plan& P, void* stream);
+int kernels_set_attributes(Plan& P);
+
+}  // namespace ssco

@@ -1,0 +1,931 @@
+// ssco_kernels.cu -- sm_103a kernels of the numeric phase and their launchers.
+//
+// Data layout (all per instance b, instance-outermost):
+//   K      double [B][nnz_K]        assembled values, in assembly-group order
+//   panel  T      [B][panel_total]  factor columns of every front, r x w col-major
+//   upd    T      [B][upd_total]    update matrices, (r-w)^2 col-major (lower used)
+//   pvec   T      [B][pvec_total]   forward-solve passing vectors (r-w per front)
+//   vecT   T      [B][n]            rhs / y / x of the T-precision solves
+//   bp, xp, rr, mu double [B][n]    permuted rhs, solution, residual; adjoint
+// T = double (SSCO_FP64) or float (SSCO_FP32_REFINE).
+//
+// Schedule (host-built): assembly is one launch over all groups (Sec. 4.3/4.4
+// leaf tables, coalesced term-major layout of Sec. 4.8).  The factorization
+// visits the levels of the supernodal forest in increasing height; within a
+// level, fronts are independent (Sec. 4.3 "no group member depends on
+// another") and each size class is one launch.  A front's dense partial
+// factorization is the tagged dense block of Sec. 4.2.4: its update matrix
+// is a global intermediate (Sec. 4.2.1) consumed by its parent through a
+// relative map (address coherence, Sec. 4.8).
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cmath>
+#include <cstdint>
+
+#include "ssco_internal.h"
+
+namespace ssco {
+
+namespace {
+
+constexpr int kSmemMax = 227 * 1024;
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Deterministic block reduction (fixed tree) of a sum and a max; result valid
+// in thread 0.  blockDim.x must be a multiple of 32 and <= 1024.
+__device__ void block_sum_max(double& s, double& mx) {
+    __shared__ double ss[32], sm[32];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    s = warp_sum(s);
+    mx = warp_max(mx);
+    __syncthreads();
+    if (lane == 0) {
+        ss[wid] = s;
+        sm[wid] = mx;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        s = lane < nw ? ss[lane] : 0.0;
+        mx = lane < nw ? sm[lane] : 0.0;
+        s = warp_sum(s);
+        mx = warp_max(mx);
+    }
+}
+
+// --------------------------------------------------------------------------
+// a1: assembly.  K[slot_base+i] = cadd + sum_t c_t vals[idx_t] (+ shift)
+// --------------------------------------------------------------------------
+template <class VT>
+__global__ void __launch_bounds__(256) k_assemble(const AsmGroup* __restrict__ groups,
+                                                  const AsmChunk* __restrict__ chunks,
+                                                  const int32_t* __restrict__ idx,
+                                                  const double* __restrict__ coef,
+                                                  const VT* __restrict__ vals, int64_t m,
+                                                  const double* __restrict__ shift, int32_t n_pats,
+                                                  double* __restrict__ K, int64_t nnzK) {
+    const AsmChunk ch = chunks[blockIdx.x];
+    const AsmGroup g = groups[ch.group];
+    const int i = ch.start + (int)threadIdx.x;
+    if (i >= g.nmem) return;
+    const int b = blockIdx.y;
+    const VT* v = vals + (int64_t)b * m;
+    const int32_t* ix = idx + g.idx_off + i;
+    double acc = g.cadd;
+    if (g.uniform) {
+        double s = 0.0;
+        for (int t = 0; t < g.nterms; ++t) s += (double)v[ix[(int64_t)t * g.nmem]];
+        acc += g.coef * s;
+    } else {
+        const double* cx = coef + g.coef_off + i;
+        for (int t = 0; t < g.nterms; ++t) acc += cx[(int64_t)t * g.nmem] * (double)v[ix[(int64_t)t * g.nmem]];
+    }
+    if (g.diag) acc += shift[(int64_t)b * n_pats + g.sys];
+    K[(int64_t)b * nnzK + g.slot_base + i] = acc;
+}
+
+__global__ void k_fill_i32(int32_t* p, int64_t n, int32_t v) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+
+// --------------------------------------------------------------------------
+// a3: small fronts, one CTA per (front, instance), front resident in shared
+// memory: gather K, extend-add children, partial Cholesky, write panel+update.
+// --------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(256) k_front_small(const DevTables t, const int32_t* __restrict__ list,
+                                                     const double* __restrict__ K, int64_t nnzK,
+                                                     T* __restrict__ panel, int64_t panel_total,
+                                                     T* __restrict__ upd, int64_t upd_total,
+                                                     int32_t* __restrict__ bad_col, int32_t n_pats) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* F = reinterpret_cast<T*>(smem_raw);
+    const FrontDesc d = t.fronts[list[blockIdx.x]];
+    const int b = blockIdx.y;
+    const int r = d.r, w = d.w;
+    const int lane = threadIdx.x, warp = threadIdx.y, nw = blockDim.y;
+    const int tid = lane + 32 * warp, nth = 32 * nw;
+    for (int q = tid; q < r * r; q += nth) F[q] = T(0);
+    __syncthreads();
+    const double* Kb = K + (int64_t)b * nnzK;
+    const int32_t* kl = t.klist + 2 * d.klist_off;
+    for (int q = tid; q < d.klist_n; q += nth) F[kl[2 * q + 1]] = (T)Kb[kl[2 * q]];
+    for (int c = 0; c < d.nchild; ++c) {
+        __syncthreads();
+        const FrontDesc cd = t.fronts[t.child_ids[d.child_off + c]];
+        const int rc = cd.r - cd.w;
+        const int32_t* map = t.relmap + cd.relmap_off;
+        const T* S = upd + (int64_t)b * upd_total + cd.upd_off;
+        for (int kk = warp; kk < rc; kk += nw) {
+            const int mk = map[kk] * r;
+            const T* Sk = S + (int64_t)kk * rc;
+            for (int ii = kk + lane; ii < rc; ii += 32) F[map[ii] + mk] += Sk[ii];
+        }
+    }
+    __syncthreads();
+    // right-looking partial factorization; column j is scaled one step late so
+    // that a single barrier per column suffices.
+    T prev_inv = T(1), prev_l = T(1);
+    bool failed = false;
+    for (int j = 0; j < w; ++j) {
+        T djj = F[j + j * r];
+        if (!(djj > T(0))) {
+            if (tid == 0 && !failed) atomicMin(&bad_col[(int64_t)b * n_pats + d.sys], d.f + j - (int)t.sys_n_off[d.sys]);
+            failed = true;
+            djj = T(1);
+        }
+        const T invd = T(1) / djj;
+        if (j > 0) {
+            for (int i = j + tid; i < r; i += nth) F[i + (j - 1) * r] *= prev_inv;
+            if (tid == 0) F[(j - 1) + (j - 1) * r] = prev_l;
+        }
+        for (int k = j + 1 + warp; k < r; k += nw) {
+            const T lk = F[k + j * r] * invd;
+            T* Fk = F + k * r;
+            const T* Fj = F + j * r;
+            for (int i = k + lane; i < r; i += 32) Fk[i] -= Fj[i] * lk;
+        }
+        prev_l = sqrt(djj);
+        prev_inv = T(1) / prev_l;
+        __syncthreads();
+    }
+    if (w > 0) {
+        const int j = w - 1;
+        for (int i = j + 1 + tid; i < r; i += nth) F[i + j * r] *= prev_inv;
+        if (tid == 0) F[j + j * r] = prev_l;
+    }
+    __syncthreads();
+    T* Pb = panel + (int64_t)b * panel_total + d.panel_off;
+    for (int jj = warp; jj < w; jj += nw)
+        for (int i = lane; i < r; i += 32) Pb[(int64_t)jj * r + i] = i >= jj ? F[i + jj * r] : T(0);
+    const int ru = r - w;
+    if (ru > 0) {
+        T* Ub = upd + (int64_t)b * upd_total + d.upd_off;
+        for (int kk = warp; kk < ru; kk += nw)
+            for (int ii = kk + lane; ii < ru; ii += 32) Ub[(int64_t)kk * ru + ii] = F[(w + ii) + (w + kk) * r];
+    }
+}
+
+// --------------------------------------------------------------------------
+// a4: big fronts (r > small_front_max), dense panel in global memory.
+// --------------------------------------------------------------------------
+// Panel and update initialised from the children's update matrices through
+// inverse maps (pull, fixed child order => deterministic, no atomics).
+template <class T>
+__global__ void __launch_bounds__(256) k_big_init(const DevTables t, const int32_t* __restrict__ list,
+                                                  T* __restrict__ panel, int64_t panel_total,
+                                                  T* __restrict__ upd, int64_t upd_total) {
+    const FrontDesc d = t.fronts[list[blockIdx.y]];
+    const int b = blockIdx.z;
+    const int r = d.r, w = d.w;
+    const int64_t nt = (r + 31) / 32;
+    const int64_t tile = blockIdx.x;
+    if (tile >= nt * (nt + 1) / 2) return;
+    int64_t ti = (int64_t)((sqrt(8.0 * (double)tile + 1.0) - 1.0) * 0.5);
+    while (ti * (ti + 1) / 2 > tile) --ti;
+    while ((ti + 1) * (ti + 2) / 2 <= tile) ++ti;
+    const int64_t tj = tile - ti * (ti + 1) / 2;
+    const int i = (int)(ti * 32) + threadIdx.x;
+    T* Pb = panel + (int64_t)b * panel_total + d.panel_off;
+    T* Ub = upd + (int64_t)b * upd_total + d.upd_off;
+    const int ru = r - w;
+    for (int jj = threadIdx.y; jj < 32; jj += blockDim.y) {
+        const int j = (int)(tj * 32) + jj;
+        if (i >= r || j >= r || i < j) continue;
+        T acc = T(0);
+        for (int c = 0; c < d.nchild; ++c) {
+            const int32_t* inv = t.invmap + d.inv_off + (int64_t)c * r;
+            const int a = inv[i], bb = inv[j];
+            if (a >= 0 && bb >= 0) {
+                const FrontDesc cd = t.fronts[t.child_ids[d.child_off + c]];
+                const int rc = cd.r - cd.w;
+                acc += upd[(int64_t)b * upd_total + cd.upd_off + (int64_t)bb * rc + a];
+            }
+        }
+        if (j < w)
+            Pb[(int64_t)j * r + i] = acc;
+        else
+            Ub[(int64_t)(j - w) * ru + (i - w)] = acc;
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_big_kscatter(const DevTables t, const int32_t* __restrict__ list,
+                                                      const double* __restrict__ K, int64_t nnzK,
+                                                      T* __restrict__ panel, int64_t panel_total) {
+    const FrontDesc d = t.fronts[list[blockIdx.y]];
+    const int b = blockIdx.z;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= d.klist_n) return;
+    const int32_t* kl = t.klist + 2 * (d.klist_off + q);
+    panel[(int64_t)b * panel_total + d.panel_off + kl[1]] += (T)K[(int64_t)b * nnzK + kl[0]];
+}
+
+// Left-looking block update of panel column block kb (nb = 32 columns):
+// P[c0:r, c0:c0+nbk] -= P[c0:r, 0:c0] * P[c0:c0+nbk, 0:c0]^T.
+// CTA tile 64 rows x 32 columns, 256 threads, 4x2 outputs per thread.
+template <class T>
+__global__ void __launch_bounds__(256) k_big_gemm(const DevTables t, const int32_t* __restrict__ list, int kb,
+                                                  T* __restrict__ panel, int64_t panel_total) {
+    const FrontDesc d = t.fronts[list[blockIdx.y]];
+    const int b = blockIdx.z;
+    const int r = d.r, w = d.w;
+    const int c0 = kb * 32;
+    if (c0 >= w) return;
+    const int nbk = min(32, w - c0);
+    const int row0 = c0 + blockIdx.x * 64;
+    if (row0 >= r) return;
+    T* Pb = panel + (int64_t)b * panel_total + d.panel_off;
+    __shared__ T As[16][64 + 1];
+    __shared__ T Bs[16][32 + 1];
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    T acc[4][2];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) acc[a][0] = acc[a][1] = T(0);
+    for (int k0 = 0; k0 < c0; k0 += 16) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = tid + q * 256;
+            const int mm = e & 63, kk = e >> 6;
+            const int row = row0 + mm, col = k0 + kk;
+            As[kk][mm] = (row < r && col < c0) ? Pb[(int64_t)col * r + row] : T(0);
+        }
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int e = tid + q * 256;
+            const int nn = e & 31, kk = e >> 5;
+            const int row = c0 + nn, col = k0 + kk;
+            Bs[kk][nn] = (nn < nbk && col < c0) ? Pb[(int64_t)col * r + row] : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            T a[4], bv[2];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) a[q] = As[kk][tx * 4 + q];
+            bv[0] = Bs[kk][ty * 2];
+            bv[1] = Bs[kk][ty * 2 + 1];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                acc[q][0] += a[q] * bv[0];
+                acc[q][1] += a[q] * bv[1];
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            const int row = row0 + tx * 4 + q, cl = ty * 2 + p;
+            if (row < r && cl < nbk && row >= c0 + cl) Pb[(int64_t)(c0 + cl) * r + row] -= acc[q][p];
+        }
+}
+
+// Factor the diagonal block of column block kb (every CTA redundantly, in
+// shared memory) and solve the rows below: X = P[rows, blk] L_kk^{-T}.
+// blockIdx.x == 0 writes the diagonal block; blockIdx.x >= 1 handles 256 rows.
+template <class T>
+__global__ void __launch_bounds__(256) k_big_potrf_trsm(const DevTables t, const int32_t* __restrict__ list, int kb,
+                                                        T* __restrict__ panel, int64_t panel_total,
+                                                        int32_t* __restrict__ bad_col, int32_t n_pats) {
+    const FrontDesc d = t.fronts[list[blockIdx.y]];
+    const int b = blockIdx.z;
+    const int r = d.r, w = d.w;
+    const int c0 = kb * 32;
+    if (c0 >= w) return;
+    const int nbk = min(32, w - c0);
+    const int rbeg = c0 + nbk + ((int)blockIdx.x - 1) * 256;
+    if (blockIdx.x > 0 && rbeg >= r) return;
+    T* Pb = panel + (int64_t)b * panel_total + d.panel_off;
+    __shared__ T Ld[32][33];
+    const int tid = threadIdx.x;
+    for (int e = tid; e < 32 * 32; e += 256) {
+        const int i = e & 31, j = e >> 5;
+        Ld[i][j] = (i < nbk && j <= i) ? Pb[(int64_t)(c0 + j) * r + c0 + i] : T(0);
+    }
+    __syncthreads();
+    if (tid < 32) {
+        const int i = tid;
+        bool failed = false;
+        for (int j = 0; j < nbk; ++j) {
+            T djj = Ld[j][j];
+            __syncwarp();
+            if (!(djj > T(0))) {
+                if (i == 0 && blockIdx.x == 0 && !failed)
+                    atomicMin(&bad_col[(int64_t)b * n_pats + d.sys], d.f + c0 + j - (int)t.sys_n_off[d.sys]);
+                failed = true;
+                djj = T(1);
+            }
+            const T ljj = sqrt(djj);
+            if (i > j && i < nbk) Ld[i][j] /= ljj;
+            if (i == j) Ld[j][j] = ljj;
+            __syncwarp();
+            if (i > j && i < nbk) {
+                const T lij = Ld[i][j];
+                for (int k = j + 1; k <= i; ++k) Ld[i][k] -= lij * Ld[k][j];
+            }
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    if (blockIdx.x == 0) {
+        for (int e = tid; e < 32 * 32; e += 256) {
+            const int i = e & 31, j = e >> 5;
+            if (i < nbk && j <= i) Pb[(int64_t)(c0 + j) * r + c0 + i] = Ld[i][j];
+        }
+        return;
+    }
+    const int row = rbeg + tid;
+    if (row >= r) return;
+    T x[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) x[j] = j < nbk ? Pb[(int64_t)(c0 + j) * r + row] : T(0);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        if (j < nbk) {
+            T s = x[j];
+#pragma unroll
+            for (int l = 0; l < j; ++l) s -= x[l] * Ld[j][l];
+            x[j] = s / Ld[j][j];
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+        if (j < nbk) Pb[(int64_t)(c0 + j) * r + row] = x[j];
+}
+
+// Update matrix of a big front: U(lower) -= L21 L21^T, L21 = P[w:r, 0:w].
+// CTA tile 64x64 of U's lower triangle, 256 threads, 4x4 per thread.
+template <class T>
+__global__ void __launch_bounds__(256) k_big_syrk(const DevTables t, const int32_t* __restrict__ list,
+                                                  const T* __restrict__ panel, int64_t panel_total,
+                                                  T* __restrict__ upd, int64_t upd_total) {
+    const FrontDesc d = t.fronts[list[blockIdx.y]];
+    const int b = blockIdx.z;
+    const int r = d.r, w = d.w, ru = r - w;
+    if (ru <= 0) return;
+    const int64_t nt = (ru + 63) / 64;
+    const int64_t tile = blockIdx.x;
+    if (tile >= nt * (nt + 1) / 2) return;
+    int64_t ti = (int64_t)((sqrt(8.0 * (double)tile + 1.0) - 1.0) * 0.5);
+    while (ti * (ti + 1) / 2 > tile) --ti;
+    while ((ti + 1) * (ti + 2) / 2 <= tile) ++ti;
+    const int64_t tj = tile - ti * (ti + 1) / 2;
+    const T* Pb = panel + (int64_t)b * panel_total + d.panel_off;
+    T* Ub = upd + (int64_t)b * upd_total + d.upd_off;
+    __shared__ T As[16][64 + 1];
+    __shared__ T Bs[16][64 + 1];
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    const int i0 = (int)ti * 64, j0 = (int)tj * 64;
+    T acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[a][c] = T(0);
+    for (int k0 = 0; k0 < w; k0 += 16) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = tid + q * 256;
+            const int mm = e & 63, kk = e >> 6;
+            const int col = k0 + kk;
+            const int ra = i0 + mm, rb = j0 + mm;
+            As[kk][mm] = (ra < ru && col < w) ? Pb[(int64_t)col * r + w + ra] : T(0);
+            Bs[kk][mm] = (rb < ru && col < w) ? Pb[(int64_t)col * r + w + rb] : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            T a[4], bv[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                a[q] = As[kk][tx * 4 + q];
+                bv[q] = Bs[kk][ty * 4 + q];
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int p = 0; p < 4; ++p) acc[q][p] += a[q] * bv[p];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            const int i = i0 + tx * 4 + q, j = j0 + ty * 4 + p;
+            if (i < ru && j < ru && i >= j) Ub[(int64_t)j * ru + i] -= acc[q][p];
+        }
+}
+
+// --------------------------------------------------------------------------
+// a5: level-scheduled solves, one CTA per (front, instance).
+// --------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(256) k_fwd(const DevTables t, const int32_t* __restrict__ list,
+                                             const T* __restrict__ panel, int64_t panel_total,
+                                             T* __restrict__ vec, int64_t n, T* __restrict__ pvec,
+                                             int64_t pvec_total, const int32_t* __restrict__ active,
+                                             int32_t n_pats) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* v = reinterpret_cast<T*>(smem_raw);
+    __shared__ T yblk[32];
+    const FrontDesc d = t.fronts[list[blockIdx.x]];
+    const int b = blockIdx.y;
+    if (active && !active[(int64_t)b * n_pats + d.sys]) return;
+    const int r = d.r, w = d.w;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    T* vb = vec + (int64_t)b * n;
+    const T* Pb = panel + (int64_t)b * panel_total + d.panel_off;
+    T* pv = pvec + (int64_t)b * pvec_total;
+    for (int k = tid; k < r; k += nth) v[k] = k < w ? vb[d.f + k] : T(0);
+    for (int c = 0; c < d.nchild; ++c) {
+        __syncthreads();
+        const FrontDesc cd = t.fronts[t.child_ids[d.child_off + c]];
+        const int rc = cd.r - cd.w;
+        const int32_t* map = t.relmap + cd.relmap_off;
+        for (int k = tid; k < rc; k += nth) v[map[k]] += pv[cd.pvec_off + k];
+    }
+    __syncthreads();
+    for (int jb = 0; jb < w; jb += 32) {
+        const int nbk = min(32, w - jb);
+        if (tid < 32) {
+            const int l = tid;
+            T val = l < nbk ? v[jb + l] : T(0);
+            for (int j = 0; j < nbk; ++j) {
+                const T yj = __shfl_sync(0xffffffffu, val, j) / Pb[(int64_t)(jb + j) * r + jb + j];
+                if (l == j) val = yj;
+                if (l > j && l < nbk) val -= Pb[(int64_t)(jb + j) * r + jb + l] * yj;
+            }
+            if (l < nbk) {
+                v[jb + l] = val;
+                yblk[l] = val;
+            }
+        }
+        __syncthreads();
+        for (int i = jb + nbk + tid; i < r; i += nth) {
+            T s = T(0);
+            for (int j = 0; j < nbk; ++j) s += Pb[(int64_t)(jb + j) * r + i] * yblk[j];
+            v[i] -= s;
+        }
+        __syncthreads();
+    }
+    for (int k = tid; k < w; k += nth) vb[d.f + k] = v[k];
+    for (int k = tid; k < r - w; k += nth) pv[d.pvec_off + k] = v[w + k];
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_bwd(const DevTables t, const int32_t* __restrict__ list,
+                                             const T* __restrict__ panel, int64_t panel_total,
+                                             T* __restrict__ vec, int64_t n, const int32_t* __restrict__ active,
+                                             int32_t n_pats) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* v = reinterpret_cast<T*>(smem_raw);
+    __shared__ T dots[32];
+    const FrontDesc d = t.fronts[list[blockIdx.x]];
+    const int b = blockIdx.y;
+    if (active && !active[(int64_t)b * n_pats + d.sys]) return;
+    const int r = d.r, w = d.w;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nw = nth >> 5;
+    T* vb = vec + (int64_t)b * n;
+    const T* Pb = panel + (int64_t)b * panel_total + d.panel_off;
+    const int32_t* rows = t.rows + d.rows_off;
+    for (int k = tid; k < r; k += nth) v[k] = k < w ? vb[d.f + k] : vb[rows[k]];
+    __syncthreads();
+    const int nblk = (w + 31) / 32;
+    for (int bi = nblk - 1; bi >= 0; --bi) {
+        const int jb = bi * 32;
+        const int nbk = min(32, w - jb);
+        for (int c = warp; c < nbk; c += nw) {
+            const T* col = Pb + (int64_t)(jb + c) * r;
+            T s = T(0);
+            for (int i = jb + nbk + lane; i < r; i += 32) s += col[i] * v[i];
+            s = warp_sum(s);
+            if (lane == 0) dots[c] = s;
+        }
+        __syncthreads();
+        if (tid < 32) {
+            const int l = tid;
+            T val = l < nbk ? v[jb + l] - dots[l] : T(0);
+            for (int j = nbk - 1; j >= 0; --j) {
+                const T xj = __shfl_sync(0xffffffffu, val, j) / Pb[(int64_t)(jb + j) * r + jb + j];
+                if (l == j) val = xj;
+                if (l < j) val -= Pb[(int64_t)(jb + l) * r + jb + j] * xj;
+            }
+            if (l < nbk) v[jb + l] = val;
+        }
+        __syncthreads();
+    }
+    for (int k = tid; k < w; k += nth) vb[d.f + k] = v[k];
+}
+
+// --------------------------------------------------------------------------
+// a6: vectors, residual and refinement control (FP64)
+// --------------------------------------------------------------------------
+__global__ void k_permute_in(const double* __restrict__ bu, const int32_t* __restrict__ perm, int64_t n,
+                             double* __restrict__ bp) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t o = (int64_t)blockIdx.y * n;
+    bp[o + i] = bu[o + perm[i]];
+}
+
+__global__ void k_permute_out(const double* __restrict__ xp, const int32_t* __restrict__ perm, int64_t n,
+                              double* __restrict__ xu) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t o = (int64_t)blockIdx.y * n;
+    xu[o + perm[i]] = xp[o + i];
+}
+
+template <class T>
+__global__ void k_to_T(const double* __restrict__ src, T* __restrict__ dst, int64_t total) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < total) dst[i] = (T)src[i];
+}
+
+template <class T>
+__global__ void k_from_T(const T* __restrict__ src, double* __restrict__ dst, int64_t total) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < total) dst[i] = (double)src[i];
+}
+
+// per-system init: ||b||_2, counters
+__global__ void k_sys_init(const double* __restrict__ bp, const int64_t* __restrict__ sys_n_off, int32_t n_pats,
+                           int64_t n, double* __restrict__ bnorm, int32_t* __restrict__ active,
+                           int32_t* __restrict__ sstatus, int32_t* __restrict__ iters, double* __restrict__ resid,
+                           double* __restrict__ r1, double* __restrict__ r2) {
+    const int s = blockIdx.x;
+    const int b = s / n_pats, k = s % n_pats;
+    const double* v = bp + (int64_t)b * n;
+    double sum = 0.0, mx = 0.0;
+    for (int64_t i = sys_n_off[k] + threadIdx.x; i < sys_n_off[k + 1]; i += blockDim.x) sum += v[i] * v[i];
+    block_sum_max(sum, mx);
+    if (threadIdx.x == 0) {
+        bnorm[s] = sqrt(sum);
+        active[s] = 1;
+        sstatus[s] = SSCO_OK;
+        iters[s] = 0;
+        resid[s] = 0.0;
+        r1[s] = INFINITY;
+        r2[s] = INFINITY;
+    }
+}
+
+// rr = bp - K~ xp, symmetric CSR over permuted rows
+__global__ void __launch_bounds__(256) k_resid(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                               const int32_t* __restrict__ slot, const double* __restrict__ K,
+                                               int64_t nnzK, const double* __restrict__ bp,
+                                               const double* __restrict__ xp, double* __restrict__ rr, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int b = blockIdx.y;
+    const double* Kb = K + (int64_t)b * nnzK;
+    const double* xb = xp + (int64_t)b * n;
+    double s = 0.0;
+    for (int64_t q = rp[i]; q < rp[i + 1]; ++q) s += Kb[slot[q]] * xb[col[q]];
+    rr[(int64_t)b * n + i] = bp[(int64_t)b * n + i] - s;
+}
+
+// residual test and refinement decision for one system per CTA
+__global__ void k_check(const double* __restrict__ rr, const int64_t* __restrict__ sys_n_off, int32_t n_pats,
+                        int64_t n, const double* __restrict__ bnorm, int32_t* __restrict__ active,
+                        int32_t* __restrict__ sstatus, int32_t* __restrict__ iters, double* __restrict__ resid,
+                        double* __restrict__ r1, double* __restrict__ r2, double* __restrict__ sigma,
+                        int32_t* __restrict__ any_active, int it, int maxit, double tol, int refine) {
+    const int s = blockIdx.x;
+    if (!active[s]) return;
+    const int b = s / n_pats, k = s % n_pats;
+    const double* v = rr + (int64_t)b * n;
+    double sum = 0.0, mx = 0.0;
+    for (int64_t i = sys_n_off[k] + threadIdx.x; i < sys_n_off[k + 1]; i += blockDim.x) {
+        const double a = v[i];
+        sum += a * a;
+        mx = fmax(mx, fabs(a));
+        if (!(fabs(a) <= 1.7976931348623157e308)) mx = INFINITY;
+    }
+    block_sum_max(sum, mx);
+    if (threadIdx.x != 0) return;
+    const double rn = sqrt(sum);
+    const double bn = bnorm[s];
+    double res = bn > 0.0 ? rn / bn : (rn > 0.0 ? INFINITY : 0.0);
+    if (!(mx <= 1.7976931348623157e308)) res = NAN;
+    resid[s] = res;
+    iters[s] = it;
+    int act = 0;
+    if (!(res == res) || isinf(res)) {
+        sstatus[s] = SSCO_ERR_NONFINITE;
+    } else if (res <= tol) {
+        sstatus[s] = SSCO_OK;
+    } else if (!refine || it >= maxit || (it >= 2 && res > 0.5 * r2[s])) {
+        sstatus[s] = SSCO_ERR_NO_CONVERGE;
+    } else {
+        act = 1;
+        sigma[s] = mx;
+    }
+    active[s] = act;
+    r2[s] = r1[s];
+    r1[s] = res;
+    if (act) atomicAdd(any_active, 1);
+}
+
+template <class T>
+__global__ void k_cast_scaled(const double* __restrict__ rr, const int32_t* __restrict__ row_sys, int32_t n_pats,
+                              int64_t n, const int32_t* __restrict__ active, const double* __restrict__ sigma,
+                              T* __restrict__ vecT) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int b = blockIdx.y;
+    const int s = b * n_pats + row_sys[i];
+    const int64_t o = (int64_t)b * n + i;
+    vecT[o] = active[s] ? (T)(rr[o] / sigma[s]) : T(0);
+}
+
+template <class T>
+__global__ void k_update(const T* __restrict__ vecT, const int32_t* __restrict__ row_sys, int32_t n_pats, int64_t n,
+                         const int32_t* __restrict__ active, const double* __restrict__ sigma,
+                         double* __restrict__ xp) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int b = blockIdx.y;
+    const int s = b * n_pats + row_sys[i];
+    const int64_t o = (int64_t)b * n + i;
+    if (active[s]) xp[o] += sigma[s] * (double)vecT[o];
+}
+
+// --------------------------------------------------------------------------
+// a7: adjoint reductions (original ordering)
+// --------------------------------------------------------------------------
+__global__ void k_grad_atwa(const DevTables t, int64_t nrows, const double* __restrict__ mu,
+                            const double* __restrict__ x, int64_t n, double* __restrict__ vbar, int64_t m) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= nrows) return;
+    const int b = blockIdx.y;
+    const double* mb = mu + (int64_t)b * n;
+    const double* xb = x + (int64_t)b * n;
+    double am = 0.0, ax = 0.0;
+    for (int64_t q = t.g_rowptr[g]; q < t.g_rowptr[g + 1]; ++q) {
+        const double a = t.g_aval[q];
+        am += a * mb[t.g_colind[q]];
+        ax += a * xb[t.g_colind[q]];
+    }
+    vbar[(int64_t)b * m + t.g_rows_all[g]] = -am * ax;
+}
+
+__global__ void k_grad_elem(const DevTables t, int64_t nelem, const double* __restrict__ mu,
+                            const double* __restrict__ x, int64_t n, double* __restrict__ vbar, int64_t m) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= nelem) return;
+    const int b = blockIdx.y;
+    const double* mb = mu + (int64_t)b * n;
+    const double* xb = x + (int64_t)b * n;
+    const int dim = t.e_dim[g];
+    const int32_t* dofs = t.e_dofs + t.e_off[g];
+    const double* K0 = t.e_K0 + t.e_k0off[g];
+    double acc = 0.0;
+    int p = 0;
+    for (int i = 0; i < dim; ++i) {
+        const int u = dofs[i];
+        for (int j = 0; j <= i; ++j, ++p) {
+            const int v = dofs[j];
+            if (u < 0 || v < 0) continue;
+            double c = mb[u] * xb[v];
+            if (i != j) c += mb[v] * xb[u];
+            acc += K0[p] * c;
+        }
+    }
+    vbar[(int64_t)b * m + t.e_elems_all[g]] = -acc;
+}
+
+__global__ void k_shift_bar(const DevTables t, int32_t n_pats, int64_t n, const double* __restrict__ mu,
+                            const double* __restrict__ x, double* __restrict__ sbar) {
+    const int s = blockIdx.x;
+    const int b = s / n_pats, k = s % n_pats;
+    const double* mb = mu + (int64_t)b * n;
+    const double* xb = x + (int64_t)b * n;
+    double sum = 0.0, mx = 0.0;
+    for (int64_t i = t.sys_n_off[k] + threadIdx.x; i < t.sys_n_off[k + 1]; i += blockDim.x)
+        if (t.shifted[i]) {
+            const int o = t.perm[i];
+            sum += mb[o] * xb[o];
+        }
+    block_sum_max(sum, mx);
+    if (threadIdx.x == 0) sbar[s] = -sum;
+}
+
+// --------------------------------------------------------------------------
+inline unsigned cdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
+
+template <class T>
+T* wsp(Plan& P, size_t off) {
+    return reinterpret_cast<T*>(P.d_ws + off);
+}
+
+template <class T>
+int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cudaStream_t s) {
+    const int B = P.B;
+    const int64_t S = (int64_t)B * P.n_pats;
+    double* K = wsp<double>(P, P.ws.K);
+    T* panel = wsp<T>(P, P.ws.panel);
+    T* upd = wsp<T>(P, P.ws.upd);
+    int32_t* bad = wsp<int32_t>(P, P.ws.bad_col);
+    k_fill_i32<<<cdiv(S, 256), 256, 0, s>>>(bad, S, INT_MAX);
+    P.launches++;
+    if (!P.chunks.empty()) {
+        dim3 g((unsigned)P.chunks.size(), B);
+        if (vdt == SSCO_VALS_F64)
+            k_assemble<double><<<g, 256, 0, s>>>(P.dt.groups, P.dt.chunks, P.dt.asm_idx, P.dt.asm_coef,
+                                                 (const double*)vals, P.m, shift, P.n_pats, K, P.nnzK);
+        else
+            k_assemble<float><<<g, 256, 0, s>>>(P.dt.groups, P.dt.chunks, P.dt.asm_idx, P.dt.asm_coef,
+                                                (const float*)vals, P.m, shift, P.n_pats, K, P.nnzK);
+        P.launches++;
+    }
+    for (const LaunchList& ll : P.fact_launches) {
+        const int32_t* list = P.dt.front_lists + ll.list_off;
+        if (ll.cls > 0) {
+            const int nw = ll.cls <= 32 ? 2 : (ll.cls <= 64 ? 4 : 8);
+            const size_t smem = (size_t)ll.rmax * ll.rmax * sizeof(T);
+            k_front_small<T><<<dim3(ll.count, B), dim3(32, nw), smem, s>>>(P.dt, list, K, P.nnzK, panel,
+                                                                           P.panel_total, upd, P.upd_total, bad,
+                                                                           P.n_pats);
+            P.launches++;
+        } else {
+            k_big_init<T><<<dim3((unsigned)ll.max_lower_tiles, ll.count, B), dim3(32, 8), 0, s>>>(
+                P.dt, list, panel, P.panel_total, upd, P.upd_total);
+            k_big_kscatter<T><<<dim3(cdiv(ll.max_klist, 256), ll.count, B), 256, 0, s>>>(P.dt, list, K, P.nnzK,
+                                                                                       panel, P.panel_total);
+            P.launches += 2;
+            const int nkb = (ll.wmax + 31) / 32;
+            for (int kb = 0; kb < nkb; ++kb) {
+                if (kb > 0) {
+                    k_big_gemm<T><<<dim3(cdiv(ll.rmax - kb * 32, 64), ll.count, B), 256, 0, s>>>(
+                        P.dt, list, kb, panel, P.panel_total);
+                    P.launches++;
+                }
+                k_big_potrf_trsm<T><<<dim3(1 + cdiv(ll.rmax, 256), ll.count, B), 256, 0, s>>>(
+                    P.dt, list, kb, panel, P.panel_total, bad, P.n_pats);
+                P.launches++;
+            }
+            if (ll.max_syrk_tiles > 0) {
+                k_big_syrk<T><<<dim3((unsigned)ll.max_syrk_tiles, ll.count, B), 256, 0, s>>>(
+                    P.dt, list, panel, P.panel_total, upd, P.upd_total);
+                P.launches++;
+            }
+        }
+    }
+    return (int)cudaGetLastError();
+}
+
+template <class T>
+void run_trisolve(Plan& P, const int32_t* active, cudaStream_t s) {
+    const int B = P.B;
+    T* panel = wsp<T>(P, P.ws.panel);
+    T* vecT = wsp<T>(P, P.ws.vecT);
+    T* pvec = wsp<T>(P, P.ws.pvec);
+    for (const LaunchList& ll : P.solve_launches) {
+        const size_t smem = (size_t)ll.rmax * sizeof(T);
+        k_fwd<T><<<dim3(ll.count, B), 256, smem, s>>>(P.dt, P.dt.front_lists + ll.list_off, panel, P.panel_total,
+                                                        vecT, P.n, pvec, P.pvec_total, active, P.n_pats);
+        P.launches++;
+    }
+    for (auto it = P.solve_launches.rbegin(); it != P.solve_launches.rend(); ++it) {
+        const LaunchList& ll = *it;
+        const size_t smem = (size_t)ll.rmax * sizeof(T);
+        k_bwd<T><<<dim3(ll.count, B), 256, smem, s>>>(P.dt, P.dt.front_lists + ll.list_off, panel, P.panel_total,
+                                                        vecT, P.n, active, P.n_pats);
+        P.launches++;
+    }
+}
+
+// x = K^-1 b for all systems (b, x device, original ordering)
+template <class T>
+int run_solve(Plan& P, const double* b, double* x, cudaStream_t s) {
+    const int B = P.B;
+    const int64_t n = P.n, S = (int64_t)B * P.n_pats;
+    double* bp = wsp<double>(P, P.ws.bp);
+    double* xp = wsp<double>(P, P.ws.xp);
+    double* rr = wsp<double>(P, P.ws.rr);
+    T* vecT = wsp<T>(P, P.ws.vecT);
+    int32_t* active = wsp<int32_t>(P, P.ws.active);
+    int32_t* sst = wsp<int32_t>(P, P.ws.sstatus);
+    int32_t* iters = wsp<int32_t>(P, P.ws.iters);
+    int32_t* anyp = wsp<int32_t>(P, P.ws.any_active);
+    double* resid = wsp<double>(P, P.ws.resid);
+    double* bnorm = wsp<double>(P, P.ws.bnorm);
+    double* r1 = wsp<double>(P, P.ws.r1);
+    double* r2 = wsp<double>(P, P.ws.r2);
+    double* sigma = wsp<double>(P, P.ws.sigma);
+    const double* K = wsp<double>(P, P.ws.K);
+    const dim3 gv(cdiv(n, 256), B);
+    const int refine = P.prec == SSCO_FP32_REFINE;
+    k_permute_in<<<gv, 256, 0, s>>>(b, P.dt.perm, n, bp);
+    k_sys_init<<<(unsigned)S, 256, 0, s>>>(bp, P.dt.sys_n_off, P.n_pats, n, bnorm, active, sst, iters, resid, r1, r2);
+    k_to_T<T><<<cdiv((int64_t)B * n, 256), 256, 0, s>>>(bp, vecT, (int64_t)B * n);
+    P.launches += 3;
+    run_trisolve<T>(P, nullptr, s);
+    k_from_T<T><<<cdiv((int64_t)B * n, 256), 256, 0, s>>>(vecT, xp, (int64_t)B * n);
+    P.launches++;
+    for (int it = 0;; ++it) {
+        k_resid<<<gv, 256, 0, s>>>(P.dt.sp_rowptr, P.dt.sp_col, P.dt.sp_slot, K, P.nnzK, bp, xp, rr, n);
+        cudaMemsetAsync(anyp, 0, 4, s);
+        k_check<<<(unsigned)S, 256, 0, s>>>(rr, P.dt.sys_n_off, P.n_pats, n, bnorm, active, sst, iters, resid, r1, r2,
+                                            sigma, anyp, it, P.maxit, P.tol, refine);
+        P.launches += 2;
+        if (!refine) break;
+        int e = (int)cudaMemcpyAsync(P.h_flag, anyp, 4, cudaMemcpyDeviceToHost, s);
+        if (!e) e = (int)cudaStreamSynchronize(s);
+        if (e) return e;
+        if (*P.h_flag == 0) break;
+        k_cast_scaled<T><<<gv, 256, 0, s>>>(rr, P.dt.row_sys, P.n_pats, n, active, sigma, vecT);
+        P.launches++;
+        run_trisolve<T>(P, active, s);
+        k_update<T><<<gv, 256, 0, s>>>(vecT, P.dt.row_sys, P.n_pats, n, active, sigma, xp);
+        P.launches++;
+    }
+    k_permute_out<<<gv, 256, 0, s>>>(xp, P.dt.perm, n, x);
+    P.launches++;
+    return (int)cudaGetLastError();
+}
+
+template <class T>
+void set_attr_T() {
+    cudaFuncSetAttribute(k_front_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
+    cudaFuncSetAttribute(k_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax - 1024);
+    cudaFuncSetAttribute(k_bwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax - 1024);
+}
+
+}  // namespace
+
+int kernels_set_attributes(Plan& P) {
+    if (P.tsize == 8)
+        set_attr_T<double>();
+    else
+        set_attr_T<float>();
+    return (int)cudaGetLastError();
+}
+
+int launch_reset_status(Plan& P, void* stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t S = (int64_t)P.B * P.n_pats;
+    k_fill_i32<<<cdiv(S, 256), 256, 0, s>>>(wsp<int32_t>(P, P.ws.bad_col), S, INT_MAX);
+    k_fill_i32<<<cdiv(S, 256), 256, 0, s>>>(wsp<int32_t>(P, P.ws.sstatus), S, SSCO_OK);
+    k_fill_i32<<<cdiv(S, 256), 256, 0, s>>>(wsp<int32_t>(P, P.ws.iters), S, 0);
+    cudaMemsetAsync(P.d_ws + P.ws.resid, 0, (size_t)S * 8, s);
+    return (int)cudaGetLastError();
+}
+
+int launch_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, void* stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    return P.tsize == 8 ? run_numeric<double>(P, vals, vdt, shift, s) : run_numeric<float>(P, vals, vdt, shift, s);
+}
+
+int launch_solve(Plan& P, const double* b, double* x, void* stream, bool* ok) {
+    cudaStream_t s = (cudaStream_t)stream;
+    *ok = true;
+    return P.tsize == 8 ? run_solve<double>(P, b, x, s) : run_solve<float>(P, b, x, s);
+}
+
+int launch_backward(Plan& P, const double* x, const double* xbar, double* vals_bar, double* shift_bar,
+                    double* b_bar, void* stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    double* mu = wsp<double>(P, P.ws.mu);
+    int e = P.tsize == 8 ? run_solve<double>(P, xbar, mu, s) : run_solve<float>(P, xbar, mu, s);
+    if (e) return e;
+    const int B = P.B;
+    const int64_t n = P.n, S = (int64_t)B * P.n_pats;
+    const int64_t nrows = (int64_t)P.g_rows_all.size(), nel = (int64_t)P.e_elems_all.size();
+    if (nrows > 0) {
+        k_grad_atwa<<<dim3(cdiv(nrows, 256), B), 256, 0, s>>>(P.dt, nrows, mu, x, n, vals_bar, P.m);
+        P.launches++;
+    }
+    if (nel > 0) {
+        k_grad_elem<<<dim3(cdiv(nel, 128), B), 128, 0, s>>>(P.dt, nel, mu, x, n, vals_bar, P.m);
+        P.launches++;
+    }
+    if (shift_bar) {
+        k_shift_bar<<<(unsigned)S, 256, 0, s>>>(P.dt, P.n_pats, n, mu, x, shift_bar);
+        P.launches++;
+    }
+    e = (int)cudaMemcpyAsync(b_bar, mu, (size_t)B * n * 8, cudaMemcpyDeviceToDevice, s);
+    if (e) return e;
+    return (int)cudaGetLastError();
+}
+
+}  // namespace ssco

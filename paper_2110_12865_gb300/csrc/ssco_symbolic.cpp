@@ -1,0 +1,842 @@
+// ssco_symbolic.cpp -- host symbolic phase: everything that depends only on
+// the sparsity structure, computed once per plan.
+//
+// Mapping to the paper's method (Sec. 4):
+//  * Unrolling the program for a fixed structure (Sec. 3.1/4.7) is done at
+//    the granularity of K entries (assembly) and of dense fronts (Cholesky):
+//    per-entry expression trees of L would be far too many (the factor of a
+//    3D problem has ~1e8-1e9 entries), so a front -- a fundamental or
+//    relaxed-amalgamated supernode -- plays the role of an explicitly tagged
+//    dense block (Sec. 4.2.4) whose intermediates (the update matrix) are
+//    global intermediates stored once (Sec. 4.2.1).
+//  * Grouping by structure and level (Sec. 4.3): assembly entries are grouped
+//    by (pattern, term count, diagonal flag, constant-add); fronts by
+//    (height in the supernodal forest, size class).  Height (longest path
+//    from the leaves) guarantees no front depends on another of its level.
+//  * Leaf harvesting (Sec. 4.4, App. B): each assembly group stores its leaf
+//    table term-major / member-innermost (the coalesced layout of Sec. 4.8);
+//    a constant shared by all terms of a group (+-1 for incidence matrices)
+//    is folded into the group ("uniform") instead of being stored per term.
+//  * Address coherence (Sec. 4.8): a front addresses its rows through one
+//    relative map per (child, parent) pair instead of per-entry indices.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "ssco_internal.h"
+
+namespace ssco {
+
+namespace {
+
+struct Term {
+    int32_t row;
+    int32_t vidx;
+    double coef;
+};
+
+ssco_status bad(Plan& P, ssco_status s, const std::string& msg) {
+    P.last_error = msg;
+    return s;
+}
+
+ssco_status validate(Plan& P, const ssco_pattern* p, int k) {
+    std::string pre = "pattern " + std::to_string(k) + ": ";
+    if (!p) return bad(P, SSCO_ERR_INVALID_ARG, pre + "NULL pattern");
+    if (p->kind != SSCO_KIND_ATWA && p->kind != SSCO_KIND_ELEM)
+        return bad(P, SSCO_ERR_INVALID_ARG, pre + "unknown kind");
+    if (p->n < 1 || p->m < 0) return bad(P, SSCO_ERR_INVALID_ARG, pre + "n must be >= 1, m >= 0");
+    std::vector<int32_t> mark((size_t)p->n, -1);
+    if (p->kind == SSCO_KIND_ATWA) {
+        if (!p->rowptr) return bad(P, SSCO_ERR_INVALID_ARG, pre + "rowptr is NULL");
+        if (p->rowptr[0] != 0) return bad(P, SSCO_ERR_PATTERN, pre + "rowptr[0] != 0");
+        for (int32_t e = 0; e < p->m; ++e)
+            if (p->rowptr[e + 1] < p->rowptr[e])
+                return bad(P, SSCO_ERR_PATTERN, pre + "rowptr decreases at row " + std::to_string(e));
+        int64_t nnz = p->rowptr[p->m];
+        if (nnz > 0 && (!p->colind || !p->aval))
+            return bad(P, SSCO_ERR_INVALID_ARG, pre + "colind/aval is NULL");
+        for (int32_t e = 0; e < p->m; ++e) {
+            for (int64_t a = p->rowptr[e]; a < p->rowptr[e + 1]; ++a) {
+                int32_t c = p->colind[a];
+                if (c < 0 || c >= p->n)
+                    return bad(P, SSCO_ERR_PATTERN, pre + "column index out of range in row " + std::to_string(e));
+                if (mark[c] == e)
+                    return bad(P, SSCO_ERR_PATTERN, pre + "duplicate column in row " + std::to_string(e));
+                mark[c] = e;
+                if (!std::isfinite(p->aval[a]))
+                    return bad(P, SSCO_ERR_NONFINITE, pre + "non-finite entry of A");
+            }
+        }
+    } else {
+        if (p->elem_dim < 1 || p->elem_dim > 64)
+            return bad(P, SSCO_ERR_INVALID_ARG, pre + "elem_dim must be in [1, 64]");
+        if (p->m > 0 && (!p->elem_dofs || !p->elem_K0))
+            return bad(P, SSCO_ERR_INVALID_ARG, pre + "elem_dofs/elem_K0 is NULL");
+        int64_t npk = (int64_t)p->elem_dim * (p->elem_dim + 1) / 2;
+        for (int32_t e = 0; e < p->m; ++e) {
+            for (int32_t i = 0; i < p->elem_dim; ++i) {
+                int32_t d = p->elem_dofs[(int64_t)e * p->elem_dim + i];
+                if (d < -1 || d >= p->n)
+                    return bad(P, SSCO_ERR_PATTERN, pre + "DOF index out of range in element " + std::to_string(e));
+                if (d >= 0) {
+                    if (mark[d] == e)
+                        return bad(P, SSCO_ERR_PATTERN, pre + "duplicate DOF in element " + std::to_string(e));
+                    mark[d] = e;
+                }
+            }
+            for (int64_t q = 0; q < npk; ++q)
+                if (!std::isfinite(p->elem_K0[(int64_t)e * npk + q]))
+                    return bad(P, SSCO_ERR_NONFINITE, pre + "non-finite element block entry");
+        }
+    }
+    if (p->perm) {
+        std::vector<char> seen((size_t)p->n, 0);
+        for (int32_t i = 0; i < p->n; ++i) {
+            int32_t v = p->perm[i];
+            if (v < 0 || v >= p->n || seen[v]) return bad(P, SSCO_ERR_PATTERN, pre + "perm is not a permutation");
+            seen[v] = 1;
+        }
+    }
+    return SSCO_OK;
+}
+
+constexpr int32_t kClasses[] = {32, 64, 96, 128, 160, 192, 224};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+ssco_status analyze_impl(const ssco_pattern* const* pats, int32_t n_pats, const ssco_op* op, Plan& P) {
+    if (!pats || n_pats < 1 || !op) return bad(P, SSCO_ERR_INVALID_ARG, "pats/op NULL or n_pats < 1");
+    if (op->precision != SSCO_FP64 && op->precision != SSCO_FP32_REFINE)
+        return bad(P, SSCO_ERR_INVALID_ARG, "unknown precision");
+    if (op->batch < 1) return bad(P, SSCO_ERR_INVALID_ARG, "batch must be >= 1");
+    P.prec = op->precision;
+    P.B = op->batch;
+    P.tol = op->refine_tol > 0 ? op->refine_tol : 1e-10;
+    P.maxit = op->refine_max_iter > 0 ? op->refine_max_iter : 30;
+    P.tsize = P.prec == SSCO_FP64 ? 8 : 4;
+    int32_t smax_default = P.prec == SSCO_FP64 ? 160 : 224;
+    P.small_max = op->small_front_max > 0 ? std::min(op->small_front_max, smax_default) : smax_default;
+    P.amalg = op->amalgamate;
+    P.n_pats = n_pats;
+
+    for (int k = 0; k < n_pats; ++k) {
+        ssco_status s = validate(P, pats[k], k);
+        if (s != SSCO_OK) return s;
+    }
+    // --- concatenation -----------------------------------------------------
+    P.pats.resize(n_pats);
+    int64_t n = 0, m = 0;
+    for (int k = 0; k < n_pats; ++k) {
+        PatMeta& pm = P.pats[k];
+        pm.kind = pats[k]->kind;
+        pm.n = pats[k]->n;
+        pm.m = pats[k]->m;
+        pm.dim = pats[k]->kind == SSCO_KIND_ELEM ? pats[k]->elem_dim : 0;
+        pm.n_off = n;
+        pm.m_off = m;
+        n += pm.n;
+        m += pm.m;
+    }
+    if (n >= (int64_t)INT32_MAX || m >= (int64_t)INT32_MAX)
+        return bad(P, SSCO_ERR_UNSUPPORTED, "total n or m exceeds int32");
+    P.n = n;
+    P.m = m;
+    P.perm.resize(n);
+    std::vector<int32_t> iperm(n);
+    for (int k = 0; k < n_pats; ++k) {
+        const PatMeta& pm = P.pats[k];
+        for (int32_t i = 0; i < pm.n; ++i) {
+            int32_t old = pats[k]->perm ? pats[k]->perm[i] : i;
+            P.perm[pm.n_off + i] = (int32_t)(pm.n_off + old);
+            iperm[pm.n_off + old] = (int32_t)(pm.n_off + i);
+        }
+    }
+
+    // --- K~ pattern and per-entry terms ------------------------------------
+    std::vector<int64_t> tcount(n + 1, 0);
+    std::vector<char> referenced(n, 0);
+    for (int k = 0; k < n_pats; ++k) {
+        const ssco_pattern* p = pats[k];
+        if (p->kind == SSCO_KIND_ATWA) {
+            for (int32_t e = 0; e < p->m; ++e)
+                for (int64_t a = p->rowptr[e]; a < p->rowptr[e + 1]; ++a)
+                    for (int64_t b = a; b < p->rowptr[e + 1]; ++b) {
+                        int32_t u = iperm[P.pats[k].n_off + p->colind[a]];
+                        int32_t v = iperm[P.pats[k].n_off + p->colind[b]];
+                        tcount[std::min(u, v) + 1]++;
+                    }
+        } else {
+            int32_t d = p->elem_dim;
+            for (int32_t e = 0; e < p->m; ++e)
+                for (int32_t i = 0; i < d; ++i)
+                    for (int32_t j = 0; j <= i; ++j) {
+                        int32_t gu = p->elem_dofs[(int64_t)e * d + i], gv = p->elem_dofs[(int64_t)e * d + j];
+                        if (gu < 0 || gv < 0) continue;
+                        int32_t u = iperm[P.pats[k].n_off + gu], v = iperm[P.pats[k].n_off + gv];
+                        tcount[std::min(u, v) + 1]++;
+                        referenced[u] = referenced[v] = 1;
+                    }
+        }
+    }
+    for (int64_t j = 0; j < n; ++j) tcount[j + 1] += tcount[j];
+    std::vector<Term> terms((size_t)tcount[n]);
+    {
+        std::vector<int64_t> fill(tcount.begin(), tcount.end() - 1);
+        for (int k = 0; k < n_pats; ++k) {
+            const ssco_pattern* p = pats[k];
+            const PatMeta& pm = P.pats[k];
+            if (p->kind == SSCO_KIND_ATWA) {
+                for (int32_t e = 0; e < p->m; ++e)
+                    for (int64_t a = p->rowptr[e]; a < p->rowptr[e + 1]; ++a)
+                        for (int64_t b = a; b < p->rowptr[e + 1]; ++b) {
+                            int32_t u = iperm[pm.n_off + p->colind[a]];
+                            int32_t v = iperm[pm.n_off + p->colind[b]];
+                            Term t{std::max(u, v), (int32_t)(pm.m_off + e), p->aval[a] * p->aval[b]};
+                            terms[fill[std::min(u, v)]++] = t;
+                        }
+            } else {
+                int32_t d = p->elem_dim;
+                for (int32_t e = 0; e < p->m; ++e) {
+                    int32_t q = 0;
+                    for (int32_t i = 0; i < d; ++i)
+                        for (int32_t j = 0; j <= i; ++j, ++q) {
+                            int32_t gu = p->elem_dofs[(int64_t)e * d + i], gv = p->elem_dofs[(int64_t)e * d + j];
+                            if (gu < 0 || gv < 0) continue;
+                            int32_t u = iperm[pm.n_off + gu], v = iperm[pm.n_off + gv];
+                            Term t{std::max(u, v), (int32_t)(pm.m_off + e),
+                                   p->elem_K0[(int64_t)e * ((int64_t)d * (d + 1) / 2) + q]};
+                            terms[fill[std::min(u, v)]++] = t;
+                        }
+                }
+            }
+        }
+    }
+    // per column: stable sort by row (generation order kept within a row)
+    std::vector<int32_t> row_sys(n);
+    for (int k = 0; k < n_pats; ++k)
+        for (int64_t i = P.pats[k].n_off; i < P.pats[k].n_off + P.pats[k].n; ++i) row_sys[i] = k;
+    P.Kcolptr.assign(n + 1, 0);
+    P.Krowind.clear();
+    // slots in CSC order with their term ranges
+    std::vector<int64_t> slot_tbeg, slot_tend;
+    std::vector<int32_t> slot_diag;   // 1: receives the shift
+    std::vector<double> slot_cadd;
+    slot_tbeg.reserve(tcount[n] / 2 + n);
+    for (int64_t j = 0; j < n; ++j) {
+        auto b0 = terms.begin() + tcount[j], b1 = terms.begin() + tcount[j + 1];
+        std::stable_sort(b0, b1, [](const Term& x, const Term& y) { return x.row < y.row; });
+        int k = row_sys[j];
+        bool elem = P.pats[k].kind == SSCO_KIND_ELEM;
+        // diagonal first, always present
+        int64_t t = tcount[j];
+        int64_t te = t;
+        while (te < tcount[j + 1] && terms[te].row == j) ++te;
+        P.Krowind.push_back((int32_t)j);
+        slot_tbeg.push_back(t);
+        slot_tend.push_back(te);
+        if (elem && !referenced[j]) {
+            slot_diag.push_back(0);
+            slot_cadd.push_back(1.0);
+        } else {
+            slot_diag.push_back(1);
+            slot_cadd.push_back(0.0);
+        }
+        t = te;
+        while (t < tcount[j + 1]) {
+            int32_t r = terms[t].row;
+            te = t;
+            while (te < tcount[j + 1] && terms[te].row == r) ++te;
+            P.Krowind.push_back(r);
+            slot_tbeg.push_back(t);
+            slot_tend.push_back(te);
+            slot_diag.push_back(0);
+            slot_cadd.push_back(0.0);
+            t = te;
+        }
+        P.Kcolptr[j + 1] = (int64_t)P.Krowind.size();
+    }
+    P.nnzK = (int64_t)P.Krowind.size();
+    if (P.nnzK >= (int64_t)INT32_MAX) return bad(P, SSCO_ERR_UNSUPPORTED, "nnz(K) exceeds int32");
+
+    // --- assembly groups (Sec. 4.3 / 4.4) ---------------------------------
+    {
+        struct Key {
+            int32_t sys, nterms, diag;
+            double cadd;
+            bool operator<(const Key& o) const {
+                if (sys != o.sys) return sys < o.sys;
+                if (diag != o.diag) return diag < o.diag;
+                if (cadd != o.cadd) return cadd < o.cadd;
+                return nterms < o.nterms;
+            }
+        };
+        std::vector<int64_t> order(P.nnzK);
+        std::iota(order.begin(), order.end(), 0);
+        std::vector<int32_t> slot_col(P.nnzK);
+        for (int64_t j = 0; j < n; ++j)
+            for (int64_t q = P.Kcolptr[j]; q < P.Kcolptr[j + 1]; ++q) slot_col[q] = (int32_t)j;
+        auto key_of = [&](int64_t q) {
+            return Key{row_sys[slot_col[q]], (int32_t)(slot_tend[q] - slot_tbeg[q]), slot_diag[q], slot_cadd[q]};
+        };
+        std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return key_of(a) < key_of(b); });
+        P.kslot_of_q.assign(P.nnzK, 0);
+        P.groups.clear();
+        P.asm_idx.clear();
+        P.asm_coef.clear();
+        int64_t g0 = 0;
+        while (g0 < P.nnzK) {
+            Key kk = key_of(order[g0]);
+            int64_t g1 = g0;
+            while (g1 < P.nnzK) {
+                Key k2 = key_of(order[g1]);
+                if (k2.sys != kk.sys || k2.nterms != kk.nterms || k2.diag != kk.diag || k2.cadd != kk.cadd) break;
+                ++g1;
+            }
+            AsmGroup g{};
+            g.nmem = (int32_t)(g1 - g0);
+            g.nterms = kk.nterms;
+            g.diag = kk.diag;
+            g.sys = kk.sys;
+            g.cadd = kk.cadd;
+            g.slot_base = g0;
+            // uniform constant?
+            bool uniform = true;
+            double c0 = 0.0;
+            bool have = false;
+            for (int64_t i = g0; i < g1 && uniform; ++i)
+                for (int64_t t = slot_tbeg[order[i]]; t < slot_tend[order[i]]; ++t) {
+                    if (!have) {
+                        c0 = terms[t].coef;
+                        have = true;
+                    } else if (terms[t].coef != c0) {
+                        uniform = false;
+                        break;
+                    }
+                }
+            g.uniform = uniform ? 1 : 0;
+            g.coef = uniform ? c0 : 0.0;
+            g.idx_off = (int64_t)P.asm_idx.size();
+            g.coef_off = uniform ? 0 : (int64_t)P.asm_coef.size();
+            P.asm_idx.resize(P.asm_idx.size() + (size_t)g.nmem * g.nterms);
+            if (!uniform) P.asm_coef.resize(P.asm_coef.size() + (size_t)g.nmem * g.nterms);
+            for (int64_t i = g0; i < g1; ++i) {
+                int64_t q = order[i];
+                P.kslot_of_q[q] = (int32_t)i;
+                for (int32_t t = 0; t < g.nterms; ++t) {
+                    const Term& tm = terms[slot_tbeg[q] + t];
+                    P.asm_idx[g.idx_off + (int64_t)t * g.nmem + (i - g0)] = tm.vidx;
+                    if (!uniform) P.asm_coef[g.coef_off + (int64_t)t * g.nmem + (i - g0)] = tm.coef;
+                }
+            }
+            P.groups.push_back(g);
+            g0 = g1;
+        }
+        P.chunks.clear();
+        for (size_t gi = 0; gi < P.groups.size(); ++gi)
+            for (int32_t s = 0; s < P.groups[gi].nmem; s += 256) P.chunks.push_back(AsmChunk{(int32_t)gi, s});
+    }
+    std::vector<Term>().swap(terms);
+
+    // --- elimination forest (Liu's algorithm with path compression) --------
+    // strict-lower row lists of K~
+    std::vector<int64_t> rptr(n + 1, 0);
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t q = P.Kcolptr[j] + 1; q < P.Kcolptr[j + 1]; ++q) rptr[P.Krowind[q] + 1]++;
+    for (int64_t i = 0; i < n; ++i) rptr[i + 1] += rptr[i];
+    std::vector<int32_t> rcol(rptr[n]);
+    {
+        std::vector<int64_t> fill(rptr.begin(), rptr.end() - 1);
+        for (int64_t j = 0; j < n; ++j)
+            for (int64_t q = P.Kcolptr[j] + 1; q < P.Kcolptr[j + 1]; ++q) rcol[fill[P.Krowind[q]]++] = (int32_t)j;
+    }
+    P.parent.assign(n, -1);
+    {
+        std::vector<int32_t> anc(n, -1);
+        for (int64_t i = 0; i < n; ++i)
+            for (int64_t q = rptr[i]; q < rptr[i + 1]; ++q) {
+                int32_t r = rcol[q];
+                while (anc[r] != -1 && anc[r] != i) {
+                    int32_t t = anc[r];
+                    anc[r] = (int32_t)i;
+                    r = t;
+                }
+                if (anc[r] == -1) {
+                    anc[r] = (int32_t)i;
+                    P.parent[r] = (int32_t)i;
+                }
+            }
+    }
+    // --- column counts by row-subtree traversal ----------------------------
+    P.colcount.assign(n, 1);
+    {
+        std::vector<int32_t> mark(n, -1);
+        for (int64_t i = 0; i < n; ++i) {
+            mark[i] = (int32_t)i;
+            for (int64_t q = rptr[i]; q < rptr[i + 1]; ++q) {
+                int32_t k = rcol[q];
+                while (mark[k] != i) {
+                    mark[k] = (int32_t)i;
+                    P.colcount[k]++;
+                    k = P.parent[k];
+                }
+            }
+        }
+    }
+    std::vector<int64_t>().swap(rptr);
+    std::vector<int32_t>().swap(rcol);
+    P.nnzL = 0;
+    P.flops_exact = 0;
+    for (int64_t j = 0; j < n; ++j) {
+        P.nnzL += P.colcount[j];
+        P.flops_exact += (double)P.colcount[j] * P.colcount[j];
+    }
+    // column levels (height)
+    P.col_level.assign(n, 0);
+    std::vector<int32_t> nchild(n, 0);
+    for (int64_t j = 0; j < n; ++j)
+        if (P.parent[j] >= 0) {
+            nchild[P.parent[j]]++;
+            P.col_level[P.parent[j]] = std::max(P.col_level[P.parent[j]], P.col_level[j] + 1);
+        }
+    P.max_col_level = 0;
+    for (int64_t j = 0; j < n; ++j) P.max_col_level = std::max(P.max_col_level, P.col_level[j]);
+
+    // --- fundamental supernodes -------------------------------------------
+    P.snode_first.clear();
+    for (int64_t j = 0; j < n; ++j) {
+        bool joins = j > 0 && P.parent[j - 1] == j && nchild[j] == 1 && P.colcount[j] == P.colcount[j - 1] - 1;
+        if (!joins) P.snode_first.push_back((int32_t)j);
+    }
+    int32_t ns = (int32_t)P.snode_first.size();
+    P.snode_first.push_back((int32_t)n);
+    std::vector<int32_t> col2sn(n);
+    for (int32_t s = 0; s < ns; ++s)
+        for (int32_t j = P.snode_first[s]; j < P.snode_first[s + 1]; ++j) col2sn[j] = s;
+    P.sn_parent.assign(ns, -1);
+    P.sn_level.assign(ns, 0);
+    for (int32_t s = 0; s < ns; ++s) {
+        int32_t last = P.snode_first[s + 1] - 1;
+        if (P.parent[last] >= 0) P.sn_parent[s] = col2sn[P.parent[last]];
+    }
+    for (int32_t s = 0; s < ns; ++s)
+        if (P.sn_parent[s] >= 0) P.sn_level[P.sn_parent[s]] = std::max(P.sn_level[P.sn_parent[s]], P.sn_level[s] + 1);
+    // supernode row structures
+    {
+        std::vector<int32_t> sn_head(ns, -1), sn_next(ns, -1);
+        for (int32_t s = ns - 1; s >= 0; --s)
+            if (P.sn_parent[s] >= 0) {
+                sn_next[s] = sn_head[P.sn_parent[s]];
+                sn_head[P.sn_parent[s]] = s;
+            }
+        std::vector<int32_t> mark(n, -1);
+        P.sn_rows_off.assign(ns + 1, 0);
+        P.sn_rows.clear();
+        std::vector<int32_t> below;
+        for (int32_t s = 0; s < ns; ++s) {
+            int32_t f = P.snode_first[s], l = P.snode_first[s + 1] - 1;
+            below.clear();
+            for (int32_t j = f; j <= l; ++j)
+                for (int64_t q = P.Kcolptr[j]; q < P.Kcolptr[j + 1]; ++q) {
+                    int32_t i = P.Krowind[q];
+                    if (i > l && mark[i] != s) {
+                        mark[i] = s;
+                        below.push_back(i);
+                    }
+                }
+            for (int32_t c = sn_head[s]; c >= 0; c = sn_next[c])
+                for (int64_t q = P.sn_rows_off[c]; q < P.sn_rows_off[c + 1]; ++q) {
+                    int32_t i = P.sn_rows[q];
+                    if (i > l && mark[i] != s) {
+                        mark[i] = s;
+                        below.push_back(i);
+                    }
+                }
+            std::sort(below.begin(), below.end());
+            for (int32_t j = f; j <= l; ++j) P.sn_rows.push_back(j);
+            P.sn_rows.insert(P.sn_rows.end(), below.begin(), below.end());
+            P.sn_rows_off[s + 1] = (int64_t)P.sn_rows.size();
+            if ((int64_t)(l - f + 1) + (int64_t)below.size() != P.colcount[f])
+                return bad(P, SSCO_ERR_PATTERN, "internal: supernode structure disagrees with column counts");
+        }
+    }
+
+    // --- numeric partition: relaxed amalgamation of adjacent child fronts --
+    struct FB {
+        int32_t f, w, r;
+        double zeros;
+        int32_t last_sn;
+    };
+    std::vector<FB> fb;
+    for (int32_t s = 0; s < ns; ++s) {
+        FB cur{P.snode_first[s], P.snode_first[s + 1] - P.snode_first[s],
+               (int32_t)(P.sn_rows_off[s + 1] - P.sn_rows_off[s]), 0.0, s};
+        if (P.amalg > 0 && !fb.empty() && P.sn_parent[fb.back().last_sn] == s) {
+            const FB& c = fb.back();
+            int32_t wm = c.w + cur.w;
+            int32_t rm = c.w + cur.r;
+            double zeros = c.zeros + (double)c.w * (double)(rm - c.r);
+            double entries = (double)wm * rm - (double)wm * (wm - 1) / 2.0;
+            double zf = zeros / entries;
+            bool ok = wm <= 4 || (wm <= 16 && zf <= 0.8) || (wm <= 48 && zf <= 0.1) || zf <= 0.05;
+            if (ok && rm <= 16384) {
+                fb.back() = FB{c.f, wm, rm, zeros, s};
+                continue;
+            }
+        }
+        fb.push_back(cur);
+    }
+    int32_t nf = (int32_t)fb.size();
+    P.front_first.resize(nf + 1);
+    std::vector<int32_t> col2f(n);
+    for (int32_t F = 0; F < nf; ++F) {
+        P.front_first[F] = fb[F].f;
+        for (int32_t j = fb[F].f; j < fb[F].f + fb[F].w; ++j) col2f[j] = F;
+    }
+    P.front_first[nf] = (int32_t)n;
+    P.fronts.assign(nf, FrontDesc{});
+    P.rows.clear();
+    P.panel_total = P.upd_total = P.pvec_total = 0;
+    P.max_rows = 0;
+    P.flops_numeric = 0;
+    for (int32_t F = 0; F < nf; ++F) {
+        FrontDesc& d = P.fronts[F];
+        const FB& b = fb[F];
+        int32_t s = b.last_sn;
+        d.f = b.f;
+        d.w = b.w;
+        d.r = b.r;
+        d.sys = row_sys[b.f];
+        d.rows_off = (int64_t)P.rows.size();
+        for (int32_t j = b.f; j < P.snode_first[s]; ++j) P.rows.push_back(j);
+        P.rows.insert(P.rows.end(), P.sn_rows.begin() + P.sn_rows_off[s], P.sn_rows.begin() + P.sn_rows_off[s + 1]);
+        if ((int64_t)P.rows.size() - d.rows_off != d.r)
+            return bad(P, SSCO_ERR_PATTERN, "internal: front row count mismatch");
+        d.parent = d.r > d.w ? col2f[P.rows[d.rows_off + d.w]] : -1;
+        d.panel_off = P.panel_total;
+        d.upd_off = P.upd_total;
+        d.pvec_off = P.pvec_total;
+        P.panel_total += (int64_t)d.r * d.w;
+        P.upd_total += (int64_t)(d.r - d.w) * (d.r - d.w);
+        P.pvec_total += d.r - d.w;
+        P.max_rows = std::max(P.max_rows, d.r);
+        for (int32_t k = 0; k < d.w; ++k) P.flops_numeric += (double)(d.r - k) * (d.r - k);
+        d.relmap_off = -1;
+        d.inv_off = -1;
+        d.nchild = 0;
+    }
+    // children lists (ascending child id)
+    {
+        std::vector<int32_t> cnt(nf, 0);
+        for (int32_t F = 0; F < nf; ++F)
+            if (P.fronts[F].parent >= 0) cnt[P.fronts[F].parent]++;
+        int32_t off = 0;
+        for (int32_t F = 0; F < nf; ++F) {
+            P.fronts[F].child_off = off;
+            off += cnt[F];
+        }
+        P.child_ids.assign(off, 0);
+        for (int32_t F = 0; F < nf; ++F) {
+            int32_t p = P.fronts[F].parent;
+            if (p >= 0) P.child_ids[P.fronts[p].child_off + P.fronts[p].nchild++] = F;
+        }
+    }
+    // levels (height) of the numeric forest
+    P.front_level.assign(nf, 0);
+    for (int32_t F = 0; F < nf; ++F) {
+        int32_t p = P.fronts[F].parent;
+        if (p >= 0) P.front_level[p] = std::max(P.front_level[p], P.front_level[F] + 1);
+    }
+    P.n_levels = 0;
+    for (int32_t F = 0; F < nf; ++F) P.n_levels = std::max(P.n_levels, P.front_level[F] + 1);
+    // relative maps, inverse maps, K lists
+    {
+        std::vector<int32_t> pos(n, -1);
+        P.relmap.clear();
+        P.invmap.clear();
+        P.klist.clear();
+        for (int32_t F = 0; F < nf; ++F) {
+            FrontDesc& d = P.fronts[F];
+            for (int32_t k = 0; k < d.r; ++k) pos[P.rows[d.rows_off + k]] = k;
+            bool big = d.r > P.small_max;
+            if (big && d.nchild > 0) {
+                d.inv_off = (int64_t)P.invmap.size();
+                P.invmap.resize(P.invmap.size() + (size_t)d.nchild * d.r, -1);
+            }
+            for (int32_t c = 0; c < d.nchild; ++c) {
+                FrontDesc& cd = P.fronts[P.child_ids[d.child_off + c]];
+                cd.relmap_off = (int64_t)P.relmap.size();
+                for (int32_t k = 0; k < cd.r - cd.w; ++k) {
+                    int32_t row = P.rows[cd.rows_off + cd.w + k];
+                    int32_t pp = pos[row];
+                    if (pp < 0) return bad(P, SSCO_ERR_PATTERN, "internal: child row missing in parent front");
+                    P.relmap.push_back(pp);
+                    if (big) P.invmap[d.inv_off + (int64_t)c * d.r + pp] = k;
+                }
+            }
+            d.klist_off = (int64_t)P.klist.size() / 2;
+            for (int32_t j = d.f; j < d.f + d.w; ++j)
+                for (int64_t q = P.Kcolptr[j]; q < P.Kcolptr[j + 1]; ++q) {
+                    int32_t i = P.Krowind[q];
+                    P.klist.push_back(P.kslot_of_q[q]);
+                    P.klist.push_back((int32_t)((int64_t)(j - d.f) * d.r + pos[i]));
+                }
+            d.klist_n = (int32_t)((int64_t)P.klist.size() / 2 - d.klist_off);
+            for (int32_t k = 0; k < d.r; ++k) pos[P.rows[d.rows_off + k]] = -1;
+        }
+    }
+    // launch lists per level
+    {
+        std::vector<std::vector<int32_t>> by_level(P.n_levels);
+        for (int32_t F = 0; F < nf; ++F) by_level[P.front_level[F]].push_back(F);
+        P.front_lists.clear();
+        P.fact_launches.clear();
+        P.solve_launches.clear();
+        for (int32_t L = 0; L < P.n_levels; ++L) {
+            const auto& fl = by_level[L];
+            // solve: all fronts of the level, largest first
+            {
+                std::vector<int32_t> srt(fl);
+                std::stable_sort(srt.begin(), srt.end(),
+                                 [&](int32_t a, int32_t b) { return P.fronts[a].r > P.fronts[b].r; });
+                LaunchList ll{};
+                ll.level = L;
+                ll.cls = 0;
+                ll.list_off = (int64_t)P.front_lists.size();
+                ll.count = (int32_t)srt.size();
+                for (int32_t F : srt) {
+                    ll.rmax = std::max(ll.rmax, P.fronts[F].r);
+                    ll.wmax = std::max(ll.wmax, P.fronts[F].w);
+                }
+                P.front_lists.insert(P.front_lists.end(), srt.begin(), srt.end());
+                P.solve_launches.push_back(ll);
+            }
+            // factor: small fronts by size class, then big fronts
+            for (int32_t ci = 0; ci < (int32_t)(sizeof(kClasses) / sizeof(kClasses[0])); ++ci) {
+                int32_t hi = kClasses[ci];
+                int32_t lo = ci == 0 ? 0 : kClasses[ci - 1];
+                if (lo >= P.small_max) break;
+                hi = std::min(hi, P.small_max);
+                LaunchList ll{};
+                ll.level = L;
+                ll.cls = hi;
+                ll.list_off = (int64_t)P.front_lists.size();
+                for (int32_t F : fl)
+                    if (P.fronts[F].r > lo && P.fronts[F].r <= hi) {
+                        P.front_lists.push_back(F);
+                        ll.count++;
+                        ll.rmax = std::max(ll.rmax, P.fronts[F].r);
+                        ll.wmax = std::max(ll.wmax, P.fronts[F].w);
+                    }
+                if (ll.count > 0) P.fact_launches.push_back(ll);
+            }
+            LaunchList bl{};
+            bl.level = L;
+            bl.cls = -1;
+            bl.list_off = (int64_t)P.front_lists.size();
+            for (int32_t F : fl) {
+                const FrontDesc& d = P.fronts[F];
+                if (d.r <= P.small_max) continue;
+                P.front_lists.push_back(F);
+                bl.count++;
+                bl.rmax = std::max(bl.rmax, d.r);
+                bl.wmax = std::max(bl.wmax, d.w);
+                int64_t t = (d.r + 31) / 32;
+                bl.max_lower_tiles = std::max(bl.max_lower_tiles, t * (t + 1) / 2);
+                int64_t u = (d.r - d.w + 63) / 64;
+                bl.max_syrk_tiles = std::max(bl.max_syrk_tiles, u * (u + 1) / 2);
+                bl.max_klist = std::max(bl.max_klist, d.klist_n);
+            }
+            if (bl.count > 0) P.fact_launches.push_back(bl);
+        }
+    }
+
+    // --- symmetric CSR of K~ for the FP64 residual -------------------------
+    {
+        P.sp_rowptr.assign(n + 1, 0);
+        for (int64_t j = 0; j < n; ++j)
+            for (int64_t q = P.Kcolptr[j]; q < P.Kcolptr[j + 1]; ++q) {
+                int32_t i = P.Krowind[q];
+                P.sp_rowptr[i + 1]++;
+                if (i != j) P.sp_rowptr[j + 1]++;
+            }
+        for (int64_t i = 0; i < n; ++i) P.sp_rowptr[i + 1] += P.sp_rowptr[i];
+        P.sp_col.assign(P.sp_rowptr[n], 0);
+        P.sp_slot.assign(P.sp_rowptr[n], 0);
+        std::vector<int64_t> fill(P.sp_rowptr.begin(), P.sp_rowptr.end() - 1);
+        for (int64_t j = 0; j < n; ++j)
+            for (int64_t q = P.Kcolptr[j]; q < P.Kcolptr[j + 1]; ++q) {
+                int32_t i = P.Krowind[q];
+                P.sp_col[fill[i]] = (int32_t)j;
+                P.sp_slot[fill[i]++] = P.kslot_of_q[q];
+                if (i != j) {
+                    P.sp_col[fill[j]] = i;
+                    P.sp_slot[fill[j]++] = P.kslot_of_q[q];
+                }
+            }
+        // columns come out ascending within each row: row i first receives
+        // (j, .) from every column j < i in order, then its own column i.
+        P.row_sys = row_sys;
+        P.sys_n_off.resize(n_pats + 1);
+        for (int k = 0; k < n_pats; ++k) P.sys_n_off[k] = P.pats[k].n_off;
+        P.sys_n_off[n_pats] = n;
+        P.shifted.assign(n, 1);
+        for (int64_t j = 0; j < n; ++j)
+            if (P.pats[row_sys[j]].kind == SSCO_KIND_ELEM && !referenced[j]) P.shifted[j] = 0;
+    }
+
+    // --- adjoint tables (original ordering, concatenated) -------------------
+    {
+        P.g_rowptr.assign(1, 0);
+        P.g_colind.clear();
+        P.g_aval.clear();
+        P.g_row_sys.clear();
+        P.g_rows_all.clear();
+        P.e_dofs.clear();
+        P.e_K0.clear();
+        P.e_sys.clear();
+        P.e_off.clear();
+        P.e_k0off.clear();
+        P.e_dim.clear();
+        P.e_elems_all.clear();
+        for (int k = 0; k < n_pats; ++k) {
+            const ssco_pattern* p = pats[k];
+            const PatMeta& pm = P.pats[k];
+            if (p->kind == SSCO_KIND_ATWA) {
+                for (int32_t e = 0; e < p->m; ++e) {
+                    for (int64_t a = p->rowptr[e]; a < p->rowptr[e + 1]; ++a) {
+                        P.g_colind.push_back((int32_t)(pm.n_off + p->colind[a]));
+                        P.g_aval.push_back(p->aval[a]);
+                    }
+                    P.g_rowptr.push_back((int64_t)P.g_colind.size());
+                    P.g_row_sys.push_back(k);
+                    P.g_rows_all.push_back((int32_t)(pm.m_off + e));
+                }
+            } else {
+                int32_t d = p->elem_dim;
+                int64_t npk = (int64_t)d * (d + 1) / 2;
+                for (int32_t e = 0; e < p->m; ++e) {
+                    P.e_off.push_back((int64_t)P.e_dofs.size());
+                    P.e_k0off.push_back((int64_t)P.e_K0.size());
+                    P.e_dim.push_back(d);
+                    P.e_sys.push_back(k);
+                    P.e_elems_all.push_back((int32_t)(pm.m_off + e));
+                    for (int32_t i = 0; i < d; ++i) {
+                        int32_t g = p->elem_dofs[(int64_t)e * d + i];
+                        P.e_dofs.push_back(g < 0 ? -1 : (int32_t)(pm.n_off + g));
+                    }
+                    P.e_K0.insert(P.e_K0.end(), p->elem_K0 + (int64_t)e * npk, p->elem_K0 + (int64_t)(e + 1) * npk);
+                }
+            }
+        }
+    }
+    build_blob(P);
+    compute_ws_layout(P);
+    return SSCO_OK;
+}
+
+// ---------------------------------------------------------------------------
+namespace {
+template <class T>
+size_t put(std::vector<uint8_t>& blob, const std::vector<T>& v) {
+    size_t off = (blob.size() + 255) & ~(size_t)255;
+    blob.resize(off + std::max<size_t>(v.size() * sizeof(T), 16), 0);
+    if (!v.empty()) std::memcpy(blob.data() + off, v.data(), v.size() * sizeof(T));
+    return off;
+}
+}  // namespace
+
+void build_blob(Plan& P) {
+    std::vector<uint8_t>& b = P.blob;
+    b.clear();
+    P.toff.fronts = put(b, P.fronts);
+    P.toff.rows = put(b, P.rows);
+    P.toff.child_ids = put(b, P.child_ids);
+    P.toff.relmap = put(b, P.relmap);
+    P.toff.invmap = put(b, P.invmap);
+    P.toff.klist = put(b, P.klist);
+    P.toff.front_lists = put(b, P.front_lists);
+    P.toff.groups = put(b, P.groups);
+    P.toff.chunks = put(b, P.chunks);
+    P.toff.asm_idx = put(b, P.asm_idx);
+    P.toff.asm_coef = put(b, P.asm_coef);
+    P.toff.sp_rowptr = put(b, P.sp_rowptr);
+    P.toff.sp_col = put(b, P.sp_col);
+    P.toff.sp_slot = put(b, P.sp_slot);
+    P.toff.perm = put(b, P.perm);
+    P.toff.row_sys = put(b, P.row_sys);
+    P.toff.sys_n_off = put(b, P.sys_n_off);
+    P.toff.g_rowptr = put(b, P.g_rowptr);
+    P.toff.g_colind = put(b, P.g_colind);
+    P.toff.g_aval = put(b, P.g_aval);
+    P.toff.g_row_sys = put(b, P.g_row_sys);
+    P.toff.e_dofs = put(b, P.e_dofs);
+    P.toff.e_K0 = put(b, P.e_K0);
+    P.toff.e_sys = put(b, P.e_sys);
+    P.toff.e_off = put(b, P.e_off);
+    P.toff.e_k0off = put(b, P.e_k0off);
+    P.toff.e_dim = put(b, P.e_dim);
+    P.toff.shifted = put(b, P.shifted);
+    P.toff.g_rows_all = put(b, P.g_rows_all);
+    P.toff.e_elems_all = put(b, P.e_elems_all);
+    b.resize((b.size() + 255) & ~(size_t)255);
+}
+
+void compute_ws_layout(Plan& P) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off += (std::max<size_t>(bytes, 16) + 255) & ~(size_t)255;
+        return o;
+    };
+    const size_t B = (size_t)P.B, n = (size_t)P.n, S = (size_t)P.B * P.n_pats;
+    WsLayout& w = P.ws;
+    w.K = take(B * P.nnzK * 8);
+    w.panel = take(B * P.panel_total * P.tsize);
+    w.upd = take(B * P.upd_total * P.tsize);
+    w.pvec = take(B * P.pvec_total * P.tsize);
+    w.vecT = take(B * n * P.tsize);
+    w.bp = take(B * n * 8);
+    w.xp = take(B * n * 8);
+    w.rr = take(B * n * 8);
+    w.mu = take(B * n * 8);
+    w.xbar_p = take(B * n * 8);
+    w.bad_col = take(S * 4);
+    w.sstatus = take(S * 4);
+    w.iters = take(S * 4);
+    w.active = take(S * 4);
+    w.any_active = take(4);
+    w.resid = take(S * 8);
+    w.bnorm = take(S * 8);
+    w.r1 = take(S * 8);
+    w.r2 = take(S * 8);
+    w.sigma = take(S * 8);
+    w.sbar = take(S * 8);
+    w.st_vals = take(B * (size_t)P.m * 8);
+    w.st_shift = take(S * 8);
+    w.st_b = take(B * n * 8);
+    w.st_x = take(B * n * 8);
+    w.total = off;
+}
+
+void export_L_pattern(const Plan& P, std::vector<int64_t>* colptr, std::vector<int32_t>* rowind) {
+    int32_t ns = (int32_t)P.snode_first.size() - 1;
+    if (colptr) {
+        colptr->assign(P.n + 1, 0);
+        for (int64_t j = 0; j < P.n; ++j) (*colptr)[j + 1] = (*colptr)[j] + P.colcount[j];
+    }
+    if (rowind) {
+        rowind->clear();
+        rowind->reserve(P.nnzL);
+        for (int32_t s = 0; s < ns; ++s) {
+            int32_t f = P.snode_first[s], w = P.snode_first[s + 1] - f;
+            for (int32_t k = 0; k < w; ++k)
+                rowind->insert(rowind->end(), P.sn_rows.begin() + P.sn_rows_off[s] + k,
+                               P.sn_rows.begin() + P.sn_rows_off[s + 1]);
+        }
+    }
+}
+
+}  // namespace ssco

@@ -343,7 +343,11 @@ def elasticity_problem(k: int, batch: int = 1, cfg: int = 2, jitter: float = 0.1
         bi = rng.standard_normal(n)
         bi[dof_fixed] = 0.0
         b[i] = bi
-    perm = expand_perm(nested_dissection(dims), 3)
+    # Fixed DOFs are decoupled identity rows: numbering them first leaves the
+    # fill unchanged and keeps every separator's free columns contiguous.
+    dperm = expand_perm(nested_dissection(dims), 3)
+    fixed_first = dof_fixed[dperm]
+    perm = np.concatenate([dperm[fixed_first], dperm[~fixed_first]]).astype(np.int32)
     return Problem(kind=KIND_ELEM, name=f"elast{k}", n=n, m=m, elem_dim=12,
                    elem_dofs=np.ascontiguousarray(elem_dofs),
                    elem_K0=np.ascontiguousarray(pack_lower(Ke)), perm=perm,

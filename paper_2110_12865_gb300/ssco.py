@@ -1,0 +1,319 @@
+"""Thin Python binding of the C ABI in ``include/ssco.h`` (libssco.so).
+
+Argument marshalling only: every step of the numeric path runs in the
+library's CUDA kernels; PyTorch provides device memory and streams.  If the
+shared library is missing this module raises at import -- there is no
+fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+from . import problems as _problems
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libssco.so")
+
+SSCO_OK = 0
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "PATTERN", 3: "NOT_SPD", 4: "NONFINITE",
+                5: "NO_CONVERGE", 6: "TIMEOUT", 7: "CUDA", 8: "OOM", 9: "UNSUPPORTED", 10: "STATE"}
+FP64, FP32_REFINE = 0, 1
+VALS_F64, VALS_F32 = 0, 1
+(EXPORT_PERM, EXPORT_ETREE, EXPORT_COLCOUNT, EXPORT_L_COLPTR, EXPORT_L_ROWIND, EXPORT_COL_LEVEL,
+ EXPORT_SNODE_FIRST, EXPORT_SN_PARENT, EXPORT_SN_LEVEL, EXPORT_K_COLPTR, EXPORT_K_ROWIND,
+ EXPORT_GROUPS, EXPORT_GROUP_COEF, EXPORT_FRONT_FIRST, EXPORT_FRONT_LEVEL) = range(15)
+
+EXPORTED_SYMBOLS = [
+    "ssco_analyze", "ssco_plan_info", "ssco_plan_export", "ssco_bind", "ssco_numeric", "ssco_solve",
+    "ssco_backward", "ssco_status_get", "ssco_export_L", "ssco_export_K", "ssco_refactor_solve_host",
+    "ssco_last_launch_count", "ssco_last_error", "ssco_status_string", "ssco_plan_save", "ssco_plan_load",
+    "ssco_destroy",
+]
+
+
+class SscoError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Pattern(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("n", C.c_int32), ("m", C.c_int32),
+                ("rowptr", C.c_void_p), ("colind", C.c_void_p), ("aval", C.c_void_p),
+                ("elem_dim", C.c_int32), ("elem_dofs", C.c_void_p), ("elem_K0", C.c_void_p),
+                ("perm", C.c_void_p)]
+
+
+class Op(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("batch", C.c_int32), ("refine_tol", C.c_double),
+                ("refine_max_iter", C.c_int32), ("small_front_max", C.c_int32),
+                ("amalgamate", C.c_int32), ("reserved", C.c_int32 * 3)]
+
+
+class Info(C.Structure):
+    _fields_ = [(k, C.c_int64) for k in
+                ["n", "n_pats", "batch", "n_systems", "m", "nnz_K", "nnz_L", "n_snodes", "n_fronts",
+                 "n_levels", "max_col_level", "panel_entries", "update_entries", "max_front_rows",
+                 "n_assembly_groups", "assembly_terms", "tables_bytes", "workspace_bytes"]] + \
+              [("factor_flops", C.c_double), ("factor_flops_exact", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Loads libssco.so (built by ``paper_2110_12865_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libssco.so not built ({path}); run paper_2110_12865_gb300.build.build()")
+    L = C.CDLL(path)
+    vp, i32, i64, dbl, sz = C.c_void_p, C.c_int32, C.c_int64, C.c_double, C.c_size_t
+    sig = {
+        "ssco_analyze": (i32, [C.POINTER(C.POINTER(Pattern)), i32, C.POINTER(Op), C.POINTER(vp)]),
+        "ssco_plan_info": (i32, [vp, C.POINTER(Info)]),
+        "ssco_plan_export": (i32, [vp, i32, vp, sz]),
+        "ssco_bind": (i32, [vp, vp, sz, vp, sz, vp]),
+        "ssco_numeric": (i32, [vp, vp, i32, vp, vp]),
+        "ssco_solve": (i32, [vp, vp, vp, vp]),
+        "ssco_backward": (i32, [vp, vp, vp, vp, vp, vp, vp]),
+        "ssco_status_get": (i32, [vp, vp, vp, vp, vp, vp]),
+        "ssco_export_L": (i32, [vp, vp, vp]),
+        "ssco_export_K": (i32, [vp, vp, vp]),
+        "ssco_refactor_solve_host": (i32, [vp, vp, i32, vp, vp, vp, vp]),
+        "ssco_last_launch_count": (i64, [vp]),
+        "ssco_last_error": (C.c_char_p, [vp]),
+        "ssco_status_string": (C.c_char_p, [i32]),
+        "ssco_plan_save": (i32, [vp, C.c_char_p]),
+        "ssco_plan_load": (i32, [C.c_char_p, C.POINTER(vp)]),
+        "ssco_destroy": (None, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, torch.Tensor):
+        return C.c_void_p(a.data_ptr())
+    return C.c_void_p(a.ctypes.data)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+class Plan:
+    """An analyzed fixed structure plus (after :meth:`bind`) its device memory.
+
+    ``problems`` is one problem dict (see ``problems.py``) or a list of them
+    (several patterns concatenated, one value set each per instance)."""
+
+    def __init__(self, problems, precision=FP64, batch=None, refine_tol=1e-10, refine_max_iter=30,
+                 small_front_max=0, amalgamate=1, _handle=None):
+        self.L = load_library()
+        if _handle is not None:
+            self._h = _handle
+        else:
+            probs = problems if isinstance(problems, (list, tuple)) else [problems]
+            self._keep = []
+            pats = []
+            for p in probs:
+                pat = Pattern()
+                pat.kind, pat.n, pat.m = int(p["kind"]), int(p["n"]), int(p["m"])
+                if pat.kind == _problems.KIND_ATWA:
+                    rp = np.ascontiguousarray(p["rowptr"], np.int64)
+                    ci = np.ascontiguousarray(p["colind"], np.int32)
+                    av = np.ascontiguousarray(p["aval"], np.float64)
+                    self._keep += [rp, ci, av]
+                    pat.rowptr, pat.colind, pat.aval = rp.ctypes.data, ci.ctypes.data, av.ctypes.data
+                elif pat.kind == _problems.KIND_ELEM:
+                    dofs = np.ascontiguousarray(p["elem_dofs"], np.int32)
+                    K0 = np.ascontiguousarray(p["elem_K0"], np.float64)
+                    self._keep += [dofs, K0]
+                    pat.elem_dim = int(p["elem_dim"])
+                    pat.elem_dofs, pat.elem_K0 = dofs.ctypes.data, K0.ctypes.data
+                if p.get("perm") is not None:
+                    pm = np.ascontiguousarray(p["perm"], np.int32)
+                    self._keep.append(pm)
+                    pat.perm = pm.ctypes.data
+                pats.append(pat)
+            arr = (C.POINTER(Pattern) * len(pats))(*[C.pointer(q) for q in pats])
+            op = Op()
+            op.precision = precision
+            op.batch = int(batch if batch is not None else probs[0].get("batch", 1))
+            op.refine_tol = refine_tol
+            op.refine_max_iter = refine_max_iter
+            op.small_front_max = small_front_max
+            op.amalgamate = amalgamate
+            h = C.c_void_p()
+            st = self.L.ssco_analyze(arr, len(pats), C.byref(op), C.byref(h))
+            if st != SSCO_OK:
+                raise SscoError(st, self.L.ssco_last_error(None).decode())
+            self._h = h
+            self._keep = None
+        inf = Info()
+        self._check(self.L.ssco_plan_info(self._h, C.byref(inf)))
+        self.info = inf.as_dict()
+        self.n = self.info["n"]
+        self.m = self.info["m"]
+        self.batch = self.info["batch"]
+        self.n_pats = self.info["n_pats"]
+        self.n_systems = self.info["n_systems"]
+        self.precision = precision
+        self.tables = None
+        self.ws = None
+        self.device = None
+
+    # -- plumbing -----------------------------------------------------------
+    def _check(self, st):
+        if st != SSCO_OK:
+            raise SscoError(st, self.L.ssco_last_error(self._h).decode())
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.ssco_destroy(h)
+            self._h = None
+
+    # -- structure ------------------------------------------------------------
+    _EXPORT_DTYPES = {EXPORT_PERM: np.int32, EXPORT_ETREE: np.int32, EXPORT_COLCOUNT: np.int32,
+                      EXPORT_L_COLPTR: np.int64, EXPORT_L_ROWIND: np.int32, EXPORT_COL_LEVEL: np.int32,
+                      EXPORT_SNODE_FIRST: np.int32, EXPORT_SN_PARENT: np.int32, EXPORT_SN_LEVEL: np.int32,
+                      EXPORT_K_COLPTR: np.int64, EXPORT_K_ROWIND: np.int32, EXPORT_GROUPS: np.int64,
+                      EXPORT_GROUP_COEF: np.float64, EXPORT_FRONT_FIRST: np.int32,
+                      EXPORT_FRONT_LEVEL: np.int32}
+
+    def export(self, what):
+        i = self.info
+        n = i["n"]
+        sizes = {EXPORT_PERM: n, EXPORT_ETREE: n, EXPORT_COLCOUNT: n, EXPORT_L_COLPTR: n + 1,
+                 EXPORT_L_ROWIND: i["nnz_L"], EXPORT_COL_LEVEL: n, EXPORT_SNODE_FIRST: i["n_snodes"] + 1,
+                 EXPORT_SN_PARENT: i["n_snodes"], EXPORT_SN_LEVEL: i["n_snodes"], EXPORT_K_COLPTR: n + 1,
+                 EXPORT_K_ROWIND: i["nnz_K"], EXPORT_GROUPS: 4 * i["n_assembly_groups"],
+                 EXPORT_GROUP_COEF: i["n_assembly_groups"], EXPORT_FRONT_FIRST: i["n_fronts"] + 1,
+                 EXPORT_FRONT_LEVEL: i["n_fronts"]}
+        out = np.zeros(max(int(sizes[what]), 1), self._EXPORT_DTYPES[what])
+        self._check(self.L.ssco_plan_export(self._h, what, out.ctypes.data, out.nbytes))
+        out = out[: int(sizes[what])]
+        return out.reshape(-1, 4) if what == EXPORT_GROUPS else out
+
+    def save(self, path):
+        self._check(self.L.ssco_plan_save(self._h, path.encode()))
+
+    @classmethod
+    def load(cls, path, precision=None):
+        L = load_library()
+        h = C.c_void_p()
+        st = L.ssco_plan_load(path.encode(), C.byref(h))
+        if st != SSCO_OK:
+            raise SscoError(st, L.ssco_last_error(None).decode())
+        return cls(None, precision=precision if precision is not None else FP64, _handle=h)
+
+    # -- device ---------------------------------------------------------------
+    def bind(self, device="cuda", stream=None):
+        """Allocates the table buffer and workspace with torch and binds them."""
+        self.device = torch.device(device)
+        tb = int(self.info["tables_bytes"])
+        wb = int(self.info["workspace_bytes"])
+        self.tables = torch.empty(tb + 256, dtype=torch.uint8, device=self.device)
+        self.ws = torch.empty(wb + 256, dtype=torch.uint8, device=self.device)
+        t0 = (-self.tables.data_ptr()) % 256
+        w0 = (-self.ws.data_ptr()) % 256
+        self._check(self.L.ssco_bind(self._h, C.c_void_p(self.tables.data_ptr() + t0), tb,
+                                     C.c_void_p(self.ws.data_ptr() + w0), wb, _stream_ptr(stream)))
+        return self
+
+    def numeric(self, vals: torch.Tensor, shift: torch.Tensor, stream=None):
+        """vals: [B, m] float64/float32 on the device; shift: [n_systems] float64."""
+        assert vals.is_cuda and vals.is_contiguous() and vals.numel() == self.batch * self.m
+        assert shift.is_cuda and shift.dtype == torch.float64 and shift.numel() == self.n_systems
+        dt = VALS_F64 if vals.dtype == torch.float64 else VALS_F32
+        assert vals.dtype in (torch.float64, torch.float32)
+        self._check(self.L.ssco_numeric(self._h, _ptr(vals), dt, _ptr(shift), _stream_ptr(stream)))
+
+    def solve(self, b: torch.Tensor, x: torch.Tensor | None = None, stream=None):
+        assert b.is_cuda and b.dtype == torch.float64 and b.is_contiguous()
+        if x is None:
+            x = torch.empty_like(b)
+        self._check(self.L.ssco_solve(self._h, _ptr(b), _ptr(x), _stream_ptr(stream)))
+        return x
+
+    def backward(self, x, xbar, stream=None, want_shift=True):
+        vbar = torch.empty((self.batch, self.m), dtype=torch.float64, device=x.device)
+        sbar = torch.empty(self.n_systems, dtype=torch.float64, device=x.device) if want_shift else None
+        bbar = torch.empty_like(xbar)
+        self._check(self.L.ssco_backward(self._h, _ptr(x), _ptr(xbar.contiguous()), _ptr(vbar), _ptr(sbar),
+                                         _ptr(bbar), _stream_ptr(stream)))
+        return vbar, sbar, bbar
+
+    def status(self, stream=None):
+        S = self.n_systems
+        st = np.zeros(S, np.int32)
+        it = np.zeros(S, np.int32)
+        rs = np.zeros(S, np.float64)
+        bc = np.zeros(S, np.int32)
+        self.L.ssco_status_get(self._h, _stream_ptr(stream), st.ctypes.data, it.ctypes.data, rs.ctypes.data,
+                               bc.ctypes.data)
+        return {"status": st, "iters": it, "resid": rs, "bad_col": bc}
+
+    def export_L(self, stream=None):
+        out = np.zeros((self.batch, int(self.info["nnz_L"])))
+        self._check(self.L.ssco_export_L(self._h, out.ctypes.data, _stream_ptr(stream)))
+        return out
+
+    def export_K(self, stream=None):
+        out = np.zeros((self.batch, int(self.info["nnz_K"])))
+        self._check(self.L.ssco_export_K(self._h, out.ctypes.data, _stream_ptr(stream)))
+        return out
+
+    def refactor_solve_host(self, vals: np.ndarray, shift: np.ndarray, b: np.ndarray, x: np.ndarray = None,
+                            stream=None):
+        """End-to-end call on host buffers (numpy or pinned torch CPU tensors)."""
+        dt = VALS_F64 if vals.dtype in (np.float64, torch.float64) else VALS_F32
+        if x is None:
+            x = np.empty_like(b)
+        self._check(self.L.ssco_refactor_solve_host(self._h, _ptr(vals), dt, _ptr(shift), _ptr(b), _ptr(x),
+                                                    _stream_ptr(stream)))
+        return x
+
+    def last_launch_count(self):
+        return int(self.L.ssco_last_launch_count(self._h))
+
+
+class SscoSolve(torch.autograd.Function):
+    """x = K(vals, shift)^-1 b with the hand-written adjoint (ssco_backward)."""
+
+    @staticmethod
+    def forward(ctx, plan: Plan, vals, shift, b):
+        plan.numeric(vals.contiguous(), shift.contiguous())
+        x = plan.solve(b.contiguous())
+        ctx.plan = plan
+        ctx.save_for_backward(x)
+        ctx.vals_dtype = vals.dtype
+        return x
+
+    @staticmethod
+    def backward(ctx, xbar):
+        (x,) = ctx.saved_tensors
+        vbar, sbar, bbar = ctx.plan.backward(x, xbar.contiguous())
+        return None, vbar.to(ctx.vals_dtype), sbar, bbar
+
+
+def ssco_solve(plan: Plan, vals, shift, b):
+    return SscoSolve.apply(plan, vals, shift, b)

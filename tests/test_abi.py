@@ -1,0 +1,193 @@
+"""Host-side checks of the C ABI (no GPU): the library loads, exports every
+symbol the header declares, and its symbolic phase matches the oracle's
+structures bit for bit."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2110_12865_gb300 import build as B
+from paper_2110_12865_gb300 import problems as P
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def S():
+    B.build()
+    from paper_2110_12865_gb300 import ssco
+    return ssco
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "ssco.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ssco_[a-z_A-Z0-9]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol(S):
+    import ctypes
+    lib = ctypes.CDLL(S.LIB_PATH)
+    names = header_functions()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) == set(S.EXPORTED_SYMBOLS)
+
+
+def symbolic_matches(S, p, **kw):
+    pl = S.Plan(p, **kw)
+    r = O.refactor_solve(p)
+    Kp, Sy = r.Kp, r.S
+    assert np.array_equal(pl.export(S.EXPORT_PERM), p.perm)
+    assert np.array_equal(pl.export(S.EXPORT_K_COLPTR), Kp.colptr)
+    assert np.array_equal(pl.export(S.EXPORT_K_ROWIND), Kp.rowind)
+    assert np.array_equal(pl.export(S.EXPORT_ETREE), Sy.parent)
+    assert np.array_equal(pl.export(S.EXPORT_COLCOUNT), Sy.colcount)
+    assert np.array_equal(pl.export(S.EXPORT_L_COLPTR), Sy.Lcolptr)
+    assert np.array_equal(pl.export(S.EXPORT_L_ROWIND), Sy.Lrowind)
+    assert np.array_equal(pl.export(S.EXPORT_COL_LEVEL), Sy.col_level)
+    assert np.array_equal(pl.export(S.EXPORT_SNODE_FIRST), Sy.snode_first)
+    assert np.array_equal(pl.export(S.EXPORT_SN_PARENT), Sy.sn_parent)
+    assert np.array_equal(pl.export(S.EXPORT_SN_LEVEL), Sy.sn_level)
+    assert pl.info["nnz_L"] == Sy.nnzL and pl.info["nnz_K"] == Kp.nnz
+    return pl
+
+
+@pytest.mark.parametrize("name", ["grid32", "elast5", "trigrid24"])
+@pytest.mark.parametrize("amalg", [0, 1])
+def test_symbolic_parity_workloads(S, name, amalg):
+    symbolic_matches(S, P.workload(name), amalgamate=amalg)
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_symbolic_parity_random(S, seed):
+    rng = np.random.default_rng(500 + seed)
+    n = int(rng.integers(1, 400))
+    p = P.random_spd_pattern(n, int(rng.integers(0, 3 * n + 1)), rng)
+    symbolic_matches(S, p)
+
+
+def test_symbolic_parity_full_size_grid256(S):
+    symbolic_matches(S, P.workload("grid256"))
+
+
+def test_multi_pattern_concatenation(S):
+    """Several patterns in one plan: the structures are the block-diagonal
+    union of the per-pattern ones (offset by the preceding unknowns)."""
+    probs = [P.trigrid_problem(s, 1, cfg=3, seed_offset=k) for k, s in enumerate([5, 9, 7])]
+    probs.append(P.elasticity_problem(2, cfg=2))
+    pl = S.Plan(probs)
+    par = pl.export(S.EXPORT_ETREE)
+    cc = pl.export(S.EXPORT_COLCOUNT)
+    lev = pl.export(S.EXPORT_COL_LEVEL)
+    off = 0
+    for p in probs:
+        r = O.refactor_solve(p)
+        sl = slice(off, off + p.n)
+        exp_par = np.where(r.S.parent >= 0, r.S.parent + off, -1)
+        assert np.array_equal(par[sl], exp_par)
+        assert np.array_equal(cc[sl], r.S.colcount)
+        assert np.array_equal(lev[sl], r.S.col_level)
+        off += p.n
+    assert pl.info["n"] == off and pl.info["n_pats"] == 4
+
+
+def test_fronts_partition_and_levels(S):
+    """Numeric partition: contiguous fronts covering all columns; a front's
+    level exceeds all its children's (members of one level are independent,
+    Sec. 4.3)."""
+    p = P.workload("elast5")
+    pl = S.Plan(p, amalgamate=1)
+    ff = pl.export(S.EXPORT_FRONT_FIRST)
+    fl = pl.export(S.EXPORT_FRONT_LEVEL)
+    et = pl.export(S.EXPORT_ETREE)
+    assert ff[0] == 0 and ff[-1] == p.n and np.all(np.diff(ff) > 0)
+    col2f = np.repeat(np.arange(len(fl)), np.diff(ff))
+    for f in range(len(fl)):
+        last = ff[f + 1] - 1
+        # inside a front the etree is a chain
+        assert np.all(et[ff[f]:last] == np.arange(ff[f] + 1, last + 1))
+        if et[last] >= 0:
+            assert fl[col2f[et[last]]] > fl[f]
+
+
+def test_assembly_groups_leaf_tables(S):
+    """Grouping by term count with uniform-constant folding (Sec. 4.3, 4.4,
+    App. B): for an incidence matrix every coefficient is +1 (diagonal) or
+    -1 (off-diagonal), so every group is uniform; diagonal term counts are
+    the vertex degrees."""
+    p = P.grid_problem(9, 7, cfg=1)
+    pl = S.Plan(p)
+    g = pl.export(S.EXPORT_GROUPS)
+    c = pl.export(S.EXPORT_GROUP_COEF)
+    assert g[:, 0].sum() == pl.info["nnz_K"]
+    assert np.all(g[:, 2] == 1)
+    deg = np.bincount(p.edges.ravel(), minlength=p.n)
+    diag = g[g[:, 3] == 1]
+    assert sorted(diag[:, 1]) == sorted(set(deg))
+    assert dict(zip(diag[:, 1], diag[:, 0])) == {d: int(np.sum(deg == d)) for d in set(deg)}
+    assert np.all(c[g[:, 3] == 1] == 1.0) and np.all(c[g[:, 3] == 0] == -1.0)
+    assert (g[:, 0] * g[:, 1]).sum() == pl.info["assembly_terms"]
+    pe = S.Plan(P.elasticity_problem(2, cfg=2))
+    ge = pe.export(S.EXPORT_GROUPS)
+    assert np.all(ge[ge[:, 1] > 0, 2] == 0)  # element blocks: varying constants
+
+
+@pytest.mark.parametrize("bad", ["perm_dup", "col_range", "dup_col", "dofs_range", "bad_kind", "zero_n",
+                                 "rowptr", "nan_aval"])
+def test_invalid_patterns_rejected(S, bad):
+    p = P.grid_problem(4, 4, cfg=1)
+    if bad == "perm_dup":
+        p["perm"] = p.perm.copy()
+        p.perm[1] = p.perm[0]
+    elif bad == "col_range":
+        p["colind"] = p.colind.copy()
+        p.colind[3] = p.n
+    elif bad == "dup_col":
+        p["colind"] = p.colind.copy()
+        p.colind[1] = p.colind[0]
+    elif bad == "bad_kind":
+        p["kind"] = 7
+    elif bad == "zero_n":
+        p["n"] = 0
+    elif bad == "rowptr":
+        p["rowptr"] = p.rowptr.copy()
+        p.rowptr[2] = p.rowptr[1] - 1
+    elif bad == "nan_aval":
+        p["aval"] = p.aval.copy()
+        p.aval[0] = np.nan
+    elif bad == "dofs_range":
+        p = P.elasticity_problem(1, cfg=2)
+        p["elem_dofs"] = p.elem_dofs.copy()
+        p.elem_dofs[0, 0] = p.n
+    with pytest.raises(S.SscoError) as ei:
+        S.Plan(p)
+    assert ei.value.status in (1, 2, 4)
+
+
+def test_plan_save_load_roundtrip(S, tmp_path):
+    p = P.workload("elast5")
+    pl = S.Plan(p, precision=S.FP32_REFINE)
+    f = str(tmp_path / "plan.bin")
+    pl.save(f)
+    q = S.Plan.load(f, precision=S.FP32_REFINE)
+    assert q.info == pl.info
+    for what in range(15):
+        assert np.array_equal(q.export(what), pl.export(what))
+    with open(f, "r+b") as fh:
+        fh.write(b"garbage!")
+    with pytest.raises(S.SscoError):
+        S.Plan.load(f)
+
+
+def test_fixed_dofs_are_identity_rows(S):
+    p = P.elasticity_problem(3, cfg=2)
+    pl = S.Plan(p)
+    cc = pl.export(S.EXPORT_COLCOUNT)
+    iperm = np.argsort(p.perm)
+    fixed_new = iperm[np.nonzero(p.dof_fixed)[0]]
+    assert np.all(cc[fixed_new] == 1)
+    assert np.all(pl.export(S.EXPORT_ETREE)[fixed_new] == -1)

@@ -1,0 +1,276 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances (FP64 path): K entries 1e-14 relative to max|K|; L columns
+||dL_j|| <= 1e-12 ||L_j||; relative residual ||b - K x|| / ||b|| <= 1e-10
+with the oracle's K.  FP32 + refinement: the same residual bound; the error
+against the oracle's FP64 solution is reported and bounded by
+kappa-scaled limits.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2110_12865_gb300 import problems as P
+
+pytestmark = pytest.mark.gpu
+
+RESID_TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def S():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2110_12865_gb300 import build
+    build.build()
+    from paper_2110_12865_gb300 import ssco
+    return ssco
+
+
+def run(S, probs, precision, batch=None, **kw):
+    probs_l = probs if isinstance(probs, list) else [probs]
+    B = batch if batch is not None else probs_l[0].batch
+    pl = S.Plan(probs, precision=precision, batch=B, **kw).bind()
+    vals = np.concatenate([np.asarray(p.vals[:B]) for p in probs_l], axis=1)
+    shift = np.stack([np.asarray(p.shift[:B], np.float64) for p in probs_l], axis=1).reshape(-1)
+    b = np.concatenate([p.b[:B] for p in probs_l], axis=1)
+    vt = torch.tensor(vals, device="cuda")
+    pl.numeric(vt, torch.tensor(shift, device="cuda"))
+    x = pl.solve(torch.tensor(b, device="cuda")).cpu().numpy()
+    st = pl.status()
+    return pl, x, st, vals, shift, b
+
+
+def check_against_oracle(S, pl, p, x, st, inst, sys_index, col_off=0, exact_L=True, check_K=True):
+    r = O.refactor_solve(p, inst)
+    n = p.n
+    xi = x[inst, col_off:col_off + n] if x.ndim == 2 else x
+    res = np.linalg.norm(O.symv(r.K, xi) - p.b[inst]) / np.linalg.norm(p.b[inst])
+    assert st["status"][sys_index] == 0, (st, sys_index)
+    assert res <= RESID_TOL, res
+    assert st["resid"][sys_index] <= RESID_TOL
+    err = np.linalg.norm(xi - r.x) / np.linalg.norm(r.x)
+    return r, res, err
+
+
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("kw", [{}, {"small_front_max": 32}, {"amalgamate": 0}])
+def test_fp64_grid32_L_entries(S, kw):
+    p = P.workload("grid32")
+    pl, x, st, *_ = run(S, p, S.FP64, **kw)
+    r, res, err = check_against_oracle(S, pl, p, x, st, 0, 0)
+    K = pl.export_K()[0]
+    assert np.max(np.abs(K - r.Kp.val)) <= 1e-14 * np.abs(r.Kp.val).max()
+    L = pl.export_L()[0]
+    Lc = r.S.Lcolptr
+    for j in range(p.n):
+        a, b = Lc[j], Lc[j + 1]
+        assert np.linalg.norm(L[a:b] - r.L[a:b]) <= 1e-12 * np.linalg.norm(r.L[a:b]), j
+    assert err < 1e-12
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("kw", [{}, {"small_front_max": 32}])
+def test_elasticity_small(S, prec, kw):
+    p = P.elasticity_problem(6, cfg=2)
+    precision = S.FP64 if prec == "fp64" else S.FP32_REFINE
+    pl, x, st, *_ = run(S, p, precision, **kw)
+    r, res, err = check_against_oracle(S, pl, p, x, st, 0, 0)
+    K = pl.export_K()[0]
+    assert np.max(np.abs(K - r.Kp.val)) <= 1e-14 * np.abs(r.Kp.val).max()
+    if prec == "fp64":
+        L = pl.export_L()[0]
+        Lc = r.S.Lcolptr
+        colerr = max(np.linalg.norm(L[Lc[j]:Lc[j + 1]] - r.L[Lc[j]:Lc[j + 1]]) /
+                     np.linalg.norm(r.L[Lc[j]:Lc[j + 1]]) for j in range(p.n))
+        assert colerr <= 1e-12
+        assert err < 1e-10
+    else:
+        assert st["iters"][0] >= 1
+        assert err < 1e-8
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_fp64_random_patterns(S, seed):
+    rng = np.random.default_rng(900 + seed)
+    n = int(rng.integers(1, 500))
+    p = P.random_spd_pattern(n, int(rng.integers(0, 4 * n + 1)), rng, batch=2)
+    pl, x, st, *_ = run(S, p, S.FP64, small_front_max=int(rng.choice([0, 32, 64])))
+    for inst in range(2):
+        r, res, err = check_against_oracle(S, pl, p, x, st, inst, inst)
+        L = pl.export_L()[inst]
+        Lc = r.S.Lcolptr
+        for j in range(n):
+            a, b = Lc[j], Lc[j + 1]
+            assert np.linalg.norm(L[a:b] - r.L[a:b]) <= 1e-12 * np.linalg.norm(r.L[a:b])
+
+
+def test_fp32_batched_trigrid(S):
+    p = P.trigrid_problem(24, batch=8, cfg=3)
+    pl, x, st, *_ = run(S, p, S.FP32_REFINE)
+    for inst in range(8):
+        check_against_oracle(S, pl, p, x, st, inst, inst)
+    assert np.all(st["iters"] >= 1)
+
+
+def test_multi_pattern_uneven(S):
+    probs = [P.trigrid_problem(s, 1, cfg=3, seed_offset=100 + k) for k, s in enumerate([5, 11, 17, 23, 30, 9])]
+    pl, x, st, *_ = run(S, probs, S.FP32_REFINE, batch=1)
+    off = 0
+    for k, p in enumerate(probs):
+        check_against_oracle(S, pl, p, x, st, 0, k, col_off=off)
+        off += p.n
+
+
+def test_batch_and_patterns_combined(S):
+    probs = [P.grid_problem(6, 5, batch=3, cfg=1), P.elasticity_problem(2, batch=3, cfg=2)]
+    pl, x, st, *_ = run(S, probs, S.FP64, batch=3)
+    for inst in range(3):
+        off = 0
+        for k, p in enumerate(probs):
+            check_against_oracle(S, pl, p, x, st, inst, inst * 2 + k, col_off=off)
+            off += p.n
+
+
+def test_not_spd_reports_first_column(S):
+    rng = np.random.default_rng(21)
+    found = 0
+    for t in range(10):
+        p = P.random_spd_pattern(60, 80, rng, batch=1)
+        p["vals"] = rng.uniform(-0.3, 2.0, (1, p.m))
+        p["shift"] = np.array([-0.05])
+        r = O.refactor_solve(p)
+        pl, x, st, *_ = run(S, p, S.FP64)
+        if r.bad >= 0:
+            found += 1
+            assert st["status"][0] == 3 and st["bad_col"][0] == r.bad
+        else:
+            assert st["bad_col"][0] == -1
+    assert found >= 3
+
+
+def test_nonfinite_values_flagged(S):
+    p = P.grid_problem(8, 8, batch=2, cfg=1)
+    p["vals"] = p.vals.copy()
+    p.vals[1, 5] = np.nan
+    pl, x, st, *_ = run(S, p, S.FP32_REFINE)
+    assert st["status"][0] == 0
+    assert st["status"][1] != 0
+
+
+def test_deterministic_and_host_e2e(S):
+    p = P.trigrid_problem(20, batch=3, cfg=3)
+    pl, x1, st, vals, shift, b = run(S, p, S.FP32_REFINE)
+    pl.numeric(torch.tensor(vals, device="cuda"), torch.tensor(shift, device="cuda"))
+    x2 = pl.solve(torch.tensor(b, device="cuda")).cpu().numpy()
+    assert np.array_equal(x1, x2)
+    x3 = pl.refactor_solve_host(np.ascontiguousarray(vals), np.ascontiguousarray(shift), np.ascontiguousarray(b))
+    assert np.array_equal(x1, x3)
+    assert pl.last_launch_count() > 0
+
+
+def test_plan_file_roundtrip_runs(S, tmp_path):
+    p = P.elasticity_problem(4, cfg=2)
+    pl0 = S.Plan(p, precision=S.FP32_REFINE)
+    f = str(tmp_path / "p.bin")
+    pl0.save(f)
+    pl = S.Plan.load(f, precision=S.FP32_REFINE).bind()
+    pl.numeric(torch.tensor(p.vals, device="cuda"), torch.tensor(p.shift, device="cuda"))
+    x = pl.solve(torch.tensor(p.b, device="cuda")).cpu().numpy()
+    check_against_oracle(S, pl, p, x, pl.status(), 0, 0)
+
+
+# ---------------------------------------------------------------------------
+# adjoint
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_gradient_matches_oracle(S, prec):
+    p = P.grid_problem(16, 16, batch=2, cfg=4)
+    precision = S.FP64 if prec == "fp64" else S.FP32_REFINE
+    pl, x, st, vals, shift, b = run(S, p, precision)
+    xt = torch.tensor(x, device="cuda")
+    xbar = 2.0 * (xt - torch.tensor(p.xstar, device="cuda"))
+    vbar, sbar, bbar = pl.backward(xt, xbar)
+    vbar, sbar, bbar = vbar.cpu().numpy(), sbar.cpu().numpy(), bbar.cpu().numpy()
+    for inst in range(2):
+        r = O.refactor_solve(p, inst)
+        gv, gs, gb = O.backward(p, r, 2.0 * (r.x - p.xstar[inst]), inst)
+        tol = 1e-9 if prec == "fp64" else 1e-7
+        assert np.max(np.abs(vbar[inst] - gv)) <= tol * np.abs(gv).max()
+        assert abs(sbar[inst] - gs) <= tol * abs(gs)
+        assert np.max(np.abs(bbar[inst] - gb)) <= tol * np.abs(gb).max()
+
+
+def test_gradient_elasticity(S):
+    p = P.elasticity_problem(3, cfg=2)
+    p["xstar"] = np.random.default_rng(2).standard_normal((1, p.n)) * 1e-4
+    pl, x, st, *_ = run(S, p, S.FP64)
+    xt = torch.tensor(x, device="cuda")
+    xbar = 2.0 * (xt - torch.tensor(p.xstar, device="cuda"))
+    vbar, _, _ = pl.backward(xt, xbar)
+    r = O.refactor_solve(p)
+    gv, _, _ = O.backward(p, r, 2.0 * (r.x - p.xstar[0]))
+    assert np.max(np.abs(vbar.cpu().numpy()[0] - gv)) <= 1e-9 * np.abs(gv).max()
+
+
+def test_autograd_function(S):
+    p = P.grid_problem(12, 10, batch=1, cfg=4)
+    pl = S.Plan(p, precision=S.FP64).bind()
+    w = torch.tensor(p.vals, device="cuda", requires_grad=True)
+    s = torch.tensor(p.shift, device="cuda", requires_grad=True)
+    b = torch.tensor(p.b, device="cuda", requires_grad=True)
+    x = S.ssco_solve(pl, w, s, b)
+    loss = ((x - torch.tensor(p.xstar, device="cuda")) ** 2).sum()
+    loss.backward()
+    r = O.refactor_solve(p)
+    gv, gs, gb = O.backward(p, r, 2.0 * (r.x - p.xstar[0]))
+    assert np.max(np.abs(w.grad.cpu().numpy()[0] - gv)) <= 1e-9 * np.abs(gv).max()
+    assert abs(s.grad.item() - gs) <= 1e-9 * abs(gs)
+    assert np.max(np.abs(b.grad.cpu().numpy()[0] - gb)) <= 1e-9 * np.abs(gb).max()
+
+
+# ---------------------------------------------------------------------------
+# full-size configurations (the bench's launch configuration)
+# ---------------------------------------------------------------------------
+def test_full_grid32_fp64(S):
+    p = P.workload("grid32")
+    pl, x, st, *_ = run(S, p, S.FP64)
+    check_against_oracle(S, pl, p, x, st, 0, 0)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_full_elast24(S, prec):
+    p = P.workload("elast24")
+    precision = S.FP64 if prec == "fp64" else S.FP32_REFINE
+    pl, x, st, *_ = run(S, p, precision)
+    r, res, err = check_against_oracle(S, pl, p, x, st, 0, 0)
+    if prec == "fp64":
+        L = pl.export_L()[0]
+        rng = np.random.default_rng(0)
+        Lc = r.S.Lcolptr
+        for j in rng.choice(p.n, 2000, replace=False):
+            a, b = Lc[j], Lc[j + 1]
+            assert np.linalg.norm(L[a:b] - r.L[a:b]) <= 1e-12 * np.linalg.norm(r.L[a:b])
+
+
+def test_full_arap128_batch256(S):
+    p = P.workload("arap128")
+    pl, x, st, *_ = run(S, p, S.FP32_REFINE)
+    assert np.all(st["status"] == 0) and np.all(st["resid"] <= RESID_TOL)
+    for inst in [0, 77, 255]:
+        K = O.assemble(p, inst)
+        res = np.linalg.norm(O.symv(K, x[inst]) - p.b[inst]) / np.linalg.norm(p.b[inst])
+        assert res <= RESID_TOL
+
+
+def test_full_grid256_gradient(S):
+    p = P.workload("grid256")
+    pl, x, st, *_ = run(S, p, S.FP64)
+    r, res, err = check_against_oracle(S, pl, p, x, st, 0, 0)
+    xt = torch.tensor(x, device="cuda")
+    xbar = 2.0 * (xt - torch.tensor(p.xstar, device="cuda"))
+    vbar, sbar, bbar = pl.backward(xt, xbar)
+    gv, gs, gb = O.backward(p, r, 2.0 * (r.x - p.xstar[0]))
+    vb = vbar.cpu().numpy()[0]
+    assert np.max(np.abs(vb - gv)) <= 1e-8 * np.abs(gv).max()
