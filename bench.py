@@ -1,0 +1,467 @@
+#!/usr/bin/env python
+"""Bench: batched refactor+solve/s on one GB300 (or N, one process each).
+
+Default workload (the batched configuration): 256 value sets on one
+triangulated 128x128 grid (cotangent weights from per-instance jittered
+vertices, per-instance shift) plus 64 single-instance triangulated grids of
+uneven size (32^2 .. 256^2); FP32 factorization + FP64 iterative refinement
+to relative residual 1e-10.  A step = assemble + refactor + solve of all 320
+systems.  Inputs are resident in HBM when the timed region starts; L2 is
+flushed (256 MiB write) between timed steps.  The same steps are also run in
+the plain FP64 form for comparison, end to end through the host-buffer C-ABI
+call, and once more with per-kernel CUDA events for the roofline.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload arap|elast24|grid32|grid256|elast48]
+
+Under torchrun each rank solves its own value sets (weak scaling; no data-path
+collective).  `--impl reference` times the FP64 CPU oracle (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2110_12865_gb300 import problems as P  # noqa: E402
+
+FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
+FP64_PEAK_TFLOPS = 1.25                                   # GB300 FP64 (recipe table)
+HBM_FALLBACK_GBS = 6800.0
+HBM_KINDS = {"assemble", "fwd_solve", "bwd_solve", "resid", "vector", "check", "big_init", "big_kscatter", "grad"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="arap")
+    ap.add_argument("--no-extras", action="store_true", help="only the timed FP32 region")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# workloads: list of (problem-or-list, batch) sharing one step
+# ---------------------------------------------------------------------------
+def make_workload(name: str, rank: int):
+    if name == "arap":
+        a = P.trigrid_problem(128, batch=256, cfg=3, seed_offset=rank * 256)
+        u = [P.trigrid_problem(s, 1, cfg=3, seed_offset=100_000 + rank * 64 + k)
+             for k, s in enumerate(P.uneven_trigrid_sides(64))]
+        desc = {"workload": "arap128x256+uneven64", "patterns": 1 + 64, "batch": 256,
+                "n_main": a.n, "n_uneven_total": int(sum(q.n for q in u)),
+                "sides_uneven": [32, 256]}
+        return [(a, 256), (u, 1)], desc
+    if name == "elast24":
+        e = P.elasticity_problem(24, batch=1, cfg=2)
+        if rank:
+            e = _reseed_elast(e, rank)
+        return [(e, 1)], {"workload": "elast24 (24^3 Kuhn tets, 46875 DOF)", "batch": 1, "n": e.n}
+    if name == "elast48":
+        e = P.elasticity_problem(48, batch=16, cfg=5)
+        return [(e, 16)], {"workload": "elast48x16 (48^3 Kuhn tets, 352947 DOF)", "batch": 16, "n": e.n}
+    if name == "grid32":
+        g = P.grid_problem(32, 32, batch=1, cfg=1)
+        return [(g, 1)], {"workload": "grid32 (5-point, n=1024)", "batch": 1, "n": g.n}
+    if name == "grid256":
+        g = P.grid_problem(256, 256, batch=1, cfg=4, w_dtype=np.float32)
+        return [(g, 1)], {"workload": "grid256 (5-point, n=65536, w fp32)", "batch": 1, "n": g.n}
+    raise SystemExit(f"unknown workload {name}")
+
+
+def _reseed_elast(e, rank):
+    rng = np.random.default_rng(P.seed_for(2, 1000 + rank))
+    e["vals"] = 10.0 ** rng.uniform(3.0, 5.0, e.vals.shape)
+    b = rng.standard_normal(e.b.shape)
+    b[:, e.dof_fixed] = 0.0
+    e["b"] = b
+    return e
+
+
+def probs_of(item):
+    return item if isinstance(item, list) else [item]
+
+
+def stacked_inputs(item, B):
+    ps = probs_of(item)
+    vals = np.concatenate([np.asarray(p.vals[:B]) for p in ps], axis=1)
+    shift = np.stack([np.asarray(p.shift[:B], np.float64) for p in ps], axis=1).reshape(-1)
+    b = np.concatenate([p.b[:B] for p in ps], axis=1)
+    return np.ascontiguousarray(vals), np.ascontiguousarray(shift), np.ascontiguousarray(b)
+
+
+def units_of(work):
+    return sum(B * len(probs_of(item)) for item, B in work)
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        mhz, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                mhz.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not mhz:
+            return None
+        return {"sm_mhz": statistics.median(mhz), "sm_max_mhz": max(mx), "samples": len(mhz),
+                "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2110_12865_gb300 import build as B
+    B.build()
+    from paper_2110_12865_gb300 import ssco as S
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    work, desc = make_workload(args.workload, rank)
+    units = units_of(work)
+    stream = torch.cuda.current_stream()
+
+    def setup(precision):
+        plans, dev_in, host_in = [], [], []
+        for item, Bt in work:
+            pl = S.Plan(item, precision=precision, batch=Bt).bind(dev)
+            v, s, b = stacked_inputs(item, Bt)
+            dev_in.append((torch.tensor(v, device=dev), torch.tensor(s, device=dev), torch.tensor(b, device=dev),
+                           torch.empty(b.shape, dtype=torch.float64, device=dev)))
+            host_in.append((torch.tensor(v).pin_memory(), torch.tensor(s).pin_memory(), torch.tensor(b).pin_memory(),
+                            torch.empty(b.shape, dtype=torch.float64).pin_memory()))
+            plans.append(pl)
+        return plans, dev_in, host_in
+
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def step(plans, dev_in):
+        n = 0
+        for pl, (v, s, b, x) in zip(plans, dev_in):
+            pl.numeric(v, s)
+            n += pl.last_launch_count()
+            pl.solve(b, x)
+            n += pl.last_launch_count()
+        return n
+
+    def timed(plans, dev_in, K, W, sampler=None):
+        for _ in range(W):
+            step(plans, dev_in)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        if sampler:
+            sampler.start()
+        ms, launches = [], 0
+        t0 = time.perf_counter()
+        for _ in range(K):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            launches += step(plans, dev_in)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        clocks = sampler.stop() if sampler else None
+        if dist:
+            dist.barrier()
+        return ms, launches, wall, clocks
+
+    def status_summary(plans):
+        res, its, ok = [], [], True
+        for pl in plans:
+            st = pl.status()
+            ok &= bool(np.all(st["status"] == 0))
+            res.append(float(st["resid"].max()))
+            its += list(st["iters"])
+        return ok, max(res), its
+
+    # ---- headline: FP32 factor + FP64 refinement -------------------------
+    plans32, dev32, host32 = setup(S.FP32_REFINE)
+    sampler = ClockSampler(local_rank)
+    ms, launches, wall, clocks = timed(plans32, dev32, args.steps, args.warmup, sampler)
+    ok32, res32, its32 = status_summary(plans32)
+    tot_ms = sum(ms)
+    if dist:
+        t = torch.tensor([tot_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    value = units * world * args.steps / (tot_ms / 1e3)
+
+    out = {
+        "metric": "batched refactor+solve/s (FP32 factor + FP64 refinement to rel. residual 1e-10)",
+        "value": value, "unit": "systems/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 factor / f64 residual+update", "data": "synthetic (seeded meshes, see DESIGN.md)",
+        "config": dict(desc, precision="fp32+refine", units_per_step=units, l2="flushed between steps "
+                       "(256 MiB write); per-step working set also exceeds L2",
+                       parallelism=f"independent value sets per rank x{world}"),
+        "gpu_launches": launches,
+        "all_status_ok": ok32, "max_rel_residual": res32,
+        "refine_iters": {"min": int(min(its32)), "max": int(max(its32)), "mean": float(np.mean(its32))},
+        "wall_s_timed": wall,
+    }
+    if clocks:
+        out["clocks"] = clocks
+    xs32 = _pick_samples(work, dev32)
+    if args.no_extras:
+        out["_xcheck"] = {"fp32": xs32}
+        return out, rank
+
+    # ---- per-kernel events over a repeat of the timed steps ---------------
+    for pl in plans32:
+        pl.profile_enable(200_000)
+    for _ in range(args.steps):
+        flush.fill_(1)
+        step(plans32, dev32)
+    stats = {}
+    for pl in plans32:
+        for k, v in pl.profile_read().items():
+            a = stats.setdefault(k, {"launches": 0, "ms": 0.0, "flops": 0.0, "bytes": 0.0})
+            for f in a:
+                a[f] += v[f]
+        pl.profile_enable(0)
+    kernels = {k: dict(v, share=v["ms"] / max(1e-12, sum(x["ms"] for x in stats.values())))
+               for k, v in stats.items() if v["launches"]}
+    top = max(kernels, key=lambda k: kernels[k]["ms"])
+    kv = kernels[top]
+    peaks = measured_peaks()
+    if top in HBM_KINDS:
+        peak = peaks["hbm_gbs"] if peaks else HBM_FALLBACK_GBS
+        achieved = kv["bytes"] / (kv["ms"] / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback"}
+    else:
+        peak = FP32_SIMT_PEAK_TFLOPS
+        achieved = kv["flops"] / (kv["ms"] / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
+    roof.update({"frac": achieved / peak, "traffic": None, "kernel": top,
+                 "launches": kv["launches"], "avg_launch_us": kv["ms"] * 1e3 / kv["launches"],
+                 "measured": "CUDA events per launch on the launch stream, over a repeat of the timed steps"})
+    out["roofline"] = roof
+    out["kernels"] = {k: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps,
+                          "share": round(v["share"], 4),
+                          "GBps": v["bytes"] / max(v["ms"], 1e-9) / 1e6,
+                          "TFLOPs": v["flops"] / max(v["ms"], 1e-9) / 1e9} for k, v in kernels.items()}
+
+    # ---- end to end through the host-buffer C-ABI call --------------------
+    def e2e_step():
+        for pl, (v, s, b, x) in zip(plans32, host32):
+            pl.refactor_solve_host(v, s, b, x)
+    for _ in range(args.warmup):
+        e2e_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    h2d = sum(v.numel() * v.element_size() + s.numel() * 8 + b.numel() * 8 for v, s, b, _ in host32)
+    d2h = sum(x.numel() * 8 for *_, x in host32)
+    out["e2e"] = {"value": units * world * args.steps / e2e_s, "unit": "systems/s",
+                  "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                  "api": "ssco_refactor_solve_host (pinned host buffers, copies inside the timed region)"}
+
+    # ---- the plain FP64 GPU form on the same work -------------------------
+    del plans32, dev32, host32
+    torch.cuda.empty_cache()
+    plans64, dev64, _ = setup(S.FP64)
+    k64 = max(3, args.steps // 2)
+    ms64, _, _, _ = timed(plans64, dev64, k64, 2)
+    ok64, res64, _ = status_summary(plans64)
+    out["fp64"] = {"value": units * world * k64 / (sum(ms64) / 1e3), "unit": "systems/s",
+                   "ms_per_step": sum(ms64) / k64, "all_status_ok": ok64, "max_rel_residual": res64,
+                   "steps": k64}
+    out["fp32_refine_over_fp64"] = out["value"] / out["fp64"]["value"]
+    out["_xcheck"] = {"fp32": xs32, "fp64": _pick_samples(work, dev64)}
+    return out, rank
+
+
+def _pick_samples(work, dev_in):
+    """A few (problem, instance, GPU x) triples for the error-vs-oracle check."""
+    picks = []
+    for (item, Bt), (_, _, _, x) in zip(work, dev_in):
+        ps = probs_of(item)
+        xh = x.cpu().numpy()
+        if len(ps) == 1:
+            for i in sorted({0, Bt - 1}):
+                picks.append((ps[0], i, xh[i]))
+        else:
+            off = 0
+            for k, p in enumerate(ps):
+                if k in (0, len(ps) - 1):
+                    picks.append((p, 0, xh[0, off:off + p.n]))
+                off += p.n
+    return picks
+
+
+def oracle_errors(picks):
+    """max ||x_gpu - x_oracle|| / ||x_oracle|| over the picked systems."""
+    from oracle import oracle as O
+    err = 0.0
+    for p, i, x in picks:
+        r = O.refactor_solve(p, i)
+        err = max(err, float(np.linalg.norm(x - r.x) / np.linalg.norm(r.x)))
+    return {"max_rel_err_vs_oracle": err, "systems_checked": len(picks)}
+
+
+# ---------------------------------------------------------------------------
+def oracle_sample(work, frac_main=None, n_uneven=None, rank=0):
+    """Oracle work list: (problem, instance) pairs of a bounded sample."""
+    items = []
+    for item, Bt in work:
+        ps = probs_of(item)
+        if len(ps) == 1:
+            nb = Bt if frac_main is None else max(1, min(Bt, frac_main))
+            items += [(ps[0], i) for i in range(nb)]
+        else:
+            sel = ps if n_uneven is None else ps[:: max(1, len(ps) // n_uneven)][:n_uneven]
+            items += [(p, 0) for p in sel]
+    return items
+
+
+def time_oracle(items, symbs=None):
+    from oracle import oracle as O
+    t0 = time.perf_counter()
+    for p, i in items:
+        O.refactor_solve(p, i, symb=symbs[id(p)] if symbs else None)
+    return time.perf_counter() - t0
+
+
+def prepare_symbolic(items):
+    from oracle import oracle as O
+    symbs = {}
+    for p, i in items:
+        if id(p) not in symbs:
+            symbs[id(p)] = O.Symbolic(O.permute(O.assemble(p, i), p.perm))
+    return symbs
+
+
+def cpu_baseline(args, work):
+    if args.workload == "arap":
+        items = oracle_sample(work)            # the whole step: 256 + 64 systems
+        sample = "all 320 systems of one step (256 ARAP + 64 uneven), FP64 oracle, symbolic excluded"
+    elif args.workload == "elast48":
+        return None
+    else:
+        items = oracle_sample(work)
+        sample = "one full step (all systems), FP64 oracle, symbolic excluded"
+    symbs = prepare_symbolic(items)
+    t = time_oracle(items, symbs)
+    return {"value": len(items) / t, "unit": "systems/s", "cores": 1, "kind": "oracle", "sample": sample,
+            "seconds": t}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    work, desc = make_workload(args.workload, 0)
+    if args.workload == "arap":
+        items = oracle_sample(work, frac_main=16, n_uneven=4)
+        sample = "16 ARAP instances + 4 uneven grids per step"
+    else:
+        items = oracle_sample(work)
+        sample = "all systems of one step"
+    symbs = prepare_symbolic(items)
+    for _ in range(args.warmup):
+        time_oracle(items[:2], symbs)
+    times = [time_oracle(items, symbs) for _ in range(args.steps)]
+    tot = sum(times)
+    value = len(items) * args.steps / tot
+    return {"impl": "reference", "metric": "batched refactor+solve/s (FP32 factor + FP64 refinement to rel. "
+            "residual 1e-10)", "value": value, "unit": "systems/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(desc, precision="fp64 oracle"),
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": sample, "value": value, "unit": "systems/s"},
+            "e2e": {"value": value, "unit": "systems/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    out, r = run_ours(args, rank, world, local_rank)
+    if r == 0:
+        xc = out.pop("_xcheck", None) or {}
+        if args.workload != "elast48":
+            out["error_vs_oracle"] = {k: oracle_errors(v) for k, v in xc.items()}
+        if not args.no_extras and world == 1:
+            work, _ = make_workload(args.workload, 0)
+            out["cpu_baseline"] = cpu_baseline(args, work)
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

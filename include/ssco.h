@@ -202,12 +202,12 @@ ssco_status ssco_backward(ssco_plan plan, const double* x, const double* xbar, d
 ssco_status ssco_status_get(ssco_plan plan, void* stream, int32_t* status, int32_t* iters,
                             double* resid, int32_t* bad_col);
 
-/* Writes the factor in CSC order of SSCO_EXPORT_L_ROWIND, as double
- * [B][nnz_L] (device).  Asynchronous. */
-ssco_status ssco_export_L(ssco_plan plan, double* dev_out, void* stream);
-/* Writes K~ values in CSC order of SSCO_EXPORT_K_ROWIND, double [B][nnz_K]
- * (device).  Asynchronous. */
-ssco_status ssco_export_K(ssco_plan plan, double* dev_out, void* stream);
+/* Synchronizes `stream`, then writes the factor in the CSC order of
+ * SSCO_EXPORT_L_ROWIND to the HOST array host_out, as double [B][nnz_L]. */
+ssco_status ssco_export_L(ssco_plan plan, double* host_out, void* stream);
+/* Synchronizes `stream`, then writes K~ in the CSC order of
+ * SSCO_EXPORT_K_ROWIND to the HOST array host_out, double [B][nnz_K]. */
+ssco_status ssco_export_K(ssco_plan plan, double* host_out, void* stream);
 
 /* End-to-end call on HOST buffers: copies vals/shift/b to the device
  * (staging areas inside the workspace), runs numeric + solve, copies x back
@@ -218,6 +218,40 @@ ssco_status ssco_refactor_solve_host(ssco_plan plan, const void* vals, int32_t v
 /* Number of kernel launches the last ssco_numeric / ssco_solve /
  * ssco_backward / ssco_refactor_solve_host call issued (host counter). */
 int64_t ssco_last_launch_count(ssco_plan plan);
+
+/* Per-kernel timing.  ssco_profile_enable(plan, max_launches) creates a pool
+ * of 2*max_launches CUDA events (0 releases it and turns profiling off);
+ * while on, every kernel launch is bracketed by events on its own stream
+ * and its algorithmic work (flops, bytes) is recorded.  Launches beyond the
+ * pool are not recorded.  ssco_profile_read synchronizes the device, sums
+ * the records by kernel kind into out[SSCO_K_COUNT] and clears them. */
+enum {
+    SSCO_K_ASSEMBLE = 0,     /* assembly gather-MAC over the leaf tables      */
+    SSCO_K_FRONT_SMALL = 1,  /* one-CTA front factorization in shared memory  */
+    SSCO_K_BIG_INIT = 2,     /* big front: pull children's update matrices    */
+    SSCO_K_BIG_KSCATTER = 3, /* big front: add K entries                      */
+    SSCO_K_BIG_GEMM = 4,     /* big front: left-looking block-column update   */
+    SSCO_K_BIG_POTRF = 5,    /* big front: diagonal block + triangular solve  */
+    SSCO_K_BIG_SYRK = 6,     /* big front: update matrix -= L21 L21^T         */
+    SSCO_K_FWD = 7,          /* forward solve, one level                      */
+    SSCO_K_BWD = 8,          /* backward solve, one level                     */
+    SSCO_K_RESID = 9,        /* FP64 residual b - K x                         */
+    SSCO_K_CHECK = 10,       /* per-system norms and refinement decision      */
+    SSCO_K_VECTOR = 11,      /* permutations, casts, updates, status fills    */
+    SSCO_K_GRAD = 12,        /* adjoint reductions                            */
+    SSCO_K_COUNT = 13
+};
+typedef struct {
+    int32_t kind;
+    int32_t reserved;
+    int64_t launches;
+    double ms;     /* summed event time of the recorded launches */
+    double flops;  /* summed algorithmic floating-point operations */
+    double bytes;  /* summed algorithmic bytes moved              */
+} ssco_kernel_stat;
+ssco_status ssco_profile_enable(ssco_plan plan, int32_t max_launches);
+ssco_status ssco_profile_read(ssco_plan plan, ssco_kernel_stat* out);
+const char* ssco_kernel_name(int32_t kind);
 
 const char* ssco_last_error(ssco_plan plan);
 const char* ssco_status_string(ssco_status s);

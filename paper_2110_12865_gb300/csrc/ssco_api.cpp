@@ -433,6 +433,22 @@ ssco_status ssco_refactor_solve_host(ssco_plan h, const void* vals, int32_t vals
 
 int64_t ssco_last_launch_count(ssco_plan h) { return h ? h->P.launches : 0; }
 
+ssco_status ssco_profile_enable(ssco_plan h, int32_t max_launches) {
+    if (!h || max_launches < 0) return fail(h, SSCO_ERR_INVALID_ARG, "bad argument");
+    int e = profile_enable(h->P, max_launches);
+    if (e) return cuda_fail(h, e, "event pool");
+    return SSCO_OK;
+}
+
+ssco_status ssco_profile_read(ssco_plan h, ssco_kernel_stat* out) {
+    if (!h || !out) return fail(h, SSCO_ERR_INVALID_ARG, "NULL argument");
+    int e = profile_read(h->P, out);
+    if (e) return cuda_fail(h, e, "profile read");
+    return SSCO_OK;
+}
+
+const char* ssco_kernel_name(int32_t kind) { return kernel_kind_name(kind); }
+
 ssco_status ssco_plan_save(ssco_plan h, const char* path) {
     if (!h || !path) return fail(h, SSCO_ERR_INVALID_ARG, "NULL argument");
     Writer w;
@@ -470,6 +486,7 @@ ssco_status ssco_plan_load(const char* path, ssco_plan* out) {
 
 void ssco_destroy(ssco_plan h) {
     if (!h) return;
+    if (!h->P.ev_pool.empty()) profile_enable(h->P, 0);
     if (h->P.h_flag) cudaFreeHost(h->P.h_flag);
     delete h;
 }

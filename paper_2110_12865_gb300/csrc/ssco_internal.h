@@ -103,6 +103,14 @@ struct WsLayout {
     size_t total;
 };
 
+// One profiled launch: two CUDA events from the plan's pool and the
+// algorithmic work of the launch.
+struct ProfRec {
+    int32_t kind;
+    int32_t ev;
+    double flops, bytes;
+};
+
 struct PatMeta {
     int32_t kind, n, m, dim;
     int64_t n_off, m_off;
@@ -185,6 +193,12 @@ struct Plan {
 
     std::string last_error;
     int64_t launches = 0;
+
+    // per-kernel CUDA-event profiling (ssco_profile_enable / _read)
+    bool prof = false;
+    std::vector<void*> ev_pool;  // cudaEvent_t
+    size_t ev_used = 0;
+    std::vector<ProfRec> prof_recs;
 };
 
 // symbolic phase (ssco_symbolic.cpp)
@@ -201,5 +215,8 @@ int launch_backward(Plan& P, const double* x, const double* xbar, double* vals_b
                     double* shift_bar, double* b_bar, void* stream);
 int launch_reset_status(Plan& P, void* stream);
 int kernels_set_attributes(Plan& P);
+const char* kernel_kind_name(int kind);
+int profile_enable(Plan& P, int32_t max_launches);
+int profile_read(Plan& P, ssco_kernel_stat* out);
 
 }  // namespace ssco

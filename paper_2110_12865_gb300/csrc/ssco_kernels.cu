@@ -29,8 +29,6 @@ namespace ssco {
 
 namespace {
 
-constexpr int kSmemMax = 227 * 1024;
-
 __device__ __forceinline__ double warp_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
@@ -436,6 +434,16 @@ __global__ void __launch_bounds__(256) k_big_syrk(const DevTables t, const int32
 // --------------------------------------------------------------------------
 // a5: level-scheduled solves, one CTA per (front, instance).
 // --------------------------------------------------------------------------
+// Stage the lower triangle of the 32x32 diagonal block starting at (jb, jb).
+template <class T>
+__device__ __forceinline__ void stage_diag(T (*Ld)[33], const T* __restrict__ Pb, int r, int jb, int nbk, int tid,
+                                           int nth) {
+    for (int e = tid; e < 32 * 32; e += nth) {
+        const int i = e & 31, c = e >> 5;
+        Ld[i][c] = (i < nbk && c <= i) ? Pb[(int64_t)(jb + c) * r + jb + i] : T(0);
+    }
+}
+
 template <class T>
 __global__ void __launch_bounds__(256) k_fwd(const DevTables t, const int32_t* __restrict__ list,
                                              const T* __restrict__ panel, int64_t panel_total,
@@ -444,6 +452,7 @@ __global__ void __launch_bounds__(256) k_fwd(const DevTables t, const int32_t* _
                                              int32_t n_pats) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* v = reinterpret_cast<T*>(smem_raw);
+    __shared__ T Ld[2][32][33];
     __shared__ T yblk[32];
     const FrontDesc d = t.fronts[list[blockIdx.x]];
     const int b = blockIdx.y;
@@ -454,6 +463,7 @@ __global__ void __launch_bounds__(256) k_fwd(const DevTables t, const int32_t* _
     const T* Pb = panel + (int64_t)b * panel_total + d.panel_off;
     T* pv = pvec + (int64_t)b * pvec_total;
     for (int k = tid; k < r; k += nth) v[k] = k < w ? vb[d.f + k] : T(0);
+    stage_diag(Ld[0], Pb, r, 0, min(32, w), tid, nth);
     for (int c = 0; c < d.nchild; ++c) {
         __syncthreads();
         const FrontDesc cd = t.fronts[t.child_ids[d.child_off + c]];
@@ -462,15 +472,16 @@ __global__ void __launch_bounds__(256) k_fwd(const DevTables t, const int32_t* _
         for (int k = tid; k < rc; k += nth) v[map[k]] += pv[cd.pvec_off + k];
     }
     __syncthreads();
+    int buf = 0;
     for (int jb = 0; jb < w; jb += 32) {
         const int nbk = min(32, w - jb);
         if (tid < 32) {
             const int l = tid;
             T val = l < nbk ? v[jb + l] : T(0);
             for (int j = 0; j < nbk; ++j) {
-                const T yj = __shfl_sync(0xffffffffu, val, j) / Pb[(int64_t)(jb + j) * r + jb + j];
+                const T yj = __shfl_sync(0xffffffffu, val, j) / Ld[buf][j][j];
                 if (l == j) val = yj;
-                if (l > j && l < nbk) val -= Pb[(int64_t)(jb + j) * r + jb + l] * yj;
+                if (l > j) val -= Ld[buf][l][j] * yj;
             }
             if (l < nbk) {
                 v[jb + l] = val;
@@ -478,11 +489,14 @@ __global__ void __launch_bounds__(256) k_fwd(const DevTables t, const int32_t* _
             }
         }
         __syncthreads();
+        if (jb + 32 < w) stage_diag(Ld[buf ^ 1], Pb, r, jb + 32, min(32, w - jb - 32), tid, nth);
         for (int i = jb + nbk + tid; i < r; i += nth) {
             T s = T(0);
-            for (int j = 0; j < nbk; ++j) s += Pb[(int64_t)(jb + j) * r + i] * yblk[j];
+            const T* col = Pb + (int64_t)jb * r + i;
+            for (int j = 0; j < nbk; ++j) s += col[(int64_t)j * r] * yblk[j];
             v[i] -= s;
         }
+        buf ^= 1;
         __syncthreads();
     }
     for (int k = tid; k < w; k += nth) vb[d.f + k] = v[k];
@@ -496,6 +510,7 @@ __global__ void __launch_bounds__(256) k_bwd(const DevTables t, const int32_t* _
                                              int32_t n_pats) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* v = reinterpret_cast<T*>(smem_raw);
+    __shared__ T Ld[32][33];
     __shared__ T dots[32];
     const FrontDesc d = t.fronts[list[blockIdx.x]];
     const int b = blockIdx.y;
@@ -512,6 +527,7 @@ __global__ void __launch_bounds__(256) k_bwd(const DevTables t, const int32_t* _
     for (int bi = nblk - 1; bi >= 0; --bi) {
         const int jb = bi * 32;
         const int nbk = min(32, w - jb);
+        stage_diag(Ld, Pb, r, jb, nbk, tid, nth);
         for (int c = warp; c < nbk; c += nw) {
             const T* col = Pb + (int64_t)(jb + c) * r;
             T s = T(0);
@@ -524,9 +540,9 @@ __global__ void __launch_bounds__(256) k_bwd(const DevTables t, const int32_t* _
             const int l = tid;
             T val = l < nbk ? v[jb + l] - dots[l] : T(0);
             for (int j = nbk - 1; j >= 0; --j) {
-                const T xj = __shfl_sync(0xffffffffu, val, j) / Pb[(int64_t)(jb + j) * r + jb + j];
+                const T xj = __shfl_sync(0xffffffffu, val, j) / Ld[j][j];
                 if (l == j) val = xj;
-                if (l < j) val -= Pb[(int64_t)(jb + l) * r + jb + j] * xj;
+                if (l < j) val -= Ld[j][l] * xj;
             }
             if (l < nbk) v[jb + l] = val;
         }
@@ -737,6 +753,63 @@ T* wsp(Plan& P, size_t off) {
     return reinterpret_cast<T*>(P.d_ws + off);
 }
 
+// Brackets one launch with two pooled events when profiling is on.
+struct Prof {
+    Plan& P;
+    cudaStream_t s;
+    int kind;
+    int ev = -1;
+    Prof(Plan& p, cudaStream_t st, int k) : P(p), s(st), kind(k) {
+        P.launches++;
+        if (P.prof && P.ev_used + 2 <= P.ev_pool.size()) {
+            ev = (int)P.ev_used;
+            P.ev_used += 2;
+            cudaEventRecord((cudaEvent_t)P.ev_pool[ev], s);
+        }
+    }
+    void done(double flops, double bytes) {
+        if (ev < 0) return;
+        cudaEventRecord((cudaEvent_t)P.ev_pool[ev + 1], s);
+        P.prof_recs.push_back(ProfRec{kind, ev, flops, bytes});
+    }
+};
+
+// algorithmic work of one launch over a front list (host, profiling only)
+struct Work {
+    double flops = 0, bytes = 0;
+};
+
+Work work_front_small(const Plan& P, const LaunchList& ll) {
+    Work w;
+    for (int32_t q = 0; q < ll.count; ++q) {
+        const FrontDesc& d = P.fronts[P.front_lists[ll.list_off + q]];
+        for (int32_t j = 0; j < d.w; ++j) w.flops += (double)(d.r - j) * (d.r - j);
+        double ru = d.r - d.w;
+        w.bytes += d.klist_n * 16.0 + ((double)d.r * d.w + ru * (ru + 1) / 2) * P.tsize;
+        for (int32_t c = 0; c < d.nchild; ++c) {
+            const FrontDesc& cd = P.fronts[P.child_ids[d.child_off + c]];
+            double rc = cd.r - cd.w;
+            w.bytes += rc * (rc + 1) / 2 * P.tsize + rc * 4;
+        }
+    }
+    w.flops *= P.B;
+    w.bytes *= P.B;
+    return w;
+}
+
+Work work_solve(const Plan& P, const LaunchList& ll) {
+    Work w;
+    for (int32_t q = 0; q < ll.count; ++q) {
+        const FrontDesc& d = P.fronts[P.front_lists[ll.list_off + q]];
+        double ent = (double)d.r * d.w - (double)d.w * (d.w - 1) / 2;
+        w.flops += 2 * ent;
+        w.bytes += ent * P.tsize + 2.0 * d.r * P.tsize;
+    }
+    w.flops *= P.B;
+    w.bytes *= P.B;
+    return w;
+}
+
 template <class T>
 int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cudaStream_t s) {
     const int B = P.B;
@@ -745,9 +818,13 @@ int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cud
     T* panel = wsp<T>(P, P.ws.panel);
     T* upd = wsp<T>(P, P.ws.upd);
     int32_t* bad = wsp<int32_t>(P, P.ws.bad_col);
-    k_fill_i32<<<cdiv(S, 256), 256, 0, s>>>(bad, S, INT_MAX);
-    P.launches++;
+    {
+        Prof pr(P, s, SSCO_K_VECTOR);
+        k_fill_i32<<<cdiv(S, 256), 256, 0, s>>>(bad, S, INT_MAX);
+        pr.done(0, S * 4.0);
+    }
     if (!P.chunks.empty()) {
+        Prof pr(P, s, SSCO_K_ASSEMBLE);
         dim3 g((unsigned)P.chunks.size(), B);
         if (vdt == SSCO_VALS_F64)
             k_assemble<double><<<g, 256, 0, s>>>(P.dt.groups, P.dt.chunks, P.dt.asm_idx, P.dt.asm_coef,
@@ -755,38 +832,108 @@ int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cud
         else
             k_assemble<float><<<g, 256, 0, s>>>(P.dt.groups, P.dt.chunks, P.dt.asm_idx, P.dt.asm_coef,
                                                 (const float*)vals, P.m, shift, P.n_pats, K, P.nnzK);
-        P.launches++;
+        if (pr.ev >= 0) {
+            double fl = 0, by = 0, sv = vdt == SSCO_VALS_F64 ? 8 : 4;
+            for (const AsmGroup& g2 : P.groups) {
+                double t = (double)g2.nmem * g2.nterms;
+                fl += 2 * t;
+                by += t * (4 + sv + (g2.uniform ? 0 : 8)) + g2.nmem * 8.0;
+            }
+            pr.done(fl * B, by * B);
+        }
     }
     for (const LaunchList& ll : P.fact_launches) {
         const int32_t* list = P.dt.front_lists + ll.list_off;
         if (ll.cls > 0) {
+            Prof pr(P, s, SSCO_K_FRONT_SMALL);
             const int nw = ll.cls <= 32 ? 2 : (ll.cls <= 64 ? 4 : 8);
             const size_t smem = (size_t)ll.rmax * ll.rmax * sizeof(T);
             k_front_small<T><<<dim3(ll.count, B), dim3(32, nw), smem, s>>>(P.dt, list, K, P.nnzK, panel,
                                                                            P.panel_total, upd, P.upd_total, bad,
                                                                            P.n_pats);
-            P.launches++;
-        } else {
+            if (pr.ev >= 0) {
+                Work w = work_front_small(P, ll);
+                pr.done(w.flops, w.bytes);
+            }
+            continue;
+        }
+        {
+            Prof pr(P, s, SSCO_K_BIG_INIT);
             k_big_init<T><<<dim3((unsigned)ll.max_lower_tiles, ll.count, B), dim3(32, 8), 0, s>>>(
                 P.dt, list, panel, P.panel_total, upd, P.upd_total);
+            if (pr.ev >= 0) {
+                double by = 0;
+                for (int32_t q = 0; q < ll.count; ++q) {
+                    const FrontDesc& d = P.fronts[P.front_lists[ll.list_off + q]];
+                    by += (double)d.r * (d.r + 1) / 2 * P.tsize;
+                    for (int32_t c = 0; c < d.nchild; ++c) {
+                        const FrontDesc& cd = P.fronts[P.child_ids[d.child_off + c]];
+                        double rc = cd.r - cd.w;
+                        by += rc * (rc + 1) / 2 * P.tsize + d.r * 4.0;
+                    }
+                }
+                pr.done(0, by * B);
+            }
+        }
+        {
+            Prof pr(P, s, SSCO_K_BIG_KSCATTER);
             k_big_kscatter<T><<<dim3(cdiv(ll.max_klist, 256), ll.count, B), 256, 0, s>>>(P.dt, list, K, P.nnzK,
                                                                                        panel, P.panel_total);
-            P.launches += 2;
-            const int nkb = (ll.wmax + 31) / 32;
-            for (int kb = 0; kb < nkb; ++kb) {
-                if (kb > 0) {
-                    k_big_gemm<T><<<dim3(cdiv(ll.rmax - kb * 32, 64), ll.count, B), 256, 0, s>>>(
-                        P.dt, list, kb, panel, P.panel_total);
-                    P.launches++;
-                }
-                k_big_potrf_trsm<T><<<dim3(1 + cdiv(ll.rmax, 256), ll.count, B), 256, 0, s>>>(
-                    P.dt, list, kb, panel, P.panel_total, bad, P.n_pats);
-                P.launches++;
+            if (pr.ev >= 0) {
+                double by = 0;
+                for (int32_t q = 0; q < ll.count; ++q)
+                    by += P.fronts[P.front_lists[ll.list_off + q]].klist_n * (16.0 + 2 * P.tsize);
+                pr.done(0, by * B);
             }
-            if (ll.max_syrk_tiles > 0) {
-                k_big_syrk<T><<<dim3((unsigned)ll.max_syrk_tiles, ll.count, B), 256, 0, s>>>(
-                    P.dt, list, panel, P.panel_total, upd, P.upd_total);
-                P.launches++;
+        }
+        const int nkb = (ll.wmax + 31) / 32;
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int c0 = kb * 32;
+            if (kb > 0) {
+                Prof pr(P, s, SSCO_K_BIG_GEMM);
+                k_big_gemm<T><<<dim3(cdiv(ll.rmax - c0, 64), ll.count, B), 256, 0, s>>>(P.dt, list, kb, panel,
+                                                                                        P.panel_total);
+                if (pr.ev >= 0) {
+                    double fl = 0, by = 0;
+                    for (int32_t q = 0; q < ll.count; ++q) {
+                        const FrontDesc& d = P.fronts[P.front_lists[ll.list_off + q]];
+                        if (c0 >= d.w) continue;
+                        double nbk = std::min(32, d.w - c0), mrows = d.r - c0;
+                        fl += 2 * mrows * nbk * c0;
+                        by += (mrows * c0 + nbk * c0 + 2 * mrows * nbk) * P.tsize;
+                    }
+                    pr.done(fl * B, by * B);
+                }
+            }
+            Prof pr(P, s, SSCO_K_BIG_POTRF);
+            k_big_potrf_trsm<T><<<dim3(1 + cdiv(ll.rmax, 256), ll.count, B), 256, 0, s>>>(
+                P.dt, list, kb, panel, P.panel_total, bad, P.n_pats);
+            if (pr.ev >= 0) {
+                double fl = 0, by = 0;
+                for (int32_t q = 0; q < ll.count; ++q) {
+                    const FrontDesc& d = P.fronts[P.front_lists[ll.list_off + q]];
+                    if (c0 >= d.w) continue;
+                    double nbk = std::min(32, d.w - c0), mrows = d.r - c0 - nbk;
+                    fl += nbk * nbk * nbk / 3 + mrows * nbk * nbk;
+                    by += 2 * (mrows + nbk) * nbk * P.tsize;
+                }
+                pr.done(fl * B, by * B);
+            }
+        }
+        if (ll.max_syrk_tiles > 0) {
+            Prof pr(P, s, SSCO_K_BIG_SYRK);
+            k_big_syrk<T><<<dim3((unsigned)ll.max_syrk_tiles, ll.count, B), 256, 0, s>>>(P.dt, list, panel,
+                                                                                        P.panel_total, upd,
+                                                                                        P.upd_total);
+            if (pr.ev >= 0) {
+                double fl = 0, by = 0;
+                for (int32_t q = 0; q < ll.count; ++q) {
+                    const FrontDesc& d = P.fronts[P.front_lists[ll.list_off + q]];
+                    double ru = d.r - d.w;
+                    fl += ru * (ru + 1) * d.w;
+                    by += (ru * d.w + ru * (ru + 1)) * P.tsize;
+                }
+                pr.done(fl * B, by * B);
             }
         }
     }
@@ -800,17 +947,25 @@ void run_trisolve(Plan& P, const int32_t* active, cudaStream_t s) {
     T* vecT = wsp<T>(P, P.ws.vecT);
     T* pvec = wsp<T>(P, P.ws.pvec);
     for (const LaunchList& ll : P.solve_launches) {
+        Prof pr(P, s, SSCO_K_FWD);
         const size_t smem = (size_t)ll.rmax * sizeof(T);
         k_fwd<T><<<dim3(ll.count, B), 256, smem, s>>>(P.dt, P.dt.front_lists + ll.list_off, panel, P.panel_total,
                                                         vecT, P.n, pvec, P.pvec_total, active, P.n_pats);
-        P.launches++;
+        if (pr.ev >= 0) {
+            Work w = work_solve(P, ll);
+            pr.done(w.flops, w.bytes);
+        }
     }
     for (auto it = P.solve_launches.rbegin(); it != P.solve_launches.rend(); ++it) {
         const LaunchList& ll = *it;
+        Prof pr(P, s, SSCO_K_BWD);
         const size_t smem = (size_t)ll.rmax * sizeof(T);
         k_bwd<T><<<dim3(ll.count, B), 256, smem, s>>>(P.dt, P.dt.front_lists + ll.list_off, panel, P.panel_total,
                                                         vecT, P.n, active, P.n_pats);
-        P.launches++;
+        if (pr.ev >= 0) {
+            Work w = work_solve(P, ll);
+            pr.done(w.flops, w.bytes);
+        }
     }
 }
 
@@ -835,49 +990,102 @@ int run_solve(Plan& P, const double* b, double* x, cudaStream_t s) {
     const double* K = wsp<double>(P, P.ws.K);
     const dim3 gv(cdiv(n, 256), B);
     const int refine = P.prec == SSCO_FP32_REFINE;
-    k_permute_in<<<gv, 256, 0, s>>>(b, P.dt.perm, n, bp);
-    k_sys_init<<<(unsigned)S, 256, 0, s>>>(bp, P.dt.sys_n_off, P.n_pats, n, bnorm, active, sst, iters, resid, r1, r2);
-    k_to_T<T><<<cdiv((int64_t)B * n, 256), 256, 0, s>>>(bp, vecT, (int64_t)B * n);
-    P.launches += 3;
+    const double nB = (double)n * B;
+    const double spnz = (double)P.sp_rowptr.back() * B;
+    {
+        Prof pr(P, s, SSCO_K_VECTOR);
+        k_permute_in<<<gv, 256, 0, s>>>(b, P.dt.perm, n, bp);
+        pr.done(0, nB * 20);
+    }
+    {
+        Prof pr(P, s, SSCO_K_CHECK);
+        k_sys_init<<<(unsigned)S, 256, 0, s>>>(bp, P.dt.sys_n_off, P.n_pats, n, bnorm, active, sst, iters, resid, r1,
+                                               r2);
+        pr.done(2 * nB, nB * 8);
+    }
+    {
+        Prof pr(P, s, SSCO_K_VECTOR);
+        k_to_T<T><<<cdiv((int64_t)B * n, 256), 256, 0, s>>>(bp, vecT, (int64_t)B * n);
+        pr.done(0, nB * (8 + sizeof(T)));
+    }
     run_trisolve<T>(P, nullptr, s);
-    k_from_T<T><<<cdiv((int64_t)B * n, 256), 256, 0, s>>>(vecT, xp, (int64_t)B * n);
-    P.launches++;
+    {
+        Prof pr(P, s, SSCO_K_VECTOR);
+        k_from_T<T><<<cdiv((int64_t)B * n, 256), 256, 0, s>>>(vecT, xp, (int64_t)B * n);
+        pr.done(0, nB * (8 + sizeof(T)));
+    }
     for (int it = 0;; ++it) {
-        k_resid<<<gv, 256, 0, s>>>(P.dt.sp_rowptr, P.dt.sp_col, P.dt.sp_slot, K, P.nnzK, bp, xp, rr, n);
+        {
+            Prof pr(P, s, SSCO_K_RESID);
+            k_resid<<<gv, 256, 0, s>>>(P.dt.sp_rowptr, P.dt.sp_col, P.dt.sp_slot, K, P.nnzK, bp, xp, rr, n);
+            pr.done(2 * spnz, (double)P.nnzK * B * 8 + spnz * 8 + nB * 24 + (double)P.sp_rowptr.back() * 8);
+        }
         cudaMemsetAsync(anyp, 0, 4, s);
-        k_check<<<(unsigned)S, 256, 0, s>>>(rr, P.dt.sys_n_off, P.n_pats, n, bnorm, active, sst, iters, resid, r1, r2,
-                                            sigma, anyp, it, P.maxit, P.tol, refine);
-        P.launches += 2;
+        {
+            Prof pr(P, s, SSCO_K_CHECK);
+            k_check<<<(unsigned)S, 256, 0, s>>>(rr, P.dt.sys_n_off, P.n_pats, n, bnorm, active, sst, iters, resid, r1,
+                                                r2, sigma, anyp, it, P.maxit, P.tol, refine);
+            pr.done(2 * nB, nB * 8);
+        }
         if (!refine) break;
         int e = (int)cudaMemcpyAsync(P.h_flag, anyp, 4, cudaMemcpyDeviceToHost, s);
         if (!e) e = (int)cudaStreamSynchronize(s);
         if (e) return e;
         if (*P.h_flag == 0) break;
-        k_cast_scaled<T><<<gv, 256, 0, s>>>(rr, P.dt.row_sys, P.n_pats, n, active, sigma, vecT);
-        P.launches++;
+        {
+            Prof pr(P, s, SSCO_K_VECTOR);
+            k_cast_scaled<T><<<gv, 256, 0, s>>>(rr, P.dt.row_sys, P.n_pats, n, active, sigma, vecT);
+            pr.done(nB, nB * (12 + sizeof(T)));
+        }
         run_trisolve<T>(P, active, s);
-        k_update<T><<<gv, 256, 0, s>>>(vecT, P.dt.row_sys, P.n_pats, n, active, sigma, xp);
-        P.launches++;
+        {
+            Prof pr(P, s, SSCO_K_VECTOR);
+            k_update<T><<<gv, 256, 0, s>>>(vecT, P.dt.row_sys, P.n_pats, n, active, sigma, xp);
+            pr.done(2 * nB, nB * (20 + sizeof(T)));
+        }
     }
-    k_permute_out<<<gv, 256, 0, s>>>(xp, P.dt.perm, n, x);
-    P.launches++;
+    {
+        Prof pr(P, s, SSCO_K_VECTOR);
+        k_permute_out<<<gv, 256, 0, s>>>(xp, P.dt.perm, n, x);
+        pr.done(0, nB * 20);
+    }
     return (int)cudaGetLastError();
 }
 
+// Opt each kernel with dynamic shared memory into the largest size the
+// device allows beside the kernel's static shared memory.
+template <class K>
+int allow_dynamic_smem(K kernel) {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    int e = (int)cudaFuncGetAttributes(&fa, kernel);
+    if (e) return e;
+    return (int)cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     optin - (int)fa.sharedSizeBytes);
+}
+
 template <class T>
-void set_attr_T() {
-    cudaFuncSetAttribute(k_front_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
-    cudaFuncSetAttribute(k_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax - 1024);
-    cudaFuncSetAttribute(k_bwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax - 1024);
+int set_attr_T() {
+    int e = allow_dynamic_smem(k_front_small<T>);
+    if (!e) e = allow_dynamic_smem(k_fwd<T>);
+    if (!e) e = allow_dynamic_smem(k_bwd<T>);
+    return e;
 }
 
 }  // namespace
 
+const char* kernel_kind_name(int kind) {
+    static const char* names[SSCO_K_COUNT] = {"assemble", "front_small", "big_init", "big_kscatter", "big_gemm",
+                                              "big_potrf_trsm", "big_syrk", "fwd_solve", "bwd_solve", "resid",
+                                              "check", "vector", "grad"};
+    return kind >= 0 && kind < SSCO_K_COUNT ? names[kind] : "unknown";
+}
+
 int kernels_set_attributes(Plan& P) {
-    if (P.tsize == 8)
-        set_attr_T<double>();
-    else
-        set_attr_T<float>();
+    int e = P.tsize == 8 ? set_attr_T<double>() : set_attr_T<float>();
+    if (e) return e;
     return (int)cudaGetLastError();
 }
 
@@ -912,20 +1120,62 @@ int launch_backward(Plan& P, const double* x, const double* xbar, double* vals_b
     const int64_t n = P.n, S = (int64_t)B * P.n_pats;
     const int64_t nrows = (int64_t)P.g_rows_all.size(), nel = (int64_t)P.e_elems_all.size();
     if (nrows > 0) {
+        Prof pr(P, s, SSCO_K_GRAD);
         k_grad_atwa<<<dim3(cdiv(nrows, 256), B), 256, 0, s>>>(P.dt, nrows, mu, x, n, vals_bar, P.m);
-        P.launches++;
+        pr.done(4.0 * P.g_colind.size() * B, (P.g_colind.size() * 28.0 + nrows * 8.0) * B);
     }
     if (nel > 0) {
+        Prof pr(P, s, SSCO_K_GRAD);
         k_grad_elem<<<dim3(cdiv(nel, 128), B), 128, 0, s>>>(P.dt, nel, mu, x, n, vals_bar, P.m);
-        P.launches++;
+        pr.done(4.0 * P.e_K0.size() * B, (P.e_K0.size() * 8.0 + P.e_dofs.size() * 20.0) * B);
     }
     if (shift_bar) {
+        Prof pr(P, s, SSCO_K_GRAD);
         k_shift_bar<<<(unsigned)S, 256, 0, s>>>(P.dt, P.n_pats, n, mu, x, shift_bar);
-        P.launches++;
+        pr.done(2.0 * n * B, 21.0 * n * B);
     }
     e = (int)cudaMemcpyAsync(b_bar, mu, (size_t)B * n * 8, cudaMemcpyDeviceToDevice, s);
     if (e) return e;
     return (int)cudaGetLastError();
+}
+
+int profile_enable(Plan& P, int32_t max_launches) {
+    for (void* e : P.ev_pool) cudaEventDestroy((cudaEvent_t)e);
+    P.ev_pool.clear();
+    P.prof_recs.clear();
+    P.ev_used = 0;
+    P.prof = max_launches > 0;
+    for (int32_t i = 0; i < 2 * max_launches; ++i) {
+        cudaEvent_t e;
+        int r = (int)cudaEventCreate(&e);
+        if (r) return r;
+        P.ev_pool.push_back((void*)e);
+    }
+    return 0;
+}
+
+int profile_read(Plan& P, ssco_kernel_stat* out) {
+    int e = (int)cudaDeviceSynchronize();
+    if (e) return e;
+    for (int k = 0; k < SSCO_K_COUNT; ++k) {
+        out[k].kind = k;
+        out[k].reserved = 0;
+        out[k].launches = 0;
+        out[k].ms = out[k].flops = out[k].bytes = 0;
+    }
+    for (const ProfRec& r : P.prof_recs) {
+        float ms = 0;
+        e = (int)cudaEventElapsedTime(&ms, (cudaEvent_t)P.ev_pool[r.ev], (cudaEvent_t)P.ev_pool[r.ev + 1]);
+        if (e) return e;
+        ssco_kernel_stat& o = out[r.kind];
+        o.launches++;
+        o.ms += ms;
+        o.flops += r.flops;
+        o.bytes += r.bytes;
+    }
+    P.prof_recs.clear();
+    P.ev_used = 0;
+    return 0;
 }
 
 }  // namespace ssco

@@ -31,8 +31,10 @@ EXPORTED_SYMBOLS = [
     "ssco_analyze", "ssco_plan_info", "ssco_plan_export", "ssco_bind", "ssco_numeric", "ssco_solve",
     "ssco_backward", "ssco_status_get", "ssco_export_L", "ssco_export_K", "ssco_refactor_solve_host",
     "ssco_last_launch_count", "ssco_last_error", "ssco_status_string", "ssco_plan_save", "ssco_plan_load",
-    "ssco_destroy",
+    "ssco_destroy", "ssco_profile_enable", "ssco_profile_read", "ssco_kernel_name",
 ]
+KERNEL_KINDS = ["assemble", "front_small", "big_init", "big_kscatter", "big_gemm", "big_potrf_trsm", "big_syrk",
+                "fwd_solve", "bwd_solve", "resid", "check", "vector", "grad"]
 
 
 class SscoError(RuntimeError):
@@ -52,6 +54,11 @@ class Op(C.Structure):
     _fields_ = [("precision", C.c_int32), ("batch", C.c_int32), ("refine_tol", C.c_double),
                 ("refine_max_iter", C.c_int32), ("small_front_max", C.c_int32),
                 ("amalgamate", C.c_int32), ("reserved", C.c_int32 * 3)]
+
+
+class KernelStat(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("reserved", C.c_int32), ("launches", C.c_int64), ("ms", C.c_double),
+                ("flops", C.c_double), ("bytes", C.c_double)]
 
 
 class Info(C.Structure):
@@ -95,6 +102,9 @@ def load_library(path: str = LIB_PATH):
         "ssco_plan_save": (i32, [vp, C.c_char_p]),
         "ssco_plan_load": (i32, [C.c_char_p, C.POINTER(vp)]),
         "ssco_destroy": (None, [vp]),
+        "ssco_profile_enable": (i32, [vp, i32]),
+        "ssco_profile_read": (i32, [vp, C.POINTER(KernelStat)]),
+        "ssco_kernel_name": (C.c_char_p, [i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -294,6 +304,17 @@ class Plan:
 
     def last_launch_count(self):
         return int(self.L.ssco_last_launch_count(self._h))
+
+    def profile_enable(self, max_launches: int):
+        """Per-kernel CUDA-event timing of subsequent launches (0 = off)."""
+        self._check(self.L.ssco_profile_enable(self._h, int(max_launches)))
+
+    def profile_read(self):
+        """{kernel kind: {launches, ms, flops, bytes}} summed since the last read."""
+        arr = (KernelStat * len(KERNEL_KINDS))()
+        self._check(self.L.ssco_profile_read(self._h, arr))
+        return {self.L.ssco_kernel_name(a.kind).decode(): {"launches": a.launches, "ms": a.ms, "flops": a.flops,
+                                                          "bytes": a.bytes} for a in arr}
 
 
 class SscoSolve(torch.autograd.Function):
