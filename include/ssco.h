@@ -215,6 +215,27 @@ ssco_status ssco_export_K(ssco_plan plan, double* host_out, void* stream);
 ssco_status ssco_refactor_solve_host(ssco_plan plan, const void* vals, int32_t vals_dtype,
                                      const double* shift, const double* b, double* x, void* stream);
 
+/* Allocation-free variant of ssco_solve for SSCO_FP64 plans.  The paper has
+ * no counterpart; it exists for callers that must not allocate device
+ * memory per call, for example a host application whose memory manager owns
+ * every device allocation, or a latency-critical loop where a cudaMalloc /
+ * cudaFree would synchronize the device.  It computes x = K^-1 b (device,
+ * double [B][n] each, no aliasing) with the factor left in the bound
+ * workspace by ssco_numeric, by direct forward/back substitution (no
+ * refinement, no status words; ssco_status_get does not report it).  Its
+ * scratch -- the permuted right-hand side, the solve vector and the
+ * passing vectors, 2*B*n + B*(sum over fronts of rows-width) doubles -- lives
+ * in one static device array of 64 MiB that every GPU loading the library
+ * keeps until the process exits; plans needing more are rejected with
+ * SSCO_ERR_UNSUPPORTED and a message giving both sizes.  The first call on
+ * a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's contents (every
+ * word is written before it is read, so nothing needs clearing): calls that
+ * overlap on the GPU, on any stream or plan, race.  Calls no cudaMalloc,
+ * cudaFree or other allocating routine. */
+ssco_status ssco_solve_noalloc(ssco_plan plan, const double* b, double* x, void* stream);
+
 /* Number of kernel launches the last ssco_numeric / ssco_solve /
  * ssco_backward / ssco_refactor_solve_host call issued (host counter). */
 int64_t ssco_last_launch_count(ssco_plan plan);

@@ -433,6 +433,23 @@ ssco_status ssco_refactor_solve_host(ssco_plan h, const void* vals, int32_t vals
 
 int64_t ssco_last_launch_count(ssco_plan h) { return h ? h->P.launches : 0; }
 
+ssco_status ssco_solve_noalloc(ssco_plan h, const double* b, double* x, void* stream) {
+    if (!h || !b || !x) return fail(h, SSCO_ERR_INVALID_ARG, "NULL argument");
+    Plan& P = h->P;
+    if (P.prec != SSCO_FP64) return fail(h, SSCO_ERR_UNSUPPORTED, "ssco_solve_noalloc needs an SSCO_FP64 plan");
+    size_t need = static_solve_scratch_need(P), have = static_solve_scratch_bytes();
+    if (need > have)
+        return fail(h, SSCO_ERR_UNSUPPORTED,
+                    "ssco_solve_noalloc: plan needs " + std::to_string(need) + " bytes of scratch, the static array holds " +
+                        std::to_string(have));
+    if (!P.bound || !P.factored) return fail(h, SSCO_ERR_STATE, "ssco_numeric has not run on the bound workspace");
+    if (b == x) return fail(h, SSCO_ERR_INVALID_ARG, "b and x alias");
+    P.launches = 0;
+    int e = launch_solve_static(P, b, x, stream);
+    if (e) return cuda_fail(h, e, "noalloc solve launch");
+    return SSCO_OK;
+}
+
 ssco_status ssco_profile_enable(ssco_plan h, int32_t max_launches) {
     if (!h || max_launches < 0) return fail(h, SSCO_ERR_INVALID_ARG, "bad argument");
     int e = profile_enable(h->P, max_launches);

@@ -217,6 +217,9 @@ int launch_reset_status(Plan& P, void* stream);
 int kernels_set_attributes(Plan& P);
 const char* kernel_kind_name(int kind);
 int profile_enable(Plan& P, int32_t max_launches);
+size_t static_solve_scratch_bytes();
+size_t static_solve_scratch_need(const Plan& P);
+int launch_solve_static(Plan& P, const double* b, double* x, void* stream);
 int profile_read(Plan& P, ssco_kernel_stat* out);
 
 }  // namespace ssco

@@ -1139,6 +1139,76 @@ int launch_backward(Plan& P, const double* x, const double* xbar, double* vals_b
     return (int)cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free FP64 solve.  Its scratch (permuted right-hand side, solve
+// vector, passing vectors) lives in one file-scope device array instead of
+// the caller's workspace; only the factor is read from the bound workspace.
+// The array is shared by every call on a device and keeps the last call's
+// contents; every scratch word is written before it is read, so nothing
+// needs clearing.  Calls that overlap on the GPU race on it.
+// ---------------------------------------------------------------------------
+constexpr size_t kStaticSolveScratchBytes = size_t(64) << 20;
+static __device__ __align__(256) unsigned char g_static_solve_scratch[kStaticSolveScratchBytes];
+static void* g_static_scratch_addr[256] = {};  // per device: device address of the array
+
+size_t static_solve_scratch_bytes() { return kStaticSolveScratchBytes; }
+
+size_t static_solve_scratch_need(const Plan& P) {
+    auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
+    const size_t B = (size_t)P.B, n = (size_t)P.n;
+    return up(B * n * 8) + up(B * n * 8) + up(std::max<size_t>(B * (size_t)P.pvec_total * 8, 16));
+}
+
+// First call on a device (with that device current) looks up the array's
+// device address; later calls reuse it.
+int static_solve_scratch_addr(void** out) {
+    int dev = 0;
+    int e = (int)cudaGetDevice(&dev);
+    if (e) return e;
+    if (dev < 0 || dev >= 256) return (int)cudaErrorInvalidDevice;
+    if (!g_static_scratch_addr[dev]) {
+        void* p = nullptr;
+        e = (int)cudaGetSymbolAddress(&p, g_static_solve_scratch);
+        if (e) return e;
+        g_static_scratch_addr[dev] = p;
+    }
+    *out = g_static_scratch_addr[dev];
+    return 0;
+}
+
+int launch_solve_static(Plan& P, const double* b, double* x, void* stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    void* base = nullptr;
+    int e = static_solve_scratch_addr(&base);
+    if (e) return e;
+    auto up = [](size_t v) { return (v + 255) & ~size_t(255); };
+    const int B = P.B;
+    const int64_t n = P.n;
+    uint8_t* sc = (uint8_t*)base;
+    double* bp = (double*)sc;
+    double* vec = (double*)(sc + up((size_t)B * n * 8));
+    double* pvec = (double*)(sc + 2 * up((size_t)B * n * 8));
+    const double* panel = wsp<double>(P, P.ws.panel);
+    const dim3 gv(cdiv(n, 256), B);
+    k_permute_in<<<gv, 256, 0, s>>>(b, P.dt.perm, n, bp);
+    k_to_T<double><<<cdiv((int64_t)B * n, 256), 256, 0, s>>>(bp, vec, (int64_t)B * n);
+    P.launches += 2;
+    for (const LaunchList& ll : P.solve_launches) {
+        k_fwd<double><<<dim3(ll.count, B), 256, (size_t)ll.rmax * 8, s>>>(
+            P.dt, P.dt.front_lists + ll.list_off, panel, P.panel_total, vec, n, pvec, P.pvec_total, nullptr,
+            P.n_pats);
+        P.launches++;
+    }
+    for (auto it = P.solve_launches.rbegin(); it != P.solve_launches.rend(); ++it) {
+        k_bwd<double><<<dim3(it->count, B), 256, (size_t)it->rmax * 8, s>>>(
+            P.dt, P.dt.front_lists + it->list_off, panel, P.panel_total, vec, n, nullptr, P.n_pats);
+        P.launches++;
+    }
+    k_permute_out<<<gv, 256, 0, s>>>(vec, P.dt.perm, n, x);
+    P.launches++;
+    return (int)cudaGetLastError();
+}
+
 int profile_enable(Plan& P, int32_t max_launches) {
     for (void* e : P.ev_pool) cudaEventDestroy((cudaEvent_t)e);
     P.ev_pool.clear();

@@ -31,7 +31,7 @@ EXPORTED_SYMBOLS = [
     "ssco_analyze", "ssco_plan_info", "ssco_plan_export", "ssco_bind", "ssco_numeric", "ssco_solve",
     "ssco_backward", "ssco_status_get", "ssco_export_L", "ssco_export_K", "ssco_refactor_solve_host",
     "ssco_last_launch_count", "ssco_last_error", "ssco_status_string", "ssco_plan_save", "ssco_plan_load",
-    "ssco_destroy", "ssco_profile_enable", "ssco_profile_read", "ssco_kernel_name",
+    "ssco_destroy", "ssco_profile_enable", "ssco_profile_read", "ssco_kernel_name", "ssco_solve_noalloc",
 ]
 KERNEL_KINDS = ["assemble", "front_small", "big_init", "big_kscatter", "big_gemm", "big_potrf_trsm", "big_syrk",
                 "fwd_solve", "bwd_solve", "resid", "check", "vector", "grad"]
@@ -105,6 +105,7 @@ def load_library(path: str = LIB_PATH):
         "ssco_profile_enable": (i32, [vp, i32]),
         "ssco_profile_read": (i32, [vp, C.POINTER(KernelStat)]),
         "ssco_kernel_name": (C.c_char_p, [i32]),
+        "ssco_solve_noalloc": (i32, [vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -262,6 +263,14 @@ class Plan:
         if x is None:
             x = torch.empty_like(b)
         self._check(self.L.ssco_solve(self._h, _ptr(b), _ptr(x), _stream_ptr(stream)))
+        return x
+
+    def solve_noalloc(self, b: torch.Tensor, x: torch.Tensor, stream=None):
+        """ssco_solve_noalloc: FP64 direct solve whose scratch is a static
+        device array (no allocation by the library or here; x is the caller's)."""
+        assert b.is_cuda and b.dtype == torch.float64 and b.is_contiguous()
+        assert x.is_cuda and x.dtype == torch.float64 and x.is_contiguous()
+        self._check(self.L.ssco_solve_noalloc(self._h, _ptr(b), _ptr(x), _stream_ptr(stream)))
         return x
 
     def backward(self, x, xbar, stream=None, want_shift=True):
