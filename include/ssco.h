@@ -92,9 +92,12 @@ typedef struct {
  * batch: value sets per pattern (>= 1).
  * small_front_max: fronts with more rows than this use the multi-CTA dense
  *   path (0 = default for the precision).
- * amalgamate: 0 = fundamental supernodes only; > 0 = relaxed amalgamation
- *   allowing up to that many explicit zeros per merged front column
- *   (numeric partition only; exported structures stay exact).          */
+ * amalgamate: 0 = fundamental supernodes only; 1 = relaxed amalgamation of
+ *   a front into its parent when the merge adds few explicit zeros
+ *   (numeric partition only; exported structures stay exact).
+ * tiny_front_max: subtrees whose fronts all have at most this many rows
+ *   (<= 32) are factored and solved by one warp each, front in registers,
+ *   in a single launch (0 = default 32, -1 = off).                      */
 typedef struct {
     int32_t precision;
     int32_t batch;
@@ -102,7 +105,8 @@ typedef struct {
     int32_t refine_max_iter;
     int32_t small_front_max;
     int32_t amalgamate;
-    int32_t reserved[3];
+    int32_t tiny_front_max;
+    int32_t reserved[2];
 } ssco_op;
 
 /* Sizes and counts of an analyzed plan (all for the concatenated system). */
@@ -252,7 +256,7 @@ enum {
     SSCO_K_BIG_INIT = 2,     /* big front: pull children's update matrices    */
     SSCO_K_BIG_KSCATTER = 3, /* big front: add K entries                      */
     SSCO_K_BIG_GEMM = 4,     /* big front: left-looking block-column update   */
-    SSCO_K_BIG_POTRF = 5,    /* big front: diagonal block + triangular solve  */
+    SSCO_K_BIG_POTRF = 5,    /* big front: 32x32 diagonal block Cholesky      */
     SSCO_K_BIG_SYRK = 6,     /* big front: update matrix -= L21 L21^T         */
     SSCO_K_FWD = 7,          /* forward solve, one level                      */
     SSCO_K_BWD = 8,          /* backward solve, one level                     */
@@ -260,7 +264,9 @@ enum {
     SSCO_K_CHECK = 10,       /* per-system norms and refinement decision      */
     SSCO_K_VECTOR = 11,      /* permutations, casts, updates, status fills    */
     SSCO_K_GRAD = 12,        /* adjoint reductions                            */
-    SSCO_K_COUNT = 13
+    SSCO_K_FRONT_TINY = 13,  /* warp-per-subtree factorization, tiny fronts   */
+    SSCO_K_BIG_TRSM = 14,    /* big front: rows below the diagonal block      */
+    SSCO_K_COUNT = 15
 };
 typedef struct {
     int32_t kind;

@@ -68,11 +68,13 @@ void set_dev_tables(Plan& P) {
     d.shifted = tab_ptr<uint8_t>(P, P.toff.shifted);
     d.g_rows_all = tab_ptr<int32_t>(P, P.toff.g_rows_all);
     d.e_elems_all = tab_ptr<int32_t>(P, P.toff.e_elems_all);
+    d.tiny_list = tab_ptr<int32_t>(P, P.toff.tiny_list);
+    d.tiny_off = tab_ptr<int32_t>(P, P.toff.tiny_off);
 }
 
 // ----- plan file (de)serialization -----------------------------------------
 constexpr uint64_t kMagic = 0x314F4353534F4353ull;  // "SCOSSCO1"
-constexpr uint32_t kVersion = 1;
+constexpr uint32_t kVersion = 2;
 
 struct Writer {
     std::ofstream f;
@@ -111,7 +113,7 @@ bool serialize(IO& io, Plan& P) {
     bool ok = true;
     auto S = [&](auto& x) { ok = ok && io.pod(x); };
     auto V = [&](auto& x) { ok = ok && io.vec(x); };
-    S(P.prec); S(P.B); S(P.tol); S(P.maxit); S(P.small_max); S(P.amalg); S(P.tsize);
+    S(P.prec); S(P.B); S(P.tol); S(P.maxit); S(P.small_max); S(P.amalg); S(P.tiny_max); S(P.tsize);
     S(P.n_pats); V(P.pats); S(P.n); S(P.m);
     V(P.Kcolptr); V(P.Krowind); V(P.kslot_of_q); S(P.nnzK);
     V(P.perm); V(P.parent); V(P.colcount); V(P.col_level);
@@ -120,6 +122,7 @@ bool serialize(IO& io, Plan& P) {
     V(P.fronts); V(P.front_first); V(P.front_level); V(P.rows); V(P.child_ids); V(P.relmap);
     V(P.invmap); V(P.klist); V(P.front_lists); V(P.fact_launches); V(P.solve_launches);
     S(P.n_levels); S(P.panel_total); S(P.upd_total); S(P.pvec_total); S(P.max_rows);
+    V(P.tiny_list); V(P.tiny_off); S(P.n_tiny);
     V(P.groups); V(P.chunks); V(P.asm_idx); V(P.asm_coef);
     V(P.sp_rowptr); V(P.sp_col); V(P.sp_slot); V(P.row_sys); V(P.sys_n_off); V(P.shifted);
     V(P.g_rowptr); V(P.g_colind); V(P.g_row_sys); V(P.g_rows_all); V(P.g_aval);

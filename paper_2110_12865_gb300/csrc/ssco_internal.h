@@ -92,6 +92,8 @@ struct DevTables {
     const uint8_t* shifted;     // per permuted row: receives the shift (1) or not
     const int32_t* g_rows_all;  // value indices that are ATWA rows
     const int32_t* e_elems_all; // value indices that are elements
+    const int32_t* tiny_list;   // fronts of every tiny subtree, children first
+    const int32_t* tiny_off;    // [n_tiny+1] offsets into tiny_list
 };
 
 // Byte offsets of every region of the caller's workspace.
@@ -124,6 +126,7 @@ struct Plan {
     int32_t maxit = 30;
     int32_t small_max = 0;
     int32_t amalg = 1;
+    int32_t tiny_max = 32;
     size_t tsize = 8;  // bytes of the factor type
 
     int32_t n_pats = 0;
@@ -151,6 +154,8 @@ struct Plan {
     std::vector<int32_t> rows, child_ids, relmap, invmap, klist, front_lists;
     std::vector<LaunchList> fact_launches;   // per level: small classes + big
     std::vector<LaunchList> solve_launches;  // per level: all fronts
+    std::vector<int32_t> tiny_list, tiny_off;  // warp-per-subtree fronts
+    int32_t n_tiny = 0;
     int32_t n_levels = 0;
     int64_t panel_total = 0, upd_total = 0, pvec_total = 0;
     int32_t max_rows = 0;
@@ -181,7 +186,7 @@ struct Plan {
         size_t fronts, rows, child_ids, relmap, invmap, klist, front_lists, groups, chunks,
             asm_idx, asm_coef, sp_rowptr, sp_col, sp_slot, perm, row_sys, sys_n_off, g_rowptr,
             g_colind, g_aval, g_row_sys, e_dofs, e_K0, e_sys, e_off, e_k0off, e_dim, shifted,
-            g_rows_all, e_elems_all;
+            g_rows_all, e_elems_all, tiny_list, tiny_off;
     } toff{};
     WsLayout ws{};
     uint8_t* d_tab = nullptr;

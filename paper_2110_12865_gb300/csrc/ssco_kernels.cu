@@ -134,38 +134,84 @@ __global__ void __launch_bounds__(256) k_front_small(const DevTables t, const in
         }
     }
     __syncthreads();
-    // right-looking partial factorization; column j is scaled one step late so
-    // that a single barrier per column suffices.
-    T prev_inv = T(1), prev_l = T(1);
+    // Blocked right-looking partial factorization.  Panels of kPanel columns
+    // are factored column by column (each column scaled one step late, so one
+    // barrier per column); the trailing matrix then takes one rank-kPanel
+    // update with 4x4 register tiles per thread.
+    constexpr int kPanel = 16;
     bool failed = false;
-    for (int j = 0; j < w; ++j) {
-        T djj = F[j + j * r];
-        if (!(djj > T(0))) {
-            if (tid == 0 && !failed) atomicMin(&bad_col[(int64_t)b * n_pats + d.sys], d.f + j - (int)t.sys_n_off[d.sys]);
-            failed = true;
-            djj = T(1);
+    const int tx = tid & 15, ty = tid >> 4, ny = nth >> 4;
+    for (int j0 = 0; j0 < w; j0 += kPanel) {
+        const int j1 = min(j0 + kPanel, w);
+        T prev_inv = T(1), prev_l = T(1);
+        for (int j = j0; j < j1; ++j) {
+            T djj = F[j + j * r];
+            if (!(djj > T(0))) {
+                if (tid == 0 && !failed)
+                    atomicMin(&bad_col[(int64_t)b * n_pats + d.sys], d.f + j - (int)t.sys_n_off[d.sys]);
+                failed = true;
+                djj = T(1);
+            }
+            const T invd = T(1) / djj;
+            if (j > j0) {
+                for (int i = j + tid; i < r; i += nth) F[i + (j - 1) * r] *= prev_inv;
+                if (tid == 0) F[(j - 1) + (j - 1) * r] = prev_l;
+            }
+            for (int k = j + 1 + warp; k < j1; k += nw) {
+                const T lk = F[k + j * r] * invd;
+                T* Fk = F + k * r;
+                const T* Fj = F + j * r;
+                for (int i = k + lane; i < r; i += 32) Fk[i] -= Fj[i] * lk;
+            }
+            prev_l = sqrt(djj);
+            prev_inv = T(1) / prev_l;
+            __syncthreads();
         }
-        const T invd = T(1) / djj;
-        if (j > 0) {
-            for (int i = j + tid; i < r; i += nth) F[i + (j - 1) * r] *= prev_inv;
-            if (tid == 0) F[(j - 1) + (j - 1) * r] = prev_l;
+        {
+            const int j = j1 - 1;
+            for (int i = j + 1 + tid; i < r; i += nth) F[i + j * r] *= prev_inv;
+            if (tid == 0) F[j + j * r] = prev_l;
         }
-        for (int k = j + 1 + warp; k < r; k += nw) {
-            const T lk = F[k + j * r] * invd;
-            T* Fk = F + k * r;
-            const T* Fj = F + j * r;
-            for (int i = k + lane; i < r; i += 32) Fk[i] -= Fj[i] * lk;
+        __syncthreads();
+        const int m = r - j1;
+        if (m > 0) {
+            const int tk_cols = 4 * ny;
+            for (int c0 = 0; c0 < m; c0 += tk_cols) {
+                for (int r0 = (c0 / 64) * 64; r0 < m; r0 += 64) {
+                    T acc[4][4];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) acc[a][q] = T(0);
+                    int ii[4], kk[4];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        ii[a] = j1 + r0 + tx + 16 * a;
+                        kk[a] = j1 + c0 + ty + ny * a;
+                    }
+                    for (int j = j0; j < j1; ++j) {
+                        const T* Fj = F + j * r;
+                        T ra[4], cb[4];
+#pragma unroll
+                        for (int a = 0; a < 4; ++a) {
+                            ra[a] = ii[a] < r ? Fj[ii[a]] : T(0);
+                            cb[a] = kk[a] < r ? Fj[kk[a]] : T(0);
+                        }
+#pragma unroll
+                        for (int a = 0; a < 4; ++a)
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) acc[a][q] += ra[a] * cb[q];
+                    }
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            if (ii[a] < r && kk[q] < r && ii[a] >= kk[q]) F[ii[a] + kk[q] * r] -= acc[a][q];
+                }
+            }
         }
-        prev_l = sqrt(djj);
-        prev_inv = T(1) / prev_l;
         __syncthreads();
     }
-    if (w > 0) {
-        const int j = w - 1;
-        for (int i = j + 1 + tid; i < r; i += nth) F[i + j * r] *= prev_inv;
-        if (tid == 0) F[j + j * r] = prev_l;
-    }
-    __syncthreads();
     T* Pb = panel + (int64_t)b * panel_total + d.panel_off;
     for (int jj = warp; jj < w; jj += nw)
         for (int i = lane; i < r; i += 32) Pb[(int64_t)jj * r + i] = i >= jj ? F[i + jj * r] : T(0);
@@ -174,6 +220,178 @@ __global__ void __launch_bounds__(256) k_front_small(const DevTables t, const in
         T* Ub = upd + (int64_t)b * upd_total + d.upd_off;
         for (int kk = warp; kk < ru; kk += nw)
             for (int ii = kk + lane; ii < ru; ii += 32) Ub[(int64_t)kk * ru + ii] = F[(w + ii) + (w + kk) * r];
+    }
+}
+
+// --------------------------------------------------------------------------
+// a3': tiny subtrees.  Every front of the subtree has r <= 32 rows; one warp
+// factors the whole subtree, children first, with lane i holding row i of
+// the front in registers (column broadcasts by warp shuffles).  This folds
+// the lowest levels of the forest into one launch of independent warps.
+// --------------------------------------------------------------------------
+constexpr int kTinyWarps = 8;
+
+template <class T>
+__global__ void __launch_bounds__(256) k_tiny_factor(const DevTables t, int32_t n_tiny, int32_t B,
+                                                     const double* __restrict__ K, int64_t nnzK,
+                                                     T* __restrict__ panel, int64_t panel_total,
+                                                     T* __restrict__ upd, int64_t upd_total,
+                                                     int32_t* __restrict__ bad_col, int32_t n_pats) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t item = (int64_t)blockIdx.x * kTinyWarps + wib;
+    if (item >= (int64_t)n_tiny * B) return;
+    const int st = (int)(item / B), b = (int)(item % B);
+    T(*F)[33] = reinterpret_cast<T(*)[33]>(smem_raw) + wib * 32;
+    const double* Kb = K + (int64_t)b * nnzK;
+    T* Pb = panel + (int64_t)b * panel_total;
+    T* Ub = upd + (int64_t)b * upd_total;
+    for (int q = t.tiny_off[st]; q < t.tiny_off[st + 1]; ++q) {
+        const FrontDesc d = t.fronts[t.tiny_list[q]];
+        const int r = d.r, w = d.w;
+        // fronts of a subtree are visited children-first, not in column
+        // order: record the first failing pivot of every front (atomicMin)
+        bool failed = false;
+#pragma unroll
+        for (int k = 0; k < 32; ++k) F[lane][k] = T(0);
+        __syncwarp();
+        const int32_t* kl = t.klist + 2 * d.klist_off;
+        for (int e = lane; e < d.klist_n; e += 32) {
+            const int pos = kl[2 * e + 1];
+            F[pos % r][pos / r] = (T)Kb[kl[2 * e]];
+        }
+        for (int c = 0; c < d.nchild; ++c) {
+            __syncwarp();
+            const FrontDesc cd = t.fronts[t.child_ids[d.child_off + c]];
+            const int rc = cd.r - cd.w;
+            const int32_t* map = t.relmap + cd.relmap_off;
+            const T* S = Ub + cd.upd_off;
+            if (lane < rc) {
+                const int mi = map[lane];
+                for (int kk = 0; kk <= lane; ++kk) F[mi][map[kk]] += S[lane + kk * rc];
+            }
+        }
+        __syncwarp();
+        T a[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) a[k] = F[lane][k];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            if (j < w) {
+                T djj = __shfl_sync(0xffffffffu, a[j], j);
+                if (!(djj > T(0))) {
+                    if (lane == 0 && !failed)
+                        atomicMin(&bad_col[(int64_t)b * n_pats + d.sys], d.f + j - (int)t.sys_n_off[d.sys]);
+                    failed = true;
+                    djj = T(1);
+                }
+                const T ljj = sqrt(djj);
+                const T inv = T(1) / ljj;
+                if (lane == j)
+                    a[j] = ljj;
+                else if (lane > j)
+                    a[j] *= inv;
+#pragma unroll
+                for (int k = j + 1; k < 32; ++k) {
+                    if (k < r) {
+                        const T lkj = __shfl_sync(0xffffffffu, a[j], k);
+                        if (lane >= k) a[k] -= a[j] * lkj;
+                    }
+                }
+            }
+        }
+        if (lane < r) {
+            const int ru = r - w;
+#pragma unroll
+            for (int k = 0; k < 32; ++k) {
+                if (k < w) Pb[d.panel_off + (int64_t)k * r + lane] = lane >= k ? a[k] : T(0);
+                if (k >= w && k < r && lane >= k) Ub[d.upd_off + (int64_t)(k - w) * ru + (lane - w)] = a[k];
+            }
+        }
+        __syncwarp();
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_tiny_fwd(const DevTables t, int32_t n_tiny, int32_t B,
+                                                  const T* __restrict__ panel, int64_t panel_total,
+                                                  T* __restrict__ vec, int64_t n, T* __restrict__ pvec,
+                                                  int64_t pvec_total, const int32_t* __restrict__ active,
+                                                  int32_t n_pats) {
+    __shared__ T vs[kTinyWarps][32];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t item = (int64_t)blockIdx.x * kTinyWarps + wib;
+    if (item >= (int64_t)n_tiny * B) return;
+    const int st = (int)(item / B), b = (int)(item % B);
+    const int q0 = t.tiny_off[st], q1 = t.tiny_off[st + 1];
+    if (active && !active[(int64_t)b * n_pats + t.fronts[t.tiny_list[q0]].sys]) return;
+    const T* Pb = panel + (int64_t)b * panel_total;
+    T* vb = vec + (int64_t)b * n;
+    T* pv = pvec + (int64_t)b * pvec_total;
+    for (int q = q0; q < q1; ++q) {
+        const FrontDesc d = t.fronts[t.tiny_list[q]];
+        const int r = d.r, w = d.w;
+        vs[wib][lane] = lane < w ? vb[d.f + lane] : T(0);
+        for (int c = 0; c < d.nchild; ++c) {
+            __syncwarp();
+            const FrontDesc cd = t.fronts[t.child_ids[d.child_off + c]];
+            const int rc = cd.r - cd.w;
+            if (lane < rc) vs[wib][t.relmap[cd.relmap_off + lane]] += pv[cd.pvec_off + lane];
+        }
+        __syncwarp();
+        T v = vs[wib][lane];
+        T a[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) a[j] = (j < w && lane < r) ? Pb[d.panel_off + (int64_t)j * r + lane] : T(0);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            if (j < w) {
+                const T djj = __shfl_sync(0xffffffffu, a[j], j);
+                const T yj = __shfl_sync(0xffffffffu, v, j) / djj;
+                if (lane == j)
+                    v = yj;
+                else if (lane > j)
+                    v -= a[j] * yj;
+            }
+        }
+        if (lane < w)
+            vb[d.f + lane] = v;
+        else if (lane < r)
+            pv[d.pvec_off + lane - w] = v;
+        __syncwarp();
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_tiny_bwd(const DevTables t, int32_t n_tiny, int32_t B,
+                                                  const T* __restrict__ panel, int64_t panel_total,
+                                                  T* __restrict__ vec, int64_t n, const int32_t* __restrict__ active,
+                                                  int32_t n_pats) {
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t item = (int64_t)blockIdx.x * kTinyWarps + wib;
+    if (item >= (int64_t)n_tiny * B) return;
+    const int st = (int)(item / B), b = (int)(item % B);
+    const int q0 = t.tiny_off[st], q1 = t.tiny_off[st + 1];
+    if (active && !active[(int64_t)b * n_pats + t.fronts[t.tiny_list[q0]].sys]) return;
+    const T* Pb = panel + (int64_t)b * panel_total;
+    T* vb = vec + (int64_t)b * n;
+    for (int q = q1 - 1; q >= q0; --q) {
+        const FrontDesc d = t.fronts[t.tiny_list[q]];
+        const int r = d.r, w = d.w;
+        T v = lane < w ? vb[d.f + lane] : (lane < r ? vb[t.rows[d.rows_off + lane]] : T(0));
+        T a[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) a[j] = (j < w && lane < r) ? Pb[d.panel_off + (int64_t)j * r + lane] : T(0);
+#pragma unroll
+        for (int j = 31; j >= 0; --j) {
+            if (j < w) {
+                T s = (lane > j && lane < r) ? a[j] * v : T(0);
+                s = warp_sum(s);
+                if (lane == j) v = (v - s) / a[j];
+            }
+        }
+        if (lane < w) vb[d.f + lane] = v;
+        __syncwarp();
     }
 }
 
@@ -294,60 +512,69 @@ __global__ void __launch_bounds__(256) k_big_gemm(const DevTables t, const int32
         }
 }
 
-// Factor the diagonal block of column block kb (every CTA redundantly, in
-// shared memory) and solve the rows below: X = P[rows, blk] L_kk^{-T}.
-// blockIdx.x == 0 writes the diagonal block; blockIdx.x >= 1 handles 256 rows.
+// Factor the 32x32 diagonal block of column block kb, one warp per front.
+// Its own launch: the triangular solve below must read the factored block,
+// and no CTA of one launch may overwrite what another CTA still has to load.
 template <class T>
-__global__ void __launch_bounds__(256) k_big_potrf_trsm(const DevTables t, const int32_t* __restrict__ list, int kb,
-                                                        T* __restrict__ panel, int64_t panel_total,
-                                                        int32_t* __restrict__ bad_col, int32_t n_pats) {
+__global__ void __launch_bounds__(32) k_big_potrf(const DevTables t, const int32_t* __restrict__ list, int kb,
+                                                  T* __restrict__ panel, int64_t panel_total,
+                                                  int32_t* __restrict__ bad_col, int32_t n_pats) {
+    const FrontDesc d = t.fronts[list[blockIdx.x]];
+    const int b = blockIdx.y;
+    const int r = d.r, w = d.w;
+    const int c0 = kb * 32;
+    if (c0 >= w) return;
+    const int nbk = min(32, w - c0);
+    T* Pb = panel + (int64_t)b * panel_total + d.panel_off;
+    __shared__ T Ld[32][33];
+    const int i = threadIdx.x;
+    for (int j = 0; j < 32; ++j) Ld[i][j] = (i < nbk && j <= i) ? Pb[(int64_t)(c0 + j) * r + c0 + i] : T(0);
+    __syncwarp();
+    bool failed = false;
+    for (int j = 0; j < nbk; ++j) {
+        T djj = Ld[j][j];
+        __syncwarp();
+        if (!(djj > T(0))) {
+            if (i == 0 && !failed)
+                atomicMin(&bad_col[(int64_t)b * n_pats + d.sys], d.f + c0 + j - (int)t.sys_n_off[d.sys]);
+            failed = true;
+            djj = T(1);
+        }
+        const T ljj = sqrt(djj);
+        if (i > j && i < nbk) Ld[i][j] /= ljj;
+        if (i == j) Ld[j][j] = ljj;
+        __syncwarp();
+        if (i > j && i < nbk) {
+            const T lij = Ld[i][j];
+            for (int k = j + 1; k <= i; ++k) Ld[i][k] -= lij * Ld[k][j];
+        }
+        __syncwarp();
+    }
+    if (i < nbk)
+        for (int j = 0; j <= i; ++j) Pb[(int64_t)(c0 + j) * r + c0 + i] = Ld[i][j];
+}
+
+// Rows below the diagonal block of column block kb: X = P[rows, blk] L_kk^{-T},
+// 256 rows per CTA, one row per thread.
+template <class T>
+__global__ void __launch_bounds__(256) k_big_trsm(const DevTables t, const int32_t* __restrict__ list, int kb,
+                                                  T* __restrict__ panel, int64_t panel_total) {
     const FrontDesc d = t.fronts[list[blockIdx.y]];
     const int b = blockIdx.z;
     const int r = d.r, w = d.w;
     const int c0 = kb * 32;
     if (c0 >= w) return;
     const int nbk = min(32, w - c0);
-    const int rbeg = c0 + nbk + ((int)blockIdx.x - 1) * 256;
-    if (blockIdx.x > 0 && rbeg >= r) return;
+    const int rbeg = c0 + nbk + (int)blockIdx.x * 256;
+    if (rbeg >= r) return;
     T* Pb = panel + (int64_t)b * panel_total + d.panel_off;
     __shared__ T Ld[32][33];
     const int tid = threadIdx.x;
     for (int e = tid; e < 32 * 32; e += 256) {
         const int i = e & 31, j = e >> 5;
-        Ld[i][j] = (i < nbk && j <= i) ? Pb[(int64_t)(c0 + j) * r + c0 + i] : T(0);
+        Ld[i][j] = (i < nbk && j <= i) ? Pb[(int64_t)(c0 + j) * r + c0 + i] : T(1);
     }
     __syncthreads();
-    if (tid < 32) {
-        const int i = tid;
-        bool failed = false;
-        for (int j = 0; j < nbk; ++j) {
-            T djj = Ld[j][j];
-            __syncwarp();
-            if (!(djj > T(0))) {
-                if (i == 0 && blockIdx.x == 0 && !failed)
-                    atomicMin(&bad_col[(int64_t)b * n_pats + d.sys], d.f + c0 + j - (int)t.sys_n_off[d.sys]);
-                failed = true;
-                djj = T(1);
-            }
-            const T ljj = sqrt(djj);
-            if (i > j && i < nbk) Ld[i][j] /= ljj;
-            if (i == j) Ld[j][j] = ljj;
-            __syncwarp();
-            if (i > j && i < nbk) {
-                const T lij = Ld[i][j];
-                for (int k = j + 1; k <= i; ++k) Ld[i][k] -= lij * Ld[k][j];
-            }
-            __syncwarp();
-        }
-    }
-    __syncthreads();
-    if (blockIdx.x == 0) {
-        for (int e = tid; e < 32 * 32; e += 256) {
-            const int i = e & 31, j = e >> 5;
-            if (i < nbk && j <= i) Pb[(int64_t)(c0 + j) * r + c0 + i] = Ld[i][j];
-        }
-        return;
-    }
     const int row = rbeg + tid;
     if (row >= r) return;
     T x[32];
@@ -810,6 +1037,25 @@ Work work_solve(const Plan& P, const LaunchList& ll) {
     return w;
 }
 
+Work work_tiny(const Plan& P, bool solve) {
+    Work w;
+    for (int32_t f : P.tiny_list) {
+        const FrontDesc& d = P.fronts[f];
+        double ent = (double)d.r * d.w - (double)d.w * (d.w - 1) / 2;
+        if (solve) {
+            w.flops += 2 * ent;
+            w.bytes += ent * P.tsize + 2.0 * d.r * P.tsize;
+        } else {
+            for (int32_t j = 0; j < d.w; ++j) w.flops += (double)(d.r - j) * (d.r - j);
+            double ru = d.r - d.w;
+            w.bytes += d.klist_n * 16.0 + ((double)d.r * d.w + ru * (ru + 1) / 2) * P.tsize * 2;
+        }
+    }
+    w.flops *= P.B;
+    w.bytes *= P.B;
+    return w;
+}
+
 template <class T>
 int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cudaStream_t s) {
     const int B = P.B;
@@ -840,6 +1086,16 @@ int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cud
                 by += t * (4 + sv + (g2.uniform ? 0 : 8)) + g2.nmem * 8.0;
             }
             pr.done(fl * B, by * B);
+        }
+    }
+    if (P.n_tiny > 0) {
+        Prof pr(P, s, SSCO_K_FRONT_TINY);
+        const int64_t items = (int64_t)P.n_tiny * B;
+        k_tiny_factor<T><<<cdiv(items, kTinyWarps), 32 * kTinyWarps, kTinyWarps * 32 * 33 * sizeof(T), s>>>(
+            P.dt, P.n_tiny, B, K, P.nnzK, panel, P.panel_total, upd, P.upd_total, bad, P.n_pats);
+        if (pr.ev >= 0) {
+            Work w = work_tiny(P, false);
+            pr.done(w.flops, w.bytes);
         }
     }
     for (const LaunchList& ll : P.fact_launches) {
@@ -905,16 +1161,31 @@ int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cud
                     pr.done(fl * B, by * B);
                 }
             }
-            Prof pr(P, s, SSCO_K_BIG_POTRF);
-            k_big_potrf_trsm<T><<<dim3(1 + cdiv(ll.rmax, 256), ll.count, B), 256, 0, s>>>(
-                P.dt, list, kb, panel, P.panel_total, bad, P.n_pats);
+            {
+                Prof pd(P, s, SSCO_K_BIG_POTRF);
+                k_big_potrf<T><<<dim3(ll.count, B), 32, 0, s>>>(P.dt, list, kb, panel, P.panel_total, bad, P.n_pats);
+                if (pd.ev >= 0) {
+                    double fl = 0, by = 0;
+                    for (int32_t q = 0; q < ll.count; ++q) {
+                        const FrontDesc& d = P.fronts[P.front_lists[ll.list_off + q]];
+                        if (c0 >= d.w) continue;
+                        double nbk = std::min(32, d.w - c0);
+                        fl += nbk * nbk * nbk / 3;
+                        by += nbk * nbk * P.tsize;
+                    }
+                    pd.done(fl * B, by * B);
+                }
+            }
+            Prof pr(P, s, SSCO_K_BIG_TRSM);
+            k_big_trsm<T><<<dim3(cdiv(ll.rmax - c0, 256), ll.count, B), 256, 0, s>>>(P.dt, list, kb, panel,
+                                                                                    P.panel_total);
             if (pr.ev >= 0) {
                 double fl = 0, by = 0;
                 for (int32_t q = 0; q < ll.count; ++q) {
                     const FrontDesc& d = P.fronts[P.front_lists[ll.list_off + q]];
                     if (c0 >= d.w) continue;
                     double nbk = std::min(32, d.w - c0), mrows = d.r - c0 - nbk;
-                    fl += nbk * nbk * nbk / 3 + mrows * nbk * nbk;
+                    fl += mrows * nbk * nbk;
                     by += 2 * (mrows + nbk) * nbk * P.tsize;
                 }
                 pr.done(fl * B, by * B);
@@ -946,6 +1217,16 @@ void run_trisolve(Plan& P, const int32_t* active, cudaStream_t s) {
     T* panel = wsp<T>(P, P.ws.panel);
     T* vecT = wsp<T>(P, P.ws.vecT);
     T* pvec = wsp<T>(P, P.ws.pvec);
+    const unsigned tiny_grid = cdiv((int64_t)P.n_tiny * B, kTinyWarps);
+    if (P.n_tiny > 0) {
+        Prof pr(P, s, SSCO_K_FWD);
+        k_tiny_fwd<T><<<tiny_grid, 32 * kTinyWarps, 0, s>>>(P.dt, P.n_tiny, B, panel, P.panel_total, vecT, P.n, pvec,
+                                                          P.pvec_total, active, P.n_pats);
+        if (pr.ev >= 0) {
+            Work w = work_tiny(P, true);
+            pr.done(w.flops, w.bytes);
+        }
+    }
     for (const LaunchList& ll : P.solve_launches) {
         Prof pr(P, s, SSCO_K_FWD);
         const size_t smem = (size_t)ll.rmax * sizeof(T);
@@ -964,6 +1245,15 @@ void run_trisolve(Plan& P, const int32_t* active, cudaStream_t s) {
                                                         vecT, P.n, active, P.n_pats);
         if (pr.ev >= 0) {
             Work w = work_solve(P, ll);
+            pr.done(w.flops, w.bytes);
+        }
+    }
+    if (P.n_tiny > 0) {
+        Prof pr(P, s, SSCO_K_BWD);
+        k_tiny_bwd<T><<<tiny_grid, 32 * kTinyWarps, 0, s>>>(P.dt, P.n_tiny, B, panel, P.panel_total, vecT, P.n,
+                                                          active, P.n_pats);
+        if (pr.ev >= 0) {
+            Work w = work_tiny(P, true);
             pr.done(w.flops, w.bytes);
         }
     }
@@ -1069,6 +1359,7 @@ int allow_dynamic_smem(K kernel) {
 template <class T>
 int set_attr_T() {
     int e = allow_dynamic_smem(k_front_small<T>);
+    if (!e) e = allow_dynamic_smem(k_tiny_factor<T>);
     if (!e) e = allow_dynamic_smem(k_fwd<T>);
     if (!e) e = allow_dynamic_smem(k_bwd<T>);
     return e;
@@ -1078,8 +1369,8 @@ int set_attr_T() {
 
 const char* kernel_kind_name(int kind) {
     static const char* names[SSCO_K_COUNT] = {"assemble", "front_small", "big_init", "big_kscatter", "big_gemm",
-                                              "big_potrf_trsm", "big_syrk", "fwd_solve", "bwd_solve", "resid",
-                                              "check", "vector", "grad"};
+                                              "big_potrf", "big_syrk", "fwd_solve", "bwd_solve", "resid",
+                                              "check", "vector", "grad", "front_tiny", "big_trsm"};
     return kind >= 0 && kind < SSCO_K_COUNT ? names[kind] : "unknown";
 }
 
@@ -1193,6 +1484,12 @@ int launch_solve_static(Plan& P, const double* b, double* x, void* stream) {
     k_permute_in<<<gv, 256, 0, s>>>(b, P.dt.perm, n, bp);
     k_to_T<double><<<cdiv((int64_t)B * n, 256), 256, 0, s>>>(bp, vec, (int64_t)B * n);
     P.launches += 2;
+    const unsigned tiny_grid = cdiv((int64_t)P.n_tiny * B, kTinyWarps);
+    if (P.n_tiny > 0) {
+        k_tiny_fwd<double><<<tiny_grid, 32 * kTinyWarps, 0, s>>>(P.dt, P.n_tiny, B, panel, P.panel_total, vec, n, pvec,
+                                                               P.pvec_total, nullptr, P.n_pats);
+        P.launches++;
+    }
     for (const LaunchList& ll : P.solve_launches) {
         k_fwd<double><<<dim3(ll.count, B), 256, (size_t)ll.rmax * 8, s>>>(
             P.dt, P.dt.front_lists + ll.list_off, panel, P.panel_total, vec, n, pvec, P.pvec_total, nullptr,
@@ -1202,6 +1499,11 @@ int launch_solve_static(Plan& P, const double* b, double* x, void* stream) {
     for (auto it = P.solve_launches.rbegin(); it != P.solve_launches.rend(); ++it) {
         k_bwd<double><<<dim3(it->count, B), 256, (size_t)it->rmax * 8, s>>>(
             P.dt, P.dt.front_lists + it->list_off, panel, P.panel_total, vec, n, nullptr, P.n_pats);
+        P.launches++;
+    }
+    if (P.n_tiny > 0) {
+        k_tiny_bwd<double><<<tiny_grid, 32 * kTinyWarps, 0, s>>>(P.dt, P.n_tiny, B, panel, P.panel_total, vec, n,
+                                                               nullptr, P.n_pats);
         P.launches++;
     }
     k_permute_out<<<gv, 256, 0, s>>>(vec, P.dt.perm, n, x);

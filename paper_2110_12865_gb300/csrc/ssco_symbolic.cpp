@@ -120,6 +120,7 @@ ssco_status analyze_impl(const ssco_pattern* const* pats, int32_t n_pats, const 
     int32_t smax_default = P.prec == SSCO_FP64 ? 160 : 224;
     P.small_max = op->small_front_max > 0 ? std::min(op->small_front_max, smax_default) : smax_default;
     P.amalg = op->amalgamate;
+    P.tiny_max = op->tiny_front_max == 0 ? 32 : (op->tiny_front_max < 0 ? 0 : std::min(op->tiny_front_max, 32));
     P.n_pats = n_pats;
 
     for (int k = 0; k < n_pats; ++k) {
@@ -587,14 +588,57 @@ ssco_status analyze_impl(const ssco_pattern* const* pats, int32_t n_pats, const 
             for (int32_t k = 0; k < d.r; ++k) pos[P.rows[d.rows_off + k]] = -1;
         }
     }
-    // launch lists per level
+    // tiny subtrees: every front of the subtree has at most tiny_max rows;
+    // one warp factors / solves a whole subtree, children first.
+    std::vector<char> in_tiny(nf, 0);
+    std::vector<int32_t> sched(nf, 0);
+    int32_t n_sched = 0;
     {
-        std::vector<std::vector<int32_t>> by_level(P.n_levels);
-        for (int32_t F = 0; F < nf; ++F) by_level[P.front_level[F]].push_back(F);
+        P.tiny_list.clear();
+        P.tiny_off.assign(1, 0);
+        if (P.tiny_max > 0) {
+            std::vector<char> ok(nf, 1);
+            for (int32_t F = 0; F < nf; ++F) {
+                if (P.fronts[F].r > P.tiny_max) ok[F] = 0;
+                if (P.fronts[F].parent >= 0 && !ok[F]) ok[P.fronts[F].parent] = 0;
+            }
+            in_tiny = ok;
+            std::vector<int32_t> stack;
+            for (int32_t F = 0; F < nf; ++F) {
+                int32_t p = P.fronts[F].parent;
+                if (!in_tiny[F] || (p >= 0 && in_tiny[p])) continue;
+                // postorder of the subtree rooted at F
+                stack.assign(1, F);
+                std::vector<int32_t> order;
+                while (!stack.empty()) {
+                    int32_t x = stack.back();
+                    stack.pop_back();
+                    order.push_back(x);
+                    const FrontDesc& d = P.fronts[x];
+                    for (int32_t c = 0; c < d.nchild; ++c) stack.push_back(P.child_ids[d.child_off + c]);
+                }
+                std::reverse(order.begin(), order.end());  // children before parents
+                P.tiny_list.insert(P.tiny_list.end(), order.begin(), order.end());
+                P.tiny_off.push_back((int32_t)P.tiny_list.size());
+            }
+        }
+        P.n_tiny = (int32_t)P.tiny_off.size() - 1;
+        for (int32_t F = 0; F < nf; ++F) {
+            if (in_tiny[F]) continue;
+            int32_t p = P.fronts[F].parent;
+            n_sched = std::max(n_sched, sched[F] + 1);
+            if (p >= 0) sched[p] = std::max(sched[p], sched[F] + 1);
+        }
+    }
+    // launch lists per scheduling level (fronts outside tiny subtrees)
+    {
+        std::vector<std::vector<int32_t>> by_level(n_sched);
+        for (int32_t F = 0; F < nf; ++F)
+            if (!in_tiny[F]) by_level[sched[F]].push_back(F);
         P.front_lists.clear();
         P.fact_launches.clear();
         P.solve_launches.clear();
-        for (int32_t L = 0; L < P.n_levels; ++L) {
+        for (int32_t L = 0; L < n_sched; ++L) {
             const auto& fl = by_level[L];
             // solve: all fronts of the level, largest first
             {
@@ -781,6 +825,8 @@ void build_blob(Plan& P) {
     P.toff.shifted = put(b, P.shifted);
     P.toff.g_rows_all = put(b, P.g_rows_all);
     P.toff.e_elems_all = put(b, P.e_elems_all);
+    P.toff.tiny_list = put(b, P.tiny_list);
+    P.toff.tiny_off = put(b, P.tiny_off);
     b.resize((b.size() + 255) & ~(size_t)255);
 }
 

@@ -33,8 +33,8 @@ EXPORTED_SYMBOLS = [
     "ssco_last_launch_count", "ssco_last_error", "ssco_status_string", "ssco_plan_save", "ssco_plan_load",
     "ssco_destroy", "ssco_profile_enable", "ssco_profile_read", "ssco_kernel_name", "ssco_solve_noalloc",
 ]
-KERNEL_KINDS = ["assemble", "front_small", "big_init", "big_kscatter", "big_gemm", "big_potrf_trsm", "big_syrk",
-                "fwd_solve", "bwd_solve", "resid", "check", "vector", "grad"]
+KERNEL_KINDS = ["assemble", "front_small", "big_init", "big_kscatter", "big_gemm", "big_potrf", "big_syrk",
+                "fwd_solve", "bwd_solve", "resid", "check", "vector", "grad", "front_tiny", "big_trsm"]
 
 
 class SscoError(RuntimeError):
@@ -53,7 +53,7 @@ class Pattern(C.Structure):
 class Op(C.Structure):
     _fields_ = [("precision", C.c_int32), ("batch", C.c_int32), ("refine_tol", C.c_double),
                 ("refine_max_iter", C.c_int32), ("small_front_max", C.c_int32),
-                ("amalgamate", C.c_int32), ("reserved", C.c_int32 * 3)]
+                ("amalgamate", C.c_int32), ("tiny_front_max", C.c_int32), ("reserved", C.c_int32 * 2)]
 
 
 class KernelStat(C.Structure):
@@ -136,7 +136,7 @@ class Plan:
     (several patterns concatenated, one value set each per instance)."""
 
     def __init__(self, problems, precision=FP64, batch=None, refine_tol=1e-10, refine_max_iter=30,
-                 small_front_max=0, amalgamate=1, _handle=None):
+                 small_front_max=0, amalgamate=1, tiny_front_max=0, _handle=None):
         self.L = load_library()
         if _handle is not None:
             self._h = _handle
@@ -172,6 +172,7 @@ class Plan:
             op.refine_max_iter = refine_max_iter
             op.small_front_max = small_front_max
             op.amalgamate = amalgamate
+            op.tiny_front_max = tiny_front_max
             h = C.c_void_p()
             st = self.L.ssco_analyze(arr, len(pats), C.byref(op), C.byref(h))
             if st != SSCO_OK:

@@ -55,7 +55,8 @@ def check_against_oracle(S, pl, p, x, st, inst, sys_index, col_off=0, exact_L=Tr
 
 
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("kw", [{}, {"small_front_max": 32}, {"amalgamate": 0}])
+@pytest.mark.parametrize("kw", [{}, {"small_front_max": 32}, {"amalgamate": 0}, {"tiny_front_max": -1},
+                                {"tiny_front_max": 8, "small_front_max": 40}])
 def test_fp64_grid32_L_entries(S, kw):
     p = P.workload("grid32")
     pl, x, st, *_ = run(S, p, S.FP64, **kw)
@@ -71,7 +72,7 @@ def test_fp64_grid32_L_entries(S, kw):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-@pytest.mark.parametrize("kw", [{}, {"small_front_max": 32}])
+@pytest.mark.parametrize("kw", [{}, {"small_front_max": 32}, {"tiny_front_max": -1}])
 def test_elasticity_small(S, prec, kw):
     p = P.elasticity_problem(6, cfg=2)
     precision = S.FP64 if prec == "fp64" else S.FP32_REFINE
@@ -120,6 +121,23 @@ def test_multi_pattern_uneven(S):
     off = 0
     for k, p in enumerate(probs):
         check_against_oracle(S, pl, p, x, st, 0, k, col_off=off)
+        off += p.n
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_many_big_fronts_one_plan(S, prec):
+    """Many concurrent multi-CTA fronts (24 large grids in one plan): every
+    CTA of a launch must read only what no other CTA of it writes."""
+    sides = list(range(170, 257, 4))
+    probs = [P.trigrid_problem(s, 1, cfg=3, seed_offset=300 + k) for k, s in enumerate(sides)]
+    precision = S.FP64 if prec == "fp64" else S.FP32_REFINE
+    pl, x, st, *_ = run(S, probs, precision, batch=1, small_front_max=96)
+    assert np.all(st["status"] == 0), st
+    assert np.all(st["resid"] <= RESID_TOL)
+    off = 0
+    for k, p in enumerate(probs):
+        if k in (0, len(probs) - 1):
+            check_against_oracle(S, pl, p, x, st, 0, k, col_off=off)
         off += p.n
 
 
