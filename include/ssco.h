@@ -278,6 +278,11 @@ typedef struct {
 } ssco_kernel_stat;
 ssco_status ssco_profile_enable(ssco_plan plan, int32_t max_launches);
 ssco_status ssco_profile_read(ssco_plan plan, ssco_kernel_stat* out);
+/* Per-launch trace: synchronizes the device and copies up to `cap` records
+ * in launch order (kind, milliseconds, flops, bytes; any array may be NULL)
+ * WITHOUT clearing them; *n receives the number of records held. */
+ssco_status ssco_profile_trace(ssco_plan plan, int32_t* kinds, float* ms, double* flops, double* bytes,
+                               int64_t cap, int64_t* n);
 const char* ssco_kernel_name(int32_t kind);
 
 const char* ssco_last_error(ssco_plan plan);

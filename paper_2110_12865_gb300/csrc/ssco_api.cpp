@@ -469,6 +469,14 @@ ssco_status ssco_profile_read(ssco_plan h, ssco_kernel_stat* out) {
 
 const char* ssco_kernel_name(int32_t kind) { return kernel_kind_name(kind); }
 
+ssco_status ssco_profile_trace(ssco_plan h, int32_t* kinds, float* ms, double* flops, double* bytes, int64_t cap,
+                               int64_t* n) {
+    if (!h || !n || cap < 0) return fail(h, SSCO_ERR_INVALID_ARG, "bad argument");
+    int e = profile_trace(h->P, kinds, ms, flops, bytes, cap, n);
+    if (e) return cuda_fail(h, e, "profile trace");
+    return SSCO_OK;
+}
+
 ssco_status ssco_plan_save(ssco_plan h, const char* path) {
     if (!h || !path) return fail(h, SSCO_ERR_INVALID_ARG, "NULL argument");
     Writer w;

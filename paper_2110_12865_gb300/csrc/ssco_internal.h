@@ -226,5 +226,6 @@ size_t static_solve_scratch_bytes();
 size_t static_solve_scratch_need(const Plan& P);
 int launch_solve_static(Plan& P, const double* b, double* x, void* stream);
 int profile_read(Plan& P, ssco_kernel_stat* out);
+int profile_trace(Plan& P, int32_t* kinds, float* ms, double* flops, double* bytes, int64_t cap, int64_t* n);
 
 }  // namespace ssco

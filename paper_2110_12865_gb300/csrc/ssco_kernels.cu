@@ -103,6 +103,11 @@ __global__ void k_fill_i32(int32_t* p, int64_t n, int32_t v) {
 // a3: small fronts, one CTA per (front, instance), front resident in shared
 // memory: gather K, extend-add children, partial Cholesky, write panel+update.
 // --------------------------------------------------------------------------
+// Column k of a front stored as a packed lower triangle (rows k..r-1)
+// starts at packed_col(k, r); element (i, k), i >= k, sits at
+// packed_col(k, r) + i - k.
+__device__ __forceinline__ int packed_col(int k, int r) { return k * r - ((k * (k - 1)) >> 1); }
+
 template <class T>
 __global__ void __launch_bounds__(256) k_front_small(const DevTables t, const int32_t* __restrict__ list,
                                                      const double* __restrict__ K, int64_t nnzK,
@@ -110,17 +115,22 @@ __global__ void __launch_bounds__(256) k_front_small(const DevTables t, const in
                                                      T* __restrict__ upd, int64_t upd_total,
                                                      int32_t* __restrict__ bad_col, int32_t n_pats) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* F = reinterpret_cast<T*>(smem_raw);
+    T* F = reinterpret_cast<T*>(smem_raw);  // packed lower triangle, r(r+1)/2
     const FrontDesc d = t.fronts[list[blockIdx.x]];
     const int b = blockIdx.y;
     const int r = d.r, w = d.w;
     const int lane = threadIdx.x, warp = threadIdx.y, nw = blockDim.y;
     const int tid = lane + 32 * warp, nth = 32 * nw;
-    for (int q = tid; q < r * r; q += nth) F[q] = T(0);
+    const int npk = r * (r + 1) / 2;
+    for (int q = tid; q < npk; q += nth) F[q] = T(0);
     __syncthreads();
     const double* Kb = K + (int64_t)b * nnzK;
     const int32_t* kl = t.klist + 2 * d.klist_off;
-    for (int q = tid; q < d.klist_n; q += nth) F[kl[2 * q + 1]] = (T)Kb[kl[2 * q]];
+    for (int q = tid; q < d.klist_n; q += nth) {
+        const int pos = kl[2 * q + 1];
+        const int col = pos / r, row = pos - col * r;
+        F[packed_col(col, r) + row - col] = (T)Kb[kl[2 * q]];
+    }
     for (int c = 0; c < d.nchild; ++c) {
         __syncthreads();
         const FrontDesc cd = t.fronts[t.child_ids[d.child_off + c]];
@@ -128,9 +138,10 @@ __global__ void __launch_bounds__(256) k_front_small(const DevTables t, const in
         const int32_t* map = t.relmap + cd.relmap_off;
         const T* S = upd + (int64_t)b * upd_total + cd.upd_off;
         for (int kk = warp; kk < rc; kk += nw) {
-            const int mk = map[kk] * r;
+            const int mk = map[kk];
+            T* Fk = F + packed_col(mk, r) - mk;
             const T* Sk = S + (int64_t)kk * rc;
-            for (int ii = kk + lane; ii < rc; ii += 32) F[map[ii] + mk] += Sk[ii];
+            for (int ii = kk + lane; ii < rc; ii += 32) Fk[map[ii]] += Sk[ii];
         }
     }
     __syncthreads();
@@ -145,7 +156,8 @@ __global__ void __launch_bounds__(256) k_front_small(const DevTables t, const in
         const int j1 = min(j0 + kPanel, w);
         T prev_inv = T(1), prev_l = T(1);
         for (int j = j0; j < j1; ++j) {
-            T djj = F[j + j * r];
+            T* Fj = F + packed_col(j, r) - j;
+            T djj = Fj[j];
             if (!(djj > T(0))) {
                 if (tid == 0 && !failed)
                     atomicMin(&bad_col[(int64_t)b * n_pats + d.sys], d.f + j - (int)t.sys_n_off[d.sys]);
@@ -154,13 +166,13 @@ __global__ void __launch_bounds__(256) k_front_small(const DevTables t, const in
             }
             const T invd = T(1) / djj;
             if (j > j0) {
-                for (int i = j + tid; i < r; i += nth) F[i + (j - 1) * r] *= prev_inv;
-                if (tid == 0) F[(j - 1) + (j - 1) * r] = prev_l;
+                T* Fp = F + packed_col(j - 1, r) - (j - 1);
+                for (int i = j + tid; i < r; i += nth) Fp[i] *= prev_inv;
+                if (tid == 0) Fp[j - 1] = prev_l;
             }
             for (int k = j + 1 + warp; k < j1; k += nw) {
-                const T lk = F[k + j * r] * invd;
-                T* Fk = F + k * r;
-                const T* Fj = F + j * r;
+                const T lk = Fj[k] * invd;
+                T* Fk = F + packed_col(k, r) - k;
                 for (int i = k + lane; i < r; i += 32) Fk[i] -= Fj[i] * lk;
             }
             prev_l = sqrt(djj);
@@ -169,8 +181,9 @@ __global__ void __launch_bounds__(256) k_front_small(const DevTables t, const in
         }
         {
             const int j = j1 - 1;
-            for (int i = j + 1 + tid; i < r; i += nth) F[i + j * r] *= prev_inv;
-            if (tid == 0) F[j + j * r] = prev_l;
+            T* Fj = F + packed_col(j, r) - j;
+            for (int i = j + 1 + tid; i < r; i += nth) Fj[i] *= prev_inv;
+            if (tid == 0) Fj[j] = prev_l;
         }
         __syncthreads();
         const int m = r - j1;
@@ -190,7 +203,7 @@ __global__ void __launch_bounds__(256) k_front_small(const DevTables t, const in
                         kk[a] = j1 + c0 + ty + ny * a;
                     }
                     for (int j = j0; j < j1; ++j) {
-                        const T* Fj = F + j * r;
+                        const T* Fj = F + packed_col(j, r) - j;
                         T ra[4], cb[4];
 #pragma unroll
                         for (int a = 0; a < 4; ++a) {
@@ -203,23 +216,30 @@ __global__ void __launch_bounds__(256) k_front_small(const DevTables t, const in
                             for (int q = 0; q < 4; ++q) acc[a][q] += ra[a] * cb[q];
                     }
 #pragma unroll
-                    for (int a = 0; a < 4; ++a)
+                    for (int q = 0; q < 4; ++q) {
+                        if (kk[q] >= r) continue;
+                        T* Fk = F + packed_col(kk[q], r) - kk[q];
 #pragma unroll
-                        for (int q = 0; q < 4; ++q)
-                            if (ii[a] < r && kk[q] < r && ii[a] >= kk[q]) F[ii[a] + kk[q] * r] -= acc[a][q];
+                        for (int a = 0; a < 4; ++a)
+                            if (ii[a] < r && ii[a] >= kk[q]) Fk[ii[a]] -= acc[a][q];
+                    }
                 }
             }
         }
         __syncthreads();
     }
     T* Pb = panel + (int64_t)b * panel_total + d.panel_off;
-    for (int jj = warp; jj < w; jj += nw)
-        for (int i = lane; i < r; i += 32) Pb[(int64_t)jj * r + i] = i >= jj ? F[i + jj * r] : T(0);
+    for (int jj = warp; jj < w; jj += nw) {
+        const T* Fj = F + packed_col(jj, r) - jj;
+        for (int i = lane; i < r; i += 32) Pb[(int64_t)jj * r + i] = i >= jj ? Fj[i] : T(0);
+    }
     const int ru = r - w;
     if (ru > 0) {
         T* Ub = upd + (int64_t)b * upd_total + d.upd_off;
-        for (int kk = warp; kk < ru; kk += nw)
-            for (int ii = kk + lane; ii < ru; ii += 32) Ub[(int64_t)kk * ru + ii] = F[(w + ii) + (w + kk) * r];
+        for (int kk = warp; kk < ru; kk += nw) {
+            const T* Fk = F + packed_col(w + kk, r) - (w + kk);
+            for (int ii = kk + lane; ii < ru; ii += 32) Ub[(int64_t)kk * ru + ii] = Fk[w + ii];
+        }
     }
 }
 
@@ -232,7 +252,7 @@ __global__ void __launch_bounds__(256) k_front_small(const DevTables t, const in
 constexpr int kTinyWarps = 8;
 
 template <class T>
-__global__ void __launch_bounds__(256) k_tiny_factor(const DevTables t, int32_t n_tiny, int32_t B,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_tiny_factor(const DevTables t, int32_t n_tiny, int32_t B,
                                                      const double* __restrict__ K, int64_t nnzK,
                                                      T* __restrict__ panel, int64_t panel_total,
                                                      T* __restrict__ upd, int64_t upd_total,
@@ -313,7 +333,7 @@ __global__ void __launch_bounds__(256) k_tiny_factor(const DevTables t, int32_t 
 }
 
 template <class T>
-__global__ void __launch_bounds__(256) k_tiny_fwd(const DevTables t, int32_t n_tiny, int32_t B,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_tiny_fwd(const DevTables t, int32_t n_tiny, int32_t B,
                                                   const T* __restrict__ panel, int64_t panel_total,
                                                   T* __restrict__ vec, int64_t n, T* __restrict__ pvec,
                                                   int64_t pvec_total, const int32_t* __restrict__ active,
@@ -363,7 +383,7 @@ __global__ void __launch_bounds__(256) k_tiny_fwd(const DevTables t, int32_t n_t
 }
 
 template <class T>
-__global__ void __launch_bounds__(256) k_tiny_bwd(const DevTables t, int32_t n_tiny, int32_t B,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_tiny_bwd(const DevTables t, int32_t n_tiny, int32_t B,
                                                   const T* __restrict__ panel, int64_t panel_total,
                                                   T* __restrict__ vec, int64_t n, const int32_t* __restrict__ active,
                                                   int32_t n_pats) {
@@ -662,12 +682,15 @@ __global__ void __launch_bounds__(256) k_big_syrk(const DevTables t, const int32
 // a5: level-scheduled solves, one CTA per (front, instance).
 // --------------------------------------------------------------------------
 // Stage the lower triangle of the 32x32 diagonal block starting at (jb, jb).
+// and the reciprocals of its diagonal.
 template <class T>
-__device__ __forceinline__ void stage_diag(T (*Ld)[33], const T* __restrict__ Pb, int r, int jb, int nbk, int tid,
-                                           int nth) {
+__device__ __forceinline__ void stage_diag(T (*Ld)[33], T* dinv, const T* __restrict__ Pb, int r, int jb, int nbk,
+                                           int tid, int nth) {
     for (int e = tid; e < 32 * 32; e += nth) {
         const int i = e & 31, c = e >> 5;
-        Ld[i][c] = (i < nbk && c <= i) ? Pb[(int64_t)(jb + c) * r + jb + i] : T(0);
+        const T v = (i < nbk && c <= i) ? Pb[(int64_t)(jb + c) * r + jb + i] : T(0);
+        Ld[i][c] = v;
+        if (i == c) dinv[i] = i < nbk ? T(1) / v : T(0);
     }
 }
 
@@ -680,6 +703,7 @@ __global__ void __launch_bounds__(256) k_fwd(const DevTables t, const int32_t* _
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* v = reinterpret_cast<T*>(smem_raw);
     __shared__ T Ld[2][32][33];
+    __shared__ T dinv[2][32];
     __shared__ T yblk[32];
     const FrontDesc d = t.fronts[list[blockIdx.x]];
     const int b = blockIdx.y;
@@ -690,7 +714,7 @@ __global__ void __launch_bounds__(256) k_fwd(const DevTables t, const int32_t* _
     const T* Pb = panel + (int64_t)b * panel_total + d.panel_off;
     T* pv = pvec + (int64_t)b * pvec_total;
     for (int k = tid; k < r; k += nth) v[k] = k < w ? vb[d.f + k] : T(0);
-    stage_diag(Ld[0], Pb, r, 0, min(32, w), tid, nth);
+    stage_diag(Ld[0], dinv[0], Pb, r, 0, min(32, w), tid, nth);
     for (int c = 0; c < d.nchild; ++c) {
         __syncthreads();
         const FrontDesc cd = t.fronts[t.child_ids[d.child_off + c]];
@@ -706,7 +730,7 @@ __global__ void __launch_bounds__(256) k_fwd(const DevTables t, const int32_t* _
             const int l = tid;
             T val = l < nbk ? v[jb + l] : T(0);
             for (int j = 0; j < nbk; ++j) {
-                const T yj = __shfl_sync(0xffffffffu, val, j) / Ld[buf][j][j];
+                const T yj = __shfl_sync(0xffffffffu, val, j) * dinv[buf][j];
                 if (l == j) val = yj;
                 if (l > j) val -= Ld[buf][l][j] * yj;
             }
@@ -716,7 +740,7 @@ __global__ void __launch_bounds__(256) k_fwd(const DevTables t, const int32_t* _
             }
         }
         __syncthreads();
-        if (jb + 32 < w) stage_diag(Ld[buf ^ 1], Pb, r, jb + 32, min(32, w - jb - 32), tid, nth);
+        if (jb + 32 < w) stage_diag(Ld[buf ^ 1], dinv[buf ^ 1], Pb, r, jb + 32, min(32, w - jb - 32), tid, nth);
         for (int i = jb + nbk + tid; i < r; i += nth) {
             T s = T(0);
             const T* col = Pb + (int64_t)jb * r + i;
@@ -738,6 +762,7 @@ __global__ void __launch_bounds__(256) k_bwd(const DevTables t, const int32_t* _
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* v = reinterpret_cast<T*>(smem_raw);
     __shared__ T Ld[32][33];
+    __shared__ T dinv[32];
     __shared__ T dots[32];
     const FrontDesc d = t.fronts[list[blockIdx.x]];
     const int b = blockIdx.y;
@@ -754,7 +779,7 @@ __global__ void __launch_bounds__(256) k_bwd(const DevTables t, const int32_t* _
     for (int bi = nblk - 1; bi >= 0; --bi) {
         const int jb = bi * 32;
         const int nbk = min(32, w - jb);
-        stage_diag(Ld, Pb, r, jb, nbk, tid, nth);
+        stage_diag(Ld, dinv, Pb, r, jb, nbk, tid, nth);
         for (int c = warp; c < nbk; c += nw) {
             const T* col = Pb + (int64_t)(jb + c) * r;
             T s = T(0);
@@ -767,7 +792,7 @@ __global__ void __launch_bounds__(256) k_bwd(const DevTables t, const int32_t* _
             const int l = tid;
             T val = l < nbk ? v[jb + l] - dots[l] : T(0);
             for (int j = nbk - 1; j >= 0; --j) {
-                const T xj = __shfl_sync(0xffffffffu, val, j) / Ld[j][j];
+                const T xj = __shfl_sync(0xffffffffu, val, j) * dinv[j];
                 if (l == j) val = xj;
                 if (l < j) val -= Ld[j][l] * xj;
             }
@@ -776,6 +801,139 @@ __global__ void __launch_bounds__(256) k_bwd(const DevTables t, const int32_t* _
         __syncthreads();
     }
     for (int k = tid; k < w; k += nth) vb[d.f + k] = v[k];
+}
+
+// Warp-per-(front, instance) variants of the two solves for levels that
+// supply many items (a batch of value sets): eight independent warps per
+// CTA, no block barriers; the 32x32 diagonal block is held in registers
+// (forward: lane = row, backward: lane = column) and the front's vector in
+// shared memory.  Items are front-major, so the 8 warps of a CTA read the
+// same index tables.
+template <class T>
+__global__ void __launch_bounds__(256) k_fwd_warp(const DevTables t, const int32_t* __restrict__ list,
+                                                  int32_t count, int32_t B, int32_t rmax,
+                                                  const T* __restrict__ panel, int64_t panel_total,
+                                                  T* __restrict__ vec, int64_t n, T* __restrict__ pvec,
+                                                  int64_t pvec_total, const int32_t* __restrict__ active,
+                                                  int32_t n_pats) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t item = (int64_t)blockIdx.x * 8 + wib;
+    if (item >= (int64_t)count * B) return;
+    const int fi = (int)(item / B), b = (int)(item % B);
+    const FrontDesc d = t.fronts[list[fi]];
+    if (active && !active[(int64_t)b * n_pats + d.sys]) return;
+    T* v = reinterpret_cast<T*>(smem_raw) + (int64_t)wib * rmax;
+    const int r = d.r, w = d.w;
+    T* vb = vec + (int64_t)b * n;
+    const T* Pb = panel + (int64_t)b * panel_total + d.panel_off;
+    T* pv = pvec + (int64_t)b * pvec_total;
+    for (int k = lane; k < r; k += 32) v[k] = k < w ? vb[d.f + k] : T(0);
+    for (int c = 0; c < d.nchild; ++c) {
+        __syncwarp();
+        const FrontDesc cd = t.fronts[t.child_ids[d.child_off + c]];
+        const int rc = cd.r - cd.w;
+        const int32_t* map = t.relmap + cd.relmap_off;
+        for (int k = lane; k < rc; k += 32) v[map[k]] += pv[cd.pvec_off + k];
+    }
+    __syncwarp();
+    for (int jb = 0; jb < w; jb += 32) {
+        const int nbk = min(32, w - jb);
+        T a[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) a[j] = (j < nbk && lane < nbk) ? Pb[(int64_t)(jb + j) * r + jb + lane] : T(0);
+        T val = lane < nbk ? v[jb + lane] : T(0);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            if (j < nbk) {
+                const T dj = __shfl_sync(0xffffffffu, a[j], j);
+                const T yj = __shfl_sync(0xffffffffu, val, j) / dj;
+                if (lane == j)
+                    val = yj;
+                else if (lane > j)
+                    val -= a[j] * yj;
+            }
+        }
+        if (lane < nbk) v[jb + lane] = val;
+        __syncwarp();
+        for (int i0 = jb + nbk; i0 < r; i0 += 32) {
+            const int i = i0 + lane;
+            if (i < r) {
+                const T* col = Pb + (int64_t)jb * r + i;
+                T s0 = T(0), s1 = T(0);
+                int j = 0;
+                for (; j + 1 < nbk; j += 2) {
+                    s0 += col[(int64_t)j * r] * v[jb + j];
+                    s1 += col[(int64_t)(j + 1) * r] * v[jb + j + 1];
+                }
+                if (j < nbk) s0 += col[(int64_t)j * r] * v[jb + j];
+                v[i] -= s0 + s1;
+            }
+        }
+        __syncwarp();
+    }
+    for (int k = lane; k < w; k += 32) vb[d.f + k] = v[k];
+    for (int k = lane; k < r - w; k += 32) pv[d.pvec_off + k] = v[w + k];
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_bwd_warp(const DevTables t, const int32_t* __restrict__ list,
+                                                  int32_t count, int32_t B, int32_t rmax,
+                                                  const T* __restrict__ panel, int64_t panel_total,
+                                                  T* __restrict__ vec, int64_t n, const int32_t* __restrict__ active,
+                                                  int32_t n_pats) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t item = (int64_t)blockIdx.x * 8 + wib;
+    if (item >= (int64_t)count * B) return;
+    const int fi = (int)(item / B), b = (int)(item % B);
+    const FrontDesc d = t.fronts[list[fi]];
+    if (active && !active[(int64_t)b * n_pats + d.sys]) return;
+    T* v = reinterpret_cast<T*>(smem_raw) + (int64_t)wib * rmax;
+    const int r = d.r, w = d.w;
+    T* vb = vec + (int64_t)b * n;
+    const T* Pb = panel + (int64_t)b * panel_total + d.panel_off;
+    const int32_t* rows = t.rows + d.rows_off;
+    for (int k = lane; k < r; k += 32) v[k] = k < w ? vb[d.f + k] : vb[rows[k]];
+    __syncwarp();
+    const int nblk = (w + 31) / 32;
+    for (int bi = nblk - 1; bi >= 0; --bi) {
+        const int jb = bi * 32;
+        const int nbk = min(32, w - jb);
+        T dot = T(0);
+        if (lane < nbk) {
+            const T* col = Pb + (int64_t)(jb + lane) * r;
+            T d1 = T(0), d2 = T(0), d3 = T(0);
+            int i = jb + nbk;
+            for (; i + 3 < r; i += 4) {
+                dot += col[i] * v[i];
+                d1 += col[i + 1] * v[i + 1];
+                d2 += col[i + 2] * v[i + 2];
+                d3 += col[i + 3] * v[i + 3];
+            }
+            for (; i < r; ++i) dot += col[i] * v[i];
+            dot += d1 + d2 + d3;
+        }
+        T a[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+            a[j] = (lane < nbk && j < nbk && j >= lane) ? Pb[(int64_t)(jb + lane) * r + jb + j] : T(0);
+        T val = lane < nbk ? v[jb + lane] - dot : T(0);
+#pragma unroll
+        for (int j = 31; j >= 0; --j) {
+            if (j < nbk) {
+                const T dj = __shfl_sync(0xffffffffu, a[j], j);
+                const T xj = __shfl_sync(0xffffffffu, val, j) / dj;
+                if (lane == j)
+                    val = xj;
+                else if (lane < j)
+                    val -= a[j] * xj;
+            }
+        }
+        if (lane < nbk) v[jb + lane] = val;
+        __syncwarp();
+    }
+    for (int k = lane; k < w; k += 32) vb[d.f + k] = v[k];
 }
 
 // --------------------------------------------------------------------------
@@ -1103,7 +1261,7 @@ int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cud
         if (ll.cls > 0) {
             Prof pr(P, s, SSCO_K_FRONT_SMALL);
             const int nw = ll.cls <= 32 ? 2 : (ll.cls <= 64 ? 4 : 8);
-            const size_t smem = (size_t)ll.rmax * ll.rmax * sizeof(T);
+            const size_t smem = (size_t)ll.rmax * (ll.rmax + 1) / 2 * sizeof(T);
             k_front_small<T><<<dim3(ll.count, B), dim3(32, nw), smem, s>>>(P.dt, list, K, P.nnzK, panel,
                                                                            P.panel_total, upd, P.upd_total, bad,
                                                                            P.n_pats);
@@ -1211,6 +1369,12 @@ int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cud
     return (int)cudaGetLastError();
 }
 
+// A level is solved warp-per-item when it supplies at least 8 warps per SM
+// and its fronts' vectors fit 8 to a CTA; otherwise one CTA per item.
+inline bool use_warp_solve(const LaunchList& ll, int B) {
+    return (int64_t)ll.count * B >= 8 * 152 && ll.rmax <= 1024;
+}
+
 template <class T>
 void run_trisolve(Plan& P, const int32_t* active, cudaStream_t s) {
     const int B = P.B;
@@ -1230,7 +1394,13 @@ void run_trisolve(Plan& P, const int32_t* active, cudaStream_t s) {
     for (const LaunchList& ll : P.solve_launches) {
         Prof pr(P, s, SSCO_K_FWD);
         const size_t smem = (size_t)ll.rmax * sizeof(T);
-        k_fwd<T><<<dim3(ll.count, B), 256, smem, s>>>(P.dt, P.dt.front_lists + ll.list_off, panel, P.panel_total,
+        if (use_warp_solve(ll, B)) {
+            const int64_t items = (int64_t)ll.count * B;
+            k_fwd_warp<T><<<cdiv(items, 8), 256, 8 * smem, s>>>(P.dt, P.dt.front_lists + ll.list_off, ll.count, B,
+                                                                ll.rmax, panel, P.panel_total, vecT, P.n, pvec,
+                                                                P.pvec_total, active, P.n_pats);
+        } else
+        k_fwd<T><<<dim3(ll.count, B), ll.rmax <= 128 ? 128 : 256, smem, s>>>(P.dt, P.dt.front_lists + ll.list_off, panel, P.panel_total,
                                                         vecT, P.n, pvec, P.pvec_total, active, P.n_pats);
         if (pr.ev >= 0) {
             Work w = work_solve(P, ll);
@@ -1241,7 +1411,13 @@ void run_trisolve(Plan& P, const int32_t* active, cudaStream_t s) {
         const LaunchList& ll = *it;
         Prof pr(P, s, SSCO_K_BWD);
         const size_t smem = (size_t)ll.rmax * sizeof(T);
-        k_bwd<T><<<dim3(ll.count, B), 256, smem, s>>>(P.dt, P.dt.front_lists + ll.list_off, panel, P.panel_total,
+        if (use_warp_solve(ll, B)) {
+            const int64_t items = (int64_t)ll.count * B;
+            k_bwd_warp<T><<<cdiv(items, 8), 256, 8 * smem, s>>>(P.dt, P.dt.front_lists + ll.list_off, ll.count, B,
+                                                                ll.rmax, panel, P.panel_total, vecT, P.n, active,
+                                                                P.n_pats);
+        } else
+        k_bwd<T><<<dim3(ll.count, B), ll.rmax <= 128 ? 128 : 256, smem, s>>>(P.dt, P.dt.front_lists + ll.list_off, panel, P.panel_total,
                                                         vecT, P.n, active, P.n_pats);
         if (pr.ev >= 0) {
             Work w = work_solve(P, ll);
@@ -1360,6 +1536,8 @@ template <class T>
 int set_attr_T() {
     int e = allow_dynamic_smem(k_front_small<T>);
     if (!e) e = allow_dynamic_smem(k_tiny_factor<T>);
+    if (!e) e = allow_dynamic_smem(k_fwd_warp<T>);
+    if (!e) e = allow_dynamic_smem(k_bwd_warp<T>);
     if (!e) e = allow_dynamic_smem(k_fwd<T>);
     if (!e) e = allow_dynamic_smem(k_bwd<T>);
     return e;
@@ -1522,6 +1700,23 @@ int profile_enable(Plan& P, int32_t max_launches) {
         int r = (int)cudaEventCreate(&e);
         if (r) return r;
         P.ev_pool.push_back((void*)e);
+    }
+    return 0;
+}
+
+int profile_trace(Plan& P, int32_t* kinds, float* ms, double* flops, double* bytes, int64_t cap, int64_t* n) {
+    int e = (int)cudaDeviceSynchronize();
+    if (e) return e;
+    *n = (int64_t)P.prof_recs.size();
+    for (int64_t i = 0; i < *n && i < cap; ++i) {
+        const ProfRec& r = P.prof_recs[i];
+        float t = 0;
+        e = (int)cudaEventElapsedTime(&t, (cudaEvent_t)P.ev_pool[r.ev], (cudaEvent_t)P.ev_pool[r.ev + 1]);
+        if (e) return e;
+        if (kinds) kinds[i] = r.kind;
+        if (ms) ms[i] = t;
+        if (flops) flops[i] = r.flops;
+        if (bytes) bytes[i] = r.bytes;
     }
     return 0;
 }

@@ -102,7 +102,7 @@ ssco_status validate(Plan& P, const ssco_pattern* p, int k) {
     return SSCO_OK;
 }
 
-constexpr int32_t kClasses[] = {32, 64, 96, 128, 160, 192, 224};
+constexpr int32_t kClasses[] = {32, 64, 96, 128, 160, 192, 224, 256, 288, 320};
 
 }  // namespace
 
@@ -117,7 +117,11 @@ ssco_status analyze_impl(const ssco_pattern* const* pats, int32_t n_pats, const 
     P.tol = op->refine_tol > 0 ? op->refine_tol : 1e-10;
     P.maxit = op->refine_max_iter > 0 ? op->refine_max_iter : 30;
     P.tsize = P.prec == SSCO_FP64 ? 8 : 4;
-    int32_t smax_default = P.prec == SSCO_FP64 ? 160 : 224;
+    // One CTA per (front, instance) holds the front as a packed lower
+    // triangle in shared memory (r(r+1)/2 * sizeof(T) <= 227 KB).  Its
+    // column steps are sequential, so wide fronts only pay off there when the
+    // batch supplies many CTAs; otherwise they take the multi-CTA path.
+    int32_t smax_default = P.B >= 32 ? (P.prec == SSCO_FP64 ? 224 : 320) : (P.prec == SSCO_FP64 ? 160 : 224);
     P.small_max = op->small_front_max > 0 ? std::min(op->small_front_max, smax_default) : smax_default;
     P.amalg = op->amalgamate;
     P.tiny_max = op->tiny_front_max == 0 ? 32 : (op->tiny_front_max < 0 ? 0 : std::min(op->tiny_front_max, 32));

@@ -31,7 +31,7 @@ EXPORTED_SYMBOLS = [
     "ssco_analyze", "ssco_plan_info", "ssco_plan_export", "ssco_bind", "ssco_numeric", "ssco_solve",
     "ssco_backward", "ssco_status_get", "ssco_export_L", "ssco_export_K", "ssco_refactor_solve_host",
     "ssco_last_launch_count", "ssco_last_error", "ssco_status_string", "ssco_plan_save", "ssco_plan_load",
-    "ssco_destroy", "ssco_profile_enable", "ssco_profile_read", "ssco_kernel_name", "ssco_solve_noalloc",
+    "ssco_destroy", "ssco_profile_enable", "ssco_profile_read", "ssco_kernel_name", "ssco_solve_noalloc", "ssco_profile_trace",
 ]
 KERNEL_KINDS = ["assemble", "front_small", "big_init", "big_kscatter", "big_gemm", "big_potrf", "big_syrk",
                 "fwd_solve", "bwd_solve", "resid", "check", "vector", "grad", "front_tiny", "big_trsm"]
@@ -106,6 +106,7 @@ def load_library(path: str = LIB_PATH):
         "ssco_profile_read": (i32, [vp, C.POINTER(KernelStat)]),
         "ssco_kernel_name": (C.c_char_p, [i32]),
         "ssco_solve_noalloc": (i32, [vp, vp, vp, vp]),
+        "ssco_profile_trace": (i32, [vp, vp, vp, vp, vp, i64, C.POINTER(i64)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -318,6 +319,18 @@ class Plan:
     def profile_enable(self, max_launches: int):
         """Per-kernel CUDA-event timing of subsequent launches (0 = off)."""
         self._check(self.L.ssco_profile_enable(self._h, int(max_launches)))
+
+    def profile_trace(self):
+        """Per-launch records (kind name, ms, flops, bytes) in launch order."""
+        n = C.c_int64(0)
+        self._check(self.L.ssco_profile_trace(self._h, None, None, None, None, 0, C.byref(n)))
+        k = np.zeros(n.value, np.int32)
+        ms = np.zeros(n.value, np.float32)
+        fl = np.zeros(n.value)
+        by = np.zeros(n.value)
+        self._check(self.L.ssco_profile_trace(self._h, k.ctypes.data, ms.ctypes.data, fl.ctypes.data,
+                                              by.ctypes.data, n.value, C.byref(n)))
+        return [(KERNEL_KINDS[int(a)], float(b), float(c), float(d)) for a, b, c, d in zip(k, ms, fl, by)]
 
     def profile_read(self):
         """{kernel kind: {launches, ms, flops, bytes}} summed since the last read."""

@@ -115,6 +115,19 @@ def test_fp32_batched_trigrid(S):
     assert np.all(st["iters"] >= 1)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_batched_warp_per_item_solves(S, prec):
+    """B = 64 value sets: the low levels take the warp-per-item solve kernels,
+    the top levels the CTA kernels; both must agree with the oracle."""
+    p = P.trigrid_problem(40, batch=64, cfg=3)
+    precision = S.FP64 if prec == "fp64" else S.FP32_REFINE
+    pl, x, st, *_ = run(S, p, precision)
+    assert np.all(st["status"] == 0)
+    for inst in (0, 31, 63):
+        r, res, err = check_against_oracle(S, pl, p, x, st, inst, inst)
+        assert err < (1e-12 if prec == "fp64" else 1e-8)
+
+
 def test_multi_pattern_uneven(S):
     probs = [P.trigrid_problem(s, 1, cfg=3, seed_offset=100 + k) for k, s in enumerate([5, 11, 17, 23, 30, 9])]
     pl, x, st, *_ = run(S, probs, S.FP32_REFINE, batch=1)
