@@ -70,11 +70,13 @@ void set_dev_tables(Plan& P) {
     d.e_elems_all = tab_ptr<int32_t>(P, P.toff.e_elems_all);
     d.tiny_list = tab_ptr<int32_t>(P, P.toff.tiny_list);
     d.tiny_off = tab_ptr<int32_t>(P, P.toff.tiny_off);
+    d.tiny_prog = tab_ptr<int32_t>(P, P.toff.tiny_prog);
+    d.tiny_prog_off = tab_ptr<int64_t>(P, P.toff.tiny_prog_off);
 }
 
 // ----- plan file (de)serialization -----------------------------------------
 constexpr uint64_t kMagic = 0x314F4353534F4353ull;  // "SCOSSCO1"
-constexpr uint32_t kVersion = 2;
+constexpr uint32_t kVersion = 3;
 
 struct Writer {
     std::ofstream f;
@@ -123,6 +125,7 @@ bool serialize(IO& io, Plan& P) {
     V(P.invmap); V(P.klist); V(P.front_lists); V(P.fact_launches); V(P.solve_launches);
     S(P.n_levels); S(P.panel_total); S(P.upd_total); S(P.pvec_total); S(P.max_rows);
     V(P.tiny_list); V(P.tiny_off); S(P.n_tiny);
+    V(P.tiny_prog); V(P.tiny_prog_off); S(P.tiny_prog_max); S(P.tiny_k_max);
     V(P.groups); V(P.chunks); V(P.asm_idx); V(P.asm_coef);
     V(P.sp_rowptr); V(P.sp_col); V(P.sp_slot); V(P.row_sys); V(P.sys_n_off); V(P.shifted);
     V(P.g_rowptr); V(P.g_colind); V(P.g_row_sys); V(P.g_rows_all); V(P.g_aval);

@@ -12,6 +12,12 @@
 
 namespace ssco {
 
+// Tiny-subtree programs (see build_tiny_programs in ssco_symbolic.cpp).
+constexpr int32_t kTinyHdrWords = 8;
+constexpr int32_t kTinyRecWords = 16;
+constexpr int32_t kTinyProgWords = 1024;  // per subtree, shared memory per warp
+constexpr int32_t kTinyMaxK = 256;        // K entries gathered per subtree
+
 // One front of the numeric partition (a fundamental or amalgamated
 // supernode).  Its factor columns [f, f+w) are stored as a dense r x w
 // column-major panel whose rows are rows[rows_off .. rows_off+r) (the first
@@ -94,6 +100,8 @@ struct DevTables {
     const int32_t* e_elems_all; // value indices that are elements
     const int32_t* tiny_list;   // fronts of every tiny subtree, children first
     const int32_t* tiny_off;    // [n_tiny+1] offsets into tiny_list
+    const int32_t* tiny_prog;   // per-subtree programs
+    const int64_t* tiny_prog_off;
 };
 
 // Byte offsets of every region of the caller's workspace.
@@ -156,6 +164,9 @@ struct Plan {
     std::vector<LaunchList> solve_launches;  // per level: all fronts
     std::vector<int32_t> tiny_list, tiny_off;  // warp-per-subtree fronts
     int32_t n_tiny = 0;
+    std::vector<int32_t> tiny_prog;
+    std::vector<int64_t> tiny_prog_off;
+    int32_t tiny_prog_max = 0, tiny_k_max = 0;
     int32_t n_levels = 0;
     int64_t panel_total = 0, upd_total = 0, pvec_total = 0;
     int32_t max_rows = 0;
@@ -186,7 +197,7 @@ struct Plan {
         size_t fronts, rows, child_ids, relmap, invmap, klist, front_lists, groups, chunks,
             asm_idx, asm_coef, sp_rowptr, sp_col, sp_slot, perm, row_sys, sys_n_off, g_rowptr,
             g_colind, g_aval, g_row_sys, e_dofs, e_K0, e_sys, e_off, e_k0off, e_dim, shifted,
-            g_rows_all, e_elems_all, tiny_list, tiny_off;
+            g_rows_all, e_elems_all, tiny_list, tiny_off, tiny_prog, tiny_prog_off;
     } toff{};
     WsLayout ws{};
     uint8_t* d_tab = nullptr;

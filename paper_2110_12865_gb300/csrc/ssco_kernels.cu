@@ -251,166 +251,242 @@ __global__ void __launch_bounds__(256) k_front_small(const DevTables t, const in
 // --------------------------------------------------------------------------
 constexpr int kTinyWarps = 8;
 
+// Shared-memory bytes per warp of the tiny kernels.
 template <class T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_tiny_factor(const DevTables t, int32_t n_tiny, int32_t B,
-                                                     const double* __restrict__ K, int64_t nnzK,
-                                                     T* __restrict__ panel, int64_t panel_total,
-                                                     T* __restrict__ upd, int64_t upd_total,
-                                                     int32_t* __restrict__ bad_col, int32_t n_pats) {
+__host__ __device__ inline int tiny_factor_warp_bytes(int prog_max, int k_max) {
+    return ((32 * 33 + k_max) * (int)sizeof(T) + prog_max * 4 + 15) & ~15;
+}
+template <class T>
+__host__ __device__ inline int tiny_solve_warp_bytes(int prog_max) {
+    return (32 * (int)sizeof(T) + prog_max * 4 + 15) & ~15;
+}
+
+// Loads subtree st's program into shared memory (coalesced).
+__device__ __forceinline__ void load_prog(const DevTables& t, int st, int32_t* prog, int lane) {
+    const int64_t base = t.tiny_prog_off[st];
+    const int total = (int)(t.tiny_prog_off[st + 1] - base);
+    for (int i = lane; i < total; i += 32) prog[i] = t.tiny_prog[base + i];
+    __syncwarp();
+}
+
+__device__ __forceinline__ int64_t prog_i64(const int32_t* rec, int at) {
+    return (int64_t)(uint32_t)rec[at] | ((int64_t)rec[at + 1] << 32);
+}
+
+// Partial Cholesky of one front of at most R rows held as lane-per-row
+// registers (a[k] = F[lane][k]); writes the r x w panel and the (r-w)^2
+// update.  Returns the first non-positive pivot's column or -1.
+template <class T, int R>
+__device__ __forceinline__ int tiny_chol_rows(T (*F)[33], int lane, int r, int w, T* __restrict__ Pf,
+                                              T* __restrict__ Uf) {
+    T a[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) a[k] = F[lane][k];
+    int bad = -1;
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        if (j < w) {
+            T djj = __shfl_sync(0xffffffffu, a[j], j);
+            if (!(djj > T(0))) {
+                if (bad < 0) bad = j;
+                djj = T(1);
+            }
+            const T ljj = sqrt(djj);
+            const T inv = T(1) / ljj;
+            if (lane == j)
+                a[j] = ljj;
+            else if (lane > j)
+                a[j] *= inv;
+#pragma unroll
+            for (int k = j + 1; k < R; ++k) {
+                if (k < r) {
+                    const T lkj = __shfl_sync(0xffffffffu, a[j], k);
+                    if (lane >= k) a[k] -= a[j] * lkj;
+                }
+            }
+        }
+    }
+    if (lane < r) {
+        const int ru = r - w;
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            if (k < w) Pf[(int64_t)k * r + lane] = lane >= k ? a[k] : T(0);
+            if (k >= w && k < r && lane >= k) Uf[(int64_t)(k - w) * ru + (lane - w)] = a[k];
+        }
+    }
+    return bad;
+}
+
+template <class T>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2)
+    k_tiny_factor(const DevTables t, int32_t n_tiny, int32_t B, int32_t prog_max, int32_t k_max,
+                  const double* __restrict__ K, int64_t nnzK, T* __restrict__ panel, int64_t panel_total,
+                  T* __restrict__ upd, int64_t upd_total, int32_t* __restrict__ bad_col, int32_t n_pats) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t item = (int64_t)blockIdx.x * kTinyWarps + wib;
     if (item >= (int64_t)n_tiny * B) return;
     const int st = (int)(item / B), b = (int)(item % B);
-    T(*F)[33] = reinterpret_cast<T(*)[33]>(smem_raw) + wib * 32;
+    unsigned char* mine = smem_raw + (size_t)wib * tiny_factor_warp_bytes<T>(prog_max, k_max);
+    T(*F)[33] = reinterpret_cast<T(*)[33]>(mine);
+    T* Fflat = reinterpret_cast<T*>(mine);
+    T* kv = reinterpret_cast<T*>(mine) + 32 * 33;
+    int32_t* prog = reinterpret_cast<int32_t*>(kv + k_max);
+    load_prog(t, st, prog, lane);
+    const int nf = prog[0], nk = prog[1], rec_off = prog[2], k_off = prog[4], sys = prog[7];
     const double* Kb = K + (int64_t)b * nnzK;
+    for (int e = lane; e < nk; e += 32) kv[e] = (T)Kb[prog[k_off + 2 * e]];
     T* Pb = panel + (int64_t)b * panel_total;
     T* Ub = upd + (int64_t)b * upd_total;
-    for (int q = t.tiny_off[st]; q < t.tiny_off[st + 1]; ++q) {
-        const FrontDesc d = t.fronts[t.tiny_list[q]];
-        const int r = d.r, w = d.w;
-        // fronts of a subtree are visited children-first, not in column
-        // order: record the first failing pivot of every front (atomicMin)
-        bool failed = false;
-#pragma unroll
-        for (int k = 0; k < 32; ++k) F[lane][k] = T(0);
+    const int n_off = (int)t.sys_n_off[sys];
+    __syncwarp();
+    for (int q = 0; q < nf; ++q) {
+        const int32_t* rec = prog + rec_off + kTinyRecWords * q;
+        const int r = rec[0], w = rec[1], f = rec[2], nchild = rec[3];
+        const int kbeg = rec[5], kn = rec[6];
+        const int64_t panel_off = prog_i64(rec, 10), upd_off = prog_i64(rec, 12);
+        for (int k = 0; k < r; ++k) F[lane][k] = T(0);
         __syncwarp();
-        const int32_t* kl = t.klist + 2 * d.klist_off;
-        for (int e = lane; e < d.klist_n; e += 32) {
-            const int pos = kl[2 * e + 1];
-            F[pos % r][pos / r] = (T)Kb[kl[2 * e]];
-        }
-        for (int c = 0; c < d.nchild; ++c) {
+        for (int e = lane; e < kn; e += 32) Fflat[prog[k_off + 2 * (kbeg + e) + 1]] = kv[kbeg + e];
+        for (int c = 0; c < nchild; ++c) {
             __syncwarp();
-            const FrontDesc cd = t.fronts[t.child_ids[d.child_off + c]];
-            const int rc = cd.r - cd.w;
-            const int32_t* map = t.relmap + cd.relmap_off;
-            const T* S = Ub + cd.upd_off;
+            const int32_t* crec = prog + rec_off + kTinyRecWords * prog[rec[4] + c];
+            const int rc = crec[0] - crec[1];
+            const int32_t* map = prog + crec[7];
+            const T* S = Ub + prog_i64(crec, 12);
             if (lane < rc) {
                 const int mi = map[lane];
                 for (int kk = 0; kk <= lane; ++kk) F[mi][map[kk]] += S[lane + kk * rc];
             }
         }
         __syncwarp();
-        T a[32];
-#pragma unroll
-        for (int k = 0; k < 32; ++k) a[k] = F[lane][k];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-            if (j < w) {
-                T djj = __shfl_sync(0xffffffffu, a[j], j);
-                if (!(djj > T(0))) {
-                    if (lane == 0 && !failed)
-                        atomicMin(&bad_col[(int64_t)b * n_pats + d.sys], d.f + j - (int)t.sys_n_off[d.sys]);
-                    failed = true;
-                    djj = T(1);
-                }
-                const T ljj = sqrt(djj);
-                const T inv = T(1) / ljj;
-                if (lane == j)
-                    a[j] = ljj;
-                else if (lane > j)
-                    a[j] *= inv;
-#pragma unroll
-                for (int k = j + 1; k < 32; ++k) {
-                    if (k < r) {
-                        const T lkj = __shfl_sync(0xffffffffu, a[j], k);
-                        if (lane >= k) a[k] -= a[j] * lkj;
-                    }
-                }
-            }
-        }
-        if (lane < r) {
-            const int ru = r - w;
-#pragma unroll
-            for (int k = 0; k < 32; ++k) {
-                if (k < w) Pb[d.panel_off + (int64_t)k * r + lane] = lane >= k ? a[k] : T(0);
-                if (k >= w && k < r && lane >= k) Ub[d.upd_off + (int64_t)(k - w) * ru + (lane - w)] = a[k];
-            }
-        }
+        // fronts of a subtree are visited children-first, not in column
+        // order: record the first failing pivot of every front (atomicMin)
+        int badj;
+        if (r <= 8)
+            badj = tiny_chol_rows<T, 8>(F, lane, r, w, Pb + panel_off, Ub + upd_off);
+        else if (r <= 16)
+            badj = tiny_chol_rows<T, 16>(F, lane, r, w, Pb + panel_off, Ub + upd_off);
+        else
+            badj = tiny_chol_rows<T, 32>(F, lane, r, w, Pb + panel_off, Ub + upd_off);
+        if (badj >= 0 && lane == 0) atomicMin(&bad_col[(int64_t)b * n_pats + sys], f + badj - n_off);
         __syncwarp();
     }
 }
 
+// Forward / backward substitution with the w <= W columns of one tiny
+// front; lane i holds row i.
+template <class T, int W>
+__device__ __forceinline__ T tiny_fwd_chain(const T* __restrict__ Pf, int lane, int r, int w, T v) {
+    T a[W];
+#pragma unroll
+    for (int j = 0; j < W; ++j) a[j] = (j < w && lane < r) ? Pf[(int64_t)j * r + lane] : T(0);
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+        if (j < w) {
+            const T djj = __shfl_sync(0xffffffffu, a[j], j);
+            const T yj = __shfl_sync(0xffffffffu, v, j) / djj;
+            if (lane == j)
+                v = yj;
+            else if (lane > j)
+                v -= a[j] * yj;
+        }
+    }
+    return v;
+}
+
+template <class T, int W>
+__device__ __forceinline__ T tiny_bwd_chain(const T* __restrict__ Pf, int lane, int r, int w, T v) {
+    T a[W];
+#pragma unroll
+    for (int j = 0; j < W; ++j) a[j] = (j < w && lane < r) ? Pf[(int64_t)j * r + lane] : T(0);
+#pragma unroll
+    for (int j = W - 1; j >= 0; --j) {
+        if (j < w) {
+            T s = (lane > j && lane < r) ? a[j] * v : T(0);
+            s = warp_sum(s);
+            if (lane == j) v = (v - s) / a[j];
+        }
+    }
+    return v;
+}
+
 template <class T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_tiny_fwd(const DevTables t, int32_t n_tiny, int32_t B,
+__global__ void __launch_bounds__(256) k_tiny_fwd(const DevTables t, int32_t n_tiny, int32_t B, int32_t prog_max,
                                                   const T* __restrict__ panel, int64_t panel_total,
                                                   T* __restrict__ vec, int64_t n, T* __restrict__ pvec,
                                                   int64_t pvec_total, const int32_t* __restrict__ active,
                                                   int32_t n_pats) {
-    __shared__ T vs[kTinyWarps][32];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t item = (int64_t)blockIdx.x * kTinyWarps + wib;
     if (item >= (int64_t)n_tiny * B) return;
     const int st = (int)(item / B), b = (int)(item % B);
-    const int q0 = t.tiny_off[st], q1 = t.tiny_off[st + 1];
-    if (active && !active[(int64_t)b * n_pats + t.fronts[t.tiny_list[q0]].sys]) return;
+    unsigned char* mine = smem_raw + (size_t)wib * tiny_solve_warp_bytes<T>(prog_max);
+    T* vs = reinterpret_cast<T*>(mine);
+    int32_t* prog = reinterpret_cast<int32_t*>(vs + 32);
+    load_prog(t, st, prog, lane);
+    const int nf = prog[0], rec_off = prog[2];
+    if (active && !active[(int64_t)b * n_pats + prog[7]]) return;
     const T* Pb = panel + (int64_t)b * panel_total;
     T* vb = vec + (int64_t)b * n;
     T* pv = pvec + (int64_t)b * pvec_total;
-    for (int q = q0; q < q1; ++q) {
-        const FrontDesc d = t.fronts[t.tiny_list[q]];
-        const int r = d.r, w = d.w;
-        vs[wib][lane] = lane < w ? vb[d.f + lane] : T(0);
-        for (int c = 0; c < d.nchild; ++c) {
+    for (int q = 0; q < nf; ++q) {
+        const int32_t* rec = prog + rec_off + kTinyRecWords * q;
+        const int r = rec[0], w = rec[1], f = rec[2], nchild = rec[3];
+        const int64_t panel_off = prog_i64(rec, 10), pvec_off = prog_i64(rec, 14);
+        vs[lane] = lane < w ? vb[f + lane] : T(0);
+        for (int c = 0; c < nchild; ++c) {
             __syncwarp();
-            const FrontDesc cd = t.fronts[t.child_ids[d.child_off + c]];
-            const int rc = cd.r - cd.w;
-            if (lane < rc) vs[wib][t.relmap[cd.relmap_off + lane]] += pv[cd.pvec_off + lane];
+            const int32_t* crec = prog + rec_off + kTinyRecWords * prog[rec[4] + c];
+            const int rc = crec[0] - crec[1];
+            if (lane < rc) vs[prog[crec[7] + lane]] += pv[prog_i64(crec, 14) + lane];
         }
         __syncwarp();
-        T v = vs[wib][lane];
-        T a[32];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) a[j] = (j < w && lane < r) ? Pb[d.panel_off + (int64_t)j * r + lane] : T(0);
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-            if (j < w) {
-                const T djj = __shfl_sync(0xffffffffu, a[j], j);
-                const T yj = __shfl_sync(0xffffffffu, v, j) / djj;
-                if (lane == j)
-                    v = yj;
-                else if (lane > j)
-                    v -= a[j] * yj;
-            }
-        }
+        T v = vs[lane];
+        if (w <= 8)
+            v = tiny_fwd_chain<T, 8>(Pb + panel_off, lane, r, w, v);
+        else if (w <= 16)
+            v = tiny_fwd_chain<T, 16>(Pb + panel_off, lane, r, w, v);
+        else
+            v = tiny_fwd_chain<T, 32>(Pb + panel_off, lane, r, w, v);
         if (lane < w)
-            vb[d.f + lane] = v;
+            vb[f + lane] = v;
         else if (lane < r)
-            pv[d.pvec_off + lane - w] = v;
+            pv[pvec_off + lane - w] = v;
         __syncwarp();
     }
 }
 
 template <class T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_tiny_bwd(const DevTables t, int32_t n_tiny, int32_t B,
+__global__ void __launch_bounds__(256) k_tiny_bwd(const DevTables t, int32_t n_tiny, int32_t B, int32_t prog_max,
                                                   const T* __restrict__ panel, int64_t panel_total,
                                                   T* __restrict__ vec, int64_t n, const int32_t* __restrict__ active,
                                                   int32_t n_pats) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t item = (int64_t)blockIdx.x * kTinyWarps + wib;
     if (item >= (int64_t)n_tiny * B) return;
     const int st = (int)(item / B), b = (int)(item % B);
-    const int q0 = t.tiny_off[st], q1 = t.tiny_off[st + 1];
-    if (active && !active[(int64_t)b * n_pats + t.fronts[t.tiny_list[q0]].sys]) return;
+    unsigned char* mine = smem_raw + (size_t)wib * tiny_solve_warp_bytes<T>(prog_max);
+    int32_t* prog = reinterpret_cast<int32_t*>(reinterpret_cast<T*>(mine) + 32);
+    load_prog(t, st, prog, lane);
+    const int nf = prog[0], rec_off = prog[2];
+    if (active && !active[(int64_t)b * n_pats + prog[7]]) return;
     const T* Pb = panel + (int64_t)b * panel_total;
     T* vb = vec + (int64_t)b * n;
-    for (int q = q1 - 1; q >= q0; --q) {
-        const FrontDesc d = t.fronts[t.tiny_list[q]];
-        const int r = d.r, w = d.w;
-        T v = lane < w ? vb[d.f + lane] : (lane < r ? vb[t.rows[d.rows_off + lane]] : T(0));
-        T a[32];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) a[j] = (j < w && lane < r) ? Pb[d.panel_off + (int64_t)j * r + lane] : T(0);
-#pragma unroll
-        for (int j = 31; j >= 0; --j) {
-            if (j < w) {
-                T s = (lane > j && lane < r) ? a[j] * v : T(0);
-                s = warp_sum(s);
-                if (lane == j) v = (v - s) / a[j];
-            }
-        }
-        if (lane < w) vb[d.f + lane] = v;
+    for (int q = nf - 1; q >= 0; --q) {
+        const int32_t* rec = prog + rec_off + kTinyRecWords * q;
+        const int r = rec[0], w = rec[1], f = rec[2];
+        const int64_t panel_off = prog_i64(rec, 10);
+        T v = lane < w ? vb[f + lane] : (lane < r ? vb[prog[rec[8] + lane - w]] : T(0));
+        if (w <= 8)
+            v = tiny_bwd_chain<T, 8>(Pb + panel_off, lane, r, w, v);
+        else if (w <= 16)
+            v = tiny_bwd_chain<T, 16>(Pb + panel_off, lane, r, w, v);
+        else
+            v = tiny_bwd_chain<T, 32>(Pb + panel_off, lane, r, w, v);
+        if (lane < w) vb[f + lane] = v;
         __syncwarp();
     }
 }
@@ -860,14 +936,16 @@ __global__ void __launch_bounds__(256) k_fwd_warp(const DevTables t, const int32
             const int i = i0 + lane;
             if (i < r) {
                 const T* col = Pb + (int64_t)jb * r + i;
-                T s0 = T(0), s1 = T(0);
+                T acc[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) acc[u] = T(0);
                 int j = 0;
-                for (; j + 1 < nbk; j += 2) {
-                    s0 += col[(int64_t)j * r] * v[jb + j];
-                    s1 += col[(int64_t)(j + 1) * r] * v[jb + j + 1];
+                for (; j + 7 < nbk; j += 8) {
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) acc[u] += col[(int64_t)(j + u) * r] * v[jb + j + u];
                 }
-                if (j < nbk) s0 += col[(int64_t)j * r] * v[jb + j];
-                v[i] -= s0 + s1;
+                for (; j < nbk; ++j) acc[0] += col[(int64_t)j * r] * v[jb + j];
+                v[i] -= ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
             }
         }
         __syncwarp();
@@ -1249,8 +1327,10 @@ int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cud
     if (P.n_tiny > 0) {
         Prof pr(P, s, SSCO_K_FRONT_TINY);
         const int64_t items = (int64_t)P.n_tiny * B;
-        k_tiny_factor<T><<<cdiv(items, kTinyWarps), 32 * kTinyWarps, kTinyWarps * 32 * 33 * sizeof(T), s>>>(
-            P.dt, P.n_tiny, B, K, P.nnzK, panel, P.panel_total, upd, P.upd_total, bad, P.n_pats);
+        k_tiny_factor<T><<<cdiv(items, kTinyWarps), 32 * kTinyWarps,
+                           kTinyWarps * tiny_factor_warp_bytes<T>(P.tiny_prog_max, P.tiny_k_max), s>>>(
+            P.dt, P.n_tiny, B, P.tiny_prog_max, P.tiny_k_max, K, P.nnzK, panel, P.panel_total, upd, P.upd_total, bad,
+            P.n_pats);
         if (pr.ev >= 0) {
             Work w = work_tiny(P, false);
             pr.done(w.flops, w.bytes);
@@ -1384,8 +1464,9 @@ void run_trisolve(Plan& P, const int32_t* active, cudaStream_t s) {
     const unsigned tiny_grid = cdiv((int64_t)P.n_tiny * B, kTinyWarps);
     if (P.n_tiny > 0) {
         Prof pr(P, s, SSCO_K_FWD);
-        k_tiny_fwd<T><<<tiny_grid, 32 * kTinyWarps, 0, s>>>(P.dt, P.n_tiny, B, panel, P.panel_total, vecT, P.n, pvec,
-                                                          P.pvec_total, active, P.n_pats);
+        k_tiny_fwd<T><<<tiny_grid, 32 * kTinyWarps, kTinyWarps * tiny_solve_warp_bytes<T>(P.tiny_prog_max), s>>>(
+            P.dt, P.n_tiny, B, P.tiny_prog_max, panel, P.panel_total, vecT, P.n, pvec, P.pvec_total, active,
+            P.n_pats);
         if (pr.ev >= 0) {
             Work w = work_tiny(P, true);
             pr.done(w.flops, w.bytes);
@@ -1426,8 +1507,8 @@ void run_trisolve(Plan& P, const int32_t* active, cudaStream_t s) {
     }
     if (P.n_tiny > 0) {
         Prof pr(P, s, SSCO_K_BWD);
-        k_tiny_bwd<T><<<tiny_grid, 32 * kTinyWarps, 0, s>>>(P.dt, P.n_tiny, B, panel, P.panel_total, vecT, P.n,
-                                                          active, P.n_pats);
+        k_tiny_bwd<T><<<tiny_grid, 32 * kTinyWarps, kTinyWarps * tiny_solve_warp_bytes<T>(P.tiny_prog_max), s>>>(
+            P.dt, P.n_tiny, B, P.tiny_prog_max, panel, P.panel_total, vecT, P.n, active, P.n_pats);
         if (pr.ev >= 0) {
             Work w = work_tiny(P, true);
             pr.done(w.flops, w.bytes);
@@ -1536,6 +1617,8 @@ template <class T>
 int set_attr_T() {
     int e = allow_dynamic_smem(k_front_small<T>);
     if (!e) e = allow_dynamic_smem(k_tiny_factor<T>);
+    if (!e) e = allow_dynamic_smem(k_tiny_fwd<T>);
+    if (!e) e = allow_dynamic_smem(k_tiny_bwd<T>);
     if (!e) e = allow_dynamic_smem(k_fwd_warp<T>);
     if (!e) e = allow_dynamic_smem(k_bwd_warp<T>);
     if (!e) e = allow_dynamic_smem(k_fwd<T>);
@@ -1664,8 +1747,9 @@ int launch_solve_static(Plan& P, const double* b, double* x, void* stream) {
     P.launches += 2;
     const unsigned tiny_grid = cdiv((int64_t)P.n_tiny * B, kTinyWarps);
     if (P.n_tiny > 0) {
-        k_tiny_fwd<double><<<tiny_grid, 32 * kTinyWarps, 0, s>>>(P.dt, P.n_tiny, B, panel, P.panel_total, vec, n, pvec,
-                                                               P.pvec_total, nullptr, P.n_pats);
+        k_tiny_fwd<double><<<tiny_grid, 32 * kTinyWarps, kTinyWarps * tiny_solve_warp_bytes<double>(P.tiny_prog_max),
+                             s>>>(P.dt, P.n_tiny, B, P.tiny_prog_max, panel, P.panel_total, vec, n, pvec,
+                                  P.pvec_total, nullptr, P.n_pats);
         P.launches++;
     }
     for (const LaunchList& ll : P.solve_launches) {
@@ -1680,8 +1764,9 @@ int launch_solve_static(Plan& P, const double* b, double* x, void* stream) {
         P.launches++;
     }
     if (P.n_tiny > 0) {
-        k_tiny_bwd<double><<<tiny_grid, 32 * kTinyWarps, 0, s>>>(P.dt, P.n_tiny, B, panel, P.panel_total, vec, n,
-                                                               nullptr, P.n_pats);
+        k_tiny_bwd<double><<<tiny_grid, 32 * kTinyWarps, kTinyWarps * tiny_solve_warp_bytes<double>(P.tiny_prog_max),
+                             s>>>(P.dt, P.n_tiny, B, P.tiny_prog_max, panel, P.panel_total, vec, n, nullptr,
+                                  P.n_pats);
         P.launches++;
     }
     k_permute_out<<<gv, 256, 0, s>>>(vec, P.dt.perm, n, x);

@@ -104,6 +104,82 @@ ssco_status validate(Plan& P, const ssco_pattern* p, int k) {
 
 constexpr int32_t kClasses[] = {32, 64, 96, 128, 160, 192, 224, 256, 288, 320};
 
+// Program of one tiny subtree (int32 words), loaded whole into shared memory
+// by the warp that runs it:
+//   header [kTinyHdrWords]: nfronts, nk, rec_off, child_off, k_off, map_off, total, sys
+//   per front (children first) [kTinyRecWords]: r, w, f, nchild, child list
+//     offset, first K entry, K count, relmap offset (into the parent, -1 for
+//     the subtree root), below-rows offset, pad, panel_off (2 words), upd_off
+//     (2), pvec_off (2)
+//   child lists (local front indices), K entries (kslot, row*33 + col),
+//   relative maps, below-row lists (global row indices).
+void build_tiny_programs(Plan& P) {
+    P.tiny_prog.clear();
+    P.tiny_prog_off.assign(1, 0);
+    P.tiny_prog_max = 0;
+    P.tiny_k_max = 0;
+    std::vector<int32_t> local(P.fronts.size(), -1);
+    for (int32_t st = 0; st < P.n_tiny; ++st) {
+        const int32_t q0 = P.tiny_off[st], q1 = P.tiny_off[st + 1], nfq = q1 - q0;
+        for (int32_t q = q0; q < q1; ++q) local[P.tiny_list[q]] = q - q0;
+        int64_t nch = 0, nk = 0, nmap = 0;
+        for (int32_t q = q0; q < q1; ++q) {
+            const FrontDesc& d = P.fronts[P.tiny_list[q]];
+            nch += d.nchild;
+            nk += d.klist_n;
+            nmap += d.r - d.w;
+        }
+        const int64_t rec_off = kTinyHdrWords, child_off = rec_off + (int64_t)kTinyRecWords * nfq;
+        const int64_t k_off = child_off + nch, map_off = k_off + 2 * nk, rows_off = map_off + nmap;
+        const int64_t total = rows_off + nmap;
+        std::vector<int32_t> g(total, 0);
+        g[0] = nfq;
+        g[1] = (int32_t)nk;
+        g[2] = (int32_t)rec_off;
+        g[3] = (int32_t)child_off;
+        g[4] = (int32_t)k_off;
+        g[5] = (int32_t)map_off;
+        g[6] = (int32_t)total;
+        g[7] = P.fronts[P.tiny_list[q0]].sys;
+        int64_t cpos = child_off, kpos = 0, mpos = map_off, rpos = rows_off;
+        for (int32_t q = q0; q < q1; ++q) {
+            const FrontDesc& d = P.fronts[P.tiny_list[q]];
+            int32_t* rec = &g[rec_off + (int64_t)kTinyRecWords * (q - q0)];
+            rec[0] = d.r;
+            rec[1] = d.w;
+            rec[2] = d.f;
+            rec[3] = d.nchild;
+            rec[4] = (int32_t)cpos;
+            rec[5] = (int32_t)kpos;
+            rec[6] = d.klist_n;
+            for (int32_t c = 0; c < d.nchild; ++c) g[cpos++] = local[P.child_ids[d.child_off + c]];
+            for (int32_t e = 0; e < d.klist_n; ++e) {
+                const int32_t slot = P.klist[2 * (d.klist_off + e)], pos = P.klist[2 * (d.klist_off + e) + 1];
+                const int32_t col = pos / d.r, row = pos % d.r;
+                g[k_off + 2 * (kpos + e)] = slot;
+                g[k_off + 2 * (kpos + e) + 1] = row * 33 + col;
+            }
+            kpos += d.klist_n;
+            const bool has_parent_inside = d.parent >= 0 && local[d.parent] >= 0;
+            rec[7] = has_parent_inside ? (int32_t)mpos : -1;
+            for (int32_t k = 0; k < d.r - d.w; ++k) g[mpos++] = has_parent_inside ? P.relmap[d.relmap_off + k] : 0;
+            rec[8] = (int32_t)rpos;
+            for (int32_t k = 0; k < d.r - d.w; ++k) g[rpos++] = P.rows[d.rows_off + d.w + k];
+            rec[10] = (int32_t)(d.panel_off & 0xffffffff);
+            rec[11] = (int32_t)(d.panel_off >> 32);
+            rec[12] = (int32_t)(d.upd_off & 0xffffffff);
+            rec[13] = (int32_t)(d.upd_off >> 32);
+            rec[14] = (int32_t)(d.pvec_off & 0xffffffff);
+            rec[15] = (int32_t)(d.pvec_off >> 32);
+        }
+        for (int32_t q = q0; q < q1; ++q) local[P.tiny_list[q]] = -1;
+        P.tiny_prog.insert(P.tiny_prog.end(), g.begin(), g.end());
+        P.tiny_prog_off.push_back((int64_t)P.tiny_prog.size());
+        P.tiny_prog_max = std::max<int32_t>(P.tiny_prog_max, (int32_t)total);
+        P.tiny_k_max = std::max<int32_t>(P.tiny_k_max, (int32_t)nk);
+    }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -601,10 +677,20 @@ ssco_status analyze_impl(const ssco_pattern* const* pats, int32_t n_pats, const 
         P.tiny_list.clear();
         P.tiny_off.assign(1, 0);
         if (P.tiny_max > 0) {
+            // eligible: the whole subtree has r <= tiny_max and its program
+            // (see build_tiny_programs) fits kTinyProgWords / kTinyMaxK
             std::vector<char> ok(nf, 1);
+            std::vector<int64_t> words(nf, 0), kents(nf, 0);
             for (int32_t F = 0; F < nf; ++F) {
-                if (P.fronts[F].r > P.tiny_max) ok[F] = 0;
-                if (P.fronts[F].parent >= 0 && !ok[F]) ok[P.fronts[F].parent] = 0;
+                const FrontDesc& d = P.fronts[F];
+                words[F] += kTinyRecWords + d.nchild + 2 * d.klist_n + 2 * (d.r - d.w);
+                kents[F] += d.klist_n;
+                if (d.r > P.tiny_max || words[F] + kTinyHdrWords > kTinyProgWords || kents[F] > kTinyMaxK) ok[F] = 0;
+                if (d.parent >= 0) {
+                    words[d.parent] += words[F];
+                    kents[d.parent] += kents[F];
+                    if (!ok[F]) ok[d.parent] = 0;
+                }
             }
             in_tiny = ok;
             std::vector<int32_t> stack;
@@ -627,6 +713,7 @@ ssco_status analyze_impl(const ssco_pattern* const* pats, int32_t n_pats, const 
             }
         }
         P.n_tiny = (int32_t)P.tiny_off.size() - 1;
+        build_tiny_programs(P);
         for (int32_t F = 0; F < nf; ++F) {
             if (in_tiny[F]) continue;
             int32_t p = P.fronts[F].parent;
@@ -831,6 +918,8 @@ void build_blob(Plan& P) {
     P.toff.e_elems_all = put(b, P.e_elems_all);
     P.toff.tiny_list = put(b, P.tiny_list);
     P.toff.tiny_off = put(b, P.tiny_off);
+    P.toff.tiny_prog = put(b, P.tiny_prog);
+    P.toff.tiny_prog_off = put(b, P.tiny_prog_off);
     b.resize((b.size() + 255) & ~(size_t)255);
 }
 
