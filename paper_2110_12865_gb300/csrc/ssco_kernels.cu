@@ -243,6 +243,251 @@ __global__ void __launch_bounds__(256) k_front_small(const DevTables t, const in
     }
 }
 
+// Instance-vectorized variant of k_front_small for small fronts and batches:
+// one CTA factors the same front for V consecutive value sets, stored
+// interleaved ([packed index][V]) so that one 16-byte shared-memory access
+// serves all V and the index arithmetic is paid once per V fronts (the
+// members of a group share one template expression, Sec. 4.8).
+template <class T, int V>
+struct VecOf;
+template <>
+struct VecOf<float, 4> {
+    typedef float4 type;
+};
+template <>
+struct VecOf<double, 2> {
+    typedef double2 type;
+};
+
+template <class T, int V>
+__device__ __forceinline__ void vld(const T* p, T (&x)[V]) {
+    typedef typename VecOf<T, V>::type VT;
+    const VT u = *reinterpret_cast<const VT*>(p);
+    const T* e = reinterpret_cast<const T*>(&u);
+#pragma unroll
+    for (int v = 0; v < V; ++v) x[v] = e[v];
+}
+
+template <class T, int V>
+__device__ __forceinline__ void vst(T* p, const T (&x)[V]) {
+    typedef typename VecOf<T, V>::type VT;
+    VT u;
+    T* e = reinterpret_cast<T*>(&u);
+#pragma unroll
+    for (int v = 0; v < V; ++v) e[v] = x[v];
+    *reinterpret_cast<VT*>(p) = u;
+}
+
+template <class T, int V>
+__global__ void __launch_bounds__(256) k_front_vec(const DevTables t, const int32_t* __restrict__ list, int32_t B,
+                                                   const double* __restrict__ K, int64_t nnzK,
+                                                   T* __restrict__ panel, int64_t panel_total,
+                                                   T* __restrict__ upd, int64_t upd_total,
+                                                   int32_t* __restrict__ bad_col, int32_t n_pats) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* F = reinterpret_cast<T*>(smem_raw);
+    const FrontDesc d = t.fronts[list[blockIdx.x]];
+    const int b0 = blockIdx.y * V;
+    const int nv = min(V, B - b0);
+    const int r = d.r, w = d.w;
+    const int lane = threadIdx.x, warp = threadIdx.y, nw = blockDim.y;
+    const int tid = lane + 32 * warp, nth = 32 * nw;
+    const int npk = r * (r + 1) / 2;
+    for (int q = tid; q < npk * V; q += nth) F[q] = T(0);
+    __syncthreads();
+    const int32_t* kl = t.klist + 2 * d.klist_off;
+    for (int e = tid; e < d.klist_n; e += nth) {
+        const int pos = kl[2 * e + 1], slot = kl[2 * e];
+        const int col = pos / r, row = pos - col * r;
+        T* dst = F + (int64_t)(packed_col(col, r) + row - col) * V;
+        for (int v = 0; v < nv; ++v) dst[v] = (T)K[(int64_t)(b0 + v) * nnzK + slot];
+    }
+    for (int c = 0; c < d.nchild; ++c) {
+        __syncthreads();
+        const FrontDesc cd = t.fronts[t.child_ids[d.child_off + c]];
+        const int rc = cd.r - cd.w;
+        const int32_t* map = t.relmap + cd.relmap_off;
+        const T* S0 = upd + (int64_t)b0 * upd_total + cd.upd_off;
+        for (int kk = warp; kk < rc; kk += nw) {
+            const int mk = map[kk];
+            T* Fk = F + (int64_t)(packed_col(mk, r) - mk) * V;
+            for (int ii = kk + lane; ii < rc; ii += 32) {
+                T x[V];
+                vld<T, V>(Fk + (int64_t)map[ii] * V, x);
+                const int64_t o = (int64_t)kk * rc + ii;
+#pragma unroll
+                for (int v = 0; v < V; ++v)
+                    if (v < nv) x[v] += S0[(int64_t)v * upd_total + o];
+                vst<T, V>(Fk + (int64_t)map[ii] * V, x);
+            }
+        }
+    }
+    __syncthreads();
+    constexpr int kPanel = 16;
+    bool failed[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) failed[v] = false;
+    const int tx = tid & 15, ty = tid >> 4, ny = nth >> 4;
+    const int n_off = (int)t.sys_n_off[d.sys];
+    for (int j0 = 0; j0 < w; j0 += kPanel) {
+        const int j1 = min(j0 + kPanel, w);
+        T prev_inv[V], prev_l[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) prev_inv[v] = prev_l[v] = T(1);
+        for (int j = j0; j < j1; ++j) {
+            T* Fj = F + (int64_t)(packed_col(j, r) - j) * V;
+            T djj[V], invd[V];
+            vld<T, V>(Fj + (int64_t)j * V, djj);
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                if (!(djj[v] > T(0))) {
+                    if (v < nv && tid == 0 && !failed[v])
+                        atomicMin(&bad_col[(int64_t)(b0 + v) * n_pats + d.sys], d.f + j - n_off);
+                    failed[v] = true;
+                    djj[v] = T(1);
+                }
+                invd[v] = T(1) / djj[v];
+            }
+            if (j > j0) {
+                T* Fp = F + (int64_t)(packed_col(j - 1, r) - (j - 1)) * V;
+                for (int i = j + tid; i < r; i += nth) {
+                    T x[V];
+                    vld<T, V>(Fp + (int64_t)i * V, x);
+#pragma unroll
+                    for (int v = 0; v < V; ++v) x[v] *= prev_inv[v];
+                    vst<T, V>(Fp + (int64_t)i * V, x);
+                }
+                if (tid == 0) vst<T, V>(Fp + (int64_t)(j - 1) * V, prev_l);
+            }
+            for (int k = j + 1 + warp; k < j1; k += nw) {
+                T lk[V];
+                vld<T, V>(Fj + (int64_t)k * V, lk);
+#pragma unroll
+                for (int v = 0; v < V; ++v) lk[v] *= invd[v];
+                T* Fk = F + (int64_t)(packed_col(k, r) - k) * V;
+                for (int i = k + lane; i < r; i += 32) {
+                    T x[V], y[V];
+                    vld<T, V>(Fk + (int64_t)i * V, x);
+                    vld<T, V>(Fj + (int64_t)i * V, y);
+#pragma unroll
+                    for (int v = 0; v < V; ++v) x[v] -= y[v] * lk[v];
+                    vst<T, V>(Fk + (int64_t)i * V, x);
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                prev_l[v] = sqrt(djj[v]);
+                prev_inv[v] = T(1) / prev_l[v];
+            }
+            __syncthreads();
+        }
+        {
+            const int j = j1 - 1;
+            T* Fj = F + (int64_t)(packed_col(j, r) - j) * V;
+            for (int i = j + 1 + tid; i < r; i += nth) {
+                T x[V];
+                vld<T, V>(Fj + (int64_t)i * V, x);
+#pragma unroll
+                for (int v = 0; v < V; ++v) x[v] *= prev_inv[v];
+                vst<T, V>(Fj + (int64_t)i * V, x);
+            }
+            if (tid == 0) vst<T, V>(Fj + (int64_t)j * V, prev_l);
+        }
+        __syncthreads();
+        const int m = r - j1;
+        if (m > 0) {
+            const int tk_cols = 2 * ny;
+            for (int c0 = 0; c0 < m; c0 += tk_cols) {
+                for (int r0 = (c0 / 64) * 64; r0 < m; r0 += 64) {
+                    T acc[4][2][V];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int q = 0; q < 2; ++q)
+#pragma unroll
+                            for (int v = 0; v < V; ++v) acc[a][q][v] = T(0);
+                    int ii[4], kk[2];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) ii[a] = j1 + r0 + tx + 16 * a;
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) kk[q] = j1 + c0 + ty + ny * q;
+                    for (int j = j0; j < j1; ++j) {
+                        const T* Fj = F + (int64_t)(packed_col(j, r) - j) * V;
+                        T ra[4][V], cb[2][V];
+#pragma unroll
+                        for (int a = 0; a < 4; ++a) {
+                            if (ii[a] < r)
+                                vld<T, V>(Fj + (int64_t)ii[a] * V, ra[a]);
+                            else
+#pragma unroll
+                                for (int v = 0; v < V; ++v) ra[a][v] = T(0);
+                        }
+#pragma unroll
+                        for (int q = 0; q < 2; ++q) {
+                            if (kk[q] < r)
+                                vld<T, V>(Fj + (int64_t)kk[q] * V, cb[q]);
+                            else
+#pragma unroll
+                                for (int v = 0; v < V; ++v) cb[q][v] = T(0);
+                        }
+#pragma unroll
+                        for (int a = 0; a < 4; ++a)
+#pragma unroll
+                            for (int q = 0; q < 2; ++q)
+#pragma unroll
+                                for (int v = 0; v < V; ++v) acc[a][q][v] += ra[a][v] * cb[q][v];
+                    }
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        if (kk[q] >= r) continue;
+                        T* Fk = F + (int64_t)(packed_col(kk[q], r) - kk[q]) * V;
+#pragma unroll
+                        for (int a = 0; a < 4; ++a) {
+                            if (ii[a] < r && ii[a] >= kk[q]) {
+                                T x[V];
+                                vld<T, V>(Fk + (int64_t)ii[a] * V, x);
+#pragma unroll
+                                for (int v = 0; v < V; ++v) x[v] -= acc[a][q][v];
+                                vst<T, V>(Fk + (int64_t)ii[a] * V, x);
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    T* P0 = panel + (int64_t)b0 * panel_total + d.panel_off;
+    for (int jj = warp; jj < w; jj += nw) {
+        const T* Fj = F + (int64_t)(packed_col(jj, r) - jj) * V;
+        for (int i = lane; i < r; i += 32) {
+            T x[V];
+            if (i >= jj)
+                vld<T, V>(Fj + (int64_t)i * V, x);
+            else
+#pragma unroll
+                for (int v = 0; v < V; ++v) x[v] = T(0);
+#pragma unroll
+            for (int v = 0; v < V; ++v)
+                if (v < nv) P0[(int64_t)v * panel_total + (int64_t)jj * r + i] = x[v];
+        }
+    }
+    const int ru = r - w;
+    if (ru > 0) {
+        T* U0 = upd + (int64_t)b0 * upd_total + d.upd_off;
+        for (int kk = warp; kk < ru; kk += nw) {
+            const T* Fk = F + (int64_t)(packed_col(w + kk, r) - (w + kk)) * V;
+            for (int ii = kk + lane; ii < ru; ii += 32) {
+                T x[V];
+                vld<T, V>(Fk + (int64_t)(w + ii) * V, x);
+#pragma unroll
+                for (int v = 0; v < V; ++v)
+                    if (v < nv) U0[(int64_t)v * upd_total + (int64_t)kk * ru + ii] = x[v];
+            }
+        }
+    }
+}
+
 // --------------------------------------------------------------------------
 // a3': tiny subtrees.  Every front of the subtree has r <= 32 rows; one warp
 // factors the whole subtree, children first, with lane i holding row i of
@@ -1342,6 +1587,11 @@ int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cud
             Prof pr(P, s, SSCO_K_FRONT_SMALL);
             const int nw = ll.cls <= 32 ? 2 : (ll.cls <= 64 ? 4 : 8);
             const size_t smem = (size_t)ll.rmax * (ll.rmax + 1) / 2 * sizeof(T);
+            constexpr int V = sizeof(T) == 4 ? 4 : 2;
+            if (ll.cls <= 96 && B >= V)
+                k_front_vec<T, V><<<dim3(ll.count, (B + V - 1) / V), dim3(32, nw), smem * V, s>>>(
+                    P.dt, list, B, K, P.nnzK, panel, P.panel_total, upd, P.upd_total, bad, P.n_pats);
+            else
             k_front_small<T><<<dim3(ll.count, B), dim3(32, nw), smem, s>>>(P.dt, list, K, P.nnzK, panel,
                                                                            P.panel_total, upd, P.upd_total, bad,
                                                                            P.n_pats);
@@ -1616,6 +1866,7 @@ int allow_dynamic_smem(K kernel) {
 template <class T>
 int set_attr_T() {
     int e = allow_dynamic_smem(k_front_small<T>);
+    if (!e) e = allow_dynamic_smem(k_front_vec<T, sizeof(T) == 4 ? 4 : 2>);
     if (!e) e = allow_dynamic_smem(k_tiny_factor<T>);
     if (!e) e = allow_dynamic_smem(k_tiny_fwd<T>);
     if (!e) e = allow_dynamic_smem(k_tiny_bwd<T>);

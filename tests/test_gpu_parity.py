@@ -128,6 +128,24 @@ def test_batched_warp_per_item_solves(S, prec):
         assert err < (1e-12 if prec == "fp64" else 1e-8)
 
 
+@pytest.mark.parametrize("prec,B", [("fp64", 5), ("fp32", 7)])
+def test_instance_vectorized_fronts_ragged_batch(S, prec, B):
+    """Small fronts are factored V value sets per CTA (V = 2 FP64, 4 FP32);
+    a batch that is not a multiple of V leaves a partial group."""
+    p = P.trigrid_problem(24, batch=B, cfg=3)
+    precision = S.FP64 if prec == "fp64" else S.FP32_REFINE
+    pl, x, st, *_ = run(S, p, precision)
+    assert np.all(st["status"] == 0)
+    L = pl.export_L() if prec == "fp64" else None
+    for inst in range(B):
+        r, res, err = check_against_oracle(S, pl, p, x, st, inst, inst)
+        if L is not None:
+            Lc = r.S.Lcolptr
+            for j in range(0, p.n, 7):
+                a, b = Lc[j], Lc[j + 1]
+                assert np.linalg.norm(L[inst, a:b] - r.L[a:b]) <= 1e-12 * np.linalg.norm(r.L[a:b])
+
+
 def test_multi_pattern_uneven(S):
     probs = [P.trigrid_problem(s, 1, cfg=3, seed_offset=100 + k) for k, s in enumerate([5, 11, 17, 23, 30, 9])]
     pl, x, st, *_ = run(S, probs, S.FP32_REFINE, batch=1)
