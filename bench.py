@@ -48,29 +48,33 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="arap")
     ap.add_argument("--no-extras", action="store_true", help="only the timed FP32 region")
+    ap.add_argument("--batch", type=int, default=None,
+                    help="value sets of the main pattern (default: the workload's own; smaller only for profiling)")
     return ap.parse_args()
 
 
 # ---------------------------------------------------------------------------
 # workloads: list of (problem-or-list, batch) sharing one step
 # ---------------------------------------------------------------------------
-def make_workload(name: str, rank: int):
+def make_workload(name: str, rank: int, batch=None):
     if name == "arap":
-        a = P.trigrid_problem(128, batch=256, cfg=3, seed_offset=rank * 256)
+        nb = batch or 256
+        a = P.trigrid_problem(128, batch=nb, cfg=3, seed_offset=rank * 256)
         u = [P.trigrid_problem(s, 1, cfg=3, seed_offset=100_000 + rank * 64 + k)
              for k, s in enumerate(P.uneven_trigrid_sides(64))]
-        desc = {"workload": "arap128x256+uneven64", "patterns": 1 + 64, "batch": 256,
+        desc = {"workload": f"arap128x{nb}+uneven64", "patterns": 1 + 64, "batch": nb,
                 "n_main": a.n, "n_uneven_total": int(sum(q.n for q in u)),
                 "sides_uneven": [32, 256]}
-        return [(a, 256), (u, 1)], desc
+        return [(a, nb), (u, 1)], desc
     if name == "elast24":
         e = P.elasticity_problem(24, batch=1, cfg=2)
         if rank:
             e = _reseed_elast(e, rank)
         return [(e, 1)], {"workload": "elast24 (24^3 Kuhn tets, 46875 DOF)", "batch": 1, "n": e.n}
     if name == "elast48":
-        e = P.elasticity_problem(48, batch=16, cfg=5)
-        return [(e, 16)], {"workload": "elast48x16 (48^3 Kuhn tets, 352947 DOF)", "batch": 16, "n": e.n}
+        nb = batch or 16
+        e = P.elasticity_problem(48, batch=nb, cfg=5)
+        return [(e, nb)], {"workload": f"elast48x{nb} (48^3 Kuhn tets, 352947 DOF)", "batch": nb, "n": e.n}
     if name == "grid32":
         g = P.grid_problem(32, 32, batch=1, cfg=1)
         return [(g, 1)], {"workload": "grid32 (5-point, n=1024)", "batch": 1, "n": g.n}
@@ -177,7 +181,7 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-    work, desc = make_workload(args.workload, rank)
+    work, desc = make_workload(args.workload, rank, args.batch)
     units = units_of(work)
     stream = torch.cuda.current_stream()
 
@@ -420,7 +424,7 @@ def cpu_baseline(args, work):
 def run_reference(args, rank, world):
     if rank != 0:
         return None
-    work, desc = make_workload(args.workload, 0)
+    work, desc = make_workload(args.workload, 0, args.batch)
     if args.workload == "arap":
         items = oracle_sample(work, frac_main=16, n_uneven=4)
         sample = "16 ARAP instances + 4 uneven grids per step"
@@ -458,7 +462,7 @@ def main():
         if args.workload != "elast48":
             out["error_vs_oracle"] = {k: oracle_errors(v) for k, v in xc.items()}
         if not args.no_extras and world == 1:
-            work, _ = make_workload(args.workload, 0)
+            work, _ = make_workload(args.workload, 0, args.batch)
             out["cpu_baseline"] = cpu_baseline(args, work)
         print(json.dumps(out), flush=True)
 

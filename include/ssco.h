@@ -255,9 +255,9 @@ enum {
     SSCO_K_FRONT_SMALL = 1,  /* one-CTA front factorization in shared memory  */
     SSCO_K_BIG_INIT = 2,     /* big front: pull children's update matrices    */
     SSCO_K_BIG_KSCATTER = 3, /* big front: add K entries                      */
-    SSCO_K_BIG_GEMM = 4,     /* big front: left-looking block-column update   */
+    SSCO_K_BIG_GEMM = 4,     /* big front: right-looking trailing update       */
     SSCO_K_BIG_POTRF = 5,    /* big front: 32x32 diagonal block Cholesky      */
-    SSCO_K_BIG_SYRK = 6,     /* big front: update matrix -= L21 L21^T         */
+    SSCO_K_BIG_SYRK = 6,     /* (unused; kept for numbering)                  */
     SSCO_K_FWD = 7,          /* forward solve, one level                      */
     SSCO_K_BWD = 8,          /* backward solve, one level                     */
     SSCO_K_RESID = 9,        /* FP64 residual b - K x                         */
@@ -266,7 +266,8 @@ enum {
     SSCO_K_GRAD = 12,        /* adjoint reductions                            */
     SSCO_K_FRONT_TINY = 13,  /* warp-per-subtree factorization, tiny fronts   */
     SSCO_K_BIG_TRSM = 14,    /* big front: rows below the diagonal block      */
-    SSCO_K_COUNT = 15
+    SSCO_K_FRONT_VEC = 15,   /* small fronts, V value sets per CTA            */
+    SSCO_K_COUNT = 16
 };
 typedef struct {
     int32_t kind;

@@ -791,68 +791,6 @@ __global__ void __launch_bounds__(256) k_big_kscatter(const DevTables t, const i
     panel[(int64_t)b * panel_total + d.panel_off + kl[1]] += (T)K[(int64_t)b * nnzK + kl[0]];
 }
 
-// Left-looking block update of panel column block kb (nb = 32 columns):
-// P[c0:r, c0:c0+nbk] -= P[c0:r, 0:c0] * P[c0:c0+nbk, 0:c0]^T.
-// CTA tile 64 rows x 32 columns, 256 threads, 4x2 outputs per thread.
-template <class T>
-__global__ void __launch_bounds__(256) k_big_gemm(const DevTables t, const int32_t* __restrict__ list, int kb,
-                                                  T* __restrict__ panel, int64_t panel_total) {
-    const FrontDesc d = t.fronts[list[blockIdx.y]];
-    const int b = blockIdx.z;
-    const int r = d.r, w = d.w;
-    const int c0 = kb * 32;
-    if (c0 >= w) return;
-    const int nbk = min(32, w - c0);
-    const int row0 = c0 + blockIdx.x * 64;
-    if (row0 >= r) return;
-    T* Pb = panel + (int64_t)b * panel_total + d.panel_off;
-    __shared__ T As[16][64 + 1];
-    __shared__ T Bs[16][32 + 1];
-    const int tid = threadIdx.x;
-    const int tx = tid & 15, ty = tid >> 4;
-    T acc[4][2];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) acc[a][0] = acc[a][1] = T(0);
-    for (int k0 = 0; k0 < c0; k0 += 16) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int e = tid + q * 256;
-            const int mm = e & 63, kk = e >> 6;
-            const int row = row0 + mm, col = k0 + kk;
-            As[kk][mm] = (row < r && col < c0) ? Pb[(int64_t)col * r + row] : T(0);
-        }
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int e = tid + q * 256;
-            const int nn = e & 31, kk = e >> 5;
-            const int row = c0 + nn, col = k0 + kk;
-            Bs[kk][nn] = (nn < nbk && col < c0) ? Pb[(int64_t)col * r + row] : T(0);
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < 16; ++kk) {
-            T a[4], bv[2];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) a[q] = As[kk][tx * 4 + q];
-            bv[0] = Bs[kk][ty * 2];
-            bv[1] = Bs[kk][ty * 2 + 1];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                acc[q][0] += a[q] * bv[0];
-                acc[q][1] += a[q] * bv[1];
-            }
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-        for (int p = 0; p < 2; ++p) {
-            const int row = row0 + tx * 4 + q, cl = ty * 2 + p;
-            if (row < r && cl < nbk && row >= c0 + cl) Pb[(int64_t)(c0 + cl) * r + row] -= acc[q][p];
-        }
-}
-
 // Factor the 32x32 diagonal block of column block kb, one warp per front.
 // Its own launch: the triangular solve below must read the factored block,
 // and no CTA of one launch may overwrite what another CTA still has to load.
@@ -935,68 +873,80 @@ __global__ void __launch_bounds__(256) k_big_trsm(const DevTables t, const int32
         if (j < nbk) Pb[(int64_t)(c0 + j) * r + row] = x[j];
 }
 
-// Update matrix of a big front: U(lower) -= L21 L21^T, L21 = P[w:r, 0:w].
-// CTA tile 64x64 of U's lower triangle, 256 threads, 4x4 per thread.
+// Right-looking trailing update after column block kb of a big front:
+// F[i, j] -= sum_{l in block} L[i, c0+l] L[j, c0+l] for c1 <= j <= i < r,
+// where F's column j is the panel column j (j < w) or update-matrix column
+// j - w (j >= w).  CTA tile 64x64 of the trailing lower triangle, inner
+// dimension = the block's <= 32 columns, 256 threads, 4x4 per thread.
 template <class T>
-__global__ void __launch_bounds__(256) k_big_syrk(const DevTables t, const int32_t* __restrict__ list,
-                                                  const T* __restrict__ panel, int64_t panel_total,
-                                                  T* __restrict__ upd, int64_t upd_total) {
+__global__ void __launch_bounds__(256) k_big_update(const DevTables t, const int32_t* __restrict__ list, int kb,
+                                                    T* __restrict__ panel, int64_t panel_total,
+                                                    T* __restrict__ upd, int64_t upd_total) {
     const FrontDesc d = t.fronts[list[blockIdx.y]];
     const int b = blockIdx.z;
-    const int r = d.r, w = d.w, ru = r - w;
-    if (ru <= 0) return;
-    const int64_t nt = (ru + 63) / 64;
+    const int r = d.r, w = d.w;
+    const int c0 = kb * 32;
+    if (c0 >= w) return;
+    const int nbk = min(32, w - c0);
+    const int c1 = c0 + nbk;
+    const int m = r - c1;
+    if (m <= 0) return;
+    const int64_t nt = (m + 63) / 64;
     const int64_t tile = blockIdx.x;
     if (tile >= nt * (nt + 1) / 2) return;
     int64_t ti = (int64_t)((sqrt(8.0 * (double)tile + 1.0) - 1.0) * 0.5);
     while (ti * (ti + 1) / 2 > tile) --ti;
     while ((ti + 1) * (ti + 2) / 2 <= tile) ++ti;
     const int64_t tj = tile - ti * (ti + 1) / 2;
-    const T* Pb = panel + (int64_t)b * panel_total + d.panel_off;
+    T* Pb = panel + (int64_t)b * panel_total + d.panel_off;
     T* Ub = upd + (int64_t)b * upd_total + d.upd_off;
-    __shared__ T As[16][64 + 1];
-    __shared__ T Bs[16][64 + 1];
+    const int ru = r - w;
+    __shared__ T As[32][64 + 1];
+    __shared__ T Bs[32][64 + 1];
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
-    const int i0 = (int)ti * 64, j0 = (int)tj * 64;
+    const int i0 = c1 + (int)ti * 64, j0 = c1 + (int)tj * 64;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int e = tid + q * 256;
+        const int mm = e & 63, kk = e >> 6;
+        const int ra = i0 + mm, rb = j0 + mm;
+        As[kk][mm] = (ra < r && kk < nbk) ? Pb[(int64_t)(c0 + kk) * r + ra] : T(0);
+        Bs[kk][mm] = (rb < r && kk < nbk) ? Pb[(int64_t)(c0 + kk) * r + rb] : T(0);
+    }
+    __syncthreads();
     T acc[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int c = 0; c < 4; ++c) acc[a][c] = T(0);
-    for (int k0 = 0; k0 < w; k0 += 16) {
+#pragma unroll 8
+    for (int kk = 0; kk < 32; ++kk) {
+        T a[4], bv[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const int e = tid + q * 256;
-            const int mm = e & 63, kk = e >> 6;
-            const int col = k0 + kk;
-            const int ra = i0 + mm, rb = j0 + mm;
-            As[kk][mm] = (ra < ru && col < w) ? Pb[(int64_t)col * r + w + ra] : T(0);
-            Bs[kk][mm] = (rb < ru && col < w) ? Pb[(int64_t)col * r + w + rb] : T(0);
+            a[q] = As[kk][tx + 16 * q];
+            bv[q] = Bs[kk][ty + 16 * q];
         }
-        __syncthreads();
 #pragma unroll
-        for (int kk = 0; kk < 16; ++kk) {
-            T a[4], bv[4];
+        for (int q = 0; q < 4; ++q)
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                a[q] = As[kk][tx * 4 + q];
-                bv[q] = Bs[kk][ty * 4 + q];
-            }
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-#pragma unroll
-                for (int p = 0; p < 4; ++p) acc[q][p] += a[q] * bv[p];
-        }
-        __syncthreads();
+            for (int p = 0; p < 4; ++p) acc[q][p] += a[q] * bv[p];
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
+    for (int p = 0; p < 4; ++p) {
+        const int j = j0 + ty + 16 * p;
+        if (j >= r) continue;
 #pragma unroll
-        for (int p = 0; p < 4; ++p) {
-            const int i = i0 + tx * 4 + q, j = j0 + ty * 4 + p;
-            if (i < ru && j < ru && i >= j) Ub[(int64_t)j * ru + i] -= acc[q][p];
+        for (int q = 0; q < 4; ++q) {
+            const int i = i0 + tx + 16 * q;
+            if (i >= r || i < j) continue;
+            if (j < w)
+                Pb[(int64_t)j * r + i] -= acc[q][p];
+            else
+                Ub[(int64_t)(j - w) * ru + (i - w)] -= acc[q][p];
         }
+    }
 }
 
 // --------------------------------------------------------------------------
@@ -1016,7 +966,7 @@ __device__ __forceinline__ void stage_diag(T (*Ld)[33], T* dinv, const T* __rest
 }
 
 template <class T>
-__global__ void __launch_bounds__(256) k_fwd(const DevTables t, const int32_t* __restrict__ list,
+__global__ void __launch_bounds__(512) k_fwd(const DevTables t, const int32_t* __restrict__ list,
                                              const T* __restrict__ panel, int64_t panel_total,
                                              T* __restrict__ vec, int64_t n, T* __restrict__ pvec,
                                              int64_t pvec_total, const int32_t* __restrict__ active,
@@ -1063,10 +1013,17 @@ __global__ void __launch_bounds__(256) k_fwd(const DevTables t, const int32_t* _
         __syncthreads();
         if (jb + 32 < w) stage_diag(Ld[buf ^ 1], dinv[buf ^ 1], Pb, r, jb + 32, min(32, w - jb - 32), tid, nth);
         for (int i = jb + nbk + tid; i < r; i += nth) {
-            T s = T(0);
             const T* col = Pb + (int64_t)jb * r + i;
-            for (int j = 0; j < nbk; ++j) s += col[(int64_t)j * r] * yblk[j];
-            v[i] -= s;
+            T acc[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc[u] = T(0);
+            int j = 0;
+            for (; j + 7 < nbk; j += 8) {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) acc[u] += col[(int64_t)(j + u) * r] * yblk[j + u];
+            }
+            for (; j < nbk; ++j) acc[0] += col[(int64_t)j * r] * yblk[j];
+            v[i] -= ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
         }
         buf ^= 1;
         __syncthreads();
@@ -1076,7 +1033,7 @@ __global__ void __launch_bounds__(256) k_fwd(const DevTables t, const int32_t* _
 }
 
 template <class T>
-__global__ void __launch_bounds__(256) k_bwd(const DevTables t, const int32_t* __restrict__ list,
+__global__ void __launch_bounds__(512) k_bwd(const DevTables t, const int32_t* __restrict__ list,
                                              const T* __restrict__ panel, int64_t panel_total,
                                              T* __restrict__ vec, int64_t n, const int32_t* __restrict__ active,
                                              int32_t n_pats) {
@@ -1103,9 +1060,16 @@ __global__ void __launch_bounds__(256) k_bwd(const DevTables t, const int32_t* _
         stage_diag(Ld, dinv, Pb, r, jb, nbk, tid, nth);
         for (int c = warp; c < nbk; c += nw) {
             const T* col = Pb + (int64_t)(jb + c) * r;
-            T s = T(0);
-            for (int i = jb + nbk + lane; i < r; i += 32) s += col[i] * v[i];
-            s = warp_sum(s);
+            T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+            int i = jb + nbk + lane;
+            for (; i + 96 < r; i += 128) {
+                s0 += col[i] * v[i];
+                s1 += col[i + 32] * v[i + 32];
+                s2 += col[i + 64] * v[i + 64];
+                s3 += col[i + 96] * v[i + 96];
+            }
+            for (; i < r; i += 32) s0 += col[i] * v[i];
+            T s = warp_sum((s0 + s1) + (s2 + s3));
             if (lane == 0) dots[c] = s;
         }
         __syncthreads();
@@ -1584,11 +1548,12 @@ int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cud
     for (const LaunchList& ll : P.fact_launches) {
         const int32_t* list = P.dt.front_lists + ll.list_off;
         if (ll.cls > 0) {
-            Prof pr(P, s, SSCO_K_FRONT_SMALL);
+            constexpr int V = sizeof(T) == 4 ? 4 : 2;
+            const bool vec = ll.cls <= 96 && B >= V;
+            Prof pr(P, s, vec ? SSCO_K_FRONT_VEC : SSCO_K_FRONT_SMALL);
             const int nw = ll.cls <= 32 ? 2 : (ll.cls <= 64 ? 4 : 8);
             const size_t smem = (size_t)ll.rmax * (ll.rmax + 1) / 2 * sizeof(T);
-            constexpr int V = sizeof(T) == 4 ? 4 : 2;
-            if (ll.cls <= 96 && B >= V)
+            if (vec)
                 k_front_vec<T, V><<<dim3(ll.count, (B + V - 1) / V), dim3(32, nw), smem * V, s>>>(
                     P.dt, list, B, K, P.nnzK, panel, P.panel_total, upd, P.upd_total, bad, P.n_pats);
             else
@@ -1633,22 +1598,6 @@ int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cud
         const int nkb = (ll.wmax + 31) / 32;
         for (int kb = 0; kb < nkb; ++kb) {
             const int c0 = kb * 32;
-            if (kb > 0) {
-                Prof pr(P, s, SSCO_K_BIG_GEMM);
-                k_big_gemm<T><<<dim3(cdiv(ll.rmax - c0, 64), ll.count, B), 256, 0, s>>>(P.dt, list, kb, panel,
-                                                                                        P.panel_total);
-                if (pr.ev >= 0) {
-                    double fl = 0, by = 0;
-                    for (int32_t q = 0; q < ll.count; ++q) {
-                        const FrontDesc& d = P.fronts[P.front_lists[ll.list_off + q]];
-                        if (c0 >= d.w) continue;
-                        double nbk = std::min(32, d.w - c0), mrows = d.r - c0;
-                        fl += 2 * mrows * nbk * c0;
-                        by += (mrows * c0 + nbk * c0 + 2 * mrows * nbk) * P.tsize;
-                    }
-                    pr.done(fl * B, by * B);
-                }
-            }
             {
                 Prof pd(P, s, SSCO_K_BIG_POTRF);
                 k_big_potrf<T><<<dim3(ll.count, B), 32, 0, s>>>(P.dt, list, kb, panel, P.panel_total, bad, P.n_pats);
@@ -1678,21 +1627,28 @@ int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cud
                 }
                 pr.done(fl * B, by * B);
             }
-        }
-        if (ll.max_syrk_tiles > 0) {
-            Prof pr(P, s, SSCO_K_BIG_SYRK);
-            k_big_syrk<T><<<dim3((unsigned)ll.max_syrk_tiles, ll.count, B), 256, 0, s>>>(P.dt, list, panel,
-                                                                                        P.panel_total, upd,
-                                                                                        P.upd_total);
-            if (pr.ev >= 0) {
-                double fl = 0, by = 0;
-                for (int32_t q = 0; q < ll.count; ++q) {
-                    const FrontDesc& d = P.fronts[P.front_lists[ll.list_off + q]];
-                    double ru = d.r - d.w;
-                    fl += ru * (ru + 1) * d.w;
-                    by += (ru * d.w + ru * (ru + 1)) * P.tsize;
+            int64_t tiles = 0;
+            for (int32_t q = 0; q < ll.count; ++q) {
+                const FrontDesc& d = P.fronts[P.front_lists[ll.list_off + q]];
+                if (c0 >= d.w) continue;
+                const int64_t mt = (d.r - c0 - std::min(32, d.w - c0) + 63) / 64;
+                tiles = std::max(tiles, mt * (mt + 1) / 2);
+            }
+            if (tiles > 0) {
+                Prof pu(P, s, SSCO_K_BIG_GEMM);
+                k_big_update<T><<<dim3((unsigned)tiles, ll.count, B), 256, 0, s>>>(P.dt, list, kb, panel,
+                                                                                  P.panel_total, upd, P.upd_total);
+                if (pu.ev >= 0) {
+                    double fl = 0, by = 0;
+                    for (int32_t q = 0; q < ll.count; ++q) {
+                        const FrontDesc& d = P.fronts[P.front_lists[ll.list_off + q]];
+                        if (c0 >= d.w) continue;
+                        double nbk = std::min(32, d.w - c0), m = d.r - c0 - nbk;
+                        fl += m * (m + 1) * nbk;
+                        by += (m * (m + 1) + 2 * m * nbk) * P.tsize;
+                    }
+                    pu.done(fl * B, by * B);
                 }
-                pr.done(fl * B, by * B);
             }
         }
     }
@@ -1704,6 +1660,7 @@ int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cud
 inline bool use_warp_solve(const LaunchList& ll, int B) {
     return (int64_t)ll.count * B >= 8 * 152 && ll.rmax <= 1024;
 }
+inline int solve_threads(const LaunchList& ll) { return ll.rmax <= 128 ? 128 : (ll.rmax <= 512 ? 256 : 512); }
 
 template <class T>
 void run_trisolve(Plan& P, const int32_t* active, cudaStream_t s) {
@@ -1731,7 +1688,7 @@ void run_trisolve(Plan& P, const int32_t* active, cudaStream_t s) {
                                                                 ll.rmax, panel, P.panel_total, vecT, P.n, pvec,
                                                                 P.pvec_total, active, P.n_pats);
         } else
-        k_fwd<T><<<dim3(ll.count, B), ll.rmax <= 128 ? 128 : 256, smem, s>>>(P.dt, P.dt.front_lists + ll.list_off, panel, P.panel_total,
+        k_fwd<T><<<dim3(ll.count, B), solve_threads(ll), smem, s>>>(P.dt, P.dt.front_lists + ll.list_off, panel, P.panel_total,
                                                         vecT, P.n, pvec, P.pvec_total, active, P.n_pats);
         if (pr.ev >= 0) {
             Work w = work_solve(P, ll);
@@ -1748,7 +1705,7 @@ void run_trisolve(Plan& P, const int32_t* active, cudaStream_t s) {
                                                                 ll.rmax, panel, P.panel_total, vecT, P.n, active,
                                                                 P.n_pats);
         } else
-        k_bwd<T><<<dim3(ll.count, B), ll.rmax <= 128 ? 128 : 256, smem, s>>>(P.dt, P.dt.front_lists + ll.list_off, panel, P.panel_total,
+        k_bwd<T><<<dim3(ll.count, B), solve_threads(ll), smem, s>>>(P.dt, P.dt.front_lists + ll.list_off, panel, P.panel_total,
                                                         vecT, P.n, active, P.n_pats);
         if (pr.ev >= 0) {
             Work w = work_solve(P, ll);
@@ -1880,9 +1837,9 @@ int set_attr_T() {
 }  // namespace
 
 const char* kernel_kind_name(int kind) {
-    static const char* names[SSCO_K_COUNT] = {"assemble", "front_small", "big_init", "big_kscatter", "big_gemm",
+    static const char* names[SSCO_K_COUNT] = {"assemble", "front_small", "big_init", "big_kscatter", "big_update",
                                               "big_potrf", "big_syrk", "fwd_solve", "bwd_solve", "resid",
-                                              "check", "vector", "grad", "front_tiny", "big_trsm"};
+                                              "check", "vector", "grad", "front_tiny", "big_trsm", "front_vec"};
     return kind >= 0 && kind < SSCO_K_COUNT ? names[kind] : "unknown";
 }
 

@@ -33,8 +33,8 @@ EXPORTED_SYMBOLS = [
     "ssco_last_launch_count", "ssco_last_error", "ssco_status_string", "ssco_plan_save", "ssco_plan_load",
     "ssco_destroy", "ssco_profile_enable", "ssco_profile_read", "ssco_kernel_name", "ssco_solve_noalloc", "ssco_profile_trace",
 ]
-KERNEL_KINDS = ["assemble", "front_small", "big_init", "big_kscatter", "big_gemm", "big_potrf", "big_syrk",
-                "fwd_solve", "bwd_solve", "resid", "check", "vector", "grad", "front_tiny", "big_trsm"]
+KERNEL_KINDS = ["assemble", "front_small", "big_init", "big_kscatter", "big_update", "big_potrf", "big_syrk",
+                "fwd_solve", "bwd_solve", "resid", "check", "vector", "grad", "front_tiny", "big_trsm", "front_vec"]
 
 
 class SscoError(RuntimeError):
