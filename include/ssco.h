@@ -213,9 +213,19 @@ ssco_status ssco_export_L(ssco_plan plan, double* host_out, void* stream);
  * SSCO_EXPORT_K_ROWIND to the HOST array host_out, double [B][nnz_K]. */
 ssco_status ssco_export_K(ssco_plan plan, double* host_out, void* stream);
 
+/* ssco_numeric + ssco_solve as ONE CUDA graph: the refinement loop runs on
+ * the device as a conditional WHILE node (no host round trip per
+ * iteration).  The graph is captured (on library-owned streams) on the first
+ * call for this (vals, shift, b, x, workspace) tuple and replayed by later
+ * calls with the same pointers; new pointers or ssco_bind re-capture.  Call
+ * it outside any stream capture of your own.  Asynchronous on `stream`. */
+ssco_status ssco_graph_run(ssco_plan plan, const void* vals, int32_t vals_dtype, const double* shift, const double* b,
+                           double* x, void* stream);
+
 /* End-to-end call on HOST buffers: copies vals/shift/b to the device
- * (staging areas inside the workspace), runs numeric + solve, copies x back
- * and synchronizes.  Host arrays use the same layouts as above. */
+ * (staging areas inside the workspace), runs numeric + solve as the captured
+ * graph of ssco_graph_run, copies x back and synchronizes.  Host arrays use
+ * the same layouts as above. */
 ssco_status ssco_refactor_solve_host(ssco_plan plan, const void* vals, int32_t vals_dtype,
                                      const double* shift, const double* b, double* x, void* stream);
 

@@ -267,6 +267,7 @@ ssco_status ssco_bind(ssco_plan h, void* dev_tables, size_t tables_bytes, void* 
     if (e) return cuda_fail(h, e, "table upload");
     e = cudaStreamSynchronize(s);
     if (e) return cuda_fail(h, e, "table upload sync");
+    graph_release(P);
     P.d_tab = (uint8_t*)dev_tables;
     P.d_ws = (uint8_t*)dev_ws;
     set_dev_tables(P);
@@ -406,6 +407,20 @@ ssco_status ssco_export_K(ssco_plan h, double* out, void* stream) {
     return SSCO_OK;
 }
 
+ssco_status ssco_graph_run(ssco_plan h, const void* vals, int32_t vals_dtype, const double* shift, const double* b,
+                           double* x, void* stream) {
+    if (!h || !vals || !shift || !b || !x) return fail(h, SSCO_ERR_INVALID_ARG, "NULL argument");
+    if (vals_dtype != SSCO_VALS_F64 && vals_dtype != SSCO_VALS_F32)
+        return fail(h, SSCO_ERR_INVALID_ARG, "unknown vals dtype");
+    Plan& P = h->P;
+    if (!P.bound) return fail(h, SSCO_ERR_STATE, "ssco_bind has not been called");
+    if (b == x) return fail(h, SSCO_ERR_INVALID_ARG, "b and x alias");
+    int e = launch_graph_run(P, vals, vals_dtype, shift, b, x, stream);
+    if (e) return cuda_fail(h, e, "graph capture or launch");
+    P.factored = true;
+    return SSCO_OK;
+}
+
 ssco_status ssco_refactor_solve_host(ssco_plan h, const void* vals, int32_t vals_dtype, const double* shift,
                                      const double* b, double* x, void* stream) {
     if (!h || !vals || !shift || !b || !x) return fail(h, SSCO_ERR_INVALID_ARG, "NULL argument");
@@ -421,16 +436,10 @@ ssco_status ssco_refactor_solve_host(ssco_plan h, const void* vals, int32_t vals
     if (!e) e = cudaMemcpyAsync(P.d_ws + P.ws.st_shift, shift, sb, cudaMemcpyHostToDevice, s);
     if (!e) e = cudaMemcpyAsync(P.d_ws + P.ws.st_b, b, nb, cudaMemcpyHostToDevice, s);
     if (e) return cuda_fail(h, e, "host-to-device copy");
-    int64_t l0;
-    P.launches = 0;
-    e = launch_numeric(P, P.d_ws + P.ws.st_vals, vals_dtype, (const double*)(P.d_ws + P.ws.st_shift), stream);
-    if (e) return cuda_fail(h, e, "numeric launch");
+    e = launch_graph_run(P, P.d_ws + P.ws.st_vals, vals_dtype, (const double*)(P.d_ws + P.ws.st_shift),
+                         (const double*)(P.d_ws + P.ws.st_b), (double*)(P.d_ws + P.ws.st_x), stream);
+    if (e) return cuda_fail(h, e, "graph capture or launch");
     P.factored = true;
-    l0 = P.launches;
-    bool ok = true;
-    e = launch_solve(P, (const double*)(P.d_ws + P.ws.st_b), (double*)(P.d_ws + P.ws.st_x), stream, &ok);
-    if (e) return cuda_fail(h, e, "solve launch");
-    P.launches += l0;
     e = cudaMemcpyAsync(x, P.d_ws + P.ws.st_x, nb, cudaMemcpyDeviceToHost, s);
     if (!e) e = cudaStreamSynchronize(s);
     if (e) return cuda_fail(h, e, "device-to-host copy");
@@ -518,6 +527,8 @@ ssco_status ssco_plan_load(const char* path, ssco_plan* out) {
 void ssco_destroy(ssco_plan h) {
     if (!h) return;
     if (!h->P.ev_pool.empty()) profile_enable(h->P, 0);
+    graph_release(h->P);
+    graph_destroy_streams(h->P);
     if (h->P.h_flag) cudaFreeHost(h->P.h_flag);
     delete h;
 }

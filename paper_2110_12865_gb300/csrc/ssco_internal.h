@@ -107,7 +107,7 @@ struct DevTables {
 // Byte offsets of every region of the caller's workspace.
 struct WsLayout {
     size_t K, panel, upd, pvec, vecT, bp, xp, rr, mu, xbar_p;
-    size_t bad_col, sstatus, iters, active, any_active;
+    size_t bad_col, sstatus, iters, active, any_active, it_ctr;
     size_t resid, bnorm, r1, r2, sigma, sbar;
     size_t st_vals, st_shift, st_b, st_x;
     size_t total;
@@ -207,6 +207,15 @@ struct Plan {
     bool factored = false;
     int32_t* h_flag = nullptr;  // pinned host word for the refinement loop
 
+    // captured assemble + refactor + solve graph (ssco_graph_run)
+    void* g_stream = nullptr;
+    void* g_body_stream = nullptr;
+    void* g_graph = nullptr;
+    void* g_exec = nullptr;
+    const void* g_key[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    int32_t g_vdt = -1;
+    int64_t g_launches = 0;
+
     std::string last_error;
     int64_t launches = 0;
 
@@ -230,6 +239,10 @@ int launch_solve(Plan& P, const double* b, double* x, void* stream, bool* synced
 int launch_backward(Plan& P, const double* x, const double* xbar, double* vals_bar,
                     double* shift_bar, double* b_bar, void* stream);
 int launch_reset_status(Plan& P, void* stream);
+int launch_graph_run(Plan& P, const void* vals, int32_t vals_dtype, const double* shift, const double* b, double* x,
+                     void* stream);
+void graph_release(Plan& P);
+void graph_destroy_streams(Plan& P);
 int kernels_set_attributes(Plan& P);
 const char* kernel_kind_name(int kind);
 int profile_enable(Plan& P, int32_t max_launches);

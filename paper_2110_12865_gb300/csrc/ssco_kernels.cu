@@ -1296,9 +1296,11 @@ __global__ void k_check(const double* __restrict__ rr, const int64_t* __restrict
                         int64_t n, const double* __restrict__ bnorm, int32_t* __restrict__ active,
                         int32_t* __restrict__ sstatus, int32_t* __restrict__ iters, double* __restrict__ resid,
                         double* __restrict__ r1, double* __restrict__ r2, double* __restrict__ sigma,
-                        int32_t* __restrict__ any_active, int it, int maxit, double tol, int refine) {
+                        int32_t* __restrict__ any_active, int it, int maxit, double tol, int refine,
+                        const int32_t* __restrict__ it_dev) {
     const int s = blockIdx.x;
     if (!active[s]) return;
+    if (it_dev) it = *it_dev;
     const int b = s / n_pats, k = s % n_pats;
     const double* v = rr + (int64_t)b * n;
     double sum = 0.0, mx = 0.0;
@@ -1355,6 +1357,13 @@ __global__ void k_update(const T* __restrict__ vecT, const int32_t* __restrict__
     const int s = b * n_pats + row_sys[i];
     const int64_t o = (int64_t)b * n + i;
     if (active[s]) xp[o] += sigma[s] * (double)vecT[o];
+}
+
+// Sets the refinement loop's condition (any system still active) and counts
+// the corrections done; one thread.  Used inside a captured CUDA graph.
+__global__ void k_set_cond(cudaGraphConditionalHandle h, const int32_t* __restrict__ anyp, int32_t* __restrict__ it_ctr) {
+    cudaGraphSetConditional(h, *anyp > 0 ? 1u : 0u);
+    *it_ctr += 1;
 }
 
 // --------------------------------------------------------------------------
@@ -1723,9 +1732,15 @@ void run_trisolve(Plan& P, const int32_t* active, cudaStream_t s) {
     }
 }
 
+// While capturing a graph: the refinement loop becomes a conditional WHILE
+// node whose body is captured on body_stream.
+struct GraphLoop {
+    cudaStream_t body_stream;
+};
+
 // x = K^-1 b for all systems (b, x device, original ordering)
 template <class T>
-int run_solve(Plan& P, const double* b, double* x, cudaStream_t s) {
+int run_solve(Plan& P, const double* b, double* x, cudaStream_t s, GraphLoop* gl = nullptr) {
     const int B = P.B;
     const int64_t n = P.n, S = (int64_t)B * P.n_pats;
     double* bp = wsp<double>(P, P.ws.bp);
@@ -1768,6 +1783,77 @@ int run_solve(Plan& P, const double* b, double* x, cudaStream_t s) {
         k_from_T<T><<<cdiv((int64_t)B * n, 256), 256, 0, s>>>(vecT, xp, (int64_t)B * n);
         pr.done(0, nB * (8 + sizeof(T)));
     }
+    int32_t* it_ctr = wsp<int32_t>(P, P.ws.it_ctr);
+    if (gl) {
+        // device-side loop: prologue check, then WHILE(any active) { correct; check }
+        cudaMemsetAsync(it_ctr, 0, 4, s);
+        const int32_t* it_dev = it_ctr;
+        auto check_step = [&](cudaStream_t st) {
+            {
+                Prof pr(P, st, SSCO_K_RESID);
+                k_resid<<<gv, 256, 0, st>>>(P.dt.sp_rowptr, P.dt.sp_col, P.dt.sp_slot, K, P.nnzK, bp, xp, rr, n);
+                pr.done(0, 0);
+            }
+            cudaMemsetAsync(anyp, 0, 4, st);
+            Prof pc(P, st, SSCO_K_CHECK);
+            k_check<<<(unsigned)S, 256, 0, st>>>(rr, P.dt.sys_n_off, P.n_pats, n, bnorm, active, sst, iters, resid, r1,
+                                                 r2, sigma, anyp, 0, P.maxit, P.tol, refine, it_dev);
+            pc.done(0, 0);
+        };
+        check_step(s);
+        if (refine) {
+            cudaStreamCaptureStatus cst;
+            cudaGraph_t cg = nullptr;
+            const cudaGraphNode_t* deps = nullptr;
+            const cudaGraphEdgeData* edata = nullptr;
+            size_t ndeps = 0;
+            int e = (int)cudaStreamGetCaptureInfo(s, &cst, nullptr, &cg, &deps, &edata, &ndeps);
+            if (e) return e;
+            cudaGraphConditionalHandle h;
+            e = (int)cudaGraphConditionalHandleCreate(&h, cg, 0, cudaGraphCondAssignDefault);
+            if (e) return e;
+            k_set_cond<<<1, 1, 0, s>>>(h, anyp, it_ctr);
+            P.launches++;
+            e = (int)cudaStreamGetCaptureInfo(s, &cst, nullptr, &cg, &deps, &edata, &ndeps);
+            if (e) return e;
+            cudaGraphNodeParams cp = {};
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = h;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            cudaGraphNode_t cnode;
+            e = (int)cudaGraphAddNode(&cnode, cg, deps, edata, ndeps, &cp);
+            if (e) return e;
+            e = (int)cudaStreamUpdateCaptureDependencies(s, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+            if (e) return e;
+            cudaGraph_t body = cp.conditional.phGraph_out[0];
+            cudaStream_t bs = gl->body_stream;
+            e = (int)cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+            if (e) return e;
+            {
+                Prof pr(P, bs, SSCO_K_VECTOR);
+                k_cast_scaled<T><<<gv, 256, 0, bs>>>(rr, P.dt.row_sys, P.n_pats, n, active, sigma, vecT);
+                pr.done(0, 0);
+            }
+            run_trisolve<T>(P, active, bs);
+            {
+                Prof pr(P, bs, SSCO_K_VECTOR);
+                k_update<T><<<gv, 256, 0, bs>>>(vecT, P.dt.row_sys, P.n_pats, n, active, sigma, xp);
+                pr.done(0, 0);
+            }
+            check_step(bs);
+            k_set_cond<<<1, 1, 0, bs>>>(h, anyp, it_ctr);
+            P.launches++;
+            cudaGraph_t body_out = nullptr;
+            e = (int)cudaStreamEndCapture(bs, &body_out);
+            if (e) return e;
+        }
+        Prof pr(P, s, SSCO_K_VECTOR);
+        k_permute_out<<<gv, 256, 0, s>>>(xp, P.dt.perm, n, x);
+        pr.done(0, nB * 20);
+        return (int)cudaGetLastError();
+    }
+    const int32_t* it_dev = nullptr;
     for (int it = 0;; ++it) {
         {
             Prof pr(P, s, SSCO_K_RESID);
@@ -1778,7 +1864,7 @@ int run_solve(Plan& P, const double* b, double* x, cudaStream_t s) {
         {
             Prof pr(P, s, SSCO_K_CHECK);
             k_check<<<(unsigned)S, 256, 0, s>>>(rr, P.dt.sys_n_off, P.n_pats, n, bnorm, active, sst, iters, resid, r1,
-                                                r2, sigma, anyp, it, P.maxit, P.tol, refine);
+                                                r2, sigma, anyp, it, P.maxit, P.tol, refine, it_dev);
             pr.done(2 * nB, nB * 8);
         }
         if (!refine) break;
@@ -1868,6 +1954,76 @@ int launch_solve(Plan& P, const double* b, double* x, void* stream, bool* ok) {
     cudaStream_t s = (cudaStream_t)stream;
     *ok = true;
     return P.tsize == 8 ? run_solve<double>(P, b, x, s) : run_solve<float>(P, b, x, s);
+}
+
+// Assemble + refactor + solve as one CUDA graph (refinement loop on the
+// device), captured on first use for these pointers and replayed afterwards.
+template <class T>
+int build_graph(Plan& P, const void* vals, int32_t vdt, const double* shift, const double* b, double* x) {
+    if (!P.g_stream) {
+        int e = (int)cudaStreamCreateWithFlags((cudaStream_t*)&P.g_stream, cudaStreamNonBlocking);
+        if (!e) e = (int)cudaStreamCreateWithFlags((cudaStream_t*)&P.g_body_stream, cudaStreamNonBlocking);
+        if (e) return e;
+    }
+    cudaStream_t cs = (cudaStream_t)P.g_stream;
+    const bool prof = P.prof;
+    P.prof = false;
+    P.launches = 0;
+    int e = (int)cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e) {
+        P.prof = prof;
+        return e;
+    }
+    GraphLoop gl{(cudaStream_t)P.g_body_stream};
+    int e1 = run_numeric<T>(P, vals, vdt, shift, cs);
+    int e2 = e1 ? e1 : run_solve<T>(P, b, x, cs, &gl);
+    cudaGraph_t g = nullptr;
+    int e3 = (int)cudaStreamEndCapture(cs, &g);
+    P.prof = prof;
+    if (e2 || e3) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return e2 ? e2 : e3;
+    }
+    cudaGraphExec_t ge = nullptr;
+    e = (int)cudaGraphInstantiate(&ge, g, 0);
+    if (e) {
+        cudaGraphDestroy(g);
+        return e;
+    }
+    P.g_graph = (void*)g;
+    P.g_exec = (void*)ge;
+    P.g_launches = P.launches;
+    return 0;
+}
+
+void graph_release(Plan& P) {
+    if (P.g_exec) cudaGraphExecDestroy((cudaGraphExec_t)P.g_exec);
+    if (P.g_graph) cudaGraphDestroy((cudaGraph_t)P.g_graph);
+    P.g_exec = P.g_graph = nullptr;
+}
+
+void graph_destroy_streams(Plan& P) {
+    if (P.g_stream) cudaStreamDestroy((cudaStream_t)P.g_stream);
+    if (P.g_body_stream) cudaStreamDestroy((cudaStream_t)P.g_body_stream);
+    P.g_stream = P.g_body_stream = nullptr;
+}
+
+int launch_graph_run(Plan& P, const void* vals, int32_t vdt, const double* shift, const double* b, double* x,
+                     void* stream) {
+    const void* key[5] = {vals, shift, b, x, P.d_ws};
+    bool same = P.g_exec && P.g_vdt == vdt;
+    for (int i = 0; i < 5 && same; ++i) same = P.g_key[i] == key[i];
+    if (!same) {
+        graph_release(P);
+        int e = P.tsize == 8 ? build_graph<double>(P, vals, vdt, shift, b, x)
+                             : build_graph<float>(P, vals, vdt, shift, b, x);
+        if (e) return e;
+        for (int i = 0; i < 5; ++i) P.g_key[i] = key[i];
+        P.g_vdt = vdt;
+    }
+    P.launches = P.g_launches;
+    return (int)cudaGraphLaunch((cudaGraphExec_t)P.g_exec, (cudaStream_t)stream);
 }
 
 int launch_backward(Plan& P, const double* x, const double* xbar, double* vals_bar, double* shift_bar,

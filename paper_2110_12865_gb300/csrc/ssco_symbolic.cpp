@@ -947,6 +947,7 @@ void compute_ws_layout(Plan& P) {
     w.iters = take(S * 4);
     w.active = take(S * 4);
     w.any_active = take(4);
+    w.it_ctr = take(4);
     w.resid = take(S * 8);
     w.bnorm = take(S * 8);
     w.r1 = take(S * 8);

@@ -31,7 +31,7 @@ EXPORTED_SYMBOLS = [
     "ssco_analyze", "ssco_plan_info", "ssco_plan_export", "ssco_bind", "ssco_numeric", "ssco_solve",
     "ssco_backward", "ssco_status_get", "ssco_export_L", "ssco_export_K", "ssco_refactor_solve_host",
     "ssco_last_launch_count", "ssco_last_error", "ssco_status_string", "ssco_plan_save", "ssco_plan_load",
-    "ssco_destroy", "ssco_profile_enable", "ssco_profile_read", "ssco_kernel_name", "ssco_solve_noalloc", "ssco_profile_trace",
+    "ssco_destroy", "ssco_profile_enable", "ssco_profile_read", "ssco_kernel_name", "ssco_solve_noalloc", "ssco_profile_trace", "ssco_graph_run",
 ]
 KERNEL_KINDS = ["assemble", "front_small", "big_init", "big_kscatter", "big_update", "big_potrf", "big_syrk",
                 "fwd_solve", "bwd_solve", "resid", "check", "vector", "grad", "front_tiny", "big_trsm", "front_vec"]
@@ -107,6 +107,7 @@ def load_library(path: str = LIB_PATH):
         "ssco_kernel_name": (C.c_char_p, [i32]),
         "ssco_solve_noalloc": (i32, [vp, vp, vp, vp]),
         "ssco_profile_trace": (i32, [vp, vp, vp, vp, vp, i64, C.POINTER(i64)]),
+        "ssco_graph_run": (i32, [vp, vp, i32, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -273,6 +274,14 @@ class Plan:
         assert b.is_cuda and b.dtype == torch.float64 and b.is_contiguous()
         assert x.is_cuda and x.dtype == torch.float64 and x.is_contiguous()
         self._check(self.L.ssco_solve_noalloc(self._h, _ptr(b), _ptr(x), _stream_ptr(stream)))
+        return x
+
+    def graph_run(self, vals: torch.Tensor, shift: torch.Tensor, b: torch.Tensor, x: torch.Tensor, stream=None):
+        """numeric + solve as one captured CUDA graph (re-captured when the
+        pointers change)."""
+        dt = VALS_F64 if vals.dtype == torch.float64 else VALS_F32
+        self._check(self.L.ssco_graph_run(self._h, _ptr(vals), dt, _ptr(shift), _ptr(b), _ptr(x),
+                                          _stream_ptr(stream)))
         return x
 
     def backward(self, x, xbar, stream=None, want_shift=True):

@@ -219,6 +219,39 @@ def test_deterministic_and_host_e2e(S):
     assert pl.last_launch_count() > 0
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_graph_run_matches_eager(S, prec):
+    """ssco_graph_run (numeric + solve captured once, refinement loop as a
+    conditional WHILE node) gives bit-identical results to the eager calls,
+    replays correctly, and re-captures when the pointers change."""
+    probs = [P.trigrid_problem(20, batch=3, cfg=3), P.grid_problem(9, 7, batch=3, cfg=1)]
+    precision = S.FP64 if prec == "fp64" else S.FP32_REFINE
+    pl, x_eager, st_e, vals, shift, b = run(S, probs, precision, batch=3)
+    v = torch.tensor(vals, device="cuda")
+    sh = torch.tensor(shift, device="cuda")
+    bt = torch.tensor(b, device="cuda")
+    x = torch.empty_like(bt)
+    for _ in range(3):
+        x.fill_(float("nan"))
+        pl.graph_run(v, sh, bt, x)
+        assert np.array_equal(x.cpu().numpy(), x_eager)
+    st = pl.status()
+    assert np.array_equal(st["iters"], st_e["iters"]) and np.all(st["status"] == 0)
+    # new right-hand side in a new buffer: re-capture
+    b2 = torch.tensor(np.random.default_rng(5).standard_normal(b.shape), device="cuda")
+    x2 = torch.empty_like(b2)
+    pl.graph_run(v, sh, b2, x2)
+    ref = pl.solve(b2)
+    assert np.array_equal(x2.cpu().numpy(), ref.cpu().numpy())
+    off = 0
+    xh = x2.cpu().numpy()
+    for k, p in enumerate(probs):
+        K = O.assemble(p, 1)
+        res = np.linalg.norm(O.symv(K, xh[1, off:off + p.n]) - b2.cpu().numpy()[1, off:off + p.n])
+        assert res <= RESID_TOL * np.linalg.norm(b2.cpu().numpy()[1, off:off + p.n])
+        off += p.n
+
+
 def test_plan_file_roundtrip_runs(S, tmp_path):
     p = P.elasticity_problem(4, cfg=2)
     pl0 = S.Plan(p, precision=S.FP32_REFINE)
