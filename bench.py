@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="arap")
     ap.add_argument("--no-extras", action="store_true", help="only the timed FP32 region")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="skip ssco_autotune of the launch shapes before timing")
     ap.add_argument("--batch", type=int, default=None,
                     help="value sets of the main pattern (default: the workload's own; smaller only for profiling)")
     return ap.parse_args()
@@ -75,6 +77,9 @@ def make_workload(name: str, rank: int, batch=None):
         nb = batch or 16
         e = P.elasticity_problem(48, batch=nb, cfg=5)
         return [(e, nb)], {"workload": f"elast48x{nb} (48^3 Kuhn tets, 352947 DOF)", "batch": nb, "n": e.n}
+    if name == "tiny":
+        a = P.trigrid_problem(12, batch=batch or 3, cfg=3, seed_offset=rank * 256)
+        return [(a, batch or 3)], {"workload": "trigrid12 (test size)", "batch": batch or 3, "n": a.n}
     if name == "grid32":
         g = P.grid_problem(32, 32, batch=1, cfg=1)
         return [(g, 1)], {"workload": "grid32 (5-point, n=1024)", "batch": 1, "n": g.n}
@@ -161,6 +166,19 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
+def aggregate_value(units, steps, local_ms, dist=None, device="cpu"):
+    """Whole-job throughput of a weak-scaled run: every rank processes
+    `units` systems per step; the job takes as long as the slowest rank."""
+    import torch
+    world = 1
+    if dist is not None and dist.is_initialized():
+        world = dist.get_world_size()
+        t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        local_ms = float(t.item())
+    return units * world * steps / (local_ms / 1e3), local_ms
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -192,11 +210,16 @@ def run_ours(args, rank, world, local_rank):
             v, s, b = stacked_inputs(item, Bt)
             dev_in.append((torch.tensor(v, device=dev), torch.tensor(s, device=dev), torch.tensor(b, device=dev),
                            torch.empty(b.shape, dtype=torch.float64, device=dev)))
+            if args.autotune and args.workload != "elast48":
+                # launch shapes chosen on this plan's data before the timed region
+                ms, knobs = pl.autotune(*dev_in[-1], reps=3)
+                tuned.append(knobs)
             host_in.append((torch.tensor(v).pin_memory(), torch.tensor(s).pin_memory(), torch.tensor(b).pin_memory(),
                             torch.empty(b.shape, dtype=torch.float64).pin_memory()))
             plans.append(pl)
         return plans, dev_in, host_in
 
+    tuned = []
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
 
     def eager_step(plans, dev_in):
@@ -259,12 +282,7 @@ def run_ours(args, rank, world, local_rank):
     sampler = ClockSampler(local_rank)
     ms, launches, wall, clocks = timed(plans32, dev32, args.steps, args.warmup, sampler)
     ok32, res32, its32 = status_summary(plans32)
-    tot_ms = sum(ms)
-    if dist:
-        t = torch.tensor([tot_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    value = units * world * args.steps / (tot_ms / 1e3)
+    value, tot_ms = aggregate_value(units, args.steps, sum(ms), dist, dev)
 
     out = {
         "metric": "batched refactor+solve/s (FP32 factor + FP64 refinement to rel. residual 1e-10)",
@@ -282,6 +300,7 @@ def run_ours(args, rank, world, local_rank):
     }
     if clocks:
         out["clocks"] = clocks
+    out["config"]["autotuned"] = tuned if args.autotune else None
     xs32 = _pick_samples(work, dev32)
     if args.no_extras:
         out["_xcheck"] = {"fp32": xs32}
@@ -347,6 +366,11 @@ def run_ours(args, rank, world, local_rank):
     # ---- the plain FP64 GPU form on the same work -------------------------
     del plans32, dev32, host32
     torch.cuda.empty_cache()
+    if args.workload == "elast48":
+        # the FP64 factor and update matrices of 16 value sets exceed HBM
+        out["fp64"] = {"skipped": "FP64 workspace of 16 x 48^3 exceeds device memory"}
+        out["_xcheck"] = {"fp32": xs32}
+        return out, rank
     plans64, dev64, _ = setup(S.FP64)
     k64 = max(3, args.steps // 2)
     ms64, _, _, _ = timed(plans64, dev64, k64, 2)

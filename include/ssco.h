@@ -131,6 +131,10 @@ typedef struct {
     int64_t workspace_bytes; /* device workspace size                        */
     double factor_flops;     /* sum_j c_j^2 over the numeric partition       */
     double factor_flops_exact; /* sum_j c_j^2 over the exact structure       */
+    int64_t tune_warp_items; /* launch-shape knobs (see ssco_autotune)       */
+    int64_t tune_vec_max_cls;
+    int64_t tune_solve_threads_big;
+    int64_t tuned;           /* 1 after a successful ssco_autotune           */
 } ssco_info;
 
 /* ssco_plan_export selectors (host copies; sizes in elements).          */
@@ -212,6 +216,17 @@ ssco_status ssco_export_L(ssco_plan plan, double* host_out, void* stream);
 /* Synchronizes `stream`, then writes K~ in the CSC order of
  * SSCO_EXPORT_K_ROWIND to the HOST array host_out, double [B][nnz_K]. */
 ssco_status ssco_export_K(ssco_plan plan, double* host_out, void* stream);
+
+/* Autotuner of the launch shapes of the level groups: for each knob (the
+ * item count from which a solve level runs warp-per-(front, instance), the
+ * largest front size class factored several value sets per CTA, the CTA size
+ * of solve levels with wide fronts) every candidate is timed on the caller's
+ * data (median of `reps` numeric + solve steps, CUDA events) and the fastest
+ * is kept in the plan (saved by ssco_plan_save).  Synchronizes `stream`;
+ * leaves a valid factor and solution (x) behind.  *best_ms (may be NULL)
+ * receives the best step time. */
+ssco_status ssco_autotune(ssco_plan plan, const void* vals, int32_t vals_dtype, const double* shift, const double* b,
+                          double* x, int32_t reps, void* stream, double* best_ms);
 
 /* ssco_numeric + ssco_solve as ONE CUDA graph: the refinement loop runs on
  * the device as a conditional WHILE node (no host round trip per

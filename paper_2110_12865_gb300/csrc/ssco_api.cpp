@@ -76,7 +76,7 @@ void set_dev_tables(Plan& P) {
 
 // ----- plan file (de)serialization -----------------------------------------
 constexpr uint64_t kMagic = 0x314F4353534F4353ull;  // "SCOSSCO1"
-constexpr uint32_t kVersion = 3;
+constexpr uint32_t kVersion = 4;
 
 struct Writer {
     std::ofstream f;
@@ -126,6 +126,7 @@ bool serialize(IO& io, Plan& P) {
     S(P.n_levels); S(P.panel_total); S(P.upd_total); S(P.pvec_total); S(P.max_rows);
     V(P.tiny_list); V(P.tiny_off); S(P.n_tiny);
     V(P.tiny_prog); V(P.tiny_prog_off); S(P.tiny_prog_max); S(P.tiny_k_max);
+    S(P.tune);
     V(P.groups); V(P.chunks); V(P.asm_idx); V(P.asm_coef);
     V(P.sp_rowptr); V(P.sp_col); V(P.sp_slot); V(P.row_sys); V(P.sys_n_off); V(P.shifted);
     V(P.g_rowptr); V(P.g_colind); V(P.g_row_sys); V(P.g_rows_all); V(P.g_aval);
@@ -201,6 +202,10 @@ ssco_status ssco_plan_info(ssco_plan h, ssco_info* o) {
     o->workspace_bytes = (int64_t)P.ws.total;
     o->factor_flops = P.flops_numeric;
     o->factor_flops_exact = P.flops_exact;
+    o->tune_warp_items = P.tune.warp_items;
+    o->tune_vec_max_cls = P.tune.vec_max_cls;
+    o->tune_solve_threads_big = P.tune.solve_threads_big;
+    o->tuned = P.tune.tuned;
     return SSCO_OK;
 }
 
@@ -404,6 +409,17 @@ ssco_status ssco_export_K(ssco_plan h, double* out, void* stream) {
     for (int32_t b = 0; b < P.B; ++b)
         for (int64_t q = 0; q < P.nnzK; ++q)
             out[(int64_t)b * P.nnzK + q] = host[(int64_t)b * P.nnzK + P.kslot_of_q[q]];
+    return SSCO_OK;
+}
+
+ssco_status ssco_autotune(ssco_plan h, const void* vals, int32_t vals_dtype, const double* shift, const double* b,
+                          double* x, int32_t reps, void* stream, double* best_ms) {
+    if (!h || !vals || !shift || !b || !x || reps < 1) return fail(h, SSCO_ERR_INVALID_ARG, "bad argument");
+    Plan& P = h->P;
+    if (!P.bound) return fail(h, SSCO_ERR_STATE, "ssco_bind has not been called");
+    int e = autotune(P, vals, vals_dtype, shift, b, x, reps, stream, best_ms);
+    if (e) return cuda_fail(h, e, "autotune");
+    P.factored = true;
     return SSCO_OK;
 }
 

@@ -121,6 +121,14 @@ struct ProfRec {
     double flops, bytes;
 };
 
+// Launch-shape knobs chosen by ssco_autotune (defaults are the untuned ones).
+struct Tunables {
+    int32_t warp_items = 8 * 152;  // a solve level goes warp-per-item at >= this many items
+    int32_t vec_max_cls = 96;      // largest size class factored V value sets per CTA
+    int32_t solve_threads_big = 512;  // CTA size of solve levels with fronts > 512 rows
+    int32_t tuned = 0;
+};
+
 struct PatMeta {
     int32_t kind, n, m, dim;
     int64_t n_off, m_off;
@@ -136,6 +144,7 @@ struct Plan {
     int32_t amalg = 1;
     int32_t tiny_max = 32;
     size_t tsize = 8;  // bytes of the factor type
+    Tunables tune;
 
     int32_t n_pats = 0;
     std::vector<PatMeta> pats;
@@ -242,6 +251,8 @@ int launch_reset_status(Plan& P, void* stream);
 int launch_graph_run(Plan& P, const void* vals, int32_t vals_dtype, const double* shift, const double* b, double* x,
                      void* stream);
 void graph_release(Plan& P);
+int autotune(Plan& P, const void* vals, int32_t vals_dtype, const double* shift, const double* b, double* x,
+             int32_t reps, void* stream, double* best_ms);
 void graph_destroy_streams(Plan& P);
 int kernels_set_attributes(Plan& P);
 const char* kernel_kind_name(int kind);

@@ -21,7 +21,9 @@
 
 #include <climits>
 #include <cmath>
+#include <algorithm>
 #include <cstdint>
+#include <vector>
 
 #include "ssco_internal.h"
 
@@ -1558,7 +1560,7 @@ int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cud
         const int32_t* list = P.dt.front_lists + ll.list_off;
         if (ll.cls > 0) {
             constexpr int V = sizeof(T) == 4 ? 4 : 2;
-            const bool vec = ll.cls <= 96 && B >= V;
+            const bool vec = ll.cls <= P.tune.vec_max_cls && B >= V;
             Prof pr(P, s, vec ? SSCO_K_FRONT_VEC : SSCO_K_FRONT_SMALL);
             const int nw = ll.cls <= 32 ? 2 : (ll.cls <= 64 ? 4 : 8);
             const size_t smem = (size_t)ll.rmax * (ll.rmax + 1) / 2 * sizeof(T);
@@ -1666,10 +1668,12 @@ int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cud
 
 // A level is solved warp-per-item when it supplies at least 8 warps per SM
 // and its fronts' vectors fit 8 to a CTA; otherwise one CTA per item.
-inline bool use_warp_solve(const LaunchList& ll, int B) {
-    return (int64_t)ll.count * B >= 8 * 152 && ll.rmax <= 1024;
+inline bool use_warp_solve(const Plan& P, const LaunchList& ll, int B) {
+    return (int64_t)ll.count * B >= P.tune.warp_items && ll.rmax <= 1024;
 }
-inline int solve_threads(const LaunchList& ll) { return ll.rmax <= 128 ? 128 : (ll.rmax <= 512 ? 256 : 512); }
+inline int solve_threads(const Plan& P, const LaunchList& ll) {
+    return ll.rmax <= 128 ? 128 : (ll.rmax <= 512 ? 256 : P.tune.solve_threads_big);
+}
 
 template <class T>
 void run_trisolve(Plan& P, const int32_t* active, cudaStream_t s) {
@@ -1691,13 +1695,13 @@ void run_trisolve(Plan& P, const int32_t* active, cudaStream_t s) {
     for (const LaunchList& ll : P.solve_launches) {
         Prof pr(P, s, SSCO_K_FWD);
         const size_t smem = (size_t)ll.rmax * sizeof(T);
-        if (use_warp_solve(ll, B)) {
+        if (use_warp_solve(P, ll, B)) {
             const int64_t items = (int64_t)ll.count * B;
             k_fwd_warp<T><<<cdiv(items, 8), 256, 8 * smem, s>>>(P.dt, P.dt.front_lists + ll.list_off, ll.count, B,
                                                                 ll.rmax, panel, P.panel_total, vecT, P.n, pvec,
                                                                 P.pvec_total, active, P.n_pats);
         } else
-        k_fwd<T><<<dim3(ll.count, B), solve_threads(ll), smem, s>>>(P.dt, P.dt.front_lists + ll.list_off, panel, P.panel_total,
+        k_fwd<T><<<dim3(ll.count, B), solve_threads(P, ll), smem, s>>>(P.dt, P.dt.front_lists + ll.list_off, panel, P.panel_total,
                                                         vecT, P.n, pvec, P.pvec_total, active, P.n_pats);
         if (pr.ev >= 0) {
             Work w = work_solve(P, ll);
@@ -1708,13 +1712,13 @@ void run_trisolve(Plan& P, const int32_t* active, cudaStream_t s) {
         const LaunchList& ll = *it;
         Prof pr(P, s, SSCO_K_BWD);
         const size_t smem = (size_t)ll.rmax * sizeof(T);
-        if (use_warp_solve(ll, B)) {
+        if (use_warp_solve(P, ll, B)) {
             const int64_t items = (int64_t)ll.count * B;
             k_bwd_warp<T><<<cdiv(items, 8), 256, 8 * smem, s>>>(P.dt, P.dt.front_lists + ll.list_off, ll.count, B,
                                                                 ll.rmax, panel, P.panel_total, vecT, P.n, active,
                                                                 P.n_pats);
         } else
-        k_bwd<T><<<dim3(ll.count, B), solve_threads(ll), smem, s>>>(P.dt, P.dt.front_lists + ll.list_off, panel, P.panel_total,
+        k_bwd<T><<<dim3(ll.count, B), solve_threads(P, ll), smem, s>>>(P.dt, P.dt.front_lists + ll.list_off, panel, P.panel_total,
                                                         vecT, P.n, active, P.n_pats);
         if (pr.ev >= 0) {
             Work w = work_solve(P, ll);
@@ -2024,6 +2028,73 @@ int launch_graph_run(Plan& P, const void* vals, int32_t vdt, const double* shift
     }
     P.launches = P.g_launches;
     return (int)cudaGraphLaunch((cudaGraphExec_t)P.g_exec, (cudaStream_t)stream);
+}
+
+// Coordinate descent over the launch-shape knobs: each candidate is timed
+// (CUDA events, median of `reps` eager numeric + solve steps after one
+// warm-up) on the caller's data; the fastest setting of each knob is kept.
+int autotune(Plan& P, const void* vals, int32_t vdt, const double* shift, const double* b, double* x, int32_t reps,
+             void* stream, double* best_ms) {
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    int e = (int)cudaEventCreate(&e0);
+    if (!e) e = (int)cudaEventCreate(&e1);
+    if (e) return e;
+    const bool prof = P.prof;
+    P.prof = false;
+    auto measure = [&](double* ms_out) -> int {
+        std::vector<float> t;
+        for (int i = 0; i <= reps; ++i) {
+            int r = (int)cudaEventRecord(e0, s);
+            if (!r) r = launch_numeric(P, vals, vdt, shift, s);
+            bool ok = true;
+            if (!r) r = launch_solve(P, b, x, s, &ok);
+            if (!r) r = (int)cudaEventRecord(e1, s);
+            if (!r) r = (int)cudaEventSynchronize(e1);
+            if (r) return r;
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (i > 0) t.push_back(ms);
+        }
+        std::sort(t.begin(), t.end());
+        *ms_out = t.empty() ? 0.0 : t[t.size() / 2];
+        return 0;
+    };
+    struct Knob {
+        int32_t* field;
+        std::vector<int32_t> cand;
+    };
+    std::vector<Knob> knobs = {
+        {&P.tune.warp_items, {152, 2 * 152, 4 * 152, 8 * 152, 16 * 152, 1 << 30}},
+        {&P.tune.vec_max_cls, {0, 64, 96}},
+        {&P.tune.solve_threads_big, {256, 512}},
+    };
+    double best = 0;
+    e = measure(&best);
+    for (Knob& k : knobs) {
+        if (e) break;
+        const int32_t keep = *k.field;
+        int32_t arg = keep;
+        for (int32_t c : k.cand) {
+            if (c == keep) continue;
+            *k.field = c;
+            double ms = 0;
+            e = measure(&ms);
+            if (e) break;
+            if (ms < best * 0.98) {
+                best = ms;
+                arg = c;
+            }
+        }
+        *k.field = arg;
+    }
+    P.prof = prof;
+    P.tune.tuned = e ? 0 : 1;
+    graph_release(P);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best_ms) *best_ms = best;
+    return e;
 }
 
 int launch_backward(Plan& P, const double* x, const double* xbar, double* vals_bar, double* shift_bar,

@@ -31,7 +31,7 @@ EXPORTED_SYMBOLS = [
     "ssco_analyze", "ssco_plan_info", "ssco_plan_export", "ssco_bind", "ssco_numeric", "ssco_solve",
     "ssco_backward", "ssco_status_get", "ssco_export_L", "ssco_export_K", "ssco_refactor_solve_host",
     "ssco_last_launch_count", "ssco_last_error", "ssco_status_string", "ssco_plan_save", "ssco_plan_load",
-    "ssco_destroy", "ssco_profile_enable", "ssco_profile_read", "ssco_kernel_name", "ssco_solve_noalloc", "ssco_profile_trace", "ssco_graph_run",
+    "ssco_destroy", "ssco_profile_enable", "ssco_profile_read", "ssco_kernel_name", "ssco_solve_noalloc", "ssco_profile_trace", "ssco_graph_run", "ssco_autotune",
 ]
 KERNEL_KINDS = ["assemble", "front_small", "big_init", "big_kscatter", "big_update", "big_potrf", "big_syrk",
                 "fwd_solve", "bwd_solve", "resid", "check", "vector", "grad", "front_tiny", "big_trsm", "front_vec"]
@@ -66,7 +66,8 @@ class Info(C.Structure):
                 ["n", "n_pats", "batch", "n_systems", "m", "nnz_K", "nnz_L", "n_snodes", "n_fronts",
                  "n_levels", "max_col_level", "panel_entries", "update_entries", "max_front_rows",
                  "n_assembly_groups", "assembly_terms", "tables_bytes", "workspace_bytes"]] + \
-              [("factor_flops", C.c_double), ("factor_flops_exact", C.c_double)]
+              [("factor_flops", C.c_double), ("factor_flops_exact", C.c_double)] + \
+              [(k, C.c_int64) for k in ["tune_warp_items", "tune_vec_max_cls", "tune_solve_threads_big", "tuned"]]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -108,6 +109,7 @@ def load_library(path: str = LIB_PATH):
         "ssco_solve_noalloc": (i32, [vp, vp, vp, vp]),
         "ssco_profile_trace": (i32, [vp, vp, vp, vp, vp, i64, C.POINTER(i64)]),
         "ssco_graph_run": (i32, [vp, vp, i32, vp, vp, vp, vp]),
+        "ssco_autotune": (i32, [vp, vp, i32, vp, vp, vp, i32, vp, C.POINTER(dbl)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -275,6 +277,20 @@ class Plan:
         assert x.is_cuda and x.dtype == torch.float64 and x.is_contiguous()
         self._check(self.L.ssco_solve_noalloc(self._h, _ptr(b), _ptr(x), _stream_ptr(stream)))
         return x
+
+    def autotune(self, vals: torch.Tensor, shift: torch.Tensor, b: torch.Tensor, x: torch.Tensor, reps: int = 3,
+                 stream=None):
+        """Times the launch-shape candidates on these inputs and keeps the
+        fastest (see ssco_autotune); returns (best step ms, chosen knobs)."""
+        dt = VALS_F64 if vals.dtype == torch.float64 else VALS_F32
+        best = C.c_double(0.0)
+        self._check(self.L.ssco_autotune(self._h, _ptr(vals), dt, _ptr(shift), _ptr(b), _ptr(x), int(reps),
+                                         _stream_ptr(stream), C.byref(best)))
+        inf = Info()
+        self._check(self.L.ssco_plan_info(self._h, C.byref(inf)))
+        self.info = inf.as_dict()
+        return best.value, {k: self.info[k] for k in ("tune_warp_items", "tune_vec_max_cls",
+                                                      "tune_solve_threads_big")}
 
     def graph_run(self, vals: torch.Tensor, shift: torch.Tensor, b: torch.Tensor, x: torch.Tensor, stream=None):
         """numeric + solve as one captured CUDA graph (re-captured when the

@@ -252,6 +252,25 @@ def test_graph_run_matches_eager(S, prec):
         off += p.n
 
 
+def test_autotune_keeps_parity_and_persists(S, tmp_path):
+    p = P.trigrid_problem(24, batch=16, cfg=3)
+    pl, x0, st0, vals, shift, b = run(S, p, S.FP32_REFINE)
+    v, sh, bt = (torch.tensor(a, device="cuda") for a in (vals, shift, b))
+    x = torch.empty_like(bt)
+    ms, knobs = pl.autotune(v, sh, bt, x, reps=2)
+    assert ms > 0 and pl.info["tuned"] == 1
+    assert knobs["tune_vec_max_cls"] in (0, 64, 96) and knobs["tune_solve_threads_big"] in (256, 512)
+    pl.graph_run(v, sh, bt, x)
+    st = pl.status()
+    xh = x.cpu().numpy()
+    for inst in (0, 15):
+        check_against_oracle(S, pl, p, xh, st, inst, inst)
+    f = str(tmp_path / "tuned.bin")
+    pl.save(f)
+    q = S.Plan.load(f, precision=S.FP32_REFINE)
+    assert all(q.info[k] == pl.info[k] for k in knobs) and q.info["tuned"] == 1
+
+
 def test_plan_file_roundtrip_runs(S, tmp_path):
     p = P.elasticity_problem(4, cfg=2)
     pl0 = S.Plan(p, precision=S.FP32_REFINE)

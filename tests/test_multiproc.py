@@ -1,0 +1,63 @@
+"""Multi-rank bookkeeping of bench.py on CPU ranks (gloo, world size 2).
+
+Value sets are independent, so the GPU path shards by instance with no
+collective in the data path; what needs checking is the host logic: every
+rank builds its own value sets (distinct seeds, identical to what a single
+process builds for that rank), each rank's systems solve correctly, and the
+whole-job throughput uses the slowest rank's time."""
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, out):
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    from oracle import oracle as O
+    work, _ = bench.make_workload("tiny", rank)
+    (p, B), = work
+    res = []
+    for i in range(B):
+        r = O.refactor_solve(p, i)
+        res.append(np.linalg.norm(O.symv(r.K, r.x) - p.b[i]) / np.linalg.norm(p.b[i]))
+    local_ms = 10.0 * (rank + 1)
+    value, max_ms = bench.aggregate_value(B, 4, local_ms, dist)
+    w = torch.tensor(p.vals[0][:8].copy())
+    gathered = [torch.zeros_like(w) for _ in range(world)]
+    dist.all_gather(gathered, w)
+    out[rank] = {"value": value, "max_ms": max_ms, "res": max(res),
+                 "first_vals": [g.numpy().tolist() for g in gathered]}
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_weak_scaling():
+    world = 2
+    port = _free_port()
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
+        out = dict(out)
+    import bench
+    for rank in range(world):
+        o = out[rank]
+        assert o["max_ms"] == 20.0                       # the slowest rank's time
+        assert abs(o["value"] - 3 * world * 4 / 0.020) < 1e-9
+        assert o["res"] < 1e-12
+        work, _ = bench.make_workload("tiny", rank)       # same data as a single process builds
+        assert np.allclose(out[0]["first_vals"][rank], work[0][0].vals[0][:8])
+    assert not np.allclose(out[0]["first_vals"][0], out[0]["first_vals"][1])  # distinct value sets
