@@ -45,7 +45,7 @@ typedef enum {
     SSCO_ERR_NOT_SPD = 3,      /* a pivot was not > 0 (per system)          */
     SSCO_ERR_NONFINITE = 4,    /* NaN/Inf in values or right-hand side      */
     SSCO_ERR_NO_CONVERGE = 5,  /* refinement hit its cap or stagnated       */
-    SSCO_ERR_TIMEOUT = 6,      /* a bounded device wait gave up             */
+    SSCO_ERR_TIMEOUT = 6,      /* a bounded device wait gave up (all systems) */
     SSCO_ERR_CUDA = 7,         /* a CUDA runtime call failed                */
     SSCO_ERR_OOM = 8,          /* a caller buffer is smaller than required  */
     SSCO_ERR_UNSUPPORTED = 9,  /* request outside what this build does      */
@@ -97,7 +97,9 @@ typedef struct {
  *   (numeric partition only; exported structures stay exact).
  * tiny_front_max: subtrees whose fronts all have at most this many rows
  *   (<= 32) are factored and solved by one warp each, front in registers,
- *   in a single launch (0 = default 32, -1 = off).                      */
+ *   in a single launch (0 = default 32, -1 = off).
+ * tensor_cores: 0 = FP32 trailing updates of multi-CTA fronts run on the
+ *   tcgen05 tensor cores (3xTF32), -1 = SIMT FP32 only.                 */
 typedef struct {
     int32_t precision;
     int32_t batch;
@@ -106,7 +108,8 @@ typedef struct {
     int32_t small_front_max;
     int32_t amalgamate;
     int32_t tiny_front_max;
-    int32_t reserved[2];
+    int32_t tensor_cores;
+    int32_t reserved[1];
 } ssco_op;
 
 /* Sizes and counts of an analyzed plan (all for the concatenated system). */
@@ -135,6 +138,7 @@ typedef struct {
     int64_t tune_vec_max_cls;
     int64_t tune_solve_threads_big;
     int64_t tuned;           /* 1 after a successful ssco_autotune           */
+    int64_t tune_use_tc;     /* 1: FP32 big-front updates on tensor cores    */
 } ssco_info;
 
 /* ssco_plan_export selectors (host copies; sizes in elements).          */
@@ -220,7 +224,8 @@ ssco_status ssco_export_K(ssco_plan plan, double* host_out, void* stream);
 /* Autotuner of the launch shapes of the level groups: for each knob (the
  * item count from which a solve level runs warp-per-(front, instance), the
  * largest front size class factored several value sets per CTA, the CTA size
- * of solve levels with wide fronts) every candidate is timed on the caller's
+ * of solve levels with wide fronts, tensor cores on or off for the FP32
+ * trailing updates of big fronts) every candidate is timed on the caller's
  * data (median of `reps` numeric + solve steps, CUDA events) and the fastest
  * is kept in the plan (saved by ssco_plan_save).  Synchronizes `stream`;
  * leaves a valid factor and solution (x) behind.  *best_ms (may be NULL)
@@ -292,7 +297,8 @@ enum {
     SSCO_K_FRONT_TINY = 13,  /* warp-per-subtree factorization, tiny fronts   */
     SSCO_K_BIG_TRSM = 14,    /* big front: rows below the diagonal block      */
     SSCO_K_FRONT_VEC = 15,   /* small fronts, V value sets per CTA            */
-    SSCO_K_COUNT = 16
+    SSCO_K_BIG_UPDATE_TC = 16, /* big front: trailing update on tcgen05 (3xTF32) */
+    SSCO_K_COUNT = 17
 };
 typedef struct {
     int32_t kind;

@@ -76,7 +76,7 @@ void set_dev_tables(Plan& P) {
 
 // ----- plan file (de)serialization -----------------------------------------
 constexpr uint64_t kMagic = 0x314F4353534F4353ull;  // "SCOSSCO1"
-constexpr uint32_t kVersion = 4;
+constexpr uint32_t kVersion = 5;
 
 struct Writer {
     std::ofstream f;
@@ -206,6 +206,7 @@ ssco_status ssco_plan_info(ssco_plan h, ssco_info* o) {
     o->tune_vec_max_cls = P.tune.vec_max_cls;
     o->tune_solve_threads_big = P.tune.solve_threads_big;
     o->tuned = P.tune.tuned;
+    o->tune_use_tc = P.tune.use_tc;
     return SSCO_OK;
 }
 
@@ -340,7 +341,11 @@ ssco_status ssco_status_get(ssco_plan h, void* stream, int32_t* status, int32_t*
     if (!e) e = cudaMemcpy(it.data(), P.d_ws + P.ws.iters, S * 4, cudaMemcpyDeviceToHost);
     if (!e) e = cudaMemcpy(bc.data(), P.d_ws + P.ws.bad_col, S * 4, cudaMemcpyDeviceToHost);
     if (!e) e = cudaMemcpy(rs.data(), P.d_ws + P.ws.resid, S * 8, cudaMemcpyDeviceToHost);
+    int32_t dev_err = 0;
+    if (!e) e = cudaMemcpy(&dev_err, P.d_ws + P.ws.dev_err, 4, cudaMemcpyDeviceToHost);
     if (e) return cuda_fail(h, e, "status copy");
+    if (dev_err)
+        for (size_t i = 0; i < S; ++i) st[i] = SSCO_ERR_TIMEOUT;
     ssco_status worst = SSCO_OK;
     for (size_t i = 0; i < S; ++i) {
         int32_t sc = bc[i] != INT_MAX ? (int32_t)SSCO_ERR_NOT_SPD : st[i];

@@ -107,7 +107,7 @@ struct DevTables {
 // Byte offsets of every region of the caller's workspace.
 struct WsLayout {
     size_t K, panel, upd, pvec, vecT, bp, xp, rr, mu, xbar_p;
-    size_t bad_col, sstatus, iters, active, any_active, it_ctr;
+    size_t bad_col, sstatus, iters, active, any_active, it_ctr, dev_err;
     size_t resid, bnorm, r1, r2, sigma, sbar;
     size_t st_vals, st_shift, st_b, st_x;
     size_t total;
@@ -126,6 +126,8 @@ struct Tunables {
     int32_t warp_items = 8 * 152;  // a solve level goes warp-per-item at >= this many items
     int32_t vec_max_cls = 96;      // largest size class factored V value sets per CTA
     int32_t solve_threads_big = 512;  // CTA size of solve levels with fronts > 512 rows
+    int32_t use_tc = 1;            // FP32 big-front trailing updates on tcgen05 tensor cores
+    int32_t tc_min_rows = 128;     // ... when the trailing extent reaches this many rows
     int32_t tuned = 0;
 };
 

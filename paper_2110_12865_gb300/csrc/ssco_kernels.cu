@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "ssco_internal.h"
+#include "ssco_tc.cuh"
 
 namespace ssco {
 
@@ -793,6 +794,127 @@ __global__ void __launch_bounds__(256) k_big_kscatter(const DevTables t, const i
     panel[(int64_t)b * panel_total + d.panel_off + kl[1]] += (T)K[(int64_t)b * nnzK + kl[0]];
 }
 
+// Tensor-core trailing update (FP32 factor), the dense contraction of a big
+// front: one CTA (4 warps) per 128x128 tile of the trailing lower triangle.
+// The block's <= 32 panel columns of the tile's row sets are split into TF32
+// high and low parts (x = hi + lo) in shared memory (K-major core-matrix
+// layout); tcgen05.mma kind::tf32 accumulates hi*hi' + hi*lo' + lo*hi' in
+// 128 tensor-memory columns (FP32-level accuracy from three TF32 products);
+// each warp then reads its 32 rows back and subtracts them from the front.
+constexpr int kTcSmem = 65536 + 64;
+
+__global__ void __launch_bounds__(128) k_big_update_tc(const DevTables t, const int32_t* __restrict__ list, int kb,
+                                                       float* __restrict__ panel, int64_t panel_total,
+                                                       float* __restrict__ upd, int64_t upd_total,
+                                                       int32_t* __restrict__ dev_err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    const FrontDesc d = t.fronts[list[blockIdx.y]];
+    const int b = blockIdx.z;
+    const int r = d.r, w = d.w;
+    const int c0 = kb * 32;
+    if (c0 >= w) return;
+    const int nbk = min(32, w - c0);
+    const int c1 = c0 + nbk;
+    const int m = r - c1;
+    if (m <= 0) return;
+    const int64_t nt = (m + 127) / 128;
+    const int64_t tile = blockIdx.x;
+    if (tile >= nt * (nt + 1) / 2) return;
+    int64_t ti = (int64_t)((sqrt(8.0 * (double)tile + 1.0) - 1.0) * 0.5);
+    while (ti * (ti + 1) / 2 > tile) --ti;
+    while ((ti + 1) * (ti + 2) / 2 <= tile) ++ti;
+    const int64_t tj = tile - ti * (ti + 1) / 2;
+    const int i0 = c1 + (int)ti * 128, j0 = c1 + (int)tj * 128;
+    float* Pb = panel + (int64_t)b * panel_total + d.panel_off;
+    float* Ub = upd + (int64_t)b * upd_total + d.upd_off;
+    const int ru = r - w;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    unsigned char* Ah = smem_raw;
+    unsigned char* Al = smem_raw + 16384;
+    unsigned char* Bh = smem_raw + 32768;
+    unsigned char* Bl = smem_raw + 49152;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + 65536);
+    uint32_t* slot = reinterpret_cast<uint32_t*>(smem_raw + 65536 + 16);
+    const bool diag = ti == tj;
+    for (int e = tid; e < 128 * 32; e += 128) {
+        const int mm = e & 127, k = e >> 7;
+        const int ra = i0 + mm;
+        const float x = (ra < r && k < nbk) ? Pb[(int64_t)(c0 + k) * r + ra] : 0.f;
+        const float h = tc::to_tf32(x);
+        const uint32_t off = tc::kmajor_offset(mm, k, 128);
+        *reinterpret_cast<float*>(Ah + off) = h;
+        *reinterpret_cast<float*>(Al + off) = x - h;
+        if (!diag) {
+            const int rb = j0 + mm;
+            const float y = (rb < r && k < nbk) ? Pb[(int64_t)(c0 + k) * r + rb] : 0.f;
+            const float g = tc::to_tf32(y);
+            *reinterpret_cast<float*>(Bh + off) = g;
+            *reinterpret_cast<float*>(Bl + off) = y - g;
+        }
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(slot, 128);
+        tc::tmem_relinquish();
+    }
+    if (tid == 0) {
+        tc::mbar_init(bar, 1);
+        tc::mbar_init_fence();
+    }
+    tc::fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t taddr = *slot;
+    const uint32_t lbo = 16 * 128, sbo = 128;
+    if (tid == 0) {
+        const uint32_t idesc = tc::idesc_tf32(128, 128);
+        const unsigned char* bh = diag ? Ah : Bh;
+        const unsigned char* bl = diag ? Al : Bl;
+        for (int s = 0; s < 4; ++s) {
+            const uint32_t koff = (uint32_t)s * 2 * lbo;
+            const uint64_t dah = tc::smem_desc_kmajor(Ah + koff, lbo, sbo);
+            const uint64_t dal = tc::smem_desc_kmajor(Al + koff, lbo, sbo);
+            const uint64_t dbh = tc::smem_desc_kmajor(bh + koff, lbo, sbo);
+            const uint64_t dbl = tc::smem_desc_kmajor(bl + koff, lbo, sbo);
+            tc::mma_tf32(taddr, dah, dbh, idesc, s > 0 ? 1u : 0u);
+            tc::mma_tf32(taddr, dah, dbl, idesc, 1u);
+            tc::mma_tf32(taddr, dal, dbh, idesc, 1u);
+        }
+        tc::mma_commit(bar);
+    }
+    __syncwarp();
+    bool ok = tc::mbar_wait(bar, 0, 1u << 24);
+    if (!ok) {
+        if (lane == 0) atomicExch(dev_err, 1);
+        ok = tc::mbar_wait(bar, 0, 1u << 24);
+    }
+    tc::fence_after_sync();
+    if (ok) {
+        const int i = i0 + 32 * warp + lane;
+        for (int c = 0; c < 128; c += 8) {
+            float v[8];
+            tc::tmem_ld8(taddr + ((uint32_t)(32 * warp) << 16) + (uint32_t)c, v);
+            tc::tmem_ld_wait();
+            if (i < r) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int j = j0 + c + q;
+                    if (j < r && j <= i) {
+                        if (j < w)
+                            Pb[(int64_t)j * r + i] -= v[q];
+                        else
+                            Ub[(int64_t)(j - w) * ru + (i - w)] -= v[q];
+                    }
+                }
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(taddr, 128);
+}
+
 // Factor the 32x32 diagonal block of column block kb, one warp per front.
 // Its own launch: the triangular solve below must read the factored block,
 // and no CTA of one launch may overwrite what another CTA still has to load.
@@ -1525,6 +1647,7 @@ int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cud
         k_fill_i32<<<cdiv(S, 256), 256, 0, s>>>(bad, S, INT_MAX);
         pr.done(0, S * 4.0);
     }
+    cudaMemsetAsync(P.d_ws + P.ws.dev_err, 0, 4, s);
     if (!P.chunks.empty()) {
         Prof pr(P, s, SSCO_K_ASSEMBLE);
         dim3 g((unsigned)P.chunks.size(), B);
@@ -1645,7 +1768,32 @@ int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cud
                 const int64_t mt = (d.r - c0 - std::min(32, d.w - c0) + 63) / 64;
                 tiles = std::max(tiles, mt * (mt + 1) / 2);
             }
-            if (tiles > 0) {
+            int64_t tiles128 = 0;
+            for (int32_t q = 0; q < ll.count; ++q) {
+                const FrontDesc& d = P.fronts[P.front_lists[ll.list_off + q]];
+                if (c0 >= d.w) continue;
+                const int64_t mt = (d.r - c0 - std::min(32, d.w - c0) + 127) / 128;
+                tiles128 = std::max(tiles128, mt * (mt + 1) / 2);
+            }
+            const bool tcore = sizeof(T) == 4 && P.tune.use_tc && tiles128 > 0 &&
+                               (ll.rmax - c0) >= P.tune.tc_min_rows;
+            if (tcore) {
+                Prof pu(P, s, SSCO_K_BIG_UPDATE_TC);
+                k_big_update_tc<<<dim3((unsigned)tiles128, ll.count, B), 128, kTcSmem, s>>>(
+                    P.dt, list, kb, reinterpret_cast<float*>(panel), P.panel_total, reinterpret_cast<float*>(upd),
+                    P.upd_total, wsp<int32_t>(P, P.ws.dev_err));
+                if (pu.ev >= 0) {
+                    double fl = 0, by = 0;
+                    for (int32_t q = 0; q < ll.count; ++q) {
+                        const FrontDesc& d = P.fronts[P.front_lists[ll.list_off + q]];
+                        if (c0 >= d.w) continue;
+                        double nbk = std::min(32, d.w - c0), m = d.r - c0 - nbk;
+                        fl += m * (m + 1) * nbk;
+                        by += (m * (m + 1) + 2 * m * nbk) * P.tsize;
+                    }
+                    pu.done(fl * B, by * B);
+                }
+            } else if (tiles > 0) {
                 Prof pu(P, s, SSCO_K_BIG_GEMM);
                 k_big_update<T><<<dim3((unsigned)tiles, ll.count, B), 256, 0, s>>>(P.dt, list, kb, panel,
                                                                                   P.panel_total, upd, P.upd_total);
@@ -1913,6 +2061,8 @@ int allow_dynamic_smem(K kernel) {
 template <class T>
 int set_attr_T() {
     int e = allow_dynamic_smem(k_front_small<T>);
+    if (!e && sizeof(T) == 4)
+        e = (int)cudaFuncSetAttribute(k_big_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
     if (!e) e = allow_dynamic_smem(k_front_vec<T, sizeof(T) == 4 ? 4 : 2>);
     if (!e) e = allow_dynamic_smem(k_tiny_factor<T>);
     if (!e) e = allow_dynamic_smem(k_tiny_fwd<T>);
@@ -1929,7 +2079,7 @@ int set_attr_T() {
 const char* kernel_kind_name(int kind) {
     static const char* names[SSCO_K_COUNT] = {"assemble", "front_small", "big_init", "big_kscatter", "big_update",
                                               "big_potrf", "big_syrk", "fwd_solve", "bwd_solve", "resid",
-                                              "check", "vector", "grad", "front_tiny", "big_trsm", "front_vec"};
+                                              "check", "vector", "grad", "front_tiny", "big_trsm", "front_vec", "big_update_tc"};
     return kind >= 0 && kind < SSCO_K_COUNT ? names[kind] : "unknown";
 }
 
@@ -2068,6 +2218,7 @@ int autotune(Plan& P, const void* vals, int32_t vdt, const double* shift, const 
         {&P.tune.warp_items, {152, 2 * 152, 4 * 152, 8 * 152, 16 * 152, 1 << 30}},
         {&P.tune.vec_max_cls, {0, 64, 96}},
         {&P.tune.solve_threads_big, {256, 512}},
+        {&P.tune.use_tc, {0, 1}},
     };
     double best = 0;
     e = measure(&best);

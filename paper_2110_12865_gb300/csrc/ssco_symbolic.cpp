@@ -202,6 +202,7 @@ ssco_status analyze_impl(const ssco_pattern* const* pats, int32_t n_pats, const 
     P.amalg = op->amalgamate;
     P.tiny_max = op->tiny_front_max == 0 ? 32 : (op->tiny_front_max < 0 ? 0 : std::min(op->tiny_front_max, 32));
     P.n_pats = n_pats;
+    P.tune.use_tc = op->tensor_cores < 0 ? 0 : 1;
 
     for (int k = 0; k < n_pats; ++k) {
         ssco_status s = validate(P, pats[k], k);
@@ -948,6 +949,7 @@ void compute_ws_layout(Plan& P) {
     w.active = take(S * 4);
     w.any_active = take(4);
     w.it_ctr = take(4);
+    w.dev_err = take(4);
     w.resid = take(S * 8);
     w.bnorm = take(S * 8);
     w.r1 = take(S * 8);

@@ -34,7 +34,8 @@ EXPORTED_SYMBOLS = [
     "ssco_destroy", "ssco_profile_enable", "ssco_profile_read", "ssco_kernel_name", "ssco_solve_noalloc", "ssco_profile_trace", "ssco_graph_run", "ssco_autotune",
 ]
 KERNEL_KINDS = ["assemble", "front_small", "big_init", "big_kscatter", "big_update", "big_potrf", "big_syrk",
-                "fwd_solve", "bwd_solve", "resid", "check", "vector", "grad", "front_tiny", "big_trsm", "front_vec"]
+                "fwd_solve", "bwd_solve", "resid", "check", "vector", "grad", "front_tiny", "big_trsm", "front_vec",
+                "big_update_tc"]
 
 
 class SscoError(RuntimeError):
@@ -53,7 +54,8 @@ class Pattern(C.Structure):
 class Op(C.Structure):
     _fields_ = [("precision", C.c_int32), ("batch", C.c_int32), ("refine_tol", C.c_double),
                 ("refine_max_iter", C.c_int32), ("small_front_max", C.c_int32),
-                ("amalgamate", C.c_int32), ("tiny_front_max", C.c_int32), ("reserved", C.c_int32 * 2)]
+                ("amalgamate", C.c_int32), ("tiny_front_max", C.c_int32), ("tensor_cores", C.c_int32),
+                ("reserved", C.c_int32 * 1)]
 
 
 class KernelStat(C.Structure):
@@ -67,7 +69,8 @@ class Info(C.Structure):
                  "n_levels", "max_col_level", "panel_entries", "update_entries", "max_front_rows",
                  "n_assembly_groups", "assembly_terms", "tables_bytes", "workspace_bytes"]] + \
               [("factor_flops", C.c_double), ("factor_flops_exact", C.c_double)] + \
-              [(k, C.c_int64) for k in ["tune_warp_items", "tune_vec_max_cls", "tune_solve_threads_big", "tuned"]]
+              [(k, C.c_int64) for k in ["tune_warp_items", "tune_vec_max_cls", "tune_solve_threads_big", "tuned",
+                                        "tune_use_tc"]]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -140,7 +143,7 @@ class Plan:
     (several patterns concatenated, one value set each per instance)."""
 
     def __init__(self, problems, precision=FP64, batch=None, refine_tol=1e-10, refine_max_iter=30,
-                 small_front_max=0, amalgamate=1, tiny_front_max=0, _handle=None):
+                 small_front_max=0, amalgamate=1, tiny_front_max=0, tensor_cores=0, _handle=None):
         self.L = load_library()
         if _handle is not None:
             self._h = _handle
@@ -177,6 +180,7 @@ class Plan:
             op.small_front_max = small_front_max
             op.amalgamate = amalgamate
             op.tiny_front_max = tiny_front_max
+            op.tensor_cores = tensor_cores
             h = C.c_void_p()
             st = self.L.ssco_analyze(arr, len(pats), C.byref(op), C.byref(h))
             if st != SSCO_OK:
@@ -290,7 +294,7 @@ class Plan:
         self._check(self.L.ssco_plan_info(self._h, C.byref(inf)))
         self.info = inf.as_dict()
         return best.value, {k: self.info[k] for k in ("tune_warp_items", "tune_vec_max_cls",
-                                                      "tune_solve_threads_big")}
+                                                      "tune_solve_threads_big", "tune_use_tc")}
 
     def graph_run(self, vals: torch.Tensor, shift: torch.Tensor, b: torch.Tensor, x: torch.Tensor, stream=None):
         """numeric + solve as one captured CUDA graph (re-captured when the

@@ -92,6 +92,23 @@ def test_elasticity_small(S, prec, kw):
         assert err < 1e-8
 
 
+@pytest.mark.parametrize("tc", [0, -1])
+def test_fp32_factor_accuracy_big_fronts(S, tc):
+    """FP32 factor through the multi-CTA path, trailing updates on tcgen05
+    tensor cores (3xTF32, tc=0) or SIMT FP32 (tc=-1): every column of L must
+    agree with the FP64 oracle to FP32-level accuracy (plain TF32, ~1e-3,
+    would fail), and the refined solution to the FP64 residual bound."""
+    p = P.elasticity_problem(7, cfg=2)
+    pl, x, st, *_ = run(S, p, S.FP32_REFINE, small_front_max=32, tensor_cores=tc)
+    assert pl.info["tune_use_tc"] == (1 if tc == 0 else 0)
+    r, res, err = check_against_oracle(S, pl, p, x, st, 0, 0)
+    L = pl.export_L()[0]
+    Lc = r.S.Lcolptr
+    worst = max(np.linalg.norm(L[Lc[j]:Lc[j + 1]] - r.L[Lc[j]:Lc[j + 1]]) / np.linalg.norm(r.L[Lc[j]:Lc[j + 1]])
+                for j in range(p.n))
+    assert worst <= 2e-4, worst
+
+
 @pytest.mark.parametrize("seed", range(6))
 def test_fp64_random_patterns(S, seed):
     rng = np.random.default_rng(900 + seed)
