@@ -99,7 +99,9 @@ typedef struct {
  *   (<= 32) are factored and solved by one warp each, front in registers,
  *   in a single launch (0 = default 32, -1 = off).
  * tensor_cores: 0 = FP32 trailing updates of multi-CTA fronts run on the
- *   tcgen05 tensor cores (3xTF32), -1 = SIMT FP32 only.                 */
+ *   tcgen05 tensor cores (3xTF32), -1 = SIMT FP32 only.
+ * big_panel: columns of a multi-CTA front factored between two trailing
+ *   updates (a multiple of 32 in [32, 1024]; 0 = default 128).        */
 typedef struct {
     int32_t precision;
     int32_t batch;
@@ -109,7 +111,7 @@ typedef struct {
     int32_t amalgamate;
     int32_t tiny_front_max;
     int32_t tensor_cores;
-    int32_t reserved[1];
+    int32_t big_panel;
 } ssco_op;
 
 /* Sizes and counts of an analyzed plan (all for the concatenated system). */
@@ -139,6 +141,7 @@ typedef struct {
     int64_t tune_solve_threads_big;
     int64_t tuned;           /* 1 after a successful ssco_autotune           */
     int64_t tune_use_tc;     /* 1: FP32 big-front updates on tensor cores    */
+    int64_t tune_big_panel;  /* big fronts: columns per trailing update      */
 } ssco_info;
 
 /* ssco_plan_export selectors (host copies; sizes in elements).          */

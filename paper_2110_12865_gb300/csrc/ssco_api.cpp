@@ -76,7 +76,7 @@ void set_dev_tables(Plan& P) {
 
 // ----- plan file (de)serialization -----------------------------------------
 constexpr uint64_t kMagic = 0x314F4353534F4353ull;  // "SCOSSCO1"
-constexpr uint32_t kVersion = 5;
+constexpr uint32_t kVersion = 6;
 
 struct Writer {
     std::ofstream f;
@@ -127,6 +127,7 @@ bool serialize(IO& io, Plan& P) {
     V(P.tiny_list); V(P.tiny_off); S(P.n_tiny);
     V(P.tiny_prog); V(P.tiny_prog_off); S(P.tiny_prog_max); S(P.tiny_k_max);
     S(P.tune);
+    S(P.tc_pack_total);
     V(P.groups); V(P.chunks); V(P.asm_idx); V(P.asm_coef);
     V(P.sp_rowptr); V(P.sp_col); V(P.sp_slot); V(P.row_sys); V(P.sys_n_off); V(P.shifted);
     V(P.g_rowptr); V(P.g_colind); V(P.g_row_sys); V(P.g_rows_all); V(P.g_aval);
@@ -207,6 +208,7 @@ ssco_status ssco_plan_info(ssco_plan h, ssco_info* o) {
     o->tune_solve_threads_big = P.tune.solve_threads_big;
     o->tuned = P.tune.tuned;
     o->tune_use_tc = P.tune.use_tc;
+    o->tune_big_panel = P.tune.big_panel;
     return SSCO_OK;
 }
 

@@ -17,6 +17,10 @@ constexpr int32_t kTinyHdrWords = 8;
 constexpr int32_t kTinyRecWords = 16;
 constexpr int32_t kTinyProgWords = 1024;  // per subtree, shared memory per warp
 constexpr int32_t kTinyMaxK = 256;        // K entries gathered per subtree
+// Tensor-core operand blocks of a big FP32 front: per 128-row tile, up to
+// kTcMaxPanel / 16 blocks of 128 x 16 TF32 high + low parts (4096 floats).
+constexpr int32_t kTcMaxPanel = 256;
+constexpr int64_t kTcTileFloats = (int64_t)(kTcMaxPanel / 16) * 4096;
 
 // One front of the numeric partition (a fundamental or amalgamated
 // supernode).  Its factor columns [f, f+w) are stored as a dense r x w
@@ -35,6 +39,8 @@ struct FrontDesc {
     int64_t relmap_off;           // r-w positions of this front's update rows in
                                   // the parent's rows (-1 for a root)
     int64_t inv_off;              // big fronts: [nchild][r] inverse maps (-1 if none)
+    int64_t tc_off;               // big FP32 fronts: per-instance offset (floats) of the
+                                  // tensor-core operand blocks within its level (-1 if none)
 };
 
 // Assembly leaf table of one group (Sec. 4.3/4.4): members share a term
@@ -61,7 +67,7 @@ struct LaunchList {
     int64_t list_off;   // into front_lists
     int32_t count;
     int32_t rmax, wmax;
-    int64_t max_lower_tiles;  // big: max tiles of 32x32 over the front's lower triangle
+    int64_t max_lower_tiles;  // big: max tiles of 64x64 over the front's lower triangle
     int64_t max_syrk_tiles;   // big: max 64x64 lower tiles of the update block
     int32_t max_klist;        // big: max K entries per front
 };
@@ -110,6 +116,7 @@ struct WsLayout {
     size_t bad_col, sstatus, iters, active, any_active, it_ctr, dev_err;
     size_t resid, bnorm, r1, r2, sigma, sbar;
     size_t st_vals, st_shift, st_b, st_x;
+    size_t tcpack;
     size_t total;
 };
 
@@ -128,6 +135,7 @@ struct Tunables {
     int32_t solve_threads_big = 512;  // CTA size of solve levels with fronts > 512 rows
     int32_t use_tc = 1;            // FP32 big-front trailing updates on tcgen05 tensor cores
     int32_t tc_min_rows = 128;     // ... when the trailing extent reaches this many rows
+    int32_t big_panel = 128;       // big fronts: columns per trailing-update block
     int32_t tuned = 0;
 };
 
@@ -180,6 +188,7 @@ struct Plan {
     int32_t tiny_prog_max = 0, tiny_k_max = 0;
     int32_t n_levels = 0;
     int64_t panel_total = 0, upd_total = 0, pvec_total = 0;
+    int64_t tc_pack_total = 0;  // floats per instance of tensor-core operand blocks (0 = none)
     int32_t max_rows = 0;
 
     // assembly

@@ -743,7 +743,11 @@ __global__ void __launch_bounds__(256) k_tiny_bwd(const DevTables t, int32_t n_t
 // a4: big fronts (r > small_front_max), dense panel in global memory.
 // --------------------------------------------------------------------------
 // Panel and update initialised from the children's update matrices through
-// inverse maps (pull, fixed child order => deterministic, no atomics).
+// inverse maps (pull, fixed child order => deterministic, no atomics).  One
+// CTA per 64x64 tile of the lower triangle: the tile's rows and columns of
+// up to 8 children's inverse maps are staged in shared memory, so each
+// element costs one load per child that holds it.  Thread (tx, ty) owns
+// row i0 + tx and columns j0 + ty + 4q, q < 16.
 template <class T>
 __global__ void __launch_bounds__(256) k_big_init(const DevTables t, const int32_t* __restrict__ list,
                                                   T* __restrict__ panel, int64_t panel_total,
@@ -751,34 +755,61 @@ __global__ void __launch_bounds__(256) k_big_init(const DevTables t, const int32
     const FrontDesc d = t.fronts[list[blockIdx.y]];
     const int b = blockIdx.z;
     const int r = d.r, w = d.w;
-    const int64_t nt = (r + 31) / 32;
+    const int64_t nt = (r + 63) / 64;
     const int64_t tile = blockIdx.x;
     if (tile >= nt * (nt + 1) / 2) return;
     int64_t ti = (int64_t)((sqrt(8.0 * (double)tile + 1.0) - 1.0) * 0.5);
     while (ti * (ti + 1) / 2 > tile) --ti;
     while ((ti + 1) * (ti + 2) / 2 <= tile) ++ti;
     const int64_t tj = tile - ti * (ti + 1) / 2;
-    const int i = (int)(ti * 32) + threadIdx.x;
+    const int i0 = (int)ti * 64, j0 = (int)tj * 64;
+    __shared__ int32_t si[8][64], sj[8][64];
+    __shared__ int64_t soff[8];
+    __shared__ int32_t sld[8];
+    const int tid = threadIdx.x, tx = tid & 63, ty = tid >> 6;
+    const int i = i0 + tx;
+    T acc[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc[q] = T(0);
+    for (int cb = 0; cb < d.nchild; cb += 8) {
+        const int nc = min(8, d.nchild - cb);
+        if (cb > 0) __syncthreads();
+        for (int e = tid; e < nc * 64; e += 256) {
+            const int c = e >> 6, k = e & 63;
+            const int32_t* inv = t.invmap + d.inv_off + (int64_t)(cb + c) * r;
+            si[c][k] = i0 + k < r ? inv[i0 + k] : -1;
+            sj[c][k] = j0 + k < r ? inv[j0 + k] : -1;
+        }
+        if (tid < nc) {
+            const FrontDesc cd = t.fronts[t.child_ids[d.child_off + cb + tid]];
+            soff[tid] = (int64_t)b * upd_total + cd.upd_off;
+            sld[tid] = cd.r - cd.w;
+        }
+        __syncthreads();
+        for (int c = 0; c < nc; ++c) {
+            const int a = si[c][tx];
+            if (a < 0) continue;
+            const T* U = upd + soff[c] + a;
+            const int64_t rc = sld[c];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const int bb = sj[c][ty + 4 * q];
+                if (bb >= 0 && bb <= a) acc[q] += U[(int64_t)bb * rc];
+            }
+        }
+    }
+    if (i >= r) return;
     T* Pb = panel + (int64_t)b * panel_total + d.panel_off;
     T* Ub = upd + (int64_t)b * upd_total + d.upd_off;
     const int ru = r - w;
-    for (int jj = threadIdx.y; jj < 32; jj += blockDim.y) {
-        const int j = (int)(tj * 32) + jj;
-        if (i >= r || j >= r || i < j) continue;
-        T acc = T(0);
-        for (int c = 0; c < d.nchild; ++c) {
-            const int32_t* inv = t.invmap + d.inv_off + (int64_t)c * r;
-            const int a = inv[i], bb = inv[j];
-            if (a >= 0 && bb >= 0) {
-                const FrontDesc cd = t.fronts[t.child_ids[d.child_off + c]];
-                const int rc = cd.r - cd.w;
-                acc += upd[(int64_t)b * upd_total + cd.upd_off + (int64_t)bb * rc + a];
-            }
-        }
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        const int j = j0 + ty + 4 * q;
+        if (j > i) continue;
         if (j < w)
-            Pb[(int64_t)j * r + i] = acc;
+            Pb[(int64_t)j * r + i] = acc[q];
         else
-            Ub[(int64_t)(j - w) * ru + (i - w)] = acc;
+            Ub[(int64_t)(j - w) * ru + (i - w)] = acc[q];
     }
 }
 
@@ -794,116 +825,247 @@ __global__ void __launch_bounds__(256) k_big_kscatter(const DevTables t, const i
     panel[(int64_t)b * panel_total + d.panel_off + kl[1]] += (T)K[(int64_t)b * nnzK + kl[0]];
 }
 
-// Tensor-core trailing update (FP32 factor), the dense contraction of a big
-// front: one CTA (4 warps) per 128x128 tile of the trailing lower triangle.
-// The block's <= 32 panel columns of the tile's row sets are split into TF32
-// high and low parts (x = hi + lo) in shared memory (K-major core-matrix
-// layout); tcgen05.mma kind::tf32 accumulates hi*hi' + hi*lo' + lo*hi' in
-// 128 tensor-memory columns (FP32-level accuracy from three TF32 products);
-// each warp then reads its 32 rows back and subtracts them from the front.
-constexpr int kTcSmem = 65536 + 64;
+// Tile (i0, j0) of a big-front update F[i, j] -= sum_{k0 <= l < k1} L[i, l] L[j, l]
+// over rows jlo <= i < r and columns jlo <= j < jhi, j <= i, with
+// k1 = min(k0 + nk, w), jlo = k1 and jhi = r (jend < 0: the whole trailing
+// triangle, tiles enumerated row by row over the lower triangle) or
+// jhi = min(jend, w) (the rest of the current panel block: a narrow
+// trapezoid, tiles enumerated on its row x column grid).  Returns false for
+// CTAs without a tile of this front.
+__device__ __forceinline__ bool big_update_tile(int r, int w, int k0, int nk, int jend, int ts, int64_t tile,
+                                                int& k1, int& jhi, int& i0, int& j0) {
+    if (k0 >= w) return false;
+    k1 = min(k0 + nk, w);
+    const int jlo = k1;
+    jhi = jend < 0 ? r : min(jend, w);
+    if (jhi <= jlo) return false;
+    const int64_t nrt = (r - jlo + ts - 1) / ts;
+    int64_t ti, tj;
+    if (jend < 0) {
+        if (tile >= nrt * (nrt + 1) / 2) return false;
+        ti = (int64_t)((sqrt(8.0 * (double)tile + 1.0) - 1.0) * 0.5);
+        while (ti * (ti + 1) / 2 > tile) --ti;
+        while ((ti + 1) * (ti + 2) / 2 <= tile) ++ti;
+        tj = tile - ti * (ti + 1) / 2;
+    } else {
+        const int64_t nct = (jhi - jlo + ts - 1) / ts;
+        if (tile >= nrt * nct) return false;
+        ti = tile / nct;
+        tj = tile % nct;
+        if (tj > ti) return false;
+    }
+    i0 = jlo + (int)ti * ts;
+    j0 = jlo + (int)tj * ts;
+    return true;
+}
 
-__global__ void __launch_bounds__(128) k_big_update_tc(const DevTables t, const int32_t* __restrict__ list, int kb,
-                                                       float* __restrict__ panel, int64_t panel_total,
-                                                       float* __restrict__ upd, int64_t upd_total,
-                                                       int32_t* __restrict__ dev_err) {
+// Operand blocks of the tensor-core updates (FP32 factor).  The rows of
+// the current panel block [C0, C0 + big_panel) of a big front are kept, per
+// absolute 128-row tile t (rows 128 t ..) and 16-column chunk c (columns
+// C0 + 16 c ..), as a 16 KB block: the TF32 high parts (x rounded to TF32)
+// then the low parts (x - hi), each a 128 x 16 K-major tile of 8-row x
+// 16-byte core matrices: float4 group g = 128 (k / 4) + (m % 128) at byte
+// 16 g holds columns 4 (k / 4) .. + 3 of row m.  Block (t, c) of front q
+// starts at float tc_off(q) + t kTcTileFloats + 4096 c of the instance's
+// pack.  k_big_trsm writes them as it finishes each 32-column step; rows it
+// has not written hold stale values that only reach masked outputs.
+__device__ __forceinline__ float* tc_block(float* pack, int64_t pack_total, const FrontDesc& d, int b, int row,
+                                           int chunk) {
+    return pack + (int64_t)b * pack_total + d.tc_off + (int64_t)(row >> 7) * kTcTileFloats + (int64_t)chunk * 4096;
+}
+
+// Tile (i0, j0) (multiples of 128) of a tensor-core update; same update as
+// big_update_tile, on the absolute 128-row grid of the operand blocks.
+__device__ __forceinline__ bool tc_update_tile(int r, int w, int k0, int nk, int jend, int64_t tile, int& k1,
+                                               int& jlo, int& jhi, int& i0, int& j0) {
+    if (k0 >= w) return false;
+    k1 = min(k0 + nk, w);
+    jlo = k1;
+    jhi = jend < 0 ? r : min(jend, w);
+    if (jhi <= jlo) return false;
+    const int t0 = jlo >> 7;
+    const int64_t nrt = (r + 127) / 128 - t0;
+    int64_t ti, tj;
+    if (jend < 0) {
+        if (tile >= nrt * (nrt + 1) / 2) return false;
+        ti = (int64_t)((sqrt(8.0 * (double)tile + 1.0) - 1.0) * 0.5);
+        while (ti * (ti + 1) / 2 > tile) --ti;
+        while ((ti + 1) * (ti + 2) / 2 <= tile) ++ti;
+        tj = tile - ti * (ti + 1) / 2;
+    } else {
+        const int64_t nct = (jhi + 127) / 128 - t0;
+        if (tile >= nrt * nct) return false;
+        ti = tile / nct;
+        tj = tile % nct;
+        if (tj > ti) return false;
+    }
+    i0 = (t0 + (int)ti) * 128;
+    j0 = (t0 + (int)tj) * 128;
+    return true;
+}
+
+// Tensor-core trailing update (FP32 factor), the dense contraction of a big
+// front: one CTA per 128x128 tile of the trailing lower triangle (see
+// big_update_tile, jend < 0), two CTAs per SM.  Warp 8 lane 0 streams the
+// tile's operand blocks (k_tc_pack) into a 3-stage shared-memory ring with
+// bulk asynchronous copies and issues tcgen05.mma kind::tf32 on each landed
+// chunk: hi*hi' + hi*lo' + lo*hi' accumulated in 128 tensor-memory columns
+// (FP32-level accuracy from three TF32 products); each MMA commit frees its
+// stage.  Warps 0-7 hold the epilogue: warp w reads tensor-memory lanes
+// 32 (w % 4).. and columns 64 (w / 4)..+63 in two halves and subtracts
+// them from the front, the first half's old values loaded before the wait.
+// Every wait is bounded; on expiry the kernel raises *dev_err, drains its
+// copies and MMAs (bounded), skips the update and frees its tensor memory.
+constexpr int kTcStages = 3;
+constexpr int kTcStageBytes = 32768;  // A block 16 KB + B block 16 KB
+constexpr int kTcSmem = kTcStages * kTcStageBytes + 128;
+constexpr uint32_t kTcWaitPolls = 1u << 24;
+
+__global__ void __launch_bounds__(288, 2) k_big_update_tc(const DevTables t, const int32_t* __restrict__ list,
+                                                          int kpack0, int k0, int nk, int jend,
+                                                          const float* __restrict__ pack,
+                                                          int64_t pack_total, float* __restrict__ panel,
+                                                          int64_t panel_total, float* __restrict__ upd,
+                                                          int64_t upd_total, int32_t* __restrict__ dev_err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     const FrontDesc d = t.fronts[list[blockIdx.y]];
     const int b = blockIdx.z;
     const int r = d.r, w = d.w;
-    const int c0 = kb * 32;
-    if (c0 >= w) return;
-    const int nbk = min(32, w - c0);
-    const int c1 = c0 + nbk;
-    const int m = r - c1;
-    if (m <= 0) return;
-    const int64_t nt = (m + 127) / 128;
-    const int64_t tile = blockIdx.x;
-    if (tile >= nt * (nt + 1) / 2) return;
-    int64_t ti = (int64_t)((sqrt(8.0 * (double)tile + 1.0) - 1.0) * 0.5);
-    while (ti * (ti + 1) / 2 > tile) --ti;
-    while ((ti + 1) * (ti + 2) / 2 <= tile) ++ti;
-    const int64_t tj = tile - ti * (ti + 1) / 2;
-    const int i0 = c1 + (int)ti * 128, j0 = c1 + (int)tj * 128;
-    float* Pb = panel + (int64_t)b * panel_total + d.panel_off;
-    float* Ub = upd + (int64_t)b * upd_total + d.upd_off;
-    const int ru = r - w;
+    if (d.tc_off < 0) return;
+    int k1, jlo, jhi, i0, j0;
+    if (!tc_update_tile(r, w, k0, nk, jend, blockIdx.x, k1, jlo, jhi, i0, j0)) return;
+    const bool diag = i0 == j0;
+    const int cfirst = (k0 - kpack0) >> 4;
+    const float* pk = pack + (int64_t)b * pack_total + d.tc_off + (int64_t)cfirst * 4096;
+    const float* Ablk = pk + (int64_t)(i0 >> 7) * kTcTileFloats;
+    const float* Bblk = pk + (int64_t)(j0 >> 7) * kTcTileFloats;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + kTcStages * kTcStageBytes);
+    uint64_t* empty = full + kTcStages;
+    uint64_t* accb = empty + kTcStages;
+    uint32_t* slot = reinterpret_cast<uint32_t*>(accb + 1);
+    volatile int32_t* abort_flag = reinterpret_cast<volatile int32_t*>(slot + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    unsigned char* Ah = smem_raw;
-    unsigned char* Al = smem_raw + 16384;
-    unsigned char* Bh = smem_raw + 32768;
-    unsigned char* Bl = smem_raw + 49152;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + 65536);
-    uint32_t* slot = reinterpret_cast<uint32_t*>(smem_raw + 65536 + 16);
-    const bool diag = ti == tj;
-    for (int e = tid; e < 128 * 32; e += 128) {
-        const int mm = e & 127, k = e >> 7;
-        const int ra = i0 + mm;
-        const float x = (ra < r && k < nbk) ? Pb[(int64_t)(c0 + k) * r + ra] : 0.f;
-        const float h = tc::to_tf32(x);
-        const uint32_t off = tc::kmajor_offset(mm, k, 128);
-        *reinterpret_cast<float*>(Ah + off) = h;
-        *reinterpret_cast<float*>(Al + off) = x - h;
-        if (!diag) {
-            const int rb = j0 + mm;
-            const float y = (rb < r && k < nbk) ? Pb[(int64_t)(c0 + k) * r + rb] : 0.f;
-            const float g = tc::to_tf32(y);
-            *reinterpret_cast<float*>(Bh + off) = g;
-            *reinterpret_cast<float*>(Bl + off) = y - g;
-        }
-    }
-    if (warp == 0) {
+    const int nq = (k1 - k0 + 15) / 16;
+    if (warp == 8) {
         tc::tmem_alloc(slot, 128);
         tc::tmem_relinquish();
     }
     if (tid == 0) {
-        tc::mbar_init(bar, 1);
+        for (int s = 0; s < kTcStages; ++s) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], 1);
+        }
+        tc::mbar_init(accb, 1);
+        *abort_flag = 0;
         tc::mbar_init_fence();
     }
-    tc::fence_proxy_async_smem();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t taddr = *slot;
-    const uint32_t lbo = 16 * 128, sbo = 128;
-    if (tid == 0) {
-        const uint32_t idesc = tc::idesc_tf32(128, 128);
-        const unsigned char* bh = diag ? Ah : Bh;
-        const unsigned char* bl = diag ? Al : Bl;
-        for (int s = 0; s < 4; ++s) {
-            const uint32_t koff = (uint32_t)s * 2 * lbo;
-            const uint64_t dah = tc::smem_desc_kmajor(Ah + koff, lbo, sbo);
-            const uint64_t dal = tc::smem_desc_kmajor(Al + koff, lbo, sbo);
-            const uint64_t dbh = tc::smem_desc_kmajor(bh + koff, lbo, sbo);
-            const uint64_t dbl = tc::smem_desc_kmajor(bl + koff, lbo, sbo);
-            tc::mma_tf32(taddr, dah, dbh, idesc, s > 0 ? 1u : 0u);
-            tc::mma_tf32(taddr, dah, dbl, idesc, 1u);
-            tc::mma_tf32(taddr, dal, dbh, idesc, 1u);
+    const int ru = r - w;
+    float* Pb = panel + (int64_t)b * panel_total + d.panel_off;
+    float* Ub = upd + (int64_t)b * upd_total + d.upd_off;
+    if (warp == 8) {
+        if (lane == 0) {
+            const uint32_t idesc = tc::idesc_tf32(128, 128);
+            const uint32_t lbo = 16 * 128, sbo = 128;
+            const uint32_t bytes = diag ? 16384u : 32768u;
+            bool ok = true;
+            int issued = 0, consumed = 0;
+            for (int c = 0; c < nq + kTcStages - 1; ++c) {
+                const int cm = c - (kTcStages - 1);
+                if (cm >= 0) {
+                    const int s = cm % kTcStages;
+                    if (!tc::mbar_wait(&full[s], (uint32_t)(cm / kTcStages) & 1u, kTcWaitPolls)) {
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    const unsigned char* ah = smem_raw + s * kTcStageBytes;
+                    const unsigned char* al = ah + 8192;
+                    const unsigned char* bh = diag ? ah : ah + 16384;
+                    const unsigned char* bl = diag ? al : ah + 24576;
+#pragma unroll
+                    for (int s8 = 0; s8 < 2; ++s8) {
+                        const uint32_t koff = (uint32_t)s8 * 2 * lbo;
+                        const uint64_t dah = tc::smem_desc_kmajor(ah + koff, lbo, sbo);
+                        const uint64_t dal = tc::smem_desc_kmajor(al + koff, lbo, sbo);
+                        const uint64_t dbh = tc::smem_desc_kmajor(bh + koff, lbo, sbo);
+                        const uint64_t dbl = tc::smem_desc_kmajor(bl + koff, lbo, sbo);
+                        tc::mma_tf32(taddr, dah, dbh, idesc, (cm > 0 || s8 > 0) ? 1u : 0u);
+                        tc::mma_tf32(taddr, dah, dbl, idesc, 1u);
+                        tc::mma_tf32(taddr, dal, dbh, idesc, 1u);
+                    }
+                    tc::mma_commit(&empty[s]);
+                    consumed = cm + 1;
+                }
+                if (c < nq) {
+                    const int s = c % kTcStages;
+                    if (c >= kTcStages &&
+                        !tc::mbar_wait(&empty[s], (uint32_t)(c / kTcStages - 1) & 1u, kTcWaitPolls)) {
+                        ok = false;
+                        break;
+                    }
+                    unsigned char* st = smem_raw + s * kTcStageBytes;
+                    tc::mbar_arrive_expect_tx(&full[s], bytes);
+                    tc::bulk_g2s(st, Ablk + (int64_t)c * 4096, 16384u, &full[s]);
+                    if (!diag) tc::bulk_g2s(st + 16384, Bblk + (int64_t)c * 4096, 16384u, &full[s]);
+                    issued = c + 1;
+                }
+            }
+            if (ok) {
+                tc::mma_commit(accb);
+            } else {
+                atomicExch(dev_err, 1);
+                *abort_flag = 1;
+                for (int cm = consumed; cm < issued; ++cm)
+                    tc::mbar_wait(&full[cm % kTcStages], (uint32_t)(cm / kTcStages) & 1u, kTcWaitPolls);
+                if (consumed > 0)
+                    tc::mbar_wait(&empty[(consumed - 1) % kTcStages],
+                                  (uint32_t)((consumed - 1) / kTcStages) & 1u, kTcWaitPolls);
+                tc::mbar_arrive(accb);
+            }
         }
-        tc::mma_commit(bar);
-    }
-    __syncwarp();
-    bool ok = tc::mbar_wait(bar, 0, 1u << 24);
-    if (!ok) {
-        if (lane == 0) atomicExch(dev_err, 1);
-        ok = tc::mbar_wait(bar, 0, 1u << 24);
-    }
-    tc::fence_after_sync();
-    if (ok) {
-        const int i = i0 + 32 * warp + lane;
-        for (int c = 0; c < 128; c += 8) {
-            float v[8];
-            tc::tmem_ld8(taddr + ((uint32_t)(32 * warp) << 16) + (uint32_t)c, v);
+        __syncwarp();
+    } else {
+        const int lq = warp & 3, ch = warp >> 2;
+        const int i = i0 + 32 * lq + lane;
+        bool ok = true;
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+            const int jb = j0 + 64 * ch + 32 * h;
+            float cv[32];
+#pragma unroll
+            for (int c = 0; c < 32; ++c) {
+                const int j = jb + c;
+                cv[c] = 0.f;
+                if (i < r && j <= i && j >= jlo && j < jhi)
+                    cv[c] = j < w ? Pb[(int64_t)j * r + i] : Ub[(int64_t)(j - w) * ru + (i - w)];
+            }
+            if (h == 0) {
+                if (!tc::mbar_wait(accb, 0, kTcWaitPolls)) {
+                    ok = false;
+                    if (lane == 0) atomicExch(dev_err, 1);
+                }
+                ok = __all_sync(0xffffffffu, ok && *abort_flag == 0);
+                tc::fence_after_sync();
+            }
+            if (!ok) break;
+            float v[4][8];
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                tc::tmem_ld8(taddr + ((uint32_t)(32 * lq) << 16) + (uint32_t)(64 * ch + 32 * h + 8 * c), v[c]);
             tc::tmem_ld_wait();
             if (i < r) {
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int j = j0 + c + q;
-                    if (j < r && j <= i) {
+                for (int c = 0; c < 32; ++c) {
+                    const int j = jb + c;
+                    if (j <= i && j >= jlo && j < jhi) {
                         if (j < w)
-                            Pb[(int64_t)j * r + i] -= v[q];
+                            Pb[(int64_t)j * r + i] = cv[c] - v[c >> 3][c & 7];
                         else
-                            Ub[(int64_t)(j - w) * ru + (i - w)] -= v[q];
+                            Ub[(int64_t)(j - w) * ru + (i - w)] = cv[c] - v[c >> 3][c & 7];
                     }
                 }
             }
@@ -912,7 +1074,7 @@ __global__ void __launch_bounds__(128) k_big_update_tc(const DevTables t, const 
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    if (warp == 0) tc::tmem_dealloc(taddr, 128);
+    if (warp == 8) tc::tmem_dealloc(taddr, 128);
 }
 
 // Factor the 32x32 diagonal block of column block kb, one warp per front.
@@ -961,7 +1123,8 @@ __global__ void __launch_bounds__(32) k_big_potrf(const DevTables t, const int32
 // 256 rows per CTA, one row per thread.
 template <class T>
 __global__ void __launch_bounds__(256) k_big_trsm(const DevTables t, const int32_t* __restrict__ list, int kb,
-                                                  T* __restrict__ panel, int64_t panel_total) {
+                                                  T* __restrict__ panel, int64_t panel_total,
+                                                  float* __restrict__ pack, int64_t pack_total, int kpack0) {
     const FrontDesc d = t.fronts[list[blockIdx.y]];
     const int b = blockIdx.z;
     const int r = d.r, w = d.w;
@@ -995,33 +1158,43 @@ __global__ void __launch_bounds__(256) k_big_trsm(const DevTables t, const int32
 #pragma unroll
     for (int j = 0; j < 32; ++j)
         if (j < nbk) Pb[(int64_t)(c0 + j) * r + row] = x[j];
+    if (sizeof(T) == 4 && pack && d.tc_off >= 0) {
+        // The step's two 16-column operand chunks for the tensor-core
+        // updates (columns past nbk are zero).
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float* blk = tc_block(pack, pack_total, d, b, row, ((c0 - kpack0) >> 4) + h);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float4 hi, lo;
+                float* ph = &hi.x;
+                float* pl = &lo.x;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const float xv = (float)x[16 * h + 4 * q + u];
+                    ph[u] = tc::to_tf32(xv);
+                    pl[u] = xv - ph[u];
+                }
+                const int g = 128 * q + (row & 127);
+                reinterpret_cast<float4*>(blk)[g] = hi;
+                reinterpret_cast<float4*>(blk + 2048)[g] = lo;
+            }
+        }
+    }
 }
 
-// Right-looking trailing update after column block kb of a big front:
-// F[i, j] -= sum_{l in block} L[i, c0+l] L[j, c0+l] for c1 <= j <= i < r,
-// where F's column j is the panel column j (j < w) or update-matrix column
-// j - w (j >= w).  CTA tile 64x64 of the trailing lower triangle, inner
-// dimension = the block's <= 32 columns, 256 threads, 4x4 per thread.
+// SIMT update of a big front (FP64, or FP32 without tensor cores): the
+// update of big_update_tile, CTA tile 64x64, 256 threads with 4x4 each,
+// the inner dimension k1 - k0 consumed in 32-column shared-memory chunks.
 template <class T>
-__global__ void __launch_bounds__(256) k_big_update(const DevTables t, const int32_t* __restrict__ list, int kb,
-                                                    T* __restrict__ panel, int64_t panel_total,
+__global__ void __launch_bounds__(256) k_big_update(const DevTables t, const int32_t* __restrict__ list, int k0,
+                                                    int nk, int jend, T* __restrict__ panel, int64_t panel_total,
                                                     T* __restrict__ upd, int64_t upd_total) {
     const FrontDesc d = t.fronts[list[blockIdx.y]];
     const int b = blockIdx.z;
     const int r = d.r, w = d.w;
-    const int c0 = kb * 32;
-    if (c0 >= w) return;
-    const int nbk = min(32, w - c0);
-    const int c1 = c0 + nbk;
-    const int m = r - c1;
-    if (m <= 0) return;
-    const int64_t nt = (m + 63) / 64;
-    const int64_t tile = blockIdx.x;
-    if (tile >= nt * (nt + 1) / 2) return;
-    int64_t ti = (int64_t)((sqrt(8.0 * (double)tile + 1.0) - 1.0) * 0.5);
-    while (ti * (ti + 1) / 2 > tile) --ti;
-    while ((ti + 1) * (ti + 2) / 2 <= tile) ++ti;
-    const int64_t tj = tile - ti * (ti + 1) / 2;
+    int k1, jhi, i0, j0;
+    if (!big_update_tile(r, w, k0, nk, jend, 64, blockIdx.x, k1, jhi, i0, j0)) return;
     T* Pb = panel + (int64_t)b * panel_total + d.panel_off;
     T* Ub = upd + (int64_t)b * upd_total + d.upd_off;
     const int ru = r - w;
@@ -1029,38 +1202,41 @@ __global__ void __launch_bounds__(256) k_big_update(const DevTables t, const int
     __shared__ T Bs[32][64 + 1];
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
-    const int i0 = c1 + (int)ti * 64, j0 = c1 + (int)tj * 64;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const int e = tid + q * 256;
-        const int mm = e & 63, kk = e >> 6;
-        const int ra = i0 + mm, rb = j0 + mm;
-        As[kk][mm] = (ra < r && kk < nbk) ? Pb[(int64_t)(c0 + kk) * r + ra] : T(0);
-        Bs[kk][mm] = (rb < r && kk < nbk) ? Pb[(int64_t)(c0 + kk) * r + rb] : T(0);
-    }
-    __syncthreads();
     T acc[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int c = 0; c < 4; ++c) acc[a][c] = T(0);
-#pragma unroll 8
-    for (int kk = 0; kk < 32; ++kk) {
-        T a[4], bv[4];
+    for (int kc = k0; kc < k1; kc += 32) {
+        const int nbk = min(32, k1 - kc);
+        if (kc > k0) __syncthreads();
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            a[q] = As[kk][tx + 16 * q];
-            bv[q] = Bs[kk][ty + 16 * q];
+        for (int q = 0; q < 8; ++q) {
+            const int e = tid + q * 256;
+            const int mm = e & 63, kk = e >> 6;
+            const int ra = i0 + mm, rb = j0 + mm;
+            As[kk][mm] = (ra < r && kk < nbk) ? Pb[(int64_t)(kc + kk) * r + ra] : T(0);
+            Bs[kk][mm] = (rb < r && kk < nbk) ? Pb[(int64_t)(kc + kk) * r + rb] : T(0);
         }
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < 32; ++kk) {
+            T a[4], bv[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
+            for (int q = 0; q < 4; ++q) {
+                a[q] = As[kk][tx + 16 * q];
+                bv[q] = Bs[kk][ty + 16 * q];
+            }
 #pragma unroll
-            for (int p = 0; p < 4; ++p) acc[q][p] += a[q] * bv[p];
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int p = 0; p < 4; ++p) acc[q][p] += a[q] * bv[p];
+        }
     }
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
         const int j = j0 + ty + 16 * p;
-        if (j >= r) continue;
+        if (j >= jhi) continue;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int i = i0 + tx + 16 * q;
@@ -1069,6 +1245,90 @@ __global__ void __launch_bounds__(256) k_big_update(const DevTables t, const int
                 Pb[(int64_t)j * r + i] -= acc[q][p];
             else
                 Ub[(int64_t)(j - w) * ru + (i - w)] -= acc[q][p];
+        }
+    }
+}
+
+// FP32 SIMT trailing update: CTA tile 128x128, 256 threads with 8x8 each
+// (rows 4 + 4 and columns 4 + 4, read from shared memory as float4 with one
+// wavefront per warp read), inner dimension in 16-column chunks, the next
+// chunk's global loads in flight while the current one is multiplied.
+__global__ void __launch_bounds__(256, 2) k_big_update_f32(const DevTables t, const int32_t* __restrict__ list,
+                                                           int k0, int nk, int jend, float* __restrict__ panel,
+                                                           int64_t panel_total, float* __restrict__ upd,
+                                                           int64_t upd_total) {
+    const FrontDesc d = t.fronts[list[blockIdx.y]];
+    const int b = blockIdx.z;
+    const int r = d.r, w = d.w;
+    int k1, jhi, i0, j0;
+    if (!big_update_tile(r, w, k0, nk, jend, 128, blockIdx.x, k1, jhi, i0, j0)) return;
+    float* Pb = panel + (int64_t)b * panel_total + d.panel_off;
+    float* Ub = upd + (int64_t)b * upd_total + d.upd_off;
+    const int ru = r - w;
+    __shared__ __align__(16) float As[2][16][128];
+    __shared__ __align__(16) float Bs[2][16][128];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int ra0 = (warp & 1) * 64 + (lane & 7) * 4;   // rows ra0 + {0..3}, ra0 + 32 + {0..3}
+    const int cb0 = (warp >> 1) * 32 + (lane >> 3) * 4;  // columns cb0 + {0..3}, cb0 + 16 + {0..3}
+    const int lm = tid & 127, lk = tid >> 7;              // loader: row lm, chunk columns lk + 2u
+    float la[8], lb[8];
+    const bool ain = i0 + lm < r, bin = j0 + lm < r;
+    auto gload = [&](int kc) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int kk = kc + lk + 2 * u;
+            const bool kin = kk < k1;
+            la[u] = (kin && ain) ? Pb[(int64_t)kk * r + i0 + lm] : 0.f;
+            lb[u] = (kin && bin) ? Pb[(int64_t)kk * r + j0 + lm] : 0.f;
+        }
+    };
+    auto sstore = [&](int buf) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            As[buf][lk + 2 * u][lm] = la[u];
+            Bs[buf][lk + 2 * u][lm] = lb[u];
+        }
+    };
+    float acc[8][8];
+#pragma unroll
+    for (int p = 0; p < 8; ++p)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[p][q] = 0.f;
+    const int nq = (k1 - k0 + 15) / 16;
+    gload(k0);
+    sstore(0);
+    __syncthreads();
+    for (int q = 0; q < nq; ++q) {
+        const int buf = q & 1;
+        if (q + 1 < nq) gload(k0 + 16 * (q + 1));
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][ra0]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][ra0 + 32]);
+            const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][kk][cb0]);
+            const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][kk][cb0 + 16]);
+            const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int p = 0; p < 8; ++p)
+#pragma unroll
+                for (int c = 0; c < 8; ++c) acc[p][c] += a[p] * bv[c];
+        }
+        if (q + 1 < nq) sstore(buf ^ 1);
+        __syncthreads();
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const int j = j0 + cb0 + (c & 3) + 16 * (c >> 2);
+        if (j >= jhi) continue;
+#pragma unroll
+        for (int p = 0; p < 8; ++p) {
+            const int i = i0 + ra0 + (p & 3) + 32 * (p >> 2);
+            if (i >= r || i < j) continue;
+            if (j < w)
+                Pb[(int64_t)j * r + i] -= acc[p][c];
+            else
+                Ub[(int64_t)(j - w) * ru + (i - w)] -= acc[p][c];
         }
     }
 }
@@ -1634,6 +1894,83 @@ Work work_tiny(const Plan& P, bool solve) {
     return w;
 }
 
+// Host mirror of big_update_tile (ts > 0) or tc_update_tile (ts = 0): tiles
+// of one front's update, and the update's multiply-adds (entries x K) and
+// algorithmic bytes.
+struct UpdShape {
+    int64_t tiles = 0;
+    double entries = 0, k = 0, rows = 0;
+};
+static UpdShape update_shape(const FrontDesc& d, int k0, int nk, int jend, int ts) {
+    UpdShape u;
+    if (k0 >= d.w) return u;
+    const int k1 = std::min(k0 + nk, d.w), jlo = k1;
+    const int jhi = jend < 0 ? d.r : std::min(jend, d.w);
+    if (jhi <= jlo) return u;
+    int64_t nrt, nct;
+    if (ts > 0) {
+        nrt = (d.r - jlo + ts - 1) / ts;
+        nct = (jhi - jlo + ts - 1) / ts;
+    } else {
+        nrt = (d.r + 127) / 128 - jlo / 128;
+        nct = (jhi + 127) / 128 - jlo / 128;
+    }
+    u.tiles = jend < 0 ? nrt * (nrt + 1) / 2 : nrt * nct;
+    const double nc = jhi - jlo, m = d.r - jlo;
+    u.entries = nc * m - nc * (nc - 1) / 2;
+    u.k = k1 - k0;
+    u.rows = m;
+    return u;
+}
+
+// Tensor-core operand blocks of a big-front level are written (by
+// k_big_trsm) and used when the factor is FP32, tensor cores are enabled and
+// the panel block fits the blocks' chunk slots.
+inline bool tc_level(const Plan& P, int tsize, int SB) {
+    return tsize == 4 && P.tune.use_tc && P.tc_pack_total > 0 && SB <= kTcMaxPanel;
+}
+
+// One update of every front of a big-front level (see big_update_tile):
+// F[i, j] -= L[i, k0:k1) L[j, k0:k1)^T; tensor cores (operand blocks of the
+// panel block starting at column kpack0) for FP32 when enabled, SIMT
+// otherwise.
+template <class T>
+void launch_big_update(Plan& P, const LaunchList& ll, const int32_t* list, int kpack0, int k0, int nk, int jend,
+                       T* panel, T* upd, bool tc, cudaStream_t s) {
+    const int B = P.B;
+    const bool tcore = tc && (ll.rmax - k0) >= P.tune.tc_min_rows;
+    const bool wide = sizeof(T) == 4 && jend < 0;
+    const int ts = tcore ? 0 : (wide ? 128 : 64);
+    int64_t tiles = 0;
+    double fl = 0, by = 0;
+    for (int32_t q = 0; q < ll.count; ++q) {
+        const UpdShape u = update_shape(P.fronts[P.front_lists[ll.list_off + q]], k0, nk, jend, ts);
+        tiles = std::max(tiles, u.tiles);
+        fl += 2 * u.entries * u.k;
+        by += (2 * u.entries + u.rows * u.k) * P.tsize;
+    }
+    if (tiles == 0) return;
+    if (tcore) {
+        Prof pu(P, s, SSCO_K_BIG_UPDATE_TC);
+        k_big_update_tc<<<dim3((unsigned)tiles, ll.count, B), 288, kTcSmem, s>>>(
+            P.dt, list, kpack0, k0, nk, jend, wsp<float>(P, P.ws.tcpack), P.tc_pack_total,
+            reinterpret_cast<float*>(panel), P.panel_total, reinterpret_cast<float*>(upd), P.upd_total,
+            wsp<int32_t>(P, P.ws.dev_err));
+        if (pu.ev >= 0) pu.done(fl * B, by * B);
+    } else if (wide) {
+        Prof pu(P, s, SSCO_K_BIG_GEMM);
+        k_big_update_f32<<<dim3((unsigned)tiles, ll.count, B), 256, 0, s>>>(
+            P.dt, list, k0, nk, jend, reinterpret_cast<float*>(panel), P.panel_total, reinterpret_cast<float*>(upd),
+            P.upd_total);
+        if (pu.ev >= 0) pu.done(fl * B, by * B);
+    } else {
+        Prof pu(P, s, SSCO_K_BIG_GEMM);
+        k_big_update<T><<<dim3((unsigned)tiles, ll.count, B), 256, 0, s>>>(P.dt, list, k0, nk, jend, panel,
+                                                                          P.panel_total, upd, P.upd_total);
+        if (pu.ev >= 0) pu.done(fl * B, by * B);
+    }
+}
+
 template <class T>
 int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cudaStream_t s) {
     const int B = P.B;
@@ -1702,7 +2039,7 @@ int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cud
         }
         {
             Prof pr(P, s, SSCO_K_BIG_INIT);
-            k_big_init<T><<<dim3((unsigned)ll.max_lower_tiles, ll.count, B), dim3(32, 8), 0, s>>>(
+            k_big_init<T><<<dim3((unsigned)ll.max_lower_tiles, ll.count, B), 256, 0, s>>>(
                 P.dt, list, panel, P.panel_total, upd, P.upd_total);
             if (pr.ev >= 0) {
                 double by = 0;
@@ -1729,86 +2066,54 @@ int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cud
                 pr.done(0, by * B);
             }
         }
-        const int nkb = (ll.wmax + 31) / 32;
-        for (int kb = 0; kb < nkb; ++kb) {
-            const int c0 = kb * 32;
-            {
-                Prof pd(P, s, SSCO_K_BIG_POTRF);
-                k_big_potrf<T><<<dim3(ll.count, B), 32, 0, s>>>(P.dt, list, kb, panel, P.panel_total, bad, P.n_pats);
-                if (pd.ev >= 0) {
-                    double fl = 0, by = 0;
-                    for (int32_t q = 0; q < ll.count; ++q) {
-                        const FrontDesc& d = P.fronts[P.front_lists[ll.list_off + q]];
-                        if (c0 >= d.w) continue;
-                        double nbk = std::min(32, d.w - c0);
-                        fl += nbk * nbk * nbk / 3;
-                        by += nbk * nbk * P.tsize;
+        // Panel blocks of P.tune.big_panel columns: each 32-column step is
+        // factored (potrf, trsm) and applied only to the rest of its block
+        // (narrow update, K = 32); the finished block then updates the whole
+        // trailing triangle in one pass with K = big_panel, so the trailing
+        // entries are read and written once per block instead of once per
+        // 32 columns.
+        const int SB = std::max(32, P.tune.big_panel / 32 * 32);
+        const bool tc = tc_level(P, (int)sizeof(T), SB);
+        for (int C0 = 0; C0 < ll.wmax; C0 += SB) {
+            const int Cend = C0 + SB;
+            for (int c0 = C0; c0 < std::min(Cend, (int)ll.wmax); c0 += 32) {
+                const int kb = c0 / 32;
+                {
+                    Prof pd(P, s, SSCO_K_BIG_POTRF);
+                    k_big_potrf<T><<<dim3(ll.count, B), 32, 0, s>>>(P.dt, list, kb, panel, P.panel_total, bad,
+                                                                     P.n_pats);
+                    if (pd.ev >= 0) {
+                        double fl = 0, by = 0;
+                        for (int32_t q = 0; q < ll.count; ++q) {
+                            const FrontDesc& d = P.fronts[P.front_lists[ll.list_off + q]];
+                            if (c0 >= d.w) continue;
+                            double nbk = std::min(32, d.w - c0);
+                            fl += nbk * nbk * nbk / 3;
+                            by += nbk * nbk * P.tsize;
+                        }
+                        pd.done(fl * B, by * B);
                     }
-                    pd.done(fl * B, by * B);
                 }
-            }
-            Prof pr(P, s, SSCO_K_BIG_TRSM);
-            k_big_trsm<T><<<dim3(cdiv(ll.rmax - c0, 256), ll.count, B), 256, 0, s>>>(P.dt, list, kb, panel,
-                                                                                    P.panel_total);
-            if (pr.ev >= 0) {
-                double fl = 0, by = 0;
-                for (int32_t q = 0; q < ll.count; ++q) {
-                    const FrontDesc& d = P.fronts[P.front_lists[ll.list_off + q]];
-                    if (c0 >= d.w) continue;
-                    double nbk = std::min(32, d.w - c0), mrows = d.r - c0 - nbk;
-                    fl += mrows * nbk * nbk;
-                    by += 2 * (mrows + nbk) * nbk * P.tsize;
-                }
-                pr.done(fl * B, by * B);
-            }
-            int64_t tiles = 0;
-            for (int32_t q = 0; q < ll.count; ++q) {
-                const FrontDesc& d = P.fronts[P.front_lists[ll.list_off + q]];
-                if (c0 >= d.w) continue;
-                const int64_t mt = (d.r - c0 - std::min(32, d.w - c0) + 63) / 64;
-                tiles = std::max(tiles, mt * (mt + 1) / 2);
-            }
-            int64_t tiles128 = 0;
-            for (int32_t q = 0; q < ll.count; ++q) {
-                const FrontDesc& d = P.fronts[P.front_lists[ll.list_off + q]];
-                if (c0 >= d.w) continue;
-                const int64_t mt = (d.r - c0 - std::min(32, d.w - c0) + 127) / 128;
-                tiles128 = std::max(tiles128, mt * (mt + 1) / 2);
-            }
-            const bool tcore = sizeof(T) == 4 && P.tune.use_tc && tiles128 > 0 &&
-                               (ll.rmax - c0) >= P.tune.tc_min_rows;
-            if (tcore) {
-                Prof pu(P, s, SSCO_K_BIG_UPDATE_TC);
-                k_big_update_tc<<<dim3((unsigned)tiles128, ll.count, B), 128, kTcSmem, s>>>(
-                    P.dt, list, kb, reinterpret_cast<float*>(panel), P.panel_total, reinterpret_cast<float*>(upd),
-                    P.upd_total, wsp<int32_t>(P, P.ws.dev_err));
-                if (pu.ev >= 0) {
-                    double fl = 0, by = 0;
-                    for (int32_t q = 0; q < ll.count; ++q) {
-                        const FrontDesc& d = P.fronts[P.front_lists[ll.list_off + q]];
-                        if (c0 >= d.w) continue;
-                        double nbk = std::min(32, d.w - c0), m = d.r - c0 - nbk;
-                        fl += m * (m + 1) * nbk;
-                        by += (m * (m + 1) + 2 * m * nbk) * P.tsize;
+                {
+                    Prof pr(P, s, SSCO_K_BIG_TRSM);
+                    k_big_trsm<T><<<dim3(cdiv(ll.rmax - c0, 256), ll.count, B), 256, 0, s>>>(
+                        P.dt, list, kb, panel, P.panel_total, tc ? wsp<float>(P, P.ws.tcpack) : nullptr,
+                        P.tc_pack_total, C0);
+                    if (pr.ev >= 0) {
+                        double fl = 0, by = 0;
+                        for (int32_t q = 0; q < ll.count; ++q) {
+                            const FrontDesc& d = P.fronts[P.front_lists[ll.list_off + q]];
+                            if (c0 >= d.w) continue;
+                            double nbk = std::min(32, d.w - c0), mrows = d.r - c0 - nbk;
+                            fl += mrows * nbk * nbk;
+                            by += 2 * (mrows + nbk) * nbk * P.tsize;
+                        }
+                        pr.done(fl * B, by * B);
                     }
-                    pu.done(fl * B, by * B);
                 }
-            } else if (tiles > 0) {
-                Prof pu(P, s, SSCO_K_BIG_GEMM);
-                k_big_update<T><<<dim3((unsigned)tiles, ll.count, B), 256, 0, s>>>(P.dt, list, kb, panel,
-                                                                                  P.panel_total, upd, P.upd_total);
-                if (pu.ev >= 0) {
-                    double fl = 0, by = 0;
-                    for (int32_t q = 0; q < ll.count; ++q) {
-                        const FrontDesc& d = P.fronts[P.front_lists[ll.list_off + q]];
-                        if (c0 >= d.w) continue;
-                        double nbk = std::min(32, d.w - c0), m = d.r - c0 - nbk;
-                        fl += m * (m + 1) * nbk;
-                        by += (m * (m + 1) + 2 * m * nbk) * P.tsize;
-                    }
-                    pu.done(fl * B, by * B);
-                }
+                if (c0 + 32 < Cend) launch_big_update<T>(P, ll, list, C0, c0, 32, Cend, panel, upd, tc, s);
             }
+            launch_big_update<T>(P, ll, list, C0, C0, SB, -1, panel, upd, tc, s);
         }
     }
     return (int)cudaGetLastError();
@@ -2219,6 +2524,7 @@ int autotune(Plan& P, const void* vals, int32_t vdt, const double* shift, const 
         {&P.tune.vec_max_cls, {0, 64, 96}},
         {&P.tune.solve_threads_big, {256, 512}},
         {&P.tune.use_tc, {0, 1}},
+        {&P.tune.big_panel, {32, 64, 128, 256}},
     };
     double best = 0;
     e = measure(&best);

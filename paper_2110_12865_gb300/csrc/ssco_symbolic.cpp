@@ -203,6 +203,9 @@ ssco_status analyze_impl(const ssco_pattern* const* pats, int32_t n_pats, const 
     P.tiny_max = op->tiny_front_max == 0 ? 32 : (op->tiny_front_max < 0 ? 0 : std::min(op->tiny_front_max, 32));
     P.n_pats = n_pats;
     P.tune.use_tc = op->tensor_cores < 0 ? 0 : 1;
+    if (op->big_panel != 0 && (op->big_panel < 32 || op->big_panel > 1024 || op->big_panel % 32 != 0))
+        return bad(P, SSCO_ERR_INVALID_ARG, "big_panel must be 0 or a multiple of 32 in [32, 1024]");
+    if (op->big_panel > 0) P.tune.big_panel = op->big_panel;
 
     for (int k = 0; k < n_pats; ++k) {
         ssco_status s = validate(P, pats[k], k);
@@ -607,6 +610,7 @@ ssco_status analyze_impl(const ssco_pattern* const* pats, int32_t n_pats, const 
         for (int32_t k = 0; k < d.w; ++k) P.flops_numeric += (double)(d.r - k) * (d.r - k);
         d.relmap_off = -1;
         d.inv_off = -1;
+        d.tc_off = -1;
         d.nchild = 0;
     }
     // children lists (ascending child id)
@@ -772,14 +776,20 @@ ssco_status analyze_impl(const ssco_pattern* const* pats, int32_t n_pats, const 
             bl.level = L;
             bl.cls = -1;
             bl.list_off = (int64_t)P.front_lists.size();
+            int64_t tc_level = 0;
             for (int32_t F : fl) {
-                const FrontDesc& d = P.fronts[F];
+                FrontDesc& d = P.fronts[F];
                 if (d.r <= P.small_max) continue;
+                if (P.tsize == 4 && P.tune.use_tc) {
+                    d.tc_off = tc_level;
+                    tc_level += (int64_t)((d.r + 127) / 128) * kTcTileFloats;
+                    P.tc_pack_total = std::max(P.tc_pack_total, tc_level);
+                }
                 P.front_lists.push_back(F);
                 bl.count++;
                 bl.rmax = std::max(bl.rmax, d.r);
                 bl.wmax = std::max(bl.wmax, d.w);
-                int64_t t = (d.r + 31) / 32;
+                int64_t t = (d.r + 63) / 64;
                 bl.max_lower_tiles = std::max(bl.max_lower_tiles, t * (t + 1) / 2);
                 int64_t u = (d.r - d.w + 63) / 64;
                 bl.max_syrk_tiles = std::max(bl.max_syrk_tiles, u * (u + 1) / 2);
@@ -960,6 +970,7 @@ void compute_ws_layout(Plan& P) {
     w.st_shift = take(S * 8);
     w.st_b = take(B * n * 8);
     w.st_x = take(B * n * 8);
+    w.tcpack = take(B * (size_t)P.tc_pack_total * 4);
     w.total = off;
 }
 
