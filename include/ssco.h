@@ -101,7 +101,10 @@ typedef struct {
  * tensor_cores: 0 = FP32 trailing updates of multi-CTA fronts run on the
  *   tcgen05 tensor cores (3xTF32), -1 = SIMT FP32 only.
  * big_panel: columns of a multi-CTA front factored between two trailing
- *   updates (a multiple of 32 in [32, 1024]; 0 = default 128).        */
+ *   updates (a multiple of 32 in [32, 1024]; 0 = default 128).
+ * split_rows: fronts with at least this many rows (and more than
+ *   small_front_max) are solved by multi-CTA launches over 256-column
+ *   blocks (0 = default 1024, -1 = never).                           */
 typedef struct {
     int32_t precision;
     int32_t batch;
@@ -112,6 +115,7 @@ typedef struct {
     int32_t tiny_front_max;
     int32_t tensor_cores;
     int32_t big_panel;
+    int32_t split_rows;
 } ssco_op;
 
 /* Sizes and counts of an analyzed plan (all for the concatenated system). */
@@ -142,6 +146,7 @@ typedef struct {
     int64_t tuned;           /* 1 after a successful ssco_autotune           */
     int64_t tune_use_tc;     /* 1: FP32 big-front updates on tensor cores    */
     int64_t tune_big_panel;  /* big fronts: columns per trailing update      */
+    int64_t tune_split_rows; /* fronts this large take the multi-CTA solves  */
 } ssco_info;
 
 /* ssco_plan_export selectors (host copies; sizes in elements).          */

@@ -136,6 +136,7 @@ struct Tunables {
     int32_t use_tc = 1;            // FP32 big-front trailing updates on tcgen05 tensor cores
     int32_t tc_min_rows = 128;     // ... when the trailing extent reaches this many rows
     int32_t big_panel = 128;       // big fronts: columns per trailing-update block
+    int32_t split_rows = 1024;     // fronts with at least this many rows take the split solves
     int32_t tuned = 0;
 };
 

@@ -2119,6 +2119,281 @@ int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cud
     return (int)cudaGetLastError();
 }
 
+// --------------------------------------------------------------------------
+// a5': split solves of the largest fronts.  A level supplies only
+// (fronts x instances) CTAs to the kernels above, and near the root that is
+// a few dozen for fronts of millions of entries.  A front with r >=
+// split_rows is instead solved by a sequence of launches over 256-column
+// blocks, each spreading the block's dense update over many CTAs of 256
+// threads (one per 256 rows or columns); the CTA that owns the next block
+// then solves that block's 256 x 256 triangle, so each block costs one
+// launch.  Same arithmetic as the kernels above (blocked substitution with
+// the same factor), grouped differently.
+// --------------------------------------------------------------------------
+constexpr int kSplitCB = 256;
+
+// v[0 .. nrows) := L_bb^{-1} v for the diagonal block at (jb0, jb0); all
+// threads of the CTA take part.
+template <class T>
+__device__ void split_fwd_diag(const T* __restrict__ Pb, int r, int jb0, int nrows, T* v, T (*Ld)[33], T* dinv,
+                               T* yblk) {
+    const int tid = threadIdx.x, nth = blockDim.x;
+    for (int s = 0; s < nrows; s += 32) {
+        const int nbk = min(32, nrows - s);
+        stage_diag(Ld, dinv, Pb, r, jb0 + s, nbk, tid, nth);
+        __syncthreads();
+        if (tid < 32) {
+            const int l = tid;
+            T val = l < nbk ? v[s + l] : T(0);
+            for (int j = 0; j < nbk; ++j) {
+                const T yj = __shfl_sync(0xffffffffu, val, j) * dinv[j];
+                if (l == j) val = yj;
+                if (l > j) val -= Ld[l][j] * yj;
+            }
+            if (l < nbk) {
+                v[s + l] = val;
+                yblk[l] = val;
+            }
+        }
+        __syncthreads();
+        for (int i = s + nbk + tid; i < nrows; i += nth) {
+            const T* col = Pb + (int64_t)(jb0 + s) * r + jb0 + i;
+            T a0 = T(0), a1 = T(0);
+            int j = 0;
+            for (; j + 1 < nbk; j += 2) {
+                a0 += col[(int64_t)j * r] * yblk[j];
+                a1 += col[(int64_t)(j + 1) * r] * yblk[j + 1];
+            }
+            if (j < nbk) a0 += col[(int64_t)j * r] * yblk[j];
+            v[i] -= a0 + a1;
+        }
+        __syncthreads();
+    }
+}
+
+// x[0 .. ncols) := L_bb^{-T} x for the diagonal block at (jb0, jb0), x
+// holding the block's right-hand side with every row past the block
+// already applied; all threads of the CTA take part.
+template <class T>
+__device__ void split_bwd_diag(const T* __restrict__ Pb, int r, int jb0, int ncols, T* x, T (*Ld)[33], T* dinv,
+                               T* dots) {
+    const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nth >> 5;
+    for (int sb = (ncols + 31) / 32 - 1; sb >= 0; --sb) {
+        const int s = sb * 32, nbk = min(32, ncols - s);
+        stage_diag(Ld, dinv, Pb, r, jb0 + s, nbk, tid, nth);
+        for (int c = warp; c < nbk; c += nw) {
+            const T* col = Pb + (int64_t)(jb0 + s + c) * r + jb0;
+            T acc = T(0);
+            for (int i = s + nbk + lane; i < ncols; i += 32) acc += col[i] * x[i];
+            acc = warp_sum(acc);
+            if (lane == 0) dots[c] = acc;
+        }
+        __syncthreads();
+        if (tid < 32) {
+            const int l = tid;
+            T val = l < nbk ? x[s + l] - dots[l] : T(0);
+            for (int j = nbk - 1; j >= 0; --j) {
+                const T xj = __shfl_sync(0xffffffffu, val, j) * dinv[j];
+                if (l == j) val = xj;
+                if (l < j) val -= Ld[j][l] * xj;
+            }
+            if (l < nbk) x[s + l] = val;
+        }
+        __syncthreads();
+    }
+}
+
+// Forward, first launch: CTA p gathers rows 256p.. of the front's vector
+// (own right-hand side plus the children's passing vectors, pulled through
+// the inverse maps in child order); CTA 0 then solves column block 0.
+template <class T>
+__global__ void __launch_bounds__(256) k_fsplit_init(const DevTables t, const int32_t* __restrict__ list,
+                                                     const T* __restrict__ panel, int64_t panel_total,
+                                                     T* __restrict__ vec, int64_t n, T* __restrict__ pvec,
+                                                     int64_t pvec_total, const int32_t* __restrict__ active,
+                                                     int32_t n_pats) {
+    const FrontDesc d = t.fronts[list[blockIdx.y]];
+    const int b = blockIdx.z;
+    if (active && !active[(int64_t)b * n_pats + d.sys]) return;
+    const int r = d.r, w = d.w;
+    const int row0 = (int)blockIdx.x * kSplitCB;
+    if (row0 >= r) return;
+    __shared__ T v[kSplitCB];
+    __shared__ T Ld[32][33];
+    __shared__ T dinv[32], yblk[32];
+    __shared__ int64_t coff[32];
+    const int tid = threadIdx.x;
+    T* vb = vec + (int64_t)b * n;
+    T* pv = pvec + (int64_t)b * pvec_total;
+    const int i = row0 + tid;
+    T val = (i < r && i < w) ? vb[d.f + i] : T(0);
+    for (int cb = 0; cb < d.nchild; cb += 32) {
+        const int nc = min(32, d.nchild - cb);
+        __syncthreads();
+        if (tid < nc) coff[tid] = t.fronts[t.child_ids[d.child_off + cb + tid]].pvec_off;
+        __syncthreads();
+        if (i < r)
+            for (int c = 0; c < nc; ++c) {
+                const int a = t.invmap[d.inv_off + (int64_t)(cb + c) * r + i];
+                if (a >= 0) val += pv[coff[c] + a];
+            }
+    }
+    if (blockIdx.x == 0) {
+        v[tid] = val;
+        __syncthreads();
+        split_fwd_diag(panel + (int64_t)b * panel_total + d.panel_off, r, 0, min(kSplitCB, w), v, Ld, dinv, yblk);
+        val = v[tid];
+    }
+    if (i < r) {
+        if (i < w)
+            vb[d.f + i] = val;
+        else
+            pv[d.pvec_off + i - w] = val;
+    }
+}
+
+// Forward, column block k (columns c0 = 256k .. e): rows e .. r take
+// v_i -= L[i, c0:e) y, 256 rows per CTA; CTA 0 then solves block k + 1.
+template <class T>
+__global__ void __launch_bounds__(256) k_fsplit_step(const DevTables t, const int32_t* __restrict__ list, int k,
+                                                     const T* __restrict__ panel, int64_t panel_total,
+                                                     T* __restrict__ vec, int64_t n, T* __restrict__ pvec,
+                                                     int64_t pvec_total, const int32_t* __restrict__ active,
+                                                     int32_t n_pats) {
+    const FrontDesc d = t.fronts[list[blockIdx.y]];
+    const int b = blockIdx.z;
+    if (active && !active[(int64_t)b * n_pats + d.sys]) return;
+    const int r = d.r, w = d.w;
+    const int c0 = k * kSplitCB;
+    if (c0 >= w) return;
+    const int nbk = min(kSplitCB, w - c0), e = c0 + nbk;
+    const int row0 = e + (int)blockIdx.x * kSplitCB;
+    if (row0 >= r) return;
+    __shared__ T y[kSplitCB], v[kSplitCB];
+    __shared__ T Ld[32][33];
+    __shared__ T dinv[32], yblk[32];
+    const int tid = threadIdx.x;
+    T* vb = vec + (int64_t)b * n;
+    T* pv = pvec + (int64_t)b * pvec_total;
+    const T* Pb = panel + (int64_t)b * panel_total + d.panel_off;
+    if (tid < nbk) y[tid] = vb[d.f + c0 + tid];
+    __syncthreads();
+    const int i = row0 + tid;
+    T val = T(0);
+    if (i < r) {
+        val = i < w ? vb[d.f + i] : pv[d.pvec_off + i - w];
+        const T* col = Pb + (int64_t)c0 * r + i;
+        T acc[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc[u] = T(0);
+        int j = 0;
+        for (; j + 7 < nbk; j += 8) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc[u] += col[(int64_t)(j + u) * r] * y[j + u];
+        }
+        for (; j < nbk; ++j) acc[0] += col[(int64_t)j * r] * y[j];
+        val -= ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+    }
+    if (blockIdx.x == 0 && e < w) {
+        v[tid] = val;
+        __syncthreads();
+        split_fwd_diag(Pb, r, e, min(kSplitCB, w - e), v, Ld, dinv, yblk);
+        val = v[tid];
+    }
+    if (i < r) {
+        if (i < w)
+            vb[d.f + i] = val;
+        else
+            pv[d.pvec_off + i - w] = val;
+    }
+}
+
+// Backward, first launch: the solution at the update rows w .. r (the
+// parent's, final) is staged in shared memory; CTA p takes columns 256p..
+// x_j -= L[w:r, j]^T x[w:r] (warp per column); the CTA of the last column
+// block then solves it.
+template <class T>
+__global__ void __launch_bounds__(256) k_bsplit_init(const DevTables t, const int32_t* __restrict__ list,
+                                                     const T* __restrict__ panel, int64_t panel_total,
+                                                     T* __restrict__ vec, int64_t n,
+                                                     const int32_t* __restrict__ active, int32_t n_pats) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* xr = reinterpret_cast<T*>(smem_raw);
+    const FrontDesc d = t.fronts[list[blockIdx.y]];
+    const int b = blockIdx.z;
+    if (active && !active[(int64_t)b * n_pats + d.sys]) return;
+    const int r = d.r, w = d.w, ru = r - w;
+    const int col0 = (int)blockIdx.x * kSplitCB;
+    if (col0 >= w) return;
+    const int ncols = min(kSplitCB, w - col0);
+    __shared__ T xs[kSplitCB];
+    __shared__ T Ld[32][33];
+    __shared__ T dinv[32], dots[32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    T* vb = vec + (int64_t)b * n;
+    const T* Pb = panel + (int64_t)b * panel_total + d.panel_off;
+    const int32_t* rows = t.rows + d.rows_off;
+    for (int k = tid; k < ru; k += kSplitCB) xr[k] = vb[rows[w + k]];
+    __syncthreads();
+    for (int c = warp; c < ncols; c += kSplitCB / 32) {
+        const T* col = Pb + (int64_t)(col0 + c) * r + w;
+        T a0 = T(0), a1 = T(0);
+        int q = lane;
+        for (; q + 32 < ru; q += 64) {
+            a0 += col[q] * xr[q];
+            a1 += col[q + 32] * xr[q + 32];
+        }
+        if (q < ru) a0 += col[q] * xr[q];
+        const T s = warp_sum(a0 + a1);
+        if (lane == 0) xs[c] = vb[d.f + col0 + c] - s;
+    }
+    __syncthreads();
+    if (col0 + kSplitCB >= w) split_bwd_diag(Pb, r, col0, ncols, xs, Ld, dinv, dots);
+    if (tid < ncols) vb[d.f + col0 + tid] = xs[tid];
+}
+
+// Backward, column block k (rows c0 = 256k .. e hold final x): CTA p takes
+// columns 256p .. (< c0), x_j -= L[c0:e, j]^T x[c0:e] (warp per column);
+// the CTA of block k - 1 then solves it.
+template <class T>
+__global__ void __launch_bounds__(256) k_bsplit_step(const DevTables t, const int32_t* __restrict__ list, int k,
+                                                     const T* __restrict__ panel, int64_t panel_total,
+                                                     T* __restrict__ vec, int64_t n,
+                                                     const int32_t* __restrict__ active, int32_t n_pats) {
+    const FrontDesc d = t.fronts[list[blockIdx.y]];
+    const int b = blockIdx.z;
+    if (active && !active[(int64_t)b * n_pats + d.sys]) return;
+    const int r = d.r, w = d.w;
+    const int c0 = k * kSplitCB;
+    if (c0 >= w) return;
+    const int nbk = min(kSplitCB, w - c0);
+    const int col0 = (int)blockIdx.x * kSplitCB;
+    if (col0 >= c0) return;
+    __shared__ T xk[kSplitCB], xs[kSplitCB];
+    __shared__ T Ld[32][33];
+    __shared__ T dinv[32], dots[32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    T* vb = vec + (int64_t)b * n;
+    const T* Pb = panel + (int64_t)b * panel_total + d.panel_off;
+    if (tid < nbk) xk[tid] = vb[d.f + c0 + tid];
+    __syncthreads();
+    for (int c = warp; c < kSplitCB; c += kSplitCB / 32) {
+        const T* col = Pb + (int64_t)(col0 + c) * r + c0;
+        T a0 = T(0), a1 = T(0);
+        int q = lane;
+        for (; q + 32 < nbk; q += 64) {
+            a0 += col[q] * xk[q];
+            a1 += col[q + 32] * xk[q + 32];
+        }
+        if (q < nbk) a0 += col[q] * xk[q];
+        const T s = warp_sum(a0 + a1);
+        if (lane == 0) xs[c] = vb[d.f + col0 + c] - s;
+    }
+    __syncthreads();
+    if (col0 + kSplitCB == c0) split_bwd_diag(Pb, r, col0, kSplitCB, xs, Ld, dinv, dots);
+    vb[d.f + col0 + tid] = xs[tid];
+}
+
 // A level is solved warp-per-item when it supplies at least 8 warps per SM
 // and its fronts' vectors fit 8 to a CTA; otherwise one CTA per item.
 inline bool use_warp_solve(const Plan& P, const LaunchList& ll, int B) {
@@ -2126,6 +2401,105 @@ inline bool use_warp_solve(const Plan& P, const LaunchList& ll, int B) {
 }
 inline int solve_threads(const Plan& P, const LaunchList& ll) {
     return ll.rmax <= 128 ? 128 : (ll.rmax <= 512 ? 256 : P.tune.solve_threads_big);
+}
+
+// Leading fronts of a solve level (sorted by rows, largest first) that take
+// the split solves: r >= split_rows, a big front (inverse maps present) whose
+// update rows fit the backward kernel's shared memory.
+inline int split_count(const Plan& P, const LaunchList& ll) {
+    const int thr = std::max(P.tune.split_rows, P.small_max + 1);
+    int q = 0;
+    while (q < ll.count) {
+        const FrontDesc& d = P.fronts[P.front_lists[ll.list_off + q]];
+        if (d.r < thr || (d.nchild > 0 && d.inv_off < 0) || (size_t)(d.r - d.w) * P.tsize > 160 * 1024) break;
+        ++q;
+    }
+    return q;
+}
+
+template <class T>
+void run_split_fwd(Plan& P, const LaunchList& ll, int q, const int32_t* active, cudaStream_t s) {
+    const int B = P.B;
+    const int32_t* list = P.dt.front_lists + ll.list_off;
+    T* panel = wsp<T>(P, P.ws.panel);
+    T* vecT = wsp<T>(P, P.ws.vecT);
+    T* pvec = wsp<T>(P, P.ws.pvec);
+    int rmax = 0, wmax = 0;
+    double by0 = 0, fl0 = 0;
+    for (int f = 0; f < q; ++f) {
+        const FrontDesc& d = P.fronts[P.front_lists[ll.list_off + f]];
+        rmax = std::max(rmax, d.r);
+        wmax = std::max(wmax, d.w);
+        const double nb0 = std::min(kSplitCB, d.w);
+        fl0 += nb0 * nb0;
+        by0 += (nb0 * (nb0 + 1) / 2 + d.r * (2.0 + d.nchild)) * P.tsize + d.r * 4.0 * d.nchild;
+    }
+    {
+        Prof pr(P, s, SSCO_K_FWD);
+        k_fsplit_init<T><<<dim3(cdiv(rmax, kSplitCB), q, B), kSplitCB, 0, s>>>(
+            P.dt, list, panel, P.panel_total, vecT, P.n, pvec, P.pvec_total, active, P.n_pats);
+        if (pr.ev >= 0) pr.done(fl0 * B, by0 * B);
+    }
+    const int nb = cdiv(wmax, kSplitCB);
+    for (int k = 0; k < nb; ++k) {
+        int64_t g = 0;
+        double fl = 0, by = 0;
+        for (int f = 0; f < q; ++f) {
+            const FrontDesc& d = P.fronts[P.front_lists[ll.list_off + f]];
+            const int c0 = k * kSplitCB;
+            if (c0 >= d.w) continue;
+            const int e = std::min(c0 + kSplitCB, d.w);
+            g = std::max<int64_t>(g, cdiv(d.r - e, kSplitCB));
+            const double nbk = e - c0, m = d.r - e, nn = std::min(kSplitCB, d.w - e);
+            fl += 2 * m * nbk + (e < d.w ? nn * nn : 0);
+            by += (m * nbk + (e < d.w ? nn * (nn + 1) / 2 : 0) + 2 * m + nbk) * P.tsize;
+        }
+        if (g == 0) continue;
+        Prof pr(P, s, SSCO_K_FWD);
+        k_fsplit_step<T><<<dim3((unsigned)g, q, B), kSplitCB, 0, s>>>(P.dt, list, k, panel, P.panel_total, vecT,
+                                                                       P.n, pvec, P.pvec_total, active, P.n_pats);
+        if (pr.ev >= 0) pr.done(fl * B, by * B);
+    }
+}
+
+template <class T>
+void run_split_bwd(Plan& P, const LaunchList& ll, int q, const int32_t* active, cudaStream_t s) {
+    const int B = P.B;
+    const int32_t* list = P.dt.front_lists + ll.list_off;
+    T* panel = wsp<T>(P, P.ws.panel);
+    T* vecT = wsp<T>(P, P.ws.vecT);
+    int wmax = 0, rumax = 0;
+    double by0 = 0, fl0 = 0;
+    for (int f = 0; f < q; ++f) {
+        const FrontDesc& d = P.fronts[P.front_lists[ll.list_off + f]];
+        wmax = std::max(wmax, d.w);
+        rumax = std::max(rumax, d.r - d.w);
+        const double ru = d.r - d.w, nl = d.w - (double)((d.w - 1) / kSplitCB) * kSplitCB;
+        fl0 += 2 * ru * d.w + nl * nl;
+        by0 += (ru * d.w + nl * (nl + 1) / 2 + 2.0 * d.w + ru * cdiv(d.w, kSplitCB)) * P.tsize + ru * 4.0;
+    }
+    const int nb = cdiv(wmax, kSplitCB);
+    {
+        Prof pr(P, s, SSCO_K_BWD);
+        k_bsplit_init<T><<<dim3(nb, q, B), kSplitCB, (size_t)rumax * sizeof(T), s>>>(
+            P.dt, list, panel, P.panel_total, vecT, P.n, active, P.n_pats);
+        if (pr.ev >= 0) pr.done(fl0 * B, by0 * B);
+    }
+    for (int k = nb - 1; k >= 1; --k) {
+        double fl = 0, by = 0;
+        for (int f = 0; f < q; ++f) {
+            const FrontDesc& d = P.fronts[P.front_lists[ll.list_off + f]];
+            const int c0 = k * kSplitCB;
+            if (c0 >= d.w) continue;
+            const double nbk = std::min(kSplitCB, d.w - c0);
+            fl += 2 * nbk * c0 + (double)kSplitCB * kSplitCB;
+            by += (nbk * c0 + (double)kSplitCB * (kSplitCB + 1) / 2 + 2.0 * c0 + nbk) * P.tsize;
+        }
+        Prof pr(P, s, SSCO_K_BWD);
+        k_bsplit_step<T><<<dim3(k, q, B), kSplitCB, 0, s>>>(P.dt, list, k, panel, P.panel_total, vecT, P.n, active,
+                                                             P.n_pats);
+        if (pr.ev >= 0) pr.done(fl * B, by * B);
+    }
 }
 
 template <class T>
@@ -2145,7 +2519,16 @@ void run_trisolve(Plan& P, const int32_t* active, cudaStream_t s) {
             pr.done(w.flops, w.bytes);
         }
     }
-    for (const LaunchList& ll : P.solve_launches) {
+    for (const LaunchList& ll0 : P.solve_launches) {
+        LaunchList ll = ll0;
+        const int q = split_count(P, ll);
+        if (q > 0) {
+            run_split_fwd<T>(P, ll, q, active, s);
+            ll.list_off += q;
+            ll.count -= q;
+            if (ll.count == 0) continue;
+            ll.rmax = P.fronts[P.front_lists[ll.list_off]].r;
+        }
         Prof pr(P, s, SSCO_K_FWD);
         const size_t smem = (size_t)ll.rmax * sizeof(T);
         if (use_warp_solve(P, ll, B)) {
@@ -2162,7 +2545,15 @@ void run_trisolve(Plan& P, const int32_t* active, cudaStream_t s) {
         }
     }
     for (auto it = P.solve_launches.rbegin(); it != P.solve_launches.rend(); ++it) {
-        const LaunchList& ll = *it;
+        LaunchList ll = *it;
+        const int q = split_count(P, ll);
+        if (q > 0) {
+            run_split_bwd<T>(P, ll, q, active, s);
+            ll.list_off += q;
+            ll.count -= q;
+            if (ll.count == 0) continue;
+            ll.rmax = P.fronts[P.front_lists[ll.list_off]].r;
+        }
         Prof pr(P, s, SSCO_K_BWD);
         const size_t smem = (size_t)ll.rmax * sizeof(T);
         if (use_warp_solve(P, ll, B)) {
@@ -2376,6 +2767,7 @@ int set_attr_T() {
     if (!e) e = allow_dynamic_smem(k_bwd_warp<T>);
     if (!e) e = allow_dynamic_smem(k_fwd<T>);
     if (!e) e = allow_dynamic_smem(k_bwd<T>);
+    if (!e) e = allow_dynamic_smem(k_bsplit_init<T>);
     return e;
 }
 
@@ -2525,6 +2917,7 @@ int autotune(Plan& P, const void* vals, int32_t vdt, const double* shift, const 
         {&P.tune.solve_threads_big, {256, 512}},
         {&P.tune.use_tc, {0, 1}},
         {&P.tune.big_panel, {32, 64, 128, 256}},
+        {&P.tune.split_rows, {512, 1024, 2048, 4096, 1 << 30}},
     };
     double best = 0;
     e = measure(&best);

@@ -206,6 +206,8 @@ ssco_status analyze_impl(const ssco_pattern* const* pats, int32_t n_pats, const 
     if (op->big_panel != 0 && (op->big_panel < 32 || op->big_panel > 1024 || op->big_panel % 32 != 0))
         return bad(P, SSCO_ERR_INVALID_ARG, "big_panel must be 0 or a multiple of 32 in [32, 1024]");
     if (op->big_panel > 0) P.tune.big_panel = op->big_panel;
+    if (op->split_rows < -1) return bad(P, SSCO_ERR_INVALID_ARG, "split_rows must be >= -1");
+    if (op->split_rows != 0) P.tune.split_rows = op->split_rows < 0 ? (1 << 30) : op->split_rows;
 
     for (int k = 0; k < n_pats; ++k) {
         ssco_status s = validate(P, pats[k], k);

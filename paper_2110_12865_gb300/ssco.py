@@ -55,7 +55,7 @@ class Op(C.Structure):
     _fields_ = [("precision", C.c_int32), ("batch", C.c_int32), ("refine_tol", C.c_double),
                 ("refine_max_iter", C.c_int32), ("small_front_max", C.c_int32),
                 ("amalgamate", C.c_int32), ("tiny_front_max", C.c_int32), ("tensor_cores", C.c_int32),
-                ("big_panel", C.c_int32)]
+                ("big_panel", C.c_int32), ("split_rows", C.c_int32)]
 
 
 class KernelStat(C.Structure):
@@ -70,7 +70,7 @@ class Info(C.Structure):
                  "n_assembly_groups", "assembly_terms", "tables_bytes", "workspace_bytes"]] + \
               [("factor_flops", C.c_double), ("factor_flops_exact", C.c_double)] + \
               [(k, C.c_int64) for k in ["tune_warp_items", "tune_vec_max_cls", "tune_solve_threads_big", "tuned",
-                                        "tune_use_tc", "tune_big_panel"]]
+                                        "tune_use_tc", "tune_big_panel", "tune_split_rows"]]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -144,7 +144,7 @@ class Plan:
 
     def __init__(self, problems, precision=FP64, batch=None, refine_tol=1e-10, refine_max_iter=30,
                  small_front_max=0, amalgamate=1, tiny_front_max=0, tensor_cores=0, big_panel=0,
-                 _handle=None):
+                 split_rows=0, _handle=None):
         self.L = load_library()
         if _handle is not None:
             self._h = _handle
@@ -183,6 +183,7 @@ class Plan:
             op.tiny_front_max = tiny_front_max
             op.tensor_cores = tensor_cores
             op.big_panel = big_panel
+            op.split_rows = split_rows
             h = C.c_void_p()
             st = self.L.ssco_analyze(arr, len(pats), C.byref(op), C.byref(h))
             if st != SSCO_OK:
@@ -297,7 +298,7 @@ class Plan:
         self.info = inf.as_dict()
         return best.value, {k: self.info[k] for k in ("tune_warp_items", "tune_vec_max_cls",
                                                       "tune_solve_threads_big", "tune_use_tc",
-                                                      "tune_big_panel")}
+                                                      "tune_big_panel", "tune_split_rows")}
 
     def graph_run(self, vals: torch.Tensor, shift: torch.Tensor, b: torch.Tensor, x: torch.Tensor, stream=None):
         """numeric + solve as one captured CUDA graph (re-captured when the

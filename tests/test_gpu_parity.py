@@ -109,6 +109,28 @@ def test_fp32_factor_accuracy_big_fronts(S, tc):
     assert worst <= 2e-4, worst
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_split_solves_uneven_patterns(S, prec):
+    """Multi-CTA split solves (split_rows far below the largest fronts, so
+    fronts of several widths, one with more than one 256-column block, share
+    the split launches of a level) over three patterns of uneven size, two
+    value sets each: every system meets the residual bound, and in FP64 the
+    solution equals the one-CTA-per-front solve's to 1e-12."""
+    probs = [P.elasticity_problem(10, batch=2), P.elasticity_problem(5, batch=2), P.grid_problem(24, 20, batch=2)]
+    precision = S.FP64 if prec == "fp64" else S.FP32_REFINE
+    pl, x, st, *_ = run(S, probs, precision, small_front_max=32, split_rows=40)
+    assert pl.info["max_front_rows"] > 256
+    off = 0
+    for k, p in enumerate(probs):
+        for inst in range(2):
+            check_against_oracle(S, pl, p, x, st, inst, inst * 3 + k, col_off=off)
+        off += p.n
+    if prec == "fp64":
+        _, x_ref, st_ref, *_ = run(S, probs, precision, small_front_max=32, split_rows=-1)
+        assert np.all(st_ref["status"] == 0)
+        assert np.max(np.abs(x - x_ref)) <= 1e-12 * np.max(np.abs(x_ref))
+
+
 @pytest.mark.parametrize("seed", range(6))
 def test_fp64_random_patterns(S, seed):
     rng = np.random.default_rng(900 + seed)
