@@ -101,7 +101,7 @@ typedef struct {
  * tensor_cores: 0 = FP32 trailing updates of multi-CTA fronts run on the
  *   tcgen05 tensor cores (3xTF32), -1 = SIMT FP32 only.
  * big_panel: columns of a multi-CTA front factored between two trailing
- *   updates (a multiple of 32 in [32, 1024]; 0 = default 128).
+ *   updates (a multiple of 32 in [32, 1024]; 0 = default 256).
  * split_rows: fronts with at least this many rows (and more than
  *   small_front_max) are solved by multi-CTA launches over 256-column
  *   blocks (0 = default 1024, -1 = never).                           */

@@ -499,14 +499,30 @@ __global__ void __launch_bounds__(256) k_front_vec(const DevTables t, const int3
 // --------------------------------------------------------------------------
 constexpr int kTinyWarps = 8;
 
-// Shared-memory bytes per warp of the tiny kernels.
+// Shared memory of the tiny kernels: each warp's own area (the front and
+// K values, or the solve vector) and the subtree program.  With a batch that
+// is a multiple of kTinyWarps, the warps of a CTA take the same subtree for
+// consecutive value sets and share one copy of its program (loaded once per
+// CTA instead of once per warp); otherwise each warp has its own.
+inline bool tiny_share(int32_t B) { return B % kTinyWarps == 0; }
+__host__ __device__ inline int tiny_prog_bytes(int prog_max) { return (prog_max * 4 + 15) & ~15; }
 template <class T>
-__host__ __device__ inline int tiny_factor_warp_bytes(int prog_max, int k_max) {
-    return ((32 * 33 + k_max) * (int)sizeof(T) + prog_max * 4 + 15) & ~15;
+__host__ __device__ inline int tiny_factor_own(int k_max) {
+    return ((32 * 33 + k_max) * (int)sizeof(T) + 15) & ~15;
 }
 template <class T>
-__host__ __device__ inline int tiny_solve_warp_bytes(int prog_max) {
-    return (32 * (int)sizeof(T) + prog_max * 4 + 15) & ~15;
+__host__ __device__ inline int tiny_solve_own() {
+    return (32 * (int)sizeof(T) + 15) & ~15;
+}
+template <class T>
+inline int tiny_factor_bytes(bool share, int prog_max, int k_max) {
+    return share ? tiny_prog_bytes(prog_max) + kTinyWarps * tiny_factor_own<T>(k_max)
+                 : kTinyWarps * (tiny_factor_own<T>(k_max) + tiny_prog_bytes(prog_max));
+}
+template <class T>
+inline int tiny_solve_bytes(bool share, int prog_max) {
+    return share ? tiny_prog_bytes(prog_max) + kTinyWarps * tiny_solve_own<T>()
+                 : kTinyWarps * (tiny_solve_own<T>() + tiny_prog_bytes(prog_max));
 }
 
 // Loads subtree st's program into shared memory (coalesced).
@@ -515,6 +531,24 @@ __device__ __forceinline__ void load_prog(const DevTables& t, int st, int32_t* p
     const int total = (int)(t.tiny_prog_off[st + 1] - base);
     for (int i = lane; i < total; i += 32) prog[i] = t.tiny_prog[base + i];
     __syncwarp();
+}
+// Program of this warp's subtree in shared memory, and the warp's own area
+// of `own` bytes: a CTA-wide copy (share) or one per warp.
+__device__ __forceinline__ int32_t* tiny_setup(const DevTables& t, unsigned char* smem_raw, bool share, int st,
+                                               int prog_max, int own, int wib, int lane, unsigned char** mine) {
+    if (share) {
+        int32_t* prog = reinterpret_cast<int32_t*>(smem_raw);
+        const int64_t base = t.tiny_prog_off[st];
+        const int total = (int)(t.tiny_prog_off[st + 1] - base);
+        for (int i = threadIdx.x; i < total; i += blockDim.x) prog[i] = t.tiny_prog[base + i];
+        __syncthreads();
+        *mine = smem_raw + tiny_prog_bytes(prog_max) + (size_t)wib * own;
+        return prog;
+    }
+    *mine = smem_raw + (size_t)wib * (own + tiny_prog_bytes(prog_max));
+    int32_t* prog = reinterpret_cast<int32_t*>(*mine + own);
+    load_prog(t, st, prog, lane);
+    return prog;
 }
 
 __device__ __forceinline__ int64_t prog_i64(const int32_t* rec, int at) {
@@ -569,18 +603,18 @@ template <class T>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2)
     k_tiny_factor(const DevTables t, int32_t n_tiny, int32_t B, int32_t prog_max, int32_t k_max,
                   const double* __restrict__ K, int64_t nnzK, T* __restrict__ panel, int64_t panel_total,
-                  T* __restrict__ upd, int64_t upd_total, int32_t* __restrict__ bad_col, int32_t n_pats) {
+                  T* __restrict__ upd, int64_t upd_total, int32_t* __restrict__ bad_col, int32_t n_pats,
+                  int32_t share) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t item = (int64_t)blockIdx.x * kTinyWarps + wib;
-    if (item >= (int64_t)n_tiny * B) return;
+    if (!share && item >= (int64_t)n_tiny * B) return;
     const int st = (int)(item / B), b = (int)(item % B);
-    unsigned char* mine = smem_raw + (size_t)wib * tiny_factor_warp_bytes<T>(prog_max, k_max);
+    unsigned char* mine;
+    int32_t* prog = tiny_setup(t, smem_raw, share != 0, st, prog_max, tiny_factor_own<T>(k_max), wib, lane, &mine);
     T(*F)[33] = reinterpret_cast<T(*)[33]>(mine);
     T* Fflat = reinterpret_cast<T*>(mine);
     T* kv = reinterpret_cast<T*>(mine) + 32 * 33;
-    int32_t* prog = reinterpret_cast<int32_t*>(kv + k_max);
-    load_prog(t, st, prog, lane);
     const int nf = prog[0], nk = prog[1], rec_off = prog[2], k_off = prog[4], sys = prog[7];
     const double* Kb = K + (int64_t)b * nnzK;
     for (int e = lane; e < nk; e += 32) kv[e] = (T)Kb[prog[k_off + 2 * e]];
@@ -629,11 +663,15 @@ __device__ __forceinline__ T tiny_fwd_chain(const T* __restrict__ Pf, int lane, 
     T a[W];
 #pragma unroll
     for (int j = 0; j < W; ++j) a[j] = (j < w && lane < r) ? Pf[(int64_t)j * r + lane] : T(0);
+    T dl = T(1);
+#pragma unroll
+    for (int j = 0; j < W; ++j)
+        if (lane == j && j < w) dl = a[j];
+    const T dinv = T(1) / dl;
 #pragma unroll
     for (int j = 0; j < W; ++j) {
         if (j < w) {
-            const T djj = __shfl_sync(0xffffffffu, a[j], j);
-            const T yj = __shfl_sync(0xffffffffu, v, j) / djj;
+            const T yj = __shfl_sync(0xffffffffu, v, j) * __shfl_sync(0xffffffffu, dinv, j);
             if (lane == j)
                 v = yj;
             else if (lane > j)
@@ -648,12 +686,17 @@ __device__ __forceinline__ T tiny_bwd_chain(const T* __restrict__ Pf, int lane, 
     T a[W];
 #pragma unroll
     for (int j = 0; j < W; ++j) a[j] = (j < w && lane < r) ? Pf[(int64_t)j * r + lane] : T(0);
+    T dl = T(1);
+#pragma unroll
+    for (int j = 0; j < W; ++j)
+        if (lane == j && j < w) dl = a[j];
+    const T dinv = T(1) / dl;
 #pragma unroll
     for (int j = W - 1; j >= 0; --j) {
         if (j < w) {
             T s = (lane > j && lane < r) ? a[j] * v : T(0);
             s = warp_sum(s);
-            if (lane == j) v = (v - s) / a[j];
+            if (lane == j) v = (v - s) * dinv;
         }
     }
     return v;
@@ -664,16 +707,15 @@ __global__ void __launch_bounds__(256) k_tiny_fwd(const DevTables t, int32_t n_t
                                                   const T* __restrict__ panel, int64_t panel_total,
                                                   T* __restrict__ vec, int64_t n, T* __restrict__ pvec,
                                                   int64_t pvec_total, const int32_t* __restrict__ active,
-                                                  int32_t n_pats) {
+                                                  int32_t n_pats, int32_t share) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t item = (int64_t)blockIdx.x * kTinyWarps + wib;
-    if (item >= (int64_t)n_tiny * B) return;
+    if (!share && item >= (int64_t)n_tiny * B) return;
     const int st = (int)(item / B), b = (int)(item % B);
-    unsigned char* mine = smem_raw + (size_t)wib * tiny_solve_warp_bytes<T>(prog_max);
+    unsigned char* mine;
+    int32_t* prog = tiny_setup(t, smem_raw, share != 0, st, prog_max, tiny_solve_own<T>(), wib, lane, &mine);
     T* vs = reinterpret_cast<T*>(mine);
-    int32_t* prog = reinterpret_cast<int32_t*>(vs + 32);
-    load_prog(t, st, prog, lane);
     const int nf = prog[0], rec_off = prog[2];
     if (active && !active[(int64_t)b * n_pats + prog[7]]) return;
     const T* Pb = panel + (int64_t)b * panel_total;
@@ -710,15 +752,14 @@ template <class T>
 __global__ void __launch_bounds__(256) k_tiny_bwd(const DevTables t, int32_t n_tiny, int32_t B, int32_t prog_max,
                                                   const T* __restrict__ panel, int64_t panel_total,
                                                   T* __restrict__ vec, int64_t n, const int32_t* __restrict__ active,
-                                                  int32_t n_pats) {
+                                                  int32_t n_pats, int32_t share) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t item = (int64_t)blockIdx.x * kTinyWarps + wib;
-    if (item >= (int64_t)n_tiny * B) return;
+    if (!share && item >= (int64_t)n_tiny * B) return;
     const int st = (int)(item / B), b = (int)(item % B);
-    unsigned char* mine = smem_raw + (size_t)wib * tiny_solve_warp_bytes<T>(prog_max);
-    int32_t* prog = reinterpret_cast<int32_t*>(reinterpret_cast<T*>(mine) + 32);
-    load_prog(t, st, prog, lane);
+    unsigned char* mine;
+    int32_t* prog = tiny_setup(t, smem_raw, share != 0, st, prog_max, tiny_solve_own<T>(), wib, lane, &mine);
     const int nf = prog[0], rec_off = prog[2];
     if (active && !active[(int64_t)b * n_pats + prog[7]]) return;
     const T* Pb = panel + (int64_t)b * panel_total;
@@ -1511,12 +1552,16 @@ __global__ void __launch_bounds__(256) k_fwd_warp(const DevTables t, const int32
         T a[32];
 #pragma unroll
         for (int j = 0; j < 32; ++j) a[j] = (j < nbk && lane < nbk) ? Pb[(int64_t)(jb + j) * r + jb + lane] : T(0);
+        T dl = T(1);
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+            if (lane == j && j < nbk) dl = a[j];
+        const T dinv = T(1) / dl;
         T val = lane < nbk ? v[jb + lane] : T(0);
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
             if (j < nbk) {
-                const T dj = __shfl_sync(0xffffffffu, a[j], j);
-                const T yj = __shfl_sync(0xffffffffu, val, j) / dj;
+                const T yj = __shfl_sync(0xffffffffu, val, j) * __shfl_sync(0xffffffffu, dinv, j);
                 if (lane == j)
                     val = yj;
                 else if (lane > j)
@@ -2007,10 +2052,11 @@ int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cud
     if (P.n_tiny > 0) {
         Prof pr(P, s, SSCO_K_FRONT_TINY);
         const int64_t items = (int64_t)P.n_tiny * B;
+        const bool share = tiny_share(B);
         k_tiny_factor<T><<<cdiv(items, kTinyWarps), 32 * kTinyWarps,
-                           kTinyWarps * tiny_factor_warp_bytes<T>(P.tiny_prog_max, P.tiny_k_max), s>>>(
+                           tiny_factor_bytes<T>(share, P.tiny_prog_max, P.tiny_k_max), s>>>(
             P.dt, P.n_tiny, B, P.tiny_prog_max, P.tiny_k_max, K, P.nnzK, panel, P.panel_total, upd, P.upd_total, bad,
-            P.n_pats);
+            P.n_pats, share ? 1 : 0);
         if (pr.ev >= 0) {
             Work w = work_tiny(P, false);
             pr.done(w.flops, w.bytes);
@@ -2511,9 +2557,9 @@ void run_trisolve(Plan& P, const int32_t* active, cudaStream_t s) {
     const unsigned tiny_grid = cdiv((int64_t)P.n_tiny * B, kTinyWarps);
     if (P.n_tiny > 0) {
         Prof pr(P, s, SSCO_K_FWD);
-        k_tiny_fwd<T><<<tiny_grid, 32 * kTinyWarps, kTinyWarps * tiny_solve_warp_bytes<T>(P.tiny_prog_max), s>>>(
+        k_tiny_fwd<T><<<tiny_grid, 32 * kTinyWarps, tiny_solve_bytes<T>(tiny_share(B), P.tiny_prog_max), s>>>(
             P.dt, P.n_tiny, B, P.tiny_prog_max, panel, P.panel_total, vecT, P.n, pvec, P.pvec_total, active,
-            P.n_pats);
+            P.n_pats, tiny_share(B) ? 1 : 0);
         if (pr.ev >= 0) {
             Work w = work_tiny(P, true);
             pr.done(w.flops, w.bytes);
@@ -2571,8 +2617,9 @@ void run_trisolve(Plan& P, const int32_t* active, cudaStream_t s) {
     }
     if (P.n_tiny > 0) {
         Prof pr(P, s, SSCO_K_BWD);
-        k_tiny_bwd<T><<<tiny_grid, 32 * kTinyWarps, kTinyWarps * tiny_solve_warp_bytes<T>(P.tiny_prog_max), s>>>(
-            P.dt, P.n_tiny, B, P.tiny_prog_max, panel, P.panel_total, vecT, P.n, active, P.n_pats);
+        k_tiny_bwd<T><<<tiny_grid, 32 * kTinyWarps, tiny_solve_bytes<T>(tiny_share(B), P.tiny_prog_max), s>>>(
+            P.dt, P.n_tiny, B, P.tiny_prog_max, panel, P.panel_total, vecT, P.n, active, P.n_pats,
+            tiny_share(B) ? 1 : 0);
         if (pr.ev >= 0) {
             Work w = work_tiny(P, true);
             pr.done(w.flops, w.bytes);
@@ -3032,9 +3079,9 @@ int launch_solve_static(Plan& P, const double* b, double* x, void* stream) {
     P.launches += 2;
     const unsigned tiny_grid = cdiv((int64_t)P.n_tiny * B, kTinyWarps);
     if (P.n_tiny > 0) {
-        k_tiny_fwd<double><<<tiny_grid, 32 * kTinyWarps, kTinyWarps * tiny_solve_warp_bytes<double>(P.tiny_prog_max),
-                             s>>>(P.dt, P.n_tiny, B, P.tiny_prog_max, panel, P.panel_total, vec, n, pvec,
-                                  P.pvec_total, nullptr, P.n_pats);
+        k_tiny_fwd<double><<<tiny_grid, 32 * kTinyWarps, tiny_solve_bytes<double>(false, P.tiny_prog_max), s>>>(
+            P.dt, P.n_tiny, B, P.tiny_prog_max, panel, P.panel_total, vec, n, pvec, P.pvec_total, nullptr, P.n_pats,
+            0);
         P.launches++;
     }
     for (const LaunchList& ll : P.solve_launches) {
@@ -3049,9 +3096,8 @@ int launch_solve_static(Plan& P, const double* b, double* x, void* stream) {
         P.launches++;
     }
     if (P.n_tiny > 0) {
-        k_tiny_bwd<double><<<tiny_grid, 32 * kTinyWarps, kTinyWarps * tiny_solve_warp_bytes<double>(P.tiny_prog_max),
-                             s>>>(P.dt, P.n_tiny, B, P.tiny_prog_max, panel, P.panel_total, vec, n, nullptr,
-                                  P.n_pats);
+        k_tiny_bwd<double><<<tiny_grid, 32 * kTinyWarps, tiny_solve_bytes<double>(false, P.tiny_prog_max), s>>>(
+            P.dt, P.n_tiny, B, P.tiny_prog_max, panel, P.panel_total, vec, n, nullptr, P.n_pats, 0);
         P.launches++;
     }
     k_permute_out<<<gv, 256, 0, s>>>(vec, P.dt.perm, n, x);
