@@ -557,7 +557,10 @@ __device__ __forceinline__ int64_t prog_i64(const int32_t* rec, int at) {
 
 // Partial Cholesky of one front of at most R rows held as lane-per-row
 // registers (a[k] = F[lane][k]); writes the r x w panel and the (r-w)^2
-// update.  Returns the first non-positive pivot's column or -1.
+// update.  Compact form: the pivot column is always a[0] and the registers
+// shift left by one per step, so the step loop is a runtime loop (code size
+// O(R) instead of O(R^2)).  Returns the first non-positive pivot's column
+// or -1.
 template <class T, int R>
 __device__ __forceinline__ int tiny_chol_rows(T (*F)[33], int lane, int r, int w, T* __restrict__ Pf,
                                               T* __restrict__ Uf) {
@@ -565,42 +568,40 @@ __device__ __forceinline__ int tiny_chol_rows(T (*F)[33], int lane, int r, int w
 #pragma unroll
     for (int k = 0; k < R; ++k) a[k] = F[lane][k];
     int bad = -1;
-#pragma unroll
-    for (int j = 0; j < R; ++j) {
-        if (j < w) {
-            T djj = __shfl_sync(0xffffffffu, a[j], j);
-            if (!(djj > T(0))) {
-                if (bad < 0) bad = j;
-                djj = T(1);
-            }
-            const T ljj = sqrt(djj);
-            const T inv = T(1) / ljj;
-            if (lane == j)
-                a[j] = ljj;
-            else if (lane > j)
-                a[j] *= inv;
-#pragma unroll
-            for (int k = j + 1; k < R; ++k) {
-                if (k < r) {
-                    const T lkj = __shfl_sync(0xffffffffu, a[j], k);
-                    if (lane >= k) a[k] -= a[j] * lkj;
-                }
-            }
+#pragma unroll 1
+    for (int j = 0; j < w; ++j) {
+        T djj = __shfl_sync(0xffffffffu, a[0], j);
+        if (!(djj > T(0))) {
+            if (bad < 0) bad = j;
+            djj = T(1);
         }
+        const T ljj = sqrt(djj);
+        const T inv = T(1) / ljj;
+        if (lane == j)
+            a[0] = ljj;
+        else if (lane > j)
+            a[0] *= inv;
+        if (lane < r) Pf[(int64_t)j * r + lane] = lane >= j ? a[0] : T(0);
+#pragma unroll
+        for (int k = 1; k < R; ++k) {
+            const T lkj = __shfl_sync(0xffffffffu, a[0], (j + k) & 31);
+            if (lane >= j + k && j + k < r) a[k] -= a[0] * lkj;
+        }
+#pragma unroll
+        for (int k = 0; k < R - 1; ++k) a[k] = a[k + 1];
+        a[R - 1] = T(0);
     }
     if (lane < r) {
         const int ru = r - w;
 #pragma unroll
-        for (int k = 0; k < R; ++k) {
-            if (k < w) Pf[(int64_t)k * r + lane] = lane >= k ? a[k] : T(0);
-            if (k >= w && k < r && lane >= k) Uf[(int64_t)(k - w) * ru + (lane - w)] = a[k];
-        }
+        for (int k = 0; k < R; ++k)
+            if (k < ru && lane >= w + k) Uf[(int64_t)k * ru + (lane - w)] = a[k];
     }
     return bad;
 }
 
 template <class T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2)
+__global__ void __launch_bounds__(256, 2)
     k_tiny_factor(const DevTables t, int32_t n_tiny, int32_t B, int32_t prog_max, int32_t k_max,
                   const double* __restrict__ K, int64_t nnzK, T* __restrict__ panel, int64_t panel_total,
                   T* __restrict__ upd, int64_t upd_total, int32_t* __restrict__ bad_col, int32_t n_pats,
@@ -1118,9 +1119,14 @@ __global__ void __launch_bounds__(288, 2) k_big_update_tc(const DevTables t, con
     if (warp == 8) tc::tmem_dealloc(taddr, 128);
 }
 
-// Factor the 32x32 diagonal block of column block kb, one warp per front.
-// Its own launch: the triangular solve below must read the factored block,
-// and no CTA of one launch may overwrite what another CTA still has to load.
+// Factor the 32x32 diagonal block of column block kb, one warp per front,
+// lane i holding row i in registers.  Compact form: at step j the pivot
+// column is always a[0] (the row's registers shift left by one per step), so
+// the step loop is a runtime loop and only its 31-wide body is unrolled --
+// a few hundred instructions instead of a fully unrolled 32 x 32 nest, which
+// a one-warp launch would otherwise spend fetching.  Its own launch: the
+// triangular solve below must read the factored block, and no CTA of one
+// launch may overwrite what another CTA still has to load.
 template <class T>
 __global__ void __launch_bounds__(32) k_big_potrf(const DevTables t, const int32_t* __restrict__ list, int kb,
                                                   T* __restrict__ panel, int64_t panel_total,
@@ -1131,15 +1137,15 @@ __global__ void __launch_bounds__(32) k_big_potrf(const DevTables t, const int32
     const int c0 = kb * 32;
     if (c0 >= w) return;
     const int nbk = min(32, w - c0);
-    T* Pb = panel + (int64_t)b * panel_total + d.panel_off;
-    __shared__ T Ld[32][33];
+    T* Pb = panel + (int64_t)b * panel_total + d.panel_off + (int64_t)c0 * r + c0;
     const int i = threadIdx.x;
-    for (int j = 0; j < 32; ++j) Ld[i][j] = (i < nbk && j <= i) ? Pb[(int64_t)(c0 + j) * r + c0 + i] : T(0);
-    __syncwarp();
+    T a[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) a[k] = (i < nbk && k < nbk && k <= i) ? Pb[(int64_t)k * r + i] : T(0);
     bool failed = false;
+#pragma unroll 1
     for (int j = 0; j < nbk; ++j) {
-        T djj = Ld[j][j];
-        __syncwarp();
+        T djj = __shfl_sync(0xffffffffu, a[0], j);
         if (!(djj > T(0))) {
             if (i == 0 && !failed)
                 atomicMin(&bad_col[(int64_t)b * n_pats + d.sys], d.f + c0 + j - (int)t.sys_n_off[d.sys]);
@@ -1147,17 +1153,20 @@ __global__ void __launch_bounds__(32) k_big_potrf(const DevTables t, const int32
             djj = T(1);
         }
         const T ljj = sqrt(djj);
-        if (i > j && i < nbk) Ld[i][j] /= ljj;
-        if (i == j) Ld[j][j] = ljj;
-        __syncwarp();
-        if (i > j && i < nbk) {
-            const T lij = Ld[i][j];
-            for (int k = j + 1; k <= i; ++k) Ld[i][k] -= lij * Ld[k][j];
+        if (i == j)
+            a[0] = ljj;
+        else if (i > j)
+            a[0] /= ljj;
+        if (i >= j && i < nbk) Pb[(int64_t)j * r + i] = a[0];
+#pragma unroll
+        for (int k = 1; k < 32; ++k) {
+            const T lkj = __shfl_sync(0xffffffffu, a[0], (j + k) & 31);
+            if (i >= j + k) a[k] -= a[0] * lkj;
         }
-        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < 31; ++k) a[k] = a[k + 1];
+        a[31] = T(0);
     }
-    if (i < nbk)
-        for (int j = 0; j <= i; ++j) Pb[(int64_t)(c0 + j) * r + c0 + i] = Ld[i][j];
 }
 
 // Rows below the diagonal block of column block kb: X = P[rows, blk] L_kk^{-T},
