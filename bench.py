@@ -186,6 +186,27 @@ def measured_peaks():
         return None
 
 
+KERNEL_SOURCE = os.path.join(ROOT, "paper_2110_12865_gb300", "csrc", "ssco_kernels.cu")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def ncu_traffic(kind):
+    """DRAM bytes (read + write) per launch of kernel kind `kind`, from the
+    ncu capture recorded in profiles/traffic.json -- only while the kernel
+    source it was taken on is unchanged (sha256 of ssco_kernels.cu), else
+    None."""
+    import hashlib
+    try:
+        rec = json.load(open(TRAFFIC_FILE))
+        src = hashlib.sha256(open(KERNEL_SOURCE, "rb").read()).hexdigest()
+    except Exception:
+        return None
+    k = rec.get("kernels", {}).get(kind)
+    if not k or rec.get("source_sha256") != src:
+        return None
+    return k.get("dram_bytes_per_launch")
+
+
 # ---------------------------------------------------------------------------
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -333,17 +354,23 @@ def run_ours(args, rank, world, local_rank):
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "peak_source": ("measured bf16 (MEASURED_PEAKS.json) x 1.1/2.25" if peaks else "fallback") +
                                "; 3xTF32 issues three TF32 products per counted product (ceiling frac 1/3)"}
-    elif top in HBM_KINDS:
-        peak = peaks["hbm_gbs"] if peaks else HBM_FALLBACK_GBS
-        achieved = kv["bytes"] / (kv["ms"] / 1e3) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback"}
     else:
-        peak = FP32_SIMT_PEAK_TFLOPS
-        achieved = kv["flops"] / (kv["ms"] / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
-    roof.update({"frac": achieved / peak, "traffic": None, "kernel": top,
+        # Roofline model: the kernel's binding roof is HBM unless its
+        # algorithmic intensity times the HBM peak exceeds the SIMT peak.
+        hbm = peaks["hbm_gbs"] if peaks else HBM_FALLBACK_GBS
+        intensity = kv["flops"] / max(kv["bytes"], 1.0)
+        if top in HBM_KINDS or intensity * hbm / 1e3 < FP32_SIMT_PEAK_TFLOPS:
+            peak = hbm
+            achieved = kv["bytes"] / (kv["ms"] / 1e3) / 1e9
+            roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback"}
+        else:
+            peak = FP32_SIMT_PEAK_TFLOPS
+            achieved = kv["flops"] / (kv["ms"] / 1e3) / 1e12
+            roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
+        roof["intensity_flop_per_byte"] = intensity
+    roof.update({"frac": achieved / peak, "traffic": ncu_traffic(top), "kernel": top,
                  "launches": kv["launches"], "avg_launch_us": kv["ms"] * 1e3 / kv["launches"],
                  "measured": "CUDA events per launch on the launch stream, over a repeat of the timed steps"})
     out["roofline"] = roof

@@ -111,6 +111,10 @@ __global__ void k_fill_i32(int32_t* p, int64_t n, int32_t v) {
 // packed_col(k, r) + i - k.
 __device__ __forceinline__ int packed_col(int k, int r) { return k * r - ((k * (k - 1)) >> 1); }
 
+// Zero padding after a small front's packed triangle: the trailing update
+// reads up to 3 x 16 rows / 3 x 16 columns past the last entry.
+constexpr int kSmallPad = 128;
+
 template <class T>
 __global__ void __launch_bounds__(256) k_front_small(const DevTables t, const int32_t* __restrict__ list,
                                                      const double* __restrict__ K, int64_t nnzK,
@@ -124,7 +128,7 @@ __global__ void __launch_bounds__(256) k_front_small(const DevTables t, const in
     const int r = d.r, w = d.w;
     const int lane = threadIdx.x, warp = threadIdx.y, nw = blockDim.y;
     const int tid = lane + 32 * warp, nth = 32 * nw;
-    const int npk = r * (r + 1) / 2;
+    const int npk = r * (r + 1) / 2 + kSmallPad;
     for (int q = tid; q < npk; q += nth) F[q] = T(0);
     __syncthreads();
     const double* Kb = K + (int64_t)b * nnzK;
@@ -205,14 +209,20 @@ __global__ void __launch_bounds__(256) k_front_small(const DevTables t, const in
                         ii[a] = j1 + r0 + tx + 16 * a;
                         kk[a] = j1 + c0 + ty + ny * a;
                     }
+                    // Rows or columns past r read the next column's entries
+                    // or the zero padding (all within the allocation); they
+                    // only reach accumulators the epilogue skips.
+                    const T* Fi = F + packed_col(j0, r) - j0 + ii[0];
+                    const T* Fk = F + packed_col(j0, r) - j0 + kk[0];
                     for (int j = j0; j < j1; ++j) {
-                        const T* Fj = F + packed_col(j, r) - j;
                         T ra[4], cb[4];
 #pragma unroll
                         for (int a = 0; a < 4; ++a) {
-                            ra[a] = ii[a] < r ? Fj[ii[a]] : T(0);
-                            cb[a] = kk[a] < r ? Fj[kk[a]] : T(0);
+                            ra[a] = Fi[16 * a];
+                            cb[a] = Fk[ny * a];
                         }
+                        Fi += r - j - 1;
+                        Fk += r - j - 1;
 #pragma unroll
                         for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -2078,7 +2088,7 @@ int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cud
             const bool vec = ll.cls <= P.tune.vec_max_cls && B >= V;
             Prof pr(P, s, vec ? SSCO_K_FRONT_VEC : SSCO_K_FRONT_SMALL);
             const int nw = ll.cls <= 32 ? 2 : (ll.cls <= 64 ? 4 : 8);
-            const size_t smem = (size_t)ll.rmax * (ll.rmax + 1) / 2 * sizeof(T);
+            const size_t smem = ((size_t)ll.rmax * (ll.rmax + 1) / 2 + kSmallPad) * sizeof(T);
             if (vec)
                 k_front_vec<T, V><<<dim3(ll.count, (B + V - 1) / V), dim3(32, nw), smem * V, s>>>(
                     P.dt, list, B, K, P.nnzK, panel, P.panel_total, upd, P.upd_total, bad, P.n_pats);
