@@ -147,6 +147,7 @@ typedef struct {
     int64_t tune_use_tc;     /* 1: FP32 big-front updates on tensor cores    */
     int64_t tune_big_panel;  /* big fronts: columns per trailing update      */
     int64_t tune_split_rows; /* fronts this large take the multi-CTA solves  */
+    int64_t tune_warp_front_max; /* small-front classes factored warp-per-front */
 } ssco_info;
 
 /* ssco_plan_export selectors (host copies; sizes in elements).          */

@@ -137,6 +137,8 @@ struct Tunables {
     int32_t tc_min_rows = 128;     // ... when the trailing extent reaches this many rows
     int32_t big_panel = 256;       // big fronts: columns per trailing-update block
     int32_t split_rows = 1024;     // fronts with at least this many rows take the split solves
+    int32_t warp_front_max = 0;    // small-front classes up to this size: one warp per front (levels
+                                   // of >= warp_items fronts x value sets; autotuner option)
     int32_t tuned = 0;
 };
 

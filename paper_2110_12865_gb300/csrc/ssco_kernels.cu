@@ -256,6 +256,133 @@ __global__ void __launch_bounds__(256) k_front_small(const DevTables t, const in
     }
 }
 
+// Warp-per-(front, instance) variant of k_front_small for fronts of at most
+// 64 rows: each warp assembles and factors its own front in a packed lower
+// triangle in shared memory (rmax(rmax+1)/2 entries per warp), lane l
+// owning rows l and l + 32; column-by-column right-looking with warp
+// synchronisation only.  Eight fronts per CTA and no block barriers, for
+// levels of many small fronts with few value sets (where one CTA per front
+// spends its time in barriers).  Items are front-major.
+template <class T>
+__global__ void __launch_bounds__(256) k_front_warp(const DevTables t, const int32_t* __restrict__ list,
+                                                    int32_t count, int32_t B, int32_t rmax,
+                                                    const double* __restrict__ K, int64_t nnzK,
+                                                    T* __restrict__ panel, int64_t panel_total,
+                                                    T* __restrict__ upd, int64_t upd_total,
+                                                    int32_t* __restrict__ bad_col, int32_t n_pats) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t item = (int64_t)blockIdx.x * 8 + wib;
+    if (item >= (int64_t)count * B) return;
+    const int fi = (int)(item / B), b = (int)(item % B);
+    const FrontDesc d = t.fronts[list[fi]];
+    const int r = d.r, w = d.w;
+    T* F = reinterpret_cast<T*>(smem_raw) + (int64_t)wib * (rmax * (rmax + 1) / 2);
+    const int npk = r * (r + 1) / 2;
+    for (int q = lane; q < npk; q += 32) F[q] = T(0);
+    __syncwarp();
+    const double* Kb = K + (int64_t)b * nnzK;
+    const int32_t* kl = t.klist + 2 * d.klist_off;
+    for (int q = lane; q < d.klist_n; q += 32) {
+        const int pos = kl[2 * q + 1];
+        const int col = pos / r, row = pos - col * r;
+        F[packed_col(col, r) + row - col] = (T)Kb[kl[2 * q]];
+    }
+    for (int c = 0; c < d.nchild; ++c) {
+        __syncwarp();
+        const FrontDesc cd = t.fronts[t.child_ids[d.child_off + c]];
+        const int rc = cd.r - cd.w;
+        const int32_t* map = t.relmap + cd.relmap_off;
+        const T* S = upd + (int64_t)b * upd_total + cd.upd_off;
+        const int m0 = lane < rc ? map[lane] : 0, m1 = lane + 32 < rc ? map[lane + 32] : 0;
+        for (int kk = 0; kk < rc; ++kk) {
+            const int mk = __shfl_sync(0xffffffffu, kk < 32 ? m0 : m1, kk & 31);
+            T* Fk = F + packed_col(mk, r) - mk;
+            const T* Sk = S + (int64_t)kk * rc;
+            if (lane >= kk && lane < rc) Fk[m0] += Sk[lane];
+            if (lane + 32 >= kk && lane + 32 < rc) Fk[m1] += Sk[lane + 32];
+        }
+    }
+    __syncwarp();
+    // Panels of 8 columns: the panel's entries of the lane's two rows stay in
+    // registers (p0, p1), the other rows' by shuffle; each trailing entry is
+    // read and written once per panel.
+    constexpr int PB = 8;
+    bool failed = false;
+    const int i0 = lane, i1 = lane + 32;
+    for (int j0 = 0; j0 < w; j0 += PB) {
+        const int j1 = min(j0 + PB, w);
+        T p0[PB], p1[PB];
+#pragma unroll
+        for (int q = 0; q < PB; ++q) {
+            const int j = j0 + q;
+            T v0 = T(0), v1 = T(0);
+            if (j < j1) {
+                const T* Fj = F + packed_col(j, r) - j;
+                v0 = (i0 >= j && i0 < r) ? Fj[i0] : T(0);
+                v1 = (i1 >= j && i1 < r) ? Fj[i1] : T(0);
+                // left-looking within the panel: subtract the earlier panel
+                // columns (row j's entries come from the lane holding row j)
+#pragma unroll
+                for (int pq = 0; pq < q; ++pq) {
+                    const T ljp = __shfl_sync(0xffffffffu, j < 32 ? p0[pq] : p1[pq], j & 31);
+                    v0 -= p0[pq] * ljp;
+                    v1 -= p1[pq] * ljp;
+                }
+                T djj = __shfl_sync(0xffffffffu, j < 32 ? v0 : v1, j & 31);
+                if (!(djj > T(0))) {
+                    if (lane == 0 && !failed)
+                        atomicMin(&bad_col[(int64_t)b * n_pats + d.sys], d.f + j - (int)t.sys_n_off[d.sys]);
+                    failed = true;
+                    djj = T(1);
+                }
+                const T ljj = sqrt(djj);
+                const T inv = T(1) / ljj;
+                v0 = i0 == j ? ljj : (i0 > j ? v0 * inv : T(0));
+                v1 = i1 == j ? ljj : (i1 > j ? v1 * inv : T(0));
+                T* Fw = F + packed_col(j, r) - j;
+                if (i0 >= j && i0 < r) Fw[i0] = v0;
+                if (i1 >= j && i1 < r) Fw[i1] = v1;
+            }
+            p0[q] = v0;
+            p1[q] = v1;
+        }
+        // trailing update: F(i, k) -= sum_q L(i, j0+q) L(k, j0+q), k >= j1
+        for (int k = j1; k < r; ++k) {
+            T lk[PB];
+#pragma unroll
+            for (int q = 0; q < PB; ++q) lk[q] = __shfl_sync(0xffffffffu, k < 32 ? p0[q] : p1[q], k & 31);
+            T* Fk = F + packed_col(k, r) - k;
+            if (i0 >= k && i0 < r) {
+                T a = Fk[i0];
+#pragma unroll
+                for (int q = 0; q < PB; ++q) a -= p0[q] * lk[q];
+                Fk[i0] = a;
+            }
+            if (i1 >= k && i1 < r) {
+                T a = Fk[i1];
+#pragma unroll
+                for (int q = 0; q < PB; ++q) a -= p1[q] * lk[q];
+                Fk[i1] = a;
+            }
+        }
+        __syncwarp();
+    }
+    T* Pb = panel + (int64_t)b * panel_total + d.panel_off;
+    for (int jj = 0; jj < w; ++jj) {
+        const T* Fj = F + packed_col(jj, r) - jj;
+        for (int i = lane; i < r; i += 32) Pb[(int64_t)jj * r + i] = i >= jj ? Fj[i] : T(0);
+    }
+    const int ru = r - w;
+    if (ru > 0) {
+        T* Ub = upd + (int64_t)b * upd_total + d.upd_off;
+        for (int kk = 0; kk < ru; ++kk) {
+            const T* Fk = F + packed_col(w + kk, r) - (w + kk);
+            for (int ii = kk + lane; ii < ru; ii += 32) Ub[(int64_t)kk * ru + ii] = Fk[w + ii];
+        }
+    }
+}
+
 // Instance-vectorized variant of k_front_small for small fronts and batches:
 // one CTA factors the same front for V consecutive value sets, stored
 // interleaved ([packed index][V]) so that one 16-byte shared-memory access
@@ -2085,6 +2212,18 @@ int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cud
         const int32_t* list = P.dt.front_lists + ll.list_off;
         if (ll.cls > 0) {
             constexpr int V = sizeof(T) == 4 ? 4 : 2;
+            if (ll.cls <= P.tune.warp_front_max && ll.rmax <= 64 && (int64_t)ll.count * B >= P.tune.warp_items) {
+                Prof pr(P, s, SSCO_K_FRONT_SMALL);
+                const int64_t items = (int64_t)ll.count * B;
+                k_front_warp<T><<<cdiv(items, 8), 256, 8 * (size_t)ll.rmax * (ll.rmax + 1) / 2 * sizeof(T), s>>>(
+                    P.dt, list, ll.count, B, ll.rmax, K, P.nnzK, panel, P.panel_total, upd, P.upd_total, bad,
+                    P.n_pats);
+                if (pr.ev >= 0) {
+                    Work w = work_front_small(P, ll);
+                    pr.done(w.flops, w.bytes);
+                }
+                continue;
+            }
             const bool vec = ll.cls <= P.tune.vec_max_cls && B >= V;
             Prof pr(P, s, vec ? SSCO_K_FRONT_VEC : SSCO_K_FRONT_SMALL);
             const int nw = ll.cls <= 32 ? 2 : (ll.cls <= 64 ? 4 : 8);
@@ -2834,6 +2973,7 @@ int set_attr_T() {
     if (!e) e = allow_dynamic_smem(k_fwd<T>);
     if (!e) e = allow_dynamic_smem(k_bwd<T>);
     if (!e) e = allow_dynamic_smem(k_bsplit_init<T>);
+    if (!e) e = allow_dynamic_smem(k_front_warp<T>);
     return e;
 }
 
@@ -2984,6 +3124,7 @@ int autotune(Plan& P, const void* vals, int32_t vdt, const double* shift, const 
         {&P.tune.use_tc, {0, 1}},
         {&P.tune.big_panel, {32, 64, 128, 256}},
         {&P.tune.split_rows, {512, 1024, 2048, 4096, 1 << 30}},
+        {&P.tune.warp_front_max, {0, 32, 48, 64}},
     };
     double best = 0;
     e = measure(&best);

@@ -70,7 +70,8 @@ class Info(C.Structure):
                  "n_assembly_groups", "assembly_terms", "tables_bytes", "workspace_bytes"]] + \
               [("factor_flops", C.c_double), ("factor_flops_exact", C.c_double)] + \
               [(k, C.c_int64) for k in ["tune_warp_items", "tune_vec_max_cls", "tune_solve_threads_big", "tuned",
-                                        "tune_use_tc", "tune_big_panel", "tune_split_rows"]]
+                                        "tune_use_tc", "tune_big_panel", "tune_split_rows",
+                                        "tune_warp_front_max"]]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -298,7 +299,8 @@ class Plan:
         self.info = inf.as_dict()
         return best.value, {k: self.info[k] for k in ("tune_warp_items", "tune_vec_max_cls",
                                                       "tune_solve_threads_big", "tune_use_tc",
-                                                      "tune_big_panel", "tune_split_rows")}
+                                                      "tune_big_panel", "tune_split_rows",
+                                                      "tune_warp_front_max")}
 
     def graph_run(self, vals: torch.Tensor, shift: torch.Tensor, b: torch.Tensor, x: torch.Tensor, stream=None):
         """numeric + solve as one captured CUDA graph (re-captured when the
