@@ -104,7 +104,10 @@ typedef struct {
  *   updates (a multiple of 32 in [32, 1024]; 0 = default 256).
  * split_rows: fronts with at least this many rows (and more than
  *   small_front_max) are solved by multi-CTA launches over 256-column
- *   blocks (0 = default 1024, -1 = never).                           */
+ *   blocks (0 = default 1024, -1 = never).
+ * warp_front_max: small fronts of at most this many rows (<= 64) are
+ *   factored one warp per front on levels that supply at least 8 warps per
+ *   SM (0 = default off; ssco_autotune may switch it on).            */
 typedef struct {
     int32_t precision;
     int32_t batch;
@@ -116,6 +119,7 @@ typedef struct {
     int32_t tensor_cores;
     int32_t big_panel;
     int32_t split_rows;
+    int32_t warp_front_max;
 } ssco_op;
 
 /* Sizes and counts of an analyzed plan (all for the concatenated system). */

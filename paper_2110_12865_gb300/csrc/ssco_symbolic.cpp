@@ -208,6 +208,9 @@ ssco_status analyze_impl(const ssco_pattern* const* pats, int32_t n_pats, const 
     if (op->big_panel > 0) P.tune.big_panel = op->big_panel;
     if (op->split_rows < -1) return bad(P, SSCO_ERR_INVALID_ARG, "split_rows must be >= -1");
     if (op->split_rows != 0) P.tune.split_rows = op->split_rows < 0 ? (1 << 30) : op->split_rows;
+    if (op->warp_front_max < -1 || op->warp_front_max > 64)
+        return bad(P, SSCO_ERR_INVALID_ARG, "warp_front_max must be in [-1, 64]");
+    P.tune.warp_front_max = op->warp_front_max > 0 ? op->warp_front_max : 0;
 
     for (int k = 0; k < n_pats; ++k) {
         ssco_status s = validate(P, pats[k], k);

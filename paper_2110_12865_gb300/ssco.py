@@ -55,7 +55,8 @@ class Op(C.Structure):
     _fields_ = [("precision", C.c_int32), ("batch", C.c_int32), ("refine_tol", C.c_double),
                 ("refine_max_iter", C.c_int32), ("small_front_max", C.c_int32),
                 ("amalgamate", C.c_int32), ("tiny_front_max", C.c_int32), ("tensor_cores", C.c_int32),
-                ("big_panel", C.c_int32), ("split_rows", C.c_int32)]
+                ("big_panel", C.c_int32), ("split_rows", C.c_int32),
+                ("warp_front_max", C.c_int32)]
 
 
 class KernelStat(C.Structure):
@@ -145,7 +146,7 @@ class Plan:
 
     def __init__(self, problems, precision=FP64, batch=None, refine_tol=1e-10, refine_max_iter=30,
                  small_front_max=0, amalgamate=1, tiny_front_max=0, tensor_cores=0, big_panel=0,
-                 split_rows=0, _handle=None):
+                 split_rows=0, warp_front_max=0, _handle=None):
         self.L = load_library()
         if _handle is not None:
             self._h = _handle
@@ -185,6 +186,7 @@ class Plan:
             op.tensor_cores = tensor_cores
             op.big_panel = big_panel
             op.split_rows = split_rows
+            op.warp_front_max = warp_front_max
             h = C.c_void_p()
             st = self.L.ssco_analyze(arr, len(pats), C.byref(op), C.byref(h))
             if st != SSCO_OK:

@@ -131,6 +131,28 @@ def test_split_solves_uneven_patterns(S, prec):
         assert np.max(np.abs(x - x_ref)) <= 1e-12 * np.max(np.abs(x_ref))
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_warp_per_front_small_fronts(S, prec):
+    """Warp-per-front factorization of the small-front classes (forced with
+    warp_front_max on a 256 x 256 grid, whose lowest levels hold thousands
+    of fronts): FP64 L entries within 1e-12 per column of the oracle's and
+    the same solution as the one-CTA-per-front kernel; FP32 within the
+    residual bound."""
+    p = P.workload("grid256")
+    precision = S.FP64 if prec == "fp64" else S.FP32_REFINE
+    pl, x, st, *_ = run(S, p, precision, warp_front_max=64, tiny_front_max=8)
+    assert pl.info["tune_warp_front_max"] == 64
+    r, res, err = check_against_oracle(S, pl, p, x, st, 0, 0)
+    if prec == "fp64":
+        L = pl.export_L()[0]
+        Lc = r.S.Lcolptr
+        colerr = max(np.linalg.norm(L[Lc[j]:Lc[j + 1]] - r.L[Lc[j]:Lc[j + 1]]) /
+                     np.linalg.norm(r.L[Lc[j]:Lc[j + 1]]) for j in range(p.n))
+        assert colerr <= 1e-12
+        _, x_ref, *_ = run(S, p, precision, tiny_front_max=8)
+        assert np.max(np.abs(x - x_ref)) <= 1e-12 * np.max(np.abs(x_ref))
+
+
 @pytest.mark.parametrize("seed", range(6))
 def test_fp64_random_patterns(S, seed):
     rng = np.random.default_rng(900 + seed)
