@@ -98,8 +98,10 @@ typedef struct {
  * tiny_front_max: subtrees whose fronts all have at most this many rows
  *   (<= 32) are factored and solved by one warp each, front in registers,
  *   in a single launch (0 = default 32, -1 = off).
- * tensor_cores: 0 = FP32 trailing updates of multi-CTA fronts run on the
- *   tcgen05 tensor cores (3xTF32), -1 = SIMT FP32 only.
+ * tensor_cores: 0 = FP32 updates of multi-CTA fronts run on the tcgen05
+ *   tensor cores (3xTF32), one CTA per 128 x 128 tile; 2 = the wide
+ *   trailing updates in persistent CTAs (one per SM, two TMEM
+ *   accumulators); -1 = SIMT FP32 only.
  * big_panel: columns of a multi-CTA front factored between two trailing
  *   updates (a multiple of 32 in [32, 1024]; 0 = default 256).
  * split_rows: fronts with at least this many rows (and more than

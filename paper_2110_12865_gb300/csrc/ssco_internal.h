@@ -133,7 +133,8 @@ struct Tunables {
     int32_t warp_items = 8 * 152;  // a solve level goes warp-per-item at >= this many items
     int32_t vec_max_cls = 96;      // largest size class factored V value sets per CTA
     int32_t solve_threads_big = 512;  // CTA size of solve levels with fronts > 512 rows
-    int32_t use_tc = 1;            // FP32 big-front trailing updates on tcgen05 tensor cores
+    int32_t use_tc = 1;            // FP32 big-front updates on tcgen05: 0 off, 1 per-tile CTAs,
+                                   // 2 persistent CTAs for the wide trailing updates
     int32_t tc_min_rows = 128;     // ... when the trailing extent reaches this many rows
     int32_t big_panel = 256;       // big fronts: columns per trailing-update block
     int32_t split_rows = 1024;     // fronts with at least this many rows take the split solves

@@ -1256,6 +1256,294 @@ __global__ void __launch_bounds__(288, 2) k_big_update_tc(const DevTables t, con
     if (warp == 8) tc::tmem_dealloc(taddr, 128);
 }
 
+// Persistent tensor-core trailing update (FP32 factor, jend < 0): one CTA
+// per SM walks the launch's work items -- (tile pair, front, value set),
+// pair p of a front = row tile ti and the two column tiles 2tp, 2tp+1 of
+// the trailing lower triangle on the absolute 128-row grid -- so that
+// (a) the pair shares its A operand (one A block feeds two 128x128 MMAs),
+// (b) operand chunks stream through a 4-stage ring continuously across
+// items, and (c) two TMEM accumulators of 256 columns let the epilogue of
+// item v run while the tensor core works on item v+1.  Warp 8 lane 0 loads
+// (bulk copies into the ring) and issues MMAs; warps 0-3 (columns of the
+// first tile) and 4-7 (second tile) run the epilogue.  Barriers: full/empty
+// per stage, accfull (MMA commit) and accempty (8 epilogue warps) per
+// accumulator.  Every wait is bounded and also gives up when another role
+// has raised the CTA's abort flag; on expiry the kernel raises *dev_err,
+// drains what it issued and frees its tensor memory.
+constexpr int kTcpStages = 4;
+constexpr int kTcpStageBytes = 49152;  // A, B0, B1 blocks of 16 KB
+constexpr int kTcpSmem = kTcpStages * kTcpStageBytes + 256;
+constexpr uint32_t kTcpPolls = 1u << 22;
+
+struct TcpItem {
+    bool valid;
+    int r, w, k1, jlo, ti, tj0, tj1;  // tile indices absolute (x 128 rows)
+    bool two;                          // second column tile inside the triangle
+    int64_t panel_off, upd_off, tc_off;
+    int b;
+};
+
+// Pairs of one front's trailing triangle with nrt row tiles: row tile ti
+// holds ti / 2 + 1 pairs; pairs of row tiles 2u and 2u + 1 start at u(u+1).
+__host__ __device__ inline int64_t tcp_pairs(int64_t nrt) {
+    const int64_t U = nrt / 2, e = nrt & 1;
+    return U * (U + 1) + e * (U + 1);
+}
+
+__device__ __forceinline__ TcpItem tcp_item(const DevTables& t, const int32_t* list, int count, int64_t npairs,
+                                            int k0, int nk, int64_t it) {
+    TcpItem x;
+    x.valid = false;
+    const int64_t p = it % npairs;
+    const int q = (int)((it / npairs) % count);
+    x.b = (int)(it / (npairs * count));
+    const FrontDesc d = t.fronts[list[q]];
+    if (d.tc_off < 0 || k0 >= d.w) return x;
+    x.r = d.r;
+    x.w = d.w;
+    x.k1 = min(k0 + nk, d.w);
+    x.jlo = x.k1;
+    if (x.jlo >= d.r) return x;
+    const int t0 = x.jlo >> 7;
+    const int64_t nrt = (d.r + 127) / 128 - t0;
+    if (p >= tcp_pairs(nrt)) return x;
+    int64_t u = (int64_t)((sqrt(4.0 * (double)p + 1.0) - 1.0) * 0.5);
+    while (u * (u + 1) > p) --u;
+    while ((u + 1) * (u + 2) <= p) ++u;
+    const int64_t rem = p - u * (u + 1);
+    const int64_t ti = 2 * u + rem / (u + 1), tp = rem % (u + 1);
+    if (ti >= nrt) return x;
+    x.ti = t0 + (int)ti;
+    x.tj0 = t0 + 2 * (int)tp;
+    x.tj1 = x.tj0 + 1;
+    x.two = 2 * tp + 1 <= ti;
+    x.panel_off = d.panel_off;
+    x.upd_off = d.upd_off;
+    x.tc_off = d.tc_off;
+    x.valid = true;
+    return x;
+}
+
+__global__ void __launch_bounds__(288, 1) k_big_update_tcp(const DevTables t, const int32_t* __restrict__ list,
+                                                           int32_t count, int32_t B, int64_t npairs, int k0, int nk,
+                                                           const float* __restrict__ pack, int64_t pack_total,
+                                                           float* __restrict__ panel, int64_t panel_total,
+                                                           float* __restrict__ upd, int64_t upd_total,
+                                                           int32_t* __restrict__ dev_err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + kTcpStages * kTcpStageBytes);
+    uint64_t* empty = full + kTcpStages;
+    uint64_t* accfull = empty + kTcpStages;
+    uint64_t* accempty = accfull + 2;
+    uint32_t* slot = reinterpret_cast<uint32_t*>(accempty + 2);
+    volatile int32_t* abort_flag = reinterpret_cast<volatile int32_t*>(slot + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t items = npairs * count * B;
+    if (warp == 8) {
+        tc::tmem_alloc(slot, 512);
+        tc::tmem_relinquish();
+    }
+    if (tid == 0) {
+        for (int s = 0; s < kTcpStages; ++s) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            tc::mbar_init(&accfull[a], 1);
+            tc::mbar_init(&accempty[a], 8);
+        }
+        *abort_flag = 0;
+        tc::mbar_init_fence();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t taddr = *slot;
+    if (warp == 8) {
+        if (lane == 0) {
+            const uint32_t idesc = tc::idesc_tf32(128, 128);
+            const uint32_t lbo = 16 * 128, sbo = 128;
+            // load cursor and MMA cursor over the same (item, chunk) sequence
+            int64_t itl = blockIdx.x, itm = blockIdx.x;
+            TcpItem xl = itl < items ? tcp_item(t, list, count, npairs, k0, nk, itl) : TcpItem{};
+            TcpItem xm = xl;
+            int cl = 0, cm = 0, vm = 0;
+            int64_t gl = 0, gm = 0;
+            bool ok = true;
+            auto next_valid = [&](int64_t& it, TcpItem& x) {
+                while (it < items) {
+                    x = tcp_item(t, list, count, npairs, k0, nk, it);
+                    if (x.valid) return;
+                    it += gridDim.x;
+                }
+                x.valid = false;
+            };
+            if (itl < items && !xl.valid) {
+                next_valid(itl, xl);
+                xm = xl;
+                itm = itl;
+            }
+            while (ok && itm < items && xm.valid) {
+                // loads run up to kTcpStages chunks ahead of the MMAs
+                while (itl < items && xl.valid && gl < gm + kTcpStages) {
+                    const int st = (int)(gl % kTcpStages);
+                    if (gl >= kTcpStages &&
+                        !tc::mbar_wait_abort(&empty[st], (uint32_t)((gl / kTcpStages) - 1) & 1u, kTcpPolls,
+                                             abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    unsigned char* sb = smem_raw + st * kTcpStageBytes;
+                    const float* pk = pack + (int64_t)xl.b * pack_total + xl.tc_off + (int64_t)cl * 4096;
+                    tc::mbar_arrive_expect_tx(&full[st], xl.two ? 49152u : 32768u);
+                    tc::bulk_g2s(sb, pk + (int64_t)xl.ti * kTcTileFloats, 16384u, &full[st]);
+                    tc::bulk_g2s(sb + 16384, pk + (int64_t)xl.tj0 * kTcTileFloats, 16384u, &full[st]);
+                    if (xl.two) tc::bulk_g2s(sb + 32768, pk + (int64_t)xl.tj1 * kTcTileFloats, 16384u, &full[st]);
+                    ++gl;
+                    if (++cl == (xl.k1 - k0 + 15) / 16) {
+                        cl = 0;
+                        itl += gridDim.x;
+                        next_valid(itl, xl);
+                    }
+                }
+                if (!ok) break;
+                const int st = (int)(gm % kTcpStages);
+                const int buf = vm & 1;
+                if (!tc::mbar_wait_abort(&full[st], (uint32_t)(gm / kTcpStages) & 1u, kTcpPolls, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                if (cm == 0 && vm >= 2 &&
+                    !tc::mbar_wait_abort(&accempty[buf], (uint32_t)((vm >> 1) - 1) & 1u, kTcpPolls, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                tc::fence_after_sync();
+                const unsigned char* ah = smem_raw + st * kTcpStageBytes;
+                const uint32_t d0 = taddr + (uint32_t)(buf * 256), d1 = d0 + 128;
+#pragma unroll
+                for (int s8 = 0; s8 < 2; ++s8) {
+                    const uint32_t koff = (uint32_t)s8 * 2 * lbo;
+                    const uint64_t dah = tc::smem_desc_kmajor(ah + koff, lbo, sbo);
+                    const uint64_t dal = tc::smem_desc_kmajor(ah + 8192 + koff, lbo, sbo);
+                    const uint64_t b0h = tc::smem_desc_kmajor(ah + 16384 + koff, lbo, sbo);
+                    const uint64_t b0l = tc::smem_desc_kmajor(ah + 24576 + koff, lbo, sbo);
+                    const uint32_t acc = (cm > 0 || s8 > 0) ? 1u : 0u;
+                    tc::mma_tf32(d0, dah, b0h, idesc, acc);
+                    tc::mma_tf32(d0, dah, b0l, idesc, 1u);
+                    tc::mma_tf32(d0, dal, b0h, idesc, 1u);
+                    if (xm.two) {
+                        const uint64_t b1h = tc::smem_desc_kmajor(ah + 32768 + koff, lbo, sbo);
+                        const uint64_t b1l = tc::smem_desc_kmajor(ah + 40960 + koff, lbo, sbo);
+                        tc::mma_tf32(d1, dah, b1h, idesc, acc);
+                        tc::mma_tf32(d1, dah, b1l, idesc, 1u);
+                        tc::mma_tf32(d1, dal, b1h, idesc, 1u);
+                    }
+                }
+                tc::mma_commit(&empty[st]);
+                ++gm;
+                if (++cm == (xm.k1 - k0 + 15) / 16) {
+                    tc::mma_commit(&accfull[buf]);
+                    cm = 0;
+                    ++vm;
+                    itm += gridDim.x;
+                    next_valid(itm, xm);
+                }
+            }
+            if (!ok) {
+                atomicExch(dev_err, 1);
+                *abort_flag = 1;
+                // copies issued but not consumed, then the last MMAs
+                for (int64_t g = gm; g < gl; ++g)
+                    tc::mbar_wait(&full[g % kTcpStages], (uint32_t)(g / kTcpStages) & 1u, kTcpPolls);
+                if (gm > 0)
+                    tc::mbar_wait(&empty[(gm - 1) % kTcpStages], (uint32_t)((gm - 1) / kTcpStages) & 1u,
+                                  kTcpPolls);
+            }
+        }
+        __syncwarp();
+    } else {
+        // epilogue: warps 0-3 the first column tile, 4-7 the second
+        const int lq = warp & 3, half = warp >> 2;
+        int64_t it = blockIdx.x;
+        int v = 0;
+        while (it < items) {
+            const TcpItem x = tcp_item(t, list, count, npairs, k0, nk, it);
+            it += gridDim.x;
+            if (!x.valid) continue;
+            const int buf = v & 1;
+            const bool mine = half == 0 || x.two;
+            const int i = x.ti * 128 + 32 * lq + lane;
+            const int j0 = (half == 0 ? x.tj0 : x.tj1) * 128;
+            float* Pb = panel + (int64_t)x.b * panel_total + x.panel_off;
+            float* Ub = upd + (int64_t)x.b * upd_total + x.upd_off;
+            const int r = x.r, w = x.w, ru = r - w, jlo = x.jlo;
+            float cv[32];
+            if (mine) {
+#pragma unroll
+                for (int c = 0; c < 32; ++c) {
+                    const int j = j0 + c;
+                    cv[c] = 0.f;
+                    if (i < r && j <= i && j >= jlo)
+                        cv[c] = j < w ? Pb[(int64_t)j * r + i] : Ub[(int64_t)(j - w) * ru + (i - w)];
+                }
+            }
+            bool got = tc::mbar_wait_abort(&accfull[buf], (uint32_t)(v >> 1) & 1u, kTcpPolls, abort_flag);
+            got = __all_sync(0xffffffffu, got);
+            if (!got) {
+                if (lane == 0) {
+                    atomicExch(dev_err, 1);
+                    *abort_flag = 1;
+                }
+                break;
+            }
+            tc::fence_after_sync();
+            if (mine) {
+#pragma unroll 1
+                for (int h = 0; h < 4; ++h) {
+                    const int jb = j0 + 32 * h;
+                    if (h > 0) {
+#pragma unroll
+                        for (int c = 0; c < 32; ++c) {
+                            const int j = jb + c;
+                            cv[c] = 0.f;
+                            if (i < r && j <= i && j >= jlo)
+                                cv[c] = j < w ? Pb[(int64_t)j * r + i] : Ub[(int64_t)(j - w) * ru + (i - w)];
+                        }
+                    }
+                    float vv[4][8];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        tc::tmem_ld8(taddr + ((uint32_t)(32 * lq) << 16) +
+                                         (uint32_t)(buf * 256 + half * 128 + 32 * h + 8 * c),
+                                     vv[c]);
+                    tc::tmem_ld_wait();
+                    if (i < r) {
+#pragma unroll
+                        for (int c = 0; c < 32; ++c) {
+                            const int j = jb + c;
+                            if (j <= i && j >= jlo) {
+                                if (j < w)
+                                    Pb[(int64_t)j * r + i] = cv[c] - vv[c >> 3][c & 7];
+                                else
+                                    Ub[(int64_t)(j - w) * ru + (i - w)] = cv[c] - vv[c >> 3][c & 7];
+                            }
+                        }
+                    }
+                }
+            }
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&accempty[buf]);
+            ++v;
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 8) tc::tmem_dealloc(taddr, 512);
+}
+
 // Factor the 32x32 diagonal block of column block kb, one warp per front,
 // lane i holding row i in registers.  Compact form: at step j the pivot
 // column is always a[0] (the row's registers shift left by one per step), so
@@ -2141,7 +2429,31 @@ void launch_big_update(Plan& P, const LaunchList& ll, const int32_t* list, int k
         by += (2 * u.entries + u.rows * u.k) * P.tsize;
     }
     if (tiles == 0) return;
-    if (tcore) {
+    if (tcore && jend < 0 && P.tune.use_tc >= 2 && kpack0 == k0) {
+        int64_t npairs = 0;
+        for (int32_t q = 0; q < ll.count; ++q) {
+            const FrontDesc& d = P.fronts[P.front_lists[ll.list_off + q]];
+            if (k0 >= d.w) continue;
+            const int jlo = std::min(k0 + nk, d.w);
+            if (jlo >= d.r) continue;
+            npairs = std::max(npairs, tcp_pairs((d.r + 127) / 128 - jlo / 128));
+        }
+        const int64_t items = npairs * ll.count * B;
+        if (items == 0) return;
+        static int n_sm = 0;
+        if (n_sm == 0) {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+            if (n_sm <= 0) n_sm = 1;
+        }
+        Prof pu(P, s, SSCO_K_BIG_UPDATE_TC);
+        k_big_update_tcp<<<(unsigned)std::min<int64_t>(items, n_sm), 288, kTcpSmem, s>>>(
+            P.dt, list, ll.count, B, npairs, k0, nk, wsp<float>(P, P.ws.tcpack), P.tc_pack_total,
+            reinterpret_cast<float*>(panel), P.panel_total, reinterpret_cast<float*>(upd), P.upd_total,
+            wsp<int32_t>(P, P.ws.dev_err));
+        if (pu.ev >= 0) pu.done(fl * B, by * B);
+    } else if (tcore) {
         Prof pu(P, s, SSCO_K_BIG_UPDATE_TC);
         k_big_update_tc<<<dim3((unsigned)tiles, ll.count, B), 288, kTcSmem, s>>>(
             P.dt, list, kpack0, k0, nk, jend, wsp<float>(P, P.ws.tcpack), P.tc_pack_total,
@@ -2962,8 +3274,11 @@ int allow_dynamic_smem(K kernel) {
 template <class T>
 int set_attr_T() {
     int e = allow_dynamic_smem(k_front_small<T>);
-    if (!e && sizeof(T) == 4)
+    if (!e && sizeof(T) == 4) {
         e = (int)cudaFuncSetAttribute(k_big_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+        if (!e)
+            e = (int)cudaFuncSetAttribute(k_big_update_tcp, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcpSmem);
+    }
     if (!e) e = allow_dynamic_smem(k_front_vec<T, sizeof(T) == 4 ? 4 : 2>);
     if (!e) e = allow_dynamic_smem(k_tiny_factor<T>);
     if (!e) e = allow_dynamic_smem(k_tiny_fwd<T>);
@@ -3121,7 +3436,7 @@ int autotune(Plan& P, const void* vals, int32_t vdt, const double* shift, const 
         {&P.tune.warp_items, {152, 2 * 152, 4 * 152, 8 * 152, 16 * 152, 1 << 30}},
         {&P.tune.vec_max_cls, {0, 64, 96}},
         {&P.tune.solve_threads_big, {256, 512}},
-        {&P.tune.use_tc, {0, 1}},
+        {&P.tune.use_tc, {0, 1, 2}},
         {&P.tune.big_panel, {32, 64, 128, 256}},
         {&P.tune.split_rows, {512, 1024, 2048, 4096, 1 << 30}},
         {&P.tune.warp_front_max, {0, 32, 48, 64}},

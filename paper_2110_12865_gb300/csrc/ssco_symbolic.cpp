@@ -202,7 +202,7 @@ ssco_status analyze_impl(const ssco_pattern* const* pats, int32_t n_pats, const 
     P.amalg = op->amalgamate;
     P.tiny_max = op->tiny_front_max == 0 ? 32 : (op->tiny_front_max < 0 ? 0 : std::min(op->tiny_front_max, 32));
     P.n_pats = n_pats;
-    P.tune.use_tc = op->tensor_cores < 0 ? 0 : 1;
+    P.tune.use_tc = op->tensor_cores < 0 ? 0 : (op->tensor_cores == 2 ? 2 : 1);
     if (op->big_panel != 0 && (op->big_panel < 32 || op->big_panel > 1024 || op->big_panel % 32 != 0))
         return bad(P, SSCO_ERR_INVALID_ARG, "big_panel must be 0 or a multiple of 32 in [32, 1024]");
     if (op->big_panel > 0) P.tune.big_panel = op->big_panel;

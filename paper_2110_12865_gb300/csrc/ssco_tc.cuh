@@ -80,6 +80,25 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
         : "memory");
 }
 
+// Bounded wait that also gives up when *abort becomes nonzero (checked every
+// 256 polls); returns false if it gave up.
+__device__ __forceinline__ bool mbar_wait_abort(uint64_t* bar, uint32_t phase, uint32_t max_iter,
+                                                const volatile int32_t* abort) {
+    for (uint32_t it = 0; it < max_iter; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(phase)
+            : "memory");
+        if (done) return true;
+        if ((it & 255u) == 255u && *abort) return false;
+    }
+    return false;
+}
+
 // D[tmem] (+)= A[smem] * B[smem]^T, TF32 inputs, FP32 accumulation.
 __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
                                          uint32_t accumulate) {

@@ -92,15 +92,17 @@ def test_elasticity_small(S, prec, kw):
         assert err < 1e-8
 
 
-@pytest.mark.parametrize("tc", [0, -1])
+@pytest.mark.parametrize("tc", [0, 2, -1])
 def test_fp32_factor_accuracy_big_fronts(S, tc):
-    """FP32 factor through the multi-CTA path, trailing updates on tcgen05
-    tensor cores (3xTF32, tc=0) or SIMT FP32 (tc=-1): every column of L must
+    """FP32 factor through the multi-CTA path, updates on tcgen05 tensor
+    cores (3xTF32; tc=0: one CTA per tile, tc=2: wide trailing updates in
+    persistent CTAs with two TMEM accumulators) or SIMT FP32 (tc=-1): every
+    column of L must
     agree with the FP64 oracle to FP32-level accuracy (plain TF32, ~1e-3,
     would fail), and the refined solution to the FP64 residual bound."""
     p = P.elasticity_problem(7, cfg=2)
     pl, x, st, *_ = run(S, p, S.FP32_REFINE, small_front_max=32, tensor_cores=tc)
-    assert pl.info["tune_use_tc"] == (1 if tc == 0 else 0)
+    assert pl.info["tune_use_tc"] == {0: 1, 2: 2, -1: 0}[tc]
     r, res, err = check_against_oracle(S, pl, p, x, st, 0, 0)
     L = pl.export_L()[0]
     Lc = r.S.Lcolptr
