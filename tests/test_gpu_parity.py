@@ -111,6 +111,23 @@ def test_fp32_factor_accuracy_big_fronts(S, tc):
     assert worst <= 2e-4, worst
 
 
+@pytest.mark.parametrize("big_panel", [32, 96, 256])
+def test_big_panel_blocks_fp64_L_entries(S, big_panel):
+    """Multi-CTA fronts factored in panel blocks of 32, 96 or 256 columns
+    (narrow in-block updates plus one trailing update per block): FP64
+    entries of L within 1e-12 per column of the oracle's for every block
+    width."""
+    p = P.elasticity_problem(9, cfg=2)
+    pl, x, st, *_ = run(S, p, S.FP64, small_front_max=32, big_panel=big_panel)
+    assert pl.info["tune_big_panel"] == big_panel
+    r, res, err = check_against_oracle(S, pl, p, x, st, 0, 0)
+    L = pl.export_L()[0]
+    Lc = r.S.Lcolptr
+    colerr = max(np.linalg.norm(L[Lc[j]:Lc[j + 1]] - r.L[Lc[j]:Lc[j + 1]]) / np.linalg.norm(r.L[Lc[j]:Lc[j + 1]])
+                 for j in range(p.n))
+    assert colerr <= 1e-12
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_split_solves_uneven_patterns(S, prec):
     """Multi-CTA split solves (split_rows far below the largest fronts, so
