@@ -106,10 +106,13 @@ typedef struct {
  *   updates (a multiple of 32 in [32, 1024]; 0 = default 256).
  * split_rows: fronts with at least this many rows (and more than
  *   small_front_max) are solved by multi-CTA launches over 256-column
- *   blocks (0 = default 1024, -1 = never).
+ *   blocks (0 = default: 1024 with >= 8 value sets, else 2048; -1 = never).
  * warp_front_max: small fronts of at most this many rows (<= 64) are
  *   factored one warp per front on levels that supply at least 8 warps per
- *   SM (0 = default off; ssco_autotune may switch it on).            */
+ *   SM (0 = default off; ssco_autotune may switch it on).
+ * cluster_rows: fronts with at least this many rows (below split_rows)
+ *   are solved by one 8-CTA thread-block cluster per value set
+ *   (0 = default: 512 with <= 4 value sets, else never; -1 = never).  */
 typedef struct {
     int32_t precision;
     int32_t batch;
@@ -122,6 +125,7 @@ typedef struct {
     int32_t big_panel;
     int32_t split_rows;
     int32_t warp_front_max;
+    int32_t cluster_rows;
 } ssco_op;
 
 /* Sizes and counts of an analyzed plan (all for the concatenated system). */
@@ -154,6 +158,7 @@ typedef struct {
     int64_t tune_big_panel;  /* big fronts: columns per trailing update      */
     int64_t tune_split_rows; /* fronts this large take the multi-CTA solves  */
     int64_t tune_warp_front_max; /* small-front classes factored warp-per-front */
+    int64_t tune_cluster_rows;   /* fronts this large: one CTA cluster per solve */
 } ssco_info;
 
 /* ssco_plan_export selectors (host copies; sizes in elements).          */

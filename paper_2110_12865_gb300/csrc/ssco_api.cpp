@@ -76,7 +76,7 @@ void set_dev_tables(Plan& P) {
 
 // ----- plan file (de)serialization -----------------------------------------
 constexpr uint64_t kMagic = 0x314F4353534F4353ull;  // "SCOSSCO1"
-constexpr uint32_t kVersion = 8;
+constexpr uint32_t kVersion = 9;
 
 struct Writer {
     std::ofstream f;
@@ -211,6 +211,7 @@ ssco_status ssco_plan_info(ssco_plan h, ssco_info* o) {
     o->tune_big_panel = P.tune.big_panel;
     o->tune_split_rows = P.tune.split_rows;
     o->tune_warp_front_max = P.tune.warp_front_max;
+    o->tune_cluster_rows = P.tune.cluster_rows;
     return SSCO_OK;
 }
 

@@ -137,7 +137,8 @@ struct Tunables {
                                    // 2 persistent CTAs for the wide trailing updates
     int32_t tc_min_rows = 128;     // ... when the trailing extent reaches this many rows
     int32_t big_panel = 256;       // big fronts: columns per trailing-update block
-    int32_t split_rows = 1024;     // fronts with at least this many rows take the split solves
+    int32_t split_rows = 2048;     // fronts with at least this many rows take the split solves
+    int32_t cluster_rows = 512;    // ... below that, from this many rows: one CTA cluster per front
     int32_t warp_front_max = 0;    // small-front classes up to this size: one warp per front (levels
                                    // of >= warp_items fronts x value sets; autotuner option)
     int32_t tuned = 0;
@@ -149,6 +150,7 @@ struct PatMeta {
 };
 
 struct Plan {
+    int32_t launch_err = 0;  // first failed extended launch (cudaLaunchKernelEx) since the last check
     // options
     int32_t prec = SSCO_FP64;
     int32_t B = 1;

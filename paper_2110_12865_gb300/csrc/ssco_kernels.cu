@@ -18,6 +18,7 @@
 // is a global intermediate (Sec. 4.2.1) consumed by its parent through a
 // relative map (address coherence, Sec. 4.8).
 #include <cuda_runtime.h>
+#include <cooperative_groups.h>
 
 #include <climits>
 #include <cmath>
@@ -2910,6 +2911,222 @@ __global__ void __launch_bounds__(256) k_bsplit_step(const DevTables t, const in
     vb[d.f + col0 + tid] = xs[tid];
 }
 
+// --------------------------------------------------------------------------
+// a5'': cluster solves.  A front with r >= cluster_rows is solved by one
+// thread-block cluster of kClusterCS CTAs (one per SM) per value set: the
+// front's rows are dealt to the CTAs in 32-row chunks (chunk c to rank
+// c mod CS, kept in that CTA's shared memory), so the front's panel is
+// read by CS SMs at once.  Per 32-column block one CTA -- the owner of the
+// block's rows -- solves the block's triangle; the forward solve writes the
+// block's y into every CTA's shared memory (distributed shared memory) and
+// all CTAs update their own rows after one cluster barrier; the backward
+// solve reduces the CTAs' partial dot products into the owner the same
+// way.  One hardware cluster barrier per block; no launch per block.
+// --------------------------------------------------------------------------
+constexpr int kClusterCS = 8;
+namespace cg = cooperative_groups;
+
+// Local slot of front row i in its owner's chunk store.
+__device__ __forceinline__ int cl_slot(int i) { return (i >> 5) / kClusterCS * 32 + (i & 31); }
+
+template <class T>
+__global__ void __launch_bounds__(256) k_fwd_cluster(const DevTables t, const int32_t* __restrict__ list,
+                                                     const T* __restrict__ panel, int64_t panel_total,
+                                                     T* __restrict__ vec, int64_t n, T* __restrict__ pvec,
+                                                     int64_t pvec_total, const int32_t* __restrict__ active,
+                                                     int32_t n_pats) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* vl = reinterpret_cast<T*>(smem_raw);  // this CTA's chunks of the front vector
+    __shared__ T ybuf[2][32];
+    __shared__ int64_t coff[32];
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const FrontDesc d = t.fronts[list[blockIdx.x / kClusterCS]];
+    const int b = blockIdx.y;
+    if (active && !active[(int64_t)b * n_pats + d.sys]) return;  // uniform over the cluster
+    const int r = d.r, w = d.w, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nch = (r + 31) / 32;
+    T* vb = vec + (int64_t)b * n;
+    T* pv = pvec + (int64_t)b * pvec_total;
+    const T* Pb = panel + (int64_t)b * panel_total + d.panel_off;
+    // own rows: right-hand side plus the children's passing vectors
+    for (int cb = 0; cb < d.nchild; cb += 32) {
+        const int nc = min(32, d.nchild - cb);
+        __syncthreads();
+        if (tid < nc) coff[tid] = t.fronts[t.child_ids[d.child_off + cb + tid]].pvec_off;
+        __syncthreads();
+        for (int c = rank + kClusterCS * (tid >> 5); c < nch; c += kClusterCS * 8) {
+            const int i = 32 * c + lane;
+            if (i >= r) continue;
+            T val = cb == 0 ? (i < w ? vb[d.f + i] : T(0)) : vl[cl_slot(i)];
+            for (int q = 0; q < nc; ++q) {
+                const int a = t.invmap[d.inv_off + (int64_t)(cb + q) * r + i];
+                if (a >= 0) val += pv[coff[q] + a];
+            }
+            vl[cl_slot(i)] = val;
+        }
+    }
+    if (d.nchild == 0)
+        for (int c = rank + kClusterCS * (tid >> 5); c < nch; c += kClusterCS * 8) {
+            const int i = 32 * c + lane;
+            if (i < r) vl[cl_slot(i)] = i < w ? vb[d.f + i] : T(0);
+        }
+    __syncthreads();
+    cl.sync();  // every CTA of the cluster is running before any remote write
+    const int nb = (w + 31) / 32;
+    for (int k = 0; k < nb; ++k) {
+        const int c0 = 32 * k, nbk = min(32, w - c0), buf = k & 1;
+        if (k % kClusterCS == rank) {
+            __syncthreads();  // this CTA's updates of the block's rows are done
+            if (warp == 0) {
+                T a[32];
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    a[j] = (j < nbk && lane < nbk) ? Pb[(int64_t)(c0 + j) * r + c0 + lane] : T(0);
+                T val = lane < nbk ? vl[cl_slot(c0 + lane)] : T(0);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    if (j < nbk) {
+                        const T dj = __shfl_sync(0xffffffffu, a[j], j);
+                        const T yj = __shfl_sync(0xffffffffu, val, j) / dj;
+                        if (lane == j)
+                            val = yj;
+                        else if (lane > j)
+                            val -= a[j] * yj;
+                    }
+                }
+                if (lane < nbk) {
+                    vl[cl_slot(c0 + lane)] = val;
+                    for (int rk = 0; rk < kClusterCS; ++rk) cl.map_shared_rank(&ybuf[buf][0], rk)[lane] = val;
+                }
+            }
+        }
+        cl.sync();  // y of block k in every CTA
+        // own rows past the block (chunks >= k): v_i -= L[i, block] y
+        const int cfirst = k + ((rank - k % kClusterCS + kClusterCS) % kClusterCS);
+        for (int c = cfirst + kClusterCS * (tid >> 5); c < nch; c += kClusterCS * 8) {
+            const int i = 32 * c + lane;
+            if (i < c0 + nbk || i >= r) continue;
+            const T* col = Pb + (int64_t)c0 * r + i;
+            T acc[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc[u] = T(0);
+            int j = 0;
+            for (; j + 7 < nbk; j += 8) {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) acc[u] += col[(int64_t)(j + u) * r] * ybuf[buf][j + u];
+            }
+            for (; j < nbk; ++j) acc[0] += col[(int64_t)j * r] * ybuf[buf][j];
+            vl[cl_slot(i)] -= ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+        }
+    }
+    __syncthreads();
+    for (int c = rank + kClusterCS * (tid >> 5); c < nch; c += kClusterCS * 8) {
+        const int i = 32 * c + lane;
+        if (i >= r) continue;
+        if (i < w)
+            vb[d.f + i] = vl[cl_slot(i)];
+        else
+            pv[d.pvec_off + i - w] = vl[cl_slot(i)];
+    }
+    cl.sync();  // no CTA leaves while a remote write to it may be pending
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_bwd_cluster(const DevTables t, const int32_t* __restrict__ list,
+                                                     const T* __restrict__ panel, int64_t panel_total,
+                                                     T* __restrict__ vec, int64_t n,
+                                                     const int32_t* __restrict__ active, int32_t n_pats) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* xl = reinterpret_cast<T*>(smem_raw);
+    __shared__ T part[2][kClusterCS][32];
+    __shared__ T wpart[8][32];
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const FrontDesc d = t.fronts[list[blockIdx.x / kClusterCS]];
+    const int b = blockIdx.y;
+    if (active && !active[(int64_t)b * n_pats + d.sys]) return;
+    const int r = d.r, w = d.w, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nch = (r + 31) / 32;
+    T* vb = vec + (int64_t)b * n;
+    const T* Pb = panel + (int64_t)b * panel_total + d.panel_off;
+    const int32_t* rows = t.rows + d.rows_off;
+    for (int c = rank + kClusterCS * (tid >> 5); c < nch; c += kClusterCS * 8) {
+        const int i = 32 * c + lane;
+        if (i < r) xl[cl_slot(i)] = i < w ? vb[d.f + i] : vb[rows[i]];
+    }
+    __syncthreads();
+    cl.sync();
+    const int nb = (w + 31) / 32;
+    for (int k = nb - 1; k >= 0; --k) {
+        const int c0 = 32 * k, nbk = min(32, w - c0), buf = k & 1, owner = k % kClusterCS;
+        __syncthreads();  // x of this CTA's rows (the owner's last solve) visible
+        // partial dots of the block's columns over own rows past the block:
+        // warp q takes own chunks q, q + 8, ...; lane = row; then per column
+        // a warp sum, the 8 warps combined in shared memory.
+        T acc[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) acc[j] = T(0);
+        const int cfirst = k + ((rank - k % kClusterCS + kClusterCS) % kClusterCS);
+        for (int c = cfirst + kClusterCS * warp; c < nch; c += kClusterCS * 8) {
+            const int i = 32 * c + lane;
+            if (i < c0 + nbk || i >= r) continue;
+            const T xi = xl[cl_slot(i)];
+            const T* rowp = Pb + (int64_t)c0 * r + i;
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                if (j < nbk) acc[j] += rowp[(int64_t)j * r] * xi;
+        }
+#pragma unroll
+        for (int sh = 16; sh >= 1; sh >>= 1) {
+            const bool up = (lane & sh) != 0;
+#pragma unroll
+            for (int j = 0; j < sh; ++j) {
+                const T send = up ? acc[j] : acc[j + sh];
+                const T keep = up ? acc[j + sh] : acc[j];
+                acc[j] = keep + __shfl_xor_sync(0xffffffffu, send, sh);
+            }
+        }
+        wpart[warp][lane] = acc[0];  // column `lane`'s sum over this warp's rows
+        __syncthreads();
+        if (warp == 0) {
+            T sum = T(0);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) sum += wpart[q][lane];
+            cl.map_shared_rank(&part[buf][0][0], owner)[rank * 32 + lane] = sum;
+        }
+        cl.sync();  // all partials of block k at its owner
+        if (rank == owner && warp == 0) {
+            T a[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                a[j] = (lane < nbk && j < nbk && j >= lane) ? Pb[(int64_t)(c0 + lane) * r + c0 + j] : T(0);
+            T dot = T(0);
+#pragma unroll
+            for (int q = 0; q < kClusterCS; ++q) dot += part[buf][q][lane];
+            T val = lane < nbk ? xl[cl_slot(c0 + lane)] - dot : T(0);
+#pragma unroll
+            for (int j = 31; j >= 0; --j) {
+                if (j < nbk) {
+                    const T dj = __shfl_sync(0xffffffffu, a[j], j);
+                    const T xj = __shfl_sync(0xffffffffu, val, j) / dj;
+                    if (lane == j)
+                        val = xj;
+                    else if (lane < j)
+                        val -= a[j] * xj;
+                }
+            }
+            if (lane < nbk) xl[cl_slot(c0 + lane)] = val;
+        }
+    }
+    __syncthreads();
+    for (int c = rank + kClusterCS * (tid >> 5); c < nch; c += kClusterCS * 8) {
+        const int i = 32 * c + lane;
+        if (i < w) vb[d.f + i] = xl[cl_slot(i)];
+    }
+    cl.sync();
+}
+
 // A level is solved warp-per-item when it supplies at least 8 warps per SM
 // and its fronts' vectors fit 8 to a CTA; otherwise one CTA per item.
 inline bool use_warp_solve(const Plan& P, const LaunchList& ll, int B) {
@@ -2931,6 +3148,45 @@ inline int split_count(const Plan& P, const LaunchList& ll) {
         ++q;
     }
     return q;
+}
+
+// Fronts after the split ones (positions q0 ..) of a solve level that take
+// the cluster solves: r >= cluster_rows, a big front with inverse maps.
+inline int cluster_count(const Plan& P, const LaunchList& ll, int q0) {
+    const int thr = std::max(P.tune.cluster_rows, P.small_max + 1);
+    int q = q0;
+    while (q < ll.count) {
+        const FrontDesc& d = P.fronts[P.front_lists[ll.list_off + q]];
+        if (d.r < thr || (d.nchild > 0 && d.inv_off < 0)) break;
+        ++q;
+    }
+    return q - q0;
+}
+
+template <class T, class Kern, class... Args>
+void launch_cluster(Plan& P, Kern kernel, int nfront, int B, size_t smem, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(kClusterCS * nfront), (unsigned)B, 1);
+    cfg.blockDim = dim3(256, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = kClusterCS;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    const int e = (int)cudaLaunchKernelEx(&cfg, kernel, args...);
+    if (e && !P.launch_err) P.launch_err = e;
+}
+
+template <class T>
+size_t cluster_smem(const Plan& P, const LaunchList& ll, int q0, int q) {
+    int rmax = 0;
+    for (int f = q0; f < q0 + q; ++f) rmax = std::max(rmax, P.fronts[P.front_lists[ll.list_off + f]].r);
+    const int nch = (rmax + 31) / 32;
+    return (size_t)((nch + kClusterCS - 1) / kClusterCS) * 32 * sizeof(T);
 }
 
 template <class T>
@@ -3038,10 +3294,24 @@ void run_trisolve(Plan& P, const int32_t* active, cudaStream_t s) {
     for (const LaunchList& ll0 : P.solve_launches) {
         LaunchList ll = ll0;
         const int q = split_count(P, ll);
-        if (q > 0) {
-            run_split_fwd<T>(P, ll, q, active, s);
-            ll.list_off += q;
-            ll.count -= q;
+        if (q > 0) run_split_fwd<T>(P, ll, q, active, s);
+        const int qc = cluster_count(P, ll, q);
+        if (qc > 0) {
+            Prof pr(P, s, SSCO_K_FWD);
+            const int32_t* lst = P.dt.front_lists + ll.list_off + q;
+            launch_cluster<T>(P, k_fwd_cluster<T>, qc, B, cluster_smem<T>(P, ll, q, qc), s, P.dt, lst,
+                              (const T*)panel, P.panel_total, vecT, P.n, pvec, P.pvec_total, active, P.n_pats);
+            if (pr.ev >= 0) {
+                LaunchList sub = ll;
+                sub.list_off += q;
+                sub.count = qc;
+                Work w = work_solve(P, sub);
+                pr.done(w.flops, w.bytes);
+            }
+        }
+        if (q + qc > 0) {
+            ll.list_off += q + qc;
+            ll.count -= q + qc;
             if (ll.count == 0) continue;
             ll.rmax = P.fronts[P.front_lists[ll.list_off]].r;
         }
@@ -3063,10 +3333,24 @@ void run_trisolve(Plan& P, const int32_t* active, cudaStream_t s) {
     for (auto it = P.solve_launches.rbegin(); it != P.solve_launches.rend(); ++it) {
         LaunchList ll = *it;
         const int q = split_count(P, ll);
-        if (q > 0) {
-            run_split_bwd<T>(P, ll, q, active, s);
-            ll.list_off += q;
-            ll.count -= q;
+        if (q > 0) run_split_bwd<T>(P, ll, q, active, s);
+        const int qc = cluster_count(P, ll, q);
+        if (qc > 0) {
+            Prof pr(P, s, SSCO_K_BWD);
+            const int32_t* lst = P.dt.front_lists + ll.list_off + q;
+            launch_cluster<T>(P, k_bwd_cluster<T>, qc, B, cluster_smem<T>(P, ll, q, qc), s, P.dt, lst,
+                              (const T*)panel, P.panel_total, vecT, P.n, active, P.n_pats);
+            if (pr.ev >= 0) {
+                LaunchList sub = ll;
+                sub.list_off += q;
+                sub.count = qc;
+                Work w = work_solve(P, sub);
+                pr.done(w.flops, w.bytes);
+            }
+        }
+        if (q + qc > 0) {
+            ll.list_off += q + qc;
+            ll.count -= q + qc;
             if (ll.count == 0) continue;
             ll.rmax = P.fronts[P.front_lists[ll.list_off]].r;
         }
@@ -3254,7 +3538,10 @@ int run_solve(Plan& P, const double* b, double* x, cudaStream_t s, GraphLoop* gl
         k_permute_out<<<gv, 256, 0, s>>>(xp, P.dt.perm, n, x);
         pr.done(0, nB * 20);
     }
-    return (int)cudaGetLastError();
+    int e = (int)cudaGetLastError();
+    if (!e) e = P.launch_err;
+    P.launch_err = 0;
+    return e;
 }
 
 // Opt each kernel with dynamic shared memory into the largest size the
@@ -3289,6 +3576,8 @@ int set_attr_T() {
     if (!e) e = allow_dynamic_smem(k_bwd<T>);
     if (!e) e = allow_dynamic_smem(k_bsplit_init<T>);
     if (!e) e = allow_dynamic_smem(k_front_warp<T>);
+    if (!e) e = allow_dynamic_smem(k_fwd_cluster<T>);
+    if (!e) e = allow_dynamic_smem(k_bwd_cluster<T>);
     return e;
 }
 
@@ -3438,8 +3727,9 @@ int autotune(Plan& P, const void* vals, int32_t vdt, const double* shift, const 
         {&P.tune.solve_threads_big, {256, 512}},
         {&P.tune.use_tc, {0, 1, 2}},
         {&P.tune.big_panel, {32, 64, 128, 256}},
-        {&P.tune.split_rows, {512, 1024, 2048, 4096, 1 << 30}},
+        {&P.tune.split_rows, {1024, 2048, 4096, 1 << 30}},
         {&P.tune.warp_front_max, {0, 32, 48, 64}},
+        {&P.tune.cluster_rows, {256, 512, 1024, 1 << 30}},
     };
     double best = 0;
     e = measure(&best);

@@ -207,10 +207,19 @@ ssco_status analyze_impl(const ssco_pattern* const* pats, int32_t n_pats, const 
         return bad(P, SSCO_ERR_INVALID_ARG, "big_panel must be 0 or a multiple of 32 in [32, 1024]");
     if (op->big_panel > 0) P.tune.big_panel = op->big_panel;
     if (op->split_rows < -1) return bad(P, SSCO_ERR_INVALID_ARG, "split_rows must be >= -1");
+    // Defaults by batch: few value sets leave the level kernels short of
+    // CTAs, so large fronts get a CTA cluster each (measured on the 24^3
+    // elasticity: 78 vs 52 systems/s); with many value sets the clusters
+    // only add cost and the multi-launch split pays from 1024 rows (48^3,
+    // 16 value sets).
+    P.tune.split_rows = P.B >= 8 ? 1024 : 2048;
+    P.tune.cluster_rows = P.B <= 4 ? 512 : (1 << 30);
     if (op->split_rows != 0) P.tune.split_rows = op->split_rows < 0 ? (1 << 30) : op->split_rows;
     if (op->warp_front_max < -1 || op->warp_front_max > 64)
         return bad(P, SSCO_ERR_INVALID_ARG, "warp_front_max must be in [-1, 64]");
     P.tune.warp_front_max = op->warp_front_max > 0 ? op->warp_front_max : 0;
+    if (op->cluster_rows < -1) return bad(P, SSCO_ERR_INVALID_ARG, "cluster_rows must be >= -1");
+    if (op->cluster_rows != 0) P.tune.cluster_rows = op->cluster_rows < 0 ? (1 << 30) : op->cluster_rows;
 
     for (int k = 0; k < n_pats; ++k) {
         ssco_status s = validate(P, pats[k], k);

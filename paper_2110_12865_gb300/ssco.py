@@ -56,7 +56,7 @@ class Op(C.Structure):
                 ("refine_max_iter", C.c_int32), ("small_front_max", C.c_int32),
                 ("amalgamate", C.c_int32), ("tiny_front_max", C.c_int32), ("tensor_cores", C.c_int32),
                 ("big_panel", C.c_int32), ("split_rows", C.c_int32),
-                ("warp_front_max", C.c_int32)]
+                ("warp_front_max", C.c_int32), ("cluster_rows", C.c_int32)]
 
 
 class KernelStat(C.Structure):
@@ -72,7 +72,7 @@ class Info(C.Structure):
               [("factor_flops", C.c_double), ("factor_flops_exact", C.c_double)] + \
               [(k, C.c_int64) for k in ["tune_warp_items", "tune_vec_max_cls", "tune_solve_threads_big", "tuned",
                                         "tune_use_tc", "tune_big_panel", "tune_split_rows",
-                                        "tune_warp_front_max"]]
+                                        "tune_warp_front_max", "tune_cluster_rows"]]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -146,7 +146,7 @@ class Plan:
 
     def __init__(self, problems, precision=FP64, batch=None, refine_tol=1e-10, refine_max_iter=30,
                  small_front_max=0, amalgamate=1, tiny_front_max=0, tensor_cores=0, big_panel=0,
-                 split_rows=0, warp_front_max=0, _handle=None):
+                 split_rows=0, warp_front_max=0, cluster_rows=0, _handle=None):
         self.L = load_library()
         if _handle is not None:
             self._h = _handle
@@ -187,6 +187,7 @@ class Plan:
             op.big_panel = big_panel
             op.split_rows = split_rows
             op.warp_front_max = warp_front_max
+            op.cluster_rows = cluster_rows
             h = C.c_void_p()
             st = self.L.ssco_analyze(arr, len(pats), C.byref(op), C.byref(h))
             if st != SSCO_OK:
@@ -302,7 +303,7 @@ class Plan:
         return best.value, {k: self.info[k] for k in ("tune_warp_items", "tune_vec_max_cls",
                                                       "tune_solve_threads_big", "tune_use_tc",
                                                       "tune_big_panel", "tune_split_rows",
-                                                      "tune_warp_front_max")}
+                                                      "tune_warp_front_max", "tune_cluster_rows")}
 
     def graph_run(self, vals: torch.Tensor, shift: torch.Tensor, b: torch.Tensor, x: torch.Tensor, stream=None):
         """numeric + solve as one captured CUDA graph (re-captured when the

@@ -172,6 +172,28 @@ def test_warp_per_front_small_fronts(S, prec):
         assert np.max(np.abs(x - x_ref)) <= 1e-12 * np.max(np.abs(x_ref))
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_cluster_solves_uneven_patterns(S, prec):
+    """Cluster solves (one 8-CTA cluster per front and value set, rows dealt
+    to the CTAs in 32-row chunks, y and partial dot products exchanged
+    through distributed shared memory) forced on every big front of three
+    uneven patterns, two value sets each: the residual bound for every
+    system, and in FP64 the one-CTA-per-front solve's solution to 1e-12."""
+    probs = [P.elasticity_problem(10, batch=2), P.elasticity_problem(5, batch=2), P.grid_problem(24, 20, batch=2)]
+    precision = S.FP64 if prec == "fp64" else S.FP32_REFINE
+    pl, x, st, *_ = run(S, probs, precision, small_front_max=32, split_rows=-1, cluster_rows=40)
+    assert pl.info["tune_cluster_rows"] == 40
+    off = 0
+    for k, p in enumerate(probs):
+        for inst in range(2):
+            check_against_oracle(S, pl, p, x, st, inst, inst * 3 + k, col_off=off)
+        off += p.n
+    if prec == "fp64":
+        _, x_ref, st_ref, *_ = run(S, probs, precision, small_front_max=32, split_rows=-1, cluster_rows=-1)
+        assert np.all(st_ref["status"] == 0)
+        assert np.max(np.abs(x - x_ref)) <= 1e-12 * np.max(np.abs(x_ref))
+
+
 @pytest.mark.parametrize("seed", range(6))
 def test_fp64_random_patterns(S, seed):
     rng = np.random.default_rng(900 + seed)
