@@ -2312,9 +2312,18 @@ struct Prof {
             cudaEventRecord((cudaEvent_t)P.ev_pool[ev], s);
         }
     }
+    bool ended = false;
+    // Records the end event; call right after the launch, before any host
+    // work, so that host time is not charged to the kernel.
+    void end() {
+        if (ev >= 0 && !ended) {
+            cudaEventRecord((cudaEvent_t)P.ev_pool[ev + 1], s);
+            ended = true;
+        }
+    }
     void done(double flops, double bytes) {
         if (ev < 0) return;
-        cudaEventRecord((cudaEvent_t)P.ev_pool[ev + 1], s);
+        end();
         P.prof_recs.push_back(ProfRec{kind, ev, flops, bytes});
     }
 };
@@ -2498,6 +2507,7 @@ int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cud
         else
             k_assemble<float><<<g, 256, 0, s>>>(P.dt.groups, P.dt.chunks, P.dt.asm_idx, P.dt.asm_coef,
                                                 (const float*)vals, P.m, shift, P.n_pats, K, P.nnzK);
+        pr.end();
         if (pr.ev >= 0) {
             double fl = 0, by = 0, sv = vdt == SSCO_VALS_F64 ? 8 : 4;
             for (const AsmGroup& g2 : P.groups) {
@@ -2516,6 +2526,7 @@ int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cud
                            tiny_factor_bytes<T>(share, P.tiny_prog_max, P.tiny_k_max), s>>>(
             P.dt, P.n_tiny, B, P.tiny_prog_max, P.tiny_k_max, K, P.nnzK, panel, P.panel_total, upd, P.upd_total, bad,
             P.n_pats, share ? 1 : 0);
+        pr.end();
         if (pr.ev >= 0) {
             Work w = work_tiny(P, false);
             pr.done(w.flops, w.bytes);
@@ -2531,6 +2542,7 @@ int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cud
                 k_front_warp<T><<<cdiv(items, 8), 256, 8 * (size_t)ll.rmax * (ll.rmax + 1) / 2 * sizeof(T), s>>>(
                     P.dt, list, ll.count, B, ll.rmax, K, P.nnzK, panel, P.panel_total, upd, P.upd_total, bad,
                     P.n_pats);
+                pr.end();
                 if (pr.ev >= 0) {
                     Work w = work_front_small(P, ll);
                     pr.done(w.flops, w.bytes);
@@ -2548,6 +2560,7 @@ int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cud
             k_front_small<T><<<dim3(ll.count, B), dim3(32, nw), smem, s>>>(P.dt, list, K, P.nnzK, panel,
                                                                            P.panel_total, upd, P.upd_total, bad,
                                                                            P.n_pats);
+            pr.end();
             if (pr.ev >= 0) {
                 Work w = work_front_small(P, ll);
                 pr.done(w.flops, w.bytes);
@@ -2558,6 +2571,7 @@ int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cud
             Prof pr(P, s, SSCO_K_BIG_INIT);
             k_big_init<T><<<dim3((unsigned)ll.max_lower_tiles, ll.count, B), 256, 0, s>>>(
                 P.dt, list, panel, P.panel_total, upd, P.upd_total);
+            pr.end();
             if (pr.ev >= 0) {
                 double by = 0;
                 for (int32_t q = 0; q < ll.count; ++q) {
@@ -2576,6 +2590,7 @@ int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cud
             Prof pr(P, s, SSCO_K_BIG_KSCATTER);
             k_big_kscatter<T><<<dim3(cdiv(ll.max_klist, 256), ll.count, B), 256, 0, s>>>(P.dt, list, K, P.nnzK,
                                                                                        panel, P.panel_total);
+            pr.end();
             if (pr.ev >= 0) {
                 double by = 0;
                 for (int32_t q = 0; q < ll.count; ++q)
@@ -2599,6 +2614,7 @@ int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cud
                     Prof pd(P, s, SSCO_K_BIG_POTRF);
                     k_big_potrf<T><<<dim3(ll.count, B), 32, 0, s>>>(P.dt, list, kb, panel, P.panel_total, bad,
                                                                      P.n_pats);
+                    pd.end();
                     if (pd.ev >= 0) {
                         double fl = 0, by = 0;
                         for (int32_t q = 0; q < ll.count; ++q) {
@@ -2616,6 +2632,7 @@ int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cud
                     k_big_trsm<T><<<dim3(cdiv(ll.rmax - c0, 256), ll.count, B), 256, 0, s>>>(
                         P.dt, list, kb, panel, P.panel_total, tc ? wsp<float>(P, P.ws.tcpack) : nullptr,
                         P.tc_pack_total, C0);
+                    pr.end();
                     if (pr.ev >= 0) {
                         double fl = 0, by = 0;
                         for (int32_t q = 0; q < ll.count; ++q) {
@@ -3286,6 +3303,7 @@ void run_trisolve(Plan& P, const int32_t* active, cudaStream_t s) {
         k_tiny_fwd<T><<<tiny_grid, 32 * kTinyWarps, tiny_solve_bytes<T>(tiny_share(B), P.tiny_prog_max), s>>>(
             P.dt, P.n_tiny, B, P.tiny_prog_max, panel, P.panel_total, vecT, P.n, pvec, P.pvec_total, active,
             P.n_pats, tiny_share(B) ? 1 : 0);
+        pr.end();
         if (pr.ev >= 0) {
             Work w = work_tiny(P, true);
             pr.done(w.flops, w.bytes);
@@ -3301,6 +3319,7 @@ void run_trisolve(Plan& P, const int32_t* active, cudaStream_t s) {
             const int32_t* lst = P.dt.front_lists + ll.list_off + q;
             launch_cluster<T>(P, k_fwd_cluster<T>, qc, B, cluster_smem<T>(P, ll, q, qc), s, P.dt, lst,
                               (const T*)panel, P.panel_total, vecT, P.n, pvec, P.pvec_total, active, P.n_pats);
+            pr.end();
             if (pr.ev >= 0) {
                 LaunchList sub = ll;
                 sub.list_off += q;
@@ -3325,6 +3344,7 @@ void run_trisolve(Plan& P, const int32_t* active, cudaStream_t s) {
         } else
         k_fwd<T><<<dim3(ll.count, B), solve_threads(P, ll), smem, s>>>(P.dt, P.dt.front_lists + ll.list_off, panel, P.panel_total,
                                                         vecT, P.n, pvec, P.pvec_total, active, P.n_pats);
+        pr.end();
         if (pr.ev >= 0) {
             Work w = work_solve(P, ll);
             pr.done(w.flops, w.bytes);
@@ -3340,6 +3360,7 @@ void run_trisolve(Plan& P, const int32_t* active, cudaStream_t s) {
             const int32_t* lst = P.dt.front_lists + ll.list_off + q;
             launch_cluster<T>(P, k_bwd_cluster<T>, qc, B, cluster_smem<T>(P, ll, q, qc), s, P.dt, lst,
                               (const T*)panel, P.panel_total, vecT, P.n, active, P.n_pats);
+            pr.end();
             if (pr.ev >= 0) {
                 LaunchList sub = ll;
                 sub.list_off += q;
@@ -3364,6 +3385,7 @@ void run_trisolve(Plan& P, const int32_t* active, cudaStream_t s) {
         } else
         k_bwd<T><<<dim3(ll.count, B), solve_threads(P, ll), smem, s>>>(P.dt, P.dt.front_lists + ll.list_off, panel, P.panel_total,
                                                         vecT, P.n, active, P.n_pats);
+        pr.end();
         if (pr.ev >= 0) {
             Work w = work_solve(P, ll);
             pr.done(w.flops, w.bytes);
@@ -3374,6 +3396,7 @@ void run_trisolve(Plan& P, const int32_t* active, cudaStream_t s) {
         k_tiny_bwd<T><<<tiny_grid, 32 * kTinyWarps, tiny_solve_bytes<T>(tiny_share(B), P.tiny_prog_max), s>>>(
             P.dt, P.n_tiny, B, P.tiny_prog_max, panel, P.panel_total, vecT, P.n, active, P.n_pats,
             tiny_share(B) ? 1 : 0);
+        pr.end();
         if (pr.ev >= 0) {
             Work w = work_tiny(P, true);
             pr.done(w.flops, w.bytes);
