@@ -242,6 +242,12 @@ struct Plan {
     int32_t g_vdt = -1;
     int64_t g_launches = 0;
 
+    // auxiliary streams for the independent launch lists of a level, with a
+    // fork event and one join event per stream (created on first use)
+    void* aux_stream[4] = {nullptr, nullptr, nullptr, nullptr};
+    void* aux_join[4] = {nullptr, nullptr, nullptr, nullptr};
+    void* aux_fork = nullptr;
+
     std::string last_error;
     int64_t launches = 0;
 

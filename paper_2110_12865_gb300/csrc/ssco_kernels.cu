@@ -2484,6 +2484,28 @@ void launch_big_update(Plan& P, const LaunchList& ll, const int32_t* list, int k
     }
 }
 
+// Creates the plan's auxiliary streams and events on first use; returns how
+// many are available (0 if creation failed, or while per-launch profiling is
+// on, so that each launch's events time that kernel alone: everything then
+// runs on the caller's stream).
+inline int ensure_aux_streams(Plan& P) {
+    if (P.prof) return 0;
+    if (!P.aux_fork) {
+        cudaEvent_t f;
+        if (cudaEventCreateWithFlags(&f, cudaEventDisableTiming) != cudaSuccess) return 0;
+        for (int i = 0; i < 4; ++i) {
+            cudaStream_t st;
+            cudaEvent_t e;
+            if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return 0;
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return 0;
+            P.aux_stream[i] = st;
+            P.aux_join[i] = e;
+        }
+        P.aux_fork = f;
+    }
+    return 4;
+}
+
 template <class T>
 int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cudaStream_t s) {
     const int B = P.B;
@@ -2532,14 +2554,43 @@ int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cud
             pr.done(w.flops, w.bytes);
         }
     }
-    for (const LaunchList& ll : P.fact_launches) {
+    // The launch lists of one level (the size classes of small fronts, the
+    // big fronts) are independent: all but the last go to the plan's
+    // auxiliary streams, forked from s at the level's start and joined back
+    // at the next level's (in a captured graph: parallel branches).
+    const int n_aux = ensure_aux_streams(P);
+    size_t lvl_begin = 0, lvl_end = 0;
+    int nl = 0;
+    auto join_level = [&]() {
+        if (nl <= 1) return;
+        for (int k = 0; k < std::min(nl - 1, n_aux); ++k) {
+            cudaEventRecord((cudaEvent_t)P.aux_join[k], (cudaStream_t)P.aux_stream[k]);
+            cudaStreamWaitEvent(s, (cudaEvent_t)P.aux_join[k], 0);
+        }
+    };
+    for (size_t li = 0; li < P.fact_launches.size(); ++li) {
+        const LaunchList& ll = P.fact_launches[li];
+        if (li == lvl_end) {
+            join_level();
+            lvl_begin = li;
+            lvl_end = li;
+            while (lvl_end < P.fact_launches.size() && P.fact_launches[lvl_end].level == ll.level) ++lvl_end;
+            nl = n_aux > 0 ? (int)(lvl_end - lvl_begin) : 1;
+            if (nl > 1) {
+                cudaEventRecord((cudaEvent_t)P.aux_fork, s);
+                for (int k = 0; k < std::min(nl - 1, n_aux); ++k)
+                    cudaStreamWaitEvent((cudaStream_t)P.aux_stream[k], (cudaEvent_t)P.aux_fork, 0);
+            }
+        }
+        const int kk = (int)(li - lvl_begin);
+        cudaStream_t st = (nl > 1 && kk < nl - 1) ? (cudaStream_t)P.aux_stream[kk % n_aux] : s;
         const int32_t* list = P.dt.front_lists + ll.list_off;
         if (ll.cls > 0) {
             constexpr int V = sizeof(T) == 4 ? 4 : 2;
             if (ll.cls <= P.tune.warp_front_max && ll.rmax <= 64 && (int64_t)ll.count * B >= P.tune.warp_items) {
-                Prof pr(P, s, SSCO_K_FRONT_SMALL);
+                Prof pr(P, st, SSCO_K_FRONT_SMALL);
                 const int64_t items = (int64_t)ll.count * B;
-                k_front_warp<T><<<cdiv(items, 8), 256, 8 * (size_t)ll.rmax * (ll.rmax + 1) / 2 * sizeof(T), s>>>(
+                k_front_warp<T><<<cdiv(items, 8), 256, 8 * (size_t)ll.rmax * (ll.rmax + 1) / 2 * sizeof(T), st>>>(
                     P.dt, list, ll.count, B, ll.rmax, K, P.nnzK, panel, P.panel_total, upd, P.upd_total, bad,
                     P.n_pats);
                 pr.end();
@@ -2550,14 +2601,14 @@ int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cud
                 continue;
             }
             const bool vec = ll.cls <= P.tune.vec_max_cls && B >= V;
-            Prof pr(P, s, vec ? SSCO_K_FRONT_VEC : SSCO_K_FRONT_SMALL);
+            Prof pr(P, st, vec ? SSCO_K_FRONT_VEC : SSCO_K_FRONT_SMALL);
             const int nw = ll.cls <= 32 ? 2 : (ll.cls <= 64 ? 4 : 8);
             const size_t smem = ((size_t)ll.rmax * (ll.rmax + 1) / 2 + kSmallPad) * sizeof(T);
             if (vec)
-                k_front_vec<T, V><<<dim3(ll.count, (B + V - 1) / V), dim3(32, nw), smem * V, s>>>(
+                k_front_vec<T, V><<<dim3(ll.count, (B + V - 1) / V), dim3(32, nw), smem * V, st>>>(
                     P.dt, list, B, K, P.nnzK, panel, P.panel_total, upd, P.upd_total, bad, P.n_pats);
             else
-            k_front_small<T><<<dim3(ll.count, B), dim3(32, nw), smem, s>>>(P.dt, list, K, P.nnzK, panel,
+            k_front_small<T><<<dim3(ll.count, B), dim3(32, nw), smem, st>>>(P.dt, list, K, P.nnzK, panel,
                                                                            P.panel_total, upd, P.upd_total, bad,
                                                                            P.n_pats);
             pr.end();
@@ -2568,8 +2619,8 @@ int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cud
             continue;
         }
         {
-            Prof pr(P, s, SSCO_K_BIG_INIT);
-            k_big_init<T><<<dim3((unsigned)ll.max_lower_tiles, ll.count, B), 256, 0, s>>>(
+            Prof pr(P, st, SSCO_K_BIG_INIT);
+            k_big_init<T><<<dim3((unsigned)ll.max_lower_tiles, ll.count, B), 256, 0, st>>>(
                 P.dt, list, panel, P.panel_total, upd, P.upd_total);
             pr.end();
             if (pr.ev >= 0) {
@@ -2587,8 +2638,8 @@ int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cud
             }
         }
         {
-            Prof pr(P, s, SSCO_K_BIG_KSCATTER);
-            k_big_kscatter<T><<<dim3(cdiv(ll.max_klist, 256), ll.count, B), 256, 0, s>>>(P.dt, list, K, P.nnzK,
+            Prof pr(P, st, SSCO_K_BIG_KSCATTER);
+            k_big_kscatter<T><<<dim3(cdiv(ll.max_klist, 256), ll.count, B), 256, 0, st>>>(P.dt, list, K, P.nnzK,
                                                                                        panel, P.panel_total);
             pr.end();
             if (pr.ev >= 0) {
@@ -2611,8 +2662,8 @@ int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cud
             for (int c0 = C0; c0 < std::min(Cend, (int)ll.wmax); c0 += 32) {
                 const int kb = c0 / 32;
                 {
-                    Prof pd(P, s, SSCO_K_BIG_POTRF);
-                    k_big_potrf<T><<<dim3(ll.count, B), 32, 0, s>>>(P.dt, list, kb, panel, P.panel_total, bad,
+                    Prof pd(P, st, SSCO_K_BIG_POTRF);
+                    k_big_potrf<T><<<dim3(ll.count, B), 32, 0, st>>>(P.dt, list, kb, panel, P.panel_total, bad,
                                                                      P.n_pats);
                     pd.end();
                     if (pd.ev >= 0) {
@@ -2628,8 +2679,8 @@ int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cud
                     }
                 }
                 {
-                    Prof pr(P, s, SSCO_K_BIG_TRSM);
-                    k_big_trsm<T><<<dim3(cdiv(ll.rmax - c0, 256), ll.count, B), 256, 0, s>>>(
+                    Prof pr(P, st, SSCO_K_BIG_TRSM);
+                    k_big_trsm<T><<<dim3(cdiv(ll.rmax - c0, 256), ll.count, B), 256, 0, st>>>(
                         P.dt, list, kb, panel, P.panel_total, tc ? wsp<float>(P, P.ws.tcpack) : nullptr,
                         P.tc_pack_total, C0);
                     pr.end();
@@ -2645,11 +2696,12 @@ int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cud
                         pr.done(fl * B, by * B);
                     }
                 }
-                if (c0 + 32 < Cend) launch_big_update<T>(P, ll, list, C0, c0, 32, Cend, panel, upd, tc, s);
+                if (c0 + 32 < Cend) launch_big_update<T>(P, ll, list, C0, c0, 32, Cend, panel, upd, tc, st);
             }
-            launch_big_update<T>(P, ll, list, C0, C0, SB, -1, panel, upd, tc, s);
+            launch_big_update<T>(P, ll, list, C0, C0, SB, -1, panel, upd, tc, st);
         }
     }
+    join_level();
     return (int)cudaGetLastError();
 }
 
@@ -3691,6 +3743,13 @@ void graph_destroy_streams(Plan& P) {
     if (P.g_stream) cudaStreamDestroy((cudaStream_t)P.g_stream);
     if (P.g_body_stream) cudaStreamDestroy((cudaStream_t)P.g_body_stream);
     P.g_stream = P.g_body_stream = nullptr;
+    for (int i = 0; i < 4; ++i) {
+        if (P.aux_stream[i]) cudaStreamDestroy((cudaStream_t)P.aux_stream[i]);
+        if (P.aux_join[i]) cudaEventDestroy((cudaEvent_t)P.aux_join[i]);
+        P.aux_stream[i] = P.aux_join[i] = nullptr;
+    }
+    if (P.aux_fork) cudaEventDestroy((cudaEvent_t)P.aux_fork);
+    P.aux_fork = nullptr;
 }
 
 int launch_graph_run(Plan& P, const void* vals, int32_t vdt, const double* shift, const double* b, double* x,
