@@ -433,7 +433,7 @@ __global__ void __launch_bounds__(256) k_front_vec(const DevTables t, const int3
     const int r = d.r, w = d.w;
     const int lane = threadIdx.x, warp = threadIdx.y, nw = blockDim.y;
     const int tid = lane + 32 * warp, nth = 32 * nw;
-    const int npk = r * (r + 1) / 2;
+    const int npk = r * (r + 1) / 2 + kSmallPad;
     for (int q = tid; q < npk * V; q += nth) F[q] = T(0);
     __syncthreads();
     const int32_t* kl = t.klist + 2 * d.klist_off;
@@ -552,25 +552,19 @@ __global__ void __launch_bounds__(256) k_front_vec(const DevTables t, const int3
                     for (int a = 0; a < 4; ++a) ii[a] = j1 + r0 + tx + 16 * a;
 #pragma unroll
                     for (int q = 0; q < 2; ++q) kk[q] = j1 + c0 + ty + ny * q;
+                    // rows / columns past r read the next column's entries or
+                    // the zero padding (within the allocation); they only
+                    // reach accumulators the epilogue skips
+                    const T* Fi = F + (int64_t)(packed_col(j0, r) - j0 + ii[0]) * V;
+                    const T* Fk = F + (int64_t)(packed_col(j0, r) - j0 + kk[0]) * V;
                     for (int j = j0; j < j1; ++j) {
-                        const T* Fj = F + (int64_t)(packed_col(j, r) - j) * V;
                         T ra[4][V], cb[2][V];
 #pragma unroll
-                        for (int a = 0; a < 4; ++a) {
-                            if (ii[a] < r)
-                                vld<T, V>(Fj + (int64_t)ii[a] * V, ra[a]);
-                            else
+                        for (int a = 0; a < 4; ++a) vld<T, V>(Fi + (int64_t)(16 * a) * V, ra[a]);
 #pragma unroll
-                                for (int v = 0; v < V; ++v) ra[a][v] = T(0);
-                        }
-#pragma unroll
-                        for (int q = 0; q < 2; ++q) {
-                            if (kk[q] < r)
-                                vld<T, V>(Fj + (int64_t)kk[q] * V, cb[q]);
-                            else
-#pragma unroll
-                                for (int v = 0; v < V; ++v) cb[q][v] = T(0);
-                        }
+                        for (int q = 0; q < 2; ++q) vld<T, V>(Fk + (int64_t)(ny * q) * V, cb[q]);
+                        Fi += (int64_t)(r - j - 1) * V;
+                        Fk += (int64_t)(r - j - 1) * V;
 #pragma unroll
                         for (int a = 0; a < 4; ++a)
 #pragma unroll
