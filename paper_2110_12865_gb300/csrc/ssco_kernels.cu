@@ -733,7 +733,7 @@ __device__ __forceinline__ int tiny_chol_rows(T (*F)[33], int lane, int r, int w
 }
 
 template <class T>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2)
     k_tiny_factor(const DevTables t, int32_t n_tiny, int32_t B, int32_t prog_max, int32_t k_max,
                   const double* __restrict__ K, int64_t nnzK, T* __restrict__ panel, int64_t panel_total,
                   T* __restrict__ upd, int64_t upd_total, int32_t* __restrict__ bad_col, int32_t n_pats,

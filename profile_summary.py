@@ -84,14 +84,21 @@ def traffic(path, kinds):
             continue
         by = value(d, {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "KB": 1e3, "MB": 1e6, "GB": 1e9})
         per[(d["ID"], stem(d["Kernel Name"]))][d["Metric Name"]] += by
-    out = {"source_sha256": hashlib.sha256(open(KERNEL_SOURCE, "rb").read()).hexdigest(),
-           "capture": os.path.basename(path), "kernels": {}}
+    sha = hashlib.sha256(open(KERNEL_SOURCE, "rb").read()).hexdigest()
+    dst = os.path.join(ROOT, "profiles", "traffic.json")
+    out = {"source_sha256": sha, "kernels": {}}
+    try:  # merge with earlier captures of the same kernel source
+        old = json.load(open(dst))
+        if old.get("source_sha256") == sha:
+            out = old
+    except Exception:
+        pass
     for kind in kinds:
         stems = set(KIND_STEMS[kind])
         vals = [v["dram__bytes_read.sum"] + v["dram__bytes_write.sum"] for (i, st), v in per.items() if st in stems]
         if vals:
-            out["kernels"][kind] = {"launches": len(vals), "dram_bytes_per_launch": sum(vals) / len(vals)}
-    dst = os.path.join(ROOT, "profiles", "traffic.json")
+            out["kernels"][kind] = {"launches": len(vals), "dram_bytes_per_launch": sum(vals) / len(vals),
+                                    "capture": os.path.basename(path)}
     json.dump(out, open(dst, "w"), indent=1)
     print(json.dumps(out, indent=1))
 
