@@ -30,10 +30,10 @@ KERNEL_SOURCE = os.path.join(ROOT, "paper_2110_12865_gb300", "csrc", "ssco_kerne
 KIND_STEMS = {
     "assemble": ["k_assemble"], "front_small": ["k_front_small"], "front_vec": ["k_front_vec"],
     "front_tiny": ["k_tiny_factor"], "big_init": ["k_big_init"], "big_kscatter": ["k_big_kscatter"],
-    "big_potrf": ["k_big_potrf"], "big_trsm": ["k_big_trsm"], "big_update_tc": ["k_big_update_tc"],
+    "big_potrf": ["k_big_potrf"], "big_trsm": ["k_big_trsm"], "big_update_tc": ["k_big_update_tc", "k_big_update_tcp"],
     "big_update": ["k_big_update", "k_big_update_f32"],
-    "fwd_solve": ["k_fwd", "k_fwd_warp", "k_tiny_fwd", "k_fsplit_init", "k_fsplit_step"],
-    "bwd_solve": ["k_bwd", "k_bwd_warp", "k_tiny_bwd", "k_bsplit_init", "k_bsplit_step"],
+    "fwd_solve": ["k_fwd", "k_fwd_warp", "k_tiny_fwd", "k_fsplit_init", "k_fsplit_step", "k_fwd_cluster"],
+    "bwd_solve": ["k_bwd", "k_bwd_warp", "k_tiny_bwd", "k_bsplit_init", "k_bsplit_step", "k_bwd_cluster"],
     "resid": ["k_resid"], "check": ["k_check"],
 }
 
