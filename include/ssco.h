@@ -290,6 +290,25 @@ ssco_status ssco_refactor_solve_host(ssco_plan plan, const void* vals, int32_t v
  * cudaFree or other allocating routine. */
 ssco_status ssco_solve_noalloc(ssco_plan plan, const double* b, double* x, void* stream);
 
+/* Value construction upstream of assembly (no plan): cotangent edge weights
+ * of a planar triangle mesh from vertex positions, per value set (the
+ * cotangent Laplacian of Sec. 5.3's mesh experiments):
+ *   w[b][e] = 1/2 * sum over the triangles holding edge e of
+ *             cot(angle opposite e),  cot = (u . v) / |u x v|,
+ * u, v the two edges leaving that corner (unsigned area, so weights may be
+ * negative on obtuse angles).  All pointers are device pointers:
+ *   tri      [n_tri][3] int32 vertex ids;
+ *   tri_edge [n_tri][3] int32 id of the edge opposite each corner;
+ *   xy       [batch][n_vert][2] double positions;
+ *   w        [batch][n_edge] double, overwritten.
+ * Each edge must belong to at most two triangles (then the result does not
+ * depend on summation order); a degenerate triangle gives non-finite
+ * weights (the numeric phase then reports SSCO_ERR_NONFINITE).  Async on
+ * `stream`; returns SSCO_ERR_INVALID_ARG for inconsistent sizes or null
+ * pointers, SSCO_ERR_CUDA if the launch fails. */
+ssco_status ssco_cotan_weights(const int32_t* tri, const int32_t* tri_edge, int64_t n_tri, int64_t n_vert,
+                               int64_t n_edge, int32_t batch, const double* xy, double* w, void* stream);
+
 /* Number of kernel launches the last ssco_numeric / ssco_solve /
  * ssco_backward / ssco_refactor_solve_host call issued (host counter). */
 int64_t ssco_last_launch_count(ssco_plan plan);

@@ -75,6 +75,8 @@ def lib():
         L.or_grad_atwa.argtypes = [C.c_int32, i64p, i32p, f64p, f64p, f64p, f64p]
         L.or_grad_elem.restype = None
         L.or_grad_elem.argtypes = [C.c_int32, C.c_int32, i32p, f64p, f64p, f64p, f64p]
+        L.or_cotan_weights.restype = None
+        L.or_cotan_weights.argtypes = [C.c_int64, i32p, i32p, f64p, C.c_int64, f64p]
         _lib = L
     return _lib
 
@@ -236,3 +238,14 @@ def backward(p, r: Result, xbar, inst: int = 0):
     vbar = grad_vals(p, mu, r.x)
     sbar = -float(np.dot(mu[shifted_mask(p)], r.x[shifted_mask(p)]))
     return vbar, sbar, mu
+
+
+def cotan_weights(tri, tri_edge, xy, n_edge: int):
+    """Cotangent edge weights of one value set (Sec. 5.3 mesh experiments):
+    w_e = 1/2 sum over the triangles holding e of cot(angle opposite e),
+    cot = (u . v)/|u x v|; tri / tri_edge [n_tri][3], xy [n_vert][2]."""
+    tri = _c(tri, np.int32)
+    te = _c(tri_edge, np.int32)
+    w = np.empty(int(n_edge))
+    lib().or_cotan_weights(tri.shape[0], tri, te, _c(xy, np.float64), int(n_edge), w)
+    return w

@@ -467,3 +467,24 @@ void or_grad_elem(int32_t m, int32_t dim, const int32_t* dofs, const double* K0,
         Ebar[e] = -g;
     }
 }
+
+/* Cotangent edge weights of a planar triangle mesh (the cotangent Laplacian
+ * of the mesh experiments, Sec. 5.3): for every triangle and each of its
+ * corners k with the other two corners i, j (in the triangle's cyclic
+ * order), cot(angle at k) = (u . v) / |u x v| with u = p_i - p_k,
+ * v = p_j - p_k, and half of it is added to the edge opposite k.  One value
+ * set; xy is [n_vert][2]. */
+void or_cotan_weights(int64_t n_tri, const int32_t* tri, const int32_t* tri_edge, const double* xy, int64_t n_edge,
+                      double* w) {
+    for (int64_t e = 0; e < n_edge; ++e) w[e] = 0.0;
+    for (int64_t t = 0; t < n_tri; ++t) {
+        for (int c = 0; c < 3; ++c) {
+            int32_t k = tri[3 * t + c], i = tri[3 * t + (c + 1) % 3], j = tri[3 * t + (c + 2) % 3];
+            double ux = xy[2 * i] - xy[2 * k], uy = xy[2 * i + 1] - xy[2 * k + 1];
+            double vx = xy[2 * j] - xy[2 * k], vy = xy[2 * j + 1] - xy[2 * k + 1];
+            double dot = ux * vx + uy * vy;
+            double cross = fabs(ux * vy - uy * vx);
+            w[tri_edge[3 * t + c]] += 0.5 * dot / cross;
+        }
+    }
+}

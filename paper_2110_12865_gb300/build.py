@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libssco.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["ssco_api.cpp", "ssco_symbolic.cpp", "ssco_kernels.cu"]
+SOURCES = ["ssco_api.cpp", "ssco_symbolic.cpp", "ssco_kernels.cu", "ssco_values.cu"]
 HEADERS = ["ssco_internal.h"]
 
 NVCC = os.environ.get("NVCC", "nvcc")

@@ -300,15 +300,17 @@ def trigrid_problem(s: int, batch: int = 1, cfg: int = 3, jitter: float = 0.3,
     vals = np.empty((batch, m))
     shifts = np.empty(batch)
     b = np.empty((batch, n))
+    positions = np.empty((batch, n, 2))
     for i in range(batch):
         rng = np.random.default_rng(seed_for(cfg, seed_offset + i))
         pos = base + rng.uniform(-jitter * h, jitter * h, base.shape)
+        positions[i] = pos
         vals[i] = cotan_weights(pos, faces, (edges, opp))
         shifts[i] = rng.uniform(1e-3, 1e-1)
         b[i] = rng.standard_normal(n)
     perm = nested_dissection((s, s))
     return _atwa(f"trigrid{s}", n, m, rowptr, colind, aval, perm, vals, shifts, b,
-                 dims=(s, s), edges=edges)
+                 dims=(s, s), edges=edges, faces=faces, opp=opp, positions=positions)
 
 
 def uneven_trigrid_sides(count: int = 64, lo: int = 32, ratio: float = 8.0):

@@ -32,6 +32,7 @@ EXPORTED_SYMBOLS = [
     "ssco_backward", "ssco_status_get", "ssco_export_L", "ssco_export_K", "ssco_refactor_solve_host",
     "ssco_last_launch_count", "ssco_last_error", "ssco_status_string", "ssco_plan_save", "ssco_plan_load",
     "ssco_destroy", "ssco_profile_enable", "ssco_profile_read", "ssco_kernel_name", "ssco_solve_noalloc", "ssco_profile_trace", "ssco_graph_run", "ssco_autotune",
+    "ssco_cotan_weights",
 ]
 KERNEL_KINDS = ["assemble", "front_small", "big_init", "big_kscatter", "big_update", "big_potrf", "big_syrk",
                 "fwd_solve", "bwd_solve", "resid", "check", "vector", "grad", "front_tiny", "big_trsm", "front_vec",
@@ -103,6 +104,7 @@ def load_library(path: str = LIB_PATH):
         "ssco_export_K": (i32, [vp, vp, vp]),
         "ssco_refactor_solve_host": (i32, [vp, vp, i32, vp, vp, vp, vp]),
         "ssco_last_launch_count": (i64, [vp]),
+        "ssco_cotan_weights": (i32, [vp, vp, i64, i64, i64, i32, vp, vp, vp]),
         "ssco_last_error": (C.c_char_p, [vp]),
         "ssco_status_string": (C.c_char_p, [i32]),
         "ssco_plan_save": (i32, [vp, C.c_char_p]),
@@ -399,3 +401,22 @@ class SscoSolve(torch.autograd.Function):
 
 def ssco_solve(plan: Plan, vals, shift, b):
     return SscoSolve.apply(plan, vals, shift, b)
+
+
+def cotan_weights(tri: torch.Tensor, tri_edge: torch.Tensor, xy: torch.Tensor, n_edge: int, stream=None, out=None):
+    """Cotangent edge weights [batch, n_edge] (float64, device) of a planar
+    triangle mesh from vertex positions xy [batch, n_vert, 2] (float64,
+    device); tri / tri_edge [n_tri, 3] int32 device tensors (vertex ids,
+    edge opposite each corner).  See ssco_cotan_weights in ssco.h."""
+    L = load_library()
+    tri = tri.to(torch.int32).contiguous()
+    tri_edge = tri_edge.to(torch.int32).contiguous()
+    xy = xy.to(torch.float64).contiguous()
+    batch, n_vert = int(xy.shape[0]), int(xy.shape[1])
+    w = out if out is not None else torch.empty((batch, int(n_edge)), dtype=torch.float64, device=xy.device)
+    assert w.dtype == torch.float64 and w.is_contiguous() and tuple(w.shape) == (batch, int(n_edge))
+    st = L.ssco_cotan_weights(_ptr(tri), _ptr(tri_edge), int(tri.shape[0]), n_vert, int(n_edge), batch, _ptr(xy),
+                              _ptr(w), _stream_ptr(stream))
+    if st != SSCO_OK:
+        raise SscoError(st, "ssco_cotan_weights")
+    return w

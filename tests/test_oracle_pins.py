@@ -425,3 +425,59 @@ def test_adjoint_symmetry():
     a = np.dot(r.S.solve(r.L, p.perm, u), v)
     b = np.dot(u, r.S.solve(r.L, p.perm, v))
     assert abs(a - b) <= 1e-12 * max(abs(a), 1.0)
+
+
+# ---------------------------------------------------------------------------
+# Cotangent weights (value construction upstream of assembly, Sec. 5.3):
+# pinned by closed-form triangles, similarity invariance and the linear
+# precision of the cotangent Laplacian on planar meshes.
+def _edges_of(faces):
+    return P.faces_to_edges(np.asarray(faces, np.int64))
+
+
+def test_cotan_right_isoceles_and_equilateral():
+    # corner at the right angle: cot 90 = 0; the 45-degree corners: cot = 1
+    w = O.cotan_weights([[0, 1, 2]], [[0, 1, 2]], [[0.0, 0.0], [1.0, 0.0], [0.0, 1.0]], 3)
+    assert np.array_equal(w, [0.0, 0.5, 0.5])
+    h = np.sqrt(3.0) / 2
+    w = O.cotan_weights([[0, 1, 2]], [[0, 1, 2]], [[0.0, 0.0], [1.0, 0.0], [0.5, h]], 3)
+    assert np.allclose(w, 0.5 / np.sqrt(3.0), rtol=0, atol=1e-15)
+
+
+def test_cotan_two_right_triangles_share_a_diagonal():
+    faces = [[0, 1, 2], [0, 2, 3]]  # unit square split along (0,0)-(1,1)
+    edges, opp = _edges_of(faces)
+    xy = [[0.0, 0.0], [1.0, 0.0], [1.0, 1.0], [0.0, 1.0]]
+    w = O.cotan_weights(faces, opp, xy, edges.shape[0])
+    diag = [e for e, (a, b) in enumerate(edges) if {int(a), int(b)} == {0, 2}][0]
+    assert w[diag] == 0.0  # both opposite corners are right angles
+    assert np.allclose(np.delete(w, diag), 0.5, rtol=0, atol=1e-15)
+
+
+def test_cotan_similarity_invariance_and_linear_precision():
+    s = 9
+    faces = P.trigrid_faces(s, s)
+    edges, opp = P.faces_to_edges(faces)
+    rng = np.random.default_rng(7)
+    base = np.stack(np.meshgrid(np.arange(s), np.arange(s), indexing="ij"), -1).reshape(-1, 2) / (s - 1.0)
+    xy = base + rng.uniform(-0.3, 0.3, base.shape) / (s - 1.0)
+    w = O.cotan_weights(faces, opp, xy, edges.shape[0])
+    th, sc, tr = 0.7, 3.5, np.array([2.0, -1.0])
+    R = np.array([[np.cos(th), -np.sin(th)], [np.sin(th), np.cos(th)]])
+    w2 = O.cotan_weights(faces, opp, sc * xy @ R.T + tr, edges.shape[0])
+    assert np.allclose(w2, w, rtol=1e-12, atol=1e-12)
+    # sum_j w_ij (p_j - p_i) = 0 at every interior vertex of a planar mesh
+    acc = np.zeros_like(xy)
+    for e, (a, b) in enumerate(edges):
+        acc[a] += w[e] * (xy[b] - xy[a])
+        acc[b] += w[e] * (xy[a] - xy[b])
+    ij = np.stack(np.meshgrid(np.arange(s), np.arange(s), indexing="ij"), -1).reshape(-1, 2)
+    interior = (ij.min(1) > 0) & (ij.max(1) < s - 1)
+    assert np.abs(acc[interior]).max() <= 1e-12
+
+
+def test_trigrid_problem_values_are_the_oracle_cotan_weights():
+    p = P.trigrid_problem(12, batch=2, cfg=3)
+    for i in range(2):
+        w = O.cotan_weights(p.faces, p.opp, p.positions[i], p.m)
+        assert np.array_equal(w, p.vals[i])
