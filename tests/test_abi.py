@@ -191,3 +191,42 @@ def test_fixed_dofs_are_identity_rows(S):
     fixed_new = iperm[np.nonzero(p.dof_fixed)[0]]
     assert np.all(cc[fixed_new] == 1)
     assert np.all(pl.export(S.EXPORT_ETREE)[fixed_new] == -1)
+
+
+@pytest.mark.parametrize("opt", [{"big_panel": 48}, {"big_panel": 16}, {"big_panel": 2048}, {"split_rows": -2},
+                                 {"warp_front_max": 65}, {"warp_front_max": -2}, {"cluster_rows": -5}])
+def test_invalid_plan_options_rejected(S, opt):
+    """Out-of-range launch-shape options are refused at analyze time with
+    SSCO_ERR_INVALID_ARG (host only, no device work)."""
+    with pytest.raises(S.SscoError) as ei:
+        S.Plan(P.grid_problem(6, 6, cfg=1), **opt)
+    assert ei.value.status == 1
+
+
+@pytest.mark.parametrize("opt,key,want", [({"big_panel": 96}, "tune_big_panel", 96),
+                                          ({"split_rows": -1}, "tune_split_rows", 1 << 30),
+                                          ({"cluster_rows": 300}, "tune_cluster_rows", 300),
+                                          ({"warp_front_max": 48}, "tune_warp_front_max", 48),
+                                          ({"tensor_cores": -1}, "tune_use_tc", 0),
+                                          ({"tensor_cores": 2}, "tune_use_tc", 2)])
+def test_plan_options_reach_the_tunables(S, opt, key, want):
+    pl = S.Plan(P.grid_problem(6, 6, cfg=1), precision=S.FP32_REFINE, **opt)
+    assert pl.info[key] == want
+
+
+def test_batch_dependent_solve_defaults(S):
+    """Few value sets: CTA clusters for fronts >= 512 rows and split solves
+    from 2048; many: no clusters, split from 1024."""
+    one = S.Plan(P.grid_problem(6, 6, batch=1, cfg=1), precision=S.FP32_REFINE)
+    many = S.Plan(P.grid_problem(6, 6, batch=16, cfg=1), precision=S.FP32_REFINE)
+    assert (one.info["tune_cluster_rows"], one.info["tune_split_rows"]) == (512, 2048)
+    assert (many.info["tune_cluster_rows"], many.info["tune_split_rows"]) == (1 << 30, 1024)
+
+
+def test_cotan_weights_argument_checks(S):
+    """ssco_cotan_weights refuses inconsistent sizes and null pointers before
+    touching the device."""
+    L = S.load_library()
+    assert L.ssco_cotan_weights(None, None, 1, 3, 3, 1, None, None, None) == 1  # null tables
+    assert L.ssco_cotan_weights(None, None, -1, 3, 3, 1, None, None, None) == 1  # negative count
+    assert L.ssco_cotan_weights(None, None, 0, 3, 3, 0, None, None, None) == 1  # batch < 1
