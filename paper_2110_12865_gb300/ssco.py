@@ -144,7 +144,20 @@ class Plan:
     """An analyzed fixed structure plus (after :meth:`bind`) its device memory.
 
     ``problems`` is one problem dict (see ``problems.py``) or a list of them
-    (several patterns concatenated, one value set each per instance)."""
+    (several patterns concatenated, one value set each per instance).
+
+    Options (the fields of ``ssco_op`` in ``ssco.h``; 0 = the default):
+    ``precision`` FP64 or FP32_REFINE (FP32 factor, FP64 refinement to
+    ``refine_tol`` within ``refine_max_iter`` corrections); ``batch`` value
+    sets per pattern; ``small_front_max`` rows above which a front takes the
+    multi-CTA path; ``amalgamate`` relaxed supernode merging (numeric
+    partition only); ``tiny_front_max`` warp-per-subtree fronts (<= 32, -1
+    off); ``tensor_cores`` 0 tcgen05 updates per tile, 2 persistent trailing
+    updates, -1 SIMT only; ``big_panel`` columns per trailing update of a big
+    front; ``split_rows`` / ``cluster_rows`` front sizes from which solves run
+    as multi-launch splits / one CTA cluster per front (-1 never);
+    ``warp_front_max`` small-front classes factored one warp per front.
+    ``autotune`` re-chooses the launch-shape options on the caller's data."""
 
     def __init__(self, problems, precision=FP64, batch=None, refine_tol=1e-10, refine_max_iter=30,
                  small_front_max=0, amalgamate=1, tiny_front_max=0, tensor_cores=0, big_panel=0,
