@@ -125,7 +125,8 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        import tempfile
+        self.path = os.path.join(tempfile.gettempdir(), f"ssco_bench_clocks_rank{index}_{os.getpid()}.csv")
 
     def start(self):
         try:
@@ -322,7 +323,7 @@ def run_ours(args, rank, world, local_rank):
         "metric": "batched refactor+solve/s (FP32 factor + FP64 refinement to rel. residual 1e-10)",
         "value": value, "unit": "systems/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 factor / f64 residual+update", "data": "synthetic (seeded meshes, see DESIGN.md)",
+        "dtype": "f32 factor / f64 residual+update", "data": "synthetic (seeded meshes and value sets)",
         "config": dict(desc, precision="fp32+refine", units_per_step=units, l2="flushed between steps "
                        "(256 MiB write); per-step working set also exceeds L2",
                        parallelism=f"independent value sets per rank x{world}",
