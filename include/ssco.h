@@ -48,7 +48,7 @@ typedef enum {
     SSCO_ERR_TIMEOUT = 6,      /* a bounded device wait gave up (all systems) */
     SSCO_ERR_CUDA = 7,         /* a CUDA runtime call failed                */
     SSCO_ERR_OOM = 8,          /* a caller buffer is smaller than required  */
-    SSCO_ERR_UNSUPPORTED = 9,  /* request outside what this build does      */
+    SSCO_ERR_UNSUPPORTED = 9,  /* request outside what the library supports  */
     SSCO_ERR_STATE = 10        /* call order violated (e.g. solve unbound)  */
 } ssco_status;
 
