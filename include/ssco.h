@@ -89,7 +89,7 @@ typedef struct {
  *   in FP32 and refines in FP64: r = b - K x with the FP64 K, d = solve32(r),
  *   x += d, until ||r||_2 <= refine_tol*||b||_2, refine_max_iter iterations,
  *   or stagnation (||r|| not halved over two iterations).
- * batch: value sets per pattern (>= 1).
+ * batch: value sets per pattern (1 .. 65535).
  * small_front_max: fronts with more rows than this use the multi-CTA dense
  *   path (0 = default for the precision).
  * amalgamate: 0 = fundamental supernodes only; 1 = relaxed amalgamation of

@@ -188,6 +188,8 @@ ssco_status analyze_impl(const ssco_pattern* const* pats, int32_t n_pats, const 
     if (op->precision != SSCO_FP64 && op->precision != SSCO_FP32_REFINE)
         return bad(P, SSCO_ERR_INVALID_ARG, "unknown precision");
     if (op->batch < 1) return bad(P, SSCO_ERR_INVALID_ARG, "batch must be >= 1");
+    // value sets are a grid dimension of the level launches
+    if (op->batch > 65535) return bad(P, SSCO_ERR_INVALID_ARG, "batch must be <= 65535");
     P.prec = op->precision;
     P.B = op->batch;
     P.tol = op->refine_tol > 0 ? op->refine_tol : 1e-10;
@@ -809,6 +811,8 @@ ssco_status analyze_impl(const ssco_pattern* const* pats, int32_t n_pats, const 
                 bl.max_syrk_tiles = std::max(bl.max_syrk_tiles, u * (u + 1) / 2);
                 bl.max_klist = std::max(bl.max_klist, d.klist_n);
             }
+            if (bl.count > 65535)  // the big-front kernels put the level's fronts in grid y
+                return bad(P, SSCO_ERR_UNSUPPORTED, "more than 65535 multi-CTA fronts in one level");
             if (bl.count > 0) P.fact_launches.push_back(bl);
         }
     }

@@ -194,7 +194,8 @@ def test_fixed_dofs_are_identity_rows(S):
 
 
 @pytest.mark.parametrize("opt", [{"big_panel": 48}, {"big_panel": 16}, {"big_panel": 2048}, {"split_rows": -2},
-                                 {"warp_front_max": 65}, {"warp_front_max": -2}, {"cluster_rows": -5}])
+                                 {"warp_front_max": 65}, {"warp_front_max": -2}, {"cluster_rows": -5},
+                                 {"batch": 0}, {"batch": 65536}])
 def test_invalid_plan_options_rejected(S, opt):
     """Out-of-range launch-shape options are refused at analyze time with
     SSCO_ERR_INVALID_ARG (host only, no device work)."""
