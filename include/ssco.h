@@ -301,13 +301,17 @@ ssco_status ssco_solve_noalloc(ssco_plan plan, const double* b, double* x, void*
  *   tri_edge [n_tri][3] int32 id of the edge opposite each corner;
  *   xy       [batch][n_vert][2] double positions;
  *   w        [batch][n_edge] double, overwritten.
+ *   n_bad    optional device int32: incremented once per triangle whose
+ *            vertex or edge ids are out of range (such triangles are
+ *            skipped, never dereferenced); may be NULL.
  * Each edge must belong to at most two triangles (then the result does not
  * depend on summation order); a degenerate triangle gives non-finite
  * weights (the numeric phase then reports SSCO_ERR_NONFINITE).  Async on
  * `stream`; returns SSCO_ERR_INVALID_ARG for inconsistent sizes or null
  * pointers, SSCO_ERR_CUDA if the launch fails. */
 ssco_status ssco_cotan_weights(const int32_t* tri, const int32_t* tri_edge, int64_t n_tri, int64_t n_vert,
-                               int64_t n_edge, int32_t batch, const double* xy, double* w, void* stream);
+                               int64_t n_edge, int32_t batch, const double* xy, double* w, int32_t* n_bad,
+                               void* stream);
 
 /* Number of kernel launches the last ssco_numeric / ssco_solve /
  * ssco_backward / ssco_refactor_solve_host call issued (host counter). */

@@ -18,15 +18,24 @@ namespace {
 // manifold mesh, so the sums do not depend on the order of the atomics.
 __global__ void k_cotan(const int32_t* __restrict__ tri, const int32_t* __restrict__ tri_edge, int64_t n_tri,
                         int64_t n_vert, int64_t n_edge, int32_t batch, const double* __restrict__ xy,
-                        double* __restrict__ w) {
+                        double* __restrict__ w, int32_t* __restrict__ n_bad) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int b = blockIdx.y;
     if (t >= n_tri || b >= batch) return;
     const double* p = xy + (int64_t)b * n_vert * 2;
     double* wb = w + (int64_t)b * n_edge;
     int v[3];
+    bool ok = true;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) v[c] = tri[3 * t + c];
+    for (int c = 0; c < 3; ++c) {
+        v[c] = tri[3 * t + c];
+        const int e = tri_edge[3 * t + c];
+        ok = ok && v[c] >= 0 && v[c] < n_vert && e >= 0 && e < n_edge;
+    }
+    if (!ok) {  // out-of-range ids: skipped and counted, never dereferenced
+        if (n_bad && b == 0) atomicAdd(n_bad, 1);
+        return;
+    }
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const int k = v[c], i = v[(c + 1) % 3], j = v[(c + 2) % 3];
@@ -43,7 +52,7 @@ __global__ void k_cotan(const int32_t* __restrict__ tri, const int32_t* __restri
 
 extern "C" ssco_status ssco_cotan_weights(const int32_t* tri, const int32_t* tri_edge, int64_t n_tri, int64_t n_vert,
                                           int64_t n_edge, int32_t batch, const double* xy, double* w,
-                                          void* stream) {
+                                          int32_t* n_bad, void* stream) {
     if (n_tri < 0 || n_vert < 0 || n_edge < 0 || batch < 1 || batch > 65535) return SSCO_ERR_INVALID_ARG;
     if ((n_tri > 0 && (!tri || !tri_edge || !xy)) || (n_edge > 0 && !w)) return SSCO_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
@@ -51,7 +60,7 @@ extern "C" ssco_status ssco_cotan_weights(const int32_t* tri, const int32_t* tri
         return SSCO_ERR_CUDA;
     if (n_tri > 0) {
         const dim3 grid((unsigned)((n_tri + 255) / 256), (unsigned)batch);
-        ssco::k_cotan<<<grid, 256, 0, s>>>(tri, tri_edge, n_tri, n_vert, n_edge, batch, xy, w);
+        ssco::k_cotan<<<grid, 256, 0, s>>>(tri, tri_edge, n_tri, n_vert, n_edge, batch, xy, w, n_bad);
         if (cudaGetLastError() != cudaSuccess) return SSCO_ERR_CUDA;
     }
     return SSCO_OK;

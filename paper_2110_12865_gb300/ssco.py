@@ -18,7 +18,7 @@ from . import problems as _problems
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libssco.so")
 
-SSCO_OK = 0
+SSCO_OK, SSCO_ERR_INVALID_ARG = 0, 1
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "PATTERN", 3: "NOT_SPD", 4: "NONFINITE",
                 5: "NO_CONVERGE", 6: "TIMEOUT", 7: "CUDA", 8: "OOM", 9: "UNSUPPORTED", 10: "STATE"}
 FP64, FP32_REFINE = 0, 1
@@ -104,7 +104,7 @@ def load_library(path: str = LIB_PATH):
         "ssco_export_K": (i32, [vp, vp, vp]),
         "ssco_refactor_solve_host": (i32, [vp, vp, i32, vp, vp, vp, vp]),
         "ssco_last_launch_count": (i64, [vp]),
-        "ssco_cotan_weights": (i32, [vp, vp, i64, i64, i64, i32, vp, vp, vp]),
+        "ssco_cotan_weights": (i32, [vp, vp, i64, i64, i64, i32, vp, vp, vp, vp]),
         "ssco_last_error": (C.c_char_p, [vp]),
         "ssco_status_string": (C.c_char_p, [i32]),
         "ssco_plan_save": (i32, [vp, C.c_char_p]),
@@ -416,11 +416,14 @@ def ssco_solve(plan: Plan, vals, shift, b):
     return SscoSolve.apply(plan, vals, shift, b)
 
 
-def cotan_weights(tri: torch.Tensor, tri_edge: torch.Tensor, xy: torch.Tensor, n_edge: int, stream=None, out=None):
+def cotan_weights(tri: torch.Tensor, tri_edge: torch.Tensor, xy: torch.Tensor, n_edge: int, stream=None, out=None,
+                  check=True):
     """Cotangent edge weights [batch, n_edge] (float64, device) of a planar
     triangle mesh from vertex positions xy [batch, n_vert, 2] (float64,
     device); tri / tri_edge [n_tri, 3] int32 device tensors (vertex ids,
-    edge opposite each corner).  See ssco_cotan_weights in ssco.h."""
+    edge opposite each corner).  See ssco_cotan_weights in ssco.h.  With
+    ``check`` the call synchronizes and raises if any triangle carried an
+    out-of-range id (those triangles are skipped on the device)."""
     L = load_library()
     tri = tri.to(torch.int32).contiguous()
     tri_edge = tri_edge.to(torch.int32).contiguous()
@@ -428,8 +431,11 @@ def cotan_weights(tri: torch.Tensor, tri_edge: torch.Tensor, xy: torch.Tensor, n
     batch, n_vert = int(xy.shape[0]), int(xy.shape[1])
     w = out if out is not None else torch.empty((batch, int(n_edge)), dtype=torch.float64, device=xy.device)
     assert w.dtype == torch.float64 and w.is_contiguous() and tuple(w.shape) == (batch, int(n_edge))
+    nbad = torch.zeros(1, dtype=torch.int32, device=xy.device) if check else None
     st = L.ssco_cotan_weights(_ptr(tri), _ptr(tri_edge), int(tri.shape[0]), n_vert, int(n_edge), batch, _ptr(xy),
-                              _ptr(w), _stream_ptr(stream))
+                              _ptr(w), _ptr(nbad) if check else None, _stream_ptr(stream))
     if st != SSCO_OK:
         raise SscoError(st, "ssco_cotan_weights")
+    if check and int(nbad.item()) > 0:
+        raise SscoError(SSCO_ERR_INVALID_ARG, f"ssco_cotan_weights: {int(nbad.item())} triangles with out-of-range ids")
     return w

@@ -228,6 +228,6 @@ def test_cotan_weights_argument_checks(S):
     """ssco_cotan_weights refuses inconsistent sizes and null pointers before
     touching the device."""
     L = S.load_library()
-    assert L.ssco_cotan_weights(None, None, 1, 3, 3, 1, None, None, None) == 1  # null tables
-    assert L.ssco_cotan_weights(None, None, -1, 3, 3, 1, None, None, None) == 1  # negative count
-    assert L.ssco_cotan_weights(None, None, 0, 3, 3, 0, None, None, None) == 1  # batch < 1
+    assert L.ssco_cotan_weights(None, None, 1, 3, 3, 1, None, None, None, None) == 1  # null tables
+    assert L.ssco_cotan_weights(None, None, -1, 3, 3, 1, None, None, None, None) == 1  # negative count
+    assert L.ssco_cotan_weights(None, None, 0, 3, 3, 0, None, None, None, None) == 1  # batch < 1

@@ -216,6 +216,11 @@ def test_cotan_weights_on_device_match_oracle(S):
     x2 = pl.solve(b).cpu().numpy()
     assert np.array_equal(x1, x2)
     assert np.all(pl.status()["status"] == 0)
+    # out-of-range ids are skipped on the device (never dereferenced) and reported
+    bad = te.clone()
+    bad[5, 1] = p.m + 7
+    with pytest.raises(S.SscoError):
+        S.cotan_weights(tri, bad, torch.tensor(p.positions, device="cuda"), p.m)
 
 
 @pytest.mark.parametrize("seed", range(6))
