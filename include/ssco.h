@@ -363,7 +363,10 @@ const char* ssco_kernel_name(int32_t kind);
 const char* ssco_last_error(ssco_plan plan);
 const char* ssco_status_string(ssco_status s);
 
-/* Versioned binary file of the host plan (no device state). */
+/* Versioned binary file of the host plan (no device state): magic, version,
+ * the plan's tables, then a 64-bit FNV-1a digest of everything before it.
+ * Load returns SSCO_ERR_INVALID_ARG for another version, a truncated file,
+ * trailing bytes or a digest mismatch; the caller owns the returned plan. */
 ssco_status ssco_plan_save(ssco_plan plan, const char* path);
 ssco_status ssco_plan_load(const char* path, ssco_plan* out);
 void ssco_destroy(ssco_plan plan);

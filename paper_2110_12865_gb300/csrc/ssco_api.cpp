@@ -76,37 +76,57 @@ void set_dev_tables(Plan& P) {
 
 // ----- plan file (de)serialization -----------------------------------------
 constexpr uint64_t kMagic = 0x314F4353534F4353ull;  // "SCOSSCO1"
-constexpr uint32_t kVersion = 9;
+constexpr uint32_t kVersion = 10;
 
+// 64-bit FNV-1a (Fowler, Noll, Vo) over the payload bytes: the file ends
+// with the digest, so a plan whose tables were damaged after saving is
+// refused at load instead of indexing device memory with bad maps.
+struct Fnv1a {
+    uint64_t h = 0xcbf29ce484222325ull;
+    void add(const void* p, size_t n) {
+        const unsigned char* c = static_cast<const unsigned char*>(p);
+        for (size_t i = 0; i < n; ++i) h = (h ^ c[i]) * 0x100000001b3ull;
+    }
+};
 struct Writer {
     std::ofstream f;
+    Fnv1a sum;
+    void raw(const void* p, size_t n) {
+        f.write(static_cast<const char*>(p), (std::streamsize)n);
+        sum.add(p, n);
+    }
     template <class T>
     bool pod(const T& v) {
-        f.write(reinterpret_cast<const char*>(&v), sizeof(T));
+        raw(&v, sizeof(T));
         return (bool)f;
     }
     template <class T>
     bool vec(const std::vector<T>& v) {
         uint64_t n = v.size();
         pod(n);
-        if (n) f.write(reinterpret_cast<const char*>(v.data()), (std::streamsize)(n * sizeof(T)));
+        if (n) raw(v.data(), n * sizeof(T));
         return (bool)f;
     }
 };
 struct Reader {
     std::ifstream f;
+    Fnv1a sum;
+    bool raw(void* p, size_t n) {
+        f.read(static_cast<char*>(p), (std::streamsize)n);
+        if (!f) return false;
+        sum.add(p, n);
+        return true;
+    }
     template <class T>
     bool pod(T& v) {
-        f.read(reinterpret_cast<char*>(&v), sizeof(T));
-        return (bool)f;
+        return raw(&v, sizeof(T));
     }
     template <class T>
     bool vec(std::vector<T>& v) {
         uint64_t n = 0;
         if (!pod(n) || n > (1ull << 40)) return false;
         v.resize(n);
-        if (n) f.read(reinterpret_cast<char*>(v.data()), (std::streamsize)(n * sizeof(T)));
-        return (bool)f;
+        return n == 0 || raw(v.data(), n * sizeof(T));
     }
 };
 
@@ -523,6 +543,8 @@ ssco_status ssco_plan_save(ssco_plan h, const char* path) {
     w.pod(kMagic);
     w.pod(kVersion);
     serialize(w, h->P);
+    const uint64_t digest = w.sum.h;
+    w.f.write(reinterpret_cast<const char*>(&digest), sizeof(digest));
     w.f.flush();
     if (!w.f) return fail(h, SSCO_ERR_INVALID_ARG, "write failed");
     return SSCO_OK;
@@ -540,9 +562,15 @@ ssco_status ssco_plan_load(const char* path, ssco_plan* out) {
         return fail(nullptr, SSCO_ERR_INVALID_ARG, "not a plan file of this version");
     ssco_plan h = new (std::nothrow) ssco_plan_s();
     if (!h) return fail(nullptr, SSCO_ERR_OOM, "host allocation failed");
-    if (!serialize(r, h->P)) {
+    bool ok = serialize(r, h->P);
+    const uint64_t got = r.sum.h;
+    uint64_t digest = 0;
+    char extra = 0;
+    ok = ok && (bool)r.f.read(reinterpret_cast<char*>(&digest), sizeof(digest)) && digest == got &&
+         !r.f.read(&extra, 1);
+    if (!ok) {
         delete h;
-        return fail(nullptr, SSCO_ERR_INVALID_ARG, "truncated or corrupt plan file");
+        return fail(nullptr, SSCO_ERR_INVALID_ARG, "truncated or corrupt plan file (checksum)");
     }
     build_blob(h->P);
     compute_ws_layout(h->P);

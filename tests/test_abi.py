@@ -177,10 +177,17 @@ def test_plan_save_load_roundtrip(S, tmp_path):
     assert q.info == pl.info
     for what in range(15):
         assert np.array_equal(q.export(what), pl.export(what))
-    with open(f, "r+b") as fh:
-        fh.write(b"garbage!")
-    with pytest.raises(S.SscoError):
-        S.Plan.load(f)
+    raw = open(f, "rb").read()
+    bad = [b"garbage!" + raw[8:],                                       # magic
+           raw[:len(raw) // 2] + bytes([raw[len(raw) // 2] ^ 0x10]) + raw[len(raw) // 2 + 1:],  # a table byte
+           raw[:-1],                                                    # truncated digest
+           raw + b"\0"]                                                 # trailing byte
+    for i, blob in enumerate(bad):
+        g = str(tmp_path / f"bad{i}.bin")
+        open(g, "wb").write(blob)
+        with pytest.raises(S.SscoError) as ei:
+            S.Plan.load(g)
+        assert ei.value.status == 1
 
 
 def test_fixed_dofs_are_identity_rows(S):
