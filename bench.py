@@ -43,7 +43,8 @@ HBM_KINDS = {"assemble", "fwd_solve", "bwd_solve", "resid", "vector", "check", "
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: about a second of device time for the workload)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="arap")
@@ -52,7 +53,10 @@ def parse():
                     help="skip ssco_autotune of the launch shapes before timing")
     ap.add_argument("--batch", type=int, default=None,
                     help="value sets of the main pattern (default: the workload's own; smaller only for profiling)")
-    return ap.parse_args()
+    a = ap.parse_args()
+    if a.steps is None:
+        a.steps = {"elast24": 20, "elast48": 5}.get(a.workload, 100)
+    return a
 
 
 # ---------------------------------------------------------------------------
@@ -345,9 +349,10 @@ def run_ours(args, rank, world, local_rank):
     # ---- per-kernel events over a repeat of the timed steps ---------------
     # (eager launches of the same kernels: events cannot bracket single
     # kernels inside a replayed graph)
+    prof_steps = min(args.steps, 50)   # bounded by the event pool of each plan
     for pl in plans32:
         pl.profile_enable(200_000)
-    for _ in range(args.steps):
+    for _ in range(prof_steps):
         flush.fill_(1)
         eager_step(plans32, dev32)
     stats = {}
@@ -389,7 +394,7 @@ def run_ours(args, rank, world, local_rank):
                  "launches": kv["launches"], "avg_launch_us": kv["ms"] * 1e3 / kv["launches"],
                  "measured": "CUDA events per launch on the launch stream, over a repeat of the timed steps"})
     out["roofline"] = roof
-    out["kernels"] = {k: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps,
+    out["kernels"] = {k: {"launches": v["launches"], "ms_per_step": v["ms"] / prof_steps,
                           "share": round(v["share"], 4),
                           "GBps": v["bytes"] / max(v["ms"], 1e-9) / 1e6,
                           "TFLOPs": v["flops"] / max(v["ms"], 1e-9) / 1e9} for k, v in kernels.items()}

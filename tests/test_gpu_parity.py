@@ -506,3 +506,44 @@ def test_full_grid256_gradient(S):
     gv, gs, gb = O.backward(p, r, 2.0 * (r.x - p.xstar[0]))
     vb = vbar.cpu().numpy()[0]
     assert np.max(np.abs(vb - gv)) <= 1e-8 * np.abs(gv).max()
+
+
+def test_full_uneven64_one_plan(S):
+    """The 64 uneven triangulated grids (sides 32..256) of the batched
+    workload, one plan, FP32 factor + refinement: every system converges and
+    sampled systems meet the residual bound with the oracle's K."""
+    ps = P.uneven_trigrids(64)
+    pl, x, st, *_ = run(S, ps, S.FP32_REFINE, batch=1)
+    assert np.all(st["status"] == 0) and np.all(st["resid"] <= RESID_TOL)
+    offs = np.concatenate([[0], np.cumsum([q.n for q in ps])])
+    for k in [0, 21, 42, 63]:
+        q = ps[k]
+        xk = x[0, offs[k]:offs[k + 1]]
+        res = np.linalg.norm(O.symv(O.assemble(q, 0), xk) - q.b[0]) / np.linalg.norm(q.b[0])
+        assert res <= RESID_TOL, (k, res)
+
+
+def test_full_elast48_batch16_with_gradient(S):
+    """48^3 Kuhn tets x 16 Young's-modulus fields, FP32 factor (tensor-core
+    panel updates) + refinement, then the adjoint for every instance.  The
+    oracle factor is out of reach at this size, so the checks are properties
+    that hold at any size, with the oracle's own assembly: the solution and
+    adjoint residuals, and the element gradient -mu_e^T K_e^0 x_e and the
+    shift gradient recomputed by the oracle from the device's mu and x."""
+    p = P.workload("elast48")
+    pl, x, st, *_ = run(S, p, S.FP32_REFINE)
+    assert np.all(st["status"] == 0) and np.all(st["resid"] <= RESID_TOL)
+    xbar = np.random.default_rng(48).standard_normal(x.shape)
+    vbar, sbar, mu = pl.backward(torch.tensor(x, device="cuda"), torch.tensor(xbar, device="cuda"))
+    vbar, sbar, mu = vbar.cpu().numpy(), sbar.cpu().numpy(), mu.cpu().numpy()
+    mask = O.shifted_mask(p)
+    for inst in [0, 15]:
+        K = O.assemble(p, inst)
+        res = np.linalg.norm(O.symv(K, x[inst]) - p.b[inst]) / np.linalg.norm(p.b[inst])
+        assert res <= RESID_TOL, (inst, res)
+        res_mu = np.linalg.norm(O.symv(K, mu[inst]) - xbar[inst]) / np.linalg.norm(xbar[inst])
+        assert res_mu <= RESID_TOL, (inst, res_mu)
+        gv = O.grad_vals(p, mu[inst], x[inst])
+        assert np.max(np.abs(vbar[inst] - gv)) <= 1e-11 * np.abs(gv).max()
+        gs = -float(np.dot(mu[inst][mask], x[inst][mask]))
+        assert abs(sbar[inst] - gs) <= 1e-12 * np.linalg.norm(mu[inst]) * np.linalg.norm(x[inst])
