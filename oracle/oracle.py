@@ -21,6 +21,7 @@ BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD_DIR, "libssco_oracle.so")
 
 _lib = None
+KIND_ELEM_BLOCKS = 2   # K = sum_e K_e, the element blocks are the per-set values
 
 i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
 i64p = np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")
@@ -77,6 +78,10 @@ def lib():
         L.or_grad_elem.argtypes = [C.c_int32, C.c_int32, i32p, f64p, f64p, f64p, f64p]
         L.or_cotan_weights.restype = None
         L.or_cotan_weights.argtypes = [C.c_int64, i32p, i32p, f64p, C.c_int64, f64p]
+        L.or_grad_blocks.restype = None
+        L.or_grad_blocks.argtypes = [C.c_int32, C.c_int32, i32p, f64p, f64p, f64p]
+        L.or_tet_stiffness.restype = C.c_int32
+        L.or_tet_stiffness.argtypes = [C.c_int64, i32p, f64p, C.c_void_p, C.c_double, f64p]
         _lib = L
     return _lib
 
@@ -117,7 +122,14 @@ def assemble(p, inst: int = 0, vals=None, shift=None) -> CSC:
         val = np.zeros(max(cap, 1))
         nz = L.or_assemble_atwa(n, m, rowptr, colind, aval, v, s, colptr, rowind, val)
     else:
-        dofs, K0 = _c(p.elem_dofs, np.int32), _c(p.elem_K0, np.float64)
+        dofs = _c(p.elem_dofs, np.int32)
+        if p.kind == KIND_ELEM_BLOCKS:
+            # K = sum_e K_e with the blocks given per value set: the element
+            # sum with unit moduli over those blocks
+            K0 = _c(v, np.float64)
+            v = np.ones(m)
+        else:
+            K0 = _c(p.elem_K0, np.float64)
         cap = L.or_elem_cap(n, m, p.elem_dim)
         rowind = np.zeros(max(cap, 1), np.int32)
         val = np.zeros(max(cap, 1))
@@ -195,6 +207,11 @@ def symv(K: CSC, x):
 
 def grad_vals(p, mu, x):
     """d loss / d vals given the adjoint mu = K^-1 xbar (original ordering)."""
+    if p.kind == KIND_ELEM_BLOCKS:
+        d = p.elem_dim
+        out = np.zeros(p.m * d * (d + 1) // 2)
+        lib().or_grad_blocks(p.m, d, _c(p.elem_dofs, np.int32), _c(mu, np.float64), _c(x, np.float64), out)
+        return out
     out = np.zeros(p.m)
     if p.kind == 0:
         lib().or_grad_atwa(p.m, _c(p.rowptr, np.int64), _c(p.colind, np.int32),
@@ -249,3 +266,16 @@ def cotan_weights(tri, tri_edge, xy, n_edge: int):
     w = np.empty(int(n_edge))
     lib().or_cotan_weights(tri.shape[0], tri, te, _c(xy, np.float64), int(n_edge), w)
     return w
+
+
+def tet_stiffness(tets, xyz, E, nu: float):
+    """Linear-tet stiffness blocks of one value set, V B^T D B (isotropic,
+    Voigt order, engineering shear), packed lower triangles [n_tet][78];
+    tets [n_tet][4], xyz [n_node][3], E [n_tet] or None (unit modulus).
+    Returns (blocks, number of singular tets)."""
+    tets = _c(tets, np.int32)
+    xyz = _c(xyz, np.float64)
+    out = np.empty((tets.shape[0], 78))
+    Ec = None if E is None else _c(E, np.float64)
+    bad = lib().or_tet_stiffness(tets.shape[0], tets, xyz, None if Ec is None else Ec.ctypes.data, float(nu), out)
+    return out, int(bad)

@@ -28,10 +28,14 @@
  *      solves        forward substitution by columns of L, backward by
  *                    columns of L^T, then un-permute;
  *      adjoint       wbar_e = -(A mu)_e (A x)_e, Ebar_e = -mu_e^T K_e^0 x_e,
- *                    shiftbar = -mu^T x over shifted diagonals, with K mu = xbar.
+ *                    shiftbar = -mu^T x over shifted diagonals, with K mu = xbar;
+ *                    per-call element blocks: -(mu_u x_v + mu_v x_u) per entry;
+ *      values        cotangent edge weights (Sec. 5.3) and linear-tet
+ *                    stiffness blocks V B^T D B from vertex positions.
  *  - Parity pins (tests): dense numpy Cholesky / solve, tridiag(-1,2,-1)
  *    closed form, reconstruction, brute-force boolean elimination, central
- *    differences.  Built with -O2 -ffp-contract=off, no fast-math.
+ *    differences; tet blocks: the Lame-constant index formula, rigid-body
+ *    null space, the constant-strain energy, scaling and rotation laws.  Built with -O2 -ffp-contract=off, no fast-math.
  */
 #include <math.h>
 #include <stdint.h>
@@ -487,4 +491,142 @@ void or_cotan_weights(int64_t n_tri, const int32_t* tri, const int32_t* tri_edge
             w[tri_edge[3 * t + c]] += 0.5 * dot / cross;
         }
     }
+}
+
+/* Adjoint of per-call element blocks (K = sum_e K_e, K_e packed row-major
+ * lower, entry p = (i, j), i >= j): with K mu = xbar and x the solution,
+ * dloss/dK_e[p] = -mu_u x_u for i == j and -(mu_u x_v + mu_v x_u) for
+ * i > j (the entry sits at (u, v) and (v, u)); 0 when u or v is fixed.
+ * One value set; out is [m][dim(dim+1)/2]. */
+void or_grad_blocks(int32_t m, int32_t dim, const int32_t* dofs, const double* mu, const double* x, double* out) {
+    int32_t npk = dim * (dim + 1) / 2;
+    for (int32_t e = 0; e < m; ++e) {
+        int32_t p = 0;
+        for (int32_t i = 0; i < dim; ++i) {
+            for (int32_t j = 0; j <= i; ++j, ++p) {
+                int32_t u = dofs[(int64_t)e * dim + i], v = dofs[(int64_t)e * dim + j];
+                double g = 0.0;
+                if (u >= 0 && v >= 0) g = (i == j) ? -(mu[u] * x[u]) : -(mu[u] * x[v] + mu[v] * x[u]);
+                out[(int64_t)e * npk + p] = g;
+            }
+        }
+    }
+}
+
+/* Stiffness block of a linear (4-node) tetrahedron in isotropic linear
+ * elasticity, built the textbook way: shape functions N_a = barycentric
+ * coordinates, their gradients from the 4x4 system [1 x_a^T] (the
+ * coefficients of N_a = alpha_a + beta_a . x), the 6x12 strain-displacement
+ * matrix B (Voigt order xx, yy, zz, yz, xz, xy with engineering shear), the
+ * 6x6 isotropic D(E, nu), and K = V B^T D B with V = |det| / 6.  Local DOF
+ * 3a+c is component c of vertex a.  One value set; xyz is [n_node][3], E
+ * per tet; out is [n_tet][78], the lower triangle packed row-major.
+ * Returns the number of tets with a singular vertex matrix (those blocks
+ * are zero). */
+static int solve4(double M[4][4], double rhs[4], double sol[4]) {
+    /* Gaussian elimination with partial pivoting on a copy */
+    double A[4][5];
+    for (int r = 0; r < 4; ++r) {
+        for (int c = 0; c < 4; ++c) A[r][c] = M[r][c];
+        A[r][4] = rhs[r];
+    }
+    for (int c = 0; c < 4; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < 4; ++r)
+            if (fabs(A[r][c]) > fabs(A[piv][c])) piv = r;
+        if (A[piv][c] == 0.0) return 0;
+        if (piv != c)
+            for (int k = 0; k < 5; ++k) {
+                double t = A[c][k];
+                A[c][k] = A[piv][k];
+                A[piv][k] = t;
+            }
+        for (int r = c + 1; r < 4; ++r) {
+            double f = A[r][c] / A[c][c];
+            for (int k = c; k < 5; ++k) A[r][k] -= f * A[c][k];
+        }
+    }
+    for (int r = 3; r >= 0; --r) {
+        double s = A[r][4];
+        for (int k = r + 1; k < 4; ++k) s -= A[r][k] * sol[k];
+        sol[r] = s / A[r][r];
+    }
+    return 1;
+}
+
+int32_t or_tet_stiffness(int64_t n_tet, const int32_t* tets, const double* xyz, const double* E, double nu,
+                         double* out) {
+    int32_t bad = 0;
+    for (int64_t t = 0; t < n_tet; ++t) {
+        double* Kp = out + t * 78;
+        double M[4][4];
+        for (int a = 0; a < 4; ++a) {
+            M[a][0] = 1.0;
+            for (int c = 0; c < 3; ++c) M[a][c + 1] = xyz[3 * (int64_t)tets[4 * t + a] + c];
+        }
+        /* N_a(x) = coefficients solving M coef = e_a: coef = (alpha, beta) */
+        double grad[4][3];
+        int ok = 1;
+        for (int a = 0; a < 4 && ok; ++a) {
+            double rhs[4] = {0, 0, 0, 0}, sol[4];
+            rhs[a] = 1.0;
+            /* N_a(x_b) = delta_ab: rows of M times the coefficient vector */
+            ok = solve4(M, rhs, sol);
+            for (int c = 0; c < 3; ++c) grad[a][c] = sol[c + 1];
+        }
+        /* det M by cofactor expansion of the edge vectors (= det J) */
+        double e1[3], e2[3], e3[3];
+        for (int c = 0; c < 3; ++c) {
+            e1[c] = M[1][c + 1] - M[0][c + 1];
+            e2[c] = M[2][c + 1] - M[0][c + 1];
+            e3[c] = M[3][c + 1] - M[0][c + 1];
+        }
+        double det = e1[0] * (e2[1] * e3[2] - e2[2] * e3[1]) - e1[1] * (e2[0] * e3[2] - e2[2] * e3[0]) +
+                     e1[2] * (e2[0] * e3[1] - e2[1] * e3[0]);
+        if (!ok || det == 0.0 || !isfinite(det)) {
+            for (int p = 0; p < 78; ++p) Kp[p] = 0.0;
+            bad++;
+            continue;
+        }
+        double V = fabs(det) / 6.0;
+        double Bm[6][12];
+        memset(Bm, 0, sizeof(Bm));
+        for (int a = 0; a < 4; ++a) {
+            double gx = grad[a][0], gy = grad[a][1], gz = grad[a][2];
+            Bm[0][3 * a + 0] = gx;
+            Bm[1][3 * a + 1] = gy;
+            Bm[2][3 * a + 2] = gz;
+            Bm[3][3 * a + 1] = gz; /* yz */
+            Bm[3][3 * a + 2] = gy;
+            Bm[4][3 * a + 0] = gz; /* xz */
+            Bm[4][3 * a + 2] = gx;
+            Bm[5][3 * a + 0] = gy; /* xy */
+            Bm[5][3 * a + 1] = gx;
+        }
+        double Ee = E ? E[t] : 1.0;
+        double lam = Ee * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+        double mu = Ee / (2.0 * (1.0 + nu));
+        double D[6][6];
+        memset(D, 0, sizeof(D));
+        for (int r = 0; r < 3; ++r) {
+            for (int c = 0; c < 3; ++c) D[r][c] = lam;
+            D[r][r] += 2.0 * mu;
+            D[r + 3][r + 3] = mu;
+        }
+        double DB[6][12];
+        for (int r = 0; r < 6; ++r)
+            for (int c = 0; c < 12; ++c) {
+                double s = 0.0;
+                for (int k = 0; k < 6; ++k) s += D[r][k] * Bm[k][c];
+                DB[r][c] = s;
+            }
+        int p = 0;
+        for (int i = 0; i < 12; ++i)
+            for (int j = 0; j <= i; ++j, ++p) {
+                double s = 0.0;
+                for (int k = 0; k < 6; ++k) s += Bm[k][i] * DB[k][j];
+                Kp[p] = V * s;
+            }
+    }
+    return bad;
 }

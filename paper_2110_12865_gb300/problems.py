@@ -33,6 +33,7 @@ SEED_BASE = 20211025
 # pattern kinds, mirrored by SSCO_KIND_* in include/ssco.h
 KIND_ATWA = 0
 KIND_ELEM = 1
+KIND_ELEM_BLOCKS = 2
 
 
 def seed_for(cfg: int, instance: int) -> int:
@@ -355,6 +356,45 @@ def elasticity_problem(k: int, batch: int = 1, cfg: int = 2, jitter: float = 0.1
                    elem_K0=np.ascontiguousarray(pack_lower(Ke)), perm=perm,
                    batch=batch, vals=vals, shift=np.zeros(batch), b=b,
                    dims=dims, pos=pos, tets=tets, dof_fixed=dof_fixed, Ke=Ke)
+
+
+def elasticity_geometry_problem(k: int, batch: int = 1, cfg: int = 6, jitter: float = 0.1,
+                                nu: float = 0.3):
+    """The k^3 Kuhn-tet elasticity mesh of elasticity_problem with the
+    geometry itself varying per value set: instance i jitters the nodes by
+    its own U[-jitter*h, jitter*h] draw and has its own E_e = 10^U[3,5].
+    The pattern takes the element blocks per call (kind ELEM_BLOCKS), so the
+    inputs are positions `pos` [batch][nodes][3], moduli `E` [batch][m] and
+    `nu`; `vals` (the blocks) is left to the caller to build from them."""
+    dims = (k + 1,) * 3
+    nn = int(np.prod(dims))
+    n = 3 * nn
+    h = 1.0 / k
+    base = np.stack(np.meshgrid(*[np.arange(k + 1)] * 3, indexing="ij"), -1).reshape(-1, 3) * h
+    tets = kuhn_tets(k)
+    node_fixed = np.isclose(base[:, 2], 0.0)
+    dofs = (tets[:, :, None] * 3 + np.arange(3)[None, None, :]).reshape(-1, 12)
+    dof_fixed = np.repeat(node_fixed, 3)
+    elem_dofs = np.where(dof_fixed[dofs], -1, dofs).astype(np.int32)
+    m = tets.shape[0]
+    pos = np.empty((batch, nn, 3))
+    E = np.empty((batch, m))
+    b = np.empty((batch, n))
+    for i in range(batch):
+        rng = np.random.default_rng(seed_for(cfg, i))
+        pos[i] = base + rng.uniform(-jitter * h, jitter * h, base.shape)
+        E[i] = 10.0 ** rng.uniform(3.0, 5.0, m)
+        bi = rng.standard_normal(n)
+        bi[dof_fixed] = 0.0
+        b[i] = bi
+    dperm = expand_perm(nested_dissection(dims), 3)
+    fixed_first = dof_fixed[dperm]
+    perm = np.concatenate([dperm[fixed_first], dperm[~fixed_first]]).astype(np.int32)
+    return Problem(kind=KIND_ELEM_BLOCKS, name=f"elastgeo{k}", n=n, m=m, elem_dim=12,
+                   elem_dofs=np.ascontiguousarray(elem_dofs), elem_K0=None, perm=perm,
+                   batch=batch, vals=None, shift=np.zeros(batch), b=b, dims=dims,
+                   pos=pos, E=E, nu=float(nu), tets=np.ascontiguousarray(tets, np.int32),
+                   dof_fixed=dof_fixed)
 
 
 def random_spd_pattern(n: int, extra_edges: int, rng, batch: int = 1):

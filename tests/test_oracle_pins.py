@@ -481,3 +481,141 @@ def test_trigrid_problem_values_are_the_oracle_cotan_weights():
     for i in range(2):
         w = O.cotan_weights(p.faces, p.opp, p.positions[i], p.m)
         assert np.array_equal(w, p.vals[i])
+
+
+# element blocks from geometry (linear tetrahedra)
+# ----------------------------------------------------------------------------
+def _random_tets(rng, count):
+    """Well-shaped random tets: a regular-ish reference tet, randomly
+    stretched, rotated and moved; positive orientation not assumed."""
+    ref = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], float)
+    out = []
+    for _ in range(count):
+        A = np.eye(3) + 0.3 * rng.standard_normal((3, 3))
+        out.append(ref @ A.T + rng.standard_normal(3))
+    return np.array(out)
+
+
+def _oracle_block(X, E, nu):
+    Kp, bad = O.tet_stiffness(np.arange(4, dtype=np.int32)[None], X, np.array([E]), nu)
+    assert bad == 0
+    K = np.zeros((12, 12))
+    ii, jj = np.tril_indices(12)
+    K[ii, jj] = Kp[0]
+    K[jj, ii] = Kp[0]
+    return K
+
+
+def test_tet_block_matches_lame_index_formula():
+    """The continuum derivation (energy mu eps:eps + lambda/2 (tr eps)^2,
+    differentiated twice in the nodal displacements) gives
+    K[3a+i][3b+j] = V (lambda g_a[i] g_b[j] + mu g_a[j] g_b[i] + mu d_ij g_a.g_b)
+    with g_a the barycentric gradients from the inverse edge matrix.  The
+    oracle builds K as V B^T D B instead; a transposed shear entry, a missing
+    factor 2 or a wrong Voigt order fails here."""
+    rng = np.random.default_rng(41)
+    for X in _random_tets(rng, 12):
+        E, nu = 10 ** rng.uniform(0, 3), rng.uniform(-0.5, 0.45)
+        lam, mu = E * nu / ((1 + nu) * (1 - 2 * nu)), E / (2 * (1 + nu))
+        J = (X[1:] - X[0]).T
+        Gi = np.linalg.inv(J)                       # rows: grad of barycentric 1..3
+        g = np.vstack([-Gi.sum(0), Gi])
+        V = abs(np.linalg.det(J)) / 6
+        Kl = np.zeros((12, 12))
+        for a in range(4):
+            for b in range(4):
+                for i in range(3):
+                    for j in range(3):
+                        Kl[3 * a + i, 3 * b + j] = V * (lam * g[a, i] * g[b, j] + mu * g[a, j] * g[b, i]
+                                                        + (mu * g[a] @ g[b] if i == j else 0.0))
+        K = _oracle_block(X, E, nu)
+        assert np.abs(K - Kl).max() <= 1e-12 * np.abs(Kl).max()
+
+
+def test_tet_block_constant_strain_energy_and_rigid_modes():
+    """An affine displacement u(x) = G x has the constant strain
+    eps = (G + G^T)/2, so 1/2 u^T K u = V (mu eps:eps + lambda/2 (tr eps)^2)
+    exactly; a rigid motion (G antisymmetric, or a translation) has none."""
+    rng = np.random.default_rng(42)
+    for X in _random_tets(rng, 8):
+        E, nu = 2.5, 0.3
+        lam, mu = E * nu / ((1 + nu) * (1 - 2 * nu)), E / (2 * (1 + nu))
+        K = _oracle_block(X, E, nu)
+        V = abs(np.linalg.det((X[1:] - X[0]).T)) / 6
+        G = rng.standard_normal((3, 3))
+        u = (X @ G.T).ravel()
+        eps = 0.5 * (G + G.T)
+        W = V * (mu * np.sum(eps * eps) + 0.5 * lam * np.trace(eps) ** 2)
+        assert abs(0.5 * u @ K @ u - W) <= 1e-12 * W
+        W_ = 0.5 * (G - G.T)
+        for r in [(X @ W_.T).ravel(), np.tile(rng.standard_normal(3), 4)]:
+            assert np.abs(K @ r).max() <= 1e-12 * np.abs(K).max() * np.abs(r).max()
+        ev = np.linalg.eigvalsh(K)
+        assert ev.min() > -1e-12 * ev.max() and np.sum(ev > 1e-9 * ev.max()) == 6
+
+
+def test_tet_block_scaling_and_rotation_laws():
+    """K(alpha X) = alpha K(X) (3D: volume ~ alpha^3, gradients ~ 1/alpha);
+    K(X R^T) = Q K(X) Q^T with Q = diag(R, R, R, R) for a rotation R;
+    K is linear in E; vertex order does not change the block up to the
+    matching DOF permutation."""
+    rng = np.random.default_rng(43)
+    X = _random_tets(rng, 1)[0]
+    K = _oracle_block(X, 1.0, 0.25)
+    assert np.abs(_oracle_block(3.0 * X, 1.0, 0.25) - 3.0 * K).max() <= 1e-12 * np.abs(K).max()
+    assert np.abs(_oracle_block(X, 7.0, 0.25) - 7.0 * K).max() <= 1e-12 * 7 * np.abs(K).max()
+    R, _ = np.linalg.qr(rng.standard_normal((3, 3)))
+    Q = np.kron(np.eye(4), R)
+    assert np.abs(_oracle_block(X @ R.T, 1.0, 0.25) - Q @ K @ Q.T).max() <= 1e-12 * np.abs(K).max()
+    order = [2, 0, 3, 1]
+    idx = np.array([3 * a + c for a in order for c in range(3)])
+    assert np.abs(_oracle_block(X[order], 1.0, 0.25) - K[np.ix_(idx, idx)]).max() <= 1e-12 * np.abs(K).max()
+
+
+def test_tet_block_degenerate_and_generator_consistency():
+    """A flat tet is reported and gives a zero block; on the pattern geometry
+    of the elasticity workloads the oracle reproduces the generator's K_e^0."""
+    X = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [1, 1, 0]], float)
+    Kp, bad = O.tet_stiffness(np.arange(4, dtype=np.int32)[None], X, None, 0.3)
+    assert bad == 1 and np.all(Kp == 0)
+    p = P.elasticity_problem(2, cfg=2)
+    Kp, bad = O.tet_stiffness(p.tets, p.pos, None, 0.3)
+    assert bad == 0
+    np.testing.assert_allclose(Kp, p.elem_K0, rtol=0, atol=1e-12 * np.abs(p.elem_K0).max())
+
+
+def test_element_blocks_pattern_assembles_as_the_element_sum():
+    """A per-call element-block pattern whose blocks are E_e K_e^0 assembles
+    to the same K as the modulus pattern of the same mesh."""
+    p = P.elasticity_problem(2, batch=1, cfg=2)
+    q = P.Problem(p)
+    q.update(kind=P.KIND_ELEM_BLOCKS, elem_K0=None, vals=(p.vals[0][:, None] * p.elem_K0).reshape(1, -1))
+    Kp, Kq = O.assemble(p).dense(), O.assemble(q).dense()
+    assert np.abs(Kp - Kq).max() <= 1e-13 * np.abs(Kp).max()
+
+
+def test_gradient_element_blocks_central_differences():
+    """d loss / d (block entry) of a per-call element-block pattern against
+    central differences of the oracle's solve: an off-diagonal entry moves
+    K_uv and K_vu together, a diagonal entry K_uu alone."""
+    g = P.elasticity_geometry_problem(2, batch=1, cfg=6)
+    Kb = np.concatenate([O.tet_stiffness(g.tets, g.pos[0], g.E[0], g.nu)[0].ravel()])
+    g["vals"] = Kb[None]
+    rng = np.random.default_rng(11)
+    g["xstar"] = rng.standard_normal((1, g.n)) * 1e-4
+    r = O.refactor_solve(g)
+    vbar, _, _ = O.backward(g, r, 2.0 * (r.x - g.xstar[0]))
+    free = np.nonzero(np.all(g.elem_dofs >= 0, axis=1))[0]
+    picks = [(e, q) for e in rng.choice(free, 3, replace=False) for q in (0, 4, 40, 77)]
+    fixed_e = int(np.nonzero(np.any(g.elem_dofs < 0, axis=1))[0][0])
+    for e, q in picks:
+        h = 1e-6 * np.abs(Kb[e * 78: (e + 1) * 78]).max()
+        vp, vm = Kb.copy(), Kb.copy()
+        vp[e * 78 + q] += h
+        vm[e * 78 + q] -= h
+        fd = fd_diff(g, fd_loss(g, vp, 0.0, g.b[0]), fd_loss(g, vm, 0.0, g.b[0])) / (2 * h)
+        assert abs(vbar[e * 78 + q] - fd) <= 1e-5 * max(abs(fd), 1e-3 * np.abs(vbar).max())
+    dofs = g.elem_dofs[fixed_e]
+    ii, jj = np.tril_indices(12)
+    on_fixed = (dofs[ii] < 0) | (dofs[jj] < 0)
+    assert np.all(vbar[fixed_e * 78: (fixed_e + 1) * 78][on_fixed] == 0)
