@@ -52,7 +52,7 @@ typedef enum {
     SSCO_ERR_STATE = 10        /* call order violated (e.g. solve unbound)  */
 } ssco_status;
 
-enum { SSCO_KIND_ATWA = 0, SSCO_KIND_ELEM = 1 };
+enum { SSCO_KIND_ATWA = 0, SSCO_KIND_ELEM = 1, SSCO_KIND_ELEM_BLOCKS = 2 };
 enum { SSCO_FP64 = 0, SSCO_FP32_REFINE = 1 };
 enum { SSCO_VALS_F64 = 0, SSCO_VALS_F32 = 1 };
 
@@ -69,6 +69,14 @@ typedef struct ssco_plan_s* ssco_plan;
  *   lower triangle (i >= j).  The per-call values are E[m].  A DOF that no
  *   element references becomes an identity row/column (K_ii = 1); every
  *   referenced DOF's diagonal receives the shift.
+ * kind = SSCO_KIND_ELEM_BLOCKS:  K = sum_e K_e with the element blocks
+ *   themselves supplied per call: the per-call values are
+ *   K_e [m][elem_dim*(elem_dim+1)/2] (row-major packed lower triangles, the
+ *   layout of elem_K0, which is ignored), so the value count per set is
+ *   m*elem_dim*(elem_dim+1)/2 (must stay below 2^31).  Entries on a fixed
+ *   DOF (-1) are dropped; identity rows and the shift as for ELEM.  The
+ *   element blocks may come from geometry on the device (ssco_tet_stiffness),
+ *   which makes the mesh positions, not only the moduli, the per-call input.
  * perm[n] (perm[new] = old) is the fill-reducing order; NULL = natural.
  *   It must be a permutation of [0,n) (else SSCO_ERR_PATTERN).          */
 typedef struct {
@@ -219,6 +227,9 @@ ssco_status ssco_solve(ssco_plan plan, const double* b, double* x, void* stream)
  * mu = K^-1 xbar (same factor, same refinement), then
  *   vals_bar_e = -(A mu)_e (A x)_e            (ATWA)
  *   vals_bar_e = -mu_e^T K_e^0 x_e            (ELEM, free DOFs)
+ *   vals_bar_(e,r,s) = -(mu_u x_v + mu_v x_u), r > s; -mu_u x_u, r = s
+ *                 (ELEM_BLOCKS: u, v the global DOFs of local r, s; 0 on
+ *                  an entry with a fixed DOF)
  *   shift_bar  = -mu^T x over shifted diagonals, per system
  *   b_bar      = mu.
  * Device arrays: x, xbar, b_bar [B][n]; vals_bar [B][m]; shift_bar
@@ -312,6 +323,34 @@ ssco_status ssco_solve_noalloc(ssco_plan plan, const double* b, double* x, void*
 ssco_status ssco_cotan_weights(const int32_t* tri, const int32_t* tri_edge, int64_t n_tri, int64_t n_vert,
                                int64_t n_edge, int32_t batch, const double* xy, double* w, int32_t* n_bad,
                                void* stream);
+
+/* Value construction upstream of assembly (no plan): stiffness blocks of
+ * linear tetrahedra from vertex positions, per value set -- the element
+ * blocks of the 3D elasticity configurations, for SSCO_KIND_ELEM_BLOCKS
+ * patterns whose geometry changes per call.  For tet t with vertices
+ * x_0..x_3 (local DOF 3a+c = component c of vertex a), J = [x_1-x_0,
+ * x_2-x_0, x_3-x_0], V = |det J|/6, g_a = grad of the barycentric
+ * coordinate of vertex a (rows of J^-1; g_0 = -(g_1+g_2+g_3)), and the
+ * isotropic Lame constants lambda = E nu/((1+nu)(1-2nu)), mu = E/(2(1+nu)):
+ *   K_t[3a+i][3b+j] = V (lambda g_a[i] g_b[j] + mu g_a[j] g_b[i]
+ *                        + mu [i==j] g_a . g_b),
+ * which equals V B^T D B of the strain-displacement matrix B and the
+ * isotropic D (Voigt order, engineering shear).  All pointers are device
+ * pointers:
+ *   tets   [n_tet][4] int32 vertex ids;
+ *   xyz    [batch][n_node][3] double positions;
+ *   E      [batch][n_tet] double Young's moduli, or NULL for E = 1;
+ *   K_e    [batch][n_tet][78] double, overwritten: the lower triangle of
+ *          K_t packed row-major (entry (r, s), r >= s, at r(r+1)/2 + s);
+ *   n_bad  optional device int32: incremented once per tet with an
+ *          out-of-range vertex id and once per (tet, value set) with a zero
+ *          or non-finite det J; such blocks are written as zeros and the ids
+ *          are never dereferenced; may be NULL.
+ * nu must lie in (-1, 0.5).  Async on `stream`; returns
+ * SSCO_ERR_INVALID_ARG for inconsistent sizes, nu or null pointers,
+ * SSCO_ERR_CUDA if the launch fails. */
+ssco_status ssco_tet_stiffness(const int32_t* tets, int64_t n_tet, int64_t n_node, int32_t batch, const double* xyz,
+                               const double* E, double nu, double* K_e, int32_t* n_bad, void* stream);
 
 /* Number of kernel launches the last ssco_numeric / ssco_solve /
  * ssco_backward / ssco_refactor_solve_host call issued (host counter). */

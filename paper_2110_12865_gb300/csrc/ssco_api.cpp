@@ -76,7 +76,7 @@ void set_dev_tables(Plan& P) {
 
 // ----- plan file (de)serialization -----------------------------------------
 constexpr uint64_t kMagic = 0x314F4353534F4353ull;  // "SCOSSCO1"
-constexpr uint32_t kVersion = 10;
+constexpr uint32_t kVersion = 11;
 
 // 64-bit FNV-1a (Fowler, Noll, Vo) over the payload bytes: the file ends
 // with the digest, so a plan whose tables were damaged after saving is
@@ -152,6 +152,7 @@ bool serialize(IO& io, Plan& P) {
     V(P.sp_rowptr); V(P.sp_col); V(P.sp_slot); V(P.row_sys); V(P.sys_n_off); V(P.shifted);
     V(P.g_rowptr); V(P.g_colind); V(P.g_row_sys); V(P.g_rows_all); V(P.g_aval);
     V(P.e_dofs); V(P.e_sys); V(P.e_dim); V(P.e_elems_all); V(P.e_off); V(P.e_k0off); V(P.e_K0);
+    V(P.blk_dofs); V(P.blk_off); V(P.blk_dim); V(P.blk_vbase);
     return ok;
 }
 
@@ -348,6 +349,9 @@ ssco_status ssco_backward(ssco_plan h, const double* x, const double* xbar, doub
     P.launches = 0;
     int e = launch_backward(P, x, xbar, vals_bar, shift_bar, b_bar, stream);
     if (e) return cuda_fail(h, e, "backward launch");
+    // ELEM_BLOCKS entries: b_bar now holds mu (same stream)
+    e = launch_grad_blocks(P, b_bar, x, vals_bar, stream);
+    if (e) return cuda_fail(h, e, "block gradient launch");
     return SSCO_OK;
 }
 

@@ -216,6 +216,10 @@ struct Plan {
     std::vector<int32_t> e_dofs, e_sys, e_dim, e_elems_all;
     std::vector<int64_t> e_off, e_k0off;
     std::vector<double> e_K0;
+    // ELEM_BLOCKS elements: DOFs (global, original order, -1 fixed), offsets
+    // into them, local DOF counts, and the value index of entry 0
+    std::vector<int32_t> blk_dofs, blk_dim, blk_vbase;
+    std::vector<int64_t> blk_off;
 
     // device binding
     std::vector<uint8_t> blob;   // host image of the device tables
@@ -223,7 +227,8 @@ struct Plan {
         size_t fronts, rows, child_ids, relmap, invmap, klist, front_lists, groups, chunks,
             asm_idx, asm_coef, sp_rowptr, sp_col, sp_slot, perm, row_sys, sys_n_off, g_rowptr,
             g_colind, g_aval, g_row_sys, e_dofs, e_K0, e_sys, e_off, e_k0off, e_dim, shifted,
-            g_rows_all, e_elems_all, tiny_list, tiny_off, tiny_prog, tiny_prog_off;
+            g_rows_all, e_elems_all, tiny_list, tiny_off, tiny_prog, tiny_prog_off, blk_dofs, blk_off,
+            blk_dim, blk_vbase;
     } toff{};
     WsLayout ws{};
     uint8_t* d_tab = nullptr;
@@ -270,6 +275,8 @@ int launch_numeric(Plan& P, const void* vals, int32_t vals_dtype, const double* 
 int launch_solve(Plan& P, const double* b, double* x, void* stream, bool* synced_ok);
 int launch_backward(Plan& P, const double* x, const double* xbar, double* vals_bar,
                     double* shift_bar, double* b_bar, void* stream);
+// vals_bar entries of ELEM_BLOCKS elements from mu and x (no-op without them)
+int launch_grad_blocks(Plan& P, const double* mu, const double* x, double* vals_bar, void* stream);
 int launch_reset_status(Plan& P, void* stream);
 int launch_graph_run(Plan& P, const void* vals, int32_t vals_dtype, const double* shift, const double* b, double* x,
                      void* stream);

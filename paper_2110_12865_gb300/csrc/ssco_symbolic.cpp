@@ -44,7 +44,7 @@ ssco_status bad(Plan& P, ssco_status s, const std::string& msg) {
 ssco_status validate(Plan& P, const ssco_pattern* p, int k) {
     std::string pre = "pattern " + std::to_string(k) + ": ";
     if (!p) return bad(P, SSCO_ERR_INVALID_ARG, pre + "NULL pattern");
-    if (p->kind != SSCO_KIND_ATWA && p->kind != SSCO_KIND_ELEM)
+    if (p->kind != SSCO_KIND_ATWA && p->kind != SSCO_KIND_ELEM && p->kind != SSCO_KIND_ELEM_BLOCKS)
         return bad(P, SSCO_ERR_INVALID_ARG, pre + "unknown kind");
     if (p->n < 1 || p->m < 0) return bad(P, SSCO_ERR_INVALID_ARG, pre + "n must be >= 1, m >= 0");
     std::vector<int32_t> mark((size_t)p->n, -1);
@@ -72,9 +72,12 @@ ssco_status validate(Plan& P, const ssco_pattern* p, int k) {
     } else {
         if (p->elem_dim < 1 || p->elem_dim > 64)
             return bad(P, SSCO_ERR_INVALID_ARG, pre + "elem_dim must be in [1, 64]");
-        if (p->m > 0 && (!p->elem_dofs || !p->elem_K0))
+        const bool blocks = p->kind == SSCO_KIND_ELEM_BLOCKS;  // element blocks come per call
+        if (p->m > 0 && (!p->elem_dofs || (!blocks && !p->elem_K0)))
             return bad(P, SSCO_ERR_INVALID_ARG, pre + "elem_dofs/elem_K0 is NULL");
         int64_t npk = (int64_t)p->elem_dim * (p->elem_dim + 1) / 2;
+        if (blocks && (int64_t)p->m * npk >= (int64_t)INT32_MAX)
+            return bad(P, SSCO_ERR_UNSUPPORTED, pre + "element block values exceed int32");
         for (int32_t e = 0; e < p->m; ++e) {
             for (int32_t i = 0; i < p->elem_dim; ++i) {
                 int32_t d = p->elem_dofs[(int64_t)e * p->elem_dim + i];
@@ -86,7 +89,7 @@ ssco_status validate(Plan& P, const ssco_pattern* p, int k) {
                     mark[d] = e;
                 }
             }
-            for (int64_t q = 0; q < npk; ++q)
+            for (int64_t q = 0; q < npk && !blocks; ++q)
                 if (!std::isfinite(p->elem_K0[(int64_t)e * npk + q]))
                     return bad(P, SSCO_ERR_NONFINITE, pre + "non-finite element block entry");
         }
@@ -234,8 +237,9 @@ ssco_status analyze_impl(const ssco_pattern* const* pats, int32_t n_pats, const 
         PatMeta& pm = P.pats[k];
         pm.kind = pats[k]->kind;
         pm.n = pats[k]->n;
-        pm.m = pats[k]->m;
-        pm.dim = pats[k]->kind == SSCO_KIND_ELEM ? pats[k]->elem_dim : 0;
+        pm.dim = pats[k]->kind == SSCO_KIND_ATWA ? 0 : pats[k]->elem_dim;
+        // values per set: one per row / element, or every packed block entry
+        pm.m = pats[k]->kind == SSCO_KIND_ELEM_BLOCKS ? pats[k]->m * (pm.dim * (pm.dim + 1) / 2) : pats[k]->m;
         pm.n_off = n;
         pm.m_off = m;
         n += pm.n;
@@ -307,8 +311,11 @@ ssco_status analyze_impl(const ssco_pattern* const* pats, int32_t n_pats, const 
                             int32_t gu = p->elem_dofs[(int64_t)e * d + i], gv = p->elem_dofs[(int64_t)e * d + j];
                             if (gu < 0 || gv < 0) continue;
                             int32_t u = iperm[pm.n_off + gu], v = iperm[pm.n_off + gv];
-                            Term t{std::max(u, v), (int32_t)(pm.m_off + e),
-                                   p->elem_K0[(int64_t)e * ((int64_t)d * (d + 1) / 2) + q]};
+                            const int64_t npk = (int64_t)d * (d + 1) / 2;
+                            // ELEM: E_e times the constant entry; ELEM_BLOCKS: the entry itself
+                            Term t = p->kind == SSCO_KIND_ELEM_BLOCKS
+                                         ? Term{std::max(u, v), (int32_t)(pm.m_off + e * npk + q), 1.0}
+                                         : Term{std::max(u, v), (int32_t)(pm.m_off + e), p->elem_K0[e * npk + q]};
                             terms[fill[std::min(u, v)]++] = t;
                         }
                 }
@@ -330,7 +337,7 @@ ssco_status analyze_impl(const ssco_pattern* const* pats, int32_t n_pats, const 
         auto b0 = terms.begin() + tcount[j], b1 = terms.begin() + tcount[j + 1];
         std::stable_sort(b0, b1, [](const Term& x, const Term& y) { return x.row < y.row; });
         int k = row_sys[j];
-        bool elem = P.pats[k].kind == SSCO_KIND_ELEM;
+        bool elem = P.pats[k].kind != SSCO_KIND_ATWA;
         // diagonal first, always present
         int64_t t = tcount[j];
         int64_t te = t;
@@ -848,7 +855,7 @@ ssco_status analyze_impl(const ssco_pattern* const* pats, int32_t n_pats, const 
         P.sys_n_off[n_pats] = n;
         P.shifted.assign(n, 1);
         for (int64_t j = 0; j < n; ++j)
-            if (P.pats[row_sys[j]].kind == SSCO_KIND_ELEM && !referenced[j]) P.shifted[j] = 0;
+            if (P.pats[row_sys[j]].kind != SSCO_KIND_ATWA && !referenced[j]) P.shifted[j] = 0;
     }
 
     // --- adjoint tables (original ordering, concatenated) -------------------
@@ -865,6 +872,10 @@ ssco_status analyze_impl(const ssco_pattern* const* pats, int32_t n_pats, const 
         P.e_k0off.clear();
         P.e_dim.clear();
         P.e_elems_all.clear();
+        P.blk_dofs.clear();
+        P.blk_off.clear();
+        P.blk_dim.clear();
+        P.blk_vbase.clear();
         for (int k = 0; k < n_pats; ++k) {
             const ssco_pattern* p = pats[k];
             const PatMeta& pm = P.pats[k];
@@ -877,6 +888,18 @@ ssco_status analyze_impl(const ssco_pattern* const* pats, int32_t n_pats, const 
                     P.g_rowptr.push_back((int64_t)P.g_colind.size());
                     P.g_row_sys.push_back(k);
                     P.g_rows_all.push_back((int32_t)(pm.m_off + e));
+                }
+            } else if (p->kind == SSCO_KIND_ELEM_BLOCKS) {
+                int32_t d = p->elem_dim;
+                int64_t npk = (int64_t)d * (d + 1) / 2;
+                for (int32_t e = 0; e < p->m; ++e) {
+                    P.blk_off.push_back((int64_t)P.blk_dofs.size());
+                    P.blk_dim.push_back(d);
+                    P.blk_vbase.push_back((int32_t)(pm.m_off + e * npk));
+                    for (int32_t i = 0; i < d; ++i) {
+                        int32_t g = p->elem_dofs[(int64_t)e * d + i];
+                        P.blk_dofs.push_back(g < 0 ? -1 : (int32_t)(pm.n_off + g));
+                    }
                 }
             } else {
                 int32_t d = p->elem_dim;
@@ -949,6 +972,10 @@ void build_blob(Plan& P) {
     P.toff.tiny_off = put(b, P.tiny_off);
     P.toff.tiny_prog = put(b, P.tiny_prog);
     P.toff.tiny_prog_off = put(b, P.tiny_prog_off);
+    P.toff.blk_dofs = put(b, P.blk_dofs);
+    P.toff.blk_off = put(b, P.blk_off);
+    P.toff.blk_dim = put(b, P.blk_dim);
+    P.toff.blk_vbase = put(b, P.blk_vbase);
     b.resize((b.size() + 255) & ~(size_t)255);
 }
 

@@ -32,7 +32,7 @@ EXPORTED_SYMBOLS = [
     "ssco_backward", "ssco_status_get", "ssco_export_L", "ssco_export_K", "ssco_refactor_solve_host",
     "ssco_last_launch_count", "ssco_last_error", "ssco_status_string", "ssco_plan_save", "ssco_plan_load",
     "ssco_destroy", "ssco_profile_enable", "ssco_profile_read", "ssco_kernel_name", "ssco_solve_noalloc", "ssco_profile_trace", "ssco_graph_run", "ssco_autotune",
-    "ssco_cotan_weights",
+    "ssco_cotan_weights", "ssco_tet_stiffness",
 ]
 KERNEL_KINDS = ["assemble", "front_small", "big_init", "big_kscatter", "big_update", "big_potrf", "big_syrk",
                 "fwd_solve", "bwd_solve", "resid", "check", "vector", "grad", "front_tiny", "big_trsm", "front_vec",
@@ -105,6 +105,7 @@ def load_library(path: str = LIB_PATH):
         "ssco_refactor_solve_host": (i32, [vp, vp, i32, vp, vp, vp, vp]),
         "ssco_last_launch_count": (i64, [vp]),
         "ssco_cotan_weights": (i32, [vp, vp, i64, i64, i64, i32, vp, vp, vp, vp]),
+        "ssco_tet_stiffness": (i32, [vp, i64, i64, i32, vp, vp, C.c_double, vp, vp, vp]),
         "ssco_last_error": (C.c_char_p, [vp]),
         "ssco_status_string": (C.c_char_p, [i32]),
         "ssco_plan_save": (i32, [vp, C.c_char_p]),
@@ -184,6 +185,11 @@ class Plan:
                     self._keep += [dofs, K0]
                     pat.elem_dim = int(p["elem_dim"])
                     pat.elem_dofs, pat.elem_K0 = dofs.ctypes.data, K0.ctypes.data
+                elif pat.kind == _problems.KIND_ELEM_BLOCKS:   # element blocks given per call
+                    dofs = np.ascontiguousarray(p["elem_dofs"], np.int32)
+                    self._keep.append(dofs)
+                    pat.elem_dim = int(p["elem_dim"])
+                    pat.elem_dofs = dofs.ctypes.data
                 if p.get("perm") is not None:
                     pm = np.ascontiguousarray(p["perm"], np.int32)
                     self._keep.append(pm)
@@ -414,6 +420,34 @@ class SscoSolve(torch.autograd.Function):
 
 def ssco_solve(plan: Plan, vals, shift, b):
     return SscoSolve.apply(plan, vals, shift, b)
+
+
+def tet_stiffness(tets: torch.Tensor, xyz: torch.Tensor, nu: float, E: torch.Tensor | None = None, stream=None,
+                  out=None, check=True):
+    """Linear-tet stiffness blocks [batch, n_tet, 78] (float64, device; packed
+    lower triangles, local DOF 3*vertex + component) from vertex positions
+    xyz [batch, n_node, 3] (float64, device), moduli E [batch, n_tet] (None =
+    1) and Poisson ratio nu; tets [n_tet, 4] int32 device tensor.  The values
+    of an ELEM_BLOCKS pattern over those tets.  See ssco_tet_stiffness in
+    ssco.h.  With ``check`` the call synchronizes and raises if any tet had
+    out-of-range ids or a degenerate shape (those blocks are zero)."""
+    L = load_library()
+    tets = tets.to(torch.int32).contiguous()
+    xyz = xyz.to(torch.float64).contiguous()
+    batch, n_node, n_tet = int(xyz.shape[0]), int(xyz.shape[1]), int(tets.shape[0])
+    if E is not None:
+        E = E.to(torch.float64).contiguous()
+        assert tuple(E.shape) == (batch, n_tet)
+    K = out if out is not None else torch.empty((batch, n_tet, 78), dtype=torch.float64, device=xyz.device)
+    assert K.dtype == torch.float64 and K.is_contiguous() and K.numel() == batch * n_tet * 78
+    nbad = torch.zeros(1, dtype=torch.int32, device=xyz.device) if check else None
+    st = L.ssco_tet_stiffness(_ptr(tets), n_tet, n_node, batch, _ptr(xyz), _ptr(E) if E is not None else None,
+                              float(nu), _ptr(K), _ptr(nbad) if check else None, _stream_ptr(stream))
+    if st != SSCO_OK:
+        raise SscoError(st, "ssco_tet_stiffness")
+    if check and int(nbad.item()) > 0:
+        raise SscoError(SSCO_ERR_INVALID_ARG, f"ssco_tet_stiffness: {int(nbad.item())} bad tets")
+    return K
 
 
 def cotan_weights(tri: torch.Tensor, tri_edge: torch.Tensor, xy: torch.Tensor, n_edge: int, stream=None, out=None,

@@ -238,3 +238,44 @@ def test_cotan_weights_argument_checks(S):
     assert L.ssco_cotan_weights(None, None, 1, 3, 3, 1, None, None, None, None) == 1  # null tables
     assert L.ssco_cotan_weights(None, None, -1, 3, 3, 1, None, None, None, None) == 1  # negative count
     assert L.ssco_cotan_weights(None, None, 0, 3, 3, 0, None, None, None, None) == 1  # batch < 1
+
+
+def test_tet_stiffness_argument_checks(S):
+    """ssco_tet_stiffness refuses inconsistent sizes, an out-of-range Poisson
+    ratio and null pointers before touching the device; no tets is a no-op."""
+    L = S.load_library()
+    assert L.ssco_tet_stiffness(None, 1, 4, 1, None, None, 0.3, None, None, None) == 1   # null tables
+    assert L.ssco_tet_stiffness(None, -1, 4, 1, None, None, 0.3, None, None, None) == 1  # negative count
+    assert L.ssco_tet_stiffness(None, 0, 4, 0, None, None, 0.3, None, None, None) == 1   # batch < 1
+    assert L.ssco_tet_stiffness(None, 0, 4, 65536, None, None, 0.3, None, None, None) == 1
+    for nu in (0.5, -1.0, 0.7, float("nan")):
+        assert L.ssco_tet_stiffness(None, 0, 4, 1, None, None, nu, None, None, None) == 1
+    assert L.ssco_tet_stiffness(None, 0, 4, 1, None, None, 0.3, None, None, None) == 0    # nothing to do
+
+
+def test_element_blocks_pattern_structure(S, tmp_path):
+    """A per-call element-block pattern has the structure of the modulus
+    pattern on the same mesh (same K and L patterns, etree, fronts); only its
+    value count grows to 78 per tet.  Its adjoint tables survive a plan file."""
+    p = P.elasticity_problem(3, cfg=2)
+    g = P.elasticity_geometry_problem(3, cfg=6)
+    a, b = S.Plan(p), S.Plan(g)
+    assert b.info["m"] == 78 * p.m and a.info["m"] == p.m
+    for k in ("n", "nnz_K", "nnz_L", "n_snodes", "n_fronts"):
+        assert a.info[k] == b.info[k], k
+    for what in (S.EXPORT_ETREE, S.EXPORT_COLCOUNT, S.EXPORT_L_COLPTR, S.EXPORT_L_ROWIND, S.EXPORT_PERM):
+        assert np.array_equal(a.export(what), b.export(what))
+    f = str(tmp_path / "blocks.bin")
+    b.save(f)
+    c = S.Plan.load(f)
+    assert c.info == b.info
+    import ctypes as C
+    pat = S.Pattern()
+    pat.kind, pat.n, pat.m, pat.elem_dim = P.KIND_ELEM_BLOCKS, 12, 1, 12   # elem_dofs left NULL
+    op = S.Op()
+    op.batch = 1
+    h = C.c_void_p()
+    arr = (C.POINTER(S.Pattern) * 1)(C.pointer(pat))
+    L = S.load_library()
+    assert L.ssco_analyze(arr, 1, C.byref(op), C.byref(h)) == 1
+    assert b"elem_dofs" in L.ssco_last_error(None)

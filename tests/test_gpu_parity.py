@@ -547,3 +547,91 @@ def test_full_elast48_batch16_with_gradient(S):
         assert np.max(np.abs(vbar[inst] - gv)) <= 1e-11 * np.abs(gv).max()
         gs = -float(np.dot(mu[inst][mask], x[inst][mask]))
         assert abs(sbar[inst] - gs) <= 1e-12 * np.linalg.norm(mu[inst]) * np.linalg.norm(x[inst])
+
+
+# ---------------------------------------------------------------------------
+# element blocks from geometry (ELEM_BLOCKS patterns, ssco_tet_stiffness)
+# ---------------------------------------------------------------------------
+def _blocks_close(Kd, Ko, rel=1e-12):
+    """Per tet: max |device - oracle| <= rel * max |oracle block|."""
+    Kd, Ko = Kd.reshape(-1, 78), Ko.reshape(-1, 78)
+    return bool(np.all(np.abs(Kd - Ko).max(axis=1) <= rel * np.abs(Ko).max(axis=1)))
+
+
+def test_tet_stiffness_on_device_match_oracle(S):
+    g = P.elasticity_geometry_problem(6, batch=3, cfg=6)
+    tets = torch.tensor(g.tets, device="cuda")
+    xyz = torch.tensor(g.pos, device="cuda")
+    K = S.tet_stiffness(tets, xyz, g.nu, torch.tensor(g.E, device="cuda")).cpu().numpy()
+    for i in range(3):
+        Ko, bad = O.tet_stiffness(g.tets, g.pos[i], g.E[i], g.nu)
+        assert bad == 0 and _blocks_close(K[i], Ko)
+    K1 = S.tet_stiffness(tets, xyz[:1], g.nu).cpu().numpy()[0]   # E omitted: unit moduli
+    assert _blocks_close(K1, O.tet_stiffness(g.tets, g.pos[0], None, g.nu)[0])
+    # an out-of-range vertex id (counted once) and a flat tet (once per value
+    # set): reported, their blocks zero, the others untouched
+    bt = g.tets[:5].copy()
+    bt[1, 2] = g.pos.shape[1]
+    bt[3, 3] = bt[3, 0]
+    btd = torch.tensor(bt, device="cuda")
+    with pytest.raises(S.SscoError) as ei:
+        S.tet_stiffness(btd, xyz, g.nu)
+    assert "4 bad tets" in str(ei.value)
+    Kb = S.tet_stiffness(btd, xyz, g.nu, check=False).cpu().numpy()
+    assert np.all(Kb[:, [1, 3]] == 0)
+    good = [0, 2, 4]
+    for i in range(3):
+        assert _blocks_close(Kb[i, good], O.tet_stiffness(bt[good], g.pos[i], None, g.nu)[0])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_element_blocks_pattern_solve_and_gradient(S, prec):
+    """An ELEM_BLOCKS plan fed the oracle's blocks: solutions meet the
+    residual bound with the oracle's K and the per-entry gradient matches the
+    oracle's adjoint; then the device chain geometry -> blocks -> solve gives
+    the same solutions (the blocks' layout is the plan's value order)."""
+    g = P.elasticity_geometry_problem(4, batch=3, cfg=6)
+    B = 3
+    precision = S.FP64 if prec == "fp64" else S.FP32_REFINE
+    Ko = np.stack([O.tet_stiffness(g.tets, g.pos[i], g.E[i], g.nu)[0].ravel() for i in range(B)])
+    pl = S.Plan(g, precision=precision, batch=B).bind()
+    zero = torch.zeros(B, dtype=torch.float64, device="cuda")
+    bt = torch.tensor(g.b, device="cuda")
+    pl.numeric(torch.tensor(Ko, device="cuda"), zero)
+    x = pl.solve(bt)
+    st = pl.status()
+    assert np.all(st["status"] == 0) and np.all(st["resid"] <= RESID_TOL)
+    xbar = torch.tensor(np.random.default_rng(5).standard_normal((B, g.n)), device="cuda")
+    vbar, sbar, mu = pl.backward(x, xbar)
+    xh, vbar = x.cpu().numpy(), vbar.cpu().numpy()
+    tol = 1e-9 if prec == "fp64" else 1e-7
+    for i in range(B):
+        r = O.refactor_solve(g, i, vals=Ko[i], shift=0.0)
+        res = np.linalg.norm(O.symv(r.K, xh[i]) - g.b[i]) / np.linalg.norm(g.b[i])
+        assert res <= RESID_TOL, (i, res)
+        gv, _, _ = O.backward(g, r, xbar[i].cpu().numpy(), i)
+        assert np.max(np.abs(vbar[i] - gv)) <= tol * np.abs(gv).max()
+    Kd = S.tet_stiffness(torch.tensor(g.tets, device="cuda"), torch.tensor(g.pos, device="cuda"), g.nu,
+                         torch.tensor(g.E, device="cuda"))
+    pl.numeric(Kd.reshape(B, -1), zero)
+    x2 = pl.solve(bt).cpu().numpy()
+    st = pl.status()
+    assert np.all(st["status"] == 0) and np.all(st["resid"] <= RESID_TOL)
+    assert np.linalg.norm(x2 - xh) <= 1e-6 * np.linalg.norm(xh)
+
+
+def test_full_elastgeo24_blocks_and_refine(S):
+    """Full 24^3 mesh (82,944 tets), geometry per call: device blocks against
+    the oracle on sampled tets, then FP32 factor + refinement on them."""
+    g = P.elasticity_geometry_problem(24, batch=1, cfg=6)
+    Kd = S.tet_stiffness(torch.tensor(g.tets, device="cuda"), torch.tensor(g.pos, device="cuda"), g.nu,
+                         torch.tensor(g.E, device="cuda"))
+    Kh = Kd.cpu().numpy()[0]
+    pick = np.random.default_rng(24).choice(g.m, 2000, replace=False)
+    Ko, bad = O.tet_stiffness(g.tets[pick], g.pos[0], g.E[0][pick], g.nu)
+    assert bad == 0 and _blocks_close(Kh[pick], Ko)
+    pl = S.Plan(g, precision=S.FP32_REFINE, batch=1).bind()
+    pl.numeric(Kd.reshape(1, -1), torch.zeros(1, dtype=torch.float64, device="cuda"))
+    pl.solve(torch.tensor(g.b, device="cuda"))
+    st = pl.status()
+    assert np.all(st["status"] == 0) and np.all(st["resid"] <= RESID_TOL)
