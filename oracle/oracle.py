@@ -279,3 +279,62 @@ def tet_stiffness(tets, xyz, E, nu: float):
     Ec = None if E is None else _c(E, np.float64)
     bad = lib().or_tet_stiffness(tets.shape[0], tets, xyz, None if Ec is None else Ec.ctypes.data, float(nu), out)
     return out, int(bad)
+
+
+# ---------------------------------------------------------------------------
+# fixed-pattern sparse matrix expressions (Sec. 5 sparse-expression and
+# structured-product experiments), by definition, in FP64
+# ---------------------------------------------------------------------------
+def expr_eval(nodes, leaf_vals, outputs, absolute: bool = False):
+    """Evaluate a DAG of sparse matrices for one value set.
+
+    nodes: ("leaf", rows, cols, rowptr, colind) | ("add", a, b) |
+    ("scale", a, alpha) | ("mul", a, b) | ("transpose", a), operands by
+    earlier index.  leaf_vals: the leaves' values concatenated in node
+    order.  Entries are dictionaries {(i, j): value} holding every
+    structurally present entry (a sum or product that happens to be zero
+    included): A + B has the union of both patterns, A B every (i, j) with
+    some k where A_ik and B_kj are present, summing A_ik B_kj over those k.
+    With `absolute` every leaf value and every alpha enters by its absolute
+    value (the scale of the rounding error of any evaluation order).
+    Returns [(rows, cols, dict)] for the requested outputs."""
+    mats, off = [], 0
+    for nd in nodes:
+        kind = nd[0]
+        if kind == "leaf":
+            _, r, c, rp, ci = nd
+            d = {}
+            for i in range(r):
+                for q in range(int(rp[i]), int(rp[i + 1])):
+                    v = float(leaf_vals[off + q])
+                    d[(i, int(ci[q]))] = abs(v) if absolute else v
+            off += int(rp[r])
+            mats.append((r, c, d))
+        elif kind == "add":
+            ra, ca, A = mats[nd[1]]
+            B = mats[nd[2]][2]
+            d = dict(A)
+            for key, v in B.items():
+                d[key] = d.get(key, 0.0) + v
+            mats.append((ra, ca, d))
+        elif kind == "scale":
+            ra, ca, A = mats[nd[1]]
+            al = abs(nd[2]) if absolute else nd[2]
+            mats.append((ra, ca, {key: al * v for key, v in A.items()}))
+        elif kind == "transpose":
+            ra, ca, A = mats[nd[1]]
+            mats.append((ca, ra, {(j, i): v for (i, j), v in A.items()}))
+        elif kind == "mul":
+            ra, _, A = mats[nd[1]]
+            _, cb, B = mats[nd[2]]
+            rows_b = {}
+            for (k, j), v in B.items():
+                rows_b.setdefault(k, []).append((j, v))
+            d = {}
+            for (i, k), a in A.items():
+                for j, b in rows_b.get(k, ()):
+                    d[(i, j)] = d.get((i, j), 0.0) + a * b
+            mats.append((ra, cb, d))
+        else:
+            raise ValueError(kind)
+    return [mats[o] for o in outputs]

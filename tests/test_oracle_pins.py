@@ -619,3 +619,103 @@ def test_gradient_element_blocks_central_differences():
     ii, jj = np.tril_indices(12)
     on_fixed = (dofs[ii] < 0) | (dofs[jj] < 0)
     assert np.all(vbar[fixed_e * 78: (fixed_e + 1) * 78][on_fixed] == 0)
+
+
+# sparse matrix expressions
+# ----------------------------------------------------------------------------
+def _rand_csr(rng, rows, cols, per_row):
+    rp, ci = [0], []
+    for _ in range(rows):
+        c = np.sort(rng.choice(cols, min(per_row, cols), replace=False))
+        ci.extend(c.tolist())
+        rp.append(len(ci))
+    return np.array(rp, np.int64), np.array(ci, np.int32)
+
+
+def _dense_eval(nodes, vals, outputs):
+    """The same expressions with dense numpy matrices (values) and boolean
+    matrices (structure) -- a different route to the same definitions."""
+    D, Pm, off = [], [], 0
+    for nd in nodes:
+        if nd[0] == "leaf":
+            _, r, c, rp, ci = nd
+            M, Pb = np.zeros((r, c)), np.zeros((r, c), bool)
+            for i in range(r):
+                M[i, ci[rp[i]:rp[i + 1]]] = vals[off + rp[i]: off + rp[i + 1]]
+                Pb[i, ci[rp[i]:rp[i + 1]]] = True
+            off += rp[r]
+            D.append(M), Pm.append(Pb)
+        elif nd[0] == "add":
+            D.append(D[nd[1]] + D[nd[2]]), Pm.append(Pm[nd[1]] | Pm[nd[2]])
+        elif nd[0] == "scale":
+            D.append(nd[2] * D[nd[1]]), Pm.append(Pm[nd[1]].copy())
+        elif nd[0] == "transpose":
+            D.append(D[nd[1]].T), Pm.append(Pm[nd[1]].T)
+        else:
+            D.append(D[nd[1]] @ D[nd[2]]), Pm.append((Pm[nd[1]].astype(int) @ Pm[nd[2]].astype(int)) > 0)
+    return [(D[o], Pm[o]) for o in outputs]
+
+
+def paper_expressions(n, rng, per_row=6):
+    """(alpha A + B)^T (beta B^T + C), A B C and (A + B)(A B + C) on random
+    n x n matrices with `per_row` entries per row (Sec. 5 sparse expressions)."""
+    leaves = [("leaf", n, n, *_rand_csr(rng, n, n, per_row)) for _ in range(3)]
+    nodes = list(leaves)  # 0 A, 1 B, 2 C
+
+    def add(nd):
+        nodes.append(nd)
+        return len(nodes) - 1
+    e1 = add(("mul", add(("transpose", add(("add", add(("scale", 0, 0.7)), 1)))),
+              add(("add", add(("scale", add(("transpose", 1)), -1.3)), 2))))
+    ab = add(("mul", 0, 1))
+    e2 = add(("mul", ab, 2))
+    e3 = add(("mul", add(("add", 0, 1)), add(("add", ab, 2))))
+    nv = sum(int(l[3][-1]) for l in leaves)
+    return nodes, [e1, e2, e3], nv
+
+
+def test_expr_oracle_matches_dense_evaluation():
+    rng = np.random.default_rng(51)
+    nodes, outs, nv = paper_expressions(40, rng, per_row=4)
+    vals = rng.standard_normal(nv)
+    got = O.expr_eval(nodes, vals, outs)
+    for (r, c, d), (M, Pb) in zip(got, _dense_eval(nodes, vals, outs)):
+        assert set(d) == set(zip(*np.nonzero(Pb)))       # structural pattern
+        G = np.zeros((r, c))
+        for (i, j), v in d.items():
+            G[i, j] = v
+        assert np.abs(G - M).max() <= 1e-12 * np.abs(M).max()
+
+
+def test_expr_oracle_tridiagonal_cube_closed_form():
+    """T = tridiag(-1, 2, -1): T^3 has interior rows (-1, 6, -15, 20, -15, 6, -1)
+    (the sixth finite difference, -(1 - x)^6 up to the shift)."""
+    n = 12
+    rp, ci, v = [0], [], []
+    for i in range(n):
+        for j, a in ((i - 1, -1.0), (i, 2.0), (i + 1, -1.0)):
+            if 0 <= j < n:
+                ci.append(j), v.append(a)
+        rp.append(len(ci))
+    nodes = [("leaf", n, n, np.array(rp), np.array(ci)), ("mul", 0, 0), ("mul", 1, 0)]
+    (_, _, d), = O.expr_eval(nodes, np.array(v), [2])
+    for i in range(3, n - 3):
+        row = [d[(i, j)] for j in range(i - 3, i + 4)]
+        assert row == [-1.0, 6.0, -15.0, 20.0, -15.0, 6.0, -1.0]
+        assert all((i, j) not in d for j in range(n) if abs(i - j) > 3)
+
+
+def test_expr_oracle_weighted_laplacian_of_a_path():
+    """A^T (W A) for the incidence matrix A of a path and W = diag(w) is the
+    weighted path Laplacian: L_ii = w_(i-1) + w_i, L_(i,i+1) = -w_i."""
+    n, m = 6, 5
+    w = np.array([0.5, 2.0, 1.5, 3.0, 0.25])
+    A = ("leaf", m, n, np.arange(0, 2 * m + 1, 2), np.array([[e, e + 1] for e in range(m)]).ravel())
+    W = ("leaf", m, m, np.arange(m + 1), np.arange(m))
+    nodes = [A, W, ("transpose", 0), ("mul", 1, 0), ("mul", 2, 3)]
+    vals = np.concatenate([np.tile([1.0, -1.0], m), w])
+    (_, _, d), = O.expr_eval(nodes, vals, [4])
+    for i in range(n):
+        assert d[(i, i)] == (w[i - 1] if i > 0 else 0.0) + (w[i] if i < m else 0.0)
+        if i < m:
+            assert d[(i, i + 1)] == -w[i] and d[(i + 1, i)] == -w[i]
