@@ -338,3 +338,63 @@ def expr_eval(nodes, leaf_vals, outputs, absolute: bool = False):
         else:
             raise ValueError(kind)
     return [mats[o] for o in outputs]
+
+
+def expr_eval_rows(nodes, leaf_vals, output, rows):
+    """Selected rows of one node of the same DAG, by the same definitions as
+    expr_eval, evaluated lazily: a row of a product needs one row of its left
+    factor and the rows of its right factor that row touches; a row of a
+    transposed leaf is a column of the leaf.  Returns {i: {j: value}}."""
+    offs, off = [], 0
+    for nd in nodes:
+        offs.append(off)
+        if nd[0] == "leaf":
+            off += int(nd[3][nd[1]])
+    cache, cols_of_leaf, full = {}, {}, {}
+
+    def leaf_row(nid, i):
+        _, r, c, rp, ci = nodes[nid]
+        return {int(ci[q]): float(leaf_vals[offs[nid] + q]) for q in range(int(rp[i]), int(rp[i + 1]))}
+
+    def column(nid, j):
+        if nodes[nid][0] == "leaf":
+            if nid not in cols_of_leaf:
+                _, r, c, rp, ci = nodes[nid]
+                cl = {}
+                for i in range(r):
+                    for q in range(int(rp[i]), int(rp[i + 1])):
+                        cl.setdefault(int(ci[q]), {})[i] = float(leaf_vals[offs[nid] + q])
+                cols_of_leaf[nid] = cl
+            return dict(cols_of_leaf[nid].get(j, {}))
+        if nid not in full:
+            (_, _, d), = expr_eval(nodes, leaf_vals, [nid])
+            cl = {}
+            for (i, jj), v in d.items():
+                cl.setdefault(jj, {})[i] = v
+            full[nid] = cl
+        return dict(full[nid].get(j, {}))
+
+    def row(nid, i):
+        key = (nid, i)
+        if key in cache:
+            return cache[key]
+        nd = nodes[nid]
+        if nd[0] == "leaf":
+            r = leaf_row(nid, i)
+        elif nd[0] == "add":
+            r = dict(row(nd[1], i))
+            for j, v in row(nd[2], i).items():
+                r[j] = r.get(j, 0.0) + v
+        elif nd[0] == "scale":
+            r = {j: nd[2] * v for j, v in row(nd[1], i).items()}
+        elif nd[0] == "transpose":
+            r = column(nd[1], i)
+        else:
+            r = {}
+            for k, a in row(nd[1], i).items():
+                for j, b in row(nd[2], k).items():
+                    r[j] = r.get(j, 0.0) + a * b
+        cache[key] = r
+        return r
+
+    return {int(i): row(output, int(i)) for i in rows}

@@ -719,3 +719,15 @@ def test_expr_oracle_weighted_laplacian_of_a_path():
         assert d[(i, i)] == (w[i - 1] if i > 0 else 0.0) + (w[i] if i < m else 0.0)
         if i < m:
             assert d[(i, i + 1)] == -w[i] and d[(i + 1, i)] == -w[i]
+
+
+def test_expr_row_oracle_equals_full_oracle():
+    """The lazy row evaluator gives the full evaluator's rows exactly (same
+    definitions; transposes of leaves and of intermediates both covered)."""
+    rng = np.random.default_rng(52)
+    nodes, outs, nv = paper_expressions(30, rng, per_row=3)
+    vals = rng.standard_normal(nv)
+    for o in outs:
+        (_, _, d), = O.expr_eval(nodes, vals, [o])
+        rows = O.expr_eval_rows(nodes, vals, o, range(30))
+        assert {(i, j): v for i, r in rows.items() for j, v in r.items()} == d
