@@ -352,6 +352,86 @@ ssco_status ssco_cotan_weights(const int32_t* tri, const int32_t* tri_edge, int6
 ssco_status ssco_tet_stiffness(const int32_t* tets, int64_t n_tet, int64_t n_node, int32_t batch, const double* xyz,
                                const double* E, double nu, double* K_e, int32_t* n_bad, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Fixed-pattern sparse matrix expressions (the paper's method applied to
+ * sparse algebra, Sec. 4 and the sparse-expression experiments of Sec. 5):
+ * a DAG of sparse matrices with fixed patterns is unrolled once on the host
+ * into scalar expressions (every entry of a product or sum), structurally
+ * identical scalar expressions are merged (hashing), each is assigned the
+ * level = longest path from the leaves, and the level groups with their
+ * harvested index tables are run by one gather-multiply-accumulate kernel
+ * per level, for `batch` value sets at once.
+ *
+ * Node ids are positions in the node array; operands must come earlier.
+ *   LEAF       a rows x cols CSR pattern (rowptr[rows+1] int64, colind
+ *              int32 strictly increasing within each row); its values are
+ *              supplied per call.
+ *   ADD        a + b (same shape; pattern = union).
+ *   SCALE      alpha * a.
+ *   MUL        a * b (a.cols == b.rows; pattern = structural product).
+ *   TRANSPOSE  a^T.
+ * Every entry of an ADD present in both operands and every entry of a MUL
+ * is stored once as an intermediate (a global intermediate in the paper's
+ * terms); scaling and transposition only relabel entries.  The products of
+ * a MUL entry are summed in ascending (k, j) order of generation after
+ * merging equal factor pairs; values are float or double (`precision` =
+ * SSCO_VALS_F64 / SSCO_VALS_F32) and accumulate in that type.
+ * Leaf values per set are the leaves' nnz concatenated in node order
+ * ([batch][n_leaf_vals]); outputs likewise ([batch][n_out_vals], in the
+ * order of `outputs`, each in its CSR order). */
+typedef struct ssco_expr_s* ssco_expr;
+enum { SSCO_EXPR_LEAF = 0, SSCO_EXPR_ADD = 1, SSCO_EXPR_SCALE = 2, SSCO_EXPR_MUL = 3, SSCO_EXPR_TRANSPOSE = 4 };
+typedef struct {
+    int32_t op;            /* SSCO_EXPR_* */
+    int32_t a, b;          /* operand node ids (-1 where unused) */
+    double alpha;          /* SCALE factor */
+    int32_t rows, cols;    /* LEAF shape */
+    const int64_t* rowptr; /* LEAF pattern (host; copied by compile) */
+    const int32_t* colind;
+} ssco_expr_node;
+typedef struct {
+    int64_t n_leaf_vals;   /* values per set: all leaves' nnz */
+    int64_t n_out_vals;    /* values per set: all outputs' nnz */
+    int64_t n_slots;       /* 1 (the constant one) + leaf values + stored intermediates */
+    int64_t n_ops;         /* stored intermediates (scalar expressions) */
+    int64_t n_terms;       /* products over all of them */
+    int64_t n_unrolled;    /* scalar expressions before hashing and relabelling */
+    int32_t n_levels;
+    int32_t batch;
+    int32_t precision;
+    int32_t unit_coef;     /* 1: every coefficient is 1 (no coefficient table) */
+    uint64_t table_bytes;  /* device tables (ssco_expr_bind) */
+    uint64_t workspace_bytes;
+} ssco_expr_info;
+enum { SSCO_EXPR_EXPORT_LEVELS = 0,   /* int64 [n_levels+1] op ranges */
+       SSCO_EXPR_EXPORT_TERM_OFF = 1, /* int64 [n_ops+1] */
+       SSCO_EXPR_EXPORT_F1 = 2,       /* int32 [n_terms] first factor slot */
+       SSCO_EXPR_EXPORT_F2 = 3,       /* int32 [n_terms] second factor slot (0 = the constant one) */
+       SSCO_EXPR_EXPORT_COEF = 4,     /* double [n_terms] */
+       SSCO_EXPR_EXPORT_OUT_SLOT = 5, /* int32 [n_out_vals] slot of each output value */
+       SSCO_EXPR_EXPORT_OUT_COEF = 6  /* double [n_out_vals] its factor */ };
+
+/* Host only.  Slot layout: slot 0 = 1, slots 1..n_leaf_vals = leaf values,
+ * then the intermediates of level 1, 2, ... (op i is slot
+ * 1 + n_leaf_vals + i).  Returns INVALID_ARG / PATTERN for malformed nodes
+ * (message in ssco_expr_last_error(NULL)), UNSUPPORTED beyond int32 slots. */
+ssco_status ssco_expr_compile(const ssco_expr_node* nodes, int32_t n_nodes, const int32_t* outputs, int32_t n_out,
+                              int32_t batch, int32_t precision, ssco_expr* out);
+ssco_status ssco_expr_get_info(ssco_expr e, ssco_expr_info* out);
+ssco_status ssco_expr_export(ssco_expr e, int32_t what, void* host_buf, uint64_t bytes);
+/* Shape and CSR pattern of the k-th output (rowptr [rows+1], colind [nnz]). */
+ssco_status ssco_expr_output_shape(ssco_expr e, int32_t k, int32_t* rows, int32_t* cols, int64_t* nnz);
+ssco_status ssco_expr_output_pattern(ssco_expr e, int32_t k, int64_t* rowptr, int32_t* colind);
+/* Caller-allocated device memory of table_bytes / workspace_bytes (256-byte
+ * aligned); the tables are copied with `stream`, which is synchronized. */
+ssco_status ssco_expr_bind(ssco_expr e, void* dev_tables, void* dev_workspace, void* stream);
+/* Evaluates every set: leaf_vals [batch][n_leaf_vals] and out_vals
+ * [batch][n_out_vals] device arrays of the program's precision.  Async;
+ * launches 2 + n_levels kernels on `stream`. */
+ssco_status ssco_expr_run(ssco_expr e, const void* leaf_vals, void* out_vals, void* stream);
+const char* ssco_expr_last_error(ssco_expr e);
+void ssco_expr_destroy(ssco_expr e);
+
 /* Number of kernel launches the last ssco_numeric / ssco_solve /
  * ssco_backward / ssco_refactor_solve_host call issued (host counter). */
 int64_t ssco_last_launch_count(ssco_plan plan);

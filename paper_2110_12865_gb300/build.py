@@ -16,8 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libssco.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["ssco_api.cpp", "ssco_symbolic.cpp", "ssco_kernels.cu", "ssco_values.cu"]
-HEADERS = ["ssco_internal.h"]
+SOURCES = ["ssco_api.cpp", "ssco_symbolic.cpp", "ssco_kernels.cu", "ssco_values.cu", "ssco_expr.cpp", "ssco_expr_run.cu"]
+HEADERS = ["ssco_internal.h", "ssco_expr_internal.h"]
 
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

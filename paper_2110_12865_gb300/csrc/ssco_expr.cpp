@@ -1,0 +1,567 @@
+// ssco_expr.cpp -- host compiler of fixed-pattern sparse matrix expressions.
+//
+// The method of the paper (Sec. 4) applied to sparse algebra: the expression
+// DAG is executed once symbolically, entry by entry.  Every entry that needs
+// arithmetic (an ADD entry present in both operands, every MUL entry) becomes
+// one scalar expression, a sum of products of two slots; structurally equal
+// scalar expressions are merged by hashing their canonical form (Sec. 4.2's
+// structural hashing; slots are the leaves of Sec. 4.4 and the stored
+// intermediates of Sec. 4.2.1); each expression's level is one more than the
+// highest level among its factors (the longest path from the leaves, so a
+// level never holds an expression together with one it depends on, Sec. 4.3),
+// and the level groups are written out as index tables (leaf harvesting,
+// Sec. 4.4), slots of one level contiguous (outputs written consecutively,
+// Sec. 4.8).  Scaling and transposition only relabel entries.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "ssco_expr_internal.h"
+
+namespace ssco {
+namespace {
+
+thread_local std::string g_expr_err;
+
+struct Handle {
+    double c;   // the entry's value is c * slot s
+    int32_t s;
+};
+struct Term {
+    int32_t f1, f2;  // factor slots, f1 >= f2 (slot 0 = the constant one)
+    double c;
+};
+
+uint64_t fnv(uint64_t h, const void* p, size_t n) {
+    const unsigned char* b = static_cast<const unsigned char*>(p);
+    for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 0x100000001b3ull;
+    return h;
+}
+
+// Scalar expressions under construction, merged by structural hashing.
+struct Builder {
+    int64_t base = 0;  // slot id of the first stored expression
+    std::vector<int32_t> level, nt;
+    std::vector<int64_t> tbeg;
+    std::vector<uint64_t> hash;
+    std::vector<Term> pool;
+    std::vector<int32_t> table;  // open addressing: expression index + 1, 0 = empty
+    int64_t n_unrolled = 0;
+    bool overflow = false;
+    std::vector<Term> t;  // the expression being built
+
+    int32_t level_of(int32_t s) const { return s >= base ? level[s - base] : 0; }
+
+    void rehash(size_t cap) {
+        table.assign(cap, 0);
+        for (size_t i = 0; i < level.size(); ++i) {
+            size_t p = hash[i] & (cap - 1);
+            while (table[p]) p = (p + 1) & (cap - 1);
+            table[p] = (int32_t)i + 1;
+        }
+    }
+
+    // The sum of the terms in `t`, as a handle: a constant multiple of one
+    // slot needs no expression; anything else is stored once.
+    Handle materialize() {
+        ++n_unrolled;
+        for (Term& x : t)
+            if (x.f1 < x.f2) std::swap(x.f1, x.f2);
+        std::sort(t.begin(), t.end(), [](const Term& a, const Term& b) {
+            return a.f1 != b.f1 ? a.f1 < b.f1 : a.f2 < b.f2;
+        });
+        size_t w = 0;
+        for (size_t r = 0; r < t.size(); ++r) {
+            if (w > 0 && t[w - 1].f1 == t[r].f1 && t[w - 1].f2 == t[r].f2)
+                t[w - 1].c += t[r].c;  // equal factor pairs: one product
+            else
+                t[w++] = t[r];
+        }
+        t.resize(w);
+        t.erase(std::remove_if(t.begin(), t.end(), [](const Term& x) { return x.c == 0.0; }), t.end());
+        if (t.empty()) return {0.0, 0};
+        if (t.size() == 1 && t[0].f2 == 0) return {t[0].c, t[0].f1};
+        uint64_t h = 0xcbf29ce484222325ull;
+        for (const Term& x : t) {
+            h = fnv(h, &x.f1, 4);
+            h = fnv(h, &x.f2, 4);
+            h = fnv(h, &x.c, 8);
+        }
+        if (table.empty()) rehash(1 << 16);
+        size_t cap = table.size(), p = h & (cap - 1);
+        while (table[p]) {
+            const int32_t i = table[p] - 1;
+            if (hash[i] == h && nt[i] == (int32_t)t.size()) {
+                const Term* q = pool.data() + tbeg[i];
+                bool same = true;
+                for (size_t k = 0; k < t.size() && same; ++k)
+                    same = q[k].f1 == t[k].f1 && q[k].f2 == t[k].f2 && q[k].c == t[k].c;
+                if (same) return {1.0, (int32_t)(base + i)};
+            }
+            p = (p + 1) & (cap - 1);
+        }
+        const int64_t idx = (int64_t)level.size();
+        if (base + idx >= (int64_t)INT32_MAX - 1) {
+            overflow = true;
+            return {0.0, 0};
+        }
+        int32_t lv = 0;
+        for (const Term& x : t) lv = std::max(lv, std::max(level_of(x.f1), level_of(x.f2)));
+        level.push_back(lv + 1);
+        nt.push_back((int32_t)t.size());
+        tbeg.push_back((int64_t)pool.size());
+        hash.push_back(h);
+        pool.insert(pool.end(), t.begin(), t.end());
+        table[p] = (int32_t)idx + 1;
+        if (2 * level.size() > cap) rehash(cap * 2);
+        return {1.0, (int32_t)(base + idx)};
+    }
+};
+
+ssco_status bad(ssco_status s, const std::string& msg) {
+    g_expr_err = msg;
+    return s;
+}
+
+ssco_status validate(const ssco_expr_node* nodes, int32_t n_nodes, const int32_t* outputs, int32_t n_out,
+                     int32_t batch, int32_t precision, std::vector<int32_t>& rows, std::vector<int32_t>& cols) {
+    if (!nodes || n_nodes < 1 || !outputs || n_out < 1) return bad(SSCO_ERR_INVALID_ARG, "no nodes or no outputs");
+    if (batch < 1 || batch > 65535) return bad(SSCO_ERR_INVALID_ARG, "batch must be in [1, 65535]");
+    if (precision != SSCO_VALS_F64 && precision != SSCO_VALS_F32)
+        return bad(SSCO_ERR_INVALID_ARG, "precision must be SSCO_VALS_F64 or SSCO_VALS_F32");
+    rows.assign(n_nodes, 0);
+    cols.assign(n_nodes, 0);
+    int64_t leaf_vals = 0;
+    for (int32_t i = 0; i < n_nodes; ++i) {
+        const ssco_expr_node& nd = nodes[i];
+        const std::string pre = "node " + std::to_string(i) + ": ";
+        auto operand = [&](int32_t a) { return a >= 0 && a < i; };
+        switch (nd.op) {
+            case SSCO_EXPR_LEAF: {
+                if (nd.rows < 0 || nd.cols < 0) return bad(SSCO_ERR_INVALID_ARG, pre + "negative shape");
+                if (!nd.rowptr) return bad(SSCO_ERR_INVALID_ARG, pre + "rowptr is NULL");
+                if (nd.rowptr[0] != 0) return bad(SSCO_ERR_PATTERN, pre + "rowptr[0] != 0");
+                for (int32_t r = 0; r < nd.rows; ++r)
+                    if (nd.rowptr[r + 1] < nd.rowptr[r]) return bad(SSCO_ERR_PATTERN, pre + "rowptr decreases");
+                const int64_t nnz = nd.rowptr[nd.rows];
+                if (nnz > 0 && !nd.colind) return bad(SSCO_ERR_INVALID_ARG, pre + "colind is NULL");
+                for (int32_t r = 0; r < nd.rows; ++r)
+                    for (int64_t q = nd.rowptr[r]; q < nd.rowptr[r + 1]; ++q) {
+                        if (nd.colind[q] < 0 || nd.colind[q] >= nd.cols)
+                            return bad(SSCO_ERR_PATTERN, pre + "column index out of range");
+                        if (q > nd.rowptr[r] && nd.colind[q] <= nd.colind[q - 1])
+                            return bad(SSCO_ERR_PATTERN, pre + "columns not strictly increasing in a row");
+                    }
+                leaf_vals += nnz;
+                rows[i] = nd.rows;
+                cols[i] = nd.cols;
+                break;
+            }
+            case SSCO_EXPR_ADD:
+                if (!operand(nd.a) || !operand(nd.b)) return bad(SSCO_ERR_INVALID_ARG, pre + "bad operand");
+                if (rows[nd.a] != rows[nd.b] || cols[nd.a] != cols[nd.b])
+                    return bad(SSCO_ERR_INVALID_ARG, pre + "ADD of different shapes");
+                rows[i] = rows[nd.a];
+                cols[i] = cols[nd.a];
+                break;
+            case SSCO_EXPR_SCALE:
+                if (!operand(nd.a)) return bad(SSCO_ERR_INVALID_ARG, pre + "bad operand");
+                if (!std::isfinite(nd.alpha)) return bad(SSCO_ERR_NONFINITE, pre + "non-finite alpha");
+                rows[i] = rows[nd.a];
+                cols[i] = cols[nd.a];
+                break;
+            case SSCO_EXPR_MUL:
+                if (!operand(nd.a) || !operand(nd.b)) return bad(SSCO_ERR_INVALID_ARG, pre + "bad operand");
+                if (cols[nd.a] != rows[nd.b]) return bad(SSCO_ERR_INVALID_ARG, pre + "MUL of incompatible shapes");
+                rows[i] = rows[nd.a];
+                cols[i] = cols[nd.b];
+                break;
+            case SSCO_EXPR_TRANSPOSE:
+                if (!operand(nd.a)) return bad(SSCO_ERR_INVALID_ARG, pre + "bad operand");
+                rows[i] = cols[nd.a];
+                cols[i] = rows[nd.a];
+                break;
+            default:
+                return bad(SSCO_ERR_INVALID_ARG, pre + "unknown op");
+        }
+    }
+    for (int32_t k = 0; k < n_out; ++k)
+        if (outputs[k] < 0 || outputs[k] >= n_nodes) return bad(SSCO_ERR_INVALID_ARG, "output id out of range");
+    if (leaf_vals + 1 >= (int64_t)INT32_MAX) return bad(SSCO_ERR_UNSUPPORTED, "leaf values exceed int32 slots");
+    return SSCO_OK;
+}
+
+ssco_status compile(const ssco_expr_node* nodes, int32_t n_nodes, const int32_t* outputs, int32_t n_out,
+                    int32_t batch, int32_t precision, ExprProgram& E) {
+    std::vector<int32_t> rows, cols;
+    ssco_status st = validate(nodes, n_nodes, outputs, n_out, batch, precision, rows, cols);
+    if (st != SSCO_OK) return st;
+    E.B = batch;
+    E.precision = precision;
+    // last use of every node, so that its entries can be released
+    std::vector<int32_t> last(n_nodes, -1);
+    for (int32_t i = 0; i < n_nodes; ++i) {
+        if (nodes[i].op != SSCO_EXPR_LEAF) last[nodes[i].a] = i;
+        if (nodes[i].op == SSCO_EXPR_ADD || nodes[i].op == SSCO_EXPR_MUL) last[nodes[i].b] = i;
+    }
+    for (int32_t k = 0; k < n_out; ++k) last[outputs[k]] = n_nodes;
+    int64_t leaf_vals = 0;
+    for (int32_t i = 0; i < n_nodes; ++i)
+        if (nodes[i].op == SSCO_EXPR_LEAF) leaf_vals += nodes[i].rowptr[nodes[i].rows];
+    E.n_leaf_vals = leaf_vals;
+    Builder bd;
+    bd.base = 1 + leaf_vals;
+    std::vector<ExprCsr> pat(n_nodes);
+    std::vector<std::vector<Handle>> hv(n_nodes);
+    std::vector<int32_t> mark, cnt;
+    int64_t leaf_off = 0;
+    for (int32_t i = 0; i < n_nodes; ++i) {
+        const ssco_expr_node& nd = nodes[i];
+        ExprCsr& P = pat[i];
+        std::vector<Handle>& H = hv[i];
+        P.rows = rows[i];
+        P.cols = cols[i];
+        if (nd.op == SSCO_EXPR_LEAF) {
+            const int64_t nnz = nd.rowptr[nd.rows];
+            P.rp.assign(nd.rowptr, nd.rowptr + nd.rows + 1);
+            P.ci.assign(nd.colind, nd.colind + nnz);
+            H.resize(nnz);
+            for (int64_t q = 0; q < nnz; ++q) H[q] = {1.0, (int32_t)(1 + leaf_off + q)};
+            leaf_off += nnz;
+        } else if (nd.op == SSCO_EXPR_SCALE) {
+            P.rp = pat[nd.a].rp;
+            P.ci = pat[nd.a].ci;
+            H = hv[nd.a];
+            for (Handle& h : H) h.c *= nd.alpha;
+        } else if (nd.op == SSCO_EXPR_TRANSPOSE) {
+            const ExprCsr& A = pat[nd.a];
+            const std::vector<Handle>& HA = hv[nd.a];
+            P.rp.assign(P.rows + 1, 0);
+            for (int32_t c : A.ci) P.rp[c + 1]++;
+            for (int32_t r = 0; r < P.rows; ++r) P.rp[r + 1] += P.rp[r];
+            P.ci.resize(A.ci.size());
+            H.resize(A.ci.size());
+            std::vector<int64_t> fill(P.rp.begin(), P.rp.end() - 1);
+            for (int32_t r = 0; r < A.rows; ++r)
+                for (int64_t q = A.rp[r]; q < A.rp[r + 1]; ++q) {
+                    const int64_t p = fill[A.ci[q]]++;
+                    P.ci[p] = r;
+                    H[p] = HA[q];
+                }
+        } else if (nd.op == SSCO_EXPR_ADD) {
+            const ExprCsr &A = pat[nd.a], &Bm = pat[nd.b];
+            const std::vector<Handle>&HA = hv[nd.a], &HB = hv[nd.b];
+            P.rp.assign(1, 0);
+            for (int32_t r = 0; r < P.rows; ++r) {
+                int64_t p = A.rp[r], q = Bm.rp[r];
+                while (p < A.rp[r + 1] || q < Bm.rp[r + 1]) {
+                    const int32_t ca = p < A.rp[r + 1] ? A.ci[p] : INT32_MAX;
+                    const int32_t cb = q < Bm.rp[r + 1] ? Bm.ci[q] : INT32_MAX;
+                    if (ca == cb) {
+                        bd.t.assign({Term{HA[p].s, 0, HA[p].c}, Term{HB[q].s, 0, HB[q].c}});
+                        H.push_back(bd.materialize());
+                        P.ci.push_back(ca);
+                        ++p, ++q;
+                    } else if (ca < cb) {
+                        H.push_back(HA[p]);
+                        P.ci.push_back(ca);
+                        ++p;
+                    } else {
+                        H.push_back(HB[q]);
+                        P.ci.push_back(cb);
+                        ++q;
+                    }
+                }
+                P.rp.push_back((int64_t)P.ci.size());
+            }
+        } else {  // MUL: entry (r, j) = sum over k of A(r, k) B(k, j)
+            const ExprCsr &A = pat[nd.a], &Bm = pat[nd.b];
+            const std::vector<Handle>&HA = hv[nd.a], &HB = hv[nd.b];
+            mark.assign(P.cols, -1);
+            cnt.assign(P.cols, 0);
+            std::vector<int32_t> jl;
+            std::vector<int64_t> off;
+            std::vector<Term> terms;
+            P.rp.assign(1, 0);
+            for (int32_t r = 0; r < P.rows; ++r) {
+                jl.clear();
+                for (int64_t p = A.rp[r]; p < A.rp[r + 1]; ++p) {
+                    const int32_t k = A.ci[p];
+                    for (int64_t q = Bm.rp[k]; q < Bm.rp[k + 1]; ++q) {
+                        const int32_t j = Bm.ci[q];
+                        if (mark[j] != r) {
+                            mark[j] = r;
+                            cnt[j] = 0;
+                            jl.push_back(j);
+                        }
+                        cnt[j]++;
+                    }
+                }
+                std::sort(jl.begin(), jl.end());
+                off.assign(jl.size() + 1, 0);
+                for (size_t x = 0; x < jl.size(); ++x) {
+                    off[x + 1] = off[x] + cnt[jl[x]];
+                    cnt[jl[x]] = (int32_t)x;  // now: the column's position in jl
+                }
+                terms.resize(off.back());
+                std::vector<int64_t> fill(off.begin(), off.end() - 1);
+                for (int64_t p = A.rp[r]; p < A.rp[r + 1]; ++p) {
+                    const int32_t k = A.ci[p];
+                    for (int64_t q = Bm.rp[k]; q < Bm.rp[k + 1]; ++q)
+                        terms[fill[cnt[Bm.ci[q]]]++] = Term{HA[p].s, HB[q].s, HA[p].c * HB[q].c};
+                }
+                for (size_t x = 0; x < jl.size(); ++x) {
+                    bd.t.assign(terms.begin() + off[x], terms.begin() + off[x + 1]);
+                    H.push_back(bd.materialize());
+                    P.ci.push_back(jl[x]);
+                }
+                P.rp.push_back((int64_t)P.ci.size());
+            }
+        }
+        if (bd.overflow) return bad(SSCO_ERR_UNSUPPORTED, "stored intermediates exceed int32 slots");
+        // release the entries of operands used for the last time
+        const int32_t ops[2] = {nd.op == SSCO_EXPR_LEAF ? -1 : nd.a,
+                                (nd.op == SSCO_EXPR_ADD || nd.op == SSCO_EXPR_MUL) ? nd.b : -1};
+        for (int32_t o : ops)
+            if (o >= 0 && last[o] == i) {
+                std::vector<Handle>().swap(hv[o]);
+                std::vector<int64_t>().swap(pat[o].rp);
+                std::vector<int32_t>().swap(pat[o].ci);
+            }
+    }
+    // level order: by level, then term count, then creation
+    const int64_t n_ops = (int64_t)bd.level.size();
+    std::vector<int32_t> order(n_ops), rank(n_ops);
+    for (int64_t i = 0; i < n_ops; ++i) order[i] = (int32_t)i;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+        return bd.level[a] != bd.level[b] ? bd.level[a] < bd.level[b] : bd.nt[a] < bd.nt[b];
+    });
+    for (int64_t r = 0; r < n_ops; ++r) rank[order[r]] = (int32_t)r;
+    const int64_t base = bd.base;
+    auto remap = [&](int32_t s) { return s >= base ? (int32_t)(base + rank[s - base]) : s; };
+    const int32_t max_level = n_ops ? bd.level[order[n_ops - 1]] : 0;
+    E.lvl_begin.assign(max_level + 1, 0);
+    for (int64_t r = 0; r < n_ops; ++r) E.lvl_begin[bd.level[order[r]]] = r + 1;
+    for (int32_t l = 1; l <= max_level; ++l) E.lvl_begin[l] = std::max(E.lvl_begin[l], E.lvl_begin[l - 1]);
+    E.term_off.assign(n_ops + 1, 0);
+    E.f1.resize(bd.pool.size());
+    E.f2.resize(bd.pool.size());
+    E.coef.resize(bd.pool.size());
+    std::vector<Term> tt;
+    for (int64_t r = 0; r < n_ops; ++r) {
+        const int32_t i = order[r];
+        tt.assign(bd.pool.begin() + bd.tbeg[i], bd.pool.begin() + bd.tbeg[i] + bd.nt[i]);
+        for (Term& x : tt) {
+            x.f1 = remap(x.f1);
+            x.f2 = remap(x.f2);
+            if (x.f1 < x.f2) std::swap(x.f1, x.f2);
+        }
+        std::sort(tt.begin(), tt.end(), [](const Term& a, const Term& b) {
+            return a.f1 != b.f1 ? a.f1 < b.f1 : a.f2 < b.f2;
+        });
+        const int64_t o = E.term_off[r];
+        for (size_t k = 0; k < tt.size(); ++k) {
+            E.f1[o + k] = tt[k].f1;
+            E.f2[o + k] = tt[k].f2;
+            E.coef[o + k] = tt[k].c;
+        }
+        E.term_off[r + 1] = o + (int64_t)tt.size();
+    }
+    E.n_ops = n_ops;
+    E.n_terms = (int64_t)bd.pool.size();
+    E.n_slots = base + n_ops;
+    E.n_unrolled = bd.n_unrolled;
+    E.unit_coef = 1;
+    for (double c : E.coef)
+        if (c != 1.0) E.unit_coef = 0;
+    E.out_slot.clear();
+    E.out_coef.clear();
+    E.out_pat.clear();
+    for (int32_t k = 0; k < n_out; ++k) {
+        const int32_t o = outputs[k];
+        E.out_pat.push_back(pat[o]);
+        for (const Handle& h : hv[o]) {
+            E.out_slot.push_back(remap(h.s));
+            E.out_coef.push_back(h.c);
+        }
+    }
+    E.n_out_vals = (int64_t)E.out_slot.size();
+    expr_layout_tables(E);
+    return SSCO_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+size_t expr_value_bytes(const ExprProgram& E) { return E.precision == SSCO_VALS_F32 ? 4 : 8; }
+
+size_t expr_workspace_bytes(const ExprProgram& E) {
+    return align256((size_t)E.n_slots * E.B * expr_value_bytes(E));
+}
+
+void expr_layout_tables(ExprProgram& E) {
+    const size_t vb = expr_value_bytes(E);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off += align256(std::max<size_t>(bytes, 16));
+        return o;
+    };
+    E.toff.term_off = take(E.term_off.size() * 8);
+    E.toff.f1 = take(E.f1.size() * 4);
+    E.toff.f2 = take(E.f2.size() * 4);
+    E.toff.coef = take(E.unit_coef ? 0 : E.coef.size() * vb);
+    E.toff.out_slot = take(E.out_slot.size() * 4);
+    E.toff.out_coef = take(E.out_coef.size() * vb);
+    E.toff.total = off;
+}
+
+std::vector<uint8_t> expr_table_image(const ExprProgram& E) {
+    std::vector<uint8_t> img(E.toff.total, 0);
+    const bool f32 = E.precision == SSCO_VALS_F32;
+    std::memcpy(img.data() + E.toff.term_off, E.term_off.data(), E.term_off.size() * 8);
+    if (!E.f1.empty()) std::memcpy(img.data() + E.toff.f1, E.f1.data(), E.f1.size() * 4);
+    if (!E.f2.empty()) std::memcpy(img.data() + E.toff.f2, E.f2.data(), E.f2.size() * 4);
+    if (!E.out_slot.empty()) std::memcpy(img.data() + E.toff.out_slot, E.out_slot.data(), E.out_slot.size() * 4);
+    auto put_vals = [&](size_t at, const std::vector<double>& v) {
+        for (size_t i = 0; i < v.size(); ++i) {
+            if (f32) {
+                const float x = (float)v[i];
+                std::memcpy(img.data() + at + 4 * i, &x, 4);
+            } else {
+                std::memcpy(img.data() + at + 8 * i, &v[i], 8);
+            }
+        }
+    };
+    if (!E.unit_coef) put_vals(E.toff.coef, E.coef);
+    put_vals(E.toff.out_coef, E.out_coef);
+    return img;
+}
+
+}  // namespace ssco
+
+using ssco::g_expr_err;
+
+extern "C" {
+
+ssco_status ssco_expr_compile(const ssco_expr_node* nodes, int32_t n_nodes, const int32_t* outputs, int32_t n_out,
+                              int32_t batch, int32_t precision, ssco_expr* out) {
+    if (!out) return ssco::bad(SSCO_ERR_INVALID_ARG, "NULL output handle");
+    *out = nullptr;
+    ssco_expr e = new (std::nothrow) ssco_expr_s();
+    if (!e) return ssco::bad(SSCO_ERR_OOM, "host allocation failed");
+    ssco_status st;
+    try {
+        st = ssco::compile(nodes, n_nodes, outputs, n_out, batch, precision, e->E);
+    } catch (const std::bad_alloc&) {
+        st = ssco::bad(SSCO_ERR_OOM, "host allocation failed while compiling");
+    }
+    if (st != SSCO_OK) {
+        delete e;
+        return st;
+    }
+    *out = e;
+    return SSCO_OK;
+}
+
+ssco_status ssco_expr_get_info(ssco_expr e, ssco_expr_info* o) {
+    if (!e || !o) return ssco::bad(SSCO_ERR_INVALID_ARG, "NULL argument");
+    const ssco::ExprProgram& E = e->E;
+    std::memset(o, 0, sizeof(*o));
+    o->n_leaf_vals = E.n_leaf_vals;
+    o->n_out_vals = E.n_out_vals;
+    o->n_slots = E.n_slots;
+    o->n_ops = E.n_ops;
+    o->n_terms = E.n_terms;
+    o->n_unrolled = E.n_unrolled;
+    o->n_levels = E.n_levels();
+    o->batch = E.B;
+    o->precision = E.precision;
+    o->unit_coef = E.unit_coef;
+    o->table_bytes = E.toff.total;
+    o->workspace_bytes = ssco::expr_workspace_bytes(E);
+    return SSCO_OK;
+}
+
+ssco_status ssco_expr_export(ssco_expr e, int32_t what, void* buf, uint64_t bytes) {
+    if (!e || !buf) return ssco::bad(SSCO_ERR_INVALID_ARG, "NULL argument");
+    const ssco::ExprProgram& E = e->E;
+    const void* src = nullptr;
+    size_t n = 0;
+    switch (what) {
+        case SSCO_EXPR_EXPORT_LEVELS: src = E.lvl_begin.data(), n = E.lvl_begin.size() * 8; break;
+        case SSCO_EXPR_EXPORT_TERM_OFF: src = E.term_off.data(), n = E.term_off.size() * 8; break;
+        case SSCO_EXPR_EXPORT_F1: src = E.f1.data(), n = E.f1.size() * 4; break;
+        case SSCO_EXPR_EXPORT_F2: src = E.f2.data(), n = E.f2.size() * 4; break;
+        case SSCO_EXPR_EXPORT_COEF: src = E.coef.data(), n = E.coef.size() * 8; break;
+        case SSCO_EXPR_EXPORT_OUT_SLOT: src = E.out_slot.data(), n = E.out_slot.size() * 4; break;
+        case SSCO_EXPR_EXPORT_OUT_COEF: src = E.out_coef.data(), n = E.out_coef.size() * 8; break;
+        default: return ssco::bad(SSCO_ERR_INVALID_ARG, "unknown export");
+    }
+    if (bytes < n) return ssco::bad(SSCO_ERR_INVALID_ARG, "export buffer too small");
+    if (n) std::memcpy(buf, src, n);
+    return SSCO_OK;
+}
+
+ssco_status ssco_expr_output_shape(ssco_expr e, int32_t k, int32_t* rows, int32_t* cols, int64_t* nnz) {
+    if (!e || k < 0 || k >= (int32_t)e->E.out_pat.size()) return ssco::bad(SSCO_ERR_INVALID_ARG, "bad output");
+    const ssco::ExprCsr& P = e->E.out_pat[k];
+    if (rows) *rows = P.rows;
+    if (cols) *cols = P.cols;
+    if (nnz) *nnz = (int64_t)P.ci.size();
+    return SSCO_OK;
+}
+
+ssco_status ssco_expr_output_pattern(ssco_expr e, int32_t k, int64_t* rowptr, int32_t* colind) {
+    if (!e || k < 0 || k >= (int32_t)e->E.out_pat.size()) return ssco::bad(SSCO_ERR_INVALID_ARG, "bad output");
+    const ssco::ExprCsr& P = e->E.out_pat[k];
+    if (rowptr) std::memcpy(rowptr, P.rp.data(), P.rp.size() * 8);
+    if (colind && !P.ci.empty()) std::memcpy(colind, P.ci.data(), P.ci.size() * 4);
+    return SSCO_OK;
+}
+
+ssco_status ssco_expr_bind(ssco_expr e, void* dev_tables, void* dev_ws, void* stream) {
+    if (!e || !dev_tables || !dev_ws) return ssco::bad(SSCO_ERR_INVALID_ARG, "NULL argument");
+    if ((reinterpret_cast<uintptr_t>(dev_tables) | reinterpret_cast<uintptr_t>(dev_ws)) & 255)
+        return ssco::bad(SSCO_ERR_INVALID_ARG, "device buffers must be 256-byte aligned");
+    ssco::ExprProgram& E = e->E;
+    const std::vector<uint8_t> img = ssco::expr_table_image(E);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(dev_tables, img.data(), img.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        E.last_error = "table upload failed";
+        return SSCO_ERR_CUDA;
+    }
+    E.d_tab = static_cast<uint8_t*>(dev_tables);
+    E.d_ws = static_cast<uint8_t*>(dev_ws);
+    E.bound = true;
+    return SSCO_OK;
+}
+
+ssco_status ssco_expr_run(ssco_expr e, const void* leaf_vals, void* out_vals, void* stream) {
+    if (!e) return ssco::bad(SSCO_ERR_INVALID_ARG, "NULL program");
+    ssco::ExprProgram& E = e->E;
+    if (!E.bound) {
+        E.last_error = "ssco_expr_bind has not run";
+        return SSCO_ERR_STATE;
+    }
+    if ((E.n_leaf_vals > 0 && !leaf_vals) || (E.n_out_vals > 0 && !out_vals)) {
+        E.last_error = "NULL values";
+        return SSCO_ERR_INVALID_ARG;
+    }
+    if (ssco::expr_launch_run(E, leaf_vals, out_vals, stream)) {
+        E.last_error = "launch failed";
+        return SSCO_ERR_CUDA;
+    }
+    return SSCO_OK;
+}
+
+const char* ssco_expr_last_error(ssco_expr e) { return e ? e->E.last_error.c_str() : g_expr_err.c_str(); }
+
+void ssco_expr_destroy(ssco_expr e) { delete e; }
+
+}  // extern "C"

@@ -397,6 +397,26 @@ def elasticity_geometry_problem(k: int, batch: int = 1, cfg: int = 6, jitter: fl
                    dof_fixed=dof_fixed)
 
 
+def laplacian_expression(p):
+    """Expression nodes (structure only) of the weighted graph Laplacian of an
+    ATWA problem, L = A^T (W A) with W = diag(w): leaves A (m x n, the
+    incidence pattern) and W (m x m diagonal); node 4 is L.  Leaf values of
+    value set b: A's entries then w_b."""
+    m, n = p.m, p.n
+    nodes = [("leaf", m, n, p.rowptr, p.colind), ("leaf", m, m, np.arange(m + 1), np.arange(m)),
+             ("transpose", 0), ("mul", 1, 0), ("mul", 2, 3)]
+    vals = np.stack([np.concatenate([p.aval, p.vals[b]]) for b in range(p.vals.shape[0])])
+    return nodes, 4, vals
+
+
+def power_expression(rows, rowptr, colind, k: int = 3):
+    """Nodes of M^k = (..(M M) M..) M for a square leaf M; the last node is M^k."""
+    nodes = [("leaf", rows, rows, rowptr, colind), ("mul", 0, 0)]
+    for _ in range(k - 2):
+        nodes.append(("mul", len(nodes) - 1, 0))
+    return nodes
+
+
 def random_spd_pattern(n: int, extra_edges: int, rng, batch: int = 1):
     """Small random graph (a spanning path plus random edges) as an
     incidence matrix with w ~ U[0.5, 2] and shift 1e-1; random permutation."""

@@ -33,6 +33,8 @@ EXPORTED_SYMBOLS = [
     "ssco_last_launch_count", "ssco_last_error", "ssco_status_string", "ssco_plan_save", "ssco_plan_load",
     "ssco_destroy", "ssco_profile_enable", "ssco_profile_read", "ssco_kernel_name", "ssco_solve_noalloc", "ssco_profile_trace", "ssco_graph_run", "ssco_autotune",
     "ssco_cotan_weights", "ssco_tet_stiffness",
+    "ssco_expr_compile", "ssco_expr_get_info", "ssco_expr_export", "ssco_expr_output_shape",
+    "ssco_expr_output_pattern", "ssco_expr_bind", "ssco_expr_run", "ssco_expr_last_error", "ssco_expr_destroy",
 ]
 KERNEL_KINDS = ["assemble", "front_small", "big_init", "big_kscatter", "big_update", "big_potrf", "big_syrk",
                 "fwd_solve", "bwd_solve", "resid", "check", "vector", "grad", "front_tiny", "big_trsm", "front_vec",
@@ -79,6 +81,21 @@ class Info(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class ExprNode(C.Structure):
+    _fields_ = [("op", C.c_int32), ("a", C.c_int32), ("b", C.c_int32), ("alpha", C.c_double),
+                ("rows", C.c_int32), ("cols", C.c_int32), ("rowptr", C.c_void_p), ("colind", C.c_void_p)]
+
+
+class ExprInfo(C.Structure):
+    _fields_ = [(k, C.c_int64) for k in ["n_leaf_vals", "n_out_vals", "n_slots", "n_ops", "n_terms",
+                                        "n_unrolled"]] + \
+              [(k, C.c_int32) for k in ["n_levels", "batch", "precision", "unit_coef"]] + \
+              [("table_bytes", C.c_uint64), ("workspace_bytes", C.c_uint64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _lib = None
 
 
@@ -118,6 +135,15 @@ def load_library(path: str = LIB_PATH):
         "ssco_profile_trace": (i32, [vp, vp, vp, vp, vp, i64, C.POINTER(i64)]),
         "ssco_graph_run": (i32, [vp, vp, i32, vp, vp, vp, vp]),
         "ssco_autotune": (i32, [vp, vp, i32, vp, vp, vp, i32, vp, C.POINTER(dbl)]),
+        "ssco_expr_compile": (i32, [C.POINTER(ExprNode), i32, vp, i32, i32, i32, C.POINTER(vp)]),
+        "ssco_expr_get_info": (i32, [vp, C.POINTER(ExprInfo)]),
+        "ssco_expr_export": (i32, [vp, i32, vp, C.c_uint64]),
+        "ssco_expr_output_shape": (i32, [vp, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i64)]),
+        "ssco_expr_output_pattern": (i32, [vp, i32, vp, vp]),
+        "ssco_expr_bind": (i32, [vp, vp, vp, vp]),
+        "ssco_expr_run": (i32, [vp, vp, vp, vp]),
+        "ssco_expr_last_error": (C.c_char_p, [vp]),
+        "ssco_expr_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -473,3 +499,124 @@ def cotan_weights(tri: torch.Tensor, tri_edge: torch.Tensor, xy: torch.Tensor, n
     if check and int(nbad.item()) > 0:
         raise SscoError(SSCO_ERR_INVALID_ARG, f"ssco_cotan_weights: {int(nbad.item())} triangles with out-of-range ids")
     return w
+
+
+# ---------------------------------------------------------------------------
+# fixed-pattern sparse matrix expressions
+# ---------------------------------------------------------------------------
+EXPR_LEAF, EXPR_ADD, EXPR_SCALE, EXPR_MUL, EXPR_TRANSPOSE = range(5)
+(EXPR_EXPORT_LEVELS, EXPR_EXPORT_TERM_OFF, EXPR_EXPORT_F1, EXPR_EXPORT_F2, EXPR_EXPORT_COEF,
+ EXPR_EXPORT_OUT_SLOT, EXPR_EXPORT_OUT_COEF) = range(7)
+
+
+class Expr:
+    """Builder of a sparse matrix expression DAG (see ssco_expr_compile in
+    ssco.h).  Every method returns a node id.
+
+        E = Expr()
+        A = E.leaf(n, n, rowptr, colind); B = E.leaf(...)
+        R = E.mul(E.add(E.scale(A, 2.0), B), E.transpose(B))
+        prog = E.compile([R], batch=4).bind()
+        out = prog.run(leaf_vals)        # [batch, n_leaf_vals] -> [batch, n_out_vals]
+    """
+
+    def __init__(self):
+        self.nodes = []      # (op, a, b, alpha, rows, cols, rowptr, colind)
+
+    def _add(self, *nd):
+        self.nodes.append(nd)
+        return len(self.nodes) - 1
+
+    def leaf(self, rows, cols, rowptr, colind):
+        return self._add(EXPR_LEAF, -1, -1, 0.0, int(rows), int(cols),
+                         np.ascontiguousarray(rowptr, np.int64), np.ascontiguousarray(colind, np.int32))
+
+    def add(self, a, b):
+        return self._add(EXPR_ADD, a, b, 0.0, 0, 0, None, None)
+
+    def scale(self, a, alpha):
+        return self._add(EXPR_SCALE, a, -1, float(alpha), 0, 0, None, None)
+
+    def mul(self, a, b):
+        return self._add(EXPR_MUL, a, b, 0.0, 0, 0, None, None)
+
+    def transpose(self, a):
+        return self._add(EXPR_TRANSPOSE, a, -1, 0.0, 0, 0, None, None)
+
+    def compile(self, outputs, batch=1, dtype=torch.float64):
+        return ExprProgram(self, list(outputs), batch, dtype)
+
+
+class ExprProgram:
+    """A compiled expression: host tables, then (after bind) device tables
+    and slot workspace owned by this object as torch tensors."""
+
+    def __init__(self, expr: Expr, outputs, batch, dtype):
+        self.L = load_library()
+        arr = (ExprNode * len(expr.nodes))()
+        for i, (op, a, b, al, r, c, rp, ci) in enumerate(expr.nodes):
+            arr[i].op, arr[i].a, arr[i].b, arr[i].alpha, arr[i].rows, arr[i].cols = op, a, b, al, r, c
+            arr[i].rowptr = rp.ctypes.data if rp is not None else None
+            arr[i].colind = ci.ctypes.data if ci is not None and ci.size else None
+        outs = np.ascontiguousarray(outputs, np.int32)
+        self.dtype = dtype
+        prec = VALS_F32 if dtype == torch.float32 else VALS_F64
+        h = C.c_void_p()
+        st = self.L.ssco_expr_compile(arr, len(expr.nodes), outs.ctypes.data, len(outs), int(batch), prec,
+                                      C.byref(h))
+        if st != SSCO_OK:
+            raise SscoError(st, self.L.ssco_expr_last_error(None).decode())
+        self._h = h
+        inf = ExprInfo()
+        self.L.ssco_expr_get_info(h, C.byref(inf))
+        self.info = inf.as_dict()
+        self.batch = int(batch)
+        self.n_out = len(outs)
+        self._tab = self._ws = None
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            self.L.ssco_expr_destroy(self._h)
+            self._h = None
+
+    def export(self, what):
+        i = self.info
+        n, dt = {EXPR_EXPORT_LEVELS: (i["n_levels"] + 1, np.int64), EXPR_EXPORT_TERM_OFF: (i["n_ops"] + 1, np.int64),
+                 EXPR_EXPORT_F1: (i["n_terms"], np.int32), EXPR_EXPORT_F2: (i["n_terms"], np.int32),
+                 EXPR_EXPORT_COEF: (i["n_terms"], np.float64), EXPR_EXPORT_OUT_SLOT: (i["n_out_vals"], np.int32),
+                 EXPR_EXPORT_OUT_COEF: (i["n_out_vals"], np.float64)}[what]
+        out = np.zeros(max(int(n), 1), dt)
+        st = self.L.ssco_expr_export(self._h, what, out.ctypes.data, out.nbytes)
+        if st != SSCO_OK:
+            raise SscoError(st, "ssco_expr_export")
+        return out[:int(n)]
+
+    def output_pattern(self, k):
+        r, c, nnz = C.c_int32(), C.c_int32(), C.c_int64()
+        self.L.ssco_expr_output_shape(self._h, k, C.byref(r), C.byref(c), C.byref(nnz))
+        rp = np.zeros(r.value + 1, np.int64)
+        ci = np.zeros(max(nnz.value, 1), np.int32)
+        self.L.ssco_expr_output_pattern(self._h, k, rp.ctypes.data, ci.ctypes.data)
+        return r.value, c.value, rp, ci[:nnz.value]
+
+    def bind(self, device="cuda", stream=None):
+        i = self.info
+        self._tab = torch.empty(max(int(i["table_bytes"]), 256), dtype=torch.uint8, device=device)
+        self._ws = torch.empty(max(int(i["workspace_bytes"]), 256), dtype=torch.uint8, device=device)
+        st = self.L.ssco_expr_bind(self._h, _ptr(self._tab), _ptr(self._ws), _stream_ptr(stream))
+        if st != SSCO_OK:
+            raise SscoError(st, "ssco_expr_bind")
+        return self
+
+    def run(self, leaf_vals: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+        """leaf_vals [batch, n_leaf_vals] -> [batch, n_out_vals] (device, program dtype)."""
+        i = self.info
+        assert leaf_vals.is_cuda and leaf_vals.dtype == self.dtype and leaf_vals.is_contiguous()
+        assert leaf_vals.numel() == self.batch * i["n_leaf_vals"]
+        if out is None:
+            out = torch.empty((self.batch, int(i["n_out_vals"])), dtype=self.dtype, device=leaf_vals.device)
+        assert out.dtype == self.dtype and out.is_contiguous() and out.numel() == self.batch * i["n_out_vals"]
+        st = self.L.ssco_expr_run(self._h, _ptr(leaf_vals), _ptr(out), _stream_ptr(stream))
+        if st != SSCO_OK:
+            raise SscoError(st, "ssco_expr_run: " + self.L.ssco_expr_last_error(self._h).decode())
+        return out

@@ -1,0 +1,231 @@
+"""Fixed-pattern sparse matrix expressions: the host compiler's tables
+(interpreted on the CPU) and the device runner (GPU) against the oracle's
+definitions; the paper's three random-matrix expressions and the cube of a
+cotangent Laplacian (Sec. 5 sparse-expression and structured-product
+experiments)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2110_12865_gb300 import problems as P
+
+
+@pytest.fixture(scope="module")
+def S():
+    from paper_2110_12865_gb300 import build
+    build.build()
+    from paper_2110_12865_gb300 import ssco
+    return ssco
+
+
+def build_expr(S, nodes):
+    """The same node tuples as the oracle, through the builder."""
+    E = S.Expr()
+    for nd in nodes:
+        if nd[0] == "leaf":
+            E.leaf(*nd[1:])
+        elif nd[0] == "add":
+            E.add(nd[1], nd[2])
+        elif nd[0] == "scale":
+            E.scale(nd[1], nd[2])
+        elif nd[0] == "mul":
+            E.mul(nd[1], nd[2])
+        else:
+            E.transpose(nd[1])
+    return E
+
+
+def interpret(S, prog, leaf_vals):
+    """Runs the exported tables on the CPU, level by level (what the device
+    runner does), in FP64; also checks that a level reads only earlier slots
+    and that its expressions are ordered by term count."""
+    i = prog.info
+    lv = prog.export(S.EXPR_EXPORT_LEVELS)
+    toff = prog.export(S.EXPR_EXPORT_TERM_OFF)
+    f1, f2 = prog.export(S.EXPR_EXPORT_F1), prog.export(S.EXPR_EXPORT_F2)
+    coef = prog.export(S.EXPR_EXPORT_COEF)
+    L, base = i["n_leaf_vals"], 1 + i["n_leaf_vals"]
+    B = leaf_vals.shape[0]
+    slots = np.zeros((i["n_slots"], B))
+    slots[0] = 1.0
+    slots[1:1 + L] = leaf_vals.T
+    for l in range(1, i["n_levels"] + 1):
+        a, b = lv[l - 1], lv[l]
+        q0, q1 = toff[a], toff[b]
+        assert f1[q0:q1].max() < base + a and f2[q0:q1].max() < base + a   # only earlier slots
+        assert np.all(f1[q0:q1] >= f2[q0:q1])
+        counts = np.diff(toff[a:b + 1])
+        assert np.all(np.diff(counts) >= 0)
+        seg = np.repeat(np.arange(b - a), counts)
+        acc = np.zeros((b - a, B))
+        np.add.at(acc, seg, coef[q0:q1, None] * slots[f1[q0:q1]] * slots[f2[q0:q1]])
+        slots[base + a: base + b] = acc
+    os_, oc = prog.export(S.EXPR_EXPORT_OUT_SLOT), prog.export(S.EXPR_EXPORT_OUT_COEF)
+    return (oc[:, None] * slots[os_]).T
+
+
+def check_outputs(S, prog, nodes, outs, vals, got, rel):
+    """Output patterns equal the oracle's structural patterns; values within
+    rel x the absolute-value evaluation (the rounding scale)."""
+    evals = [(O.expr_eval(nodes, vals[b], outs), O.expr_eval(nodes, vals[b], outs, absolute=True))
+             for b in range(vals.shape[0])]
+    col = 0
+    for k in range(len(outs)):
+        r, c, rp, ci = prog.output_pattern(k)
+        nnz = int(rp[-1])
+        keys = [(i, int(j)) for i in range(r) for j in ci[rp[i]:rp[i + 1]]]
+        for b, (res, res_abs) in enumerate(evals):
+            d, da = res[k][2], res_abs[k][2]
+            assert keys == sorted(d), "pattern"
+            ref = np.array([d[key] for key in keys])
+            bound = np.array([da[key] for key in keys])
+            assert np.all(np.abs(got[b, col:col + nnz] - ref) <= rel * bound + 1e-300)
+        col += nnz
+
+
+def random_expressions(n, seed, per_row=6):
+    from tests.test_oracle_pins import paper_expressions
+    return paper_expressions(n, np.random.default_rng(seed), per_row)
+
+
+def cotan_laplacian_cube(p):
+    """L = A^T (W A) from a triangulated grid's incidence matrix A and
+    cotangent weights W = diag(w), then L^3, in one DAG; outputs L^3 and L."""
+    nodes, l_id, _ = P.laplacian_expression(p)
+    nodes = nodes + [("mul", l_id, l_id), ("mul", l_id + 1, l_id)]
+    return nodes, [l_id + 2, l_id]
+
+
+def cotan_leaf_vals(p, B):
+    return P.laplacian_expression(p)[2][:B]
+
+
+# ---------------------------------------------------------------------------
+# host compiler (CPU)
+# ---------------------------------------------------------------------------
+def test_compiled_tables_match_oracle_random_expressions(S):
+    nodes, outs, nv = random_expressions(60, 61)
+    prog = build_expr(S, nodes).compile(outs, batch=3)
+    vals = np.random.default_rng(62).standard_normal((3, nv))
+    check_outputs(S, prog, nodes, outs, vals, interpret(S, prog, vals), 1e-13)
+
+
+def test_compiled_tables_match_oracle_cotan_laplacian_cube(S):
+    p = P.trigrid_problem(10, batch=2, cfg=3)
+    nodes, outs = cotan_laplacian_cube(p)
+    prog = build_expr(S, nodes).compile(outs, batch=2)
+    vals = cotan_leaf_vals(p, 2)
+    check_outputs(S, prog, nodes, outs, vals, interpret(S, prog, vals), 1e-13)
+    assert prog.info["n_levels"] == 4   # W A, L, L^2, L^3: one level per product in the chain
+
+
+def test_structural_hashing_merges_equal_expressions(S):
+    """A B built twice is stored once; (A B) + (A B) and A + A become scaled
+    relabellings (no new expression); A A^T stores each unordered pair of
+    rows once, so only its lower triangle (with the diagonal) is computed."""
+    rng = np.random.default_rng(63)
+    from tests.test_oracle_pins import _rand_csr
+    n = 50
+    A = ("leaf", n, n, *_rand_csr(rng, n, n, 4))
+    Bm = ("leaf", n, n, *_rand_csr(rng, n, n, 4))
+    one = build_expr(S, [A, Bm, ("mul", 0, 1)]).compile([2])
+    two = build_expr(S, [A, Bm, ("mul", 0, 1), ("mul", 0, 1), ("add", 2, 3), ("add", 0, 0)]).compile([4, 5])
+    assert two.info["n_ops"] == one.info["n_ops"]
+    oc = two.export(S.EXPR_EXPORT_OUT_COEF)
+    assert np.all(oc == 2.0)
+    aat = build_expr(S, [A, ("transpose", 0), ("mul", 0, 1)]).compile([2])
+    r, c, rp, ci = aat.output_pattern(0)
+    lower = sum(int(np.sum(ci[rp[i]:rp[i + 1]] <= i)) for i in range(r))
+    assert aat.info["n_ops"] == lower and aat.info["n_unrolled"] == int(rp[-1])
+    vals = rng.standard_normal((1, int(A[3][-1])))
+    check_outputs(S, aat, [A, ("transpose", 0), ("mul", 0, 1)], [2], vals, interpret(S, aat, vals), 1e-13)
+
+
+def test_expr_compile_rejects_malformed_nodes(S):
+    rp, ci = np.array([0, 2, 3]), np.array([0, 1, 1])
+    ok = ("leaf", 2, 2, rp, ci)
+    cases = [
+        ([("leaf", 2, 2, rp, np.array([1, 0, 1]))], [0], 2),          # columns not increasing
+        ([("leaf", 2, 2, rp, np.array([0, 2, 1]))], [0], 2),          # column out of range
+        ([ok, ("leaf", 3, 2, np.array([0, 1, 2, 3]), np.array([0, 1, 0])), ("add", 0, 1)], [2], 1),  # shapes
+        ([ok, ("leaf", 3, 2, np.array([0, 1, 2, 3]), np.array([0, 1, 0])), ("mul", 0, 1)], [2], 1),
+        ([ok, ("scale", 0, float("nan"))], [1], 4),
+        ([ok], [1], 1),                                                # output id out of range
+    ]
+    for nodes, outs, status in cases:
+        with pytest.raises(S.SscoError) as ei:
+            build_expr(S, nodes).compile(outs)
+        assert ei.value.status == status, nodes
+    with pytest.raises(S.SscoError):
+        build_expr(S, [ok]).compile([0], batch=0)
+
+
+# ---------------------------------------------------------------------------
+# device runner (GPU)
+# ---------------------------------------------------------------------------
+@pytest.mark.gpu
+@pytest.mark.parametrize("dtype,B", [(torch.float64, 1), (torch.float64, 40), (torch.float32, 3)])
+def test_expr_random_expressions_on_device(S, dtype, B):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    nodes, outs, nv = random_expressions(1000, 64 + B)
+    prog = build_expr(S, nodes).compile(outs, batch=B, dtype=dtype).bind()
+    vals = np.random.default_rng(65).standard_normal((B, nv))
+    if dtype == torch.float32:
+        vals = vals.astype(np.float32).astype(np.float64)   # the oracle sees the same inputs
+    got = prog.run(torch.tensor(vals, dtype=dtype, device="cuda")).double().cpu().numpy()
+    sel = [0, B - 1] if B > 2 else list(range(B))
+    check_outputs(S, prog, nodes, outs, vals[sel], got[sel], 1e-13 if dtype == torch.float64 else 3e-5)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_expr_cotan_laplacian_cube_on_device(S, dtype):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    p = P.trigrid_problem(24, batch=8, cfg=3)
+    nodes, outs = cotan_laplacian_cube(p)
+    prog = build_expr(S, nodes).compile(outs, batch=8, dtype=dtype).bind()
+    vals = cotan_leaf_vals(p, 8)
+    if dtype == torch.float32:
+        vals = vals.astype(np.float32).astype(np.float64)
+    got = prog.run(torch.tensor(vals, dtype=dtype, device="cuda")).double().cpu().numpy()
+    check_outputs(S, prog, nodes, outs, vals[[0, 7]], got[[0, 7]], 1e-13 if dtype == torch.float64 else 3e-5)
+
+
+@pytest.mark.gpu
+def test_full_cotan_laplacian_cube_200k_sampled_rows(S):
+    """L^3 of the cotangent Laplacian of a 448 x 448 triangulated grid
+    (200,704 vertices; the paper's largest structured product), FP32, one
+    value set, in the bench's form: a first program builds L = A^T (W A) on
+    the device, the timed program takes L as its leaf and forms (L L) L.
+    Sampled rows against the oracle's lazy row evaluation of the whole chain
+    from A and w, and the zero row sums that every Laplacian power has."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    p = P.trigrid_problem(448, batch=1, cfg=3)
+    lnodes, l_id, lvals = P.laplacian_expression(p)
+    lvals = lvals[:1].astype(np.float32).astype(np.float64)
+    lprog = build_expr(S, lnodes).compile([l_id], batch=1, dtype=torch.float32).bind()
+    Ld = lprog.run(torch.tensor(lvals, dtype=torch.float32, device="cuda"))
+    n, _, lrp, lci = lprog.output_pattern(0)
+    cube = P.power_expression(n, lrp, lci, 3)
+    prog = build_expr(S, cube).compile([len(cube) - 1], batch=1, dtype=torch.float32).bind()
+    got = prog.run(Ld).double().cpu().numpy()[0]
+    nodes, outs = cotan_laplacian_cube(p)
+    vals = lvals
+    r, c, rp, ci = prog.output_pattern(0)
+    rows = np.random.default_rng(66).choice(r, 200, replace=False)
+    ref = O.expr_eval_rows(nodes, vals[0], outs[0], rows)
+    absvals = np.abs(vals[0])
+    ref_abs = O.expr_eval_rows(nodes, absvals, outs[0], rows)
+    for i in rows:
+        cols = ci[rp[i]:rp[i + 1]]
+        assert list(cols) == sorted(ref[i])
+        want = np.array([ref[i][j] for j in cols])
+        scale = np.array([ref_abs[i][j] for j in cols])
+        assert np.all(np.abs(got[rp[i]:rp[i + 1]] - want) <= 3e-5 * scale)
+    rs = np.add.reduceat(got, rp[:-1]) if got.size else got
+    ra = np.add.reduceat(np.abs(got), rp[:-1])
+    assert np.all(np.abs(rs) <= 1e-4 * ra)
