@@ -55,7 +55,7 @@ def parse():
                     help="value sets of the main pattern (default: the workload's own; smaller only for profiling)")
     a = ap.parse_args()
     if a.steps is None:
-        a.steps = {"elast24": 20, "elast48": 5, "lll": 20}.get(a.workload, 100)
+        a.steps = {"elast24": 20, "elast48": 5, "lll": 2000}.get(a.workload, 100)
     return a
 
 
