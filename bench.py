@@ -648,6 +648,21 @@ PAPER_L3_MS = {10000: {"ours_vega20": 0.344, "ours_gtx1080": 0.326, "rocsparse_v
                200000: {"ours_vega20": 2.300, "ours_gtx1080": 8.629, "rocsparse_vega20": 3.676}}
 
 
+def expr_traffic():
+    """DRAM bytes of one 200k-vertex evaluation from the one-pass ncu capture
+    (profiles/traffic_expr.json), while the runner source is unchanged."""
+    import hashlib
+    here = os.path.dirname(os.path.abspath(__file__))
+    try:
+        rec = json.load(open(os.path.join(here, "profiles", "traffic_expr.json")))
+        src = os.path.join(here, "paper_2110_12865_gb300", "csrc", "ssco_expr_run.cu")
+        if rec["source_sha256"] == hashlib.sha256(open(src, "rb").read()).hexdigest():
+            return rec["dram_bytes_per_evaluation"]
+    except (OSError, ValueError, KeyError):
+        pass
+    return None
+
+
 def run_expr(args):
     import torch
     from paper_2110_12865_gb300 import build
@@ -718,7 +733,7 @@ def run_expr(args):
                        "api": "ssco_expr_run (4 launches: constant slot, 2 levels, output gather)"},
             "gpu_launches": 4 * args.steps,
             "roofline": {"bound": "hbm", "achieved": top["GBps"], "peak": hbm, "unit": "GB/s",
-                         "frac": top["GBps"] / hbm, "traffic": None,
+                         "frac": top["GBps"] / hbm, "traffic": expr_traffic(),
                          "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback"},
             "sizes": sizes, "clocks": clocks}
 

@@ -13,6 +13,13 @@
         the capture was taken on; bench.py reports it as `roofline.traffic`
         only while that source is unchanged.
 
+    python profile_summary.py expr-traffic LOG.csv
+        DRAM bytes of one sparse-expression evaluation: the last evaluation's
+        launches (k_expr_one .. k_expr_out*) of a `bench.py --workload lll`
+        capture, written to profiles/traffic_expr.json with the sha256 of the
+        expression runner's source; the lll bench reports it as
+        `roofline.traffic` while that source is unchanged.
+
 Kernel names are matched to library kinds by their `k_<name>` stem.
 """
 import collections
@@ -103,10 +110,33 @@ def traffic(path, kinds):
     print(json.dumps(out, indent=1))
 
 
+EXPR_SOURCE = os.path.join(ROOT, "paper_2110_12865_gb300", "csrc", "ssco_expr_run.cu")
+
+
+def expr_traffic(path):
+    per = collections.OrderedDict()
+    for d in read_rows(path):
+        st = stem(d["Kernel Name"])
+        if not st.startswith("k_expr") or d.get("Metric Name") not in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            continue
+        per.setdefault((int(d["ID"]), st), 0.0)
+        per[(int(d["ID"]), st)] += value(d, {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9})
+    launches = list(per.items())
+    starts = [i for i, ((_, st), _) in enumerate(launches) if st == "k_expr_one"]
+    last = launches[starts[-1]:]
+    out = {"source_sha256": hashlib.sha256(open(EXPR_SOURCE, "rb").read()).hexdigest(),
+           "dram_bytes_per_evaluation": sum(b for _, b in last), "launches": [st for (_, st), _ in last],
+           "capture": os.path.basename(path)}
+    json.dump(out, open(os.path.join(ROOT, "profiles", "traffic_expr.json"), "w"), indent=1)
+    print(json.dumps(out, indent=1))
+
+
 if __name__ == "__main__":
     if sys.argv[1] == "launches":
         launches(sys.argv[2])
     elif sys.argv[1] == "traffic":
         traffic(sys.argv[2], sys.argv[3:])
+    elif sys.argv[1] == "expr-traffic":
+        expr_traffic(sys.argv[2])
     else:
         raise SystemExit(__doc__)
