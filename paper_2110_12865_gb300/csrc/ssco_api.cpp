@@ -124,10 +124,14 @@ struct Reader {
     template <class T>
     bool vec(std::vector<T>& v) {
         uint64_t n = 0;
-        if (!pod(n) || n > (1ull << 40)) return false;
+        if (!pod(n)) return false;
+        // a length that the rest of the file cannot hold is damage, not a size
+        const std::streamoff here = f.tellg();
+        if (here < 0 || n > (uint64_t)(size - here) / sizeof(T)) return false;
         v.resize(n);
         return n == 0 || raw(v.data(), n * sizeof(T));
     }
+    std::streamoff size = 0;
 };
 
 template <class IO>
@@ -190,6 +194,9 @@ ssco_status ssco_analyze(const ssco_pattern* const* pats, int32_t n_pats, const 
     } catch (const std::bad_alloc&) {
         s = SSCO_ERR_OOM;
         h->P.last_error = "host allocation failed during analysis";
+    } catch (const std::exception& ex) {
+        s = SSCO_ERR_UNSUPPORTED;
+        h->P.last_error = std::string("analysis failed: ") + ex.what();
     }
     if (s != SSCO_OK) {
         g_err = h->P.last_error;
@@ -558,15 +565,22 @@ ssco_status ssco_plan_load(const char* path, ssco_plan* out) {
     if (!path || !out) return fail(nullptr, SSCO_ERR_INVALID_ARG, "NULL argument");
     *out = nullptr;
     Reader r;
-    r.f.open(path, std::ios::binary);
+    r.f.open(path, std::ios::binary | std::ios::ate);
     if (!r.f) return fail(nullptr, SSCO_ERR_INVALID_ARG, std::string("cannot open ") + path);
+    r.size = r.f.tellg();
+    r.f.seekg(0);
     uint64_t magic = 0;
     uint32_t ver = 0;
     if (!r.pod(magic) || !r.pod(ver) || magic != kMagic || ver != kVersion)
         return fail(nullptr, SSCO_ERR_INVALID_ARG, "not a plan file of this version");
     ssco_plan h = new (std::nothrow) ssco_plan_s();
     if (!h) return fail(nullptr, SSCO_ERR_OOM, "host allocation failed");
-    bool ok = serialize(r, h->P);
+    bool ok = false;
+    try {  // a damaged length field must not take the process down
+        ok = serialize(r, h->P);
+    } catch (const std::exception&) {
+        ok = false;
+    }
     const uint64_t got = r.sum.h;
     uint64_t digest = 0;
     char extra = 0;

@@ -459,6 +459,8 @@ ssco_status ssco_expr_compile(const ssco_expr_node* nodes, int32_t n_nodes, cons
         st = ssco::compile(nodes, n_nodes, outputs, n_out, batch, precision, e->E);
     } catch (const std::bad_alloc&) {
         st = ssco::bad(SSCO_ERR_OOM, "host allocation failed while compiling");
+    } catch (const std::exception& ex) {
+        st = ssco::bad(SSCO_ERR_UNSUPPORTED, std::string("compile failed: ") + ex.what());
     }
     if (st != SSCO_OK) {
         delete e;

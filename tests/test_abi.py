@@ -182,6 +182,9 @@ def test_plan_save_load_roundtrip(S, tmp_path):
            raw[:len(raw) // 2] + bytes([raw[len(raw) // 2] ^ 0x10]) + raw[len(raw) // 2 + 1:],  # a table byte
            raw[:-1],                                                    # truncated digest
            raw + b"\0"]                                                 # trailing byte
+    # 8 bytes of 0xff over each early field (counts and lengths included):
+    # refused, never a huge allocation or a crash
+    bad += [raw[:o] + b"\xff" * 8 + raw[o + 8:] for o in range(12, 400, 4)]
     for i, blob in enumerate(bad):
         g = str(tmp_path / f"bad{i}.bin")
         open(g, "wb").write(blob)

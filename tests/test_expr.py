@@ -142,6 +142,41 @@ def test_structural_hashing_merges_equal_expressions(S):
     check_outputs(S, aat, [A, ("transpose", 0), ("mul", 0, 1)], [2], vals, interpret(S, aat, vals), 1e-13)
 
 
+def test_compiled_tables_edge_cases(S):
+    """Empty rows and an empty leaf, rectangular chains, a double transpose,
+    a zero scale, exact cancellation A + (-1)A, a leaf and a repeated node as
+    outputs, and a deep power chain: tables against the oracle, structure
+    included."""
+    rng = np.random.default_rng(67)
+    from tests.test_oracle_pins import _rand_csr
+    rp, ci = _rand_csr(rng, 7, 5, 2)
+    rp[3:] -= rp[3] - rp[2]                                  # row 2 left empty
+    ci = np.delete(ci, np.s_[2 * 2:2 * 3])
+    A = ("leaf", 7, 5, rp, ci)                                # 7 x 5 with an empty row
+    Bm = ("leaf", 5, 3, *_rand_csr(rng, 5, 3, 2))             # 5 x 3
+    Z = ("leaf", 3, 3, np.zeros(4, np.int64), np.zeros(0, np.int32))   # no entries
+    Sq = ("leaf", 6, 6, *_rand_csr(rng, 6, 6, 2))
+    nodes = [A, Bm, Z, Sq,
+             ("mul", 0, 1),                 # 4: 7 x 3
+             ("transpose", 4), ("transpose", 5),   # 5, 6: (AB)^T, ((AB)^T)^T
+             ("mul", 6, 2),                 # 7: (AB) Z -> no entries
+             ("scale", 4, 0.0),             # 8: zero scale
+             ("scale", 0, -1.0), ("add", 0, 9),    # 9, 10: A - A
+             ("mul", 3, 3), ("mul", 11, 3), ("mul", 12, 3), ("mul", 13, 3), ("mul", 14, 3)]   # 11..15: Sq^2..Sq^6
+    outs = [6, 7, 8, 10, 0, 15, 6]
+    prog = build_expr(S, nodes).compile(outs, batch=2)
+    nv = sum(int(nd[3][-1]) for nd in nodes if nd[0] == "leaf")
+    vals = rng.standard_normal((2, nv))
+    got = interpret(S, prog, vals)
+    check_outputs(S, prog, nodes, outs, vals, got, 1e-13)
+    assert prog.info["n_levels"] == 5                        # Sq^2 .. Sq^6
+    r, c, rp7, _ = prog.output_pattern(1)
+    assert (r, c, int(rp7[-1])) == (7, 3, 0)
+    sizes = [int(prog.output_pattern(k)[2][-1]) for k in range(len(outs))]
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    assert np.all(got[:, off[2]:off[4]] == 0.0)              # zero scale and A - A: exactly 0
+
+
 def test_expr_compile_rejects_malformed_nodes(S):
     rp, ci = np.array([0, 2, 3]), np.array([0, 1, 1])
     ok = ("leaf", 2, 2, rp, ci)
