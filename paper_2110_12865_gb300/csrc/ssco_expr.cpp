@@ -35,10 +35,14 @@ struct Term {
     double c;
 };
 
-uint64_t fnv(uint64_t h, const void* p, size_t n) {
-    const unsigned char* b = static_cast<const unsigned char*>(p);
-    for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 0x100000001b3ull;
-    return h;
+// 64-bit mixing step (the finalizer of splitmix64) folded over the terms
+uint64_t mix(uint64_t h, uint64_t x) {
+    h ^= x + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
+    h ^= h >> 30;
+    h *= 0xbf58476d1ce4e5b9ull;
+    h ^= h >> 27;
+    h *= 0x94d049bb133111ebull;
+    return h ^ (h >> 31);
 }
 
 // Scalar expressions under construction, merged by structural hashing.
@@ -48,7 +52,9 @@ struct Builder {
     std::vector<int64_t> tbeg;
     std::vector<uint64_t> hash;
     std::vector<Term> pool;
-    std::vector<int32_t> table;  // open addressing: expression index + 1, 0 = empty
+    // open addressing: (expression index + 1, high hash bits); index 0 = empty
+    std::vector<uint64_t> table;
+    static uint64_t slot_of(int64_t i, uint64_t h) { return (uint64_t)(i + 1) | (h & 0xffffffff00000000ull); }
     int64_t n_unrolled = 0;
     bool overflow = false;
     std::vector<Term> t;  // the expression being built
@@ -60,7 +66,7 @@ struct Builder {
         for (size_t i = 0; i < level.size(); ++i) {
             size_t p = hash[i] & (cap - 1);
             while (table[p]) p = (p + 1) & (cap - 1);
-            table[p] = (int32_t)i + 1;
+            table[p] = slot_of((int64_t)i, hash[i]);
         }
     }
 
@@ -70,31 +76,33 @@ struct Builder {
         ++n_unrolled;
         for (Term& x : t)
             if (x.f1 < x.f2) std::swap(x.f1, x.f2);
-        std::sort(t.begin(), t.end(), [](const Term& a, const Term& b) {
-            return a.f1 != b.f1 ? a.f1 < b.f1 : a.f2 < b.f2;
-        });
-        size_t w = 0;
-        for (size_t r = 0; r < t.size(); ++r) {
-            if (w > 0 && t[w - 1].f1 == t[r].f1 && t[w - 1].f2 == t[r].f2)
-                t[w - 1].c += t[r].c;  // equal factor pairs: one product
-            else
-                t[w++] = t[r];
+        if (t.size() > 1) {
+            std::sort(t.begin(), t.end(), [](const Term& a, const Term& b) {
+                return a.f1 != b.f1 ? a.f1 < b.f1 : a.f2 < b.f2;
+            });
+            size_t w = 0;
+            for (size_t r = 0; r < t.size(); ++r) {
+                if (w > 0 && t[w - 1].f1 == t[r].f1 && t[w - 1].f2 == t[r].f2)
+                    t[w - 1].c += t[r].c;  // equal factor pairs: one product
+                else
+                    t[w++] = t[r];
+            }
+            t.resize(w);
         }
-        t.resize(w);
         t.erase(std::remove_if(t.begin(), t.end(), [](const Term& x) { return x.c == 0.0; }), t.end());
         if (t.empty()) return {0.0, 0};
         if (t.size() == 1 && t[0].f2 == 0) return {t[0].c, t[0].f1};
-        uint64_t h = 0xcbf29ce484222325ull;
+        uint64_t h = 0;
         for (const Term& x : t) {
-            h = fnv(h, &x.f1, 4);
-            h = fnv(h, &x.f2, 4);
-            h = fnv(h, &x.c, 8);
+            uint64_t cb;
+            std::memcpy(&cb, &x.c, 8);
+            h = mix(mix(h, ((uint64_t)(uint32_t)x.f1 << 32) | (uint32_t)x.f2), cb);
         }
         if (table.empty()) rehash(1 << 16);
         size_t cap = table.size(), p = h & (cap - 1);
         while (table[p]) {
-            const int32_t i = table[p] - 1;
-            if (hash[i] == h && nt[i] == (int32_t)t.size()) {
+            const int32_t i = (int32_t)(table[p] & 0xffffffffull) - 1;
+            if ((table[p] >> 32) == (h >> 32) && hash[i] == h && nt[i] == (int32_t)t.size()) {
                 const Term* q = pool.data() + tbeg[i];
                 bool same = true;
                 for (size_t k = 0; k < t.size() && same; ++k)
@@ -115,7 +123,7 @@ struct Builder {
         tbeg.push_back((int64_t)pool.size());
         hash.push_back(h);
         pool.insert(pool.end(), t.begin(), t.end());
-        table[p] = (int32_t)idx + 1;
+        table[p] = slot_of(idx, h);
         if (2 * level.size() > cap) rehash(cap * 2);
         return {1.0, (int32_t)(base + idx)};
     }
@@ -332,13 +340,26 @@ ssco_status compile(const ssco_expr_node* nodes, int32_t n_nodes, const int32_t*
                 std::vector<int32_t>().swap(pat[o].ci);
             }
     }
-    // level order: by level, then term count, then creation
+    // level order: by level, then term count, then creation (two stable
+    // counting passes: term count, then level)
     const int64_t n_ops = (int64_t)bd.level.size();
-    std::vector<int32_t> order(n_ops), rank(n_ops);
-    for (int64_t i = 0; i < n_ops; ++i) order[i] = (int32_t)i;
-    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
-        return bd.level[a] != bd.level[b] ? bd.level[a] < bd.level[b] : bd.nt[a] < bd.nt[b];
-    });
+    std::vector<int32_t> order(n_ops), rank(n_ops), tmp(n_ops);
+    {
+        int32_t max_nt = 0, max_lv = 0;
+        for (int64_t i = 0; i < n_ops; ++i) {
+            max_nt = std::max(max_nt, bd.nt[i]);
+            max_lv = std::max(max_lv, bd.level[i]);
+        }
+        std::vector<int64_t> cnt((size_t)std::max(max_nt, max_lv) + 2, 0);
+        for (int64_t i = 0; i < n_ops; ++i) cnt[bd.nt[i] + 1]++;
+        for (size_t k = 1; k < cnt.size(); ++k) cnt[k] += cnt[k - 1];
+        for (int64_t i = 0; i < n_ops; ++i) tmp[cnt[bd.nt[i]]++] = (int32_t)i;
+        std::fill(cnt.begin(), cnt.end(), 0);
+        for (int64_t i = 0; i < n_ops; ++i) cnt[bd.level[i] + 1]++;
+        for (size_t k = 1; k < cnt.size(); ++k) cnt[k] += cnt[k - 1];
+        for (int64_t r = 0; r < n_ops; ++r) order[cnt[bd.level[tmp[r]]]++] = tmp[r];
+    }
+    std::vector<int32_t>().swap(tmp);
     for (int64_t r = 0; r < n_ops; ++r) rank[order[r]] = (int32_t)r;
     const int64_t base = bd.base;
     auto remap = [&](int32_t s) { return s >= base ? (int32_t)(base + rank[s - base]) : s; };
