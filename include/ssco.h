@@ -373,9 +373,10 @@ ssco_status ssco_tet_stiffness(const int32_t* tets, int64_t n_tet, int64_t n_nod
  * Every entry of an ADD present in both operands and every entry of a MUL
  * is stored once as an intermediate (a global intermediate in the paper's
  * terms); scaling and transposition only relabel entries.  The products of
- * a MUL entry are summed in ascending (k, j) order of generation after
- * merging equal factor pairs; values are float or double (`precision` =
- * SSCO_VALS_F64 / SSCO_VALS_F32) and accumulate in that type.
+ * an entry are summed in ascending order of their factor slots, after equal
+ * factor pairs are merged (coefficients added) and zero coefficients
+ * dropped; values are float or double (`precision` = SSCO_VALS_F64 /
+ * SSCO_VALS_F32) and accumulate in that type.
  * Leaf values per set are the leaves' nnz concatenated in node order
  * ([batch][n_leaf_vals]); outputs likewise ([batch][n_out_vals], in the
  * order of `outputs`, each in its CSR order). */
