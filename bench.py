@@ -114,6 +114,35 @@ def stacked_inputs(item, B):
     return np.ascontiguousarray(vals), np.ascontiguousarray(shift), np.ascontiguousarray(b)
 
 
+def shared_plans(work, precision, rank, world, dist, S):
+    """The plans of a step, analyzed once per job: with several ranks, rank 0
+    runs the host symbolic phase and writes each plan file (ssco_plan_save),
+    the other ranks load it (ssco_plan_load) after a barrier.  Every rank
+    solves the same patterns for its own value sets, so the plans are equal;
+    nothing of the data path is exchanged."""
+    if world == 1 or dist is None:
+        return [S.Plan(item, precision=precision, batch=Bt) for item, Bt in work]
+    import tempfile
+    box = [tempfile.mkdtemp(prefix="ssco_plans_") if rank == 0 else None]
+    dist.broadcast_object_list(box, src=0)
+    paths = [os.path.join(box[0], f"plan{k}_p{precision}.bin") for k in range(len(work))]
+    plans = []
+    if rank == 0:
+        for (item, Bt), path in zip(work, paths):
+            pl = S.Plan(item, precision=precision, batch=Bt)
+            pl.save(path)
+            plans.append(pl)
+    dist.barrier()
+    if rank != 0:
+        plans = [S.Plan.load(path, precision=precision) for path in paths]
+    dist.barrier()   # every rank has read the files
+    if rank == 0:
+        for path in paths:
+            os.remove(path)
+        os.rmdir(box[0])
+    return plans
+
+
 def units_of(work):
     return sum(B * len(probs_of(item)) for item, B in work)
 
@@ -236,8 +265,8 @@ def run_ours(args, rank, world, local_rank):
 
     def setup(precision):
         plans, dev_in, host_in = [], [], []
-        for item, Bt in work:
-            pl = S.Plan(item, precision=precision, batch=Bt).bind(dev)
+        for (item, Bt), pl in zip(work, shared_plans(work, precision, rank, world, dist, S)):
+            pl.bind(dev)
             v, s, b = stacked_inputs(item, Bt)
             dev_in.append((torch.tensor(v, device=dev), torch.tensor(s, device=dev), torch.tensor(b, device=dev),
                            torch.empty(b.shape, dtype=torch.float64, device=dev)))

@@ -4,7 +4,8 @@ Value sets are independent, so the GPU path shards by instance with no
 collective in the data path; what needs checking is the host logic: every
 rank builds its own value sets (distinct seeds, identical to what a single
 process builds for that rank), each rank's systems solve correctly, and the
-whole-job throughput uses the slowest rank's time."""
+whole-job throughput uses the slowest rank's time; the plan is analyzed
+once, on rank 0, and reaches the other ranks through its file."""
 import os
 import socket
 
@@ -37,15 +38,22 @@ def _worker(rank, world, port, out):
         res.append(np.linalg.norm(O.symv(r.K, r.x) - p.b[i]) / np.linalg.norm(p.b[i]))
     local_ms = 10.0 * (rank + 1)
     value, max_ms = bench.aggregate_value(B, 4, local_ms, dist)
+    # the plan is analyzed once (rank 0) and replicated through its file
+    from paper_2110_12865_gb300 import ssco as S
+    pl, = bench.shared_plans(work, S.FP32_REFINE, rank, world, dist, S)
+    own = S.Plan(p, precision=S.FP32_REFINE, batch=B)
+    same_plan = pl.info == own.info and all(np.array_equal(pl.export(k), own.export(k)) for k in range(15))
     w = torch.tensor(p.vals[0][:8].copy())
     gathered = [torch.zeros_like(w) for _ in range(world)]
     dist.all_gather(gathered, w)
-    out[rank] = {"value": value, "max_ms": max_ms, "res": max(res),
+    out[rank] = {"value": value, "max_ms": max_ms, "res": max(res), "same_plan": same_plan,
                  "first_vals": [g.numpy().tolist() for g in gathered]}
     dist.destroy_process_group()
 
 
 def test_two_gloo_ranks_weak_scaling():
+    from paper_2110_12865_gb300 import build
+    build.build()
     world = 2
     port = _free_port()
     with mp.Manager() as m:
@@ -58,6 +66,7 @@ def test_two_gloo_ranks_weak_scaling():
         assert o["max_ms"] == 20.0                       # the slowest rank's time
         assert abs(o["value"] - 3 * world * 4 / 0.020) < 1e-9
         assert o["res"] < 1e-12
+        assert o["same_plan"]                             # the replicated plan is the analyzed one
         work, _ = bench.make_workload("tiny", rank)       # same data as a single process builds
         assert np.allclose(out[0]["first_vals"][rank], work[0][0].vals[0][:8])
     assert not np.allclose(out[0]["first_vals"][0], out[0]["first_vals"][1])  # distinct value sets
