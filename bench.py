@@ -644,7 +644,10 @@ def time_oracle_all_cores(items):
     import multiprocessing as mp
     ctx = mp.get_context("spawn")     # safe after CUDA initialisation
     cores = len(os.sched_getaffinity(0))
-    systems = sorted((_one_system(p, i) for p, i in items), key=lambda q: -q["n"])
+    uniq = {}   # one copy per distinct system: repeats pickle as references
+    for p, i in items:
+        uniq.setdefault((id(p), i), _one_system(p, i))
+    systems = sorted((uniq[(id(p), i)] for p, i in items), key=lambda q: -q["n"])
     chunks, loads = [[] for _ in range(min(cores, len(systems)))], [0.0] * min(cores, len(systems))
     for q in systems:
         j = int(np.argmin(loads))
