@@ -365,7 +365,11 @@ ssco_status ssco_tet_stiffness(const int32_t* tets, int64_t n_tet, int64_t n_nod
  * Node ids are positions in the node array; operands must come earlier.
  *   LEAF       a rows x cols CSR pattern (rowptr[rows+1] int64, colind
  *              int32 strictly increasing within each row); its values are
- *              supplied per call.
+ *              supplied per call.  With vmap (int64 [nnz], values in
+ *              [0, n_vals)) entry q takes the leaf's value vmap[q], so
+ *              entries may share one value (a symmetric matrix stored once);
+ *              the leaf then supplies n_vals values.  NULL vmap: one value
+ *              per entry.
  *   ADD        a + b (same shape; pattern = union).
  *   SCALE      alpha * a.
  *   MUL        a * b (a.cols == b.rows; pattern = structural product).
@@ -389,6 +393,8 @@ typedef struct {
     int32_t rows, cols;    /* LEAF shape */
     const int64_t* rowptr; /* LEAF pattern (host; copied by compile) */
     const int32_t* colind;
+    const int64_t* vmap;   /* LEAF: value of each entry, or NULL (host) */
+    int64_t n_vals;        /* LEAF with vmap: number of distinct values */
 } ssco_expr_node;
 typedef struct {
     int64_t n_leaf_vals;   /* values per set: all leaves' nnz */

@@ -288,10 +288,11 @@ def tet_stiffness(tets, xyz, E, nu: float):
 def expr_eval(nodes, leaf_vals, outputs, absolute: bool = False):
     """Evaluate a DAG of sparse matrices for one value set.
 
-    nodes: ("leaf", rows, cols, rowptr, colind) | ("add", a, b) |
+    nodes: ("leaf", rows, cols, rowptr, colind[, vmap, n_vals]) | ("add", a, b) |
     ("scale", a, alpha) | ("mul", a, b) | ("transpose", a), operands by
     earlier index.  leaf_vals: the leaves' values concatenated in node
-    order.  Entries are dictionaries {(i, j): value} holding every
+    order (with vmap, entry q of a leaf is its value vmap[q] and the leaf
+    holds n_vals values).  Entries are dictionaries {(i, j): value} holding every
     structurally present entry (a sum or product that happens to be zero
     included): A + B has the union of both patterns, A B every (i, j) with
     some k where A_ik and B_kj are present, summing A_ik B_kj over those k.
@@ -302,13 +303,14 @@ def expr_eval(nodes, leaf_vals, outputs, absolute: bool = False):
     for nd in nodes:
         kind = nd[0]
         if kind == "leaf":
-            _, r, c, rp, ci = nd
+            r, c, rp, ci = nd[1:5]
+            vm = nd[5] if len(nd) > 5 else None
             d = {}
             for i in range(r):
                 for q in range(int(rp[i]), int(rp[i + 1])):
-                    v = float(leaf_vals[off + q])
+                    v = float(leaf_vals[off + (int(vm[q]) if vm is not None else q)])
                     d[(i, int(ci[q]))] = abs(v) if absolute else v
-            off += int(rp[r])
+            off += int(nd[6]) if vm is not None else int(rp[r])
             mats.append((r, c, d))
         elif kind == "add":
             ra, ca, A = mats[nd[1]]
@@ -349,21 +351,26 @@ def expr_eval_rows(nodes, leaf_vals, output, rows):
     for nd in nodes:
         offs.append(off)
         if nd[0] == "leaf":
-            off += int(nd[3][nd[1]])
+            off += int(nd[6]) if len(nd) > 5 and nd[5] is not None else int(nd[3][nd[1]])
     cache, cols_of_leaf, full = {}, {}, {}
 
+    def leaf_value(nid, q):
+        nd = nodes[nid]
+        vm = nd[5] if len(nd) > 5 else None
+        return float(leaf_vals[offs[nid] + (int(vm[q]) if vm is not None else q)])
+
     def leaf_row(nid, i):
-        _, r, c, rp, ci = nodes[nid]
-        return {int(ci[q]): float(leaf_vals[offs[nid] + q]) for q in range(int(rp[i]), int(rp[i + 1]))}
+        rp, ci = nodes[nid][3], nodes[nid][4]
+        return {int(ci[q]): leaf_value(nid, q) for q in range(int(rp[i]), int(rp[i + 1]))}
 
     def column(nid, j):
         if nodes[nid][0] == "leaf":
             if nid not in cols_of_leaf:
-                _, r, c, rp, ci = nodes[nid]
+                r, rp, ci = nodes[nid][1], nodes[nid][3], nodes[nid][4]
                 cl = {}
                 for i in range(r):
                     for q in range(int(rp[i]), int(rp[i + 1])):
-                        cl.setdefault(int(ci[q]), {})[i] = float(leaf_vals[offs[nid] + q])
+                        cl.setdefault(int(ci[q]), {})[i] = leaf_value(nid, q)
                 cols_of_leaf[nid] = cl
             return dict(cols_of_leaf[nid].get(j, {}))
         if nid not in full:

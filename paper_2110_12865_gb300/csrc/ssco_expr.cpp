@@ -156,6 +156,12 @@ ssco_status validate(const ssco_expr_node* nodes, int32_t n_nodes, const int32_t
                     if (nd.rowptr[r + 1] < nd.rowptr[r]) return bad(SSCO_ERR_PATTERN, pre + "rowptr decreases");
                 const int64_t nnz = nd.rowptr[nd.rows];
                 if (nnz > 0 && !nd.colind) return bad(SSCO_ERR_INVALID_ARG, pre + "colind is NULL");
+                if (nd.vmap) {
+                    if (nd.n_vals < 0) return bad(SSCO_ERR_INVALID_ARG, pre + "negative n_vals");
+                    for (int64_t q = 0; q < nnz; ++q)
+                        if (nd.vmap[q] < 0 || nd.vmap[q] >= nd.n_vals)
+                            return bad(SSCO_ERR_PATTERN, pre + "vmap entry out of range");
+                }
                 for (int32_t r = 0; r < nd.rows; ++r)
                     for (int64_t q = nd.rowptr[r]; q < nd.rowptr[r + 1]; ++q) {
                         if (nd.colind[q] < 0 || nd.colind[q] >= nd.cols)
@@ -163,7 +169,7 @@ ssco_status validate(const ssco_expr_node* nodes, int32_t n_nodes, const int32_t
                         if (q > nd.rowptr[r] && nd.colind[q] <= nd.colind[q - 1])
                             return bad(SSCO_ERR_PATTERN, pre + "columns not strictly increasing in a row");
                     }
-                leaf_vals += nnz;
+                leaf_vals += nd.vmap ? nd.n_vals : nnz;
                 rows[i] = nd.rows;
                 cols[i] = nd.cols;
                 break;
@@ -216,9 +222,10 @@ ssco_status compile(const ssco_expr_node* nodes, int32_t n_nodes, const int32_t*
         if (nodes[i].op == SSCO_EXPR_ADD || nodes[i].op == SSCO_EXPR_MUL) last[nodes[i].b] = i;
     }
     for (int32_t k = 0; k < n_out; ++k) last[outputs[k]] = n_nodes;
+    auto leaf_count = [&](const ssco_expr_node& nd) { return nd.vmap ? nd.n_vals : nd.rowptr[nd.rows]; };
     int64_t leaf_vals = 0;
     for (int32_t i = 0; i < n_nodes; ++i)
-        if (nodes[i].op == SSCO_EXPR_LEAF) leaf_vals += nodes[i].rowptr[nodes[i].rows];
+        if (nodes[i].op == SSCO_EXPR_LEAF) leaf_vals += leaf_count(nodes[i]);
     E.n_leaf_vals = leaf_vals;
     Builder bd;
     bd.base = 1 + leaf_vals;
@@ -237,8 +244,8 @@ ssco_status compile(const ssco_expr_node* nodes, int32_t n_nodes, const int32_t*
             P.rp.assign(nd.rowptr, nd.rowptr + nd.rows + 1);
             P.ci.assign(nd.colind, nd.colind + nnz);
             H.resize(nnz);
-            for (int64_t q = 0; q < nnz; ++q) H[q] = {1.0, (int32_t)(1 + leaf_off + q)};
-            leaf_off += nnz;
+            for (int64_t q = 0; q < nnz; ++q) H[q] = {1.0, (int32_t)(1 + leaf_off + (nd.vmap ? nd.vmap[q] : q))};
+            leaf_off += leaf_count(nd);
         } else if (nd.op == SSCO_EXPR_SCALE) {
             P.rp = pat[nd.a].rp;
             P.ci = pat[nd.a].ci;

@@ -409,6 +409,24 @@ def laplacian_expression(p):
     return nodes, 4, vals
 
 
+def symmetric_laplacian_leaf(p):
+    """The weighted graph Laplacian of an ATWA problem as one leaf with shared
+    values (structure only): the CSR pattern of L (neighbours and the vertex
+    itself), and vmap sending (u, v) and (v, u) of edge e to value e and
+    (u, u) to value m + u; n_vals = m + n.  The values themselves (-w_e off
+    the diagonal, the sums on it) are the caller's."""
+    m, n = p.m, p.n
+    ends = np.asarray(p.colind).reshape(m, 2)
+    u = np.concatenate([ends[:, 0], ends[:, 1], np.arange(n)])
+    v = np.concatenate([ends[:, 1], ends[:, 0], np.arange(n)])
+    val = np.concatenate([np.arange(m), np.arange(m), m + np.arange(n)])
+    order = np.lexsort((v, u))
+    u, v, val = u[order], v[order], val[order]
+    rowptr = np.zeros(n + 1, np.int64)
+    np.add.at(rowptr, u + 1, 1)
+    return np.cumsum(rowptr), v.astype(np.int32), val.astype(np.int64), m + n
+
+
 def power_expression(rows, rowptr, colind, k: int = 3):
     """Nodes of M^k = (..(M M) M..) M for a square leaf M; the last node is M^k."""
     nodes = [("leaf", rows, rows, rowptr, colind), ("mul", 0, 0)]

@@ -83,7 +83,8 @@ class Info(C.Structure):
 
 class ExprNode(C.Structure):
     _fields_ = [("op", C.c_int32), ("a", C.c_int32), ("b", C.c_int32), ("alpha", C.c_double),
-                ("rows", C.c_int32), ("cols", C.c_int32), ("rowptr", C.c_void_p), ("colind", C.c_void_p)]
+                ("rows", C.c_int32), ("cols", C.c_int32), ("rowptr", C.c_void_p), ("colind", C.c_void_p),
+                ("vmap", C.c_void_p), ("n_vals", C.c_int64)]
 
 
 class ExprInfo(C.Structure):
@@ -521,27 +522,32 @@ class Expr:
     """
 
     def __init__(self):
-        self.nodes = []      # (op, a, b, alpha, rows, cols, rowptr, colind)
+        self.nodes = []      # (op, a, b, alpha, rows, cols, rowptr, colind, vmap, n_vals)
 
     def _add(self, *nd):
         self.nodes.append(nd)
         return len(self.nodes) - 1
 
-    def leaf(self, rows, cols, rowptr, colind):
+    def leaf(self, rows, cols, rowptr, colind, vmap=None, n_vals=None):
+        """A leaf with a fixed CSR pattern; with ``vmap`` entry q takes value
+        vmap[q] of the leaf's n_vals values (shared values, e.g. a symmetric
+        matrix stored once)."""
+        vm = None if vmap is None else np.ascontiguousarray(vmap, np.int64)
+        nv = 0 if vm is None else int(n_vals if n_vals is not None else (vm.max() + 1 if vm.size else 0))
         return self._add(EXPR_LEAF, -1, -1, 0.0, int(rows), int(cols),
-                         np.ascontiguousarray(rowptr, np.int64), np.ascontiguousarray(colind, np.int32))
+                         np.ascontiguousarray(rowptr, np.int64), np.ascontiguousarray(colind, np.int32), vm, nv)
 
     def add(self, a, b):
-        return self._add(EXPR_ADD, a, b, 0.0, 0, 0, None, None)
+        return self._add(EXPR_ADD, a, b, 0.0, 0, 0, None, None, None, 0)
 
     def scale(self, a, alpha):
-        return self._add(EXPR_SCALE, a, -1, float(alpha), 0, 0, None, None)
+        return self._add(EXPR_SCALE, a, -1, float(alpha), 0, 0, None, None, None, 0)
 
     def mul(self, a, b):
-        return self._add(EXPR_MUL, a, b, 0.0, 0, 0, None, None)
+        return self._add(EXPR_MUL, a, b, 0.0, 0, 0, None, None, None, 0)
 
     def transpose(self, a):
-        return self._add(EXPR_TRANSPOSE, a, -1, 0.0, 0, 0, None, None)
+        return self._add(EXPR_TRANSPOSE, a, -1, 0.0, 0, 0, None, None, None, 0)
 
     def compile(self, outputs, batch=1, dtype=torch.float64):
         return ExprProgram(self, list(outputs), batch, dtype)
@@ -554,10 +560,12 @@ class ExprProgram:
     def __init__(self, expr: Expr, outputs, batch, dtype):
         self.L = load_library()
         arr = (ExprNode * len(expr.nodes))()
-        for i, (op, a, b, al, r, c, rp, ci) in enumerate(expr.nodes):
+        for i, (op, a, b, al, r, c, rp, ci, vm, nv) in enumerate(expr.nodes):
             arr[i].op, arr[i].a, arr[i].b, arr[i].alpha, arr[i].rows, arr[i].cols = op, a, b, al, r, c
             arr[i].rowptr = rp.ctypes.data if rp is not None else None
             arr[i].colind = ci.ctypes.data if ci is not None and ci.size else None
+            arr[i].vmap = vm.ctypes.data if vm is not None and vm.size else None
+            arr[i].n_vals = nv
         outs = np.ascontiguousarray(outputs, np.int32)
         self.dtype = dtype
         prec = VALS_F32 if dtype == torch.float32 else VALS_F64

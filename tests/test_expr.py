@@ -177,6 +177,37 @@ def test_compiled_tables_edge_cases(S):
     assert np.all(got[:, off[2]:off[4]] == 0.0)              # zero scale and A - A: exactly 0
 
 
+def test_shared_leaf_values_halve_the_symmetric_square(S):
+    """The cotangent Laplacian as one leaf whose (u, v) and (v, u) entries
+    share a value (the paper's L is symmetric): structural hashing then finds
+    (L L)_uv and (L L)_vu identical, so L^2 stores only its lower triangle;
+    L^3 through the same leaf matches the oracle."""
+    p = P.trigrid_problem(12, batch=2, cfg=3)
+    rp, ci, vm, nv = P.symmetric_laplacian_leaf(p)
+    n = p.n
+    ends = np.asarray(p.colind).reshape(p.m, 2)
+    vals = np.zeros((2, nv))
+    for b in range(2):
+        w = p.vals[b]
+        d = np.zeros(n)
+        np.add.at(d, ends[:, 0], w)
+        np.add.at(d, ends[:, 1], w)
+        vals[b] = np.concatenate([-w, d])
+    leaf = ("leaf", n, n, rp, ci, vm, nv)
+    sq = build_expr(S, [leaf, ("mul", 0, 0)]).compile([1], batch=2)
+    r, c, rp2, ci2 = sq.output_pattern(0)
+    lower = sum(int(np.sum(ci2[rp2[i]:rp2[i + 1]] <= i)) for i in range(r))
+    assert sq.info["n_ops"] == lower and sq.info["n_leaf_vals"] == nv
+    check_outputs(S, sq, [leaf, ("mul", 0, 0)], [1], vals, interpret(S, sq, vals), 1e-13)
+    nodes = [leaf, ("mul", 0, 0), ("mul", 1, 0)]
+    cube = build_expr(S, nodes).compile([2], batch=2)
+    check_outputs(S, cube, nodes, [2], vals, interpret(S, cube, vals), 1e-13)
+    plain = build_expr(S, [("leaf", n, n, rp, ci), ("mul", 0, 0), ("mul", 1, 0)]).compile([2])
+    assert cube.info["n_ops"] < plain.info["n_ops"]
+    with pytest.raises(S.SscoError):
+        build_expr(S, [("leaf", n, n, rp, ci, vm, nv - 1)]).compile([0])   # vmap out of range
+
+
 def test_expr_compile_rejects_malformed_nodes(S):
     rp, ci = np.array([0, 2, 3]), np.array([0, 1, 1])
     ok = ("leaf", 2, 2, rp, ci)
