@@ -70,3 +70,16 @@ def test_two_gloo_ranks_weak_scaling():
         work, _ = bench.make_workload("tiny", rank)       # same data as a single process builds
         assert np.allclose(out[0]["first_vals"][rank], work[0][0].vals[0][:8])
     assert not np.allclose(out[0]["first_vals"][0], out[0]["first_vals"][1])  # distinct value sets
+
+
+def test_oracle_timing_on_all_host_cores():
+    """The CPU baseline deals its systems to one spawned process per host
+    core (largest first, least loaded core); each process runs only the
+    numeric oracle after a common start, and the wall time is the slowest
+    process's, so it is at most the summed busy time."""
+    import bench
+    work, _ = bench.make_workload("tiny", 0)
+    items = bench.oracle_sample(work) * 3
+    wall, busy, procs = bench.time_oracle_all_cores(items)
+    assert 1 <= procs <= min(len(os.sched_getaffinity(0)), len(items))
+    assert 0 < wall <= busy + 1e-9
