@@ -282,3 +282,26 @@ def test_element_blocks_pattern_structure(S, tmp_path):
     L = S.load_library()
     assert L.ssco_analyze(arr, 1, C.byref(op), C.byref(h)) == 1
     assert b"elem_dofs" in L.ssco_last_error(None)
+
+
+def test_expr_abi_error_paths(S):
+    """Host-side refusals of the expression ABI, all before any device call:
+    run before bind, NULL or misaligned device buffers, a short export
+    buffer, an output index out of range, every exported symbol present."""
+    import ctypes as C
+    L = S.load_library()
+    E = S.Expr()
+    A = E.leaf(3, 3, [0, 1, 2, 3], [0, 1, 2])
+    prog = E.compile([E.mul(A, A)])
+    h = prog._h
+    assert L.ssco_expr_run(h, None, None, None) == 10                     # STATE: not bound
+    assert L.ssco_expr_bind(h, None, None, None) == 1
+    assert L.ssco_expr_bind(h, C.c_void_p(0x1001), C.c_void_p(0x2000), None) == 1   # misaligned
+    buf = np.zeros(1, np.int64)
+    assert L.ssco_expr_export(h, S.EXPR_EXPORT_TERM_OFF, buf.ctypes.data, 0) == 1    # too small
+    assert L.ssco_expr_export(h, 99, buf.ctypes.data, 8) == 1                         # unknown table
+    r = C.c_int32()
+    assert L.ssco_expr_output_shape(h, 1, C.byref(r), None, None) == 1                # no output 1
+    assert L.ssco_expr_output_shape(h, 0, C.byref(r), None, None) == 0 and r.value == 3
+    assert L.ssco_expr_get_info(None, None) == 1
+    assert prog.info["n_ops"] == 3 and prog.info["n_levels"] == 1   # diagonal squares: one term each
