@@ -70,43 +70,55 @@ struct Builder {
         }
     }
 
-    // The sum of the terms in `t`, as a handle: a constant multiple of one
-    // slot needs no expression; anything else is stored once.
-    Handle materialize() {
-        ++n_unrolled;
-        for (Term& x : t)
+    // Canonical form of the sum in `v` (in place): factor pairs ordered,
+    // terms sorted, equal pairs merged, zero terms dropped.  Returns the
+    // handle when no expression is needed (a constant multiple of one slot,
+    // or zero); otherwise {0, -1} with the form's hash in *h.
+    static Handle canon(std::vector<Term>& v, uint64_t* h) {
+        for (Term& x : v)
             if (x.f1 < x.f2) std::swap(x.f1, x.f2);
-        if (t.size() > 1) {
-            std::sort(t.begin(), t.end(), [](const Term& a, const Term& b) {
+        if (v.size() > 1) {
+            std::sort(v.begin(), v.end(), [](const Term& a, const Term& b) {
                 return a.f1 != b.f1 ? a.f1 < b.f1 : a.f2 < b.f2;
             });
             size_t w = 0;
-            for (size_t r = 0; r < t.size(); ++r) {
-                if (w > 0 && t[w - 1].f1 == t[r].f1 && t[w - 1].f2 == t[r].f2)
-                    t[w - 1].c += t[r].c;  // equal factor pairs: one product
+            for (size_t r = 0; r < v.size(); ++r) {
+                if (w > 0 && v[w - 1].f1 == v[r].f1 && v[w - 1].f2 == v[r].f2)
+                    v[w - 1].c += v[r].c;  // equal factor pairs: one product
                 else
-                    t[w++] = t[r];
+                    v[w++] = v[r];
             }
-            t.resize(w);
+            v.resize(w);
         }
-        t.erase(std::remove_if(t.begin(), t.end(), [](const Term& x) { return x.c == 0.0; }), t.end());
-        if (t.empty()) return {0.0, 0};
-        if (t.size() == 1 && t[0].f2 == 0) return {t[0].c, t[0].f1};
-        uint64_t h = 0;
-        for (const Term& x : t) {
+        v.erase(std::remove_if(v.begin(), v.end(), [](const Term& x) { return x.c == 0.0; }), v.end());
+        if (v.empty()) return {0.0, 0};
+        if (v.size() == 1 && v[0].f2 == 0) return {v[0].c, v[0].f1};
+        uint64_t hh = 0;
+        for (const Term& x : v) {
             uint64_t cb;
             std::memcpy(&cb, &x.c, 8);
-            h = mix(mix(h, ((uint64_t)(uint32_t)x.f1 << 32) | (uint32_t)x.f2), cb);
+            hh = mix(mix(hh, ((uint64_t)(uint32_t)x.f1 << 32) | (uint32_t)x.f2), cb);
         }
+        *h = hh;
+        return {0.0, -1};
+    }
+
+    void prefetch(uint64_t h) const {
+        if (!table.empty()) __builtin_prefetch(&table[h & (table.size() - 1)]);
+    }
+
+    // The stored expression with canonical terms tt[0..n) and hash h: an
+    // equal earlier one, or a new one.
+    Handle lookup_insert(const Term* tt, size_t n, uint64_t h) {
         if (table.empty()) rehash(1 << 16);
         size_t cap = table.size(), p = h & (cap - 1);
         while (table[p]) {
             const int32_t i = (int32_t)(table[p] & 0xffffffffull) - 1;
-            if ((table[p] >> 32) == (h >> 32) && hash[i] == h && nt[i] == (int32_t)t.size()) {
+            if ((table[p] >> 32) == (h >> 32) && hash[i] == h && nt[i] == (int32_t)n) {
                 const Term* q = pool.data() + tbeg[i];
                 bool same = true;
-                for (size_t k = 0; k < t.size() && same; ++k)
-                    same = q[k].f1 == t[k].f1 && q[k].f2 == t[k].f2 && q[k].c == t[k].c;
+                for (size_t k = 0; k < n && same; ++k)
+                    same = q[k].f1 == tt[k].f1 && q[k].f2 == tt[k].f2 && q[k].c == tt[k].c;
                 if (same) return {1.0, (int32_t)(base + i)};
             }
             p = (p + 1) & (cap - 1);
@@ -117,15 +129,51 @@ struct Builder {
             return {0.0, 0};
         }
         int32_t lv = 0;
-        for (const Term& x : t) lv = std::max(lv, std::max(level_of(x.f1), level_of(x.f2)));
+        for (size_t k = 0; k < n; ++k) lv = std::max(lv, std::max(level_of(tt[k].f1), level_of(tt[k].f2)));
         level.push_back(lv + 1);
-        nt.push_back((int32_t)t.size());
+        nt.push_back((int32_t)n);
         tbeg.push_back((int64_t)pool.size());
         hash.push_back(h);
-        pool.insert(pool.end(), t.begin(), t.end());
+        pool.insert(pool.end(), tt, tt + n);
         table[p] = slot_of(idx, h);
         if (2 * level.size() > cap) rehash(cap * 2);
         return {1.0, (int32_t)(base + idx)};
+    }
+
+    // The sum of the terms in `t`, as a handle: a constant multiple of one
+    // slot needs no expression; anything else is stored once.
+    Handle materialize() {
+        ++n_unrolled;
+        uint64_t h = 0;
+        const Handle d = canon(t, &h);
+        return d.s >= 0 ? d : lookup_insert(t.data(), t.size(), h);
+    }
+
+    // materialize() for a batch of sums (the entries of one row of a
+    // product): all canonical forms first, their table slots prefetched,
+    // then the lookups, so that the table's cache misses overlap.
+    std::vector<Term> bt;
+    std::vector<size_t> boff;
+    std::vector<uint64_t> bh;
+    std::vector<Handle> direct;
+    void materialize_batch(const std::vector<Term>& terms, const std::vector<int64_t>& off, size_t count,
+                           std::vector<Handle>& out) {
+        bt.clear();
+        boff.assign(1, 0);
+        bh.resize(count);
+        direct.resize(count);
+        for (size_t x = 0; x < count; ++x) {
+            t.assign(terms.begin() + off[x], terms.begin() + off[x + 1]);
+            direct[x] = canon(t, &bh[x]);
+            if (direct[x].s < 0) {
+                bt.insert(bt.end(), t.begin(), t.end());
+                prefetch(bh[x]);
+            }
+            boff.push_back(bt.size());
+        }
+        n_unrolled += (int64_t)count;
+        for (size_t x = 0; x < count; ++x)
+            out.push_back(direct[x].s >= 0 ? direct[x] : lookup_insert(bt.data() + boff[x], boff[x + 1] - boff[x], bh[x]));
     }
 };
 
@@ -328,11 +376,8 @@ ssco_status compile(const ssco_expr_node* nodes, int32_t n_nodes, const int32_t*
                     for (int64_t q = Bm.rp[k]; q < Bm.rp[k + 1]; ++q)
                         terms[fill[cnt[Bm.ci[q]]]++] = Term{HA[p].s, HB[q].s, HA[p].c * HB[q].c};
                 }
-                for (size_t x = 0; x < jl.size(); ++x) {
-                    bd.t.assign(terms.begin() + off[x], terms.begin() + off[x + 1]);
-                    H.push_back(bd.materialize());
-                    P.ci.push_back(jl[x]);
-                }
+                bd.materialize_batch(terms, off, jl.size(), H);
+                P.ci.insert(P.ci.end(), jl.begin(), jl.end());
                 P.rp.push_back((int64_t)P.ci.size());
             }
         }
