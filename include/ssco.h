@@ -376,13 +376,14 @@ ssco_status ssco_tet_stiffness(const int32_t* tets, int64_t n_tet, int64_t n_nod
  *   TRANSPOSE  a^T.
  * Every entry of an ADD present in both operands and every entry of a MUL
  * is stored once as an intermediate (a global intermediate in the paper's
- * terms); scaling and transposition only relabel entries.  The products of
+ * terms) unless its canonical form is a multiple of one slot or zero (A + A,
+ * A - A); scaling and transposition only relabel entries.  The products of
  * an entry are summed in ascending order of their factor slots, after equal
  * factor pairs are merged (coefficients added) and zero coefficients
  * dropped; values are float or double (`precision` = SSCO_VALS_F64 /
  * SSCO_VALS_F32) and accumulate in that type.
- * Leaf values per set are the leaves' nnz concatenated in node order
- * ([batch][n_leaf_vals]); outputs likewise ([batch][n_out_vals], in the
+ * Leaf values per set are the leaves' values (nnz each, or n_vals with a
+ * vmap) concatenated in node order ([batch][n_leaf_vals]); outputs likewise ([batch][n_out_vals], in the
  * order of `outputs`, each in its CSR order). */
 typedef struct ssco_expr_s* ssco_expr;
 enum { SSCO_EXPR_LEAF = 0, SSCO_EXPR_ADD = 1, SSCO_EXPR_SCALE = 2, SSCO_EXPR_MUL = 3, SSCO_EXPR_TRANSPOSE = 4 };
