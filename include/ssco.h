@@ -374,10 +374,11 @@ ssco_status ssco_tet_stiffness(const int32_t* tets, int64_t n_tet, int64_t n_nod
  *   SCALE      alpha * a.
  *   MUL        a * b (a.cols == b.rows; pattern = structural product).
  *   TRANSPOSE  a^T.
- * Every entry of an ADD present in both operands and every entry of a MUL
- * is stored once as an intermediate (a global intermediate in the paper's
- * terms) unless its canonical form is a multiple of one slot or zero (A + A,
- * A - A); scaling and transposition only relabel entries.  The products of
+ * Every entry of a MUL, and (unless inlined, see inline_terms) every entry
+ * of an ADD present in both operands, is stored once as an intermediate (a
+ * global intermediate in the paper's terms) unless its canonical form is a
+ * multiple of one slot or zero (A + A, A - A); scaling and transposition
+ * only relabel entries.  The products of
  * an entry are summed in ascending order of their factor slots, after equal
  * factor pairs are merged (coefficients added) and zero coefficients
  * dropped; values are float or double (`precision` = SSCO_VALS_F64 /
@@ -419,12 +420,18 @@ enum { SSCO_EXPR_EXPORT_LEVELS = 0,   /* int64 [n_levels+1] op ranges */
        SSCO_EXPR_EXPORT_OUT_SLOT = 5, /* int32 [n_out_vals] slot of each output value */
        SSCO_EXPR_EXPORT_OUT_COEF = 6  /* double [n_out_vals] its factor */ };
 
-/* Host only.  Slot layout: slot 0 = 1, slots 1..n_leaf_vals = leaf values,
+/* Host only.  inline_terms (0..16) chooses between storing and inlining a
+ * sum (the paper's global / local decomposition): 0 stores every entry of a
+ * sum present in both operands; k > 0 keeps a sum of at most k slot
+ * multiples local instead, and the products that use it expand over its
+ * terms (at most k x k products per factor pair), so fewer intermediates
+ * and levels are stored at the cost of more products.
+ * Slot layout: slot 0 = 1, slots 1..n_leaf_vals = leaf values,
  * then the intermediates of level 1, 2, ... (op i is slot
  * 1 + n_leaf_vals + i).  Returns INVALID_ARG / PATTERN for malformed nodes
  * (message in ssco_expr_last_error(NULL)), UNSUPPORTED beyond int32 slots. */
 ssco_status ssco_expr_compile(const ssco_expr_node* nodes, int32_t n_nodes, const int32_t* outputs, int32_t n_out,
-                              int32_t batch, int32_t precision, ssco_expr* out);
+                              int32_t batch, int32_t precision, int32_t inline_terms, ssco_expr* out);
 ssco_status ssco_expr_get_info(ssco_expr e, ssco_expr_info* out);
 ssco_status ssco_expr_export(ssco_expr e, int32_t what, void* host_buf, uint64_t bytes);
 /* Shape and CSR pattern of the k-th output (rowptr [rows+1], colind [nnz]). */

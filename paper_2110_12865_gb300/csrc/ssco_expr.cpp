@@ -257,10 +257,11 @@ ssco_status validate(const ssco_expr_node* nodes, int32_t n_nodes, const int32_t
 }
 
 ssco_status compile(const ssco_expr_node* nodes, int32_t n_nodes, const int32_t* outputs, int32_t n_out,
-                    int32_t batch, int32_t precision, ExprProgram& E) {
+                    int32_t batch, int32_t precision, int32_t inline_terms, ExprProgram& E) {
     std::vector<int32_t> rows, cols;
     ssco_status st = validate(nodes, n_nodes, outputs, n_out, batch, precision, rows, cols);
     if (st != SSCO_OK) return st;
+    if (inline_terms < 0 || inline_terms > 16) return bad(SSCO_ERR_INVALID_ARG, "inline_terms must be in [0, 16]");
     E.B = batch;
     E.precision = precision;
     // last use of every node, so that its entries can be released
@@ -278,45 +279,81 @@ ssco_status compile(const ssco_expr_node* nodes, int32_t n_nodes, const int32_t*
     Builder bd;
     bd.base = 1 + leaf_vals;
     std::vector<ExprCsr> pat(n_nodes);
-    std::vector<std::vector<Handle>> hv(n_nodes);
+    // Every entry of a node is a short linear combination of slots: one
+    // handle, or, with inlining, up to `inline_terms` handles kept local
+    // (not stored) and expanded into the products that use them.
+    struct Entries {
+        std::vector<int64_t> off{0};
+        std::vector<Handle> h;
+        void push(const Handle* b, const Handle* e) {
+            h.insert(h.end(), b, e);
+            off.push_back((int64_t)h.size());
+        }
+        void push1(Handle x) {
+            h.push_back(x);
+            off.push_back((int64_t)h.size());
+        }
+        int64_t n(int64_t e) const { return off[e + 1] - off[e]; }
+        const Handle* at(int64_t e) const { return h.data() + off[e]; }
+    };
+    std::vector<Entries> ev(n_nodes);
+    std::vector<Handle> lin;
+    // canonical local combination: equal slots merged, zero coefficients dropped
+    auto canon_lin = [](std::vector<Handle>& v) {
+        std::sort(v.begin(), v.end(), [](const Handle& a, const Handle& b) { return a.s < b.s; });
+        size_t w = 0;
+        for (size_t r = 0; r < v.size(); ++r) {
+            if (w > 0 && v[w - 1].s == v[r].s)
+                v[w - 1].c += v[r].c;
+            else
+                v[w++] = v[r];
+        }
+        v.resize(w);
+        v.erase(std::remove_if(v.begin(), v.end(), [](const Handle& x) { return x.c == 0.0; }), v.end());
+    };
+    // a combination as one handle: stored unless it is a multiple of one slot
+    auto store_lin = [&](const Handle* b, int64_t n) {
+        bd.t.clear();
+        for (int64_t k = 0; k < n; ++k) bd.t.push_back(Term{b[k].s, 0, b[k].c});
+        return bd.materialize();
+    };
     std::vector<int32_t> mark, cnt;
     int64_t leaf_off = 0;
     for (int32_t i = 0; i < n_nodes; ++i) {
         const ssco_expr_node& nd = nodes[i];
         ExprCsr& P = pat[i];
-        std::vector<Handle>& H = hv[i];
+        Entries& H = ev[i];
         P.rows = rows[i];
         P.cols = cols[i];
         if (nd.op == SSCO_EXPR_LEAF) {
             const int64_t nnz = nd.rowptr[nd.rows];
             P.rp.assign(nd.rowptr, nd.rowptr + nd.rows + 1);
             P.ci.assign(nd.colind, nd.colind + nnz);
-            H.resize(nnz);
-            for (int64_t q = 0; q < nnz; ++q) H[q] = {1.0, (int32_t)(1 + leaf_off + (nd.vmap ? nd.vmap[q] : q))};
+            for (int64_t q = 0; q < nnz; ++q) H.push1({1.0, (int32_t)(1 + leaf_off + (nd.vmap ? nd.vmap[q] : q))});
             leaf_off += leaf_count(nd);
         } else if (nd.op == SSCO_EXPR_SCALE) {
             P.rp = pat[nd.a].rp;
             P.ci = pat[nd.a].ci;
-            H = hv[nd.a];
-            for (Handle& h : H) h.c *= nd.alpha;
+            H = ev[nd.a];
+            for (Handle& h : H.h) h.c *= nd.alpha;
         } else if (nd.op == SSCO_EXPR_TRANSPOSE) {
             const ExprCsr& A = pat[nd.a];
-            const std::vector<Handle>& HA = hv[nd.a];
+            const Entries& HA = ev[nd.a];
             P.rp.assign(P.rows + 1, 0);
             for (int32_t c : A.ci) P.rp[c + 1]++;
             for (int32_t r = 0; r < P.rows; ++r) P.rp[r + 1] += P.rp[r];
             P.ci.resize(A.ci.size());
-            H.resize(A.ci.size());
-            std::vector<int64_t> fill(P.rp.begin(), P.rp.end() - 1);
+            std::vector<int64_t> src(A.ci.size()), fill(P.rp.begin(), P.rp.end() - 1);
             for (int32_t r = 0; r < A.rows; ++r)
                 for (int64_t q = A.rp[r]; q < A.rp[r + 1]; ++q) {
                     const int64_t p = fill[A.ci[q]]++;
                     P.ci[p] = r;
-                    H[p] = HA[q];
+                    src[p] = q;
                 }
+            for (int64_t p = 0; p < (int64_t)src.size(); ++p) H.push(HA.at(src[p]), HA.at(src[p]) + HA.n(src[p]));
         } else if (nd.op == SSCO_EXPR_ADD) {
             const ExprCsr &A = pat[nd.a], &Bm = pat[nd.b];
-            const std::vector<Handle>&HA = hv[nd.a], &HB = hv[nd.b];
+            const Entries &HA = ev[nd.a], &HB = ev[nd.b];
             P.rp.assign(1, 0);
             for (int32_t r = 0; r < P.rows; ++r) {
                 int64_t p = A.rp[r], q = Bm.rp[r];
@@ -324,30 +361,36 @@ ssco_status compile(const ssco_expr_node* nodes, int32_t n_nodes, const int32_t*
                     const int32_t ca = p < A.rp[r + 1] ? A.ci[p] : INT32_MAX;
                     const int32_t cb = q < Bm.rp[r + 1] ? Bm.ci[q] : INT32_MAX;
                     if (ca == cb) {
-                        bd.t.assign({Term{HA[p].s, 0, HA[p].c}, Term{HB[q].s, 0, HB[q].c}});
-                        H.push_back(bd.materialize());
+                        lin.assign(HA.at(p), HA.at(p) + HA.n(p));
+                        lin.insert(lin.end(), HB.at(q), HB.at(q) + HB.n(q));
+                        if (inline_terms > 0) canon_lin(lin);
+                        if (inline_terms > 0 && (int64_t)lin.size() <= inline_terms)
+                            H.push(lin.data(), lin.data() + lin.size());   // kept local
+                        else
+                            H.push1(store_lin(lin.data(), (int64_t)lin.size()));
                         P.ci.push_back(ca);
                         ++p, ++q;
                     } else if (ca < cb) {
-                        H.push_back(HA[p]);
+                        H.push(HA.at(p), HA.at(p) + HA.n(p));
                         P.ci.push_back(ca);
                         ++p;
                     } else {
-                        H.push_back(HB[q]);
+                        H.push(HB.at(q), HB.at(q) + HB.n(q));
                         P.ci.push_back(cb);
                         ++q;
                     }
                 }
                 P.rp.push_back((int64_t)P.ci.size());
             }
-        } else {  // MUL: entry (r, j) = sum over k of A(r, k) B(k, j)
+        } else {  // MUL: entry (r, j) = sum over k of A(r, k) B(k, j), local sums expanded
             const ExprCsr &A = pat[nd.a], &Bm = pat[nd.b];
-            const std::vector<Handle>&HA = hv[nd.a], &HB = hv[nd.b];
+            const Entries &HA = ev[nd.a], &HB = ev[nd.b];
             mark.assign(P.cols, -1);
             cnt.assign(P.cols, 0);
             std::vector<int32_t> jl;
             std::vector<int64_t> off;
             std::vector<Term> terms;
+            std::vector<Handle> row;
             P.rp.assign(1, 0);
             for (int32_t r = 0; r < P.rows; ++r) {
                 jl.clear();
@@ -360,7 +403,7 @@ ssco_status compile(const ssco_expr_node* nodes, int32_t n_nodes, const int32_t*
                             cnt[j] = 0;
                             jl.push_back(j);
                         }
-                        cnt[j]++;
+                        cnt[j] += (int32_t)(HA.n(p) * HB.n(q));
                     }
                 }
                 std::sort(jl.begin(), jl.end());
@@ -373,10 +416,16 @@ ssco_status compile(const ssco_expr_node* nodes, int32_t n_nodes, const int32_t*
                 std::vector<int64_t> fill(off.begin(), off.end() - 1);
                 for (int64_t p = A.rp[r]; p < A.rp[r + 1]; ++p) {
                     const int32_t k = A.ci[p];
-                    for (int64_t q = Bm.rp[k]; q < Bm.rp[k + 1]; ++q)
-                        terms[fill[cnt[Bm.ci[q]]]++] = Term{HA[p].s, HB[q].s, HA[p].c * HB[q].c};
+                    for (int64_t q = Bm.rp[k]; q < Bm.rp[k + 1]; ++q) {
+                        int64_t& f = fill[cnt[Bm.ci[q]]];
+                        for (const Handle *a = HA.at(p), *ae = a + HA.n(p); a < ae; ++a)
+                            for (const Handle *b = HB.at(q), *be = b + HB.n(q); b < be; ++b)
+                                terms[f++] = Term{a->s, b->s, a->c * b->c};
+                    }
                 }
-                bd.materialize_batch(terms, off, jl.size(), H);
+                row.clear();
+                bd.materialize_batch(terms, off, jl.size(), row);
+                for (const Handle& h : row) H.push1(h);
                 P.ci.insert(P.ci.end(), jl.begin(), jl.end());
                 P.rp.push_back((int64_t)P.ci.size());
             }
@@ -387,11 +436,20 @@ ssco_status compile(const ssco_expr_node* nodes, int32_t n_nodes, const int32_t*
                                 (nd.op == SSCO_EXPR_ADD || nd.op == SSCO_EXPR_MUL) ? nd.b : -1};
         for (int32_t o : ops)
             if (o >= 0 && last[o] == i) {
-                std::vector<Handle>().swap(hv[o]);
+                Entries().h.swap(ev[o].h);
+                std::vector<int64_t>{0}.swap(ev[o].off);
                 std::vector<int64_t>().swap(pat[o].rp);
                 std::vector<int32_t>().swap(pat[o].ci);
             }
     }
+    // outputs: every entry as one handle (local combinations stored now)
+    std::vector<std::vector<Handle>> outh(n_out);
+    for (int32_t k = 0; k < n_out; ++k) {
+        const Entries& H = ev[outputs[k]];
+        for (int64_t e = 0; e + 1 < (int64_t)H.off.size(); ++e)
+            outh[k].push_back(H.n(e) == 1 ? *H.at(e) : store_lin(H.at(e), H.n(e)));
+    }
+    if (bd.overflow) return bad(SSCO_ERR_UNSUPPORTED, "stored intermediates exceed int32 slots");
     // level order: by level, then term count, then creation (two stable
     // counting passes: term count, then level)
     const int64_t n_ops = (int64_t)bd.level.size();
@@ -456,7 +514,7 @@ ssco_status compile(const ssco_expr_node* nodes, int32_t n_nodes, const int32_t*
     for (int32_t k = 0; k < n_out; ++k) {
         const int32_t o = outputs[k];
         E.out_pat.push_back(pat[o]);
-        for (const Handle& h : hv[o]) {
+        for (const Handle& h : outh[k]) {
             E.out_slot.push_back(remap(h.s));
             E.out_coef.push_back(h.c);
         }
@@ -522,14 +580,14 @@ using ssco::g_expr_err;
 extern "C" {
 
 ssco_status ssco_expr_compile(const ssco_expr_node* nodes, int32_t n_nodes, const int32_t* outputs, int32_t n_out,
-                              int32_t batch, int32_t precision, ssco_expr* out) {
+                              int32_t batch, int32_t precision, int32_t inline_terms, ssco_expr* out) {
     if (!out) return ssco::bad(SSCO_ERR_INVALID_ARG, "NULL output handle");
     *out = nullptr;
     ssco_expr e = new (std::nothrow) ssco_expr_s();
     if (!e) return ssco::bad(SSCO_ERR_OOM, "host allocation failed");
     ssco_status st;
     try {
-        st = ssco::compile(nodes, n_nodes, outputs, n_out, batch, precision, e->E);
+        st = ssco::compile(nodes, n_nodes, outputs, n_out, batch, precision, inline_terms, e->E);
     } catch (const std::bad_alloc&) {
         st = ssco::bad(SSCO_ERR_OOM, "host allocation failed while compiling");
     } catch (const std::exception& ex) {

@@ -136,7 +136,7 @@ def load_library(path: str = LIB_PATH):
         "ssco_profile_trace": (i32, [vp, vp, vp, vp, vp, i64, C.POINTER(i64)]),
         "ssco_graph_run": (i32, [vp, vp, i32, vp, vp, vp, vp]),
         "ssco_autotune": (i32, [vp, vp, i32, vp, vp, vp, i32, vp, C.POINTER(dbl)]),
-        "ssco_expr_compile": (i32, [C.POINTER(ExprNode), i32, vp, i32, i32, i32, C.POINTER(vp)]),
+        "ssco_expr_compile": (i32, [C.POINTER(ExprNode), i32, vp, i32, i32, i32, i32, C.POINTER(vp)]),
         "ssco_expr_get_info": (i32, [vp, C.POINTER(ExprInfo)]),
         "ssco_expr_export": (i32, [vp, i32, vp, C.c_uint64]),
         "ssco_expr_output_shape": (i32, [vp, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i64)]),
@@ -549,15 +549,17 @@ class Expr:
     def transpose(self, a):
         return self._add(EXPR_TRANSPOSE, a, -1, 0.0, 0, 0, None, None, None, 0)
 
-    def compile(self, outputs, batch=1, dtype=torch.float64):
-        return ExprProgram(self, list(outputs), batch, dtype)
+    def compile(self, outputs, batch=1, dtype=torch.float64, inline_terms=0):
+        """inline_terms > 0 keeps sums of at most that many slot multiples
+        local (expanded into their products) instead of storing them."""
+        return ExprProgram(self, list(outputs), batch, dtype, inline_terms)
 
 
 class ExprProgram:
     """A compiled expression: host tables, then (after bind) device tables
     and slot workspace owned by this object as torch tensors."""
 
-    def __init__(self, expr: Expr, outputs, batch, dtype):
+    def __init__(self, expr: Expr, outputs, batch, dtype, inline_terms=0):
         self.L = load_library()
         arr = (ExprNode * len(expr.nodes))()
         for i, (op, a, b, al, r, c, rp, ci, vm, nv) in enumerate(expr.nodes):
@@ -571,7 +573,7 @@ class ExprProgram:
         prec = VALS_F32 if dtype == torch.float32 else VALS_F64
         h = C.c_void_p()
         st = self.L.ssco_expr_compile(arr, len(expr.nodes), outs.ctypes.data, len(outs), int(batch), prec,
-                                      C.byref(h))
+                                      int(inline_terms), C.byref(h))
         if st != SSCO_OK:
             raise SscoError(st, self.L.ssco_expr_last_error(None).decode())
         self._h = h

@@ -177,6 +177,27 @@ def test_compiled_tables_edge_cases(S):
     assert np.all(got[:, off[2]:off[4]] == 0.0)              # zero scale and A - A: exactly 0
 
 
+@pytest.mark.parametrize("k", [1, 2, 4])
+def test_inlined_sums_match_oracle_and_store_less(S, k):
+    """Local sums (the paper's local expressions): with inline_terms = k a
+    sum of at most k slot multiples is not stored; the products that use it
+    expand over its terms.  Tables still match the oracle; for the paper's
+    expressions with sums feeding products, fewer intermediates are stored
+    and no more levels are needed; an inlined sum that is itself an output is
+    stored at the end."""
+    nodes, outs, nv = random_expressions(50, 68, per_row=4)
+    nodes = nodes + [("add", 0, 1)]                  # a plain sum as an extra output
+    outs = outs + [len(nodes) - 1]
+    vals = np.random.default_rng(69).standard_normal((2, nv))
+    base = build_expr(S, nodes).compile(outs, batch=2)
+    prog = build_expr(S, nodes).compile(outs, batch=2, inline_terms=k)
+    check_outputs(S, prog, nodes, outs, vals, interpret(S, prog, vals), 1e-13)
+    if k >= 2:
+        assert prog.info["n_ops"] < base.info["n_ops"] and prog.info["n_levels"] <= base.info["n_levels"]
+    with pytest.raises(S.SscoError):
+        build_expr(S, nodes).compile(outs, inline_terms=17)
+
+
 def test_shared_leaf_values_halve_the_symmetric_square(S):
     """The cotangent Laplacian as one leaf whose (u, v) and (v, u) entries
     share a value (the paper's L is symmetric): structural hashing then finds
