@@ -731,3 +731,23 @@ def test_expr_row_oracle_equals_full_oracle():
         (_, _, d), = O.expr_eval(nodes, vals, [o])
         rows = O.expr_eval_rows(nodes, vals, o, range(30))
         assert {(i, j): v for i, r in rows.items() for j, v in r.items()} == d
+
+
+def test_expr_oracle_shared_values_equal_expanded_values():
+    """A leaf whose entries share values (vmap) evaluates exactly like the
+    same leaf given one value per entry, vals[vmap]; the lazy row evaluator
+    agrees with the full one on shared leaves too."""
+    rng = np.random.default_rng(53)
+    n = 25
+    rp, ci = _rand_csr(rng, n, n, 3)
+    nnz = int(rp[-1])
+    vm = rng.integers(0, 11, nnz)
+    vals = rng.standard_normal(11)
+    shared = [("leaf", n, n, rp, ci, vm, 11), ("transpose", 0), ("mul", 0, 1), ("add", 2, 0)]
+    plain = [("leaf", n, n, rp, ci), ("transpose", 0), ("mul", 0, 1), ("add", 2, 0)]
+    for o in (2, 3):
+        (_, _, ds), = O.expr_eval(shared, vals, [o])
+        (_, _, dp), = O.expr_eval(plain, vals[vm], [o])
+        assert ds == dp
+        rows = O.expr_eval_rows(shared, vals, o, range(n))
+        assert {(i, j): v for i, r in rows.items() for j, v in r.items()} == ds
