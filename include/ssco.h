@@ -444,6 +444,12 @@ ssco_status ssco_expr_bind(ssco_expr e, void* dev_tables, void* dev_workspace, v
  * [batch][n_out_vals] device arrays of the program's precision.  Async;
  * launches 2 + n_levels kernels on `stream`. */
 ssco_status ssco_expr_run(ssco_expr e, const void* leaf_vals, void* out_vals, void* stream);
+/* Versioned file of a compiled program (host tables only; digest-checked
+ * like plan files).  Load refuses another version, damage, and tables that
+ * index outside the program's slots; the caller owns the returned program
+ * and binds it as after compile. */
+ssco_status ssco_expr_save(ssco_expr e, const char* path);
+ssco_status ssco_expr_load(const char* path, ssco_expr* out);
 const char* ssco_expr_last_error(ssco_expr e);
 void ssco_expr_destroy(ssco_expr e);
 

@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <fstream>
 #include <new>
 
 #include "ssco_expr_internal.h"
@@ -526,6 +527,62 @@ ssco_status compile(const ssco_expr_node* nodes, int32_t n_nodes, const int32_t*
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Program files: magic, version, the program, then a 64-bit FNV-1a digest
+// of everything before it (the plan files' scheme).
+constexpr uint64_t kExprMagic = 0x315058454F435353ull;  // "SSCOEXP1"
+constexpr uint32_t kExprVersion = 1;
+
+struct Fnv {
+    uint64_t h = 0xcbf29ce484222325ull;
+    void add(const void* p, size_t n) {
+        const unsigned char* c = static_cast<const unsigned char*>(p);
+        for (size_t i = 0; i < n; ++i) h = (h ^ c[i]) * 0x100000001b3ull;
+    }
+};
+struct Out {
+    std::ofstream f;
+    Fnv sum;
+    template <class T>
+    void pod(const T& v) {
+        f.write(reinterpret_cast<const char*>(&v), sizeof(T));
+        sum.add(&v, sizeof(T));
+    }
+    template <class T>
+    void vec(const std::vector<T>& v) {
+        pod((uint64_t)v.size());
+        if (!v.empty()) {
+            f.write(reinterpret_cast<const char*>(v.data()), (std::streamsize)(v.size() * sizeof(T)));
+            sum.add(v.data(), v.size() * sizeof(T));
+        }
+    }
+};
+struct In {
+    std::ifstream f;
+    Fnv sum;
+    std::streamoff size = 0;
+    template <class T>
+    bool pod(T& v) {
+        f.read(reinterpret_cast<char*>(&v), sizeof(T));
+        if (!f) return false;
+        sum.add(&v, sizeof(T));
+        return true;
+    }
+    template <class T>
+    bool vec(std::vector<T>& v) {
+        uint64_t n = 0;
+        if (!pod(n)) return false;
+        const std::streamoff here = f.tellg();
+        if (here < 0 || n > (uint64_t)(size - here) / sizeof(T)) return false;  // damage, not a size
+        v.resize(n);
+        if (n) {
+            f.read(reinterpret_cast<char*>(v.data()), (std::streamsize)(n * sizeof(T)));
+            if (!f) return false;
+            sum.add(v.data(), n * sizeof(T));
+        }
+        return true;
+    }
+};
+
 }  // namespace
 
 size_t expr_value_bytes(const ExprProgram& E) { return E.precision == SSCO_VALS_F32 ? 4 : 8; }
@@ -690,6 +747,80 @@ ssco_status ssco_expr_run(ssco_expr e, const void* leaf_vals, void* out_vals, vo
         E.last_error = "launch failed";
         return SSCO_ERR_CUDA;
     }
+    return SSCO_OK;
+}
+
+ssco_status ssco_expr_save(ssco_expr e, const char* path) {
+    if (!e || !path) return ssco::bad(SSCO_ERR_INVALID_ARG, "NULL argument");
+    const ssco::ExprProgram& E = e->E;
+    ssco::Out o;
+    o.f.open(path, std::ios::binary | std::ios::trunc);
+    if (!o.f) return ssco::bad(SSCO_ERR_INVALID_ARG, std::string("cannot open ") + path);
+    o.pod(ssco::kExprMagic);
+    o.pod(ssco::kExprVersion);
+    o.pod(E.B), o.pod(E.precision), o.pod(E.unit_coef);
+    o.pod(E.n_leaf_vals), o.pod(E.n_out_vals), o.pod(E.n_slots), o.pod(E.n_ops), o.pod(E.n_terms), o.pod(E.n_unrolled);
+    o.vec(E.lvl_begin), o.vec(E.term_off), o.vec(E.f1), o.vec(E.f2), o.vec(E.coef), o.vec(E.out_slot),
+        o.vec(E.out_coef);
+    o.pod((uint64_t)E.out_pat.size());
+    for (const ssco::ExprCsr& P : E.out_pat) o.pod(P.rows), o.pod(P.cols), o.vec(P.rp), o.vec(P.ci);
+    const uint64_t digest = o.sum.h;
+    o.f.write(reinterpret_cast<const char*>(&digest), sizeof(digest));
+    o.f.flush();
+    return o.f ? SSCO_OK : ssco::bad(SSCO_ERR_INVALID_ARG, "write failed");
+}
+
+ssco_status ssco_expr_load(const char* path, ssco_expr* out) {
+    if (!path || !out) return ssco::bad(SSCO_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    ssco::In in;
+    in.f.open(path, std::ios::binary | std::ios::ate);
+    if (!in.f) return ssco::bad(SSCO_ERR_INVALID_ARG, std::string("cannot open ") + path);
+    in.size = in.f.tellg();
+    in.f.seekg(0);
+    uint64_t magic = 0;
+    uint32_t ver = 0;
+    if (!in.pod(magic) || !in.pod(ver) || magic != ssco::kExprMagic || ver != ssco::kExprVersion)
+        return ssco::bad(SSCO_ERR_INVALID_ARG, "not an expression program file of this version");
+    ssco_expr e = new (std::nothrow) ssco_expr_s();
+    if (!e) return ssco::bad(SSCO_ERR_OOM, "host allocation failed");
+    ssco::ExprProgram& E = e->E;
+    bool ok = false;
+    try {
+        uint64_t n_pat = 0;
+        ok = in.pod(E.B) && in.pod(E.precision) && in.pod(E.unit_coef) && in.pod(E.n_leaf_vals) &&
+             in.pod(E.n_out_vals) && in.pod(E.n_slots) && in.pod(E.n_ops) && in.pod(E.n_terms) &&
+             in.pod(E.n_unrolled) && in.vec(E.lvl_begin) && in.vec(E.term_off) && in.vec(E.f1) && in.vec(E.f2) &&
+             in.vec(E.coef) && in.vec(E.out_slot) && in.vec(E.out_coef) && in.pod(n_pat) && n_pat < (1u << 20);
+        for (uint64_t k = 0; ok && k < n_pat; ++k) {
+            ssco::ExprCsr P;
+            ok = in.pod(P.rows) && in.pod(P.cols) && in.vec(P.rp) && in.vec(P.ci);
+            E.out_pat.push_back(std::move(P));
+        }
+    } catch (const std::exception&) {
+        ok = false;
+    }
+    const uint64_t got = in.sum.h;
+    uint64_t digest = 0;
+    char extra = 0;
+    ok = ok && (bool)in.f.read(reinterpret_cast<char*>(&digest), sizeof(digest)) && digest == got &&
+         !in.f.read(&extra, 1);
+    // the tables must describe a program the runner can execute safely
+    ok = ok && E.B >= 1 && E.B <= 65535 && (E.precision == SSCO_VALS_F64 || E.precision == SSCO_VALS_F32) &&
+         !E.lvl_begin.empty() && E.lvl_begin.back() == E.n_ops && (int64_t)E.term_off.size() == E.n_ops + 1 &&
+         E.term_off.back() == E.n_terms && (int64_t)E.f1.size() == E.n_terms && (int64_t)E.f2.size() == E.n_terms &&
+         (int64_t)E.coef.size() == E.n_terms && (int64_t)E.out_slot.size() == E.n_out_vals &&
+         (int64_t)E.out_coef.size() == E.n_out_vals && E.n_slots == 1 + E.n_leaf_vals + E.n_ops;
+    for (size_t l = 1; ok && l < E.lvl_begin.size(); ++l) ok = E.lvl_begin[l] >= E.lvl_begin[l - 1];
+    for (int64_t i = 0; ok && i < E.n_ops; ++i) ok = E.term_off[i + 1] >= E.term_off[i];
+    for (int64_t q = 0; ok && q < E.n_terms; ++q) ok = E.f1[q] >= 0 && E.f1[q] < E.n_slots && E.f2[q] >= 0 && E.f2[q] < E.n_slots;
+    for (int64_t j = 0; ok && j < E.n_out_vals; ++j) ok = E.out_slot[j] >= 0 && E.out_slot[j] < E.n_slots;
+    if (!ok) {
+        delete e;
+        return ssco::bad(SSCO_ERR_INVALID_ARG, "truncated, inconsistent or corrupt program file");
+    }
+    ssco::expr_layout_tables(E);
+    *out = e;
     return SSCO_OK;
 }
 

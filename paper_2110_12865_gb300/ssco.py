@@ -35,6 +35,7 @@ EXPORTED_SYMBOLS = [
     "ssco_cotan_weights", "ssco_tet_stiffness",
     "ssco_expr_compile", "ssco_expr_get_info", "ssco_expr_export", "ssco_expr_output_shape",
     "ssco_expr_output_pattern", "ssco_expr_bind", "ssco_expr_run", "ssco_expr_last_error", "ssco_expr_destroy",
+    "ssco_expr_save", "ssco_expr_load",
 ]
 KERNEL_KINDS = ["assemble", "front_small", "big_init", "big_kscatter", "big_update", "big_potrf", "big_syrk",
                 "fwd_solve", "bwd_solve", "resid", "check", "vector", "grad", "front_tiny", "big_trsm", "front_vec",
@@ -144,6 +145,8 @@ def load_library(path: str = LIB_PATH):
         "ssco_expr_bind": (i32, [vp, vp, vp, vp]),
         "ssco_expr_run": (i32, [vp, vp, vp, vp]),
         "ssco_expr_last_error": (C.c_char_p, [vp]),
+        "ssco_expr_save": (i32, [vp, C.c_char_p]),
+        "ssco_expr_load": (i32, [C.c_char_p, C.POINTER(vp)]),
         "ssco_expr_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -559,8 +562,11 @@ class ExprProgram:
     """A compiled expression: host tables, then (after bind) device tables
     and slot workspace owned by this object as torch tensors."""
 
-    def __init__(self, expr: Expr, outputs, batch, dtype, inline_terms=0):
+    def __init__(self, expr: Expr, outputs, batch, dtype, inline_terms=0, _handle=None):
         self.L = load_library()
+        if _handle is not None:
+            self._adopt(_handle)
+            return
         arr = (ExprNode * len(expr.nodes))()
         for i, (op, a, b, al, r, c, rp, ci, vm, nv) in enumerate(expr.nodes):
             arr[i].op, arr[i].a, arr[i].b, arr[i].alpha, arr[i].rows, arr[i].cols = op, a, b, al, r, c
@@ -576,13 +582,35 @@ class ExprProgram:
                                       int(inline_terms), C.byref(h))
         if st != SSCO_OK:
             raise SscoError(st, self.L.ssco_expr_last_error(None).decode())
+        self._adopt(h)
+
+    def _adopt(self, h):
         self._h = h
         inf = ExprInfo()
         self.L.ssco_expr_get_info(h, C.byref(inf))
         self.info = inf.as_dict()
-        self.batch = int(batch)
-        self.n_out = len(outs)
+        self.batch = int(self.info["batch"])
+        self.dtype = torch.float32 if self.info["precision"] == VALS_F32 else torch.float64
+        r = C.c_int32()
+        k = 0
+        while self.L.ssco_expr_output_shape(h, k, C.byref(r), None, None) == SSCO_OK:
+            k += 1
+        self.n_out = k
         self._tab = self._ws = None
+
+    def save(self, path):
+        st = self.L.ssco_expr_save(self._h, path.encode())
+        if st != SSCO_OK:
+            raise SscoError(st, self.L.ssco_expr_last_error(None).decode())
+
+    @classmethod
+    def load(cls, path):
+        L = load_library()
+        h = C.c_void_p()
+        st = L.ssco_expr_load(path.encode(), C.byref(h))
+        if st != SSCO_OK:
+            raise SscoError(st, L.ssco_expr_last_error(None).decode())
+        return cls(None, None, None, None, _handle=h)
 
     def __del__(self):
         if getattr(self, "_h", None):

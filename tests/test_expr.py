@@ -229,6 +229,32 @@ def test_shared_leaf_values_halve_the_symmetric_square(S):
         build_expr(S, [("leaf", n, n, rp, ci, vm, nv - 1)]).compile([0])   # vmap out of range
 
 
+def test_expr_program_save_load(S, tmp_path):
+    """A compiled program survives its file unchanged (info, every table,
+    output patterns); damaged, truncated or padded files are refused."""
+    nodes, outs, nv = random_expressions(40, 70, per_row=3)
+    prog = build_expr(S, nodes).compile(outs, batch=3, dtype=torch.float32, inline_terms=2)
+    f = str(tmp_path / "prog.bin")
+    prog.save(f)
+    q = S.ExprProgram.load(f)
+    assert q.info == prog.info and q.n_out == prog.n_out == len(outs) and q.dtype == torch.float32
+    for w in range(7):
+        assert np.array_equal(q.export(w), prog.export(w))
+    for k in range(len(outs)):
+        for a, b in zip(q.output_pattern(k), prog.output_pattern(k)):
+            assert np.array_equal(a, b)
+    raw = open(f, "rb").read()
+    mid = len(raw) // 2
+    bad = [b"garbage!" + raw[8:], raw[:mid] + bytes([raw[mid] ^ 1]) + raw[mid + 1:], raw[:-3], raw + b"\0"]
+    bad += [raw[:o] + b"\xff" * 8 + raw[o + 8:] for o in range(12, 120, 4)]
+    for i, blob in enumerate(bad):
+        g = str(tmp_path / f"bad{i}.bin")
+        open(g, "wb").write(blob)
+        with pytest.raises(S.SscoError) as ei:
+            S.ExprProgram.load(g)
+        assert ei.value.status == 1
+
+
 def test_expr_compile_rejects_malformed_nodes(S):
     rp, ci = np.array([0, 2, 3]), np.array([0, 1, 1])
     ok = ("leaf", 2, 2, rp, ci)
