@@ -5,7 +5,10 @@ and the CPU-baseline leg of ``bench.py``.  The library path never imports it.
 It shares nothing with the CUDA path except the seeded input generators.
 
 Each wrapper names the definition it follows; the arithmetic itself is in the
-C file (plain loops, FP64, ``-O2 -ffp-contract=off``).
+C file (plain loops, FP64, ``-O2 -ffp-contract=off``), except the
+sparse-expression evaluators at the end, which are plain Python dictionaries
+of entries (FP64) written from the definitions of sum, scaling, transpose and
+product.
 """
 from __future__ import annotations
 
