@@ -629,7 +629,7 @@ def _oracle_worker(barrier, chunk, queue):
         key = (q["name"], q["n"], q["m"])
         if key not in symbs:
             symbs[key] = O.Symbolic(O.permute(O.assemble(q, 0), q.perm))
-    barrier.wait()
+    barrier.wait(timeout=600)   # a worker that never arrives breaks the barrier: no hang
     t0 = time.perf_counter()
     for q in chunk:
         O.refactor_solve(q, 0, symb=symbs[(q["name"], q["n"], q["m"])])
@@ -657,9 +657,21 @@ def time_oracle_all_cores(items):
     procs = [ctx.Process(target=_oracle_worker, args=(barrier, c, queue)) for c in chunks]
     for pr in procs:
         pr.start()
-    times = [queue.get() for _ in procs]
-    for pr in procs:
-        pr.join()
+    import queue as _queue
+    times, deadline = [], time.monotonic() + 1800
+    try:
+        while len(times) < len(procs):
+            try:
+                times.append(queue.get(timeout=1.0))
+            except _queue.Empty:
+                dead = [pr.exitcode for pr in procs if pr.exitcode not in (None, 0)]
+                if dead or time.monotonic() > deadline:
+                    raise RuntimeError(f"oracle workers failed (exit codes {dead})" if dead else "oracle timed out")
+    finally:
+        for pr in procs:   # only the processes started here
+            if pr.is_alive() and len(times) < len(procs):
+                pr.terminate()
+            pr.join()
     return max(times), sum(times), len(procs)
 
 
