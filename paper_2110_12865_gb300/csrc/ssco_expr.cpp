@@ -806,14 +806,24 @@ ssco_status ssco_expr_load(const char* path, ssco_expr* out) {
     ok = ok && (bool)in.f.read(reinterpret_cast<char*>(&digest), sizeof(digest)) && digest == got &&
          !in.f.read(&extra, 1);
     // the tables must describe a program the runner can execute safely
+    // (counts first, so that no size below is negative and no .back() is
+    // taken of an empty table)
     ok = ok && E.B >= 1 && E.B <= 65535 && (E.precision == SSCO_VALS_F64 || E.precision == SSCO_VALS_F32) &&
-         !E.lvl_begin.empty() && E.lvl_begin.back() == E.n_ops && (int64_t)E.term_off.size() == E.n_ops + 1 &&
+         E.n_leaf_vals >= 0 && E.n_out_vals >= 0 && E.n_ops >= 0 && E.n_terms >= 0 &&
+         E.n_slots == 1 + E.n_leaf_vals + E.n_ops && !E.lvl_begin.empty() && E.lvl_begin.front() == 0 &&
+         E.lvl_begin.back() == E.n_ops && (int64_t)E.term_off.size() == E.n_ops + 1 && E.term_off.front() == 0 &&
          E.term_off.back() == E.n_terms && (int64_t)E.f1.size() == E.n_terms && (int64_t)E.f2.size() == E.n_terms &&
          (int64_t)E.coef.size() == E.n_terms && (int64_t)E.out_slot.size() == E.n_out_vals &&
-         (int64_t)E.out_coef.size() == E.n_out_vals && E.n_slots == 1 + E.n_leaf_vals + E.n_ops;
+         (int64_t)E.out_coef.size() == E.n_out_vals;
     for (size_t l = 1; ok && l < E.lvl_begin.size(); ++l) ok = E.lvl_begin[l] >= E.lvl_begin[l - 1];
     for (int64_t i = 0; ok && i < E.n_ops; ++i) ok = E.term_off[i + 1] >= E.term_off[i];
-    for (int64_t q = 0; ok && q < E.n_terms; ++q) ok = E.f1[q] >= 0 && E.f1[q] < E.n_slots && E.f2[q] >= 0 && E.f2[q] < E.n_slots;
+    // every term of a level reads only the constant, the leaves and the
+    // outputs of earlier levels (a level never reads its own or later slots)
+    for (size_t l = 0; ok && l + 1 < E.lvl_begin.size(); ++l) {
+        const int64_t lim = 1 + E.n_leaf_vals + E.lvl_begin[l];
+        for (int64_t q = E.term_off[E.lvl_begin[l]]; ok && q < E.term_off[E.lvl_begin[l + 1]]; ++q)
+            ok = E.f1[q] >= 0 && E.f1[q] < lim && E.f2[q] >= 0 && E.f2[q] < lim;
+    }
     for (int64_t j = 0; ok && j < E.n_out_vals; ++j) ok = E.out_slot[j] >= 0 && E.out_slot[j] < E.n_slots;
     if (!ok) {
         delete e;

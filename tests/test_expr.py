@@ -255,6 +255,105 @@ def test_expr_program_save_load(S, tmp_path):
         assert ei.value.status == 1
 
 
+def _fnv1a64(data: bytes) -> int:
+    h = 0xcbf29ce484222325
+    for c in data:
+        h = ((h ^ c) * 0x100000001b3) & 0xFFFFFFFFFFFFFFFF
+    return h
+
+
+def _parse_program_file(raw: bytes):
+    """Splits a program file into its header fields and tables (the layout
+    written by ssco_expr_save) so that a test can change one field and
+    re-digest the file, which the digest alone would otherwise refuse."""
+    import struct
+    off = 0
+    hdr = {}
+    for name, fmt in [("magic", "<Q"), ("ver", "<I"), ("B", "<i"), ("precision", "<i"), ("unit_coef", "<i"),
+                      ("n_leaf_vals", "<q"), ("n_out_vals", "<q"), ("n_slots", "<q"), ("n_ops", "<q"),
+                      ("n_terms", "<q"), ("n_unrolled", "<q")]:
+        hdr[name] = struct.unpack_from(fmt, raw, off)[0]
+        off += struct.calcsize(fmt)
+    vecs = {}
+    for name, dt in [("lvl_begin", np.int64), ("term_off", np.int64), ("f1", np.int32), ("f2", np.int32),
+                     ("coef", np.float64), ("out_slot", np.int32), ("out_coef", np.float64)]:
+        n = struct.unpack_from("<Q", raw, off)[0]
+        off += 8
+        vecs[name] = np.frombuffer(raw, dt, n, off).copy()
+        off += n * np.dtype(dt).itemsize
+    tail = raw[off:-8]     # output patterns, unchanged
+    return hdr, vecs, tail
+
+
+def _write_program_file(hdr, vecs, tail) -> bytes:
+    import struct
+    body = b"".join(struct.pack(fmt, hdr[name]) for name, fmt in [
+        ("magic", "<Q"), ("ver", "<I"), ("B", "<i"), ("precision", "<i"), ("unit_coef", "<i"),
+        ("n_leaf_vals", "<q"), ("n_out_vals", "<q"), ("n_slots", "<q"), ("n_ops", "<q"), ("n_terms", "<q"),
+        ("n_unrolled", "<q")])
+    for name in ["lvl_begin", "term_off", "f1", "f2", "coef", "out_slot", "out_coef"]:
+        v = vecs[name]
+        body += struct.pack("<Q", v.size) + v.tobytes()
+    body += tail
+    return body + struct.pack("<Q", _fnv1a64(body))
+
+
+def test_expr_program_load_rejects_redigested_bad_tables(S, tmp_path):
+    """The digest only detects damage: a file whose digest was recomputed
+    after a field was changed must still be refused when its tables could
+    make the runner read or write outside its buffers (negative counts or
+    offsets, a level that reads its own or a later level's outputs)."""
+    nodes, outs, nv = random_expressions(30, 50, per_row=3)
+    prog = build_expr(S, nodes).compile(outs, batch=2)
+    f = str(tmp_path / "prog.bin")
+    prog.save(f)
+    raw = open(f, "rb").read()
+    hdr, vecs, tail = _parse_program_file(raw)
+    assert _write_program_file(hdr, vecs, tail) == raw          # the parser reproduces the file
+    assert hdr["n_ops"] > 0 and vecs["lvl_begin"].size >= 3
+
+    def refused(h, v):
+        g = str(tmp_path / "bad.bin")
+        open(g, "wb").write(_write_program_file(h, v, tail))
+        with pytest.raises(S.SscoError) as ei:
+            S.ExprProgram.load(g)
+        assert ei.value.status == 1
+
+    def mod(**kw):
+        h, v = dict(hdr), {k: a.copy() for k, a in vecs.items()}
+        for k, val in kw.items():
+            if k in h:
+                h[k] = val
+            else:
+                v[k] = val
+        return h, v
+
+    # a negative leaf count with a slot count that still adds up
+    refused(*mod(n_leaf_vals=-1, n_slots=hdr["n_ops"]))
+    refused(*mod(n_out_vals=-1))
+    # no ops and an empty term offset table (no .back() of an empty vector)
+    refused(*mod(n_ops=-1, n_slots=hdr["n_leaf_vals"], term_off=np.zeros(0, np.int64),
+                 lvl_begin=np.array([0, -1], np.int64)))
+    refused(*mod(n_terms=-1))
+    # level and term tables that start below zero
+    lb = vecs["lvl_begin"].copy()
+    lb[0] = -1
+    refused(*mod(lvl_begin=lb))
+    to = vecs["term_off"].copy()
+    to[0] = -1
+    refused(*mod(term_off=to))
+    # a term of level 0 that reads an op slot (its own level's output)
+    f1 = vecs["f1"].copy()
+    f1[0] = 1 + hdr["n_leaf_vals"]
+    refused(*mod(f1=f1))
+    # a term of the last level that reads the last level's own first slot
+    lvl = vecs["lvl_begin"]
+    q_last = vecs["term_off"][lvl[-2]]
+    f2 = vecs["f2"].copy()
+    f2[q_last] = 1 + hdr["n_leaf_vals"] + lvl[-2]
+    refused(*mod(f2=f2))
+
+
 def test_expr_compile_rejects_malformed_nodes(S):
     rp, ci = np.array([0, 2, 3]), np.array([0, 1, 1])
     ok = ("leaf", 2, 2, rp, ci)
