@@ -167,6 +167,10 @@ typedef struct {
     int64_t tune_split_rows; /* fronts this large take the multi-CTA solves  */
     int64_t tune_warp_front_max; /* small-front classes factored warp-per-front */
     int64_t tune_cluster_rows;   /* fronts this large: one CTA cluster per solve */
+    int64_t tune_flow;           /* persistent dataflow launches: bit 0 solve sweeps,
+                                    bit 1 small-front factorization                 */
+    int64_t flow_fact_fronts;    /* fronts factored by the dataflow launches         */
+    int64_t flow_solve_fronts;   /* fronts solved by the dataflow sweeps             */
 } ssco_info;
 
 /* ssco_plan_export selectors (host copies; sizes in elements).          */
@@ -211,19 +215,33 @@ ssco_status ssco_plan_export(ssco_plan plan, int32_t what, void* host_buf, size_
 ssco_status ssco_bind(ssco_plan plan, void* dev_tables, size_t tables_bytes, void* dev_workspace,
                       size_t workspace_bytes, void* stream);
 
-/* Numeric phase: assemble K from vals (device, [B][m], dtype
+/* Defined by: the assembly K = A^T diag(w) A + shift*I (or the element-block
+ * sum of Sec. 4.2.4) evaluated through the grouped leaf tables of Sec. 4.3
+ * and 4.4, then the Cholesky factor P K P^T = L L^T by its textbook
+ * definition (the paper factors nothing itself: Sec. 5.5 and 5.6 time an
+ * external sparse factorization of such systems), scheduled as the level
+ * groups of Sec. 4.3.
+ * Numeric phase: assemble K from vals (device, [B][m], dtype
  * SSCO_VALS_F64/F32) and shift (device, double [n_systems]), then factor.
  * Asynchronous.  A non-positive pivot is recorded per system (read it with
  * ssco_status_get), never branched on. */
 ssco_status ssco_numeric(ssco_plan plan, const void* vals, int32_t vals_dtype, const double* shift,
                          void* stream);
 
-/* x = K^-1 b for every system (device, double [B][n] each; b and x may not
+/* Defined by: forward substitution L y = P b and back substitution
+ * L^T z = y, x = P^T z, with the factor of ssco_numeric, level by level in
+ * the order of Sec. 4.3 (reversed for L^T); the FP32 form adds iterative
+ * refinement in FP64, which the paper does not use.
+ * x = K^-1 b for every system (device, double [B][n] each; b and x may not
  * alias).  In SSCO_FP32_REFINE mode the refinement loop runs on the device;
  * the host reads one flag per iteration, so this call synchronizes `stream`. */
 ssco_status ssco_solve(ssco_plan plan, const double* b, double* x, void* stream);
 
-/* Adjoint of x = K(vals, shift)^-1 b for a scalar loss with dloss/dx = xbar:
+/* Defined by: the reverse-mode derivative of x = K^-1 b (the derivatives
+ * the paper obtains by symbolic differentiation of expression graphs, Sec.
+ * 4.9, written out by hand for this program: one more solve with the same
+ * factor, then one product per value).
+ * Adjoint of x = K(vals, shift)^-1 b for a scalar loss with dloss/dx = xbar:
  * mu = K^-1 xbar (same factor, same refinement), then
  *   vals_bar_e = -(A mu)_e (A x)_e            (ATWA)
  *   vals_bar_e = -mu_e^T K_e^0 x_e            (ELEM, free DOFs)
@@ -263,6 +281,23 @@ ssco_status ssco_export_K(ssco_plan plan, double* host_out, void* stream);
  * receives the best step time. */
 ssco_status ssco_autotune(ssco_plan plan, const void* vals, int32_t vals_dtype, const double* shift, const double* b,
                           double* x, int32_t reps, void* stream, double* best_ms);
+
+/* Dataflow launches (Sec. 4.3's level groups, scheduled by dependency).
+ * The fronts below every big front are factored, and the fronts of at most
+ * 256 rows solved, by persistent launches that walk all their levels: each
+ * front (per value set) is an item taken in level order from a ticket
+ * counter, and it waits only for the done flags of its children (factor,
+ * forward sweep) or of its parent (backward sweep), never for a whole level.
+ * flow: bit 0 the solve sweeps, bit 1 the factorization (default 3; 0 = one
+ * launch per level and size class).  max_polls bounds every wait (polls of
+ * about 256 ns; 0 = keep the current bound, default 2^22): a wait that runs
+ * out raises the plan's device error, the launch ends early and
+ * ssco_status_get reports SSCO_ERR_TIMEOUT for every system (the results of
+ * that call are invalid).  stall_item >= 0 is a test hook: that item of the
+ * first dataflow launch of each numeric (else of each forward sweep) waits
+ * on a flag that nothing sets, so the bounded wait runs out; -1 = off.
+ * Host only; invalidates the captured graph of ssco_graph_run. */
+ssco_status ssco_set_flow(ssco_plan plan, int32_t flow, int64_t max_polls, int32_t stall_item);
 
 /* ssco_numeric + ssco_solve as ONE CUDA graph: the refinement loop runs on
  * the device as a conditional WHILE node (no host round trip per

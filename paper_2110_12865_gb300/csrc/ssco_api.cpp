@@ -72,11 +72,16 @@ void set_dev_tables(Plan& P) {
     d.tiny_off = tab_ptr<int32_t>(P, P.toff.tiny_off);
     d.tiny_prog = tab_ptr<int32_t>(P, P.toff.tiny_prog);
     d.tiny_prog_off = tab_ptr<int64_t>(P, P.toff.tiny_prog_off);
+    d.flow_fact = tab_ptr<int32_t>(P, P.toff.flow_fact);
+    d.flow_fslot = tab_ptr<int32_t>(P, P.toff.flow_fslot);
+    d.flow_solve = tab_ptr<int32_t>(P, P.toff.flow_solve);
+    d.flow_sslot = tab_ptr<int32_t>(P, P.toff.flow_sslot);
+    d.flow_rest = tab_ptr<int32_t>(P, P.toff.flow_rest);
 }
 
 // ----- plan file (de)serialization -----------------------------------------
 constexpr uint64_t kMagic = 0x314F4353534F4353ull;  // "SCOSSCO1"
-constexpr uint32_t kVersion = 11;
+constexpr uint32_t kVersion = 12;
 
 // 64-bit FNV-1a (Fowler, Noll, Vo) over the payload bytes: the file ends
 // with the digest, so a plan whose tables were damaged after saving is
@@ -240,6 +245,9 @@ ssco_status ssco_plan_info(ssco_plan h, ssco_info* o) {
     o->tune_split_rows = P.tune.split_rows;
     o->tune_warp_front_max = P.tune.warp_front_max;
     o->tune_cluster_rows = P.tune.cluster_rows;
+    o->tune_flow = P.tune.flow;
+    o->flow_fact_fronts = (int64_t)P.flow_fact.size();
+    o->flow_solve_fronts = (int64_t)P.flow_solve.size();
     return SSCO_OK;
 }
 
@@ -504,6 +512,18 @@ ssco_status ssco_refactor_solve_host(ssco_plan h, const void* vals, int32_t vals
 }
 
 int64_t ssco_last_launch_count(ssco_plan h) { return h ? h->P.launches : 0; }
+
+ssco_status ssco_set_flow(ssco_plan h, int32_t flow, int64_t max_polls, int32_t stall_item) {
+    if (!h) return fail(h, SSCO_ERR_INVALID_ARG, "NULL plan");
+    if (flow < 0 || flow > 3 || max_polls < 0 || max_polls > 0xFFFFFFFFll || stall_item < -1)
+        return fail(h, SSCO_ERR_INVALID_ARG, "flow must be 0..3, max_polls 0..2^32-1, stall_item >= -1");
+    Plan& P = h->P;
+    P.tune.flow = flow;
+    if (max_polls > 0) P.tune.flow_polls = (uint32_t)max_polls;
+    P.tune.flow_stall = stall_item;
+    graph_release(P);
+    return SSCO_OK;
+}
 
 ssco_status ssco_solve_noalloc(ssco_plan h, const double* b, double* x, void* stream) {
     if (!h || !b || !x) return fail(h, SSCO_ERR_INVALID_ARG, "NULL argument");

@@ -72,6 +72,17 @@ struct LaunchList {
     int32_t max_klist;        // big: max K entries per front
 };
 
+// One persistent launch of the small-front factorization dataflow: the
+// fronts flow_fact[off .. off+count), level ascending, each factored for V
+// value sets per item by a CTA of nw warps.  A front's group holds no front
+// larger than the group's rmax, and every child of a front sits in the same
+// or an earlier group (an earlier group has finished before the launch).
+struct FlowGroup {
+    int32_t off, count;
+    int32_t rmax, V, nw;
+    int32_t pad;
+};
+
 // Typed device pointers into the bound table buffer.
 struct DevTables {
     const FrontDesc* fronts;
@@ -108,6 +119,11 @@ struct DevTables {
     const int32_t* tiny_off;    // [n_tiny+1] offsets into tiny_list
     const int32_t* tiny_prog;   // per-subtree programs
     const int64_t* tiny_prog_off;
+    const int32_t* flow_fact;   // factor dataflow fronts, group-major, level ascending
+    const int32_t* flow_fslot;  // per front: position in flow_fact, or -1
+    const int32_t* flow_solve;  // solve dataflow fronts, level ascending
+    const int32_t* flow_sslot;  // per front: position in flow_solve, or -1
+    const int32_t* flow_rest;   // front lists of the per-level launches around the dataflow
 };
 
 // Byte offsets of every region of the caller's workspace.
@@ -117,6 +133,7 @@ struct WsLayout {
     size_t resid, bnorm, r1, r2, sigma, sbar;
     size_t st_vals, st_shift, st_b, st_x;
     size_t tcpack;
+    size_t flow_fact, flow_solve;  // dataflow tickets (32 words) + done flags [slot][B]
     size_t total;
 };
 
@@ -141,6 +158,11 @@ struct Tunables {
     int32_t cluster_rows = 512;    // ... below that, from this many rows: one CTA cluster per front
     int32_t warp_front_max = 0;    // small-front classes up to this size: one warp per front (levels
                                    // of >= warp_items fronts x value sets; autotuner option)
+    int32_t flow = 3;              // persistent dataflow launches: bit 0 the solve sweeps, bit 1 the
+                                   // small-front factorization (0 = one launch per level and class)
+    uint32_t flow_polls = 1u << 22;  // bound of every dataflow wait (polls of ~256 ns)
+    int32_t flow_stall = -1;       // test hook: this item of the first dataflow launch waits on a
+                                   // flag that nothing sets (the bounded-wait path); -1 = off
     int32_t tuned = 0;
 };
 
@@ -196,6 +218,12 @@ struct Plan {
     int64_t panel_total = 0, upd_total = 0, pvec_total = 0;
     int64_t tc_pack_total = 0;  // floats per instance of tensor-core operand blocks (0 = none)
     int32_t max_rows = 0;
+    // dataflow schedules, derived from the partition by build_flow (not
+    // stored in plan files)
+    std::vector<int32_t> flow_fact, flow_fslot, flow_solve, flow_sslot, flow_rest;
+    std::vector<FlowGroup> fact_groups;
+    int32_t flow_solve_rmax = 0;
+    std::vector<LaunchList> fact_rest, solve_rest;  // per level, around the dataflow (into flow_rest)
 
     // assembly
     std::vector<AsmGroup> groups;
@@ -228,7 +256,7 @@ struct Plan {
             asm_idx, asm_coef, sp_rowptr, sp_col, sp_slot, perm, row_sys, sys_n_off, g_rowptr,
             g_colind, g_aval, g_row_sys, e_dofs, e_K0, e_sys, e_off, e_k0off, e_dim, shifted,
             g_rows_all, e_elems_all, tiny_list, tiny_off, tiny_prog, tiny_prog_off, blk_dofs, blk_off,
-            blk_dim, blk_vbase;
+            blk_dim, blk_vbase, flow_fact, flow_fslot, flow_solve, flow_sslot, flow_rest;
     } toff{};
     WsLayout ws{};
     uint8_t* d_tab = nullptr;
@@ -266,6 +294,7 @@ struct Plan {
 // symbolic phase (ssco_symbolic.cpp)
 ssco_status analyze_impl(const ssco_pattern* const* pats, int32_t n_pats, const ssco_op* op,
                          Plan& P);
+void build_flow(Plan& P);
 void build_blob(Plan& P);
 void compute_ws_layout(Plan& P);
 void export_L_pattern(const Plan& P, std::vector<int64_t>* colptr, std::vector<int32_t>* rowind);

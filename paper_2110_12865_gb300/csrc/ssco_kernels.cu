@@ -399,6 +399,18 @@ template <>
 struct VecOf<double, 2> {
     typedef double2 type;
 };
+template <>
+struct VecOf<float, 2> {
+    typedef float2 type;
+};
+template <>
+struct VecOf<float, 1> {
+    typedef float type;
+};
+template <>
+struct VecOf<double, 1> {
+    typedef double type;
+};
 
 template <class T, int V>
 __device__ __forceinline__ void vld(const T* p, T (&x)[V]) {
@@ -2082,6 +2094,498 @@ __global__ void __launch_bounds__(256) k_bwd_warp(const DevTables t, const int32
 }
 
 // --------------------------------------------------------------------------
+// Dataflow launches.  A persistent grid walks a level-ordered list of items
+// (a front for one value set, or for a group of V value sets); a warp or CTA
+// takes the next item from a ticket counter and waits only for the items it
+// depends on (its children in the factorization and the forward sweep, its
+// parent in the backward sweep), whose done flags it polls.  Tickets are
+// taken in list order by running warps or CTAs only, and an item depends
+// only on earlier items, so the earliest unfinished item never waits: the
+// schedule cannot deadlock, whatever number of CTAs is resident.  Every wait
+// is bounded: on expiry (or once another waiter has given up) the waiter
+// raises the plan's device error word (status TIMEOUT) and leaves the launch.
+// The region of a launch: [0..31] tickets (word 31 is never set: the test
+// hook waits on it), then done flags [slot][B].
+// --------------------------------------------------------------------------
+constexpr int kFlowFlags = 32;
+
+__device__ __forceinline__ int32_t flow_ld_acquire(const int32_t* p) {
+    int32_t v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void flow_st_release(int32_t* p, int32_t v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+// true once *flag >= want; false after max_polls polls, or as soon as
+// another waiter has raised *dev_err.
+__device__ bool flow_wait(const int32_t* flag, int32_t want, const int32_t* dev_err, uint32_t max_polls) {
+    for (uint32_t it = 0;; ++it) {
+        if (flow_ld_acquire(flag) >= want) return true;
+        if (it >= max_polls || *(volatile const int32_t*)dev_err) return false;
+        __nanosleep(it < 8 ? 64 : 256);
+    }
+}
+
+// Forward sweep over the dataflow fronts, one warp per (front, value set):
+// the k_fwd_warp arithmetic, after the children's done flags.  Values that
+// other warps of this launch wrote (the children's passing vectors) are read
+// past L1 (ld.global.cg).
+template <class T>
+__global__ void __launch_bounds__(256) k_flow_fwd(const DevTables t, int32_t n_front, int32_t B, int32_t rmax,
+                                                  const T* __restrict__ panel, int64_t panel_total,
+                                                  T* __restrict__ vec, int64_t n, T* __restrict__ pvec,
+                                                  int64_t pvec_total, const int32_t* __restrict__ active,
+                                                  int32_t n_pats, int32_t* __restrict__ flow,
+                                                  int32_t* __restrict__ dev_err, uint32_t max_polls, int32_t stall) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    T* v = reinterpret_cast<T*>(smem_raw) + (int64_t)wib * rmax;
+    int32_t* flags = flow + kFlowFlags;
+    const int64_t n_items = (int64_t)n_front * B;
+    for (;;) {
+        int64_t item = 0;
+        if (lane == 0) item = atomicAdd(flow, 1);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= n_items) return;
+        const int pos = (int)(item / B), b = (int)(item - (int64_t)pos * B);
+        const FrontDesc d = t.fronts[t.flow_solve[pos]];
+        if (active && !active[(int64_t)b * n_pats + d.sys]) continue;
+        bool ok = true;
+        if (item == stall) ok = flow_wait(flow + 31, 1, dev_err, max_polls);
+        for (int c = lane; ok && c < d.nchild; c += 32) {
+            const int sl = t.flow_sslot[t.child_ids[d.child_off + c]];
+            if (sl >= 0) ok = flow_wait(flags + (int64_t)sl * B + b, 1, dev_err, max_polls);
+        }
+        if (!__all_sync(0xffffffffu, ok)) {
+            if (lane == 0) atomicExch(dev_err, 1);
+            return;
+        }
+        const int r = d.r, w = d.w;
+        T* vb = vec + (int64_t)b * n;
+        const T* Pb = panel + (int64_t)b * panel_total + d.panel_off;
+        T* pv = pvec + (int64_t)b * pvec_total;
+        for (int k = lane; k < r; k += 32) v[k] = k < w ? __ldcg(vb + d.f + k) : T(0);
+        for (int c = 0; c < d.nchild; ++c) {
+            __syncwarp();
+            const FrontDesc cd = t.fronts[t.child_ids[d.child_off + c]];
+            const int rc = cd.r - cd.w;
+            const int32_t* map = t.relmap + cd.relmap_off;
+            for (int k = lane; k < rc; k += 32) v[map[k]] += __ldcg(pv + cd.pvec_off + k);
+        }
+        __syncwarp();
+        for (int jb = 0; jb < w; jb += 32) {
+            const int nbk = min(32, w - jb);
+            T a[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                a[j] = (j < nbk && lane < nbk) ? Pb[(int64_t)(jb + j) * r + jb + lane] : T(0);
+            T dl = T(1);
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                if (lane == j && j < nbk) dl = a[j];
+            const T dinv = T(1) / dl;
+            T val = lane < nbk ? v[jb + lane] : T(0);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                if (j < nbk) {
+                    const T yj = __shfl_sync(0xffffffffu, val, j) * __shfl_sync(0xffffffffu, dinv, j);
+                    if (lane == j)
+                        val = yj;
+                    else if (lane > j)
+                        val -= a[j] * yj;
+                }
+            }
+            if (lane < nbk) v[jb + lane] = val;
+            __syncwarp();
+            for (int i0 = jb + nbk; i0 < r; i0 += 32) {
+                const int i = i0 + lane;
+                if (i < r) {
+                    const T* col = Pb + (int64_t)jb * r + i;
+                    T acc[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) acc[u] = T(0);
+                    int j = 0;
+                    for (; j + 7 < nbk; j += 8) {
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) acc[u] += col[(int64_t)(j + u) * r] * v[jb + j + u];
+                    }
+                    for (; j < nbk; ++j) acc[0] += col[(int64_t)j * r] * v[jb + j];
+                    v[i] -= ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+                }
+            }
+            __syncwarp();
+        }
+        for (int k = lane; k < w; k += 32) vb[d.f + k] = v[k];
+        for (int k = lane; k < r - w; k += 32) pv[d.pvec_off + k] = v[w + k];
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence();
+            flow_st_release(flags + (int64_t)pos * B + b, 1);
+        }
+    }
+}
+
+// Backward sweep over the dataflow fronts (parents first), one warp per
+// (front, value set): the k_bwd_warp arithmetic, after the parent's done
+// flag (which implies every ancestor's: each waited for its own parent).
+template <class T>
+__global__ void __launch_bounds__(256) k_flow_bwd(const DevTables t, int32_t n_front, int32_t B, int32_t rmax,
+                                                  const T* __restrict__ panel, int64_t panel_total,
+                                                  T* __restrict__ vec, int64_t n, const int32_t* __restrict__ active,
+                                                  int32_t n_pats, int32_t* __restrict__ flow,
+                                                  int32_t* __restrict__ dev_err, uint32_t max_polls) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    T* v = reinterpret_cast<T*>(smem_raw) + (int64_t)wib * rmax;
+    int32_t* flags = flow + kFlowFlags;
+    const int64_t n_items = (int64_t)n_front * B;
+    for (;;) {
+        int64_t item = 0;
+        if (lane == 0) item = atomicAdd(flow + 1, 1);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= n_items) return;
+        const int64_t q = n_items - 1 - item;
+        const int pos = (int)(q / B), b = (int)(q - (int64_t)pos * B);
+        const FrontDesc d = t.fronts[t.flow_solve[pos]];
+        if (active && !active[(int64_t)b * n_pats + d.sys]) continue;
+        bool ok = true;
+        if (d.parent >= 0) {
+            const int sl = t.flow_sslot[d.parent];
+            if (sl >= 0) ok = flow_wait(flags + (int64_t)sl * B + b, 2, dev_err, max_polls);
+        }
+        if (!__all_sync(0xffffffffu, ok)) {
+            if (lane == 0) atomicExch(dev_err, 1);
+            return;
+        }
+        const int r = d.r, w = d.w;
+        T* vb = vec + (int64_t)b * n;
+        const T* Pb = panel + (int64_t)b * panel_total + d.panel_off;
+        const int32_t* rows = t.rows + d.rows_off;
+        for (int k = lane; k < r; k += 32) v[k] = __ldcg(vb + (k < w ? d.f + k : rows[k]));
+        __syncwarp();
+        const int nblk = (w + 31) / 32;
+        for (int bi = nblk - 1; bi >= 0; --bi) {
+            const int jb = bi * 32;
+            const int nbk = min(32, w - jb);
+            T dot = T(0);
+            if (lane < nbk) {
+                const T* col = Pb + (int64_t)(jb + lane) * r;
+                T d1 = T(0), d2 = T(0), d3 = T(0);
+                int i = jb + nbk;
+                for (; i + 3 < r; i += 4) {
+                    dot += col[i] * v[i];
+                    d1 += col[i + 1] * v[i + 1];
+                    d2 += col[i + 2] * v[i + 2];
+                    d3 += col[i + 3] * v[i + 3];
+                }
+                for (; i < r; ++i) dot += col[i] * v[i];
+                dot += d1 + d2 + d3;
+            }
+            T a[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                a[j] = (lane < nbk && j < nbk && j >= lane) ? Pb[(int64_t)(jb + lane) * r + jb + j] : T(0);
+            T val = lane < nbk ? v[jb + lane] - dot : T(0);
+#pragma unroll
+            for (int j = 31; j >= 0; --j) {
+                if (j < nbk) {
+                    const T dj = __shfl_sync(0xffffffffu, a[j], j);
+                    const T xj = __shfl_sync(0xffffffffu, val, j) / dj;
+                    if (lane == j)
+                        val = xj;
+                    else if (lane < j)
+                        val -= a[j] * xj;
+                }
+            }
+            if (lane < nbk) v[jb + lane] = val;
+            __syncwarp();
+        }
+        for (int k = lane; k < w; k += 32) vb[d.f + k] = v[k];
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence();
+            flow_st_release(flags + (int64_t)pos * B + b, 2);
+        }
+    }
+}
+
+// Small-front factorization as a dataflow launch: one CTA per item (front,
+// V consecutive value sets interleaved entry by entry in shared memory, so
+// one vector access serves all V).  Per item: zero the packed triangle and
+// gather the front's K entries (independent of the children), wait for the
+// children of this group, add their update matrices through the relative
+// maps, then a blocked right-looking partial Cholesky in panels of kFlowNB
+// columns with three barriers per panel: (1) the panel's diagonal block is
+// factored in registers with warp shuffles (lane = row x value set; V / 2
+// warps) and its L kept in shared memory; (2) every thread solves rows below
+// the block against it (a triangular solve per row, L read as broadcasts);
+// (3) the trailing triangle takes one rank-kFlowNB update in register tiles.
+// Finally the panel and the update matrix go to global memory and the
+// item's done flag is released.
+constexpr int kFlowNB = 16;
+
+template <class T, int V>
+__global__ void __launch_bounds__(256) k_front_flow(const DevTables t, int32_t off, int32_t count, int32_t B,
+                                                    const double* __restrict__ K, int64_t nnzK,
+                                                    T* __restrict__ panel, int64_t panel_total,
+                                                    T* __restrict__ upd, int64_t upd_total,
+                                                    int32_t* __restrict__ bad_col, int32_t n_pats,
+                                                    int32_t* __restrict__ flow, int32_t ticket,
+                                                    int32_t* __restrict__ dev_err, uint32_t max_polls,
+                                                    int32_t stall) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int NB = kFlowNB;
+    constexpr int CB = V == 1 ? 4 : 2;  // trailing-update columns per thread (rows: 4)
+    __shared__ int64_t s_item;
+    __shared__ int s_ok;
+    T* Ld = reinterpret_cast<T*>(smem_raw);  // [NB][NB][V] L of the diagonal block
+    T* Li = Ld + NB * NB * V;                // [NB][V] reciprocals of its diagonal
+    T* F = Li + NB * V;                      // packed lower triangle x V, then kSmallPad x V zeros
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    int32_t* flags = flow + kFlowFlags;
+    const int nG = (B + V - 1) / V;
+    const int64_t n_items = (int64_t)count * nG;
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) {
+            s_item = atomicAdd(flow + ticket, 1);
+            s_ok = 1;
+        }
+        __syncthreads();
+        const int64_t item = s_item;
+        if (item >= n_items) return;
+        const int q = (int)(item / nG), g = (int)(item - (int64_t)q * nG);
+        const int b0 = g * V, nv = min(V, B - b0);
+        const FrontDesc d = t.fronts[t.flow_fact[off + q]];
+        const int r = d.r, w = d.w;
+        const int npk = r * (r + 1) / 2 + kSmallPad;
+        for (int e = tid; e < npk * V; e += nth) F[e] = T(0);
+        __syncthreads();
+        {
+            const int32_t* kl = t.klist + 2 * d.klist_off;
+            for (int e = tid; e < d.klist_n; e += nth) {
+                const int pos = kl[2 * e + 1], slot = kl[2 * e];
+                const int col = pos / r, row = pos - col * r;
+                T* dst = F + (int64_t)(packed_col(col, r) + row - col) * V;
+#pragma unroll
+                for (int v = 0; v < V; ++v)
+                    if (v < nv) dst[v] = (T)K[(int64_t)(b0 + v) * nnzK + slot];
+            }
+        }
+        if (warp == 0) {
+            bool ok = true;
+            if (item == stall) ok = flow_wait(flow + 31, 1, dev_err, max_polls);
+            for (int c = lane; ok && c < d.nchild; c += 32) {
+                const int sl = t.flow_fslot[t.child_ids[d.child_off + c]];
+                if (sl >= off && sl < off + count) ok = flow_wait(flags + (int64_t)sl * B + g, 1, dev_err, max_polls);
+            }
+            if (!__all_sync(0xffffffffu, ok) && lane == 0) {
+                atomicExch(dev_err, 1);
+                s_ok = 0;
+            }
+        }
+        __syncthreads();
+        if (!s_ok) return;
+        // children's update matrices (written by other CTAs: read past L1)
+        for (int c = 0; c < d.nchild; ++c) {
+            const FrontDesc cd = t.fronts[t.child_ids[d.child_off + c]];
+            const int rc = cd.r - cd.w;
+            const int32_t* map = t.relmap + cd.relmap_off;
+            const T* S0 = upd + (int64_t)b0 * upd_total + cd.upd_off;
+            for (int kk = warp; kk < rc; kk += nw) {
+                const int mk = map[kk];
+                T* Fk = F + (int64_t)(packed_col(mk, r) - mk) * V;
+                const T* Sk = S0 + (int64_t)kk * rc;
+                for (int i0 = kk; i0 < rc; i0 += 128) {
+                    int mi[4];
+                    T sv[4][V];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int ii = i0 + lane + 32 * u;
+                        mi[u] = ii < rc ? map[ii] : -1;
+#pragma unroll
+                        for (int v = 0; v < V; ++v)
+                            sv[u][v] = (ii < rc && v < nv) ? __ldcg(Sk + (int64_t)v * upd_total + ii) : T(0);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        if (mi[u] < 0) continue;
+                        T x[V];
+                        vld<T, V>(Fk + (int64_t)mi[u] * V, x);
+#pragma unroll
+                        for (int v = 0; v < V; ++v) x[v] += sv[u][v];
+                        vst<T, V>(Fk + (int64_t)mi[u] * V, x);
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        const int n_off = (int)t.sys_n_off[d.sys];
+        const int dwarps = V >= 2 ? V / 2 : 1;  // warps factoring the diagonal block
+        for (int j0 = 0; j0 < w; j0 += NB) {
+            const int nb = min(NB, w - j0), j1 = j0 + nb;
+            // (1) diagonal block: lane = (row i, value set v)
+            if (warp < dwarps) {
+                const int i = lane & 15, hi = lane & 16;
+                const int v = V >= 2 ? 2 * warp + (lane >> 4) : 0;
+                T a[NB];
+#pragma unroll
+                for (int k = 0; k < NB; ++k)
+                    a[k] = (k < nb && k <= i && i < nb) ? F[(int64_t)(packed_col(j0 + k, r) + i - k) * V + v] : T(0);
+#pragma unroll
+                for (int j = 0; j < NB; ++j) {
+                    if (j < nb) {
+                        T dj = __shfl_sync(0xffffffffu, a[j], j + hi);
+                        if (!(dj > T(0))) {
+                            if (i == j && v < nv && (V >= 2 || hi == 0))
+                                atomicMin(&bad_col[(int64_t)(b0 + v) * n_pats + d.sys], d.f + j0 + j - n_off);
+                            dj = T(1);
+                        }
+                        const T lj = sqrt(dj), inv = T(1) / lj;
+                        if (i == j)
+                            a[j] = lj;
+                        else if (i > j)
+                            a[j] *= inv;
+#pragma unroll
+                        for (int k = j + 1; k < NB; ++k) {
+                            const T lk = __shfl_sync(0xffffffffu, a[j], k + hi);
+                            if (i >= k) a[k] -= a[j] * lk;
+                        }
+                    }
+                }
+                if (i < nb && (V >= 2 || hi == 0)) {
+#pragma unroll
+                    for (int k = 0; k < NB; ++k) {
+                        if (k <= i) {
+                            Ld[(i * NB + k) * V + v] = a[k];
+                            F[(int64_t)(packed_col(j0 + k, r) + i - k) * V + v] = a[k];
+                        }
+                    }
+                    Li[i * V + v] = T(1) / a[i];
+                }
+            }
+            __syncthreads();
+            // (2) rows below the block: x := x L^{-T}
+            for (int i = j1 + tid; i < r; i += nth) {
+                T x[NB][V];
+#pragma unroll
+                for (int k = 0; k < NB; ++k)
+                    if (k < nb) vld<T, V>(F + (int64_t)(packed_col(j0 + k, r) + i - j0 - k) * V, x[k]);
+#pragma unroll
+                for (int k = 0; k < NB; ++k) {
+                    if (k < nb) {
+#pragma unroll
+                        for (int m = 0; m < k; ++m) {
+                            T l[V];
+                            vld<T, V>(Ld + (k * NB + m) * V, l);
+#pragma unroll
+                            for (int v = 0; v < V; ++v) x[k][v] -= x[m][v] * l[v];
+                        }
+                        T iv[V];
+                        vld<T, V>(Li + k * V, iv);
+#pragma unroll
+                        for (int v = 0; v < V; ++v) x[k][v] *= iv[v];
+                        vst<T, V>(F + (int64_t)(packed_col(j0 + k, r) + i - j0 - k) * V, x[k]);
+                    }
+                }
+            }
+            __syncthreads();
+            // (3) trailing triangle: F[i, k] -= L[i, j0:j1] L[k, j0:j1]^T
+            const int m = r - j1;
+            if (m > 0) {
+                const int tx = tid & 15, ty = tid >> 4, ny = nth >> 4;
+                const int tk_cols = CB * ny;
+                for (int c0 = 0; c0 < m; c0 += tk_cols) {
+                    for (int r0 = (c0 / 64) * 64; r0 < m; r0 += 64) {
+                        T acc[4][CB][V];
+#pragma unroll
+                        for (int a = 0; a < 4; ++a)
+#pragma unroll
+                            for (int c = 0; c < CB; ++c)
+#pragma unroll
+                                for (int v = 0; v < V; ++v) acc[a][c][v] = T(0);
+                        int ii[4], kk[CB];
+#pragma unroll
+                        for (int a = 0; a < 4; ++a) ii[a] = j1 + r0 + tx + 16 * a;
+#pragma unroll
+                        for (int c = 0; c < CB; ++c) kk[c] = j1 + c0 + ty + ny * c;
+                        // rows / columns past r read the next column's entries
+                        // or the zero padding (within the allocation); they
+                        // only reach accumulators the epilogue skips
+                        const T* Fi = F + (int64_t)(packed_col(j0, r) - j0 + ii[0]) * V;
+                        const T* Fk = F + (int64_t)(packed_col(j0, r) - j0 + kk[0]) * V;
+                        for (int j = j0; j < j1; ++j) {
+                            T ra[4][V], cb[CB][V];
+#pragma unroll
+                            for (int a = 0; a < 4; ++a) vld<T, V>(Fi + (int64_t)(16 * a) * V, ra[a]);
+#pragma unroll
+                            for (int c = 0; c < CB; ++c) vld<T, V>(Fk + (int64_t)(ny * c) * V, cb[c]);
+                            Fi += (int64_t)(r - j - 1) * V;
+                            Fk += (int64_t)(r - j - 1) * V;
+#pragma unroll
+                            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                                for (int c = 0; c < CB; ++c)
+#pragma unroll
+                                    for (int v = 0; v < V; ++v) acc[a][c][v] += ra[a][v] * cb[c][v];
+                        }
+#pragma unroll
+                        for (int c = 0; c < CB; ++c) {
+                            if (kk[c] >= r) continue;
+                            T* Fk2 = F + (int64_t)(packed_col(kk[c], r) - kk[c]) * V;
+#pragma unroll
+                            for (int a = 0; a < 4; ++a) {
+                                if (ii[a] < r && ii[a] >= kk[c]) {
+                                    T x[V];
+                                    vld<T, V>(Fk2 + (int64_t)ii[a] * V, x);
+#pragma unroll
+                                    for (int v = 0; v < V; ++v) x[v] -= acc[a][c][v];
+                                    vst<T, V>(Fk2 + (int64_t)ii[a] * V, x);
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        // factor columns (lower part) and update matrix
+        T* P0 = panel + (int64_t)b0 * panel_total + d.panel_off;
+        for (int jj = warp; jj < w; jj += nw) {
+            const T* Fj = F + (int64_t)(packed_col(jj, r) - jj) * V;
+            for (int i = jj + lane; i < r; i += 32) {
+                T x[V];
+                vld<T, V>(Fj + (int64_t)i * V, x);
+#pragma unroll
+                for (int v = 0; v < V; ++v)
+                    if (v < nv) P0[(int64_t)v * panel_total + (int64_t)jj * r + i] = x[v];
+            }
+        }
+        const int ru = r - w;
+        if (ru > 0) {
+            T* U0 = upd + (int64_t)b0 * upd_total + d.upd_off;
+            for (int kk = warp; kk < ru; kk += nw) {
+                const T* Fk = F + (int64_t)(packed_col(w + kk, r) - (w + kk)) * V;
+                for (int ii = kk + lane; ii < ru; ii += 32) {
+                    T x[V];
+                    vld<T, V>(Fk + (int64_t)(w + ii) * V, x);
+#pragma unroll
+                    for (int v = 0; v < V; ++v)
+                        if (v < nv) U0[(int64_t)v * upd_total + (int64_t)kk * ru + ii] = x[v];
+                }
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            flow_st_release(flags + (int64_t)(off + q) * B + g, 1);
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
 // a6: vectors, residual and refinement control (FP64)
 // --------------------------------------------------------------------------
 __global__ void k_permute_in(const double* __restrict__ bu, const int32_t* __restrict__ perm, int64_t n,
@@ -2330,7 +2834,7 @@ struct Work {
 Work work_front_small(const Plan& P, const LaunchList& ll) {
     Work w;
     for (int32_t q = 0; q < ll.count; ++q) {
-        const FrontDesc& d = P.fronts[P.front_lists[ll.list_off + q]];
+        const FrontDesc& d = P.fronts[P.flow_rest[ll.list_off + q]];
         for (int32_t j = 0; j < d.w; ++j) w.flops += (double)(d.r - j) * (d.r - j);
         double ru = d.r - d.w;
         w.bytes += d.klist_n * 16.0 + ((double)d.r * d.w + ru * (ru + 1) / 2) * P.tsize;
@@ -2348,7 +2852,7 @@ Work work_front_small(const Plan& P, const LaunchList& ll) {
 Work work_solve(const Plan& P, const LaunchList& ll) {
     Work w;
     for (int32_t q = 0; q < ll.count; ++q) {
-        const FrontDesc& d = P.fronts[P.front_lists[ll.list_off + q]];
+        const FrontDesc& d = P.fronts[P.flow_rest[ll.list_off + q]];
         double ent = (double)d.r * d.w - (double)d.w * (d.w - 1) / 2;
         w.flops += 2 * ent;
         w.bytes += ent * P.tsize + 2.0 * d.r * P.tsize;
@@ -2375,6 +2879,56 @@ Work work_tiny(const Plan& P, bool solve) {
     w.flops *= P.B;
     w.bytes *= P.B;
     return w;
+}
+
+// algorithmic work of one factorization dataflow launch (its fronts, as
+// work_front_small counts them) and of one dataflow solve sweep
+Work work_flow_group(const Plan& P, const FlowGroup& g) {
+    Work w;
+    for (int32_t q = 0; q < g.count; ++q) {
+        const FrontDesc& d = P.fronts[P.flow_fact[g.off + q]];
+        for (int32_t j = 0; j < d.w; ++j) w.flops += (double)(d.r - j) * (d.r - j);
+        double ru = d.r - d.w;
+        w.bytes += d.klist_n * 16.0 + ((double)d.r * d.w - (double)d.w * (d.w - 1) / 2 + ru * (ru + 1) / 2) * P.tsize;
+        for (int32_t c = 0; c < d.nchild; ++c) {
+            const FrontDesc& cd = P.fronts[P.child_ids[d.child_off + c]];
+            double rc = cd.r - cd.w;
+            w.bytes += rc * (rc + 1) / 2 * P.tsize + rc * 4;
+        }
+    }
+    w.flops *= P.B;
+    w.bytes *= P.B;
+    return w;
+}
+
+Work work_flow_solve(const Plan& P) {
+    Work w;
+    for (int32_t F : P.flow_solve) {
+        const FrontDesc& d = P.fronts[F];
+        double ent = (double)d.r * d.w - (double)d.w * (d.w - 1) / 2;
+        w.flops += 2 * ent;
+        w.bytes += ent * P.tsize + 2.0 * d.r * P.tsize;
+    }
+    w.flops *= P.B;
+    w.bytes *= P.B;
+    return w;
+}
+
+// Grid of a persistent dataflow launch: as many CTAs as fit on the device
+// at once (more would only find the ticket counter exhausted), at most one
+// per item.
+template <class Kern>
+unsigned flow_grid(Kern kernel, int threads, size_t smem, int64_t items) {
+    static int n_sm = 0;
+    if (n_sm == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        if (n_sm <= 0) n_sm = 1;
+    }
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem) != cudaSuccess || per < 1) per = 1;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)per * n_sm));
 }
 
 // Host mirror of big_update_tile (ts > 0) or tc_update_tile (ts = 0): tiles
@@ -2427,7 +2981,7 @@ void launch_big_update(Plan& P, const LaunchList& ll, const int32_t* list, int k
     int64_t tiles = 0;
     double fl = 0, by = 0;
     for (int32_t q = 0; q < ll.count; ++q) {
-        const UpdShape u = update_shape(P.fronts[P.front_lists[ll.list_off + q]], k0, nk, jend, ts);
+        const UpdShape u = update_shape(P.fronts[P.flow_rest[ll.list_off + q]], k0, nk, jend, ts);
         tiles = std::max(tiles, u.tiles);
         fl += 2 * u.entries * u.k;
         by += (2 * u.entries + u.rows * u.k) * P.tsize;
@@ -2436,7 +2990,7 @@ void launch_big_update(Plan& P, const LaunchList& ll, const int32_t* list, int k
     if (tcore && jend < 0 && P.tune.use_tc >= 2 && kpack0 == k0) {
         int64_t npairs = 0;
         for (int32_t q = 0; q < ll.count; ++q) {
-            const FrontDesc& d = P.fronts[P.front_lists[ll.list_off + q]];
+            const FrontDesc& d = P.fronts[P.flow_rest[ll.list_off + q]];
             if (k0 >= d.w) continue;
             const int jlo = std::min(k0 + nk, d.w);
             if (jlo >= d.r) continue;
@@ -2548,6 +3102,45 @@ int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cud
             pr.done(w.flops, w.bytes);
         }
     }
+    // Small fronts below every big front: one persistent dataflow launch per
+    // size group (children wait through done flags, not level boundaries).
+    const bool fflow = (P.tune.flow & 2) && !P.fact_groups.empty() && (int64_t)P.flow_fact.size() * B < (1LL << 30);
+    if (fflow) {
+        int32_t* fl = wsp<int32_t>(P, P.ws.flow_fact);
+        cudaMemsetAsync(fl, 0, 128 + (size_t)B * P.flow_fact.size() * 4, s);
+        for (size_t gi = 0; gi < P.fact_groups.size(); ++gi) {
+            const FlowGroup& g = P.fact_groups[gi];
+            const size_t smem =
+                ((size_t)kFlowNB * kFlowNB + kFlowNB + (size_t)g.rmax * (g.rmax + 1) / 2 + kSmallPad) * g.V * sizeof(T);
+            const int64_t items = (int64_t)g.count * ((B + g.V - 1) / g.V);
+            const int stall = gi == 0 ? P.tune.flow_stall : -1;
+            const int th = 32 * g.nw;
+            int32_t* derr = wsp<int32_t>(P, P.ws.dev_err);
+            Prof pr(P, s, g.V > 1 ? SSCO_K_FRONT_VEC : SSCO_K_FRONT_SMALL);
+#define SSCO_FLOW_LAUNCH(VV)                                                                                     \
+    k_front_flow<T, VV><<<flow_grid(k_front_flow<T, VV>, th, smem, items), th, smem, s>>>(                      \
+        P.dt, g.off, g.count, B, K, P.nnzK, panel, P.panel_total, upd, P.upd_total, bad, P.n_pats, fl, (int)gi, \
+        derr, P.tune.flow_polls, stall)
+            // (the shared memory above is sized for g.V: exactly the
+            // instantiation launched; build_flow makes g.V one of 1, 2 or 4,
+            // 4 only for FP32)
+            if (g.V == 1)
+                SSCO_FLOW_LAUNCH(1);
+            else if (g.V == 2)
+                SSCO_FLOW_LAUNCH(2);
+            else if (g.V == 4 && sizeof(T) == 4)
+                SSCO_FLOW_LAUNCH(sizeof(T) == 4 ? 4 : 2);
+            else
+                return (int)cudaErrorInvalidConfiguration;
+#undef SSCO_FLOW_LAUNCH
+            pr.end();
+            if (pr.ev >= 0) {
+                Work w = work_flow_group(P, g);
+                pr.done(w.flops, w.bytes);
+            }
+        }
+    }
+    const std::vector<LaunchList>& FL = fflow ? P.fact_rest : P.fact_launches;
     // The launch lists of one level (the size classes of small fronts, the
     // big fronts) are independent: all but the last go to the plan's
     // auxiliary streams, forked from s at the level's start and joined back
@@ -2562,13 +3155,13 @@ int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cud
             cudaStreamWaitEvent(s, (cudaEvent_t)P.aux_join[k], 0);
         }
     };
-    for (size_t li = 0; li < P.fact_launches.size(); ++li) {
-        const LaunchList& ll = P.fact_launches[li];
+    for (size_t li = 0; li < FL.size(); ++li) {
+        const LaunchList& ll = FL[li];
         if (li == lvl_end) {
             join_level();
             lvl_begin = li;
             lvl_end = li;
-            while (lvl_end < P.fact_launches.size() && P.fact_launches[lvl_end].level == ll.level) ++lvl_end;
+            while (lvl_end < FL.size() && FL[lvl_end].level == ll.level) ++lvl_end;
             nl = n_aux > 0 ? (int)(lvl_end - lvl_begin) : 1;
             if (nl > 1) {
                 cudaEventRecord((cudaEvent_t)P.aux_fork, s);
@@ -2578,7 +3171,7 @@ int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cud
         }
         const int kk = (int)(li - lvl_begin);
         cudaStream_t st = (nl > 1 && kk < nl - 1) ? (cudaStream_t)P.aux_stream[kk % n_aux] : s;
-        const int32_t* list = P.dt.front_lists + ll.list_off;
+        const int32_t* list = P.dt.flow_rest + ll.list_off;
         if (ll.cls > 0) {
             constexpr int V = sizeof(T) == 4 ? 4 : 2;
             if (ll.cls <= P.tune.warp_front_max && ll.rmax <= 64 && (int64_t)ll.count * B >= P.tune.warp_items) {
@@ -2620,7 +3213,7 @@ int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cud
             if (pr.ev >= 0) {
                 double by = 0;
                 for (int32_t q = 0; q < ll.count; ++q) {
-                    const FrontDesc& d = P.fronts[P.front_lists[ll.list_off + q]];
+                    const FrontDesc& d = P.fronts[P.flow_rest[ll.list_off + q]];
                     by += (double)d.r * (d.r + 1) / 2 * P.tsize;
                     for (int32_t c = 0; c < d.nchild; ++c) {
                         const FrontDesc& cd = P.fronts[P.child_ids[d.child_off + c]];
@@ -2639,7 +3232,7 @@ int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cud
             if (pr.ev >= 0) {
                 double by = 0;
                 for (int32_t q = 0; q < ll.count; ++q)
-                    by += P.fronts[P.front_lists[ll.list_off + q]].klist_n * (16.0 + 2 * P.tsize);
+                    by += P.fronts[P.flow_rest[ll.list_off + q]].klist_n * (16.0 + 2 * P.tsize);
                 pr.done(0, by * B);
             }
         }
@@ -2663,7 +3256,7 @@ int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cud
                     if (pd.ev >= 0) {
                         double fl = 0, by = 0;
                         for (int32_t q = 0; q < ll.count; ++q) {
-                            const FrontDesc& d = P.fronts[P.front_lists[ll.list_off + q]];
+                            const FrontDesc& d = P.fronts[P.flow_rest[ll.list_off + q]];
                             if (c0 >= d.w) continue;
                             double nbk = std::min(32, d.w - c0);
                             fl += nbk * nbk * nbk / 3;
@@ -2681,7 +3274,7 @@ int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cud
                     if (pr.ev >= 0) {
                         double fl = 0, by = 0;
                         for (int32_t q = 0; q < ll.count; ++q) {
-                            const FrontDesc& d = P.fronts[P.front_lists[ll.list_off + q]];
+                            const FrontDesc& d = P.fronts[P.flow_rest[ll.list_off + q]];
                             if (c0 >= d.w) continue;
                             double nbk = std::min(32, d.w - c0), mrows = d.r - c0 - nbk;
                             fl += mrows * nbk * nbk;
@@ -3206,7 +3799,7 @@ inline int split_count(const Plan& P, const LaunchList& ll) {
     const int thr = std::max(P.tune.split_rows, P.small_max + 1);
     int q = 0;
     while (q < ll.count) {
-        const FrontDesc& d = P.fronts[P.front_lists[ll.list_off + q]];
+        const FrontDesc& d = P.fronts[P.flow_rest[ll.list_off + q]];
         if (d.r < thr || (d.nchild > 0 && d.inv_off < 0) || (size_t)(d.r - d.w) * P.tsize > 160 * 1024) break;
         ++q;
     }
@@ -3219,7 +3812,7 @@ inline int cluster_count(const Plan& P, const LaunchList& ll, int q0) {
     const int thr = std::max(P.tune.cluster_rows, P.small_max + 1);
     int q = q0;
     while (q < ll.count) {
-        const FrontDesc& d = P.fronts[P.front_lists[ll.list_off + q]];
+        const FrontDesc& d = P.fronts[P.flow_rest[ll.list_off + q]];
         if (d.r < thr || (d.nchild > 0 && d.inv_off < 0)) break;
         ++q;
     }
@@ -3247,7 +3840,7 @@ void launch_cluster(Plan& P, Kern kernel, int nfront, int B, size_t smem, cudaSt
 template <class T>
 size_t cluster_smem(const Plan& P, const LaunchList& ll, int q0, int q) {
     int rmax = 0;
-    for (int f = q0; f < q0 + q; ++f) rmax = std::max(rmax, P.fronts[P.front_lists[ll.list_off + f]].r);
+    for (int f = q0; f < q0 + q; ++f) rmax = std::max(rmax, P.fronts[P.flow_rest[ll.list_off + f]].r);
     const int nch = (rmax + 31) / 32;
     return (size_t)((nch + kClusterCS - 1) / kClusterCS) * 32 * sizeof(T);
 }
@@ -3255,14 +3848,14 @@ size_t cluster_smem(const Plan& P, const LaunchList& ll, int q0, int q) {
 template <class T>
 void run_split_fwd(Plan& P, const LaunchList& ll, int q, const int32_t* active, cudaStream_t s) {
     const int B = P.B;
-    const int32_t* list = P.dt.front_lists + ll.list_off;
+    const int32_t* list = P.dt.flow_rest + ll.list_off;
     T* panel = wsp<T>(P, P.ws.panel);
     T* vecT = wsp<T>(P, P.ws.vecT);
     T* pvec = wsp<T>(P, P.ws.pvec);
     int rmax = 0, wmax = 0;
     double by0 = 0, fl0 = 0;
     for (int f = 0; f < q; ++f) {
-        const FrontDesc& d = P.fronts[P.front_lists[ll.list_off + f]];
+        const FrontDesc& d = P.fronts[P.flow_rest[ll.list_off + f]];
         rmax = std::max(rmax, d.r);
         wmax = std::max(wmax, d.w);
         const double nb0 = std::min(kSplitCB, d.w);
@@ -3280,7 +3873,7 @@ void run_split_fwd(Plan& P, const LaunchList& ll, int q, const int32_t* active, 
         int64_t g = 0;
         double fl = 0, by = 0;
         for (int f = 0; f < q; ++f) {
-            const FrontDesc& d = P.fronts[P.front_lists[ll.list_off + f]];
+            const FrontDesc& d = P.fronts[P.flow_rest[ll.list_off + f]];
             const int c0 = k * kSplitCB;
             if (c0 >= d.w) continue;
             const int e = std::min(c0 + kSplitCB, d.w);
@@ -3300,13 +3893,13 @@ void run_split_fwd(Plan& P, const LaunchList& ll, int q, const int32_t* active, 
 template <class T>
 void run_split_bwd(Plan& P, const LaunchList& ll, int q, const int32_t* active, cudaStream_t s) {
     const int B = P.B;
-    const int32_t* list = P.dt.front_lists + ll.list_off;
+    const int32_t* list = P.dt.flow_rest + ll.list_off;
     T* panel = wsp<T>(P, P.ws.panel);
     T* vecT = wsp<T>(P, P.ws.vecT);
     int wmax = 0, rumax = 0;
     double by0 = 0, fl0 = 0;
     for (int f = 0; f < q; ++f) {
-        const FrontDesc& d = P.fronts[P.front_lists[ll.list_off + f]];
+        const FrontDesc& d = P.fronts[P.flow_rest[ll.list_off + f]];
         wmax = std::max(wmax, d.w);
         rumax = std::max(rumax, d.r - d.w);
         const double ru = d.r - d.w, nl = d.w - (double)((d.w - 1) / kSplitCB) * kSplitCB;
@@ -3323,7 +3916,7 @@ void run_split_bwd(Plan& P, const LaunchList& ll, int q, const int32_t* active, 
     for (int k = nb - 1; k >= 1; --k) {
         double fl = 0, by = 0;
         for (int f = 0; f < q; ++f) {
-            const FrontDesc& d = P.fronts[P.front_lists[ll.list_off + f]];
+            const FrontDesc& d = P.fronts[P.flow_rest[ll.list_off + f]];
             const int c0 = k * kSplitCB;
             if (c0 >= d.w) continue;
             const double nbk = std::min(kSplitCB, d.w - c0);
@@ -3344,6 +3937,14 @@ void run_trisolve(Plan& P, const int32_t* active, cudaStream_t s) {
     T* vecT = wsp<T>(P, P.ws.vecT);
     T* pvec = wsp<T>(P, P.ws.pvec);
     const unsigned tiny_grid = cdiv((int64_t)P.n_tiny * B, kTinyWarps);
+    // fronts of at most flow_solve_rmax rows below every larger front: one
+    // persistent dataflow launch per sweep (warp per front and value set)
+    const bool sflow = (P.tune.flow & 1) && !P.flow_solve.empty() && (int64_t)P.flow_solve.size() * B < (1LL << 30);
+    int32_t* sfl = wsp<int32_t>(P, P.ws.flow_solve);
+    int32_t* derr = wsp<int32_t>(P, P.ws.dev_err);
+    const size_t fsmem = 8 * (size_t)P.flow_solve_rmax * sizeof(T);
+    const int64_t fitems = (int64_t)P.flow_solve.size() * B;
+    if (sflow) cudaMemsetAsync(sfl, 0, 128 + (size_t)fitems * 4, s);
     if (P.n_tiny > 0) {
         Prof pr(P, s, SSCO_K_FWD);
         k_tiny_fwd<T><<<tiny_grid, 32 * kTinyWarps, tiny_solve_bytes<T>(tiny_share(B), P.tiny_prog_max), s>>>(
@@ -3355,14 +3956,26 @@ void run_trisolve(Plan& P, const int32_t* active, cudaStream_t s) {
             pr.done(w.flops, w.bytes);
         }
     }
-    for (const LaunchList& ll0 : P.solve_launches) {
+    if (sflow) {
+        Prof pr(P, s, SSCO_K_FWD);
+        k_flow_fwd<T><<<flow_grid(k_flow_fwd<T>, 256, fsmem, (fitems + 7) / 8), 256, fsmem, s>>>(
+            P.dt, (int32_t)P.flow_solve.size(), B, P.flow_solve_rmax, panel, P.panel_total, vecT, P.n, pvec,
+            P.pvec_total, active, P.n_pats, sfl, derr, P.tune.flow_polls, P.tune.flow_stall);
+        pr.end();
+        if (pr.ev >= 0) {
+            Work w = work_flow_solve(P);
+            pr.done(w.flops, w.bytes);
+        }
+    }
+    const std::vector<LaunchList>& SL = sflow ? P.solve_rest : P.solve_launches;
+    for (const LaunchList& ll0 : SL) {
         LaunchList ll = ll0;
         const int q = split_count(P, ll);
         if (q > 0) run_split_fwd<T>(P, ll, q, active, s);
         const int qc = cluster_count(P, ll, q);
         if (qc > 0) {
             Prof pr(P, s, SSCO_K_FWD);
-            const int32_t* lst = P.dt.front_lists + ll.list_off + q;
+            const int32_t* lst = P.dt.flow_rest + ll.list_off + q;
             launch_cluster<T>(P, k_fwd_cluster<T>, qc, B, cluster_smem<T>(P, ll, q, qc), s, P.dt, lst,
                               (const T*)panel, P.panel_total, vecT, P.n, pvec, P.pvec_total, active, P.n_pats);
             pr.end();
@@ -3378,17 +3991,17 @@ void run_trisolve(Plan& P, const int32_t* active, cudaStream_t s) {
             ll.list_off += q + qc;
             ll.count -= q + qc;
             if (ll.count == 0) continue;
-            ll.rmax = P.fronts[P.front_lists[ll.list_off]].r;
+            ll.rmax = P.fronts[P.flow_rest[ll.list_off]].r;
         }
         Prof pr(P, s, SSCO_K_FWD);
         const size_t smem = (size_t)ll.rmax * sizeof(T);
         if (use_warp_solve(P, ll, B)) {
             const int64_t items = (int64_t)ll.count * B;
-            k_fwd_warp<T><<<cdiv(items, 8), 256, 8 * smem, s>>>(P.dt, P.dt.front_lists + ll.list_off, ll.count, B,
+            k_fwd_warp<T><<<cdiv(items, 8), 256, 8 * smem, s>>>(P.dt, P.dt.flow_rest + ll.list_off, ll.count, B,
                                                                 ll.rmax, panel, P.panel_total, vecT, P.n, pvec,
                                                                 P.pvec_total, active, P.n_pats);
         } else
-        k_fwd<T><<<dim3(ll.count, B), solve_threads(P, ll), smem, s>>>(P.dt, P.dt.front_lists + ll.list_off, panel, P.panel_total,
+        k_fwd<T><<<dim3(ll.count, B), solve_threads(P, ll), smem, s>>>(P.dt, P.dt.flow_rest + ll.list_off, panel, P.panel_total,
                                                         vecT, P.n, pvec, P.pvec_total, active, P.n_pats);
         pr.end();
         if (pr.ev >= 0) {
@@ -3396,14 +4009,14 @@ void run_trisolve(Plan& P, const int32_t* active, cudaStream_t s) {
             pr.done(w.flops, w.bytes);
         }
     }
-    for (auto it = P.solve_launches.rbegin(); it != P.solve_launches.rend(); ++it) {
+    for (auto it = SL.rbegin(); it != SL.rend(); ++it) {
         LaunchList ll = *it;
         const int q = split_count(P, ll);
         if (q > 0) run_split_bwd<T>(P, ll, q, active, s);
         const int qc = cluster_count(P, ll, q);
         if (qc > 0) {
             Prof pr(P, s, SSCO_K_BWD);
-            const int32_t* lst = P.dt.front_lists + ll.list_off + q;
+            const int32_t* lst = P.dt.flow_rest + ll.list_off + q;
             launch_cluster<T>(P, k_bwd_cluster<T>, qc, B, cluster_smem<T>(P, ll, q, qc), s, P.dt, lst,
                               (const T*)panel, P.panel_total, vecT, P.n, active, P.n_pats);
             pr.end();
@@ -3419,21 +4032,32 @@ void run_trisolve(Plan& P, const int32_t* active, cudaStream_t s) {
             ll.list_off += q + qc;
             ll.count -= q + qc;
             if (ll.count == 0) continue;
-            ll.rmax = P.fronts[P.front_lists[ll.list_off]].r;
+            ll.rmax = P.fronts[P.flow_rest[ll.list_off]].r;
         }
         Prof pr(P, s, SSCO_K_BWD);
         const size_t smem = (size_t)ll.rmax * sizeof(T);
         if (use_warp_solve(P, ll, B)) {
             const int64_t items = (int64_t)ll.count * B;
-            k_bwd_warp<T><<<cdiv(items, 8), 256, 8 * smem, s>>>(P.dt, P.dt.front_lists + ll.list_off, ll.count, B,
+            k_bwd_warp<T><<<cdiv(items, 8), 256, 8 * smem, s>>>(P.dt, P.dt.flow_rest + ll.list_off, ll.count, B,
                                                                 ll.rmax, panel, P.panel_total, vecT, P.n, active,
                                                                 P.n_pats);
         } else
-        k_bwd<T><<<dim3(ll.count, B), solve_threads(P, ll), smem, s>>>(P.dt, P.dt.front_lists + ll.list_off, panel, P.panel_total,
+        k_bwd<T><<<dim3(ll.count, B), solve_threads(P, ll), smem, s>>>(P.dt, P.dt.flow_rest + ll.list_off, panel, P.panel_total,
                                                         vecT, P.n, active, P.n_pats);
         pr.end();
         if (pr.ev >= 0) {
             Work w = work_solve(P, ll);
+            pr.done(w.flops, w.bytes);
+        }
+    }
+    if (sflow) {
+        Prof pr(P, s, SSCO_K_BWD);
+        k_flow_bwd<T><<<flow_grid(k_flow_bwd<T>, 256, fsmem, (fitems + 7) / 8), 256, fsmem, s>>>(
+            P.dt, (int32_t)P.flow_solve.size(), B, P.flow_solve_rmax, panel, P.panel_total, vecT, P.n, active,
+            P.n_pats, sfl, derr, P.tune.flow_polls);
+        pr.end();
+        if (pr.ev >= 0) {
+            Work w = work_flow_solve(P);
             pr.done(w.flops, w.bytes);
         }
     }
@@ -3647,6 +4271,11 @@ int set_attr_T() {
     if (!e) e = allow_dynamic_smem(k_front_warp<T>);
     if (!e) e = allow_dynamic_smem(k_fwd_cluster<T>);
     if (!e) e = allow_dynamic_smem(k_bwd_cluster<T>);
+    if (!e) e = allow_dynamic_smem(k_flow_fwd<T>);
+    if (!e) e = allow_dynamic_smem(k_flow_bwd<T>);
+    if (!e) e = allow_dynamic_smem(k_front_flow<T, 1>);
+    if (!e) e = allow_dynamic_smem(k_front_flow<T, 2>);
+    if (!e && sizeof(T) == 4) e = allow_dynamic_smem(k_front_flow<T, sizeof(T) == 4 ? 4 : 2>);
     return e;
 }
 
@@ -3798,6 +4427,7 @@ int autotune(Plan& P, const void* vals, int32_t vdt, const double* shift, const 
         std::vector<int32_t> cand;
     };
     std::vector<Knob> knobs = {
+        {&P.tune.flow, {0, 1, 2, 3}},
         {&P.tune.warp_items, {152, 2 * 152, 4 * 152, 8 * 152, 16 * 152, 1 << 30}},
         {&P.tune.vec_max_cls, {0, 64, 96}},
         {&P.tune.solve_threads_big, {256, 512}},
@@ -3927,13 +4557,13 @@ int launch_solve_static(Plan& P, const double* b, double* x, void* stream) {
     }
     for (const LaunchList& ll : P.solve_launches) {
         k_fwd<double><<<dim3(ll.count, B), 256, (size_t)ll.rmax * 8, s>>>(
-            P.dt, P.dt.front_lists + ll.list_off, panel, P.panel_total, vec, n, pvec, P.pvec_total, nullptr,
+            P.dt, P.dt.flow_rest + ll.list_off, panel, P.panel_total, vec, n, pvec, P.pvec_total, nullptr,
             P.n_pats);
         P.launches++;
     }
     for (auto it = P.solve_launches.rbegin(); it != P.solve_launches.rend(); ++it) {
         k_bwd<double><<<dim3(it->count, B), 256, (size_t)it->rmax * 8, s>>>(
-            P.dt, P.dt.front_lists + it->list_off, panel, P.panel_total, vec, n, nullptr, P.n_pats);
+            P.dt, P.dt.flow_rest + it->list_off, panel, P.panel_total, vec, n, nullptr, P.n_pats);
         P.launches++;
     }
     if (P.n_tiny > 0) {

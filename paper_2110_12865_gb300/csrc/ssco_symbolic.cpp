@@ -935,9 +935,122 @@ size_t put(std::vector<uint8_t>& blob, const std::vector<T>& v) {
 }
 }  // namespace
 
+
+// Dataflow schedules.  The fronts outside tiny subtrees are handed to
+// persistent launches that walk many levels at once: every front is an item
+// (per value set, or per group of V value sets) taken in level order by
+// whichever warp or CTA is free, and it waits only for its own children (the
+// factorization and the forward sweep) or its own parent (the backward
+// sweep) through per-item done flags, instead of for a whole level (Sec. 4.3
+// groups a level's independent expressions; the flags keep exactly the
+// dependencies that grouping respects).
+//   factor: fronts with no big (multi-CTA) front below them, in groups by
+//     the largest front of their subtree (so a child never sits in a later
+//     group than its parent); groups run in increasing size, one launch each.
+//   solve:  fronts of at most kFlowSolveRmax rows with no larger front below
+//     them, one warp per (front, value set).
+// Fronts outside the dataflow keep their per-level launches (fact_rest,
+// solve_rest; lists in flow_rest, which starts with a copy of front_lists).
+constexpr int32_t kFlowSolveRmax = 256;
+
+void build_flow(Plan& P) {
+    const int32_t nf = (int32_t)P.fronts.size();
+    std::vector<char> tiny(nf, 0);
+    for (int32_t F : P.tiny_list) tiny[F] = 1;
+    // height among the fronts outside tiny subtrees; the largest front of
+    // each subtree (children precede parents in front order)
+    std::vector<int32_t> lvl(nf, 0), sub_r(nf, 0);
+    std::vector<char> solve_ok(nf, 1);
+    const int32_t srmax = std::min(kFlowSolveRmax, std::max(P.small_max, 32));
+    for (int32_t F = 0; F < nf; ++F) {
+        const FrontDesc& d = P.fronts[F];
+        sub_r[F] = std::max(sub_r[F], d.r);
+        if (d.r > srmax) solve_ok[F] = 0;
+        const int32_t p = d.parent;
+        if (p < 0) continue;
+        sub_r[p] = std::max(sub_r[p], sub_r[F]);
+        if (!tiny[F]) {
+            lvl[p] = std::max(lvl[p], lvl[F] + 1);
+            if (!solve_ok[F]) solve_ok[p] = 0;
+        }
+    }
+    std::vector<int32_t> order;
+    for (int32_t F = 0; F < nf; ++F)
+        if (!tiny[F]) order.push_back(F);
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+        if (lvl[a] != lvl[b]) return lvl[a] < lvl[b];
+        return P.fronts[a].r > P.fronts[b].r;
+    });
+    // factor groups by the largest front of the subtree
+    const int32_t T = (int32_t)P.tsize;
+    struct Cls {
+        int32_t hi, V, nw;
+    };
+    std::vector<Cls> cls;
+    if (T == 4)
+        cls = {{64, 4, 4}, {128, 2, 8}, {P.small_max, 1, 8}};
+    else
+        cls = {{64, 2, 4}, {128, 1, 8}, {P.small_max, 1, 8}};
+    P.flow_fact.clear();
+    P.flow_fslot.assign(nf, -1);
+    P.fact_groups.clear();
+    int32_t lo = 0;
+    for (const Cls& c : cls) {
+        const int32_t hi = std::min(c.hi, P.small_max);
+        if (hi <= lo) continue;
+        FlowGroup g{};
+        g.off = (int32_t)P.flow_fact.size();
+        g.V = c.V;  // a power of two the kernel is instantiated for, at most the batch
+        while (g.V > 1 && g.V > P.B) g.V /= 2;
+        g.nw = c.nw;
+        for (int32_t F : order)
+            if (sub_r[F] > lo && sub_r[F] <= hi) {
+                P.flow_fslot[F] = (int32_t)P.flow_fact.size();
+                P.flow_fact.push_back(F);
+                g.rmax = std::max(g.rmax, P.fronts[F].r);
+            }
+        g.count = (int32_t)P.flow_fact.size() - g.off;
+        if (g.count > 0) P.fact_groups.push_back(g);
+        lo = hi;
+    }
+    P.flow_solve.clear();
+    P.flow_sslot.assign(nf, -1);
+    P.flow_solve_rmax = 0;
+    for (int32_t F : order)
+        if (solve_ok[F]) {
+            P.flow_sslot[F] = (int32_t)P.flow_solve.size();
+            P.flow_solve.push_back(F);
+            P.flow_solve_rmax = std::max(P.flow_solve_rmax, P.fronts[F].r);
+        }
+    // per-level launches of the other fronts (same level lists, filtered)
+    P.flow_rest = P.front_lists;
+    auto filter = [&](const std::vector<LaunchList>& src, const std::vector<int32_t>& slot,
+                      std::vector<LaunchList>& dst) {
+        dst.clear();
+        for (const LaunchList& ll : src) {
+            LaunchList q = ll;
+            q.list_off = (int64_t)P.flow_rest.size();
+            q.count = 0;
+            q.rmax = q.wmax = 0;
+            for (int32_t i = 0; i < ll.count; ++i) {
+                const int32_t F = P.front_lists[ll.list_off + i];
+                if (slot[F] >= 0) continue;
+                P.flow_rest.push_back(F);
+                q.count++;
+                q.rmax = std::max(q.rmax, P.fronts[F].r);
+                q.wmax = std::max(q.wmax, P.fronts[F].w);
+            }
+            if (q.count > 0) dst.push_back(q);
+        }
+    };
+    filter(P.fact_launches, P.flow_fslot, P.fact_rest);
+    filter(P.solve_launches, P.flow_sslot, P.solve_rest);
+}
+
 void build_blob(Plan& P) {
     std::vector<uint8_t>& b = P.blob;
     b.clear();
+    build_flow(P);
     P.toff.fronts = put(b, P.fronts);
     P.toff.rows = put(b, P.rows);
     P.toff.child_ids = put(b, P.child_ids);
@@ -976,6 +1089,11 @@ void build_blob(Plan& P) {
     P.toff.blk_off = put(b, P.blk_off);
     P.toff.blk_dim = put(b, P.blk_dim);
     P.toff.blk_vbase = put(b, P.blk_vbase);
+    P.toff.flow_fact = put(b, P.flow_fact);
+    P.toff.flow_fslot = put(b, P.flow_fslot);
+    P.toff.flow_solve = put(b, P.flow_solve);
+    P.toff.flow_sslot = put(b, P.flow_sslot);
+    P.toff.flow_rest = put(b, P.flow_rest);
     b.resize((b.size() + 255) & ~(size_t)255);
 }
 
@@ -1016,6 +1134,8 @@ void compute_ws_layout(Plan& P) {
     w.st_b = take(B * n * 8);
     w.st_x = take(B * n * 8);
     w.tcpack = take(B * (size_t)P.tc_pack_total * 4);
+    w.flow_fact = take(128 + B * P.flow_fact.size() * 4);
+    w.flow_solve = take(128 + B * P.flow_solve.size() * 4);
     w.total = off;
 }
 

@@ -35,7 +35,7 @@ EXPORTED_SYMBOLS = [
     "ssco_cotan_weights", "ssco_tet_stiffness",
     "ssco_expr_compile", "ssco_expr_get_info", "ssco_expr_export", "ssco_expr_output_shape",
     "ssco_expr_output_pattern", "ssco_expr_bind", "ssco_expr_run", "ssco_expr_last_error", "ssco_expr_destroy",
-    "ssco_expr_save", "ssco_expr_load",
+    "ssco_expr_save", "ssco_expr_load", "ssco_set_flow",
 ]
 KERNEL_KINDS = ["assemble", "front_small", "big_init", "big_kscatter", "big_update", "big_potrf", "big_syrk",
                 "fwd_solve", "bwd_solve", "resid", "check", "vector", "grad", "front_tiny", "big_trsm", "front_vec",
@@ -76,7 +76,8 @@ class Info(C.Structure):
               [("factor_flops", C.c_double), ("factor_flops_exact", C.c_double)] + \
               [(k, C.c_int64) for k in ["tune_warp_items", "tune_vec_max_cls", "tune_solve_threads_big", "tuned",
                                         "tune_use_tc", "tune_big_panel", "tune_split_rows",
-                                        "tune_warp_front_max", "tune_cluster_rows"]]
+                                        "tune_warp_front_max", "tune_cluster_rows", "tune_flow",
+                                        "flow_fact_fronts", "flow_solve_fronts"]]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -148,6 +149,7 @@ def load_library(path: str = LIB_PATH):
         "ssco_expr_save": (i32, [vp, C.c_char_p]),
         "ssco_expr_load": (i32, [C.c_char_p, C.POINTER(vp)]),
         "ssco_expr_destroy": (None, [vp]),
+        "ssco_set_flow": (i32, [vp, i32, i64, i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -354,7 +356,7 @@ class Plan:
         return best.value, {k: self.info[k] for k in ("tune_warp_items", "tune_vec_max_cls",
                                                       "tune_solve_threads_big", "tune_use_tc",
                                                       "tune_big_panel", "tune_split_rows",
-                                                      "tune_warp_front_max", "tune_cluster_rows")}
+                                                      "tune_warp_front_max", "tune_cluster_rows", "tune_flow")}
 
     def graph_run(self, vals: torch.Tensor, shift: torch.Tensor, b: torch.Tensor, x: torch.Tensor, stream=None):
         """numeric + solve as one captured CUDA graph (re-captured when the
@@ -401,6 +403,16 @@ class Plan:
         self._check(self.L.ssco_refactor_solve_host(self._h, _ptr(vals), dt, _ptr(shift), _ptr(b), _ptr(x),
                                                     _stream_ptr(stream)))
         return x
+
+    def set_flow(self, flow=3, max_polls=0, stall_item=-1):
+        """Dataflow launches on (bit 0 solve sweeps, bit 1 factorization) or
+        off; bound of every wait (0 = keep); test hook stall_item (see
+        ssco_set_flow)."""
+        self._check(self.L.ssco_set_flow(self._h, int(flow), int(max_polls), int(stall_item)))
+        inf = Info()
+        self._check(self.L.ssco_plan_info(self._h, C.byref(inf)))
+        self.info = inf.as_dict()
+        return self
 
     def last_launch_count(self):
         return int(self.L.ssco_last_launch_count(self._h))

@@ -635,3 +635,80 @@ def test_full_elastgeo24_blocks_and_refine(S):
     pl.solve(torch.tensor(g.b, device="cuda"))
     st = pl.status()
     assert np.all(st["status"] == 0) and np.all(st["resid"] <= RESID_TOL)
+
+
+# ---------------------------------------------------------------------------
+# dataflow launches (persistent grids walking all levels, per-item done flags)
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("case", ["uneven_trigrids", "elast_big_fronts", "trigrid_batch"])
+def test_dataflow_matches_level_launches(S, prec, case):
+    """The default schedule (one persistent launch per factorization size
+    group and per solve sweep, items waiting on their children's or parent's
+    done flags) against one launch per level and size class (flow=0): the
+    factors agree to rounding (per column; blocked panels reorder the sums)
+    and both solutions meet the residual bound with the oracle's K."""
+    precision = S.FP64 if prec == "fp64" else S.FP32_REFINE
+    if case == "uneven_trigrids":
+        probs = [P.trigrid_problem(s, 1, cfg=3, seed_offset=k) for k, s in enumerate([9, 17, 23, 31, 40])]
+        B, kw = 1, {}
+    elif case == "elast_big_fronts":
+        probs = [P.elasticity_problem(8, batch=2, cfg=2)]
+        B, kw = 2, {"small_front_max": 96}
+    else:
+        probs = [P.trigrid_problem(20, batch=7, cfg=3)]
+        B, kw = 7, {}
+    item = probs if len(probs) > 1 else probs[0]
+    pl = S.Plan(item, precision=precision, batch=B, **kw).bind()
+    assert pl.info["tune_flow"] == 3 and pl.info["flow_fact_fronts"] > 0 and pl.info["flow_solve_fronts"] > 0
+    vals = np.concatenate([np.asarray(p.vals[:B]) for p in probs], axis=1)
+    shift = np.stack([np.asarray(p.shift[:B], np.float64) for p in probs], axis=1).reshape(-1)
+    b = np.concatenate([p.b[:B] for p in probs], axis=1)
+    vt, st_, bt = (torch.tensor(a, device="cuda") for a in (vals, shift, b))
+    res = {}
+    for flow in (0, 3):
+        pl.set_flow(flow)
+        pl.numeric(vt, st_)
+        x = pl.solve(bt).cpu().numpy()
+        st = pl.status()
+        assert np.all(st["status"] == 0), (flow, st)
+        res[flow] = (pl.export_L(), x)
+    L0, L3 = res[0][0], res[3][0]
+    tol = 1e-12 if prec == "fp64" else 2e-5
+    off = 0
+    for k, p in enumerate(probs):
+        r = O.refactor_solve(p, 0)
+        for i in range(B):
+            xi = res[3][1][i, off:off + p.n]
+            assert np.linalg.norm(O.symv(r.K if i == 0 else O.refactor_solve(p, i).K, xi) - p.b[i]) <= \
+                RESID_TOL * np.linalg.norm(p.b[i])
+        off += p.n
+    # per column of the concatenated factor (exported in CSC order of L)
+    Lc = np.concatenate([[0], np.cumsum(pl.export(S.EXPORT_COLCOUNT))])
+    for i in range(B):
+        for j in range(len(Lc) - 1):
+            a, e = Lc[j], Lc[j + 1]
+            assert np.linalg.norm(L3[i, a:e] - L0[i, a:e]) <= tol * np.linalg.norm(L0[i, a:e]), (i, j)
+
+
+def test_dataflow_wait_timeout_reports_status(S):
+    """Bounded waits: with the test hook one item of the first dataflow
+    launch waits on a flag that nothing sets; after max_polls polls it gives
+    up, the launches end early and every system reports SSCO_ERR_TIMEOUT
+    (the device stays usable).  The next call without the hook is correct."""
+    p = P.trigrid_problem(24, batch=8, cfg=3)
+    pl = S.Plan(p, precision=S.FP32_REFINE).bind()
+    vt, st_, bt = (torch.tensor(a, device="cuda") for a in (p.vals, p.shift, p.b))
+    for stall in (0, 5):
+        pl.set_flow(3, max_polls=2000, stall_item=stall)
+        pl.numeric(vt, st_)
+        pl.solve(bt)
+        st = pl.status()
+        assert np.all(st["status"] == 6), st["status"]
+    pl.set_flow(3, max_polls=1 << 22, stall_item=-1)
+    pl.numeric(vt, st_)
+    x = pl.solve(bt).cpu().numpy()
+    st = pl.status()
+    assert np.all(st["status"] == 0)
+    for i in range(p.batch):
+        r = O.refactor_solve(p, i)
+        assert np.linalg.norm(O.symv(r.K, x[i]) - p.b[i]) <= RESID_TOL * np.linalg.norm(p.b[i])

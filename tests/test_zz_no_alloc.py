@@ -29,6 +29,39 @@ def rel(a, b):
     return float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
 
 
+@pytest.mark.parametrize("case", ["grid32", "elast10_big_fronts"])
+def test_noalloc_matches_oracle_two_calls(S, case):
+    """The allocation-free solve against the FP64 oracle's solution (same
+    1e-12 relative bound as the direct FP64 parity tests), on a grid plan of
+    small fronts and on an elasticity plan whose fronts above 32 rows take
+    the multi-CTA path (small_front_max=32): the allocation-free solve runs
+    its own fixed-shape launches over those large fronts, which ssco_solve
+    would split or cluster.  Two right-hand sides in a row."""
+    from oracle import oracle as O
+    if case == "grid32":
+        p = P.grid_problem(32, 32, batch=3, cfg=1)
+        kw = {}
+    else:
+        p = P.elasticity_problem(10, batch=2, cfg=2)
+        kw = {"small_front_max": 32, "split_rows": 64, "cluster_rows": 48}
+    pl = S.Plan(p, precision=S.FP64, **kw).bind()
+    if kw:
+        assert pl.info["max_front_rows"] > 4 * 32      # several 32-column blocks per big front
+    pl.numeric(torch.tensor(p.vals, device="cuda"), torch.tensor(p.shift, device="cuda"))
+    rng = np.random.default_rng(P.seed_for(9, 0))
+    b2h = rng.standard_normal(p.b.shape)
+    if case != "grid32":
+        b2h[:, p.dof_fixed] = 0.0
+    for bh in (np.asarray(p.b), b2h):
+        x = torch.full((p.batch, p.n), float("nan"), dtype=torch.float64, device="cuda")
+        pl.solve_noalloc(torch.tensor(bh, device="cuda"), x)
+        torch.cuda.synchronize()
+        xh = x.cpu().numpy()
+        for i in range(p.batch):
+            r = O.refactor_solve(p, i, b=bh[i])
+            assert np.linalg.norm(xh[i] - r.x) <= 1e-12 * np.linalg.norm(r.x), (case, i)
+
+
 def test_noalloc_matches_solve_two_calls(S):
     p = P.grid_problem(32, 32, batch=3, cfg=1)
     pl = S.Plan(p, precision=S.FP64).bind()
