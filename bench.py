@@ -241,6 +241,36 @@ def ncu_traffic(kind):
     return k.get("dram_bytes_per_launch")
 
 
+def step_bytes(plans, statuses, vals_bytes):
+    """Algorithmic bytes of one step (every system refactored and solved):
+    per value set of a plan with n unknowns, m values, z_K entries of K and
+    z_L structural entries of L (exact pattern, no amalgamation zeros),
+    s_f bytes per factor entry and I refinement corrections,
+
+      B_alg = m s_w + 2 z_K 8 + z_L s_f + (1+I) 2 z_L s_f + I z_K 8 + (4+3I) n 8
+
+    (read the values, write and read K, write L once, read L twice per
+    solve, one FP64 SpMV per correction, the vectors).  I is the plan's mean
+    over its systems.  The bytes the method moves beyond that are reported
+    apart: the update matrices (written by a front, read by its parent) and
+    the explicit zeros that the dense panels add to L."""
+    alg = upd = pad = 0.0
+    iters = []
+    for pl, st in zip(plans, statuses):
+        i = pl.info
+        B, npat = int(i["batch"]), int(i["n_pats"])
+        sf = 4 if pl.precision == 1 else 8
+        its = np.asarray(st["iters"], np.float64).reshape(B, npat)
+        I = its.mean(axis=1)   # per value set (all patterns of one instance)
+        n, m, zK, zL = float(i["n"]), float(i["m"]), float(i["nnz_K"]), float(i["nnz_L"])
+        alg += float(np.sum(m * vals_bytes + 2 * zK * 8 + zL * sf + (1 + I) * 2 * zL * sf + I * zK * 8
+                            + (4 + 3 * I) * n * 8))
+        upd += B * 2.0 * float(i["update_entries"]) * sf
+        pad += B * float(i["panel_entries"] - i["nnz_L"]) * sf
+        iters += list(its.ravel())
+    return alg, upd, pad, float(np.mean(iters)) if iters else 0.0
+
+
 # ---------------------------------------------------------------------------
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -350,6 +380,8 @@ def run_ours(args, rank, world, local_rank):
     sampler = ClockSampler(local_rank)
     ms, launches, wall, clocks = timed(plans32, dev32, args.steps, args.warmup, sampler)
     ok32, res32, its32 = status_summary(plans32)
+    step_status32 = [pl.status() for pl in plans32]
+    work_vals_dtype = np.asarray(probs_of(work[0][0])[0].vals).dtype
     value, tot_ms = aggregate_value(units, args.steps, sum(ms), dist, dev)
 
     out = {
@@ -422,6 +454,15 @@ def run_ours(args, rank, world, local_rank):
     roof.update({"frac": achieved / peak, "traffic": ncu_traffic(top), "kernel": top,
                  "launches": kv["launches"], "avg_launch_us": kv["ms"] * 1e3 / kv["launches"],
                  "measured": "CUDA events per launch on the launch stream, over a repeat of the timed steps"})
+    # the whole step against the same HBM peak (B_alg of step_bytes)
+    alg, updb, padb, imean = step_bytes(plans32, step_status32, 8 if work_vals_dtype == np.float64 else 4)
+    hbm = peaks["hbm_gbs"] if peaks else HBM_FALLBACK_GBS
+    ms_step = out["ms_per_step"]
+    roof["step"] = {"bytes": alg, "GBps": alg / (ms_step / 1e3) / 1e9,
+                    "frac": alg / (ms_step / 1e3) / 1e9 / hbm, "mean_corrections": imean,
+                    "non_algorithmic_bytes": {"update_matrices": updb, "panel_zeros": padb},
+                    "definition": "B_alg = m s_w + 2 z_K 8 + z_L s_f + (1+I) 2 z_L s_f + I z_K 8 + (4+3I) n 8 "
+                                  "per value set, exact z_L, I = refinement corrections; over ms_per_step"}
     out["roofline"] = roof
     out["kernels"] = {k: {"launches": v["launches"], "ms_per_step": v["ms"] / prof_steps,
                           "share": round(v["share"], 4),
@@ -518,6 +559,12 @@ def run_ours(args, rank, world, local_rank):
                    "on an element-block plan (default launch shapes)"}
         del gpl
 
+    # ---- gradient throughput: the differentiable-solve configuration (a
+    # 256x256 5-point grid, w in FP32, loss ||x - x*||^2): forward refactor +
+    # solve, then the hand-written adjoint through the autograd Function ----
+    if args.workload == "arap":
+        out["gradient"] = gradient_rate(S, dev, stream, flush, args.steps, args.warmup, world)
+
     # ---- end to end through the host-buffer C-ABI call --------------------
     import concurrent.futures
     pool = concurrent.futures.ThreadPoolExecutor(max_workers=len(plans32))
@@ -565,6 +612,55 @@ def run_ours(args, rank, world, local_rank):
     out["fp32_refine_over_fp64"] = out["value"] / out["fp64"]["value"]
     out["_xcheck"] = {"fp32": xs32, "fp64": _pick_samples(work, dev64)}
     return out, rank
+
+
+def gradient_rate(S, dev, stream, flush, steps, warmup, world):
+    """(refactor + solve + adjoint)/s on the 256x256 grid with FP32 weights:
+    x = SscoSolve(w, shift, b), loss = ||x - x*||^2, loss.backward() gives
+    dloss/dw through ssco_backward.  The gradient is compared once, after
+    the timed steps, with the FP64 oracle's analytic gradient."""
+    import torch
+    g = P.grid_problem(256, 256, batch=1, cfg=4, w_dtype=np.float32)
+    gpl = S.Plan(g, precision=S.FP32_REFINE, batch=1).bind(dev)
+    w0 = torch.tensor(np.asarray(g.vals, np.float32), device=dev)
+    sh = torch.tensor(np.asarray(g.shift, np.float64), device=dev)
+    b = torch.tensor(g.b, device=dev)
+    xs = torch.tensor(g.xstar, device=dev)
+
+    def one():
+        w = w0.clone().requires_grad_(True)
+        x = S.ssco_solve(gpl, w, sh, b)
+        loss = ((x - xs) ** 2).sum()
+        loss.backward()
+        return w.grad, x
+    for _ in range(max(warmup, 3)):
+        one()
+    torch.cuda.synchronize()
+    k = max(5, min(steps, 50))
+    ms = []
+    for _ in range(k):
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        gw, x = one()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    st = gpl.status()
+    out = {"value": world * k / (sum(ms) / 1e3), "unit": "(refactor+solve+adjoint)/s", "steps": k,
+           "ms_per_step": sum(ms) / k, "all_status_ok": bool(np.all(st["status"] == 0)),
+           "workload": "grid256 (5-point, n=65536, 130560 edges, w fp32), loss ||x - x*||^2",
+           "api": "SscoSolve (torch.autograd.Function): ssco_numeric + ssco_solve, ssco_backward"}
+    try:
+        from oracle import oracle as O
+        r = O.refactor_solve(g, 0)
+        gv, _, _ = O.backward(g, r, 2.0 * (r.x - g.xstar[0]), 0)
+        d = gw.detach().double().cpu().numpy().ravel()
+        out["grad_rel_err_vs_oracle"] = float(np.max(np.abs(d - gv)) / np.max(np.abs(gv)))
+    except Exception as e:   # the oracle library is built by __graft_entry__.build()
+        out["grad_rel_err_vs_oracle"] = f"not checked: {e}"
+    del gpl
+    return out
 
 
 def _pick_samples(work, dev_in):
