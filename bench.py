@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="only the timed FP32 region")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="skip ssco_autotune of the launch shapes before timing")
+    ap.add_argument("--oracle-limit", type=float, default=None,
+                    help="seconds a CPU-oracle worker may run (default: scaled with its dealt work)")
     ap.add_argument("--batch", type=int, default=None,
                     help="value sets of the main pattern (default: the workload's own; smaller only for profiling)")
     a = ap.parse_args()
@@ -287,10 +289,10 @@ def run_ours(args, rank, world, local_rank):
     work, desc = make_workload(args.workload, rank, args.batch)
     units = units_of(work)
     stream = torch.cuda.current_stream()
-    # The plans of a step are independent (separate patterns): plan 0 runs on
-    # the timing stream, every other plan on its own stream forked from it
-    # and joined back before the step's end event, so that the latency-bound
-    # levels of one overlap the work of another.
+    # The plans of a step are independent (separate patterns): the timed
+    # step runs them as concurrent branches of one graph, so that the
+    # latency-bound levels of one overlap the work of another; the
+    # host-buffer calls of the end-to-end measurement use one stream each.
     streams = [stream] + [torch.cuda.Stream(device=dev) for _ in work[1:]]
 
     def setup(precision):
@@ -324,18 +326,11 @@ def run_ours(args, rank, world, local_rank):
     launches_per_step = {}
 
     def step(plans, dev_in):
-        # one captured CUDA graph per plan (numeric + solve, refinement loop
-        # on the device); the kernels it runs are those of an eager step
-        fork = torch.cuda.Event()
-        fork.record(stream)
-        for i, (pl, (v, s, b, x)) in enumerate(zip(plans, dev_in)):
-            if i:
-                streams[i].wait_event(fork)
-            pl.graph_run(v, s, b, x, stream=streams[i])
-        for st in streams[1:len(plans)]:
-            join = torch.cuda.Event()
-            join.record(st)
-            stream.wait_event(join)
+        # ONE captured CUDA graph for the whole step: every plan's numeric +
+        # solve (refinement loop on the device) is an independent branch;
+        # the kernels it runs are those of an eager step
+        S.graph_run_many(plans, [t[0] for t in dev_in], [t[1] for t in dev_in], [t[2] for t in dev_in],
+                         [t[3] for t in dev_in], stream=stream)
         return launches_per_step.get(id(plans), 0)
 
     def timed(plans, dev_in, K, W, sampler=None):
@@ -392,8 +387,8 @@ def run_ours(args, rank, world, local_rank):
         "config": dict(desc, precision="fp32+refine", units_per_step=units, l2="flushed between steps "
                        "(256 MiB write); per-step working set also exceeds L2",
                        parallelism=f"independent value sets per rank x{world}",
-                       api="ssco_graph_run: one captured CUDA graph per plan, plans on concurrent streams, "
-                           "refinement loop on the device"),
+                       api="ssco_graph_run_many: one captured CUDA graph per step, the plans as concurrent "
+                           "branches, refinement loops on the device"),
         "gpu_launches": launches,
         "all_status_ok": ok32, "max_rel_residual": res32,
         "refine_iters": {"min": int(min(its32)), "max": int(max(its32)), "mean": float(np.mean(its32))},
@@ -485,17 +480,9 @@ def run_ours(args, rank, world, local_rank):
                         torch.tensor(pos, device=dev), int(m_off[-1])))
 
         def geo_step(plans, dev_in):
-            fork = torch.cuda.Event()
-            fork.record(stream)
-            for i, (pl, (v, s, b, x), (tri, te, pos, mt)) in enumerate(zip(plans, dev_in, geo)):
-                if i:
-                    streams[i].wait_event(fork)
-                S.cotan_weights(tri, te, pos, mt, stream=streams[i], out=v, check=False)
-                pl.graph_run(v, s, b, x, stream=streams[i])
-            for st in streams[1:len(plans)]:
-                join = torch.cuda.Event()
-                join.record(st)
-                stream.wait_event(join)
+            for (v, s, b, x), (tri, te, pos, mt) in zip(dev_in, geo):
+                S.cotan_weights(tri, te, pos, mt, stream=stream, out=v, check=False)
+            step(plans, dev_in)
 
         for _ in range(args.warmup):
             geo_step(plans32, dev32)
@@ -514,7 +501,7 @@ def run_ours(args, rank, world, local_rank):
         out["values_from_geometry"] = {
             "value": units * world * args.steps / (sum(gms) / 1e3), "unit": "systems/s",
             "ms_per_step": sum(gms) / args.steps, "all_status_ok": okg, "max_rel_residual": resg,
-            "api": "ssco_cotan_weights (positions -> cotangent weights on the device) + ssco_graph_run"}
+            "api": "ssco_cotan_weights (positions -> cotangent weights on the device) + ssco_graph_run_many"}
         del geo
 
     # ---- values from geometry (elasticity): the same mesh with the vertex
@@ -716,7 +703,7 @@ def _one_system(p, i):
     return q
 
 
-def _oracle_worker(barrier, chunk, queue):
+def _oracle_worker(barrier, chunk, queue, limit_s):
     """One host core: the symbolic phase of its patterns first (untimed), then,
     after every worker is ready, its systems through the oracle."""
     from oracle import oracle as O
@@ -725,18 +712,29 @@ def _oracle_worker(barrier, chunk, queue):
         key = (q["name"], q["n"], q["m"])
         if key not in symbs:
             symbs[key] = O.Symbolic(O.permute(O.assemble(q, 0), q.perm))
-    barrier.wait(timeout=600)   # a worker that never arrives breaks the barrier: no hang
+    barrier.wait(timeout=limit_s)   # a worker that never arrives breaks the barrier: no hang
     t0 = time.perf_counter()
     for q in chunk:
         O.refactor_solve(q, 0, symb=symbs[(q["name"], q["n"], q["m"])])
     queue.put(time.perf_counter() - t0)
 
 
-def time_oracle_all_cores(items):
+def oracle_limit_s(loads):
+    """Bound on one worker's run (its symbolic phase, then its systems): a
+    generous multiple of the dealt work (about 2e-6 s per unit of n^1.5,
+    which covers the 3D elasticity patterns, whose cost grows faster than
+    the planar ones the load model is fitted to), never below 10 minutes."""
+    return 600.0 + 2e-6 * max(loads, default=0.0)
+
+
+def time_oracle_all_cores(items, limit_s=None):
     """The oracle on every host core: the systems are dealt to one spawned
     process per core (largest first, to the least loaded core), the
     processes start together at a barrier, and the wall time is the slowest
-    one's.  Returns (wall seconds, summed busy seconds, processes)."""
+    one's.  A worker that dies, or a run beyond limit_s (default: scaled
+    with the dealt work, see oracle_limit_s) raises RuntimeError after the
+    other workers are stopped.  Returns (wall seconds, summed busy seconds,
+    processes, the limit used)."""
     import multiprocessing as mp
     ctx = mp.get_context("spawn")     # safe after CUDA initialisation
     cores = len(os.sched_getaffinity(0))
@@ -749,12 +747,14 @@ def time_oracle_all_cores(items):
         j = int(np.argmin(loads))
         chunks[j].append(q)
         loads[j] += q["n"] ** 1.5       # nested-dissection cost of a 2D pattern
+    if limit_s is None:
+        limit_s = oracle_limit_s(loads)
     barrier, queue = ctx.Barrier(len(chunks)), ctx.Queue()
-    procs = [ctx.Process(target=_oracle_worker, args=(barrier, c, queue)) for c in chunks]
+    procs = [ctx.Process(target=_oracle_worker, args=(barrier, c, queue, limit_s)) for c in chunks]
     for pr in procs:
         pr.start()
     import queue as _queue
-    times, deadline = [], time.monotonic() + 1800
+    times, deadline = [], time.monotonic() + 2 * limit_s
     try:
         while len(times) < len(procs):
             try:
@@ -768,7 +768,7 @@ def time_oracle_all_cores(items):
             if pr.is_alive() and len(times) < len(procs):
                 pr.terminate()
             pr.join()
-    return max(times), sum(times), len(procs)
+    return max(times), sum(times), len(procs), limit_s
 
 
 def cpu_baseline(args, work):
@@ -780,10 +780,10 @@ def cpu_baseline(args, work):
     else:
         items = oracle_sample(work)
         sample = "one full step (all systems), FP64 oracle, symbolic excluded"
-    wall, busy, procs = time_oracle_all_cores(items)
+    wall, busy, procs, limit = time_oracle_all_cores(items, args.oracle_limit)
     return {"value": len(items) / wall, "unit": "systems/s", "cores": procs, "kind": "oracle",
             "sample": sample + f", one process per host core ({procs})", "seconds": wall,
-            "value_per_core": len(items) / busy}
+            "value_per_core": len(items) / busy, "limit_s": limit}
 
 
 def run_reference(args, rank, world):
@@ -798,7 +798,7 @@ def run_reference(args, rank, world):
         sample = "all systems of one step"
     # all steps' systems at once, over every host core (warm-up is moot for
     # the compiled oracle; the symbolic phase is outside the timed region)
-    tot, busy, procs = time_oracle_all_cores(items * args.steps)
+    tot, busy, procs, limit = time_oracle_all_cores(items * args.steps, args.oracle_limit)
     value = len(items) * args.steps / tot
     return {"impl": "reference", "metric": "batched refactor+solve/s (FP32 factor + FP64 refinement to rel. "
             "residual 1e-10)", "value": value, "unit": "systems/s", "n_gpus": world, "steps": args.steps,
@@ -807,7 +807,7 @@ def run_reference(args, rank, world):
             "config": dict(desc, precision="fp64 oracle"),
             "cpu_baseline": {"kind": "oracle", "cores": procs, "sample": sample + f" x {args.steps} steps, one "
                              f"process per host core", "value": value, "unit": "systems/s",
-                             "value_per_core": len(items) * args.steps / busy},
+                             "value_per_core": len(items) * args.steps / busy, "limit_s": limit},
             "e2e": {"value": value, "unit": "systems/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 

@@ -120,7 +120,22 @@ typedef struct {
  *   SM (0 = default off; ssco_autotune may switch it on).
  * cluster_rows: fronts with at least this many rows (below split_rows)
  *   are solved by one 8-CTA thread-block cluster per value set
- *   (0 = default: 512 with <= 4 value sets, else never; -1 = never).  */
+ *   (0 = default: 512 with <= 4 value sets, else never; -1 = never).
+ * refine_mode (SSCO_FP32_REFINE): 0 = the plain refinement above; 1 =
+ *   GMRES-IR: each correction solves K d = r by restarted GMRES in FP64,
+ *   right-preconditioned by the FP32 factor (d = sum_i y_i M^-1 v_i with
+ *   M = L L^T applied as two FP32 triangular solves), until the GMRES
+ *   residual estimate falls by 1e-4 or gmres_restart steps; 2 = plain
+ *   refinement first, then GMRES-IR for the systems where it stagnated or
+ *   ran out of iterations (each phase has refine_max_iter corrections).  A
+ *   plan with refine_mode != 0 holds 2*gmres_restart + 1 more FP64 vectors
+ *   [B][n] in its workspace; its ssco_graph_run runs the eager calls (it
+ *   synchronizes `stream`).  There the FP32 factor is only a preconditioner:
+ *   a non-positive FP32 pivot is replaced by 1 and reported in bad_col, and
+ *   the system's status is the refinement's (OK once the FP64 residual met
+ *   refine_tol), not SSCO_ERR_NOT_SPD.
+ * gmres_restart: Krylov vectors per GMRES-IR correction (1 .. 64; 0 =
+ *   default 16).  */
 typedef struct {
     int32_t precision;
     int32_t batch;
@@ -134,6 +149,8 @@ typedef struct {
     int32_t split_rows;
     int32_t warp_front_max;
     int32_t cluster_rows;
+    int32_t refine_mode;
+    int32_t gmres_restart;
 } ssco_op;
 
 /* Sizes and counts of an analyzed plan (all for the concatenated system). */
@@ -233,8 +250,13 @@ ssco_status ssco_numeric(ssco_plan plan, const void* vals, int32_t vals_dtype, c
  * the order of Sec. 4.3 (reversed for L^T); the FP32 form adds iterative
  * refinement in FP64, which the paper does not use.
  * x = K^-1 b for every system (device, double [B][n] each; b and x may not
- * alias).  In SSCO_FP32_REFINE mode the refinement loop runs on the device;
- * the host reads one flag per iteration, so this call synchronizes `stream`. */
+ * alias).  Asynchronous.  In SSCO_FP32_REFINE mode the refinement loop runs
+ * on the device as a captured CUDA graph with a conditional WHILE node,
+ * captured on the first call for a (b, x) pointer pair (two pairs are kept)
+ * and replayed afterwards; make that first call outside any stream capture
+ * of your own.  With refine_mode != 0 (GMRES-IR), or while per-launch
+ * profiling is on, the loop is host-driven and the call synchronizes
+ * `stream`. */
 ssco_status ssco_solve(ssco_plan plan, const double* b, double* x, void* stream);
 
 /* Defined by: the reverse-mode derivative of x = K^-1 b (the derivatives
@@ -251,7 +273,9 @@ ssco_status ssco_solve(ssco_plan plan, const double* b, double* x, void* stream)
  *   shift_bar  = -mu^T x over shifted diagonals, per system
  *   b_bar      = mu.
  * Device arrays: x, xbar, b_bar [B][n]; vals_bar [B][m]; shift_bar
- * [n_systems] (may be NULL).  Synchronizes `stream` like ssco_solve. */
+ * [n_systems] (may be NULL).  Its solve behaves like ssco_solve's (a
+ * captured graph for FP32 plans with plain refinement, keyed by xbar and
+ * the workspace's adjoint vector). */
 ssco_status ssco_backward(ssco_plan plan, const double* x, const double* xbar, double* vals_bar,
                           double* shift_bar, double* b_bar, void* stream);
 
@@ -307,6 +331,20 @@ ssco_status ssco_set_flow(ssco_plan plan, int32_t flow, int64_t max_polls, int32
  * it outside any stream capture of your own.  Asynchronous on `stream`. */
 ssco_status ssco_graph_run(ssco_plan plan, const void* vals, int32_t vals_dtype, const double* shift, const double* b,
                            double* x, void* stream);
+
+/* ssco_graph_run over several plans as ONE CUDA graph: each plan's
+ * assemble + refactor + solve (with its own device-side refinement loop)
+ * is an independent branch of the graph, so the latency-bound levels of one
+ * plan overlap the work of the others (e.g. many value sets on one pattern
+ * beside single instances of patterns of uneven size).  Array arguments
+ * have one entry per plan, as for ssco_graph_run.  The graph is held by
+ * plans[0] and re-captured when a plan, a pointer or a dtype changes, or
+ * after anything that releases a plan's graphs (ssco_bind, ssco_autotune,
+ * ssco_set_flow).  No plan may appear twice; call it outside any stream
+ * capture of your own.  Asynchronous on `stream`. */
+ssco_status ssco_graph_run_many(const ssco_plan* plans, int32_t n_plans, const void* const* vals,
+                                const int32_t* vals_dtype, const double* const* shift, const double* const* b,
+                                double* const* x, void* stream);
 
 /* End-to-end call on HOST buffers: copies vals/shift/b to the device
  * (staging areas inside the workspace), runs numeric + solve as the captured

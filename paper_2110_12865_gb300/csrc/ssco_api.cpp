@@ -144,7 +144,8 @@ bool serialize(IO& io, Plan& P) {
     bool ok = true;
     auto S = [&](auto& x) { ok = ok && io.pod(x); };
     auto V = [&](auto& x) { ok = ok && io.vec(x); };
-    S(P.prec); S(P.B); S(P.tol); S(P.maxit); S(P.small_max); S(P.amalg); S(P.tiny_max); S(P.tsize);
+    S(P.prec); S(P.B); S(P.tol); S(P.maxit); S(P.refine_mode); S(P.gmres_m); S(P.small_max); S(P.amalg);
+    S(P.tiny_max); S(P.tsize);
     S(P.n_pats); V(P.pats); S(P.n); S(P.m);
     V(P.Kcolptr); V(P.Krowind); V(P.kslot_of_q); S(P.nnzK);
     V(P.perm); V(P.parent); V(P.colcount); V(P.col_level);
@@ -391,8 +392,13 @@ ssco_status ssco_status_get(ssco_plan h, void* stream, int32_t* status, int32_t*
     if (dev_err)
         for (size_t i = 0; i < S; ++i) st[i] = SSCO_ERR_TIMEOUT;
     ssco_status worst = SSCO_OK;
+    // With GMRES-IR the FP32 factor is only a preconditioner: a non-positive
+    // FP32 pivot (replaced by 1, reported in bad_col) does not end the system,
+    // whose status is the refinement's (OK once the FP64 residual met the
+    // tolerance).
+    const bool pivot_is_final = !(P.prec == SSCO_FP32_REFINE && P.refine_mode != 0);
     for (size_t i = 0; i < S; ++i) {
-        int32_t sc = bc[i] != INT_MAX ? (int32_t)SSCO_ERR_NOT_SPD : st[i];
+        int32_t sc = bc[i] != INT_MAX && pivot_is_final ? (int32_t)SSCO_ERR_NOT_SPD : st[i];
         if (status) status[i] = sc;
         if (iters) iters[i] = it[i];
         if (resid) resid[i] = rs[i];
@@ -483,6 +489,30 @@ ssco_status ssco_graph_run(ssco_plan h, const void* vals, int32_t vals_dtype, co
     int e = launch_graph_run(P, vals, vals_dtype, shift, b, x, stream);
     if (e) return cuda_fail(h, e, "graph capture or launch");
     P.factored = true;
+    return SSCO_OK;
+}
+
+ssco_status ssco_graph_run_many(const ssco_plan* plans, int32_t n_plans, const void* const* vals,
+                                const int32_t* vals_dtype, const double* const* shift, const double* const* b,
+                                double* const* x, void* stream) {
+    if (!plans || n_plans < 1 || n_plans > 1024 || !vals || !vals_dtype || !shift || !b || !x)
+        return fail(nullptr, SSCO_ERR_INVALID_ARG, "NULL argument or plan count outside 1..1024");
+    std::vector<Plan*> ps(n_plans);
+    for (int32_t i = 0; i < n_plans; ++i) {
+        if (!plans[i]) return fail(nullptr, SSCO_ERR_INVALID_ARG, "NULL plan");
+        for (int32_t k = 0; k < i; ++k)
+            if (plans[k] == plans[i]) return fail(plans[i], SSCO_ERR_INVALID_ARG, "a plan appears twice");
+        Plan& P = plans[i]->P;
+        if (!vals[i] || !shift[i] || !b[i] || !x[i]) return fail(plans[i], SSCO_ERR_INVALID_ARG, "NULL argument");
+        if (vals_dtype[i] != SSCO_VALS_F64 && vals_dtype[i] != SSCO_VALS_F32)
+            return fail(plans[i], SSCO_ERR_INVALID_ARG, "unknown vals dtype");
+        if (!P.bound) return fail(plans[i], SSCO_ERR_STATE, "ssco_bind has not been called");
+        if (b[i] == x[i]) return fail(plans[i], SSCO_ERR_INVALID_ARG, "b and x alias");
+        ps[i] = &P;
+    }
+    int e = launch_graph_run_many(ps.data(), n_plans, vals, vals_dtype, shift, b, x, stream);
+    if (e) return cuda_fail(plans[0], e, "multi-plan graph capture or launch");
+    for (Plan* P : ps) P->factored = true;
     return SSCO_OK;
 }
 
@@ -606,6 +636,8 @@ ssco_status ssco_plan_load(const char* path, ssco_plan* out) {
     char extra = 0;
     ok = ok && (bool)r.f.read(reinterpret_cast<char*>(&digest), sizeof(digest)) && digest == got &&
          !r.f.read(&extra, 1);
+    // options that size the workspace must be in their documented ranges
+    ok = ok && h->P.refine_mode >= 0 && h->P.refine_mode <= 2 && h->P.gmres_m >= 1 && h->P.gmres_m <= 64;
     if (!ok) {
         delete h;
         return fail(nullptr, SSCO_ERR_INVALID_ARG, "truncated or corrupt plan file (checksum)");

@@ -134,6 +134,7 @@ struct WsLayout {
     size_t st_vals, st_shift, st_b, st_x;
     size_t tcpack;
     size_t flow_fact, flow_solve;  // dataflow tickets (32 words) + done flags [slot][B]
+    size_t gm_V, gm_Z, gm_H, gm_g, gm_cs, gm_sn, gm_hp, gm_y, gm_beta, gm_hn, gm_act, gm_k;  // GMRES-IR
     size_t total;
 };
 
@@ -178,6 +179,8 @@ struct Plan {
     int32_t B = 1;
     double tol = 1e-10;
     int32_t maxit = 30;
+    int32_t refine_mode = 0;  // 0 plain, 1 GMRES-IR, 2 plain then GMRES-IR where it stagnated
+    int32_t gmres_m = 16;     // Krylov vectors per GMRES-IR correction
     int32_t small_max = 0;
     int32_t amalg = 1;
     int32_t tiny_max = 32;
@@ -274,6 +277,22 @@ struct Plan {
     const void* g_key[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     int32_t g_vdt = -1;
     int64_t g_launches = 0;
+    uint64_t g_gen = 0;  // incremented whenever this plan's captured graphs are released
+
+    // solve-only graphs of the FP32 refinement (ssco_solve, ssco_backward):
+    // two cached (b, x) pointer pairs, least recently used replaced
+    void* s_graph[2] = {nullptr, nullptr};
+    void* s_exec[2] = {nullptr, nullptr};
+    const void* s_key[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    int64_t s_launches[2] = {0, 0};
+    int32_t s_next = 0;
+    bool eager_only = false;  // set while ssco_autotune times its candidates
+
+    // one graph over several plans (ssco_graph_run_many; held by the first plan)
+    void* m_graph = nullptr;
+    void* m_exec = nullptr;
+    std::vector<const void*> m_key;  // plans, their generations, pointers and dtypes
+    int64_t m_launches = 0;
 
     // auxiliary streams for the independent launch lists of a level, with a
     // fork event and one join event per stream (created on first use)
@@ -309,6 +328,8 @@ int launch_grad_blocks(Plan& P, const double* mu, const double* x, double* vals_
 int launch_reset_status(Plan& P, void* stream);
 int launch_graph_run(Plan& P, const void* vals, int32_t vals_dtype, const double* shift, const double* b, double* x,
                      void* stream);
+int launch_graph_run_many(Plan* const* plans, int32_t n, const void* const* vals, const int32_t* vals_dtype,
+                          const double* const* shift, const double* const* b, double* const* x, void* stream);
 void graph_release(Plan& P);
 int autotune(Plan& P, const void* vals, int32_t vals_dtype, const double* shift, const double* b, double* x,
              int32_t reps, void* stream, double* best_ms);

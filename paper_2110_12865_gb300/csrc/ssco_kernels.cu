@@ -744,6 +744,43 @@ __device__ __forceinline__ int tiny_chol_rows(T (*F)[33], int lane, int r, int w
     return bad;
 }
 
+// The same partial Cholesky for fronts of at most R <= 16 rows, fully
+// unrolled: column k stays in register a[k] (no shifting) and every step's
+// update of the later columns is one shuffle and one multiply-add per
+// column with no per-lane predicate -- rows above a column's diagonal take
+// values that are never stored.
+template <class T, int R>
+__device__ __forceinline__ int tiny_chol_rows_unrolled(T (*F)[33], int lane, int r, int w, T* __restrict__ Pf,
+                                                       T* __restrict__ Uf) {
+    T a[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) a[k] = F[lane][k];
+    int bad = -1;
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        if (j < w) {
+            T djj = __shfl_sync(0xffffffffu, a[j], j);
+            if (!(djj > T(0))) {
+                if (bad < 0) bad = j;
+                djj = T(1);
+            }
+            const T ljj = sqrt(djj);
+            const T inv = T(1) / ljj;
+            a[j] = lane == j ? ljj : a[j] * inv;
+            if (lane < r) Pf[(int64_t)j * r + lane] = lane >= j ? a[j] : T(0);
+#pragma unroll
+            for (int k = j + 1; k < R; ++k) a[k] -= a[j] * __shfl_sync(0xffffffffu, a[j], k);
+        }
+    }
+    if (lane < r) {
+        const int ru = r - w;
+#pragma unroll
+        for (int k = 0; k < R; ++k)
+            if (k >= w && k < r && lane >= k) Uf[(int64_t)(k - w) * ru + (lane - w)] = a[k];
+    }
+    return bad;
+}
+
 template <class T>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2)
     k_tiny_factor(const DevTables t, int32_t n_tiny, int32_t B, int32_t prog_max, int32_t k_max,
@@ -791,9 +828,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2)
         // order: record the first failing pivot of every front (atomicMin)
         int badj;
         if (r <= 8)
-            badj = tiny_chol_rows<T, 8>(F, lane, r, w, Pb + panel_off, Ub + upd_off);
+            badj = tiny_chol_rows_unrolled<T, 8>(F, lane, r, w, Pb + panel_off, Ub + upd_off);
         else if (r <= 16)
-            badj = tiny_chol_rows<T, 16>(F, lane, r, w, Pb + panel_off, Ub + upd_off);
+            badj = tiny_chol_rows_unrolled<T, 16>(F, lane, r, w, Pb + panel_off, Ub + upd_off);
         else
             badj = tiny_chol_rows<T, 32>(F, lane, r, w, Pb + panel_off, Ub + upd_off);
         if (badj >= 0 && lane == 0) atomicMin(&bad_col[(int64_t)b * n_pats + sys], f + badj - n_off);
@@ -1954,6 +1991,70 @@ __global__ void __launch_bounds__(512) k_bwd(const DevTables t, const int32_t* _
     for (int k = tid; k < w; k += nth) vb[d.f + k] = v[k];
 }
 
+// The triangular solve with one front's 32-column diagonal block of
+// nbk <= NB columns (starting at column jb), by one warp: forward, lane l
+// holds row jb + l of the block and v_l on entry, y_l on return; backward,
+// lane l holds column jb + l (its entries on and below the diagonal) and
+// v_l - dot_l on entry, x_l on return.  Instantiated for NB = 8, 16, 32 so
+// that the narrow fronts of the lower levels do not step through 32
+// predicated columns.
+template <class T, int NB>
+__device__ __forceinline__ T diag_fwd(const T* __restrict__ Pb, int r, int jb, int nbk, int lane, T val) {
+    T a[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) a[j] = (j < nbk && lane < nbk) ? Pb[(int64_t)(jb + j) * r + jb + lane] : T(0);
+    T dl = T(1);
+#pragma unroll
+    for (int j = 0; j < NB; ++j)
+        if (lane == j && j < nbk) dl = a[j];
+    const T dinv = T(1) / dl;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+        if (j < nbk) {
+            const T yj = __shfl_sync(0xffffffffu, val, j) * __shfl_sync(0xffffffffu, dinv, j);
+            if (lane == j)
+                val = yj;
+            else if (lane > j)
+                val -= a[j] * yj;
+        }
+    }
+    return val;
+}
+
+template <class T, int NB>
+__device__ __forceinline__ T diag_bwd(const T* __restrict__ Pb, int r, int jb, int nbk, int lane, T val) {
+    T a[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j)
+        a[j] = (lane < nbk && j < nbk && j >= lane) ? Pb[(int64_t)(jb + lane) * r + jb + j] : T(0);
+#pragma unroll
+    for (int j = NB - 1; j >= 0; --j) {
+        if (j < nbk) {
+            const T dj = __shfl_sync(0xffffffffu, a[j], j);
+            const T xj = __shfl_sync(0xffffffffu, val, j) / dj;
+            if (lane == j)
+                val = xj;
+            else if (lane < j)
+                val -= a[j] * xj;
+        }
+    }
+    return val;
+}
+
+template <class T>
+__device__ __forceinline__ T diag_fwd_any(const T* __restrict__ Pb, int r, int jb, int nbk, int lane, T val) {
+    if (nbk <= 8) return diag_fwd<T, 8>(Pb, r, jb, nbk, lane, val);
+    if (nbk <= 16) return diag_fwd<T, 16>(Pb, r, jb, nbk, lane, val);
+    return diag_fwd<T, 32>(Pb, r, jb, nbk, lane, val);
+}
+
+template <class T>
+__device__ __forceinline__ T diag_bwd_any(const T* __restrict__ Pb, int r, int jb, int nbk, int lane, T val) {
+    if (nbk <= 8) return diag_bwd<T, 8>(Pb, r, jb, nbk, lane, val);
+    if (nbk <= 16) return diag_bwd<T, 16>(Pb, r, jb, nbk, lane, val);
+    return diag_bwd<T, 32>(Pb, r, jb, nbk, lane, val);
+}
+
 // Warp-per-(front, instance) variants of the two solves for levels that
 // supply many items (a batch of value sets): eight independent warps per
 // CTA, no block barriers; the 32x32 diagonal block is held in registers
@@ -1990,25 +2091,8 @@ __global__ void __launch_bounds__(256) k_fwd_warp(const DevTables t, const int32
     __syncwarp();
     for (int jb = 0; jb < w; jb += 32) {
         const int nbk = min(32, w - jb);
-        T a[32];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) a[j] = (j < nbk && lane < nbk) ? Pb[(int64_t)(jb + j) * r + jb + lane] : T(0);
-        T dl = T(1);
-#pragma unroll
-        for (int j = 0; j < 32; ++j)
-            if (lane == j && j < nbk) dl = a[j];
-        const T dinv = T(1) / dl;
         T val = lane < nbk ? v[jb + lane] : T(0);
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-            if (j < nbk) {
-                const T yj = __shfl_sync(0xffffffffu, val, j) * __shfl_sync(0xffffffffu, dinv, j);
-                if (lane == j)
-                    val = yj;
-                else if (lane > j)
-                    val -= a[j] * yj;
-            }
-        }
+        val = diag_fwd_any<T>(Pb, r, jb, nbk, lane, val);
         if (lane < nbk) v[jb + lane] = val;
         __syncwarp();
         for (int i0 = jb + nbk; i0 < r; i0 += 32) {
@@ -2071,22 +2155,8 @@ __global__ void __launch_bounds__(256) k_bwd_warp(const DevTables t, const int32
             for (; i < r; ++i) dot += col[i] * v[i];
             dot += d1 + d2 + d3;
         }
-        T a[32];
-#pragma unroll
-        for (int j = 0; j < 32; ++j)
-            a[j] = (lane < nbk && j < nbk && j >= lane) ? Pb[(int64_t)(jb + lane) * r + jb + j] : T(0);
         T val = lane < nbk ? v[jb + lane] - dot : T(0);
-#pragma unroll
-        for (int j = 31; j >= 0; --j) {
-            if (j < nbk) {
-                const T dj = __shfl_sync(0xffffffffu, a[j], j);
-                const T xj = __shfl_sync(0xffffffffu, val, j) / dj;
-                if (lane == j)
-                    val = xj;
-                else if (lane < j)
-                    val -= a[j] * xj;
-            }
-        }
+        val = diag_bwd_any<T>(Pb, r, jb, nbk, lane, val);
         if (lane < nbk) v[jb + lane] = val;
         __syncwarp();
     }
@@ -2127,185 +2197,197 @@ __device__ bool flow_wait(const int32_t* flag, int32_t want, const int32_t* dev_
     }
 }
 
-// Forward sweep over the dataflow fronts, one warp per (front, value set):
-// the k_fwd_warp arithmetic, after the children's done flags.  Values that
-// other warps of this launch wrote (the children's passing vectors) are read
+// Forward sweep over the dataflow fronts.  One CTA of G warps per item
+// (front, G consecutive value sets): the ticket, the front's descriptor and
+// the children's done flags (one per item) are shared by the G warps, and
+// warp w does the k_fwd_warp arithmetic for value set g*G + w.  Values that
+// other CTAs of this launch wrote (the children's passing vectors) are read
 // past L1 (ld.global.cg).
 template <class T>
-__global__ void __launch_bounds__(256) k_flow_fwd(const DevTables t, int32_t n_front, int32_t B, int32_t rmax,
-                                                  const T* __restrict__ panel, int64_t panel_total,
-                                                  T* __restrict__ vec, int64_t n, T* __restrict__ pvec,
-                                                  int64_t pvec_total, const int32_t* __restrict__ active,
-                                                  int32_t n_pats, int32_t* __restrict__ flow,
-                                                  int32_t* __restrict__ dev_err, uint32_t max_polls, int32_t stall) {
+__global__ void __launch_bounds__(256, 2) k_flow_fwd(const DevTables t, int32_t n_front, int32_t B, int32_t rmax,
+                                                     const T* __restrict__ panel, int64_t panel_total,
+                                                     T* __restrict__ vec, int64_t n, T* __restrict__ pvec,
+                                                     int64_t pvec_total, const int32_t* __restrict__ active,
+                                                     int32_t n_pats, int32_t* __restrict__ flow,
+                                                     int32_t* __restrict__ dev_err, uint32_t max_polls,
+                                                     int32_t stall) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    __shared__ int64_t s_item;
+    __shared__ int s_ok;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, G = blockDim.x >> 5;
     T* v = reinterpret_cast<T*>(smem_raw) + (int64_t)wib * rmax;
     int32_t* flags = flow + kFlowFlags;
-    const int64_t n_items = (int64_t)n_front * B;
+    const int nG = (B + G - 1) / G;
+    const int64_t n_items = (int64_t)n_front * nG;
     for (;;) {
-        int64_t item = 0;
-        if (lane == 0) item = atomicAdd(flow, 1);
-        item = __shfl_sync(0xffffffffu, item, 0);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            s_item = atomicAdd(flow, 1);
+            s_ok = 1;
+        }
+        __syncthreads();
+        const int64_t item = s_item;
         if (item >= n_items) return;
-        const int pos = (int)(item / B), b = (int)(item - (int64_t)pos * B);
+        const int pos = (int)(item / nG), g = (int)(item - (int64_t)pos * nG);
+        const int b = g * G + wib;
         const FrontDesc d = t.fronts[t.flow_solve[pos]];
-        if (active && !active[(int64_t)b * n_pats + d.sys]) continue;
-        bool ok = true;
-        if (item == stall) ok = flow_wait(flow + 31, 1, dev_err, max_polls);
-        for (int c = lane; ok && c < d.nchild; c += 32) {
-            const int sl = t.flow_sslot[t.child_ids[d.child_off + c]];
-            if (sl >= 0) ok = flow_wait(flags + (int64_t)sl * B + b, 1, dev_err, max_polls);
-        }
-        if (!__all_sync(0xffffffffu, ok)) {
-            if (lane == 0) atomicExch(dev_err, 1);
-            return;
-        }
-        const int r = d.r, w = d.w;
-        T* vb = vec + (int64_t)b * n;
-        const T* Pb = panel + (int64_t)b * panel_total + d.panel_off;
-        T* pv = pvec + (int64_t)b * pvec_total;
-        for (int k = lane; k < r; k += 32) v[k] = k < w ? __ldcg(vb + d.f + k) : T(0);
-        for (int c = 0; c < d.nchild; ++c) {
-            __syncwarp();
-            const FrontDesc cd = t.fronts[t.child_ids[d.child_off + c]];
-            const int rc = cd.r - cd.w;
-            const int32_t* map = t.relmap + cd.relmap_off;
-            for (int k = lane; k < rc; k += 32) v[map[k]] += __ldcg(pv + cd.pvec_off + k);
-        }
-        __syncwarp();
-        for (int jb = 0; jb < w; jb += 32) {
-            const int nbk = min(32, w - jb);
-            T a[32];
-#pragma unroll
-            for (int j = 0; j < 32; ++j)
-                a[j] = (j < nbk && lane < nbk) ? Pb[(int64_t)(jb + j) * r + jb + lane] : T(0);
-            T dl = T(1);
-#pragma unroll
-            for (int j = 0; j < 32; ++j)
-                if (lane == j && j < nbk) dl = a[j];
-            const T dinv = T(1) / dl;
-            T val = lane < nbk ? v[jb + lane] : T(0);
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                if (j < nbk) {
-                    const T yj = __shfl_sync(0xffffffffu, val, j) * __shfl_sync(0xffffffffu, dinv, j);
-                    if (lane == j)
-                        val = yj;
-                    else if (lane > j)
-                        val -= a[j] * yj;
-                }
+        if (wib == 0) {
+            bool ok = true;
+            if (item == stall) ok = flow_wait(flow + 31, 1, dev_err, max_polls);
+            for (int c = lane; ok && c < d.nchild; c += 32) {
+                const int sl = t.flow_sslot[t.child_ids[d.child_off + c]];
+                if (sl >= 0) ok = flow_wait(flags + (int64_t)sl * B + g, 1, dev_err, max_polls);
             }
-            if (lane < nbk) v[jb + lane] = val;
+            if (!__all_sync(0xffffffffu, ok) && lane == 0) {
+                atomicExch(dev_err, 1);
+                s_ok = 0;
+            }
+        }
+        __syncthreads();
+        if (!s_ok) return;
+        if (b < B && !(active && !active[(int64_t)b * n_pats + d.sys])) {
+            const int r = d.r, w = d.w;
+            T* vb = vec + (int64_t)b * n;
+            const T* Pb = panel + (int64_t)b * panel_total + d.panel_off;
+            T* pv = pvec + (int64_t)b * pvec_total;
+            for (int k = lane; k < r; k += 32) v[k] = k < w ? __ldcg(vb + d.f + k) : T(0);
+            for (int c = 0; c < d.nchild; ++c) {
+                __syncwarp();
+                const FrontDesc cd = t.fronts[t.child_ids[d.child_off + c]];
+                const int rc = cd.r - cd.w;
+                const int32_t* map = t.relmap + cd.relmap_off;
+                for (int k = lane; k < rc; k += 32) v[map[k]] += __ldcg(pv + cd.pvec_off + k);
+            }
             __syncwarp();
-            for (int i0 = jb + nbk; i0 < r; i0 += 32) {
-                const int i = i0 + lane;
-                if (i < r) {
-                    const T* col = Pb + (int64_t)jb * r + i;
-                    T acc[8];
+            for (int jb = 0; jb < w; jb += 32) {
+                const int nbk = min(32, w - jb);
+                T val = lane < nbk ? v[jb + lane] : T(0);
+                val = diag_fwd_any<T>(Pb, r, jb, nbk, lane, val);
+                if (lane < nbk) v[jb + lane] = val;
+                __syncwarp();
+                // rows below the block, four per lane (rows i0 + lane + 32u):
+                // 8 columns x 4 rows = 32 independent loads in flight per lane
+                const T* colb = Pb + (int64_t)jb * r;
+                for (int i0 = jb + nbk; i0 < r; i0 += 128) {
+                    int ii[4];
+                    T acc[4];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) acc[u] = T(0);
-                    int j = 0;
-                    for (; j + 7 < nbk; j += 8) {
-#pragma unroll
-                        for (int u = 0; u < 8; ++u) acc[u] += col[(int64_t)(j + u) * r] * v[jb + j + u];
+                    for (int u = 0; u < 4; ++u) {
+                        ii[u] = min(i0 + lane + 32 * u, r - 1);
+                        acc[u] = T(0);
                     }
-                    for (; j < nbk; ++j) acc[0] += col[(int64_t)j * r] * v[jb + j];
-                    v[i] -= ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+                    for (int j0 = 0; j0 < nbk; j0 += 8) {
+                        T x[8][4];
+#pragma unroll
+                        for (int c = 0; c < 8; ++c)
+#pragma unroll
+                            for (int u = 0; u < 4; ++u)
+                                x[c][u] = j0 + c < nbk ? colb[(int64_t)(j0 + c) * r + ii[u]] : T(0);
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) {
+                            const T y = j0 + c < nbk ? v[jb + j0 + c] : T(0);
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) acc[u] += x[c][u] * y;
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (i0 + lane + 32 * u < r) v[ii[u]] -= acc[u];
                 }
+                __syncwarp();
             }
-            __syncwarp();
+            for (int k = lane; k < w; k += 32) vb[d.f + k] = v[k];
+            for (int k = lane; k < r - w; k += 32) pv[d.pvec_off + k] = v[w + k];
         }
-        for (int k = lane; k < w; k += 32) vb[d.f + k] = v[k];
-        for (int k = lane; k < r - w; k += 32) pv[d.pvec_off + k] = v[w + k];
-        __syncwarp();
-        if (lane == 0) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
             __threadfence();
-            flow_st_release(flags + (int64_t)pos * B + b, 1);
+            flow_st_release(flags + (int64_t)pos * B + g, 1);
         }
     }
 }
 
-// Backward sweep over the dataflow fronts (parents first), one warp per
-// (front, value set): the k_bwd_warp arithmetic, after the parent's done
-// flag (which implies every ancestor's: each waited for its own parent).
+// Backward sweep over the dataflow fronts (parents first), CTA items as in
+// the forward sweep: the k_bwd_warp arithmetic per value set, after the
+// parent's done flag (which implies every ancestor's: each waited for its
+// own parent).
 template <class T>
-__global__ void __launch_bounds__(256) k_flow_bwd(const DevTables t, int32_t n_front, int32_t B, int32_t rmax,
-                                                  const T* __restrict__ panel, int64_t panel_total,
-                                                  T* __restrict__ vec, int64_t n, const int32_t* __restrict__ active,
-                                                  int32_t n_pats, int32_t* __restrict__ flow,
-                                                  int32_t* __restrict__ dev_err, uint32_t max_polls) {
+__global__ void __launch_bounds__(256, 2) k_flow_bwd(const DevTables t, int32_t n_front, int32_t B, int32_t rmax,
+                                                     const T* __restrict__ panel, int64_t panel_total,
+                                                     T* __restrict__ vec, int64_t n,
+                                                     const int32_t* __restrict__ active, int32_t n_pats,
+                                                     int32_t* __restrict__ flow, int32_t* __restrict__ dev_err,
+                                                     uint32_t max_polls) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    __shared__ int64_t s_item;
+    __shared__ int s_ok;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, G = blockDim.x >> 5;
     T* v = reinterpret_cast<T*>(smem_raw) + (int64_t)wib * rmax;
     int32_t* flags = flow + kFlowFlags;
-    const int64_t n_items = (int64_t)n_front * B;
+    const int nG = (B + G - 1) / G;
+    const int64_t n_items = (int64_t)n_front * nG;
     for (;;) {
-        int64_t item = 0;
-        if (lane == 0) item = atomicAdd(flow + 1, 1);
-        item = __shfl_sync(0xffffffffu, item, 0);
-        if (item >= n_items) return;
-        const int64_t q = n_items - 1 - item;
-        const int pos = (int)(q / B), b = (int)(q - (int64_t)pos * B);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            s_item = atomicAdd(flow + 1, 1);
+            s_ok = 1;
+        }
+        __syncthreads();
+        if (s_item >= n_items) return;
+        const int64_t q = n_items - 1 - s_item;
+        const int pos = (int)(q / nG), g = (int)(q - (int64_t)pos * nG);
+        const int b = g * G + wib;
         const FrontDesc d = t.fronts[t.flow_solve[pos]];
-        if (active && !active[(int64_t)b * n_pats + d.sys]) continue;
-        bool ok = true;
-        if (d.parent >= 0) {
-            const int sl = t.flow_sslot[d.parent];
-            if (sl >= 0) ok = flow_wait(flags + (int64_t)sl * B + b, 2, dev_err, max_polls);
-        }
-        if (!__all_sync(0xffffffffu, ok)) {
-            if (lane == 0) atomicExch(dev_err, 1);
-            return;
-        }
-        const int r = d.r, w = d.w;
-        T* vb = vec + (int64_t)b * n;
-        const T* Pb = panel + (int64_t)b * panel_total + d.panel_off;
-        const int32_t* rows = t.rows + d.rows_off;
-        for (int k = lane; k < r; k += 32) v[k] = __ldcg(vb + (k < w ? d.f + k : rows[k]));
-        __syncwarp();
-        const int nblk = (w + 31) / 32;
-        for (int bi = nblk - 1; bi >= 0; --bi) {
-            const int jb = bi * 32;
-            const int nbk = min(32, w - jb);
-            T dot = T(0);
-            if (lane < nbk) {
-                const T* col = Pb + (int64_t)(jb + lane) * r;
-                T d1 = T(0), d2 = T(0), d3 = T(0);
-                int i = jb + nbk;
-                for (; i + 3 < r; i += 4) {
-                    dot += col[i] * v[i];
-                    d1 += col[i + 1] * v[i + 1];
-                    d2 += col[i + 2] * v[i + 2];
-                    d3 += col[i + 3] * v[i + 3];
-                }
-                for (; i < r; ++i) dot += col[i] * v[i];
-                dot += d1 + d2 + d3;
+        if (wib == 0) {
+            bool ok = true;
+            if (d.parent >= 0) {
+                const int sl = t.flow_sslot[d.parent];
+                if (sl >= 0) ok = flow_wait(flags + (int64_t)sl * B + g, 2, dev_err, max_polls);
             }
-            T a[32];
-#pragma unroll
-            for (int j = 0; j < 32; ++j)
-                a[j] = (lane < nbk && j < nbk && j >= lane) ? Pb[(int64_t)(jb + lane) * r + jb + j] : T(0);
-            T val = lane < nbk ? v[jb + lane] - dot : T(0);
-#pragma unroll
-            for (int j = 31; j >= 0; --j) {
-                if (j < nbk) {
-                    const T dj = __shfl_sync(0xffffffffu, a[j], j);
-                    const T xj = __shfl_sync(0xffffffffu, val, j) / dj;
-                    if (lane == j)
-                        val = xj;
-                    else if (lane < j)
-                        val -= a[j] * xj;
-                }
+            if (!__all_sync(0xffffffffu, ok) && lane == 0) {
+                atomicExch(dev_err, 1);
+                s_ok = 0;
             }
-            if (lane < nbk) v[jb + lane] = val;
+        }
+        __syncthreads();
+        if (!s_ok) return;
+        if (b < B && !(active && !active[(int64_t)b * n_pats + d.sys])) {
+            const int r = d.r, w = d.w;
+            T* vb = vec + (int64_t)b * n;
+            const T* Pb = panel + (int64_t)b * panel_total + d.panel_off;
+            const int32_t* rows = t.rows + d.rows_off;
+            for (int k = lane; k < r; k += 32) v[k] = __ldcg(vb + (k < w ? d.f + k : rows[k]));
             __syncwarp();
+            const int nblk = (w + 31) / 32;
+            for (int bi = nblk - 1; bi >= 0; --bi) {
+                const int jb = bi * 32;
+                const int nbk = min(32, w - jb);
+                // lane j: dot_j = sum over rows i below the block of L[i, jb+j] v[i]
+                T dot = T(0);
+                if (lane < nbk) {
+                    const T* col = Pb + (int64_t)(jb + lane) * r;
+                    T d1 = T(0), d2 = T(0), d3 = T(0);
+                    int i = jb + nbk;
+                    for (; i + 3 < r; i += 4) {
+                        dot += col[i] * v[i];
+                        d1 += col[i + 1] * v[i + 1];
+                        d2 += col[i + 2] * v[i + 2];
+                        d3 += col[i + 3] * v[i + 3];
+                    }
+                    for (; i < r; ++i) dot += col[i] * v[i];
+                    dot += d1 + d2 + d3;
+                }
+                T val = lane < nbk ? v[jb + lane] - dot : T(0);
+                val = diag_bwd_any<T>(Pb, r, jb, nbk, lane, val);
+                if (lane < nbk) v[jb + lane] = val;
+                __syncwarp();
+            }
+            for (int k = lane; k < w; k += 32) vb[d.f + k] = v[k];
         }
-        for (int k = lane; k < w; k += 32) vb[d.f + k] = v[k];
-        __syncwarp();
-        if (lane == 0) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
             __threadfence();
-            flow_st_release(flags + (int64_t)pos * B + b, 2);
+            flow_st_release(flags + (int64_t)pos * B + g, 2);
         }
     }
 }
@@ -2394,30 +2476,40 @@ __global__ void __launch_bounds__(256) k_front_flow(const DevTables t, int32_t o
             const int rc = cd.r - cd.w;
             const int32_t* map = t.relmap + cd.relmap_off;
             const T* S0 = upd + (int64_t)b0 * upd_total + cd.upd_off;
-            for (int kk = warp; kk < rc; kk += nw) {
-                const int mk = map[kk];
-                T* Fk = F + (int64_t)(packed_col(mk, r) - mk) * V;
-                const T* Sk = S0 + (int64_t)kk * rc;
-                for (int i0 = kk; i0 < rc; i0 += 128) {
-                    int mi[4];
-                    T sv[4][V];
+            // the warp walks (column kk, 32-row chunk) pairs of its columns
+            // (kk = warp, warp + nw, ...), EB pairs at a time: all their
+            // loads are issued before the shared-memory adds
+            constexpr int EB = V >= 4 ? 4 : 8;
+            int kk = warp, i0 = warp;
+            while (kk < rc) {
+                int mi[EB], mk[EB];
+                T sv[EB][V];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int ii = i0 + lane + 32 * u;
-                        mi[u] = ii < rc ? map[ii] : -1;
+                for (int e = 0; e < EB; ++e) {
+                    const int ii = i0 + lane;
+                    const bool ok = kk < rc && ii < rc;
+                    mi[e] = ok ? map[ii] : -1;
+                    mk[e] = ok ? map[kk] : 0;
+                    const T* Sk = S0 + (int64_t)kk * rc + ii;
 #pragma unroll
-                        for (int v = 0; v < V; ++v)
-                            sv[u][v] = (ii < rc && v < nv) ? __ldcg(Sk + (int64_t)v * upd_total + ii) : T(0);
+                    for (int v = 0; v < V; ++v) sv[e][v] = (ok && v < nv) ? __ldcg(Sk + (int64_t)v * upd_total) : T(0);
+                    if (kk < rc) {
+                        i0 += 32;
+                        if (i0 >= rc) {
+                            kk += nw;
+                            i0 = kk;
+                        }
                     }
+                }
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        if (mi[u] < 0) continue;
-                        T x[V];
-                        vld<T, V>(Fk + (int64_t)mi[u] * V, x);
+                for (int e = 0; e < EB; ++e) {
+                    if (mi[e] < 0) continue;
+                    T* Fe = F + (int64_t)(packed_col(mk[e], r) - mk[e] + mi[e]) * V;
+                    T x[V];
+                    vld<T, V>(Fe, x);
 #pragma unroll
-                        for (int v = 0; v < V; ++v) x[v] += sv[u][v];
-                        vst<T, V>(Fk + (int64_t)mi[u] * V, x);
-                    }
+                    for (int v = 0; v < V; ++v) x[v] += sv[e][v];
+                    vst<T, V>(Fe, x);
                 }
             }
             __syncthreads();
@@ -2443,7 +2535,9 @@ __global__ void __launch_bounds__(256) k_front_flow(const DevTables t, int32_t o
                                 atomicMin(&bad_col[(int64_t)(b0 + v) * n_pats + d.sys], d.f + j0 + j - n_off);
                             dj = T(1);
                         }
-                        const T lj = sqrt(dj), inv = T(1) / lj;
+                        // one reciprocal square root instead of a square
+                        // root and a division on the pivot chain
+                        const T inv = rsqrt(dj), lj = dj * inv;
                         if (i == j)
                             a[j] = lj;
                         else if (i > j)
@@ -2719,6 +2813,220 @@ __global__ void k_update(const T* __restrict__ vecT, const int32_t* __restrict__
     const int s = b * n_pats + row_sys[i];
     const int64_t o = (int64_t)b * n + i;
     if (active[s]) xp[o] += sigma[s] * (double)vecT[o];
+}
+
+// --------------------------------------------------------------------------
+// GMRES-IR (refine_mode 1, 2): a correction solves K d = r by restarted
+// GMRES in FP64 with the FP32 factor as right preconditioner, d = Z y with
+// z_j = M^-1 v_j, M = L L^T (two FP32 triangular solves).  All active
+// systems advance in lockstep; per-system masks stop a system's inner
+// iteration when its residual estimate has fallen by kGmresEta.
+// Orthogonalisation: classical Gram-Schmidt applied twice (CGS2).
+// --------------------------------------------------------------------------
+constexpr double kGmresEta = 1e-4;
+
+// Per system: V_0 = r / beta with beta = resid * ||b|| (the 2-norm k_check
+// measured), g = (beta, 0, ...), the inner mask from the outer mask.
+__global__ void k_gm_start(const double* __restrict__ rr, const int32_t* __restrict__ row_sys, int32_t n_pats,
+                           int64_t n, const int32_t* __restrict__ active, const double* __restrict__ resid,
+                           const double* __restrict__ bnorm, double* __restrict__ V0) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int b = blockIdx.y;
+    const int s = b * n_pats + row_sys[i];
+    const int64_t o = (int64_t)b * n + i;
+    const double beta = resid[s] * bnorm[s];
+    V0[o] = active[s] && beta > 0.0 ? rr[o] / beta : 0.0;
+}
+
+__global__ void k_gm_init(int64_t S, int m, const int32_t* __restrict__ active, const double* __restrict__ resid,
+                          const double* __restrict__ bnorm, double* __restrict__ beta, double* __restrict__ g,
+                          int32_t* __restrict__ gact, int32_t* __restrict__ kdone) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    const double bt = resid[s] * bnorm[s];
+    beta[s] = bt;
+    for (int i = 0; i <= m; ++i) g[s * (m + 1) + i] = i == 0 ? bt : 0.0;
+    gact[s] = active[s] && bt > 0.0 ? 1 : 0;
+    kdone[s] = 0;
+}
+
+// vecT = (T) V_j on masked systems (unit-norm vectors need no scaling)
+template <class T>
+__global__ void k_gm_cast(const double* __restrict__ v, const int32_t* __restrict__ row_sys, int32_t n_pats,
+                          int64_t n, const int32_t* __restrict__ mask, T* __restrict__ vecT) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int b = blockIdx.y;
+    const int64_t o = (int64_t)b * n + i;
+    vecT[o] = mask[b * n_pats + row_sys[i]] ? (T)v[o] : T(0);
+}
+
+// z = (double) vecT, w = K z (symmetric CSR over permuted rows), masked
+template <class T>
+__global__ void __launch_bounds__(256) k_gm_spmv(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                                 const int32_t* __restrict__ slot, const double* __restrict__ K,
+                                                 int64_t nnzK, const int32_t* __restrict__ row_sys, int32_t n_pats,
+                                                 int64_t n, const int32_t* __restrict__ mask,
+                                                 const T* __restrict__ vecT, double* __restrict__ w) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int b = blockIdx.y;
+    const int64_t o = (int64_t)b * n + i;
+    if (!mask[b * n_pats + row_sys[i]]) {
+        w[o] = 0.0;
+        return;
+    }
+    const double* Kb = K + (int64_t)b * nnzK;
+    const T* zb = vecT + (int64_t)b * n;
+    double acc = 0.0;
+    for (int64_t q = rp[i]; q < rp[i + 1]; ++q) acc += Kb[slot[q]] * (double)zb[col[q]];
+    w[o] = acc;
+}
+
+template <class T>
+__global__ void k_gm_storez(const T* __restrict__ vecT, int64_t total, double* __restrict__ z) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < total) z[i] = (double)vecT[i];
+}
+
+// hp[s][i] = <V_i, w> over the rows of system s, i = ibase + blockIdx.y;
+// with ibase = j + 1 and w = V_j+1 it is the squared norm <w, w>
+__global__ void k_gm_dots(const double* __restrict__ V, int64_t vstride, int ibase, const double* __restrict__ w,
+                          const int64_t* __restrict__ sys_n_off, int32_t n_pats, int64_t n,
+                          const int32_t* __restrict__ mask, int m, double* __restrict__ hp) {
+    const int s = blockIdx.x, i = ibase + (int)blockIdx.y;
+    if (!mask[s]) return;
+    const int b = s / n_pats, k = s % n_pats;
+    const double* vi = V + i * vstride + (int64_t)b * n;
+    const double* wb = w + (int64_t)b * n;
+    double sum = 0.0, mx = 0.0;
+    for (int64_t r = sys_n_off[k] + threadIdx.x; r < sys_n_off[k + 1]; r += blockDim.x) sum += vi[r] * wb[r];
+    block_sum_max(sum, mx);
+    if (threadIdx.x == 0) hp[(int64_t)s * (m + 1) + i] = sum;
+}
+
+// w -= sum_{i <= j} hp[s][i] V_i, and H[s][i][j] += hp[s][i]
+__global__ void k_gm_orth(const double* __restrict__ V, int64_t vstride, const int32_t* __restrict__ row_sys,
+                          int32_t n_pats, int64_t n, const int32_t* __restrict__ mask, int m, int j,
+                          const double* __restrict__ hp, double* __restrict__ w) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int b = blockIdx.y;
+    const int s = b * n_pats + row_sys[r];
+    if (!mask[s]) return;
+    const int64_t o = (int64_t)b * n + r;
+    const double* h = hp + (int64_t)s * (m + 1);
+    double acc = w[o];
+    for (int i = 0; i <= j; ++i) acc -= h[i] * V[i * vstride + o];
+    w[o] = acc;
+}
+
+__global__ void k_gm_hacc(int64_t S, int m, int j, const int32_t* __restrict__ mask, const double* __restrict__ hp,
+                          double* __restrict__ H) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S || !mask[s]) return;
+    for (int i = 0; i <= j; ++i) H[(s * (m + 1) + i) * m + j] += hp[s * (m + 1) + i];
+}
+
+// Column j of each system's Hessenberg matrix: its subdiagonal ||w||, the
+// earlier rotations, a new Givens rotation, the residual estimate |g_j+1|;
+// a system whose estimate fell below eta * beta (or whose w vanished)
+// leaves the inner iteration with k = j + 1 vectors.
+__global__ void k_gm_givens(int64_t S, int m, int j, int32_t* __restrict__ mask, const double* __restrict__ hp,
+                            double* __restrict__ H, double* __restrict__ cs, double* __restrict__ sn,
+                            double* __restrict__ g, const double* __restrict__ beta, double* __restrict__ hn,
+                            int32_t* __restrict__ kdone, int32_t* __restrict__ any) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S || !mask[s]) return;
+    double* Hs = H + s * (m + 1) * m;
+    double* c = cs + s * m;
+    double* sv = sn + s * m;
+    double* gs = g + s * (m + 1);
+    const double wn = sqrt(fmax(hp[s * (m + 1) + j + 1], 0.0));
+    hn[s] = wn;
+    Hs[(j + 1) * m + j] = wn;
+    for (int i = 0; i < j; ++i) {
+        const double a = Hs[i * m + j], bb = Hs[(i + 1) * m + j];
+        Hs[i * m + j] = c[i] * a + sv[i] * bb;
+        Hs[(i + 1) * m + j] = -sv[i] * a + c[i] * bb;
+    }
+    const double a = Hs[j * m + j], bb = Hs[(j + 1) * m + j];
+    const double rho = hypot(a, bb);
+    const double cj = rho > 0.0 ? a / rho : 1.0, sj = rho > 0.0 ? bb / rho : 0.0;
+    c[j] = cj;
+    sv[j] = sj;
+    Hs[j * m + j] = rho;
+    Hs[(j + 1) * m + j] = 0.0;
+    gs[j + 1] = -sj * gs[j];
+    gs[j] = cj * gs[j];
+    kdone[s] = j + 1;
+    if (!(fabs(gs[j + 1]) > kGmresEta * beta[s]) || !(wn > 0.0) || j + 1 == m)
+        mask[s] = 0;
+    else
+        atomicAdd(any, 1);
+}
+
+// V_j+1 = w / ||w|| on systems still iterating
+__global__ void k_gm_next(const int32_t* __restrict__ row_sys, int32_t n_pats, int64_t n,
+                          const int32_t* __restrict__ mask, const double* __restrict__ hn, double* __restrict__ w) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int b = blockIdx.y;
+    const int s = b * n_pats + row_sys[r];
+    if (!mask[s]) return;
+    const int64_t o = (int64_t)b * n + r;
+    w[o] /= hn[s];
+}
+
+// y = R^-1 g over the k = kdone rotated columns (upper triangular R), per system
+__global__ void k_gm_backsolve(int64_t S, int m, const int32_t* __restrict__ active, const double* __restrict__ H,
+                               const double* __restrict__ g, const int32_t* __restrict__ kdone,
+                               double* __restrict__ y) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S || !active[s]) return;
+    const double* Hs = H + s * (m + 1) * m;
+    const double* gs = g + s * (m + 1);
+    double* ys = y + s * m;
+    const int k = kdone[s];
+    for (int i = k - 1; i >= 0; --i) {
+        double acc = gs[i];
+        for (int l = i + 1; l < k; ++l) acc -= Hs[i * m + l] * ys[l];
+        const double d = Hs[i * m + i];
+        ys[i] = d != 0.0 ? acc / d : 0.0;
+    }
+}
+
+// x += sum_{i < k} y_i z_i
+__global__ void k_gm_update(const double* __restrict__ Z, int64_t vstride, const int32_t* __restrict__ row_sys,
+                            int32_t n_pats, int64_t n, const int32_t* __restrict__ active,
+                            const int32_t* __restrict__ kdone, int m, const double* __restrict__ y,
+                            double* __restrict__ xp) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int b = blockIdx.y;
+    const int s = b * n_pats + row_sys[r];
+    if (!active[s]) return;
+    const int64_t o = (int64_t)b * n + r;
+    const double* ys = y + (int64_t)s * m;
+    double acc = 0.0;
+    for (int i = 0; i < kdone[s]; ++i) acc += ys[i] * Z[i * vstride + o];
+    xp[o] += acc;
+}
+
+// Systems that stopped with NO_CONVERGE are handed to the GMRES phase:
+// active again, status OK, stagnation history reset.
+__global__ void k_gm_reopen(int64_t S, int32_t* __restrict__ active, int32_t* __restrict__ sstatus,
+                            double* __restrict__ r1, double* __restrict__ r2, int32_t* __restrict__ any) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    if (sstatus[s] == SSCO_ERR_NO_CONVERGE) {
+        active[s] = 1;
+        sstatus[s] = SSCO_OK;
+        r1[s] = INFINITY;
+        r2[s] = INFINITY;
+        atomicAdd(any, 1);
+    }
 }
 
 // Sets the refinement loop's condition (any system still active) and counts
@@ -3942,9 +4250,11 @@ void run_trisolve(Plan& P, const int32_t* active, cudaStream_t s) {
     const bool sflow = (P.tune.flow & 1) && !P.flow_solve.empty() && (int64_t)P.flow_solve.size() * B < (1LL << 30);
     int32_t* sfl = wsp<int32_t>(P, P.ws.flow_solve);
     int32_t* derr = wsp<int32_t>(P, P.ws.dev_err);
-    const size_t fsmem = 8 * (size_t)P.flow_solve_rmax * sizeof(T);
-    const int64_t fitems = (int64_t)P.flow_solve.size() * B;
-    if (sflow) cudaMemsetAsync(sfl, 0, 128 + (size_t)fitems * 4, s);
+    // items of G value sets (one warp each) per CTA
+    const int G = std::min(8, B);
+    const size_t fsmem = (size_t)G * P.flow_solve_rmax * sizeof(T);
+    const int64_t fitems = (int64_t)P.flow_solve.size() * ((B + G - 1) / G);
+    if (sflow) cudaMemsetAsync(sfl, 0, 128 + (size_t)P.flow_solve.size() * B * 4, s);
     if (P.n_tiny > 0) {
         Prof pr(P, s, SSCO_K_FWD);
         k_tiny_fwd<T><<<tiny_grid, 32 * kTinyWarps, tiny_solve_bytes<T>(tiny_share(B), P.tiny_prog_max), s>>>(
@@ -3958,7 +4268,7 @@ void run_trisolve(Plan& P, const int32_t* active, cudaStream_t s) {
     }
     if (sflow) {
         Prof pr(P, s, SSCO_K_FWD);
-        k_flow_fwd<T><<<flow_grid(k_flow_fwd<T>, 256, fsmem, (fitems + 7) / 8), 256, fsmem, s>>>(
+        k_flow_fwd<T><<<flow_grid(k_flow_fwd<T>, 32 * G, fsmem, fitems), 32 * G, fsmem, s>>>(
             P.dt, (int32_t)P.flow_solve.size(), B, P.flow_solve_rmax, panel, P.panel_total, vecT, P.n, pvec,
             P.pvec_total, active, P.n_pats, sfl, derr, P.tune.flow_polls, P.tune.flow_stall);
         pr.end();
@@ -4052,7 +4362,7 @@ void run_trisolve(Plan& P, const int32_t* active, cudaStream_t s) {
     }
     if (sflow) {
         Prof pr(P, s, SSCO_K_BWD);
-        k_flow_bwd<T><<<flow_grid(k_flow_bwd<T>, 256, fsmem, (fitems + 7) / 8), 256, fsmem, s>>>(
+        k_flow_bwd<T><<<flow_grid(k_flow_bwd<T>, 32 * G, fsmem, fitems), 32 * G, fsmem, s>>>(
             P.dt, (int32_t)P.flow_solve.size(), B, P.flow_solve_rmax, panel, P.panel_total, vecT, P.n, active,
             P.n_pats, sfl, derr, P.tune.flow_polls);
         pr.end();
@@ -4073,6 +4383,13 @@ void run_trisolve(Plan& P, const int32_t* active, cudaStream_t s) {
         }
     }
 }
+
+// One GMRES-IR correction of every active system: d = Z y from GMRES(m)
+// on K d = r (r in rr from the last residual, beta = its 2-norm), then
+// x += d.  Synchronizes once per inner step to stop when every system's
+// residual estimate has converged.
+template <class T>
+int gmres_correction(Plan& P, cudaStream_t s);
 
 // While capturing a graph: the refinement loop becomes a conditional WHILE
 // node whose body is captured on body_stream.
@@ -4196,6 +4513,11 @@ int run_solve(Plan& P, const double* b, double* x, cudaStream_t s, GraphLoop* gl
         return (int)cudaGetLastError();
     }
     const int32_t* it_dev = nullptr;
+    // refine_mode 1: every correction by GMRES-IR; 2: plain corrections,
+    // then GMRES-IR for the systems those left NO_CONVERGE (with a fresh
+    // budget of maxit corrections)
+    bool gm_phase = refine && P.refine_mode == 1;
+    int maxit = P.maxit;
     for (int it = 0;; ++it) {
         {
             Prof pr(P, s, SSCO_K_RESID);
@@ -4206,14 +4528,30 @@ int run_solve(Plan& P, const double* b, double* x, cudaStream_t s, GraphLoop* gl
         {
             Prof pr(P, s, SSCO_K_CHECK);
             k_check<<<(unsigned)S, 256, 0, s>>>(rr, P.dt.sys_n_off, P.n_pats, n, bnorm, active, sst, iters, resid, r1,
-                                                r2, sigma, anyp, it, P.maxit, P.tol, refine, it_dev);
+                                                r2, sigma, anyp, it, maxit, P.tol, refine, it_dev);
             pr.done(2 * nB, nB * 8);
         }
         if (!refine) break;
         int e = (int)cudaMemcpyAsync(P.h_flag, anyp, 4, cudaMemcpyDeviceToHost, s);
         if (!e) e = (int)cudaStreamSynchronize(s);
         if (e) return e;
-        if (*P.h_flag == 0) break;
+        if (*P.h_flag == 0) {
+            if (P.refine_mode != 2 || gm_phase) break;
+            cudaMemsetAsync(anyp, 0, 4, s);
+            k_gm_reopen<<<cdiv(S, 256), 256, 0, s>>>(S, active, sst, r1, r2, anyp);
+            P.launches++;
+            e = (int)cudaMemcpyAsync(P.h_flag, anyp, 4, cudaMemcpyDeviceToHost, s);
+            if (!e) e = (int)cudaStreamSynchronize(s);
+            if (e) return e;
+            if (*P.h_flag == 0) break;
+            gm_phase = true;
+            maxit = it + P.maxit;
+        }
+        if (gm_phase) {
+            e = gmres_correction<T>(P, s);
+            if (e) return e;
+            continue;
+        }
         {
             Prof pr(P, s, SSCO_K_VECTOR);
             k_cast_scaled<T><<<gv, 256, 0, s>>>(rr, P.dt.row_sys, P.n_pats, n, active, sigma, vecT);
@@ -4235,6 +4573,80 @@ int run_solve(Plan& P, const double* b, double* x, cudaStream_t s, GraphLoop* gl
     if (!e) e = P.launch_err;
     P.launch_err = 0;
     return e;
+}
+
+template <class T>
+int gmres_correction(Plan& P, cudaStream_t s) {
+    const int B = P.B, m = P.gmres_m;
+    const int64_t n = P.n, S = (int64_t)B * P.n_pats, vstride = (int64_t)B * n;
+    const dim3 gv(cdiv(n, 256), B);
+    const unsigned gs = cdiv(S, 256);
+    double* V = wsp<double>(P, P.ws.gm_V);
+    double* Z = wsp<double>(P, P.ws.gm_Z);
+    double* H = wsp<double>(P, P.ws.gm_H);
+    double* g = wsp<double>(P, P.ws.gm_g);
+    double* cs = wsp<double>(P, P.ws.gm_cs);
+    double* sn = wsp<double>(P, P.ws.gm_sn);
+    double* hp = wsp<double>(P, P.ws.gm_hp);
+    double* y = wsp<double>(P, P.ws.gm_y);
+    double* beta = wsp<double>(P, P.ws.gm_beta);
+    double* hn = wsp<double>(P, P.ws.gm_hn);
+    int32_t* gact = wsp<int32_t>(P, P.ws.gm_act);
+    int32_t* kdone = wsp<int32_t>(P, P.ws.gm_k);
+    int32_t* active = wsp<int32_t>(P, P.ws.active);
+    int32_t* anyp = wsp<int32_t>(P, P.ws.any_active);
+    const double* rr = wsp<double>(P, P.ws.rr);
+    const double* resid = wsp<double>(P, P.ws.resid);
+    const double* bnorm = wsp<double>(P, P.ws.bnorm);
+    double* xp = wsp<double>(P, P.ws.xp);
+    T* vecT = wsp<T>(P, P.ws.vecT);
+    const double* K = wsp<double>(P, P.ws.K);
+    cudaMemsetAsync(H, 0, (size_t)S * (m + 1) * m * 8, s);
+    k_gm_init<<<gs, 256, 0, s>>>(S, m, active, resid, bnorm, beta, g, gact, kdone);
+    k_gm_start<<<gv, 256, 0, s>>>(rr, P.dt.row_sys, P.n_pats, n, active, resid, bnorm, V);
+    P.launches += 2;
+    for (int j = 0; j < m; ++j) {
+        double* W = V + (int64_t)(j + 1) * vstride;
+        {
+            Prof pr(P, s, SSCO_K_VECTOR);
+            k_gm_cast<T><<<gv, 256, 0, s>>>(V + (int64_t)j * vstride, P.dt.row_sys, P.n_pats, n, gact, vecT);
+            pr.done(0, (double)vstride * (8 + sizeof(T)));
+        }
+        run_trisolve<T>(P, gact, s);
+        {
+            Prof pr(P, s, SSCO_K_RESID);
+            k_gm_storez<T><<<cdiv(vstride, 256), 256, 0, s>>>(vecT, vstride, Z + (int64_t)j * vstride);
+            k_gm_spmv<T><<<gv, 256, 0, s>>>(P.dt.sp_rowptr, P.dt.sp_col, P.dt.sp_slot, K, P.nnzK, P.dt.row_sys,
+                                           P.n_pats, n, gact, vecT, W);
+            P.launches++;
+            pr.done(0, 0);
+        }
+        {
+            Prof pr(P, s, SSCO_K_CHECK);
+            for (int pass = 0; pass < 2; ++pass) {  // CGS2
+                k_gm_dots<<<dim3((unsigned)S, j + 1), 256, 0, s>>>(V, vstride, 0, W, P.dt.sys_n_off, P.n_pats, n,
+                                                                  gact, m, hp);
+                k_gm_orth<<<gv, 256, 0, s>>>(V, vstride, P.dt.row_sys, P.n_pats, n, gact, m, j, hp, W);
+                k_gm_hacc<<<gs, 256, 0, s>>>(S, m, j, gact, hp, H);
+                P.launches += 3;
+            }
+            k_gm_dots<<<dim3((unsigned)S, 1), 256, 0, s>>>(V, vstride, j + 1, W, P.dt.sys_n_off, P.n_pats, n, gact,
+                                                          m, hp);
+            cudaMemsetAsync(anyp, 0, 4, s);
+            k_gm_givens<<<gs, 256, 0, s>>>(S, m, j, gact, hp, H, cs, sn, g, beta, hn, kdone, anyp);
+            k_gm_next<<<gv, 256, 0, s>>>(P.dt.row_sys, P.n_pats, n, gact, hn, W);
+            P.launches += 2;
+            pr.done(0, 0);
+        }
+        int e = (int)cudaMemcpyAsync(P.h_flag, anyp, 4, cudaMemcpyDeviceToHost, s);
+        if (!e) e = (int)cudaStreamSynchronize(s);
+        if (e) return e;
+        if (*P.h_flag == 0) break;
+    }
+    k_gm_backsolve<<<gs, 256, 0, s>>>(S, m, active, H, g, kdone, y);
+    k_gm_update<<<gv, 256, 0, s>>>(Z, vstride, P.dt.row_sys, P.n_pats, n, active, kdone, m, y, xp);
+    P.launches += 2;
+    return (int)cudaGetLastError();
 }
 
 // Opt each kernel with dynamic shared memory into the largest size the
@@ -4309,9 +4721,63 @@ int launch_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, 
     return P.tsize == 8 ? run_numeric<double>(P, vals, vdt, shift, s) : run_numeric<float>(P, vals, vdt, shift, s);
 }
 
+// The FP32 refinement loop of a solve as a captured graph (conditional
+// WHILE node, no host round trip per iteration), cached per (b, x) pair.
+int solve_graph_run(Plan& P, const double* b, double* x, cudaStream_t stream) {
+    int slot = -1;
+    for (int i = 0; i < 2; ++i)
+        if (P.s_exec[i] && P.s_key[i][0] == b && P.s_key[i][1] == x) slot = i;
+    if (slot < 0) {
+        slot = P.s_next;
+        P.s_next ^= 1;
+        if (P.s_exec[slot]) cudaGraphExecDestroy((cudaGraphExec_t)P.s_exec[slot]);
+        if (P.s_graph[slot]) cudaGraphDestroy((cudaGraph_t)P.s_graph[slot]);
+        P.s_exec[slot] = P.s_graph[slot] = nullptr;
+        if (!P.g_stream) {
+            int e = (int)cudaStreamCreateWithFlags((cudaStream_t*)&P.g_stream, cudaStreamNonBlocking);
+            if (!e) e = (int)cudaStreamCreateWithFlags((cudaStream_t*)&P.g_body_stream, cudaStreamNonBlocking);
+            if (e) return e;
+        }
+        cudaStream_t cs = (cudaStream_t)P.g_stream;
+        P.launches = 0;
+        int e = (int)cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e) return e;
+        GraphLoop gl{(cudaStream_t)P.g_body_stream};
+        const int e2 = P.tsize == 8 ? run_solve<double>(P, b, x, cs, &gl) : run_solve<float>(P, b, x, cs, &gl);
+        cudaGraph_t g = nullptr;
+        const int e3 = (int)cudaStreamEndCapture(cs, &g);
+        if (e2 || e3) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return e2 ? e2 : e3;
+        }
+        cudaGraphExec_t ge = nullptr;
+        e = (int)cudaGraphInstantiate(&ge, g, 0);
+        if (e) {
+            cudaGraphDestroy(g);
+            return e;
+        }
+        P.s_graph[slot] = (void*)g;
+        P.s_exec[slot] = (void*)ge;
+        P.s_key[slot][0] = b;
+        P.s_key[slot][1] = x;
+        P.s_launches[slot] = P.launches;
+    }
+    P.launches = P.s_launches[slot];
+    return (int)cudaGraphLaunch((cudaGraphExec_t)P.s_exec[slot], stream);
+}
+
+// FP32 plans with plain refinement run the solve as a captured graph (so the
+// call does not synchronize); per-launch profiling and the autotuner's
+// timings use the eager launches.
+inline bool solve_by_graph(const Plan& P) {
+    return P.prec == SSCO_FP32_REFINE && P.refine_mode == 0 && !P.prof && !P.eager_only;
+}
+
 int launch_solve(Plan& P, const double* b, double* x, void* stream, bool* ok) {
     cudaStream_t s = (cudaStream_t)stream;
     *ok = true;
+    if (solve_by_graph(P)) return solve_graph_run(P, b, x, s);
     return P.tsize == 8 ? run_solve<double>(P, b, x, s) : run_solve<float>(P, b, x, s);
 }
 
@@ -4360,6 +4826,17 @@ void graph_release(Plan& P) {
     if (P.g_exec) cudaGraphExecDestroy((cudaGraphExec_t)P.g_exec);
     if (P.g_graph) cudaGraphDestroy((cudaGraph_t)P.g_graph);
     P.g_exec = P.g_graph = nullptr;
+    if (P.m_exec) cudaGraphExecDestroy((cudaGraphExec_t)P.m_exec);
+    if (P.m_graph) cudaGraphDestroy((cudaGraph_t)P.m_graph);
+    P.m_exec = P.m_graph = nullptr;
+    P.m_key.clear();
+    for (int i = 0; i < 2; ++i) {
+        if (P.s_exec[i]) cudaGraphExecDestroy((cudaGraphExec_t)P.s_exec[i]);
+        if (P.s_graph[i]) cudaGraphDestroy((cudaGraph_t)P.s_graph[i]);
+        P.s_exec[i] = P.s_graph[i] = nullptr;
+        P.s_key[i][0] = P.s_key[i][1] = nullptr;
+    }
+    P.g_gen++;
 }
 
 void graph_destroy_streams(Plan& P) {
@@ -4377,6 +4854,11 @@ void graph_destroy_streams(Plan& P) {
 
 int launch_graph_run(Plan& P, const void* vals, int32_t vdt, const double* shift, const double* b, double* x,
                      void* stream) {
+    if (P.refine_mode != 0) {  // the GMRES-IR loops are host-driven: eager calls
+        bool ok = true;
+        int e = launch_numeric(P, vals, vdt, shift, stream);
+        return e ? e : launch_solve(P, b, x, stream, &ok);
+    }
     const void* key[5] = {vals, shift, b, x, P.d_ws};
     bool same = P.g_exec && P.g_vdt == vdt;
     for (int i = 0; i < 5 && same; ++i) same = P.g_key[i] == key[i];
@@ -4392,6 +4874,98 @@ int launch_graph_run(Plan& P, const void* vals, int32_t vdt, const double* shift
     return (int)cudaGraphLaunch((cudaGraphExec_t)P.g_exec, (cudaStream_t)stream);
 }
 
+// Several plans' assemble + refactor + solve steps as the independent
+// branches of ONE captured graph (each with its own device-side refinement
+// loop): the capture forks from plans[0]'s capture stream to each plan's
+// own capture stream and joins back.  Held by plans[0], re-captured when a
+// plan, a pointer, a dtype or a plan's generation (bumped by every release
+// of its graphs, e.g. after ssco_autotune or ssco_set_flow) changes.
+template <class T>
+int capture_branch(Plan& P, const void* vals, int32_t vdt, const double* shift, const double* b, double* x,
+                   cudaStream_t cs) {
+    GraphLoop gl{(cudaStream_t)P.g_body_stream};
+    int e = run_numeric<T>(P, vals, vdt, shift, cs);
+    return e ? e : run_solve<T>(P, b, x, cs, &gl);
+}
+
+int launch_graph_run_many(Plan* const* plans, int32_t n, const void* const* vals, const int32_t* vdt,
+                          const double* const* shift, const double* const* b, double* const* x, void* stream) {
+    for (int32_t i = 0; i < n; ++i)
+        if (plans[i]->refine_mode != 0) {  // host-driven GMRES-IR loops: every plan eagerly, in turn
+            for (int32_t k = 0; k < n; ++k) {
+                int e = launch_graph_run(*plans[k], vals[k], vdt[k], shift[k], b[k], x[k], stream);
+                if (e) return e;
+            }
+            return 0;
+        }
+    Plan& P0 = *plans[0];
+    std::vector<const void*> key;
+    for (int32_t i = 0; i < n; ++i) {
+        const Plan& Pi = *plans[i];
+        key.insert(key.end(), {(const void*)plans[i], (const void*)(uintptr_t)Pi.g_gen, vals[i], shift[i], b[i],
+                               x[i], Pi.d_ws, (const void*)(intptr_t)vdt[i]});
+    }
+    if (!P0.m_exec || key != P0.m_key) {
+        if (P0.m_exec) cudaGraphExecDestroy((cudaGraphExec_t)P0.m_exec);
+        if (P0.m_graph) cudaGraphDestroy((cudaGraph_t)P0.m_graph);
+        P0.m_exec = P0.m_graph = nullptr;
+        P0.m_key.clear();
+        for (int32_t i = 0; i < n; ++i) {
+            Plan& Pi = *plans[i];
+            if (!Pi.g_stream) {
+                int e = (int)cudaStreamCreateWithFlags((cudaStream_t*)&Pi.g_stream, cudaStreamNonBlocking);
+                if (!e) e = (int)cudaStreamCreateWithFlags((cudaStream_t*)&Pi.g_body_stream, cudaStreamNonBlocking);
+                if (e) return e;
+            }
+        }
+        cudaStream_t cs = (cudaStream_t)P0.g_stream;
+        std::vector<cudaEvent_t> ev(2 * n, nullptr);
+        for (auto& e1 : ev)
+            if (cudaEventCreateWithFlags(&e1, cudaEventDisableTiming) != cudaSuccess) return (int)cudaErrorUnknown;
+        std::vector<bool> prof(n);
+        int64_t launches = 0;
+        int err = (int)cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (!err) err = (int)cudaEventRecord(ev[0], cs);
+        for (int32_t i = 0; i < n && !err; ++i) {
+            Plan& Pi = *plans[i];
+            cudaStream_t si = i == 0 ? cs : (cudaStream_t)Pi.g_stream;
+            if (i > 0) err = (int)cudaStreamWaitEvent(si, ev[0], 0);
+            prof[i] = Pi.prof;
+            Pi.prof = false;
+            Pi.launches = 0;
+            if (!err)
+                err = Pi.tsize == 8 ? capture_branch<double>(Pi, vals[i], vdt[i], shift[i], b[i], x[i], si)
+                                    : capture_branch<float>(Pi, vals[i], vdt[i], shift[i], b[i], x[i], si);
+            Pi.prof = prof[i];
+            launches += Pi.launches;
+            if (!err && i > 0) {
+                err = (int)cudaEventRecord(ev[n + i], si);
+                if (!err) err = (int)cudaStreamWaitEvent(cs, ev[n + i], 0);
+            }
+        }
+        cudaGraph_t g = nullptr;
+        const int e3 = (int)cudaStreamEndCapture(cs, &g);
+        for (auto e1 : ev) cudaEventDestroy(e1);
+        if (err || e3) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return err ? err : e3;
+        }
+        cudaGraphExec_t ge = nullptr;
+        err = (int)cudaGraphInstantiate(&ge, g, 0);
+        if (err) {
+            cudaGraphDestroy(g);
+            return err;
+        }
+        P0.m_graph = (void*)g;
+        P0.m_exec = (void*)ge;
+        P0.m_key = key;
+        P0.m_launches = launches;
+    }
+    for (int32_t i = 0; i < n; ++i) plans[i]->launches = i == 0 ? P0.m_launches : 0;
+    return (int)cudaGraphLaunch((cudaGraphExec_t)P0.m_exec, (cudaStream_t)stream);
+}
+
 // Coordinate descent over the launch-shape knobs: each candidate is timed
 // (CUDA events, median of `reps` eager numeric + solve steps after one
 // warm-up) on the caller's data; the fastest setting of each knob is kept.
@@ -4404,6 +4978,7 @@ int autotune(Plan& P, const void* vals, int32_t vdt, const double* shift, const 
     if (e) return e;
     const bool prof = P.prof;
     P.prof = false;
+    P.eager_only = true;  // candidates change the launch shapes between timings
     auto measure = [&](double* ms_out) -> int {
         std::vector<float> t;
         for (int i = 0; i <= reps; ++i) {
@@ -4457,6 +5032,7 @@ int autotune(Plan& P, const void* vals, int32_t vdt, const double* shift, const 
         *k.field = arg;
     }
     P.prof = prof;
+    P.eager_only = false;
     P.tune.tuned = e ? 0 : 1;
     graph_release(P);
     cudaEventDestroy(e0);
@@ -4469,7 +5045,11 @@ int launch_backward(Plan& P, const double* x, const double* xbar, double* vals_b
                     double* b_bar, void* stream) {
     cudaStream_t s = (cudaStream_t)stream;
     double* mu = wsp<double>(P, P.ws.mu);
-    int e = P.tsize == 8 ? run_solve<double>(P, xbar, mu, s) : run_solve<float>(P, xbar, mu, s);
+    int e;
+    if (solve_by_graph(P))
+        e = solve_graph_run(P, xbar, mu, s);
+    else
+        e = P.tsize == 8 ? run_solve<double>(P, xbar, mu, s) : run_solve<float>(P, xbar, mu, s);
     if (e) return e;
     const int B = P.B;
     const int64_t n = P.n, S = (int64_t)B * P.n_pats;

@@ -197,6 +197,11 @@ ssco_status analyze_impl(const ssco_pattern* const* pats, int32_t n_pats, const 
     P.B = op->batch;
     P.tol = op->refine_tol > 0 ? op->refine_tol : 1e-10;
     P.maxit = op->refine_max_iter > 0 ? op->refine_max_iter : 30;
+    if (op->refine_mode < 0 || op->refine_mode > 2) return bad(P, SSCO_ERR_INVALID_ARG, "refine_mode must be 0, 1 or 2");
+    if (op->gmres_restart < 0 || op->gmres_restart > 64)
+        return bad(P, SSCO_ERR_INVALID_ARG, "gmres_restart must be in 0..64");
+    P.refine_mode = op->precision == SSCO_FP32_REFINE ? op->refine_mode : 0;
+    P.gmres_m = op->gmres_restart > 0 ? op->gmres_restart : 16;
     P.tsize = P.prec == SSCO_FP64 ? 8 : 4;
     // One CTA per (front, instance) holds the front as a packed lower
     // triangle in shared memory (r(r+1)/2 * sizeof(T) <= 227 KB).  Its
@@ -1136,6 +1141,23 @@ void compute_ws_layout(Plan& P) {
     w.tcpack = take(B * (size_t)P.tc_pack_total * 4);
     w.flow_fact = take(128 + B * P.flow_fact.size() * 4);
     w.flow_solve = take(128 + B * P.flow_solve.size() * 4);
+    {
+        // GMRES-IR: Krylov basis V (m+1 vectors), preconditioned vectors Z
+        // (m), per system the Hessenberg matrix, rotations, right-hand side
+        const size_t m = P.refine_mode ? (size_t)P.gmres_m : 0;
+        w.gm_V = take(m ? (m + 1) * B * n * 8 : 0);
+        w.gm_Z = take(m * B * n * 8);
+        w.gm_H = take(m ? S * (m + 1) * m * 8 : 0);
+        w.gm_g = take(m ? S * (m + 1) * 8 : 0);
+        w.gm_cs = take(S * m * 8);
+        w.gm_sn = take(S * m * 8);
+        w.gm_hp = take(m ? S * (m + 1) * 8 : 0);
+        w.gm_y = take(S * m * 8);
+        w.gm_beta = take(m ? S * 8 : 0);
+        w.gm_hn = take(m ? S * 8 : 0);
+        w.gm_act = take(m ? S * 4 : 0);
+        w.gm_k = take(m ? S * 4 : 0);
+    }
     w.total = off;
 }
 

@@ -13,12 +13,11 @@ import os
 import numpy as np
 import torch
 
-from . import problems as _problems
-
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libssco.so")
 
 SSCO_OK, SSCO_ERR_INVALID_ARG = 0, 1
+KIND_ATWA, KIND_ELEM, KIND_ELEM_BLOCKS = 0, 1, 2
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "PATTERN", 3: "NOT_SPD", 4: "NONFINITE",
                 5: "NO_CONVERGE", 6: "TIMEOUT", 7: "CUDA", 8: "OOM", 9: "UNSUPPORTED", 10: "STATE"}
 FP64, FP32_REFINE = 0, 1
@@ -35,7 +34,7 @@ EXPORTED_SYMBOLS = [
     "ssco_cotan_weights", "ssco_tet_stiffness",
     "ssco_expr_compile", "ssco_expr_get_info", "ssco_expr_export", "ssco_expr_output_shape",
     "ssco_expr_output_pattern", "ssco_expr_bind", "ssco_expr_run", "ssco_expr_last_error", "ssco_expr_destroy",
-    "ssco_expr_save", "ssco_expr_load", "ssco_set_flow",
+    "ssco_expr_save", "ssco_expr_load", "ssco_set_flow", "ssco_graph_run_many",
 ]
 KERNEL_KINDS = ["assemble", "front_small", "big_init", "big_kscatter", "big_update", "big_potrf", "big_syrk",
                 "fwd_solve", "bwd_solve", "resid", "check", "vector", "grad", "front_tiny", "big_trsm", "front_vec",
@@ -60,7 +59,8 @@ class Op(C.Structure):
                 ("refine_max_iter", C.c_int32), ("small_front_max", C.c_int32),
                 ("amalgamate", C.c_int32), ("tiny_front_max", C.c_int32), ("tensor_cores", C.c_int32),
                 ("big_panel", C.c_int32), ("split_rows", C.c_int32),
-                ("warp_front_max", C.c_int32), ("cluster_rows", C.c_int32)]
+                ("warp_front_max", C.c_int32), ("cluster_rows", C.c_int32),
+                ("refine_mode", C.c_int32), ("gmres_restart", C.c_int32)]
 
 
 class KernelStat(C.Structure):
@@ -150,6 +150,7 @@ def load_library(path: str = LIB_PATH):
         "ssco_expr_load": (i32, [C.c_char_p, C.POINTER(vp)]),
         "ssco_expr_destroy": (None, [vp]),
         "ssco_set_flow": (i32, [vp, i32, i64, i32]),
+        "ssco_graph_run_many": (i32, [vp, i32, vp, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -173,11 +174,42 @@ def _stream_ptr(stream):
     return C.c_void_p(stream.cuda_stream)
 
 
+def atwa_pattern(n, rowptr, colind, aval, perm=None):
+    """Pattern of K = A^T diag(w) A + shift I: A is m x n in CSR (rowptr
+    [m+1], colind [nnz] in [0, n), aval [nnz] the constant entries); the
+    per-call values are w [m].  perm[new] = old (None = natural order)."""
+    rowptr = np.asarray(rowptr, np.int64)
+    return {"kind": KIND_ATWA, "n": int(n), "m": int(rowptr.size - 1), "rowptr": rowptr,
+            "colind": np.asarray(colind, np.int32), "aval": np.asarray(aval, np.float64), "perm": perm}
+
+
+def elem_pattern(n, elem_dofs, elem_K0, perm=None):
+    """Pattern of K = sum_e E_e K_e^0: elem_dofs [m][d] global DOFs (-1 =
+    fixed), elem_K0 [m][d(d+1)/2] row-major packed lower triangles; the
+    per-call values are E [m]."""
+    dofs = np.asarray(elem_dofs, np.int32)
+    return {"kind": KIND_ELEM, "n": int(n), "m": int(dofs.shape[0]), "elem_dim": int(dofs.shape[1]),
+            "elem_dofs": dofs, "elem_K0": np.asarray(elem_K0, np.float64), "perm": perm}
+
+
+def elem_blocks_pattern(n, elem_dofs, perm=None):
+    """Pattern of K = sum_e K_e over m elements with the element blocks
+    themselves as the per-call values ([m][d(d+1)/2] packed lower
+    triangles per value set)."""
+    dofs = np.asarray(elem_dofs, np.int32)
+    return {"kind": KIND_ELEM_BLOCKS, "n": int(n), "m": int(dofs.shape[0]), "elem_dim": int(dofs.shape[1]),
+            "elem_dofs": dofs, "perm": perm}
+
+
 class Plan:
     """An analyzed fixed structure plus (after :meth:`bind`) its device memory.
 
-    ``problems`` is one problem dict (see ``problems.py``) or a list of them
-    (several patterns concatenated, one value set each per instance).
+    ``problems`` is one pattern or a list of them (several patterns
+    concatenated, one value set each per instance).  A pattern is a mapping
+    with the fields of ``ssco_pattern``: build one from arrays with
+    :func:`atwa_pattern`, :func:`elem_pattern` or :func:`elem_blocks_pattern`
+    (the seeded workload generators in ``problems.py`` return such mappings
+    too, with their inputs attached).
 
     Options (the fields of ``ssco_op`` in ``ssco.h``; 0 = the default):
     ``precision`` FP64 or FP32_REFINE (FP32 factor, FP64 refinement to
@@ -189,12 +221,15 @@ class Plan:
     updates, -1 SIMT only; ``big_panel`` columns per trailing update of a big
     front; ``split_rows`` / ``cluster_rows`` front sizes from which solves run
     as multi-launch splits / one CTA cluster per front (-1 never);
-    ``warp_front_max`` small-front classes factored one warp per front.
+    ``warp_front_max`` small-front classes factored one warp per front;
+    ``refine_mode`` 0 plain refinement, 1 GMRES-IR (FP64 GMRES preconditioned
+    by the FP32 factor, ``gmres_restart`` Krylov vectors), 2 plain refinement
+    then GMRES-IR for the systems where it stagnated.
     ``autotune`` re-chooses the launch-shape options on the caller's data."""
 
     def __init__(self, problems, precision=FP64, batch=None, refine_tol=1e-10, refine_max_iter=30,
                  small_front_max=0, amalgamate=1, tiny_front_max=0, tensor_cores=0, big_panel=0,
-                 split_rows=0, warp_front_max=0, cluster_rows=0, _handle=None):
+                 split_rows=0, warp_front_max=0, cluster_rows=0, refine_mode=0, gmres_restart=0, _handle=None):
         self.L = load_library()
         if _handle is not None:
             self._h = _handle
@@ -205,19 +240,19 @@ class Plan:
             for p in probs:
                 pat = Pattern()
                 pat.kind, pat.n, pat.m = int(p["kind"]), int(p["n"]), int(p["m"])
-                if pat.kind == _problems.KIND_ATWA:
+                if pat.kind == KIND_ATWA:
                     rp = np.ascontiguousarray(p["rowptr"], np.int64)
                     ci = np.ascontiguousarray(p["colind"], np.int32)
                     av = np.ascontiguousarray(p["aval"], np.float64)
                     self._keep += [rp, ci, av]
                     pat.rowptr, pat.colind, pat.aval = rp.ctypes.data, ci.ctypes.data, av.ctypes.data
-                elif pat.kind == _problems.KIND_ELEM:
+                elif pat.kind == KIND_ELEM:
                     dofs = np.ascontiguousarray(p["elem_dofs"], np.int32)
                     K0 = np.ascontiguousarray(p["elem_K0"], np.float64)
                     self._keep += [dofs, K0]
                     pat.elem_dim = int(p["elem_dim"])
                     pat.elem_dofs, pat.elem_K0 = dofs.ctypes.data, K0.ctypes.data
-                elif pat.kind == _problems.KIND_ELEM_BLOCKS:   # element blocks given per call
+                elif pat.kind == KIND_ELEM_BLOCKS:   # element blocks given per call
                     dofs = np.ascontiguousarray(p["elem_dofs"], np.int32)
                     self._keep.append(dofs)
                     pat.elem_dim = int(p["elem_dim"])
@@ -241,6 +276,8 @@ class Plan:
             op.split_rows = split_rows
             op.warp_front_max = warp_front_max
             op.cluster_rows = cluster_rows
+            op.refine_mode = refine_mode
+            op.gmres_restart = gmres_restart
             h = C.c_void_p()
             st = self.L.ssco_analyze(arr, len(pats), C.byref(op), C.byref(h))
             if st != SSCO_OK:
@@ -458,6 +495,20 @@ class SscoSolve(torch.autograd.Function):
         (x,) = ctx.saved_tensors
         vbar, sbar, bbar = ctx.plan.backward(x, xbar.contiguous())
         return None, vbar.to(ctx.vals_dtype), sbar, bbar
+
+
+def graph_run_many(plans, vals, shifts, bs, xs, stream=None):
+    """Several plans' numeric + solve as ONE captured CUDA graph (independent
+    branches; see ssco_graph_run_many).  Lists with one entry per plan."""
+    L = load_library()
+    n = len(plans)
+    arr = lambda ts: (C.c_void_p * n)(*[t.data_ptr() for t in ts])
+    dts = (C.c_int32 * n)(*[VALS_F64 if v.dtype == torch.float64 else VALS_F32 for v in vals])
+    hs = (C.c_void_p * n)(*[p._h.value if isinstance(p._h, C.c_void_p) else p._h for p in plans])
+    st = L.ssco_graph_run_many(hs, n, arr(vals), dts, arr(shifts), arr(bs), arr(xs), _stream_ptr(stream))
+    if st != SSCO_OK:
+        raise SscoError(st, L.ssco_last_error(plans[0]._h).decode())
+    return xs
 
 
 def ssco_solve(plan: Plan, vals, shift, b):

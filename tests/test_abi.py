@@ -305,3 +305,23 @@ def test_expr_abi_error_paths(S):
     assert L.ssco_expr_output_shape(h, 0, C.byref(r), None, None) == 0 and r.value == 3
     assert L.ssco_expr_get_info(None, None) == 1
     assert prog.info["n_ops"] == 3 and prog.info["n_levels"] == 1   # diagonal squares: one term each
+
+
+def test_plan_from_plain_arrays_matches_problem_dicts(S):
+    """A plan built from plain CSR / element arrays (atwa_pattern,
+    elem_pattern, elem_blocks_pattern) is the plan built from the workload
+    generators' dicts: same perm, L pattern and assembly groups."""
+    g = P.grid_problem(9, 7, batch=2, cfg=1)
+    e = P.elasticity_problem(3, batch=1, cfg=2)
+    eg = P.elasticity_geometry_problem(2, batch=1)
+    pairs = [(g, S.atwa_pattern(g.n, g.rowptr, g.colind, g.aval, g.perm)),
+             (e, S.elem_pattern(e.n, e.elem_dofs, e.elem_K0, e.perm)),
+             (eg, S.elem_blocks_pattern(eg.n, eg.elem_dofs, eg.perm))]
+    for prob, pat in pairs:
+        a = S.Plan(prob, precision=S.FP64, batch=1)
+        b = S.Plan(pat, precision=S.FP64, batch=1)
+        assert a.info == b.info
+        for what in (S.EXPORT_PERM, S.EXPORT_L_COLPTR, S.EXPORT_L_ROWIND, S.EXPORT_GROUPS):
+            assert np.array_equal(a.export(what), b.export(what))
+    both = S.Plan([pairs[0][1], pairs[1][1]], precision=S.FP32_REFINE, batch=1)
+    assert both.info["n"] == g.n + e.n and both.info["n_pats"] == 2

@@ -111,6 +111,25 @@ def test_fp32_factor_accuracy_big_fronts(S, tc):
     assert worst <= 2e-4, worst
 
 
+def test_fp32_tensor_core_factor_entries_elast24(S):
+    """The FP32 factor of the 24^3 elasticity system through the multi-CTA
+    tcgen05 path at full size: fronts span many 128 x 128 tensor-core tiles
+    in both dimensions (widths beyond 256 columns, so the narrow in-block
+    updates and the wide trailing updates both run, with ragged tile edges),
+    and every column of L agrees with the FP64 oracle to FP32-level
+    accuracy (the same 2e-4 per-column bound as the small-case test)."""
+    p = P.elasticity_problem(24, batch=1, cfg=2)
+    pl, x, st, *_ = run(S, p, S.FP32_REFINE)
+    widths = np.diff(pl.export(S.EXPORT_FRONT_FIRST))
+    assert pl.info["tune_use_tc"] == 1 and widths.max() > 256 and pl.info["max_front_rows"] > 1024
+    r, res, err = check_against_oracle(S, pl, p, x, st, 0, 0)
+    L = pl.export_L()[0]
+    Lc = r.S.Lcolptr
+    num = np.sqrt(np.add.reduceat((L - r.L) ** 2, Lc[:-1]))
+    den = np.sqrt(np.add.reduceat(r.L ** 2, Lc[:-1]))
+    assert np.max(num / den) <= 2e-4, np.max(num / den)
+
+
 @pytest.mark.parametrize("big_panel", [32, 96, 256])
 def test_big_panel_blocks_fp64_L_entries(S, big_panel):
     """Multi-CTA fronts factored in panel blocks of 32, 96 or 256 columns
@@ -381,6 +400,44 @@ def test_graph_run_matches_eager(S, prec):
         res = np.linalg.norm(O.symv(K, xh[1, off:off + p.n]) - b2.cpu().numpy()[1, off:off + p.n])
         assert res <= RESID_TOL * np.linalg.norm(b2.cpu().numpy()[1, off:off + p.n])
         off += p.n
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_graph_run_many_matches_single_graphs(S, prec):
+    """Several plans as ONE captured graph (ssco_graph_run_many: a batched
+    pattern and a plan of uneven patterns, each with its own refinement loop
+    as a branch) give bit-identical results to each plan's own graph and to
+    the eager calls, replay correctly, and re-capture when a pointer changes
+    or a plan's knobs change."""
+    precision = S.FP64 if prec == "fp64" else S.FP32_REFINE
+    items = [(P.trigrid_problem(20, batch=6, cfg=3), 6),
+             ([P.trigrid_problem(s, 1, cfg=3, seed_offset=k) for k, s in enumerate([9, 14, 21])], 1)]
+    plans, ins, ref = [], [], []
+    for item, B in items:
+        pl, x_eager, st, vals, shift, b = run(S, item, precision, batch=B)
+        plans.append(pl)
+        ins.append([torch.tensor(a, device="cuda") for a in (vals, shift, b)] +
+                   [torch.empty((B, pl.n), dtype=torch.float64, device="cuda")])
+        ref.append((x_eager, st["iters"]))
+    for rep in range(3):
+        for t in ins:
+            t[3].fill_(float("nan"))
+        S.graph_run_many(plans, [t[0] for t in ins], [t[1] for t in ins], [t[2] for t in ins], [t[3] for t in ins])
+        for pl, t, (xe, it) in zip(plans, ins, ref):
+            assert np.array_equal(t[3].cpu().numpy(), xe)
+            st = pl.status()
+            assert np.all(st["status"] == 0) and np.array_equal(st["iters"], it)
+    # a plan's knobs change (its graphs are released): the group re-captures
+    plans[1].set_flow(0)
+    S.graph_run_many(plans, [t[0] for t in ins], [t[1] for t in ins], [t[2] for t in ins], [t[3] for t in ins])
+    xs = [t[3].cpu().numpy() for t in ins]
+    for pl, t, x in zip(plans, ins, xs):
+        single = torch.empty_like(t[3])
+        pl.graph_run(t[0], t[1], t[2], single)
+        assert np.array_equal(single.cpu().numpy(), x)
+    with pytest.raises(S.SscoError):
+        S.graph_run_many([plans[0], plans[0]], [ins[0][0]] * 2, [ins[0][1]] * 2, [ins[0][2]] * 2,
+                         [ins[0][3], ins[0][3].clone()])
 
 
 def test_autotune_keeps_parity_and_persists(S, tmp_path):
@@ -712,3 +769,106 @@ def test_dataflow_wait_timeout_reports_status(S):
     for i in range(p.batch):
         r = O.refactor_solve(p, i)
         assert np.linalg.norm(O.symv(r.K, x[i]) - p.b[i]) <= RESID_TOL * np.linalg.norm(p.b[i])
+
+
+# ---------------------------------------------------------------------------
+# GMRES-IR (refine_mode 1 / 2)
+def _ill_conditioned_grid(batch=2):
+    """A 16x16 5-point grid Laplacian with the tiny shift 2e-9 (kappa ~ 5e9,
+    so kappa * u32 > 1) and right-hand sides b = K x* with seeded x* ~ N(0,1):
+    in FP32 the last pivot (about n * shift = 5e-7) is below the rounding
+    noise of the elimination, so the FP32 factor is at best a perturbed one
+    and plain refinement cannot reach 1e-10 with it (it stagnates, or the
+    pivot comes out non-positive), while the FP64 residual floor of this b
+    stays near 1e-16."""
+    p = P.grid_problem(16, 16, batch=batch, cfg=1, shift=2e-9)
+    rng = np.random.default_rng(P.seed_for(7, 0))
+    xs = rng.standard_normal((batch, p.n))
+    p["b"] = np.stack([O.symv(O.assemble(p, i), xs[i]) for i in range(batch)])
+    return p
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_gmres_ir_converges_where_plain_refinement_stagnates(S, mode):
+    """Plain refinement fails on the ill-conditioned grid (NO_CONVERGE, or
+    NOT_SPD when the FP32 last pivot comes out non-positive); GMRES-IR (every
+    correction by FP64 GMRES preconditioned with the FP32 factor, or as the
+    fallback after plain refinement stagnated) reaches the 1e-10 residual
+    with the oracle's K, and its solution agrees with the oracle's FP64
+    solution within the forward-error bound that kappa allows."""
+    p = _ill_conditioned_grid()
+    vt, st_, bt = (torch.tensor(a, device="cuda") for a in (p.vals, p.shift, p.b))
+    plain = S.Plan(p, precision=S.FP32_REFINE).bind()
+    plain.numeric(vt, st_)
+    plain.solve(bt)
+    st0 = plain.status()
+    assert np.all((st0["status"] == 5) | (st0["status"] == 3)), st0
+    assert np.all(st0["resid"] > 1e-10)
+    pl = S.Plan(p, precision=S.FP32_REFINE, refine_mode=mode).bind()
+    pl.numeric(vt, st_)
+    x = pl.solve(bt).cpu().numpy()
+    st = pl.status()
+    assert np.all(st["status"] == 0), st
+    for i in range(p.batch):
+        r = O.refactor_solve(p, i)
+        assert np.linalg.norm(O.symv(r.K, x[i]) - p.b[i]) <= RESID_TOL * np.linalg.norm(p.b[i])
+        # forward error: at most kappa (~5e9) times the 1e-10 residual; here
+        # it sits in the near-null constant mode, far inside that bound
+        assert np.linalg.norm(x[i] - r.x) <= 1e-2 * np.linalg.norm(r.x)
+    # the graph entry point runs the same (eager) calls for these plans
+    x2 = torch.empty_like(bt)
+    pl.graph_run(vt, st_, bt, x2)
+    assert np.all(pl.status()["status"] == 0)
+
+
+def test_gmres_ir_on_well_conditioned_batch_matches_plain(S):
+    """On an ordinary batched plan GMRES-IR needs at most as many corrections
+    as plain refinement and meets the same residual bound."""
+    p = P.trigrid_problem(20, batch=5, cfg=3)
+    vt, st_, bt = (torch.tensor(a, device="cuda") for a in (p.vals, p.shift, p.b))
+    its = {}
+    for mode in (0, 1):
+        pl = S.Plan(p, precision=S.FP32_REFINE, refine_mode=mode, gmres_restart=8).bind()
+        pl.numeric(vt, st_)
+        x = pl.solve(bt).cpu().numpy()
+        st = pl.status()
+        assert np.all(st["status"] == 0)
+        its[mode] = st["iters"]
+        for i in range(p.batch):
+            r = O.refactor_solve(p, i)
+            assert np.linalg.norm(O.symv(r.K, x[i]) - p.b[i]) <= RESID_TOL * np.linalg.norm(p.b[i])
+    assert np.all(its[1] <= its[0])
+
+
+def test_fp32_solve_graph_matches_eager_and_recaptures(S):
+    """ssco_solve of an FP32 plan runs its refinement loop as a captured
+    graph (no host round trip): the result and the per-system iteration
+    counts are bit-identical to the host-driven loop (forced here by
+    per-launch profiling), for two right-hand-side buffers in turn (the two
+    cached graphs) and for a third (a re-capture), and the adjoint through
+    its own cached graph matches its host-driven form."""
+    p = P.trigrid_problem(16, batch=4, cfg=3)
+    pl = S.Plan(p, precision=S.FP32_REFINE).bind()
+    vt, st_ = torch.tensor(p.vals, device="cuda"), torch.tensor(p.shift, device="cuda")
+    pl.numeric(vt, st_)
+    rng = np.random.default_rng(11)
+    bs = [torch.tensor(rng.standard_normal(p.b.shape), device="cuda") for _ in range(3)]
+    graph_x, eager_x = [], []
+    for rep in range(2):
+        for b in bs:
+            graph_x.append((pl.solve(b).cpu().numpy(), pl.status()["iters"].copy()))
+    pl.profile_enable(1000)
+    for b in bs:
+        eager_x.append((pl.solve(b).cpu().numpy(), pl.status()["iters"].copy()))
+    pl.profile_enable(0)
+    for k, (x, it) in enumerate(graph_x):
+        xe, ite = eager_x[k % 3]
+        assert np.array_equal(x, xe) and np.array_equal(it, ite)
+    x = pl.solve(bs[0])
+    xbar = 2.0 * (x - torch.tensor(rng.standard_normal(p.b.shape), device="cuda"))
+    g1 = [t.cpu().numpy() for t in pl.backward(x, xbar)]
+    pl.profile_enable(1000)
+    g2 = [t.cpu().numpy() for t in pl.backward(x, xbar)]
+    pl.profile_enable(0)
+    for a, c in zip(g1, g2):
+        assert np.array_equal(a, c)

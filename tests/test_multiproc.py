@@ -80,6 +80,27 @@ def test_oracle_timing_on_all_host_cores():
     import bench
     work, _ = bench.make_workload("tiny", 0)
     items = bench.oracle_sample(work) * 3
-    wall, busy, procs = bench.time_oracle_all_cores(items)
+    wall, busy, procs, limit = bench.time_oracle_all_cores(items)
     assert 1 <= procs <= min(len(os.sched_getaffinity(0)), len(items))
     assert 0 < wall <= busy + 1e-9
+    assert limit >= 600.0
+
+
+def test_oracle_timing_fails_fast_when_a_worker_dies():
+    """A worker whose oracle call raises (here: a system of an unknown kind)
+    ends the CPU baseline with RuntimeError within seconds, and no worker
+    process is left behind (the others were waiting at the start barrier)."""
+    import multiprocessing as mp
+    import time
+    import bench
+    work, _ = bench.make_workload("tiny", 0)
+    items = bench.oracle_sample(work) * 2
+    bad = bench._one_system(*items[0])
+    bad["kind"] = 99                                 # neither A^T W A nor element blocks
+    bad["name"] = "broken"
+    items = [(bad, 0)] + items
+    t0 = time.monotonic()
+    with pytest.raises(RuntimeError):
+        bench.time_oracle_all_cores(items, limit_s=60.0)
+    assert time.monotonic() - t0 < 30.0
+    assert not [c for c in mp.active_children() if c.is_alive()]
