@@ -185,7 +185,8 @@ typedef struct {
     int64_t tune_warp_front_max; /* small-front classes factored warp-per-front */
     int64_t tune_cluster_rows;   /* fronts this large: one CTA cluster per solve */
     int64_t tune_flow;           /* persistent dataflow launches: bit 0 solve sweeps,
-                                    bit 1 small-front factorization                 */
+                                    bit 1 small-front factorization; bit 2 the panel
+                                    core for per-level small fronts                 */
     int64_t flow_fact_fronts;    /* fronts factored by the dataflow launches         */
     int64_t flow_solve_fronts;   /* fronts solved by the dataflow sweeps             */
 } ssco_info;
@@ -313,7 +314,10 @@ ssco_status ssco_autotune(ssco_plan plan, const void* vals, int32_t vals_dtype, 
  * counter, and it waits only for the done flags of its children (factor,
  * forward sweep) or of its parent (backward sweep), never for a whole level.
  * flow: bit 0 the solve sweeps, bit 1 the factorization (default 3; 0 = one
- * launch per level and size class).  max_polls bounds every wait (polls of
+ * launch per level and size class); bit 2: the per-level launches of small
+ * fronts (those outside the dataflow) use the dataflow kernel's dense core
+ * (a 16-column panel per three barriers) instead of the column-step
+ * kernels.  max_polls bounds every wait (polls of
  * about 256 ns; 0 = keep the current bound, default 2^22): a wait that runs
  * out raises the plan's device error, the launch ends early and
  * ssco_status_get reports SSCO_ERR_TIMEOUT for every system (the results of

@@ -159,6 +159,8 @@ struct Tunables {
     int32_t cluster_rows = 512;    // ... below that, from this many rows: one CTA cluster per front
     int32_t warp_front_max = 0;    // small-front classes up to this size: one warp per front (levels
                                    // of >= warp_items fronts x value sets; autotuner option)
+    int32_t front_core = 0;        // per-level small fronts: 0 column-step kernels (k_front_small/vec),
+                                   // 1 the dataflow kernel's panel core, one CTA per item
     int32_t flow = 3;              // persistent dataflow launches: bit 0 the solve sweeps, bit 1 the
                                    // small-front factorization (0 = one launch per level and class)
     uint32_t flow_polls = 1u << 22;  // bound of every dataflow wait (polls of ~256 ns)

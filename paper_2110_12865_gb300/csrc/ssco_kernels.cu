@@ -2407,8 +2407,14 @@ __global__ void __launch_bounds__(256, 2) k_flow_bwd(const DevTables t, int32_t 
 // item's done flag is released.
 constexpr int kFlowNB = 16;
 
+//
+// With ticket < 0 the same kernel serves one level's launch list instead:
+// one CTA per item (blockIdx.x), no ticket, no waits, no flags (the
+// children were factored by earlier launches on the stream); fl is then
+// the level's front list and off is unused.
 template <class T, int V>
-__global__ void __launch_bounds__(256) k_front_flow(const DevTables t, int32_t off, int32_t count, int32_t B,
+__global__ void __launch_bounds__(256) k_front_flow(const DevTables t, const int32_t* __restrict__ fl, int32_t off,
+                                                    int32_t count, int32_t B,
                                                     const double* __restrict__ K, int64_t nnzK,
                                                     T* __restrict__ panel, int64_t panel_total,
                                                     T* __restrict__ upd, int64_t upd_total,
@@ -2429,10 +2435,10 @@ __global__ void __launch_bounds__(256) k_front_flow(const DevTables t, int32_t o
     int32_t* flags = flow + kFlowFlags;
     const int nG = (B + V - 1) / V;
     const int64_t n_items = (int64_t)count * nG;
-    for (;;) {
+    for (int rep = 0;; ++rep) {
         __syncthreads();
         if (tid == 0) {
-            s_item = atomicAdd(flow + ticket, 1);
+            s_item = ticket >= 0 ? (int64_t)atomicAdd(flow + ticket, 1) : (rep == 0 ? (int64_t)blockIdx.x : n_items);
             s_ok = 1;
         }
         __syncthreads();
@@ -2440,7 +2446,7 @@ __global__ void __launch_bounds__(256) k_front_flow(const DevTables t, int32_t o
         if (item >= n_items) return;
         const int q = (int)(item / nG), g = (int)(item - (int64_t)q * nG);
         const int b0 = g * V, nv = min(V, B - b0);
-        const FrontDesc d = t.fronts[t.flow_fact[off + q]];
+        const FrontDesc d = t.fronts[fl[q]];
         const int r = d.r, w = d.w;
         const int npk = r * (r + 1) / 2 + kSmallPad;
         for (int e = tid; e < npk * V; e += nth) F[e] = T(0);
@@ -2456,7 +2462,7 @@ __global__ void __launch_bounds__(256) k_front_flow(const DevTables t, int32_t o
                     if (v < nv) dst[v] = (T)K[(int64_t)(b0 + v) * nnzK + slot];
             }
         }
-        if (warp == 0) {
+        if (warp == 0 && ticket >= 0) {
             bool ok = true;
             if (item == stall) ok = flow_wait(flow + 31, 1, dev_err, max_polls);
             for (int c = lane; ok && c < d.nchild; c += 32) {
@@ -2672,7 +2678,7 @@ __global__ void __launch_bounds__(256) k_front_flow(const DevTables t, int32_t o
             }
         }
         __syncthreads();
-        if (tid == 0) {
+        if (tid == 0 && ticket >= 0) {
             __threadfence();
             flow_st_release(flags + (int64_t)(off + q) * B + g, 1);
         }
@@ -3427,8 +3433,8 @@ int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cud
             Prof pr(P, s, g.V > 1 ? SSCO_K_FRONT_VEC : SSCO_K_FRONT_SMALL);
 #define SSCO_FLOW_LAUNCH(VV)                                                                                     \
     k_front_flow<T, VV><<<flow_grid(k_front_flow<T, VV>, th, smem, items), th, smem, s>>>(                      \
-        P.dt, g.off, g.count, B, K, P.nnzK, panel, P.panel_total, upd, P.upd_total, bad, P.n_pats, fl, (int)gi, \
-        derr, P.tune.flow_polls, stall)
+        P.dt, P.dt.flow_fact + g.off, g.off, g.count, B, K, P.nnzK, panel, P.panel_total, upd, P.upd_total, bad, \
+        P.n_pats, fl, (int)gi, derr, P.tune.flow_polls, stall)
             // (the shared memory above is sized for g.V: exactly the
             // instantiation launched; build_flow makes g.V one of 1, 2 or 4,
             // 4 only for FP32)
@@ -3488,6 +3494,37 @@ int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cud
                 k_front_warp<T><<<cdiv(items, 8), 256, 8 * (size_t)ll.rmax * (ll.rmax + 1) / 2 * sizeof(T), st>>>(
                     P.dt, list, ll.count, B, ll.rmax, K, P.nnzK, panel, P.panel_total, upd, P.upd_total, bad,
                     P.n_pats);
+                pr.end();
+                if (pr.ev >= 0) {
+                    Work w = work_front_small(P, ll);
+                    pr.done(w.flops, w.bytes);
+                }
+                continue;
+            }
+            if (P.tune.front_core == 1) {
+                // the dataflow kernel's core (three barriers per 16-column
+                // panel), one CTA per (front, value-set group) of this list
+                const int fV = ll.rmax <= 64 ? (sizeof(T) == 4 ? 4 : 2) : (ll.rmax <= 128 && sizeof(T) == 4 ? 2 : 1);
+                int gV = fV;
+                while (gV > 1 && gV > B) gV /= 2;
+                const int th = ll.rmax <= 64 ? 128 : 256;
+                const size_t fsm = ((size_t)kFlowNB * kFlowNB + kFlowNB + (size_t)ll.rmax * (ll.rmax + 1) / 2 +
+                                    kSmallPad) * gV * sizeof(T);
+                const unsigned grid = (unsigned)((int64_t)ll.count * ((B + gV - 1) / gV));
+                int32_t* derr = wsp<int32_t>(P, P.ws.dev_err);
+                Prof pr(P, st, gV > 1 ? SSCO_K_FRONT_VEC : SSCO_K_FRONT_SMALL);
+                if (gV == 1)
+                    k_front_flow<T, 1><<<grid, th, fsm, st>>>(P.dt, list, 0, ll.count, B, K, P.nnzK, panel,
+                                                             P.panel_total, upd, P.upd_total, bad, P.n_pats, nullptr,
+                                                             -1, derr, 0, -1);
+                else if (gV == 2 || sizeof(T) == 8)
+                    k_front_flow<T, 2><<<grid, th, fsm, st>>>(P.dt, list, 0, ll.count, B, K, P.nnzK, panel,
+                                                             P.panel_total, upd, P.upd_total, bad, P.n_pats, nullptr,
+                                                             -1, derr, 0, -1);
+                else
+                    k_front_flow<T, sizeof(T) == 4 ? 4 : 2><<<grid, th, fsm, st>>>(
+                        P.dt, list, 0, ll.count, B, K, P.nnzK, panel, P.panel_total, upd, P.upd_total, bad, P.n_pats,
+                        nullptr, -1, derr, 0, -1);
                 pr.end();
                 if (pr.ev >= 0) {
                     Work w = work_front_small(P, ll);
@@ -5003,6 +5040,7 @@ int autotune(Plan& P, const void* vals, int32_t vdt, const double* shift, const 
     };
     std::vector<Knob> knobs = {
         {&P.tune.flow, {0, 1, 2, 3}},
+        {&P.tune.front_core, {0, 1}},
         {&P.tune.warp_items, {152, 2 * 152, 4 * 152, 8 * 152, 16 * 152, 1 << 30}},
         {&P.tune.vec_max_cls, {0, 64, 96}},
         {&P.tune.solve_threads_big, {256, 512}},
