@@ -116,6 +116,93 @@ __device__ __forceinline__ int packed_col(int k, int r) { return k * r - ((k * (
 // reads up to 3 x 16 rows / 3 x 16 columns past the last entry.
 constexpr int kSmallPad = 128;
 
+template <class T, int V>
+struct VecOf;
+template <>
+struct VecOf<float, 4> {
+    typedef float4 type;
+};
+template <>
+struct VecOf<double, 2> {
+    typedef double2 type;
+};
+template <>
+struct VecOf<float, 2> {
+    typedef float2 type;
+};
+template <>
+struct VecOf<float, 1> {
+    typedef float type;
+};
+template <>
+struct VecOf<double, 1> {
+    typedef double type;
+};
+
+template <class T, int V>
+__device__ __forceinline__ void vld(const T* p, T (&x)[V]) {
+    typedef typename VecOf<T, V>::type VT;
+    const VT u = *reinterpret_cast<const VT*>(p);
+    const T* e = reinterpret_cast<const T*>(&u);
+#pragma unroll
+    for (int v = 0; v < V; ++v) x[v] = e[v];
+}
+
+template <class T, int V>
+__device__ __forceinline__ void vst(T* p, const T (&x)[V]) {
+    typedef typename VecOf<T, V>::type VT;
+    VT u;
+    T* e = reinterpret_cast<T*>(&u);
+#pragma unroll
+    for (int v = 0; v < V; ++v) e[v] = x[v];
+    *reinterpret_cast<VT*>(p) = u;
+}
+
+// Adds one child's update matrix (rc x rc, lower triangle, column-major;
+// value set v at S + v * vstride) into the front's packed triangle F (V
+// value sets interleaved) through the child's relative map: the warp walks
+// (column kk, 32-row chunk) pairs of its columns kk = warp, warp + nw, ...,
+// kEB pairs at a time, issuing all their loads before the shared-memory
+// adds (one memory round trip per kEB pairs instead of per pair).
+template <class T, int V>
+__device__ __forceinline__ void extend_add(T* __restrict__ F, int r, const T* __restrict__ S, int64_t vstride,
+                                           int nv, const int32_t* __restrict__ map, int rc, int warp, int nw,
+                                           int lane) {
+    constexpr int EB = V >= 4 ? 4 : 8;
+    int kk = warp, i0 = warp;
+    while (kk < rc) {
+        int mi[EB], mk[EB];
+        T sv[EB][V];
+#pragma unroll
+        for (int e = 0; e < EB; ++e) {
+            const int ii = i0 + lane;
+            const bool ok = kk < rc && ii < rc;
+            mi[e] = ok ? map[ii] : -1;
+            mk[e] = ok ? map[kk] : 0;
+            const T* Sk = S + (int64_t)kk * rc + ii;
+#pragma unroll
+            for (int v = 0; v < V; ++v) sv[e][v] = (ok && v < nv) ? Sk[(int64_t)v * vstride] : T(0);
+            if (kk < rc) {
+                i0 += 32;
+                if (i0 >= rc) {
+                    kk += nw;
+                    i0 = kk;
+                }
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < EB; ++e) {
+            if (mi[e] < 0) continue;
+            T* Fe = F + (int64_t)(packed_col(mk[e], r) - mk[e] + mi[e]) * V;
+            T x[V];
+            vld<T, V>(Fe, x);
+#pragma unroll
+            for (int v = 0; v < V; ++v) x[v] += sv[e][v];
+            vst<T, V>(Fe, x);
+        }
+    }
+}
+
 template <class T>
 __global__ void __launch_bounds__(256) k_front_small(const DevTables t, const int32_t* __restrict__ list,
                                                      const double* __restrict__ K, int64_t nnzK,
@@ -142,15 +229,8 @@ __global__ void __launch_bounds__(256) k_front_small(const DevTables t, const in
     for (int c = 0; c < d.nchild; ++c) {
         __syncthreads();
         const FrontDesc cd = t.fronts[t.child_ids[d.child_off + c]];
-        const int rc = cd.r - cd.w;
-        const int32_t* map = t.relmap + cd.relmap_off;
-        const T* S = upd + (int64_t)b * upd_total + cd.upd_off;
-        for (int kk = warp; kk < rc; kk += nw) {
-            const int mk = map[kk];
-            T* Fk = F + packed_col(mk, r) - mk;
-            const T* Sk = S + (int64_t)kk * rc;
-            for (int ii = kk + lane; ii < rc; ii += 32) Fk[map[ii]] += Sk[ii];
-        }
+        extend_add<T, 1>(F, r, upd + (int64_t)b * upd_total + cd.upd_off, upd_total, 1, t.relmap + cd.relmap_off,
+                         cd.r - cd.w, warp, nw, lane);
     }
     __syncthreads();
     // Blocked right-looking partial factorization.  Panels of kPanel columns
@@ -390,48 +470,6 @@ __global__ void __launch_bounds__(256) k_front_warp(const DevTables t, const int
 // serves all V and the index arithmetic is paid once per V fronts (the
 // members of a group share one template expression, Sec. 4.8).
 template <class T, int V>
-struct VecOf;
-template <>
-struct VecOf<float, 4> {
-    typedef float4 type;
-};
-template <>
-struct VecOf<double, 2> {
-    typedef double2 type;
-};
-template <>
-struct VecOf<float, 2> {
-    typedef float2 type;
-};
-template <>
-struct VecOf<float, 1> {
-    typedef float type;
-};
-template <>
-struct VecOf<double, 1> {
-    typedef double type;
-};
-
-template <class T, int V>
-__device__ __forceinline__ void vld(const T* p, T (&x)[V]) {
-    typedef typename VecOf<T, V>::type VT;
-    const VT u = *reinterpret_cast<const VT*>(p);
-    const T* e = reinterpret_cast<const T*>(&u);
-#pragma unroll
-    for (int v = 0; v < V; ++v) x[v] = e[v];
-}
-
-template <class T, int V>
-__device__ __forceinline__ void vst(T* p, const T (&x)[V]) {
-    typedef typename VecOf<T, V>::type VT;
-    VT u;
-    T* e = reinterpret_cast<T*>(&u);
-#pragma unroll
-    for (int v = 0; v < V; ++v) e[v] = x[v];
-    *reinterpret_cast<VT*>(p) = u;
-}
-
-template <class T, int V>
 __global__ void __launch_bounds__(256) k_front_vec(const DevTables t, const int32_t* __restrict__ list, int32_t B,
                                                    const double* __restrict__ K, int64_t nnzK,
                                                    T* __restrict__ panel, int64_t panel_total,
@@ -458,22 +496,8 @@ __global__ void __launch_bounds__(256) k_front_vec(const DevTables t, const int3
     for (int c = 0; c < d.nchild; ++c) {
         __syncthreads();
         const FrontDesc cd = t.fronts[t.child_ids[d.child_off + c]];
-        const int rc = cd.r - cd.w;
-        const int32_t* map = t.relmap + cd.relmap_off;
-        const T* S0 = upd + (int64_t)b0 * upd_total + cd.upd_off;
-        for (int kk = warp; kk < rc; kk += nw) {
-            const int mk = map[kk];
-            T* Fk = F + (int64_t)(packed_col(mk, r) - mk) * V;
-            for (int ii = kk + lane; ii < rc; ii += 32) {
-                T x[V];
-                vld<T, V>(Fk + (int64_t)map[ii] * V, x);
-                const int64_t o = (int64_t)kk * rc + ii;
-#pragma unroll
-                for (int v = 0; v < V; ++v)
-                    if (v < nv) x[v] += S0[(int64_t)v * upd_total + o];
-                vst<T, V>(Fk + (int64_t)map[ii] * V, x);
-            }
-        }
+        extend_add<T, V>(F, r, upd + (int64_t)b0 * upd_total + cd.upd_off, upd_total, nv, t.relmap + cd.relmap_off,
+                         cd.r - cd.w, warp, nw, lane);
     }
     __syncthreads();
     constexpr int kPanel = 16;
