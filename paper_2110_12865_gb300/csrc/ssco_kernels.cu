@@ -158,6 +158,29 @@ __device__ __forceinline__ void vst(T* p, const T (&x)[V]) {
     *reinterpret_cast<VT*>(p) = u;
 }
 
+// What a front's extend-add reads of a child; the first kChildRefs
+// children's are loaded into shared memory when the CTA starts (one thread
+// each, overlapping the zeroing of the front), so each child costs no
+// dependent descriptor loads later.
+struct ChildRef {
+    int64_t upd_off, map_off;
+    int32_t rc, pad;
+};
+constexpr int kChildRefs = 32;
+
+__device__ __forceinline__ void prefetch_children(const DevTables& t, const FrontDesc& d, ChildRef* s_ch, int tid) {
+    if (tid < min(d.nchild, kChildRefs)) {
+        const FrontDesc& cd = t.fronts[t.child_ids[d.child_off + tid]];
+        s_ch[tid] = ChildRef{cd.upd_off, cd.relmap_off, cd.r - cd.w, 0};
+    }
+}
+
+__device__ __forceinline__ ChildRef child_ref(const DevTables& t, const FrontDesc& d, const ChildRef* s_ch, int c) {
+    if (c < kChildRefs) return s_ch[c];
+    const FrontDesc& cd = t.fronts[t.child_ids[d.child_off + c]];
+    return ChildRef{cd.upd_off, cd.relmap_off, cd.r - cd.w, 0};
+}
+
 // Adds one child's update matrix (rc x rc, lower triangle, column-major;
 // value set v at S + v * vstride) into the front's packed triangle F (V
 // value sets interleaved) through the child's relative map: the warp walks
@@ -203,6 +226,11 @@ __device__ __forceinline__ void extend_add(T* __restrict__ F, int r, const T* __
     }
 }
 
+// Correctly rounded reciprocal (one instruction sequence instead of a
+// division) for the pivot chain of the column steps.
+__device__ __forceinline__ float rcp_rn(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp_rn(double x) { return __drcp_rn(x); }
+
 template <class T>
 __global__ void __launch_bounds__(256) k_front_small(const DevTables t, const int32_t* __restrict__ list,
                                                      const double* __restrict__ K, int64_t nnzK,
@@ -217,6 +245,8 @@ __global__ void __launch_bounds__(256) k_front_small(const DevTables t, const in
     const int lane = threadIdx.x, warp = threadIdx.y, nw = blockDim.y;
     const int tid = lane + 32 * warp, nth = 32 * nw;
     const int npk = r * (r + 1) / 2 + kSmallPad;
+    __shared__ ChildRef s_ch[kChildRefs];
+    prefetch_children(t, d, s_ch, tid);
     for (int q = tid; q < npk; q += nth) F[q] = T(0);
     __syncthreads();
     const double* Kb = K + (int64_t)b * nnzK;
@@ -228,9 +258,9 @@ __global__ void __launch_bounds__(256) k_front_small(const DevTables t, const in
     }
     for (int c = 0; c < d.nchild; ++c) {
         __syncthreads();
-        const FrontDesc cd = t.fronts[t.child_ids[d.child_off + c]];
-        extend_add<T, 1>(F, r, upd + (int64_t)b * upd_total + cd.upd_off, upd_total, 1, t.relmap + cd.relmap_off,
-                         cd.r - cd.w, warp, nw, lane);
+        const ChildRef cr = child_ref(t, d, s_ch, c);
+        extend_add<T, 1>(F, r, upd + (int64_t)b * upd_total + cr.upd_off, upd_total, 1, t.relmap + cr.map_off, cr.rc,
+                         warp, nw, lane);
     }
     __syncthreads();
     // Blocked right-looking partial factorization.  Panels of kPanel columns
@@ -252,7 +282,7 @@ __global__ void __launch_bounds__(256) k_front_small(const DevTables t, const in
                 failed = true;
                 djj = T(1);
             }
-            const T invd = T(1) / djj;
+            const T invd = rcp_rn(djj);
             if (j > j0) {
                 T* Fp = F + packed_col(j - 1, r) - (j - 1);
                 for (int i = j + tid; i < r; i += nth) Fp[i] *= prev_inv;
@@ -263,8 +293,8 @@ __global__ void __launch_bounds__(256) k_front_small(const DevTables t, const in
                 T* Fk = F + packed_col(k, r) - k;
                 for (int i = k + lane; i < r; i += 32) Fk[i] -= Fj[i] * lk;
             }
-            prev_l = sqrt(djj);
-            prev_inv = T(1) / prev_l;
+            prev_inv = rsqrt(djj);
+            prev_l = djj * prev_inv;
             __syncthreads();
         }
         {
@@ -484,6 +514,8 @@ __global__ void __launch_bounds__(256) k_front_vec(const DevTables t, const int3
     const int lane = threadIdx.x, warp = threadIdx.y, nw = blockDim.y;
     const int tid = lane + 32 * warp, nth = 32 * nw;
     const int npk = r * (r + 1) / 2 + kSmallPad;
+    __shared__ ChildRef s_ch[kChildRefs];
+    prefetch_children(t, d, s_ch, tid);
     for (int q = tid; q < npk * V; q += nth) F[q] = T(0);
     __syncthreads();
     const int32_t* kl = t.klist + 2 * d.klist_off;
@@ -495,9 +527,9 @@ __global__ void __launch_bounds__(256) k_front_vec(const DevTables t, const int3
     }
     for (int c = 0; c < d.nchild; ++c) {
         __syncthreads();
-        const FrontDesc cd = t.fronts[t.child_ids[d.child_off + c]];
-        extend_add<T, V>(F, r, upd + (int64_t)b0 * upd_total + cd.upd_off, upd_total, nv, t.relmap + cd.relmap_off,
-                         cd.r - cd.w, warp, nw, lane);
+        const ChildRef cr = child_ref(t, d, s_ch, c);
+        extend_add<T, V>(F, r, upd + (int64_t)b0 * upd_total + cr.upd_off, upd_total, nv, t.relmap + cr.map_off, cr.rc,
+                         warp, nw, lane);
     }
     __syncthreads();
     constexpr int kPanel = 16;
@@ -523,7 +555,7 @@ __global__ void __launch_bounds__(256) k_front_vec(const DevTables t, const int3
                     failed[v] = true;
                     djj[v] = T(1);
                 }
-                invd[v] = T(1) / djj[v];
+                invd[v] = rcp_rn(djj[v]);
             }
             if (j > j0) {
                 T* Fp = F + (int64_t)(packed_col(j - 1, r) - (j - 1)) * V;
@@ -553,8 +585,8 @@ __global__ void __launch_bounds__(256) k_front_vec(const DevTables t, const int3
             }
 #pragma unroll
             for (int v = 0; v < V; ++v) {
-                prev_l[v] = sqrt(djj[v]);
-                prev_inv[v] = T(1) / prev_l[v];
+                prev_inv[v] = rsqrt(djj[v]);
+                prev_l[v] = djj[v] * prev_inv[v];
             }
             __syncthreads();
         }
@@ -1878,6 +1910,62 @@ __global__ void __launch_bounds__(256, 2) k_big_update_f32(const DevTables t, co
 
 // --------------------------------------------------------------------------
 // a5: level-scheduled solves, one CTA per (front, instance).
+// A front's vector for the forward sweep, by one warp: v[k] = own
+// right-hand side (k < w) or 0, plus every child's passing vector through
+// its relative map, children in order with a warp barrier between them
+// (two children may reach the same row); each child's rows are loaded four
+// chunks of 32 at a time before they are added.  CG: passing vectors
+// written by other CTAs of the same launch are read past L1.
+template <class T, bool CG>
+__device__ __forceinline__ void gather_fwd(const DevTables& t, const FrontDesc& d, const T* __restrict__ vb,
+                                           const T* __restrict__ pv, T* __restrict__ v, int lane) {
+    const int r = d.r, w = d.w, nc = d.nchild;
+    for (int k = lane; k < r; k += 32) v[k] = k < w ? (CG ? __ldcg(vb + d.f + k) : vb[d.f + k]) : T(0);
+    for (int c = 0; c < nc; ++c) {
+        const FrontDesc& cd = t.fronts[t.child_ids[d.child_off + c]];
+        const int rc = cd.r - cd.w;
+        const int32_t* map = t.relmap + cd.relmap_off;
+        const T* src = pv + cd.pvec_off;
+        __syncwarp();
+        for (int k0 = 0; k0 < rc; k0 += 128) {
+            int m[4];
+            T x[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int k = k0 + lane + 32 * u;
+                m[u] = k < rc ? map[k] : -1;
+                x[u] = k < rc ? (CG ? __ldcg(src + k) : src[k]) : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (m[u] >= 0) v[m[u]] += x[u];
+        }
+    }
+}
+
+// A front's vector for the backward sweep, by one warp: its own columns'
+// values and the (final) values at its other rows, up to 256 rows per batch
+// of loads.  CG: values written by other CTAs of the same launch.
+template <class T, bool CG>
+__device__ __forceinline__ void gather_bwd(const FrontDesc& d, const int32_t* __restrict__ rows,
+                                           const T* __restrict__ vb, T* __restrict__ v, int lane) {
+    const int r = d.r, w = d.w;
+    for (int k0 = 0; k0 < r; k0 += 256) {
+        int idx[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int k = k0 + lane + 32 * u;
+            idx[u] = k < w ? d.f + k : (k < r ? rows[k] : -1);
+        }
+        T x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) x[u] = idx[u] >= 0 ? (CG ? __ldcg(vb + idx[u]) : vb[idx[u]]) : T(0);
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (k0 + lane + 32 * u < r) v[k0 + lane + 32 * u] = x[u];
+    }
+}
+
 // --------------------------------------------------------------------------
 // Stage the lower triangle of the 32x32 diagonal block starting at (jb, jb).
 // and the reciprocals of its diagonal.
@@ -2104,14 +2192,7 @@ __global__ void __launch_bounds__(256) k_fwd_warp(const DevTables t, const int32
     T* vb = vec + (int64_t)b * n;
     const T* Pb = panel + (int64_t)b * panel_total + d.panel_off;
     T* pv = pvec + (int64_t)b * pvec_total;
-    for (int k = lane; k < r; k += 32) v[k] = k < w ? vb[d.f + k] : T(0);
-    for (int c = 0; c < d.nchild; ++c) {
-        __syncwarp();
-        const FrontDesc cd = t.fronts[t.child_ids[d.child_off + c]];
-        const int rc = cd.r - cd.w;
-        const int32_t* map = t.relmap + cd.relmap_off;
-        for (int k = lane; k < rc; k += 32) v[map[k]] += pv[cd.pvec_off + k];
-    }
+    gather_fwd<T, false>(t, d, vb, pv, v, lane);
     __syncwarp();
     for (int jb = 0; jb < w; jb += 32) {
         const int nbk = min(32, w - jb);
@@ -2159,7 +2240,7 @@ __global__ void __launch_bounds__(256) k_bwd_warp(const DevTables t, const int32
     T* vb = vec + (int64_t)b * n;
     const T* Pb = panel + (int64_t)b * panel_total + d.panel_off;
     const int32_t* rows = t.rows + d.rows_off;
-    for (int k = lane; k < r; k += 32) v[k] = k < w ? vb[d.f + k] : vb[rows[k]];
+    gather_bwd<T, false>(d, rows, vb, v, lane);
     __syncwarp();
     const int nblk = (w + 31) / 32;
     for (int bi = nblk - 1; bi >= 0; --bi) {
@@ -2274,14 +2355,7 @@ __global__ void __launch_bounds__(256, 2) k_flow_fwd(const DevTables t, int32_t 
             T* vb = vec + (int64_t)b * n;
             const T* Pb = panel + (int64_t)b * panel_total + d.panel_off;
             T* pv = pvec + (int64_t)b * pvec_total;
-            for (int k = lane; k < r; k += 32) v[k] = k < w ? __ldcg(vb + d.f + k) : T(0);
-            for (int c = 0; c < d.nchild; ++c) {
-                __syncwarp();
-                const FrontDesc cd = t.fronts[t.child_ids[d.child_off + c]];
-                const int rc = cd.r - cd.w;
-                const int32_t* map = t.relmap + cd.relmap_off;
-                for (int k = lane; k < rc; k += 32) v[map[k]] += __ldcg(pv + cd.pvec_off + k);
-            }
+            gather_fwd<T, true>(t, d, vb, pv, v, lane);
             __syncwarp();
             for (int jb = 0; jb < w; jb += 32) {
                 const int nbk = min(32, w - jb);
@@ -2380,7 +2454,7 @@ __global__ void __launch_bounds__(256, 2) k_flow_bwd(const DevTables t, int32_t 
             T* vb = vec + (int64_t)b * n;
             const T* Pb = panel + (int64_t)b * panel_total + d.panel_off;
             const int32_t* rows = t.rows + d.rows_off;
-            for (int k = lane; k < r; k += 32) v[k] = __ldcg(vb + (k < w ? d.f + k : rows[k]));
+            gather_bwd<T, true>(d, rows, vb, v, lane);
             __syncwarp();
             const int nblk = (w + 31) / 32;
             for (int bi = nblk - 1; bi >= 0; --bi) {
