@@ -488,6 +488,11 @@ typedef struct {
     int32_t unit_coef;     /* 1: every coefficient is 1 (no coefficient table) */
     uint64_t table_bytes;  /* device tables (ssco_expr_bind) */
     uint64_t workspace_bytes;
+    /* what the optional steps of ssco_expr_compile_opts did (0 after load) */
+    int64_t n_alg_merged;  /* expressions replaced by a multiple of an equal slot */
+    int64_t n_alg_zero;    /* expressions found equal to zero */
+    int64_t n_factored;    /* factorization steps */
+    int64_t n_inlined;     /* linear intermediates substituted into their users */
 } ssco_expr_info;
 enum { SSCO_EXPR_EXPORT_LEVELS = 0,   /* int64 [n_levels+1] op ranges */
        SSCO_EXPR_EXPORT_TERM_OFF = 1, /* int64 [n_ops+1] */
@@ -509,6 +514,46 @@ enum { SSCO_EXPR_EXPORT_LEVELS = 0,   /* int64 [n_levels+1] op ranges */
  * (message in ssco_expr_last_error(NULL)), UNSUPPORTED beyond int32 slots. */
 ssco_status ssco_expr_compile(const ssco_expr_node* nodes, int32_t n_nodes, const int32_t* outputs, int32_t n_out,
                               int32_t batch, int32_t precision, int32_t inline_terms, ssco_expr* out);
+
+/* ssco_expr_compile with the optional steps of the method (all off = 0,
+ * which gives ssco_expr_compile's tables byte for byte).  Host only.
+ *   algebraic   1: algebraic hashing (Sec. 4.1.2, App. A).  Every slot gets
+ *               the value of its polynomial in the leaf variables at three
+ *               seeded points of the field of integers mod 2^61 - 1
+ *               (coefficients, finite doubles, map there exactly).  An
+ *               expression whose values are all zero is dropped (the entry
+ *               becomes 0, App. D "constant expressions"; with this op set
+ *               no other constant can arise); one whose values are c times
+ *               an existing slot's -- c a double confirmed exactly in the
+ *               field -- becomes c times that slot (so (A+B)C and AC+BC,
+ *               or the mirror entries of a symmetric product, are stored
+ *               once).  Two different polynomials of degree d are merged
+ *               with probability at most (d / (2^61 - 1))^3.
+ *   factor_min  0 or >= 2: factorization (App. D).  While a slot is a factor
+ *               of at least factor_min products of one sum, the slot shared
+ *               by the most is taken out: its partners' sum is stored as a
+ *               linear expression (hashed like any other) and those
+ *               products become one.
+ *   t_ref, t_compl  global decomposition (Sec. 4.2.1; 0 and 0 = off).  A
+ *               linear intermediate (a sum of slot multiples) that is no
+ *               output and is referenced fewer than t_ref times or has
+ *               fewer than t_compl terms is not stored: its terms are
+ *               substituted into the products that use it.  Products stay
+ *               stored (substituting one would give three-factor terms).
+ * Fraction reduction and square-root elimination (App. D) have nothing to
+ * act on: the node set has no division and no roots.  These steps change
+ * the order of the arithmetic (the paper notes the same): results agree
+ * with the plain tables up to rounding, not bit for bit.  reserved must be
+ * 0.  Errors as ssco_expr_compile, INVALID_ARG for options out of range. */
+typedef struct {
+    int32_t batch, precision, inline_terms; /* as in ssco_expr_compile */
+    int32_t algebraic;                      /* 0 / 1 */
+    int32_t factor_min;                     /* 0, or >= 2 */
+    int32_t t_ref, t_compl;                 /* >= 0 */
+    int32_t reserved;                       /* 0 */
+} ssco_expr_opts;
+ssco_status ssco_expr_compile_opts(const ssco_expr_node* nodes, int32_t n_nodes, const int32_t* outputs,
+                                   int32_t n_out, const ssco_expr_opts* opts, ssco_expr* out);
 ssco_status ssco_expr_get_info(ssco_expr e, ssco_expr_info* out);
 ssco_status ssco_expr_export(ssco_expr e, int32_t what, void* host_buf, uint64_t bytes);
 /* Shape and CSR pattern of the k-th output (rowptr [rows+1], colind [nnz]). */

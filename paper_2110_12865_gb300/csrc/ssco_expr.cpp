@@ -12,6 +12,13 @@
 // and the level groups are written out as index tables (leaf harvesting,
 // Sec. 4.4), slots of one level contiguous (outputs written consecutively,
 // Sec. 4.8).  Scaling and transposition only relabel entries.
+//
+// Optional steps (ssco_expr_opts): algebraic hashing (Sec. 4.1.2, App. A)
+// merges expressions equal as polynomials and drops those equal to zero;
+// factorization (App. D) takes a slot shared by several products of a sum
+// out of them; the global decomposition (Sec. 4.2.1) keeps a linear
+// intermediate stored only if it is referenced at least t_ref times and has
+// at least t_compl terms, and expands the others into their users.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -46,6 +53,79 @@ uint64_t mix(uint64_t h, uint64_t x) {
     return h ^ (h >> 31);
 }
 
+// ---- algebraic keys (Sec. 4.1.2, App. A) ----------------------------------
+// A slot's key is the value of its polynomial in the leaf variables at
+// kAlgPoints seeded points of the prime field Z_p, p = 2^61 - 1: a leaf
+// variable takes a pseudo-random nonzero element per point, the constant one
+// takes 1, sums add and products multiply (the paper's rule for + and *).
+// A coefficient is a finite double, exactly m 2^e with an integer m; it maps
+// to m 2^e mod p, which is exact because 2 is invertible mod p (2^61 = 1), so
+// the keys of the stored tables' own coefficients are exact as well.
+// Polynomials that are equal get equal keys whatever their structure; two
+// different ones of degree d agree at one random point with probability at
+// most d / p (Schwartz-Zippel), at all points with its kAlgPoints-th power.
+constexpr uint64_t kP = (1ull << 61) - 1;
+constexpr int kAlgPoints = 3;
+
+uint64_t fadd(uint64_t a, uint64_t b) {
+    const uint64_t s = a + b;
+    return s >= kP ? s - kP : s;
+}
+uint64_t fneg(uint64_t a) { return a ? kP - a : 0; }
+uint64_t fmul(uint64_t a, uint64_t b) {  // a, b < p: a b < p^2, and 2^61 = 1 mod p
+    const unsigned __int128 z = (unsigned __int128)a * b;
+    const uint64_t s = ((uint64_t)z & kP) + (uint64_t)(z >> 61);
+    return s >= kP ? s - kP : s;
+}
+uint64_t finv(uint64_t a) {  // a^(p-2) = 1/a (Fermat), a != 0
+    uint64_t r = 1;
+    for (uint64_t e = kP - 2; e; e >>= 1) {
+        if (e & 1) r = fmul(r, a);
+        a = fmul(a, a);
+    }
+    return r;
+}
+uint64_t fdyadic(double c) {  // the field image of a finite double
+    if (c == 0.0) return 0;
+    int e = 0;
+    const double f = std::frexp(std::fabs(c), &e);       // |c| = f 2^e, f in [0.5, 1)
+    const uint64_t m = (uint64_t)std::ldexp(f, 53);      // exact: < 2^53 < p
+    const int k = (((e - 53) % 61) + 61) % 61;           // 2^(e - 53) = 2^k mod p
+    const uint64_t r = fmul(m, 1ull << k);
+    return c < 0 ? fneg(r) : r;
+}
+uint64_t splitmix(uint64_t x) {
+    x += 0x9e3779b97f4a7c15ull;
+    x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
+    x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
+    return x ^ (x >> 31);
+}
+uint64_t leaf_key(int64_t s, int j) { return 1 + splitmix(0x5a17c0de00000000ull ^ ((uint64_t)s << 2 | (uint64_t)j)) % (kP - 1); }
+// a real point as well (values in [0.5, 1.5)), to name the factor between
+// two expressions whose keys are proportional
+double leaf_real(int64_t s) { return 0.5 + (double)(splitmix(0x7ea1000000000000ull ^ (uint64_t)s) >> 11) * 0x1p-53; }
+
+// The double c with field image r near the real ratio q, if there is one:
+// q itself, its neighbours, or q rounded to fewer significant bits (the
+// multiples that occur -- 2, -1, 0.5, products of the SCALE factors -- are
+// short binary fractions or the doubles the factors multiply to).
+bool recover_factor(double q, uint64_t r, double* c) {
+    if (!std::isfinite(q) || q == 0.0) return false;
+    double x = q;
+    for (int k = 0; k < 3; ++k, x = std::nextafter(x, HUGE_VAL))
+        if (fdyadic(x) == r) return *c = x, true;
+    x = std::nextafter(q, -HUGE_VAL);
+    for (int k = 0; k < 2; ++k, x = std::nextafter(x, -HUGE_VAL))
+        if (fdyadic(x) == r) return *c = x, true;
+    int e = 0;
+    const double f = std::frexp(q, &e);
+    for (int b = 48; b >= 1; b -= (b > 16 ? 4 : 1)) {
+        x = std::ldexp(std::nearbyint(std::ldexp(f, b)), e - b);
+        if (x != 0.0 && fdyadic(x) == r) return *c = x, true;
+    }
+    return false;
+}
+
 // Scalar expressions under construction, merged by structural hashing.
 struct Builder {
     int64_t base = 0;  // slot id of the first stored expression
@@ -60,7 +140,60 @@ struct Builder {
     bool overflow = false;
     std::vector<Term> t;  // the expression being built
 
+    // optional steps
+    bool algebraic = false;   // algebraic hashing
+    int32_t factor_min = 0;   // factorization: a slot shared by >= this many products (0 = off)
+    int64_t n_alg_merged = 0, n_alg_zero = 0, n_factored = 0;
+    // per stored expression: its keys, the inverse of its first key and its
+    // value at the real point (algebraic hashing only)
+    std::vector<uint64_t> akey, ainv;
+    std::vector<double> areal;
+    // slots by normalized key (keys 1.. divided by key 0): every slot whose
+    // key 0 is nonzero, the constant and the leaves included
+    struct AlgEntry {
+        uint64_t n1, n2;
+        int64_t slot1;  // slot + 1; 0 = empty
+    };
+    std::vector<AlgEntry> atab;
+    int64_t a_count = 0;
+
     int32_t level_of(int32_t s) const { return s >= base ? level[s - base] : 0; }
+
+    uint64_t key_of(int64_t s, int j) const {
+        return s == 0 ? 1 : s < base ? leaf_key(s, j) : akey[(size_t)(s - base) * kAlgPoints + j];
+    }
+    uint64_t inv_of(int64_t s) const {
+        return s == 0 ? 1 : s < base ? finv(leaf_key(s, 0)) : ainv[(size_t)(s - base)];
+    }
+    double real_of(int64_t s) const { return s == 0 ? 1.0 : s < base ? leaf_real(s) : areal[(size_t)(s - base)]; }
+
+    size_t alg_probe(uint64_t n1, uint64_t n2) const {
+        const size_t cap = atab.size();
+        size_t p = (size_t)mix(n1, n2) & (cap - 1);
+        while (atab[p].slot1 && !(atab[p].n1 == n1 && atab[p].n2 == n2)) p = (p + 1) & (cap - 1);
+        return p;
+    }
+    void alg_insert(int64_t slot, uint64_t n1, uint64_t n2) {
+        if (2 * (a_count + 1) > (int64_t)atab.size()) {
+            std::vector<AlgEntry> old;
+            old.swap(atab);
+            atab.assign(std::max<size_t>(1 << 16, old.size() * 2), AlgEntry{0, 0, 0});
+            for (const AlgEntry& e : old)
+                if (e.slot1) atab[alg_probe(e.n1, e.n2)] = e;
+        }
+        const size_t p = alg_probe(n1, n2);
+        if (atab[p].slot1) return;  // keep the first slot of this key
+        atab[p] = AlgEntry{n1, n2, slot + 1};
+        ++a_count;
+    }
+    // the constant one and every leaf, before the first expression
+    void alg_start() {
+        if (!algebraic) return;
+        for (int64_t s = 0; s < base; ++s) {
+            const uint64_t i0 = inv_of(s);
+            alg_insert(s, fmul(key_of(s, 1), i0), fmul(key_of(s, 2), i0));
+        }
+    }
 
     void rehash(size_t cap) {
         table.assign(cap, 0);
@@ -124,10 +257,46 @@ struct Builder {
             }
             p = (p + 1) & (cap - 1);
         }
+        // algebraic hashing: an expression equal to zero needs no slot; one
+        // equal to c times an existing slot reuses it
+        uint64_t k[kAlgPoints] = {0, 0, 0}, n1 = 0, n2 = 0, i0 = 0;
+        double real = 0.0;
+        if (algebraic) {
+            for (size_t q = 0; q < n; ++q) {
+                const uint64_t c = fdyadic(tt[q].c);
+                for (int j = 0; j < kAlgPoints; ++j)
+                    k[j] = fadd(k[j], fmul(c, fmul(key_of(tt[q].f1, j), key_of(tt[q].f2, j))));
+                real += tt[q].c * real_of(tt[q].f1) * real_of(tt[q].f2);
+            }
+            if (k[0] == 0 && k[1] == 0 && k[2] == 0) {
+                ++n_alg_zero;
+                return {0.0, 0};
+            }
+            if (k[0] != 0) {
+                i0 = finv(k[0]);
+                n1 = fmul(k[1], i0);
+                n2 = fmul(k[2], i0);
+                const AlgEntry& e = atab[alg_probe(n1, n2)];
+                double c = 0.0;
+                if (e.slot1) {
+                    const int64_t s = e.slot1 - 1;
+                    if (recover_factor(real / real_of(s), fmul(k[0], inv_of(s)), &c)) {
+                        ++n_alg_merged;
+                        return {c, (int32_t)s};
+                    }
+                }
+            }
+        }
         const int64_t idx = (int64_t)level.size();
         if (base + idx >= (int64_t)INT32_MAX - 1) {
             overflow = true;
             return {0.0, 0};
+        }
+        if (algebraic) {
+            akey.insert(akey.end(), k, k + kAlgPoints);
+            ainv.push_back(i0);
+            areal.push_back(real);
+            if (k[0] != 0) alg_insert(base + idx, n1, n2);
         }
         int32_t lv = 0;
         for (size_t k = 0; k < n; ++k) lv = std::max(lv, std::max(level_of(tt[k].f1), level_of(tt[k].f2)));
@@ -141,14 +310,59 @@ struct Builder {
         return {1.0, (int32_t)(base + idx)};
     }
 
-    // The sum of the terms in `t`, as a handle: a constant multiple of one
-    // slot needs no expression; anything else is stored once.
-    Handle materialize() {
+    // Factorization (App. D) of the canonical sum v, in place: while some
+    // slot is a factor of at least factor_min of its products, the slot
+    // shared by the most (the smallest on ties) is taken out -- its
+    // partners' sum becomes a linear expression of its own (merged by
+    // hashing like any other) and those products become one.  A linear sum
+    // has distinct slots, so the partners' sum is never factored again.
+    bool factor(std::vector<Term>& v) {
+        bool any = false;
+        std::vector<int32_t> fs;
+        std::vector<Term> inner, rest;
+        for (;;) {
+            fs.clear();
+            for (const Term& x : v) {
+                if (x.f1 > 0) fs.push_back(x.f1);
+                if (x.f2 > 0 && x.f2 != x.f1) fs.push_back(x.f2);
+            }
+            std::sort(fs.begin(), fs.end());
+            int32_t best = -1;
+            size_t most = 0;
+            for (size_t i = 0; i < fs.size();) {
+                size_t j = i;
+                while (j < fs.size() && fs[j] == fs[i]) ++j;
+                if (j - i > most) most = j - i, best = fs[i];
+                i = j;
+            }
+            if (most < 2 || (int64_t)most < factor_min) return any;
+            inner.clear();
+            rest.clear();
+            for (const Term& x : v) {
+                if (x.f1 == best || x.f2 == best)
+                    inner.push_back(Term{x.f1 == best ? x.f2 : x.f1, 0, x.c});
+                else
+                    rest.push_back(x);
+            }
+            const Handle h = materialize_vec(inner);
+            if (h.c != 0.0) rest.push_back(Term{best, h.s, h.c});
+            v.swap(rest);
+            ++n_factored;
+            any = true;
+        }
+    }
+
+    // The sum of the terms in v (reordered in place), as a handle: a
+    // constant multiple of one slot needs no expression; anything else is
+    // stored once.
+    Handle materialize_vec(std::vector<Term>& v) {
         ++n_unrolled;
         uint64_t h = 0;
-        const Handle d = canon(t, &h);
-        return d.s >= 0 ? d : lookup_insert(t.data(), t.size(), h);
+        Handle d = canon(v, &h);
+        if (d.s < 0 && factor_min > 0 && factor(v)) d = canon(v, &h);
+        return d.s >= 0 ? d : lookup_insert(v.data(), v.size(), h);
     }
+    Handle materialize() { return materialize_vec(t); }
 
     // materialize() for a batch of sums (the entries of one row of a
     // product): all canonical forms first, their table slots prefetched,
@@ -159,6 +373,13 @@ struct Builder {
     std::vector<Handle> direct;
     void materialize_batch(const std::vector<Term>& terms, const std::vector<int64_t>& off, size_t count,
                            std::vector<Handle>& out) {
+        if (factor_min > 0) {  // factored one at a time
+            for (size_t x = 0; x < count; ++x) {
+                t.assign(terms.begin() + off[x], terms.begin() + off[x + 1]);
+                out.push_back(materialize());
+            }
+            return;
+        }
         bt.clear();
         boff.assign(1, 0);
         bh.resize(count);
@@ -257,12 +478,109 @@ ssco_status validate(const ssco_expr_node* nodes, int32_t n_nodes, const int32_t
     return SSCO_OK;
 }
 
+// Global decomposition (Sec. 4.2.1) of the expressions in bd into nb.
+// Reference counts are taken over the stored expressions' products and the
+// outputs.  A linear expression (every product has the constant one as a
+// factor) that is no output and is referenced fewer than t_ref times or has
+// fewer than t_compl terms (its complexity: one multiply-add per term) is
+// not stored: its terms are substituted into every product that uses it.  A
+// product is never substituted (its users' terms would get three factors).
+// The expressions that stay are rebuilt in level order, so that hashing
+// merges what the substitution made equal.
+void decompose(Builder& bd, std::vector<std::vector<Handle>>& outh, int32_t t_ref, int32_t t_compl, Builder& nb,
+               int64_t* n_inlined) {
+    const int64_t n = (int64_t)bd.level.size(), base = bd.base;
+    std::vector<int32_t> refs(n, 0);
+    std::vector<uint8_t> keep(n, 0);
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t q = bd.tbeg[i]; q < bd.tbeg[i] + bd.nt[i]; ++q) {
+            if (bd.pool[q].f1 >= base) ++refs[bd.pool[q].f1 - base];
+            if (bd.pool[q].f2 >= base) ++refs[bd.pool[q].f2 - base];
+        }
+    for (const auto& o : outh)
+        for (const Handle& h : o)
+            if (h.s >= base) keep[h.s - base] = 1;
+    for (int64_t i = 0; i < n; ++i) {
+        bool linear = true;
+        for (int64_t q = bd.tbeg[i]; q < bd.tbeg[i] + bd.nt[i] && linear; ++q) linear = bd.pool[q].f2 == 0;
+        if (!linear || (refs[i] >= t_ref && bd.nt[i] >= t_compl)) keep[i] = 1;
+    }
+    std::vector<int32_t>().swap(refs);
+    // level order (operands first)
+    int32_t max_lv = 0;
+    for (int64_t i = 0; i < n; ++i) max_lv = std::max(max_lv, bd.level[i]);
+    std::vector<int64_t> cnt((size_t)max_lv + 2, 0);
+    std::vector<int64_t> order(n);
+    for (int64_t i = 0; i < n; ++i) cnt[bd.level[i] + 1]++;
+    for (size_t k = 1; k < cnt.size(); ++k) cnt[k] += cnt[k - 1];
+    for (int64_t i = 0; i < n; ++i) order[cnt[bd.level[i]]++] = i;
+    // each old expression as a list of new handles (one, or an inlined sum)
+    std::vector<int64_t> mbeg(n, 0), mlen(n, 0);
+    std::vector<Handle> mpool;
+    std::vector<Handle> lin;
+    auto sub = [&](int32_t s, const Handle** b, int64_t* len, Handle* own) {
+        if (s < base) {
+            *own = Handle{1.0, s};
+            *b = own;
+            *len = 1;
+        } else {
+            *b = mpool.data() + mbeg[s - base];
+            *len = mlen[s - base];
+        }
+    };
+    for (int64_t i : order) {
+        nb.t.clear();
+        for (int64_t q = bd.tbeg[i]; q < bd.tbeg[i] + bd.nt[i]; ++q) {
+            const Term x = bd.pool[q];
+            const Handle *A, *B;
+            int64_t na, nbb;
+            Handle oa, ob;
+            sub(x.f1, &A, &na, &oa);
+            sub(x.f2, &B, &nbb, &ob);
+            for (int64_t u = 0; u < na; ++u)
+                for (int64_t v = 0; v < nbb; ++v) nb.t.push_back(Term{A[u].s, B[v].s, x.c * A[u].c * B[v].c});
+        }
+        mbeg[i] = (int64_t)mpool.size();
+        if (keep[i]) {
+            mpool.push_back(nb.materialize());
+        } else {  // linear: every product is (slot, the constant one)
+            lin.clear();
+            for (const Term& x : nb.t) lin.push_back(Handle{x.c, x.f1 ? x.f1 : x.f2});
+            std::sort(lin.begin(), lin.end(), [](const Handle& a, const Handle& b) { return a.s < b.s; });
+            size_t w = 0;
+            for (size_t r = 0; r < lin.size(); ++r) {
+                if (w > 0 && lin[w - 1].s == lin[r].s)
+                    lin[w - 1].c += lin[r].c;
+                else
+                    lin[w++] = lin[r];
+            }
+            lin.resize(w);
+            lin.erase(std::remove_if(lin.begin(), lin.end(), [](const Handle& h) { return h.c == 0.0; }), lin.end());
+            mpool.insert(mpool.end(), lin.begin(), lin.end());
+            ++*n_inlined;
+        }
+        mlen[i] = (int64_t)mpool.size() - mbeg[i];
+    }
+    for (auto& o : outh)
+        for (Handle& h : o)
+            if (h.s >= base) {  // kept: one handle (none if it vanished)
+                const int64_t i = h.s - base;
+                h = mlen[i] ? Handle{h.c * mpool[mbeg[i]].c, mpool[mbeg[i]].s} : Handle{0.0, 0};
+            }
+    nb.n_unrolled = bd.n_unrolled;
+}
+
 ssco_status compile(const ssco_expr_node* nodes, int32_t n_nodes, const int32_t* outputs, int32_t n_out,
-                    int32_t batch, int32_t precision, int32_t inline_terms, ExprProgram& E) {
+                    const ssco_expr_opts& opt, ExprProgram& E) {
+    const int32_t batch = opt.batch, precision = opt.precision, inline_terms = opt.inline_terms;
     std::vector<int32_t> rows, cols;
     ssco_status st = validate(nodes, n_nodes, outputs, n_out, batch, precision, rows, cols);
     if (st != SSCO_OK) return st;
     if (inline_terms < 0 || inline_terms > 16) return bad(SSCO_ERR_INVALID_ARG, "inline_terms must be in [0, 16]");
+    if (opt.algebraic < 0 || opt.algebraic > 1) return bad(SSCO_ERR_INVALID_ARG, "algebraic must be 0 or 1");
+    if (opt.factor_min < 0 || opt.factor_min == 1) return bad(SSCO_ERR_INVALID_ARG, "factor_min must be 0 or >= 2");
+    if (opt.t_ref < 0 || opt.t_compl < 0) return bad(SSCO_ERR_INVALID_ARG, "t_ref and t_compl must be >= 0");
+    if (opt.reserved != 0) return bad(SSCO_ERR_INVALID_ARG, "reserved option must be 0");
     E.B = batch;
     E.precision = precision;
     // last use of every node, so that its entries can be released
@@ -279,6 +597,9 @@ ssco_status compile(const ssco_expr_node* nodes, int32_t n_nodes, const int32_t*
     E.n_leaf_vals = leaf_vals;
     Builder bd;
     bd.base = 1 + leaf_vals;
+    bd.algebraic = opt.algebraic != 0;
+    bd.factor_min = opt.factor_min;
+    bd.alg_start();
     std::vector<ExprCsr> pat(n_nodes);
     // Every entry of a node is a short linear combination of slots: one
     // handle, or, with inlining, up to `inline_terms` handles kept local
@@ -451,6 +772,24 @@ ssco_status compile(const ssco_expr_node* nodes, int32_t n_nodes, const int32_t*
             outh[k].push_back(H.n(e) == 1 ? *H.at(e) : store_lin(H.at(e), H.n(e)));
     }
     if (bd.overflow) return bad(SSCO_ERR_UNSUPPORTED, "stored intermediates exceed int32 slots");
+    int64_t n_inlined = 0;
+    if (opt.t_ref > 0 || opt.t_compl > 0) {
+        Builder nb;
+        nb.base = bd.base;
+        nb.algebraic = bd.algebraic;
+        nb.factor_min = bd.factor_min;
+        nb.alg_start();
+        decompose(bd, outh, opt.t_ref, opt.t_compl, nb, &n_inlined);
+        nb.n_alg_merged += bd.n_alg_merged;
+        nb.n_alg_zero += bd.n_alg_zero;
+        nb.n_factored += bd.n_factored;
+        bd = std::move(nb);
+        if (bd.overflow) return bad(SSCO_ERR_UNSUPPORTED, "stored intermediates exceed int32 slots");
+    }
+    E.n_alg_merged = bd.n_alg_merged;
+    E.n_alg_zero = bd.n_alg_zero;
+    E.n_factored = bd.n_factored;
+    E.n_inlined = n_inlined;
     // level order: by level, then term count, then creation (two stable
     // counting passes: term count, then level)
     const int64_t n_ops = (int64_t)bd.level.size();
@@ -592,6 +931,47 @@ size_t expr_workspace_bytes(const ExprProgram& E) {
 }
 
 void expr_layout_tables(ExprProgram& E) {
+    // groups: runs of equal term count inside a level (the compiler orders
+    // a level's expressions by term count, so a level has one run per count)
+    E.groups.clear();
+    E.chunks.clear();
+    E.lvl_chunk.assign(1, 0);
+    E.chunk_members = std::max(1, 256 / std::min(E.B, 256));
+    int64_t n1 = 0, n2 = 0, nc = 0;
+    for (int32_t l = 0; l < E.n_levels(); ++l) {
+        for (int64_t op = E.lvl_begin[l]; op < E.lvl_begin[l + 1];) {
+            const int64_t nt = E.term_off[op + 1] - E.term_off[op];
+            int64_t r = op + 1;
+            while (r < E.lvl_begin[l + 1] && E.term_off[r + 1] - E.term_off[r] == nt) ++r;
+            ExprProgram::Group g{};
+            g.nterms = (int32_t)nt;
+            g.nmem = (int32_t)(r - op);
+            g.op0 = op;
+            g.quad = 0;
+            g.uniform = 1;
+            g.c_uniform = nt > 0 ? E.coef[E.term_off[op]] : 1.0;
+            for (int64_t q = E.term_off[op]; q < E.term_off[r]; ++q) {
+                if (E.f2[q] != 0) g.quad = 1;
+                if (E.coef[q] != g.c_uniform) g.uniform = 0;
+            }
+            const int64_t cells = nt * g.nmem;
+            g.i1_off = n1;
+            n1 += cells;
+            g.i2_off = g.quad ? n2 : 0;
+            if (g.quad) n2 += cells;
+            g.coef_off = g.uniform ? 0 : nc;
+            if (!g.uniform) nc += cells;
+            const int32_t gi = (int32_t)E.groups.size();
+            E.groups.push_back(g);
+            for (int32_t m = 0; m < g.nmem; m += E.chunk_members) E.chunks.push_back(ExprProgram::Chunk{gi, m});
+            op = r;
+        }
+        E.lvl_chunk.push_back((int64_t)E.chunks.size());
+    }
+    E.n_i1 = n1, E.n_i2 = n2, E.n_coef = nc;
+    E.out_unit = 1;
+    for (double c : E.out_coef)
+        if (c != 1.0) E.out_unit = 0;
     const size_t vb = expr_value_bytes(E);
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -599,34 +979,47 @@ void expr_layout_tables(ExprProgram& E) {
         off += align256(std::max<size_t>(bytes, 16));
         return o;
     };
-    E.toff.term_off = take(E.term_off.size() * 8);
-    E.toff.f1 = take(E.f1.size() * 4);
-    E.toff.f2 = take(E.f2.size() * 4);
-    E.toff.coef = take(E.unit_coef ? 0 : E.coef.size() * vb);
+    E.toff.groups = take(E.groups.size() * sizeof(ExprProgram::Group));
+    E.toff.chunks = take(E.chunks.size() * sizeof(ExprProgram::Chunk));
+    E.toff.i1 = take((size_t)n1 * 4);
+    E.toff.i2 = take((size_t)n2 * 4);
+    E.toff.coef = take((size_t)nc * vb);
     E.toff.out_slot = take(E.out_slot.size() * 4);
-    E.toff.out_coef = take(E.out_coef.size() * vb);
+    E.toff.out_coef = take(E.out_unit ? 0 : E.out_coef.size() * vb);
     E.toff.total = off;
 }
 
 std::vector<uint8_t> expr_table_image(const ExprProgram& E) {
     std::vector<uint8_t> img(E.toff.total, 0);
     const bool f32 = E.precision == SSCO_VALS_F32;
-    std::memcpy(img.data() + E.toff.term_off, E.term_off.data(), E.term_off.size() * 8);
-    if (!E.f1.empty()) std::memcpy(img.data() + E.toff.f1, E.f1.data(), E.f1.size() * 4);
-    if (!E.f2.empty()) std::memcpy(img.data() + E.toff.f2, E.f2.data(), E.f2.size() * 4);
-    if (!E.out_slot.empty()) std::memcpy(img.data() + E.toff.out_slot, E.out_slot.data(), E.out_slot.size() * 4);
-    auto put_vals = [&](size_t at, const std::vector<double>& v) {
-        for (size_t i = 0; i < v.size(); ++i) {
-            if (f32) {
-                const float x = (float)v[i];
-                std::memcpy(img.data() + at + 4 * i, &x, 4);
-            } else {
-                std::memcpy(img.data() + at + 8 * i, &v[i], 8);
-            }
+    auto put_val = [&](size_t at, double v) {
+        if (f32) {
+            const float x = (float)v;
+            std::memcpy(img.data() + at, &x, 4);
+        } else {
+            std::memcpy(img.data() + at, &v, 8);
         }
     };
-    if (!E.unit_coef) put_vals(E.toff.coef, E.coef);
-    put_vals(E.toff.out_coef, E.out_coef);
+    const size_t vb = expr_value_bytes(E);
+    if (!E.groups.empty())
+        std::memcpy(img.data() + E.toff.groups, E.groups.data(), E.groups.size() * sizeof(ExprProgram::Group));
+    if (!E.chunks.empty())
+        std::memcpy(img.data() + E.toff.chunks, E.chunks.data(), E.chunks.size() * sizeof(ExprProgram::Chunk));
+    int32_t* i1 = reinterpret_cast<int32_t*>(img.data() + E.toff.i1);
+    int32_t* i2 = reinterpret_cast<int32_t*>(img.data() + E.toff.i2);
+    for (const ExprProgram::Group& g : E.groups)
+        for (int32_t m = 0; m < g.nmem; ++m) {
+            const int64_t q0 = E.term_off[g.op0 + m];
+            for (int32_t t = 0; t < g.nterms; ++t) {
+                const int64_t cell = (int64_t)t * g.nmem + m;
+                i1[g.i1_off + cell] = E.f1[q0 + t];
+                if (g.quad) i2[g.i2_off + cell] = E.f2[q0 + t];
+                if (!g.uniform) put_val(E.toff.coef + (size_t)(g.coef_off + cell) * vb, E.coef[q0 + t]);
+            }
+        }
+    if (!E.out_slot.empty()) std::memcpy(img.data() + E.toff.out_slot, E.out_slot.data(), E.out_slot.size() * 4);
+    if (!E.out_unit)
+        for (size_t j = 0; j < E.out_coef.size(); ++j) put_val(E.toff.out_coef + j * vb, E.out_coef[j]);
     return img;
 }
 
@@ -638,13 +1031,23 @@ extern "C" {
 
 ssco_status ssco_expr_compile(const ssco_expr_node* nodes, int32_t n_nodes, const int32_t* outputs, int32_t n_out,
                               int32_t batch, int32_t precision, int32_t inline_terms, ssco_expr* out) {
-    if (!out) return ssco::bad(SSCO_ERR_INVALID_ARG, "NULL output handle");
+    ssco_expr_opts o;
+    std::memset(&o, 0, sizeof(o));
+    o.batch = batch;
+    o.precision = precision;
+    o.inline_terms = inline_terms;
+    return ssco_expr_compile_opts(nodes, n_nodes, outputs, n_out, &o, out);
+}
+
+ssco_status ssco_expr_compile_opts(const ssco_expr_node* nodes, int32_t n_nodes, const int32_t* outputs,
+                                   int32_t n_out, const ssco_expr_opts* opts, ssco_expr* out) {
+    if (!out || !opts) return ssco::bad(SSCO_ERR_INVALID_ARG, "NULL output handle or options");
     *out = nullptr;
     ssco_expr e = new (std::nothrow) ssco_expr_s();
     if (!e) return ssco::bad(SSCO_ERR_OOM, "host allocation failed");
     ssco_status st;
     try {
-        st = ssco::compile(nodes, n_nodes, outputs, n_out, batch, precision, inline_terms, e->E);
+        st = ssco::compile(nodes, n_nodes, outputs, n_out, *opts, e->E);
     } catch (const std::bad_alloc&) {
         st = ssco::bad(SSCO_ERR_OOM, "host allocation failed while compiling");
     } catch (const std::exception& ex) {
@@ -668,6 +1071,10 @@ ssco_status ssco_expr_get_info(ssco_expr e, ssco_expr_info* o) {
     o->n_ops = E.n_ops;
     o->n_terms = E.n_terms;
     o->n_unrolled = E.n_unrolled;
+    o->n_alg_merged = E.n_alg_merged;
+    o->n_alg_zero = E.n_alg_zero;
+    o->n_factored = E.n_factored;
+    o->n_inlined = E.n_inlined;
     o->n_levels = E.n_levels();
     o->batch = E.B;
     o->precision = E.precision;
@@ -810,7 +1217,7 @@ ssco_status ssco_expr_load(const char* path, ssco_expr* out) {
     // taken of an empty table)
     ok = ok && E.B >= 1 && E.B <= 65535 && (E.precision == SSCO_VALS_F64 || E.precision == SSCO_VALS_F32) &&
          E.n_leaf_vals >= 0 && E.n_out_vals >= 0 && E.n_ops >= 0 && E.n_terms >= 0 &&
-         E.n_slots == 1 + E.n_leaf_vals + E.n_ops && !E.lvl_begin.empty() && E.lvl_begin.front() == 0 &&
+         E.n_slots == 1 + E.n_leaf_vals + E.n_ops && E.n_slots < (int64_t)INT32_MAX && !E.lvl_begin.empty() && E.lvl_begin.front() == 0 &&
          E.lvl_begin.back() == E.n_ops && (int64_t)E.term_off.size() == E.n_ops + 1 && E.term_off.front() == 0 &&
          E.term_off.back() == E.n_terms && (int64_t)E.f1.size() == E.n_terms && (int64_t)E.f2.size() == E.n_terms &&
          (int64_t)E.coef.size() == E.n_terms && (int64_t)E.out_slot.size() == E.n_out_vals &&

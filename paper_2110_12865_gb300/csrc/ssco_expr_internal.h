@@ -22,6 +22,8 @@ struct ExprProgram {
     int32_t B = 1;
     int32_t precision = SSCO_VALS_F64;
     int64_t n_leaf_vals = 0, n_out_vals = 0, n_slots = 0, n_ops = 0, n_terms = 0, n_unrolled = 0;
+    // what the optional compile steps did (not saved in program files)
+    int64_t n_alg_merged = 0, n_alg_zero = 0, n_factored = 0, n_inlined = 0;
     int32_t unit_coef = 1;
     std::vector<int64_t> lvl_begin;  // [n_levels + 1] op ranges (op i is slot op_base + i)
     std::vector<int64_t> term_off;   // [n_ops + 1]
@@ -33,9 +35,30 @@ struct ExprProgram {
     int64_t op_base() const { return 1 + n_leaf_vals; }
     int32_t n_levels() const { return (int32_t)lvl_begin.size() - 1; }
 
-    // device image
+    // device form (built from the tables above by expr_layout_tables): the
+    // expressions of a level in groups of equal term count -- the assembly
+    // groups' form -- with term-major, member-innermost factor tables (the
+    // second factor only for groups with a product of two slots, the
+    // coefficients only for groups whose coefficients differ), and chunks
+    // of members per CTA
+    struct Group {
+        int32_t nterms, nmem;
+        int32_t quad, uniform;  // quad: some term has two slot factors
+        int64_t op0;            // first expression (slot op_base + op0)
+        int64_t i1_off, i2_off, coef_off;
+        double c_uniform;
+    };
+    struct Chunk {
+        int32_t group, start;
+    };
+    std::vector<Group> groups;
+    std::vector<Chunk> chunks;
+    std::vector<int64_t> lvl_chunk;  // [n_levels + 1] chunk ranges
+    int32_t chunk_members = 256;     // members per chunk (256 / batch, at least 1)
+    int32_t out_unit = 1;            // every output factor is 1 (no factor table)
+    int64_t n_i1 = 0, n_i2 = 0, n_coef = 0;
     struct {
-        size_t term_off, f1, f2, coef, out_slot, out_coef, total;
+        size_t groups, chunks, i1, i2, coef, out_slot, out_coef, total;
     } toff{};
     uint8_t* d_tab = nullptr;
     uint8_t* d_ws = nullptr;

@@ -3,15 +3,17 @@
 // Slots live instance-innermost ([slot][batch]): the threads of a warp take
 // consecutive value sets of one scalar expression, so every factor gather is
 // one contiguous run and every lane runs the same number of terms.  With one
-// value set a warp takes 32 consecutive expressions of a level, which were
-// ordered by term count at compile time.  One launch per level (a level
-// never reads its own results), plus the transposing copies in and out.
+// value set a warp takes 32 consecutive expressions of one term-count group
+// and reads each term's factor indices as one coalesced run (the groups'
+// term-major tables).  One launch per level (a level never reads its own
+// results), plus the transposing copies in and out.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cstdint>
 
 #include "ssco_expr_internal.h"
+#include "ssco_gmac.cuh"
 
 namespace ssco {
 namespace {
@@ -44,31 +46,37 @@ __global__ void k_expr_one(T* __restrict__ slots) {
     slots[0] = T(1);
 }
 
-// one level: slot (slot0 + op) = sum over terms of coef * f1 * f2
-template <class T, bool kUnit>
+// One level: a CTA per chunk of one term-count group; the group's members
+// are consecutive expressions (slots slot0 + op0 + i) and thread f takes
+// member f / B of the chunk for value set f % B (with one value set, one
+// member per thread).  The sum itself is the assembly's gather-MAC core, with
+// a second gathered factor per term in groups that have products of two
+// slots and the plain linear form (the assembly's own) in the others.
+template <class T, bool kOne>
 __global__ void __launch_bounds__(256)
-    k_expr_level(const int64_t* __restrict__ toff, const int32_t* __restrict__ f1, const int32_t* __restrict__ f2,
-                 const T* __restrict__ coef, int64_t op0, int64_t nops, int32_t B, int64_t slot0,
+    k_expr_group(const ExprProgram::Group* __restrict__ groups, const ExprProgram::Chunk* __restrict__ chunks,
+                 int64_t chunk0, const int32_t* __restrict__ i1, const int32_t* __restrict__ i2,
+                 const T* __restrict__ coef, int32_t B, int32_t chunk_members, int64_t slot0,
                  T* __restrict__ slots) {
-    const int64_t total = nops * B;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t op = op0 + t / B;
-        const int b = (int)(t % B);
-        T acc = T(0);
-        const int64_t q1 = toff[op + 1];
-        for (int64_t q = toff[op]; q < q1; ++q) {
-            const T p = slots[(int64_t)f1[q] * B + b] * slots[(int64_t)f2[q] * B + b];
-            if (kUnit)
-                acc += p;
-            else
-                acc += coef[q] * p;
-        }
-        slots[(slot0 + op) * B + b] = acc;
+    const ExprProgram::Chunk ch = chunks[chunk0 + blockIdx.x];
+    const ExprProgram::Group g = groups[ch.group];
+    const int32_t mend = min(g.nmem, ch.start + chunk_members);
+    const int64_t work = (int64_t)(mend - ch.start) * (kOne ? 1 : B);
+    for (int64_t f = threadIdx.x; f < work; f += blockDim.x) {
+        const int32_t i = ch.start + (int32_t)(kOne ? f : f / B);
+        const int32_t b = kOne ? 0 : (int32_t)(f % B);
+        const T* __restrict__ x = slots + b;
+        auto load = [x, B](int32_t s) { return x[(int64_t)s * (kOne ? 1 : B)]; };
+        const T* cf = g.uniform ? nullptr : coef + g.coef_off + i;
+        const T cu = (T)g.c_uniform;
+        const T acc = g.quad ? gmac<T, true>(T(0), g.nterms, g.nmem, i1 + g.i1_off + i, i2 + g.i2_off + i, cf, cu, load)
+                             : gmac<T, false>(T(0), g.nterms, g.nmem, i1 + g.i1_off + i, nullptr, cf, cu, load);
+        slots[(slot0 + g.op0 + i) * (kOne ? 1 : B) + b] = acc;
     }
 }
 
 // slots [slot][b] -> out [B][N]: out[b][j] = ocoef[j] * slots[oslot[j]][b]
+// (ocoef NULL: every factor is 1)
 template <class T>
 __global__ void k_expr_out(const T* __restrict__ slots, const int32_t* __restrict__ oslot,
                            const T* __restrict__ ocoef, int64_t N, int32_t B, T* __restrict__ out) {
@@ -79,7 +87,7 @@ __global__ void k_expr_out(const T* __restrict__ slots, const int32_t* __restric
     for (int jj = ty; jj < 32; jj += 8) {
         const int64_t j = j0 + jj;
         const int b = b0 + tx;
-        if (j < N && b < B) tile[jj][tx] = ocoef[j] * slots[(int64_t)oslot[j] * B + b];
+        if (j < N && b < B) tile[jj][tx] = (ocoef ? ocoef[j] : T(1)) * slots[(int64_t)oslot[j] * B + b];
     }
     __syncthreads();
     for (int bb = ty; bb < 32; bb += 8) {
@@ -94,7 +102,7 @@ template <class T>
 __global__ void k_expr_out1(const T* __restrict__ slots, const int32_t* __restrict__ oslot,
                             const T* __restrict__ ocoef, int64_t N, T* __restrict__ out) {
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x)
-        out[j] = ocoef[j] * slots[oslot[j]];
+        out[j] = ocoef ? ocoef[j] * slots[oslot[j]] : slots[oslot[j]];
 }
 
 unsigned grid_for(int64_t work, int threads) {
@@ -116,22 +124,24 @@ int run(ExprProgram& E, const T* leaf, T* out, cudaStream_t s) {
         const dim3 g((unsigned)std::max<int64_t>(1, (L + 31) / 32), (unsigned)((B + 31) / 32));
         k_expr_in<T><<<g, dim3(32, 8), 0, s>>>(leaf, L, B, slots);
     }
-    const int64_t* toff = reinterpret_cast<const int64_t*>(tab + E.toff.term_off);
-    const int32_t* f1 = reinterpret_cast<const int32_t*>(tab + E.toff.f1);
-    const int32_t* f2 = reinterpret_cast<const int32_t*>(tab + E.toff.f2);
+    const auto* groups = reinterpret_cast<const ExprProgram::Group*>(tab + E.toff.groups);
+    const auto* chunks = reinterpret_cast<const ExprProgram::Chunk*>(tab + E.toff.chunks);
+    const int32_t* i1 = reinterpret_cast<const int32_t*>(tab + E.toff.i1);
+    const int32_t* i2 = reinterpret_cast<const int32_t*>(tab + E.toff.i2);
     const T* coef = reinterpret_cast<const T*>(tab + E.toff.coef);
     for (int32_t l = 1; l <= E.n_levels(); ++l) {
-        const int64_t op0 = E.lvl_begin[l - 1], nops = E.lvl_begin[l] - op0;
-        if (nops <= 0) continue;
-        const unsigned g = grid_for(nops * B, 256);
-        if (E.unit_coef)
-            k_expr_level<T, true><<<g, 256, 0, s>>>(toff, f1, f2, coef, op0, nops, B, E.op_base(), slots);
+        const int64_t c0 = E.lvl_chunk[l - 1], nc = E.lvl_chunk[l] - c0;
+        if (nc <= 0) continue;
+        if (B == 1)
+            k_expr_group<T, true><<<(unsigned)nc, 256, 0, s>>>(groups, chunks, c0, i1, i2, coef, B, E.chunk_members,
+                                                               E.op_base(), slots);
         else
-            k_expr_level<T, false><<<g, 256, 0, s>>>(toff, f1, f2, coef, op0, nops, B, E.op_base(), slots);
+            k_expr_group<T, false><<<(unsigned)nc, 256, 0, s>>>(groups, chunks, c0, i1, i2, coef, B, E.chunk_members,
+                                                                E.op_base(), slots);
     }
     if (N > 0) {
         const int32_t* oslot = reinterpret_cast<const int32_t*>(tab + E.toff.out_slot);
-        const T* ocoef = reinterpret_cast<const T*>(tab + E.toff.out_coef);
+        const T* ocoef = E.out_unit ? nullptr : reinterpret_cast<const T*>(tab + E.toff.out_coef);
         if (B == 1) {
             k_expr_out1<T><<<grid_for(N, 256), 256, 0, s>>>(slots, oslot, ocoef, N, out);
         } else {

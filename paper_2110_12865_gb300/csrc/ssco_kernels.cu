@@ -26,6 +26,7 @@
 #include <cstdint>
 #include <vector>
 
+#include "ssco_gmac.cuh"
 #include "ssco_internal.h"
 #include "ssco_tc.cuh"
 
@@ -84,16 +85,9 @@ __global__ void __launch_bounds__(256) k_assemble(const AsmGroup* __restrict__ g
     if (i >= g.nmem) return;
     const int b = blockIdx.y;
     const VT* v = vals + (int64_t)b * m;
-    const int32_t* ix = idx + g.idx_off + i;
-    double acc = g.cadd;
-    if (g.uniform) {
-        double s = 0.0;
-        for (int t = 0; t < g.nterms; ++t) s += (double)v[ix[(int64_t)t * g.nmem]];
-        acc += g.coef * s;
-    } else {
-        const double* cx = coef + g.coef_off + i;
-        for (int t = 0; t < g.nterms; ++t) acc += cx[(int64_t)t * g.nmem] * (double)v[ix[(int64_t)t * g.nmem]];
-    }
+    double acc = gmac<double, false>(g.cadd, g.nterms, g.nmem, idx + g.idx_off + i, nullptr,
+                                     g.uniform ? nullptr : coef + g.coef_off + i, g.coef,
+                                     [v](int32_t p) { return (double)v[p]; });
     if (g.diag) acc += shift[(int64_t)b * n_pats + g.sys];
     K[(int64_t)b * nnzK + g.slot_base + i] = acc;
 }

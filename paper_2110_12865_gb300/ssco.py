@@ -32,7 +32,7 @@ EXPORTED_SYMBOLS = [
     "ssco_last_launch_count", "ssco_last_error", "ssco_status_string", "ssco_plan_save", "ssco_plan_load",
     "ssco_destroy", "ssco_profile_enable", "ssco_profile_read", "ssco_kernel_name", "ssco_solve_noalloc", "ssco_profile_trace", "ssco_graph_run", "ssco_autotune",
     "ssco_cotan_weights", "ssco_tet_stiffness",
-    "ssco_expr_compile", "ssco_expr_get_info", "ssco_expr_export", "ssco_expr_output_shape",
+    "ssco_expr_compile", "ssco_expr_compile_opts", "ssco_expr_get_info", "ssco_expr_export", "ssco_expr_output_shape",
     "ssco_expr_output_pattern", "ssco_expr_bind", "ssco_expr_run", "ssco_expr_last_error", "ssco_expr_destroy",
     "ssco_expr_save", "ssco_expr_load", "ssco_set_flow", "ssco_graph_run_many",
 ]
@@ -89,11 +89,17 @@ class ExprNode(C.Structure):
                 ("vmap", C.c_void_p), ("n_vals", C.c_int64)]
 
 
+class ExprOpts(C.Structure):
+    _fields_ = [(k, C.c_int32) for k in ["batch", "precision", "inline_terms", "algebraic", "factor_min",
+                                        "t_ref", "t_compl", "reserved"]]
+
+
 class ExprInfo(C.Structure):
     _fields_ = [(k, C.c_int64) for k in ["n_leaf_vals", "n_out_vals", "n_slots", "n_ops", "n_terms",
                                         "n_unrolled"]] + \
               [(k, C.c_int32) for k in ["n_levels", "batch", "precision", "unit_coef"]] + \
-              [("table_bytes", C.c_uint64), ("workspace_bytes", C.c_uint64)]
+              [("table_bytes", C.c_uint64), ("workspace_bytes", C.c_uint64)] + \
+              [(k, C.c_int64) for k in ["n_alg_merged", "n_alg_zero", "n_factored", "n_inlined"]]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -139,6 +145,7 @@ def load_library(path: str = LIB_PATH):
         "ssco_graph_run": (i32, [vp, vp, i32, vp, vp, vp, vp]),
         "ssco_autotune": (i32, [vp, vp, i32, vp, vp, vp, i32, vp, C.POINTER(dbl)]),
         "ssco_expr_compile": (i32, [C.POINTER(ExprNode), i32, vp, i32, i32, i32, i32, C.POINTER(vp)]),
+        "ssco_expr_compile_opts": (i32, [C.POINTER(ExprNode), i32, vp, i32, C.POINTER(ExprOpts), C.POINTER(vp)]),
         "ssco_expr_get_info": (i32, [vp, C.POINTER(ExprInfo)]),
         "ssco_expr_export": (i32, [vp, i32, vp, C.c_uint64]),
         "ssco_expr_output_shape": (i32, [vp, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i64)]),
@@ -615,17 +622,23 @@ class Expr:
     def transpose(self, a):
         return self._add(EXPR_TRANSPOSE, a, -1, 0.0, 0, 0, None, None, None, 0)
 
-    def compile(self, outputs, batch=1, dtype=torch.float64, inline_terms=0):
+    def compile(self, outputs, batch=1, dtype=torch.float64, inline_terms=0, algebraic=False, factor_min=0,
+                t_ref=0, t_compl=0):
         """inline_terms > 0 keeps sums of at most that many slot multiples
-        local (expanded into their products) instead of storing them."""
-        return ExprProgram(self, list(outputs), batch, dtype, inline_terms)
+        local (expanded into their products) instead of storing them.  The
+        optional steps of ssco_expr_compile_opts: ``algebraic`` hashing,
+        factorization of slots shared by >= ``factor_min`` products, and the
+        global decomposition thresholds ``t_ref`` / ``t_compl``."""
+        opts = dict(inline_terms=int(inline_terms), algebraic=int(algebraic), factor_min=int(factor_min),
+                    t_ref=int(t_ref), t_compl=int(t_compl))
+        return ExprProgram(self, list(outputs), batch, dtype, opts)
 
 
 class ExprProgram:
     """A compiled expression: host tables, then (after bind) device tables
     and slot workspace owned by this object as torch tensors."""
 
-    def __init__(self, expr: Expr, outputs, batch, dtype, inline_terms=0, _handle=None):
+    def __init__(self, expr: Expr, outputs, batch, dtype, opts=None, _handle=None):
         self.L = load_library()
         if _handle is not None:
             self._adopt(_handle)
@@ -641,8 +654,8 @@ class ExprProgram:
         self.dtype = dtype
         prec = VALS_F32 if dtype == torch.float32 else VALS_F64
         h = C.c_void_p()
-        st = self.L.ssco_expr_compile(arr, len(expr.nodes), outs.ctypes.data, len(outs), int(batch), prec,
-                                      int(inline_terms), C.byref(h))
+        o = ExprOpts(batch=int(batch), precision=prec, **(opts or {}))
+        st = self.L.ssco_expr_compile_opts(arr, len(expr.nodes), outs.ctypes.data, len(outs), C.byref(o), C.byref(h))
         if st != SSCO_OK:
             raise SscoError(st, self.L.ssco_expr_last_error(None).decode())
         self._adopt(h)
