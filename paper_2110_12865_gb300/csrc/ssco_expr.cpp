@@ -934,9 +934,6 @@ void expr_layout_tables(ExprProgram& E) {
     // groups: runs of equal term count inside a level (the compiler orders
     // a level's expressions by term count, so a level has one run per count)
     E.groups.clear();
-    E.chunks.clear();
-    E.lvl_chunk.assign(1, 0);
-    E.chunk_members = std::max(1, 256 / std::min(E.B, 256));
     int64_t n1 = 0, n2 = 0, nc = 0;
     for (int32_t l = 0; l < E.n_levels(); ++l) {
         for (int64_t op = E.lvl_begin[l]; op < E.lvl_begin[l + 1];) {
@@ -961,12 +958,9 @@ void expr_layout_tables(ExprProgram& E) {
             if (g.quad) n2 += cells;
             g.coef_off = g.uniform ? 0 : nc;
             if (!g.uniform) nc += cells;
-            const int32_t gi = (int32_t)E.groups.size();
             E.groups.push_back(g);
-            for (int32_t m = 0; m < g.nmem; m += E.chunk_members) E.chunks.push_back(ExprProgram::Chunk{gi, m});
             op = r;
         }
-        E.lvl_chunk.push_back((int64_t)E.chunks.size());
     }
     E.n_i1 = n1, E.n_i2 = n2, E.n_coef = nc;
     E.out_unit = 1;
@@ -980,7 +974,6 @@ void expr_layout_tables(ExprProgram& E) {
         return o;
     };
     E.toff.groups = take(E.groups.size() * sizeof(ExprProgram::Group));
-    E.toff.chunks = take(E.chunks.size() * sizeof(ExprProgram::Chunk));
     E.toff.i1 = take((size_t)n1 * 4);
     E.toff.i2 = take((size_t)n2 * 4);
     E.toff.coef = take((size_t)nc * vb);
@@ -1003,8 +996,6 @@ std::vector<uint8_t> expr_table_image(const ExprProgram& E) {
     const size_t vb = expr_value_bytes(E);
     if (!E.groups.empty())
         std::memcpy(img.data() + E.toff.groups, E.groups.data(), E.groups.size() * sizeof(ExprProgram::Group));
-    if (!E.chunks.empty())
-        std::memcpy(img.data() + E.toff.chunks, E.chunks.data(), E.chunks.size() * sizeof(ExprProgram::Chunk));
     int32_t* i1 = reinterpret_cast<int32_t*>(img.data() + E.toff.i1);
     int32_t* i2 = reinterpret_cast<int32_t*>(img.data() + E.toff.i2);
     for (const ExprProgram::Group& g : E.groups)

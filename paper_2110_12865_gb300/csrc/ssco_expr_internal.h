@@ -39,8 +39,7 @@ struct ExprProgram {
     // expressions of a level in groups of equal term count -- the assembly
     // groups' form -- with term-major, member-innermost factor tables (the
     // second factor only for groups with a product of two slots, the
-    // coefficients only for groups whose coefficients differ), and chunks
-    // of members per CTA
+    // coefficients only for groups whose coefficients differ)
     struct Group {
         int32_t nterms, nmem;
         int32_t quad, uniform;  // quad: some term has two slot factors
@@ -48,17 +47,11 @@ struct ExprProgram {
         int64_t i1_off, i2_off, coef_off;
         double c_uniform;
     };
-    struct Chunk {
-        int32_t group, start;
-    };
-    std::vector<Group> groups;
-    std::vector<Chunk> chunks;
-    std::vector<int64_t> lvl_chunk;  // [n_levels + 1] chunk ranges
-    int32_t chunk_members = 256;     // members per chunk (256 / batch, at least 1)
+    std::vector<Group> groups;       // level by level, ascending op0
     int32_t out_unit = 1;            // every output factor is 1 (no factor table)
     int64_t n_i1 = 0, n_i2 = 0, n_coef = 0;
     struct {
-        size_t groups, chunks, i1, i2, coef, out_slot, out_coef, total;
+        size_t groups, i1, i2, coef, out_slot, out_coef, total;
     } toff{};
     uint8_t* d_tab = nullptr;
     uint8_t* d_ws = nullptr;

@@ -46,32 +46,40 @@ __global__ void k_expr_one(T* __restrict__ slots) {
     slots[0] = T(1);
 }
 
-// One level: a CTA per chunk of one term-count group; the group's members
-// are consecutive expressions (slots slot0 + op0 + i) and thread f takes
-// member f / B of the chunk for value set f % B (with one value set, one
-// member per thread).  The sum itself is the assembly's gather-MAC core, with
-// a second gathered factor per term in groups that have products of two
-// slots and the plain linear form (the assembly's own) in the others.
+// One level: thread f takes expression op_lo + f / B of the level for value
+// set f % B (with one value set, one expression per thread), grid-strided
+// over a grid capped at 16 CTAs per SM (fewer, longer-lived CTAs measured
+// faster than one CTA per chunk of a group).  Its term-count group is found
+// by binary search over the level's groups (consecutive runs of
+// expressions).  The sum itself is the assembly's gather-MAC core, with a
+// second gathered factor per term in groups that have products of two slots
+// and the plain linear form (the assembly's own) in the others.
 template <class T, bool kOne>
 __global__ void __launch_bounds__(256)
-    k_expr_group(const ExprProgram::Group* __restrict__ groups, const ExprProgram::Chunk* __restrict__ chunks,
-                 int64_t chunk0, const int32_t* __restrict__ i1, const int32_t* __restrict__ i2,
-                 const T* __restrict__ coef, int32_t B, int32_t chunk_members, int64_t slot0,
-                 T* __restrict__ slots) {
-    const ExprProgram::Chunk ch = chunks[chunk0 + blockIdx.x];
-    const ExprProgram::Group g = groups[ch.group];
-    const int32_t mend = min(g.nmem, ch.start + chunk_members);
-    const int64_t work = (int64_t)(mend - ch.start) * (kOne ? 1 : B);
-    for (int64_t f = threadIdx.x; f < work; f += blockDim.x) {
-        const int32_t i = ch.start + (int32_t)(kOne ? f : f / B);
+    k_expr_level(const ExprProgram::Group* __restrict__ groups, int32_t g0, int32_t g1, int64_t op_lo, int64_t nops,
+                const int32_t* __restrict__ i1, const int32_t* __restrict__ i2,
+                const T* __restrict__ coef, int32_t B, int64_t slot0, T* __restrict__ slots) {
+    const int64_t total = nops * (kOne ? 1 : B);
+    for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < total; f += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t op = op_lo + (kOne ? f : f / B);
         const int32_t b = kOne ? 0 : (int32_t)(f % B);
+        int32_t lo = g0, hi = g1 - 1;
+        while (lo < hi) {
+            const int32_t mid = (lo + hi + 1) >> 1;
+            if (groups[mid].op0 <= op)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        const ExprProgram::Group g = groups[lo];
+        const int32_t i = (int32_t)(op - g.op0);
         const T* __restrict__ x = slots + b;
         auto load = [x, B](int32_t s) { return x[(int64_t)s * (kOne ? 1 : B)]; };
         const T* cf = g.uniform ? nullptr : coef + g.coef_off + i;
         const T cu = (T)g.c_uniform;
         const T acc = g.quad ? gmac<T, true>(T(0), g.nterms, g.nmem, i1 + g.i1_off + i, i2 + g.i2_off + i, cf, cu, load)
                              : gmac<T, false>(T(0), g.nterms, g.nmem, i1 + g.i1_off + i, nullptr, cf, cu, load);
-        slots[(slot0 + g.op0 + i) * (kOne ? 1 : B) + b] = acc;
+        slots[(slot0 + op) * (kOne ? 1 : B) + b] = acc;
     }
 }
 
@@ -125,19 +133,24 @@ int run(ExprProgram& E, const T* leaf, T* out, cudaStream_t s) {
         k_expr_in<T><<<g, dim3(32, 8), 0, s>>>(leaf, L, B, slots);
     }
     const auto* groups = reinterpret_cast<const ExprProgram::Group*>(tab + E.toff.groups);
-    const auto* chunks = reinterpret_cast<const ExprProgram::Chunk*>(tab + E.toff.chunks);
     const int32_t* i1 = reinterpret_cast<const int32_t*>(tab + E.toff.i1);
     const int32_t* i2 = reinterpret_cast<const int32_t*>(tab + E.toff.i2);
     const T* coef = reinterpret_cast<const T*>(tab + E.toff.coef);
+    int32_t gcur = 0;
     for (int32_t l = 1; l <= E.n_levels(); ++l) {
-        const int64_t c0 = E.lvl_chunk[l - 1], nc = E.lvl_chunk[l] - c0;
-        if (nc <= 0) continue;
+        const int64_t op_lo = E.lvl_begin[l - 1], nops = E.lvl_begin[l] - op_lo;
+        int32_t g1 = gcur;
+        while (g1 < (int32_t)E.groups.size() && E.groups[g1].op0 < E.lvl_begin[l]) ++g1;
+        if (nops <= 0) {
+            gcur = g1;
+            continue;
+        }
+        const unsigned g = grid_for(nops * B, 256);
         if (B == 1)
-            k_expr_group<T, true><<<(unsigned)nc, 256, 0, s>>>(groups, chunks, c0, i1, i2, coef, B, E.chunk_members,
-                                                               E.op_base(), slots);
+            k_expr_level<T, true><<<g, 256, 0, s>>>(groups, gcur, g1, op_lo, nops, i1, i2, coef, B, E.op_base(), slots);
         else
-            k_expr_group<T, false><<<(unsigned)nc, 256, 0, s>>>(groups, chunks, c0, i1, i2, coef, B, E.chunk_members,
-                                                                E.op_base(), slots);
+            k_expr_level<T, false><<<g, 256, 0, s>>>(groups, gcur, g1, op_lo, nops, i1, i2, coef, B, E.op_base(), slots);
+        gcur = g1;
     }
     if (N > 0) {
         const int32_t* oslot = reinterpret_cast<const int32_t*>(tab + E.toff.out_slot);
