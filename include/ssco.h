@@ -186,7 +186,8 @@ typedef struct {
     int64_t tune_cluster_rows;   /* fronts this large: one CTA cluster per solve */
     int64_t tune_flow;           /* persistent dataflow launches: bit 0 solve sweeps,
                                     bit 1 small-front factorization; bit 2 the panel
-                                    core for per-level small fronts                 */
+                                    core for per-level small fronts; bit 3 big-front
+                                    steps with the diagonal factor fused (ssco_set_flow) */
     int64_t flow_fact_fronts;    /* fronts factored by the dataflow launches         */
     int64_t flow_solve_fronts;   /* fronts solved by the dataflow sweeps             */
 } ssco_info;
@@ -317,7 +318,11 @@ ssco_status ssco_autotune(ssco_plan plan, const void* vals, int32_t vals_dtype, 
  * launch per level and size class); bit 2: the per-level launches of small
  * fronts (those outside the dataflow) use the dataflow kernel's dense core
  * (a 16-column panel per three barriers) instead of the column-step
- * kernels.  max_polls bounds every wait (polls of
+ * kernels; bit 3: big fronts factor each 32-column step's diagonal block
+ * inside the triangular-solve launch (every CTA of the step factors it in
+ * shared memory; the factor reaches the panel one step later), so only a
+ * level's last step has a separate one-warp factor launch -- the same
+ * arithmetic, so the same factor.  max_polls bounds every wait (polls of
  * about 256 ns; 0 = keep the current bound, default 2^22): a wait that runs
  * out raises the plan's device error, the launch ends early and
  * ssco_status_get reports SSCO_ERR_TIMEOUT for every system (the results of

@@ -133,6 +133,8 @@ struct WsLayout {
     size_t resid, bnorm, r1, r2, sigma, sbar;
     size_t st_vals, st_shift, st_b, st_x;
     size_t tcpack;
+    size_t diag;                   // big fronts: one factored 32x32 diagonal block per (front, value set) of a level
+    size_t diag_slots;             // ... number of such slots
     size_t flow_fact, flow_solve;  // dataflow tickets (32 words) + done flags [slot][B]
     size_t gm_V, gm_Z, gm_H, gm_g, gm_cs, gm_sn, gm_hp, gm_y, gm_beta, gm_hn, gm_act, gm_k;  // GMRES-IR
     size_t total;
@@ -166,6 +168,8 @@ struct Tunables {
     uint32_t flow_polls = 1u << 22;  // bound of every dataflow wait (polls of ~256 ns)
     int32_t flow_stall = -1;       // test hook: this item of the first dataflow launch waits on a
                                    // flag that nothing sets (the bounded-wait path); -1 = off
+    int32_t big_fuse = 0;          // big fronts: 1 factors each 32-column step's diagonal block inside
+                                   // the trsm launch (no separate potrf launch but the last)
     int32_t tuned = 0;
 };
 

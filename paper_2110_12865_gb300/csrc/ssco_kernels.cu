@@ -1646,14 +1646,35 @@ __global__ void __launch_bounds__(288, 1) k_big_update_tcp(const DevTables t, co
 // a one-warp launch would otherwise spend fetching.  Its own launch: the
 // triangular solve below must read the factored block, and no CTA of one
 // launch may overwrite what another CTA still has to load.
+// Fused 32-column steps of a big front (k_big_trsm given a scratch area): every CTA
+// of the step factors the step's 32 x 32 diagonal block itself (one warp,
+// in shared memory) from the values in the panel, so the step needs no
+// separate potrf launch; the panel's copy of the block is not overwritten
+// during the step (other CTAs are still reading it) -- CTA 0 of each
+// (front, value set) leaves the factored block in a scratch slot, and the
+// next step's kernel (fused or k_big_potrf) writes it into the panel.
+template <class T>
+__device__ __forceinline__ void diag_copy_back(const T* __restrict__ Db, T* __restrict__ Pb, int r, int w, int pc,
+                                               int tid, int nth) {
+    const int nb = min(32, w - pc);
+    for (int e = tid; e < 1024; e += nth) {
+        const int i = e & 31, j = e >> 5;
+        if (i < nb && j <= i) Pb[(int64_t)(pc + j) * r + pc + i] = Db[j * 32 + i];
+    }
+}
+
 template <class T>
 __global__ void __launch_bounds__(32) k_big_potrf(const DevTables t, const int32_t* __restrict__ list, int kb,
                                                   T* __restrict__ panel, int64_t panel_total,
-                                                  int32_t* __restrict__ bad_col, int32_t n_pats) {
+                                                  int32_t* __restrict__ bad_col, int32_t n_pats,
+                                                  const T* __restrict__ diag) {
     const FrontDesc d = t.fronts[list[blockIdx.x]];
     const int b = blockIdx.y;
     const int r = d.r, w = d.w;
     const int c0 = kb * 32;
+    if (diag && kb >= 1 && c0 - 32 < w)
+        diag_copy_back(diag + ((int64_t)b * gridDim.x + blockIdx.x) * 1024,
+                       panel + (int64_t)b * panel_total + d.panel_off, r, w, c0 - 32, threadIdx.x, 32);
     if (c0 >= w) return;
     const int nbk = min(32, w - c0);
     T* Pb = panel + (int64_t)b * panel_total + d.panel_off + (int64_t)c0 * r + c0;
@@ -1693,23 +1714,75 @@ __global__ void __launch_bounds__(32) k_big_potrf(const DevTables t, const int32
 template <class T>
 __global__ void __launch_bounds__(256) k_big_trsm(const DevTables t, const int32_t* __restrict__ list, int kb,
                                                   T* __restrict__ panel, int64_t panel_total,
-                                                  float* __restrict__ pack, int64_t pack_total, int kpack0) {
+                                                  float* __restrict__ pack, int64_t pack_total, int kpack0,
+                                                  T* __restrict__ diag, int32_t* __restrict__ bad_col,
+                                                  int32_t n_pats) {
     const FrontDesc d = t.fronts[list[blockIdx.y]];
     const int b = blockIdx.z;
     const int r = d.r, w = d.w;
     const int c0 = kb * 32;
+    const int tid = threadIdx.x;
+    T* Pb = panel + (int64_t)b * panel_total + d.panel_off;
+    T* Db = diag ? diag + ((int64_t)b * gridDim.y + blockIdx.y) * 1024 : nullptr;
+    if (Db && blockIdx.x == 0 && kb >= 1 && c0 - 32 < w) {
+        diag_copy_back(Db, Pb, r, w, c0 - 32, tid, 256);
+        __syncthreads();  // the slot is rewritten below
+    }
     if (c0 >= w) return;
     const int nbk = min(32, w - c0);
     const int rbeg = c0 + nbk + (int)blockIdx.x * 256;
-    if (rbeg >= r) return;
-    T* Pb = panel + (int64_t)b * panel_total + d.panel_off;
+    if (!Db && rbeg >= r) return;
     __shared__ T Ld[32][33];
-    const int tid = threadIdx.x;
-    for (int e = tid; e < 32 * 32; e += 256) {
-        const int i = e & 31, j = e >> 5;
-        Ld[i][j] = (i < nbk && j <= i) ? Pb[(int64_t)(c0 + j) * r + c0 + i] : T(1);
+    if (Db) {
+        // factor the diagonal block (the arithmetic of k_big_potrf)
+        if (tid < 32) {
+            const int i = tid;
+            const T* Pd = Pb + (int64_t)c0 * r + c0;
+            T a[32];
+#pragma unroll
+            for (int k = 0; k < 32; ++k) a[k] = (i < nbk && k < nbk && k <= i) ? Pd[(int64_t)k * r + i] : T(0);
+            bool failed = false;
+#pragma unroll 1
+            for (int j = 0; j < nbk; ++j) {
+                T djj = __shfl_sync(0xffffffffu, a[0], j);
+                if (!(djj > T(0))) {
+                    if (i == 0 && !failed && blockIdx.x == 0)
+                        atomicMin(&bad_col[(int64_t)b * n_pats + d.sys], d.f + c0 + j - (int)t.sys_n_off[d.sys]);
+                    failed = true;
+                    djj = T(1);
+                }
+                const T ljj = sqrt(djj);
+                if (i == j)
+                    a[0] = ljj;
+                else if (i > j)
+                    a[0] /= ljj;
+                if (i >= j && i < nbk) Ld[i][j] = a[0];
+#pragma unroll
+                for (int k = 1; k < 32; ++k) {
+                    const T lkj = __shfl_sync(0xffffffffu, a[0], (j + k) & 31);
+                    if (i >= j + k) a[k] -= a[0] * lkj;
+                }
+#pragma unroll
+                for (int k = 0; k < 31; ++k) a[k] = a[k + 1];
+                a[31] = T(0);
+            }
+            for (int j = 0; j < 32; ++j)
+                if (!(i < nbk && j <= i)) Ld[i][j] = T(1);
+        }
+        __syncthreads();
+        if (blockIdx.x == 0)
+            for (int e = tid; e < 1024; e += 256) {
+                const int i = e & 31, j = e >> 5;
+                if (i < nbk && j <= i) Db[j * 32 + i] = Ld[i][j];
+            }
+        if (rbeg >= r) return;
+    } else {
+        for (int e = tid; e < 32 * 32; e += 256) {
+            const int i = e & 31, j = e >> 5;
+            Ld[i][j] = (i < nbk && j <= i) ? Pb[(int64_t)(c0 + j) * r + c0 + i] : T(1);
+        }
+        __syncthreads();
     }
-    __syncthreads();
     const int row = rbeg + tid;
     if (row >= r) return;
     T x[32];
@@ -3679,16 +3752,27 @@ int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cud
         // trailing triangle in one pass with K = big_panel, so the trailing
         // entries are read and written once per block instead of once per
         // 32 columns.
+        // With tune.big_fuse every step but the level's last factors its
+        // diagonal block inside the trsm launch (the block reaching the panel
+        // one step later through a scratch slot); the last step keeps the
+        // separate potrf, which also writes back the previous step's block.
         const int SB = std::max(32, P.tune.big_panel / 32 * 32);
         const bool tc = tc_level(P, (int)sizeof(T), SB);
+        const int kb_last = (ll.wmax - 1) / 32;
+        T* diag = wsp<T>(P, P.ws.diag);
         for (int C0 = 0; C0 < ll.wmax; C0 += SB) {
             const int Cend = C0 + SB;
             for (int c0 = C0; c0 < std::min(Cend, (int)ll.wmax); c0 += 32) {
                 const int kb = c0 / 32;
-                {
+                const bool fused = P.tune.big_fuse && kb < kb_last && (size_t)ll.count * B <= P.ws.diag_slots;
+                if (!fused) {
                     Prof pd(P, st, SSCO_K_BIG_POTRF);
                     k_big_potrf<T><<<dim3(ll.count, B), 32, 0, st>>>(P.dt, list, kb, panel, P.panel_total, bad,
-                                                                     P.n_pats);
+                                                                     P.n_pats,
+                                                                     P.tune.big_fuse && kb >= 1 &&
+                                                                             (size_t)ll.count * B <= P.ws.diag_slots
+                                                                         ? diag
+                                                                         : nullptr);
                     pd.end();
                     if (pd.ev >= 0) {
                         double fl = 0, by = 0;
@@ -3706,7 +3790,7 @@ int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cud
                     Prof pr(P, st, SSCO_K_BIG_TRSM);
                     k_big_trsm<T><<<dim3(cdiv(ll.rmax - c0, 256), ll.count, B), 256, 0, st>>>(
                         P.dt, list, kb, panel, P.panel_total, tc ? wsp<float>(P, P.ws.tcpack) : nullptr,
-                        P.tc_pack_total, C0);
+                        P.tc_pack_total, C0, fused ? diag : nullptr, bad, P.n_pats);
                     pr.end();
                     if (pr.ev >= 0) {
                         double fl = 0, by = 0;
@@ -3714,7 +3798,7 @@ int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cud
                             const FrontDesc& d = P.fronts[P.flow_rest[ll.list_off + q]];
                             if (c0 >= d.w) continue;
                             double nbk = std::min(32, d.w - c0), mrows = d.r - c0 - nbk;
-                            fl += mrows * nbk * nbk;
+                            fl += mrows * nbk * nbk + (fused ? nbk * nbk * nbk / 3 : 0);
                             by += 2 * (mrows + nbk) * nbk * P.tsize;
                         }
                         pr.done(fl * B, by * B);
@@ -5133,6 +5217,7 @@ int autotune(Plan& P, const void* vals, int32_t vdt, const double* shift, const 
     std::vector<Knob> knobs = {
         {&P.tune.flow, {0, 1, 2, 3}},
         {&P.tune.front_core, {0, 1}},
+        {&P.tune.big_fuse, {0, 1}},
         {&P.tune.warp_items, {152, 2 * 152, 4 * 152, 8 * 152, 16 * 152, 1 << 30}},
         {&P.tune.vec_max_cls, {0, 64, 96}},
         {&P.tune.solve_threads_big, {256, 512}},

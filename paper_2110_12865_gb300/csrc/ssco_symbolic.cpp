@@ -1139,6 +1139,13 @@ void compute_ws_layout(Plan& P) {
     w.st_b = take(B * n * 8);
     w.st_x = take(B * n * 8);
     w.tcpack = take(B * (size_t)P.tc_pack_total * 4);
+    {
+        size_t big_count = 0;
+        for (const LaunchList& ll : P.fact_launches)
+            if (ll.cls < 0) big_count = std::max<size_t>(big_count, (size_t)ll.count);
+        w.diag = take(B * big_count * 1024 * P.tsize);
+        w.diag_slots = B * big_count;
+    }
     w.flow_fact = take(128 + B * P.flow_fact.size() * 4);
     w.flow_solve = take(128 + B * P.flow_solve.size() * 4);
     {

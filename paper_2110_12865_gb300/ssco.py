@@ -450,8 +450,9 @@ class Plan:
 
     def set_flow(self, flow=3, max_polls=0, stall_item=-1):
         """Dataflow launches on (bit 0 solve sweeps, bit 1 factorization) or
-        off; bound of every wait (0 = keep); test hook stall_item (see
-        ssco_set_flow)."""
+        off, bit 2 the panel core for per-level small fronts, bit 3 big-front
+        steps with the diagonal factor fused into the trsm launch; bound of
+        every wait (0 = keep); test hook stall_item (see ssco_set_flow)."""
         self._check(self.L.ssco_set_flow(self._h, int(flow), int(max_polls), int(stall_item)))
         inf = Info()
         self._check(self.L.ssco_plan_info(self._h, C.byref(inf)))

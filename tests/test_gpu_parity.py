@@ -148,6 +148,59 @@ def test_big_panel_blocks_fp64_L_entries(S, big_panel):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_fused_big_front_steps_give_the_same_factor(S, prec):
+    """Big fronts with the diagonal block of each 32-column step factored
+    inside the trsm launch (ssco_set_flow bit 3): two patterns of different
+    front widths, two value sets each, panel blocks of 96 columns -- the
+    factor equals the separate-potrf factor bit for bit (same arithmetic),
+    the solve meets the residual bound, and in FP64 L matches the oracle to
+    1e-12 per column.  A non-positive pivot inside a fused step is reported
+    at the same column as without fusion."""
+    probs = [P.elasticity_problem(9, batch=2, cfg=2), P.elasticity_problem(6, batch=2, cfg=2)]
+    precision = S.FP64 if prec == "fp64" else S.FP32_REFINE
+    pl, x, st, vals, shift, b = run(S, probs, precision, small_front_max=32, big_panel=96)
+    assert pl.info["tune_flow"] & 8 == 0 and pl.info["max_front_rows"] > 128
+    L0 = pl.export_L()
+    pl.set_flow(pl.info["tune_flow"] | 8)
+    assert pl.info["tune_flow"] & 8
+    pl.numeric(torch.tensor(vals, device="cuda"), torch.tensor(shift, device="cuda"))
+    x1 = pl.solve(torch.tensor(b, device="cuda")).cpu().numpy()
+    st1 = pl.status()
+    assert np.array_equal(pl.export_L(), L0)
+    assert np.array_equal(x1, x) and np.all(st1["status"] == 0)
+    off = 0
+    for k, p in enumerate(probs):
+        for inst in range(2):
+            r, *_ = check_against_oracle(S, pl, p, x1, st1, inst, inst * 2 + k, col_off=off)
+            if prec == "fp64" and k == 0:
+                Lc = r.S.Lcolptr
+                L = pl.export_L()[inst]
+                colerr = max(np.linalg.norm(L[Lc[j]:Lc[j + 1]] - r.L[Lc[j]:Lc[j + 1]])
+                             / np.linalg.norm(r.L[Lc[j]:Lc[j + 1]]) for j in range(p.n))
+                assert colerr <= 1e-12
+        off += p.n
+    # an indefinite shift for system 0: minus twice the Rayleigh quotient of
+    # a smooth displacement (an upper bound of the smallest eigenvalue), so
+    # K + shift I has a negative eigenvalue and the factorization must fail
+    p0 = probs[0]
+    K0 = O.refactor_solve(p0, 0).K
+    v = np.tile([1.0, 0.0, 0.0], p0.n // 3) * np.linspace(1.0, 2.0, p0.n) * O.shifted_mask(p0)
+    bad_shift = shift.copy()
+    bad_shift[0] = shift[0] - 2.0 * float(v @ O.symv(K0, v)) / float(v @ v)
+    ref = O.refactor_solve(p0, 0, shift=bad_shift[0])
+    assert ref.bad >= 0
+    got = []
+    for flow in (pl.info["tune_flow"] | 8, pl.info["tune_flow"] & 7):
+        pl.set_flow(flow)
+        pl.numeric(torch.tensor(vals, device="cuda"), torch.tensor(bad_shift, device="cuda"))
+        pl.solve(torch.tensor(b, device="cuda"))
+        got.append(pl.status())
+    for g in got:
+        assert g["status"][0] == 3 and g["bad_col"][0] == ref.bad
+        assert np.all(g["status"][1:] == 0)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_split_solves_uneven_patterns(S, prec):
     """Multi-CTA split solves (split_rows far below the largest fronts, so
     fronts of several widths, one with more than one 256-column block, share
