@@ -55,6 +55,15 @@ def parse():
                     help="seconds a CPU-oracle worker may run (default: scaled with its dealt work)")
     ap.add_argument("--batch", type=int, default=None,
                     help="value sets of the main pattern (default: the workload's own; smaller only for profiling)")
+    ap.add_argument("--eager", action="store_true",
+                    help="every kernel launched eagerly, no CUDA graphs (for profilers that do not list "
+                         "kernels inside graphs; not the timed configuration)")
+    ap.add_argument("--vec2", type=int, default=None,
+                    help="vec2_max_cls plan option of the FP32 plans instead of the autotuner's choice "
+                         "(with --no-autotune and --flow: reproduces a tuned configuration for profiling)")
+    ap.add_argument("--flow", type=int, default=None,
+                    help="ssco_set_flow value for every plan instead of the autotuner's choice (with "
+                         "--no-autotune: reproduces a tuned launch configuration for profiling)")
     a = ap.parse_args()
     if a.steps is None:
         a.steps = {"elast24": 20, "elast48": 5, "lll": 2000}.get(a.workload, 100)
@@ -116,14 +125,14 @@ def stacked_inputs(item, B):
     return np.ascontiguousarray(vals), np.ascontiguousarray(shift), np.ascontiguousarray(b)
 
 
-def shared_plans(work, precision, rank, world, dist, S):
+def shared_plans(work, precision, rank, world, dist, S, **opts):
     """The plans of a step, analyzed once per job: with several ranks, rank 0
     runs the host symbolic phase and writes each plan file (ssco_plan_save),
     the other ranks load it (ssco_plan_load) after a barrier.  Every rank
     solves the same patterns for its own value sets, so the plans are equal;
     nothing of the data path is exchanged."""
     if world == 1 or dist is None:
-        return [S.Plan(item, precision=precision, batch=Bt) for item, Bt in work]
+        return [S.Plan(item, precision=precision, batch=Bt, **opts) for item, Bt in work]
     import tempfile
     box = [tempfile.mkdtemp(prefix="ssco_plans_") if rank == 0 else None]
     dist.broadcast_object_list(box, src=0)
@@ -131,7 +140,7 @@ def shared_plans(work, precision, rank, world, dist, S):
     plans = []
     if rank == 0:
         for (item, Bt), path in zip(work, paths):
-            pl = S.Plan(item, precision=precision, batch=Bt)
+            pl = S.Plan(item, precision=precision, batch=Bt, **opts)
             pl.save(path)
             plans.append(pl)
     dist.barrier()
@@ -297,7 +306,8 @@ def run_ours(args, rank, world, local_rank):
 
     def setup(precision):
         plans, dev_in, host_in = [], [], []
-        for (item, Bt), pl in zip(work, shared_plans(work, precision, rank, world, dist, S)):
+        opts = {"vec2_max_cls": args.vec2} if args.vec2 is not None and precision == S.FP32_REFINE else {}
+        for (item, Bt), pl in zip(work, shared_plans(work, precision, rank, world, dist, S, **opts)):
             pl.bind(dev)
             v, s, b = stacked_inputs(item, Bt)
             dev_in.append((torch.tensor(v, device=dev), torch.tensor(s, device=dev), torch.tensor(b, device=dev),
@@ -306,6 +316,9 @@ def run_ours(args, rank, world, local_rank):
                 # launch shapes chosen on this plan's data before the timed region
                 ms, knobs = pl.autotune(*dev_in[-1], reps=3)
                 tuned.append(knobs)
+            if args.flow is not None or args.eager:
+                pl.set_flow((args.flow if args.flow is not None else pl.info["tune_flow"] & 15) |
+                            (16 if args.eager else 0))
             host_in.append((torch.tensor(v).pin_memory(), torch.tensor(s).pin_memory(), torch.tensor(b).pin_memory(),
                             torch.empty(b.shape, dtype=torch.float64).pin_memory()))
             plans.append(pl)
@@ -326,6 +339,8 @@ def run_ours(args, rank, world, local_rank):
     launches_per_step = {}
 
     def step(plans, dev_in):
+        if args.eager:
+            return eager_step(plans, dev_in)
         # ONE captured CUDA graph for the whole step: every plan's numeric +
         # solve (refinement loop on the device) is an independent branch;
         # the kernels it runs are those of an eager step
@@ -397,6 +412,12 @@ def run_ours(args, rank, world, local_rank):
     if clocks:
         out["clocks"] = clocks
     out["config"]["autotuned"] = tuned if args.autotune else None
+    if args.flow is not None:
+        out["config"]["flow"] = args.flow
+    if args.vec2 is not None:
+        out["config"]["vec2_max_cls"] = args.vec2
+    if args.eager:
+        out["config"]["api"] = "eager ssco_numeric + ssco_solve per plan, no CUDA graphs (profiling mode)"
     xs32 = _pick_samples(work, dev32)
     if args.no_extras:
         out["_xcheck"] = {"fp32": xs32}

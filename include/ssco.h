@@ -135,7 +135,11 @@ typedef struct {
  *   the system's status is the refinement's (OK once the FP64 residual met
  *   refine_tol), not SSCO_ERR_NOT_SPD.
  * gmres_restart: Krylov vectors per GMRES-IR correction (1 .. 64; 0 =
- *   default 16).  */
+ *   default 16).
+ * vec2_max_cls (SSCO_FP32_REFINE): small-front size classes above the
+ *   four-value-set classes and up to this many rows are factored two value
+ *   sets per CTA (0 = default off; 128 or 160; ssco_autotune may switch it
+ *   on).  */
 typedef struct {
     int32_t precision;
     int32_t batch;
@@ -151,6 +155,7 @@ typedef struct {
     int32_t cluster_rows;
     int32_t refine_mode;
     int32_t gmres_restart;
+    int32_t vec2_max_cls;
 } ssco_op;
 
 /* Sizes and counts of an analyzed plan (all for the concatenated system). */
@@ -187,9 +192,12 @@ typedef struct {
     int64_t tune_flow;           /* persistent dataflow launches: bit 0 solve sweeps,
                                     bit 1 small-front factorization; bit 2 the panel
                                     core for per-level small fronts; bit 3 big-front
-                                    steps with the diagonal factor fused (ssco_set_flow) */
+                                    steps with the diagonal factor fused; bit 4 no solve
+                                    graphs (ssco_set_flow)                           */
     int64_t flow_fact_fronts;    /* fronts factored by the dataflow launches         */
     int64_t flow_solve_fronts;   /* fronts solved by the dataflow sweeps             */
+    int64_t tune_vec2_max_cls;   /* FP32 classes above tune_vec_max_cls up to this
+                                    size: two value sets per CTA (0 = none)          */
 } ssco_info;
 
 /* ssco_plan_export selectors (host copies; sizes in elements).          */
@@ -322,7 +330,10 @@ ssco_status ssco_autotune(ssco_plan plan, const void* vals, int32_t vals_dtype, 
  * inside the triangular-solve launch (every CTA of the step factors it in
  * shared memory; the factor reaches the panel one step later), so only a
  * level's last step has a separate one-warp factor launch -- the same
- * arithmetic, so the same factor.  max_polls bounds every wait (polls of
+ * arithmetic, so the same factor; bit 4: ssco_solve of an FP32 plan launches
+ * its kernels one by one instead of replaying its cached solve graph (for
+ * profilers that do not see kernels inside graphs; the call then
+ * synchronizes once per refinement step).  max_polls bounds every wait (polls of
  * about 256 ns; 0 = keep the current bound, default 2^22): a wait that runs
  * out raises the plan's device error, the launch ends early and
  * ssco_status_get reports SSCO_ERR_TIMEOUT for every system (the results of

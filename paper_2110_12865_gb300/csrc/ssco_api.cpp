@@ -246,9 +246,10 @@ ssco_status ssco_plan_info(ssco_plan h, ssco_info* o) {
     o->tune_split_rows = P.tune.split_rows;
     o->tune_warp_front_max = P.tune.warp_front_max;
     o->tune_cluster_rows = P.tune.cluster_rows;
-    o->tune_flow = P.tune.flow | (P.tune.front_core << 2) | (P.tune.big_fuse << 3);
+    o->tune_flow = P.tune.flow | (P.tune.front_core << 2) | (P.tune.big_fuse << 3) | ((int)P.no_graphs << 4);
     o->flow_fact_fronts = (int64_t)P.flow_fact.size();
     o->flow_solve_fronts = (int64_t)P.flow_solve.size();
+    o->tune_vec2_max_cls = P.tune.vec2_max_cls;
     return SSCO_OK;
 }
 
@@ -545,12 +546,13 @@ int64_t ssco_last_launch_count(ssco_plan h) { return h ? h->P.launches : 0; }
 
 ssco_status ssco_set_flow(ssco_plan h, int32_t flow, int64_t max_polls, int32_t stall_item) {
     if (!h) return fail(h, SSCO_ERR_INVALID_ARG, "NULL plan");
-    if (flow < 0 || flow > 15 || max_polls < 0 || max_polls > 0xFFFFFFFFll || stall_item < -1)
-        return fail(h, SSCO_ERR_INVALID_ARG, "flow must be 0..15, max_polls 0..2^32-1, stall_item >= -1");
+    if (flow < 0 || flow > 31 || max_polls < 0 || max_polls > 0xFFFFFFFFll || stall_item < -1)
+        return fail(h, SSCO_ERR_INVALID_ARG, "flow must be 0..31, max_polls 0..2^32-1, stall_item >= -1");
     Plan& P = h->P;
     P.tune.flow = flow & 3;
     P.tune.front_core = (flow >> 2) & 1;
     P.tune.big_fuse = (flow >> 3) & 1;
+    P.no_graphs = ((flow >> 4) & 1) != 0;
     if (max_polls > 0) P.tune.flow_polls = (uint32_t)max_polls;
     P.tune.flow_stall = stall_item;
     graph_release(P);

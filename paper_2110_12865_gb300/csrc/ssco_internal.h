@@ -152,6 +152,7 @@ struct ProfRec {
 struct Tunables {
     int32_t warp_items = 8 * 152;  // a solve level goes warp-per-item at >= this many items
     int32_t vec_max_cls = 96;      // largest size class factored V value sets per CTA
+    int32_t vec2_max_cls = 0;      // FP32: larger classes up to this size factored two value sets per CTA
     int32_t solve_threads_big = 512;  // CTA size of solve levels with fronts > 512 rows
     int32_t use_tc = 1;            // FP32 big-front updates on tcgen05: 0 off, 1 per-tile CTAs,
                                    // 2 persistent CTAs for the wide trailing updates
@@ -293,6 +294,7 @@ struct Plan {
     int64_t s_launches[2] = {0, 0};
     int32_t s_next = 0;
     bool eager_only = false;  // set while ssco_autotune times its candidates
+    bool no_graphs = false;   // ssco_set_flow bit 4: FP32 solves launch eagerly (for profilers)
 
     // one graph over several plans (ssco_graph_run_many; held by the first plan)
     void* m_graph = nullptr;

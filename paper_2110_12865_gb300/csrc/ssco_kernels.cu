@@ -3698,11 +3698,17 @@ int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cud
                 continue;
             }
             const bool vec = ll.cls <= P.tune.vec_max_cls && B >= V;
-            Prof pr(P, st, vec ? SSCO_K_FRONT_VEC : SSCO_K_FRONT_SMALL);
+            // FP32 classes above vec_max_cls: two value sets per CTA up to
+            // vec2_max_cls (the index loads and barriers shared by two)
+            const bool vec2 = !vec && sizeof(T) == 4 && ll.cls <= P.tune.vec2_max_cls && B >= 2;
+            Prof pr(P, st, vec || vec2 ? SSCO_K_FRONT_VEC : SSCO_K_FRONT_SMALL);
             const int nw = ll.cls <= 32 ? 2 : (ll.cls <= 64 ? 4 : 8);
             const size_t smem = ((size_t)ll.rmax * (ll.rmax + 1) / 2 + kSmallPad) * sizeof(T);
             if (vec)
                 k_front_vec<T, V><<<dim3(ll.count, (B + V - 1) / V), dim3(32, nw), smem * V, st>>>(
+                    P.dt, list, B, K, P.nnzK, panel, P.panel_total, upd, P.upd_total, bad, P.n_pats);
+            else if (vec2)
+                k_front_vec<T, 2><<<dim3(ll.count, (B + 1) / 2), dim3(32, nw), smem * 2, st>>>(
                     P.dt, list, B, K, P.nnzK, panel, P.panel_total, upd, P.upd_total, bad, P.n_pats);
             else
             k_front_small<T><<<dim3(ll.count, B), dim3(32, nw), smem, st>>>(P.dt, list, K, P.nnzK, panel,
@@ -4885,6 +4891,7 @@ int set_attr_T() {
             e = (int)cudaFuncSetAttribute(k_big_update_tcp, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcpSmem);
     }
     if (!e) e = allow_dynamic_smem(k_front_vec<T, sizeof(T) == 4 ? 4 : 2>);
+    if (!e && sizeof(T) == 4) e = allow_dynamic_smem(k_front_vec<T, 2>);
     if (!e) e = allow_dynamic_smem(k_tiny_factor<T>);
     if (!e) e = allow_dynamic_smem(k_tiny_fwd<T>);
     if (!e) e = allow_dynamic_smem(k_tiny_bwd<T>);
@@ -4981,10 +4988,10 @@ int solve_graph_run(Plan& P, const double* b, double* x, cudaStream_t stream) {
 }
 
 // FP32 plans with plain refinement run the solve as a captured graph (so the
-// call does not synchronize); per-launch profiling and the autotuner's
-// timings use the eager launches.
+// call does not synchronize); per-launch profiling, the autotuner's timings
+// and plans set to no_graphs use the eager launches.
 inline bool solve_by_graph(const Plan& P) {
-    return P.prec == SSCO_FP32_REFINE && P.refine_mode == 0 && !P.prof && !P.eager_only;
+    return P.prec == SSCO_FP32_REFINE && P.refine_mode == 0 && !P.prof && !P.eager_only && !P.no_graphs;
 }
 
 int launch_solve(Plan& P, const double* b, double* x, void* stream, bool* ok) {
@@ -5218,6 +5225,7 @@ int autotune(Plan& P, const void* vals, int32_t vdt, const double* shift, const 
         {&P.tune.flow, {0, 1, 2, 3}},
         {&P.tune.front_core, {0, 1}},
         {&P.tune.big_fuse, {0, 1}},
+        {&P.tune.vec2_max_cls, {0, 128, 160}},
         {&P.tune.warp_items, {152, 2 * 152, 4 * 152, 8 * 152, 16 * 152, 1 << 30}},
         {&P.tune.vec_max_cls, {0, 64, 96}},
         {&P.tune.solve_threads_big, {256, 512}},

@@ -202,6 +202,9 @@ ssco_status analyze_impl(const ssco_pattern* const* pats, int32_t n_pats, const 
         return bad(P, SSCO_ERR_INVALID_ARG, "gmres_restart must be in 0..64");
     P.refine_mode = op->precision == SSCO_FP32_REFINE ? op->refine_mode : 0;
     P.gmres_m = op->gmres_restart > 0 ? op->gmres_restart : 16;
+    if (op->vec2_max_cls != 0 && op->vec2_max_cls != 128 && op->vec2_max_cls != 160)
+        return bad(P, SSCO_ERR_INVALID_ARG, "vec2_max_cls must be 0, 128 or 160");
+    P.tune.vec2_max_cls = op->precision == SSCO_FP32_REFINE ? op->vec2_max_cls : 0;
     P.tsize = P.prec == SSCO_FP64 ? 8 : 4;
     // One CTA per (front, instance) holds the front as a packed lower
     // triangle in shared memory (r(r+1)/2 * sizeof(T) <= 227 KB).  Its

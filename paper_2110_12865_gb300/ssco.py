@@ -60,7 +60,7 @@ class Op(C.Structure):
                 ("amalgamate", C.c_int32), ("tiny_front_max", C.c_int32), ("tensor_cores", C.c_int32),
                 ("big_panel", C.c_int32), ("split_rows", C.c_int32),
                 ("warp_front_max", C.c_int32), ("cluster_rows", C.c_int32),
-                ("refine_mode", C.c_int32), ("gmres_restart", C.c_int32)]
+                ("refine_mode", C.c_int32), ("gmres_restart", C.c_int32), ("vec2_max_cls", C.c_int32)]
 
 
 class KernelStat(C.Structure):
@@ -77,7 +77,7 @@ class Info(C.Structure):
               [(k, C.c_int64) for k in ["tune_warp_items", "tune_vec_max_cls", "tune_solve_threads_big", "tuned",
                                         "tune_use_tc", "tune_big_panel", "tune_split_rows",
                                         "tune_warp_front_max", "tune_cluster_rows", "tune_flow",
-                                        "flow_fact_fronts", "flow_solve_fronts"]]
+                                        "flow_fact_fronts", "flow_solve_fronts", "tune_vec2_max_cls"]]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -231,12 +231,15 @@ class Plan:
     ``warp_front_max`` small-front classes factored one warp per front;
     ``refine_mode`` 0 plain refinement, 1 GMRES-IR (FP64 GMRES preconditioned
     by the FP32 factor, ``gmres_restart`` Krylov vectors), 2 plain refinement
-    then GMRES-IR for the systems where it stagnated.
+    then GMRES-IR for the systems where it stagnated; ``vec2_max_cls`` (FP32)
+    larger small-front classes up to 128 or 160 rows factored two value sets
+    per CTA.
     ``autotune`` re-chooses the launch-shape options on the caller's data."""
 
     def __init__(self, problems, precision=FP64, batch=None, refine_tol=1e-10, refine_max_iter=30,
                  small_front_max=0, amalgamate=1, tiny_front_max=0, tensor_cores=0, big_panel=0,
-                 split_rows=0, warp_front_max=0, cluster_rows=0, refine_mode=0, gmres_restart=0, _handle=None):
+                 split_rows=0, warp_front_max=0, cluster_rows=0, refine_mode=0, gmres_restart=0, vec2_max_cls=0,
+                 _handle=None):
         self.L = load_library()
         if _handle is not None:
             self._h = _handle
@@ -285,6 +288,7 @@ class Plan:
             op.cluster_rows = cluster_rows
             op.refine_mode = refine_mode
             op.gmres_restart = gmres_restart
+            op.vec2_max_cls = vec2_max_cls
             h = C.c_void_p()
             st = self.L.ssco_analyze(arr, len(pats), C.byref(op), C.byref(h))
             if st != SSCO_OK:
@@ -400,7 +404,8 @@ class Plan:
         return best.value, {k: self.info[k] for k in ("tune_warp_items", "tune_vec_max_cls",
                                                       "tune_solve_threads_big", "tune_use_tc",
                                                       "tune_big_panel", "tune_split_rows",
-                                                      "tune_warp_front_max", "tune_cluster_rows", "tune_flow")}
+                                                      "tune_warp_front_max", "tune_cluster_rows", "tune_flow",
+                                                      "tune_vec2_max_cls")}
 
     def graph_run(self, vals: torch.Tensor, shift: torch.Tensor, b: torch.Tensor, x: torch.Tensor, stream=None):
         """numeric + solve as one captured CUDA graph (re-captured when the

@@ -200,6 +200,25 @@ def test_fused_big_front_steps_give_the_same_factor(S, prec):
         assert np.all(g["status"][1:] == 0)
 
 
+def test_two_value_sets_per_cta_for_larger_classes(S):
+    """FP32 small-front classes of 128 and 160 rows factored two value sets
+    per CTA (vec2_max_cls = 160), with an odd batch so that the last CTA of
+    every front holds one value set: the factor agrees with the
+    one-value-set-per-CTA factor to FP32 rounding and the solves meet the
+    residual bound against the oracle's K."""
+    p = P.trigrid_problem(96, batch=5, cfg=3)
+    pl0, x0, st0, *_ = run(S, p, S.FP32_REFINE)
+    pl1, x1, st1, *_ = run(S, p, S.FP32_REFINE, vec2_max_cls=160)
+    assert pl0.info["tune_vec2_max_cls"] == 0 and pl1.info["tune_vec2_max_cls"] == 160
+    assert pl1.info["max_front_rows"] > 128
+    L0, L1 = pl0.export_L(), pl1.export_L()
+    assert np.max(np.abs(L1 - L0)) <= 1e-5 * np.max(np.abs(L0))
+    for inst in (0, 3, 4):
+        check_against_oracle(S, pl1, p, x1, st1, inst, inst)
+    with pytest.raises(S.SscoError):
+        S.Plan(p, precision=S.FP32_REFINE, vec2_max_cls=100)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_split_solves_uneven_patterns(S, prec):
     """Multi-CTA split solves (split_rows far below the largest fronts, so
@@ -501,6 +520,7 @@ def test_autotune_keeps_parity_and_persists(S, tmp_path):
     ms, knobs = pl.autotune(v, sh, bt, x, reps=2)
     assert ms > 0 and pl.info["tuned"] == 1
     assert knobs["tune_vec_max_cls"] in (0, 64, 96) and knobs["tune_solve_threads_big"] in (256, 512)
+    assert knobs["tune_vec2_max_cls"] in (0, 128, 160)
     pl.graph_run(v, sh, bt, x)
     st = pl.status()
     xh = x.cpu().numpy()
@@ -897,8 +917,9 @@ def test_fp32_solve_graph_matches_eager_and_recaptures(S):
     graph (no host round trip): the result and the per-system iteration
     counts are bit-identical to the host-driven loop (forced here by
     per-launch profiling), for two right-hand-side buffers in turn (the two
-    cached graphs) and for a third (a re-capture), and the adjoint through
-    its own cached graph matches its host-driven form."""
+    cached graphs) and for a third (a re-capture), the same with graphs
+    switched off (ssco_set_flow bit 4), and the adjoint through its own
+    cached graph matches its host-driven form."""
     p = P.trigrid_problem(16, batch=4, cfg=3)
     pl = S.Plan(p, precision=S.FP32_REFINE).bind()
     vt, st_ = torch.tensor(p.vals, device="cuda"), torch.tensor(p.shift, device="cuda")
@@ -916,6 +937,14 @@ def test_fp32_solve_graph_matches_eager_and_recaptures(S):
     for k, (x, it) in enumerate(graph_x):
         xe, ite = eager_x[k % 3]
         assert np.array_equal(x, xe) and np.array_equal(it, ite)
+    # ssco_set_flow bit 4: eager launches without profiling, same results
+    flow = pl.info["tune_flow"]
+    pl.set_flow(flow | 16)
+    assert pl.info["tune_flow"] & 16
+    for k, b in enumerate(bs):
+        assert np.array_equal(pl.solve(b).cpu().numpy(), eager_x[k][0])
+        assert pl.last_launch_count() > 3
+    pl.set_flow(flow)
     x = pl.solve(bs[0])
     xbar = 2.0 * (x - torch.tensor(rng.standard_normal(p.b.shape), device="cuda"))
     g1 = [t.cpu().numpy() for t in pl.backward(x, xbar)]
