@@ -387,6 +387,12 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- headline: FP32 factor + FP64 refinement -------------------------
     plans32, dev32, host32 = setup(S.FP32_REFINE)
+    tuned_many = None
+    if args.autotune and len(plans32) > 1 and args.workload != "elast48":
+        # the plans' dataflow choices decided together, on the step's graph
+        ms_many, flows = S.autotune_many(plans32, [t[0] for t in dev32], [t[1] for t in dev32],
+                                         [t[2] for t in dev32], [t[3] for t in dev32], reps=5)
+        tuned_many = {"step_ms": ms_many, "tune_flow": flows}
     sampler = ClockSampler(local_rank)
     ms, launches, wall, clocks = timed(plans32, dev32, args.steps, args.warmup, sampler)
     ok32, res32, its32 = status_summary(plans32)
@@ -412,6 +418,8 @@ def run_ours(args, rank, world, local_rank):
     if clocks:
         out["clocks"] = clocks
     out["config"]["autotuned"] = tuned if args.autotune else None
+    if tuned_many is not None:
+        out["config"]["autotuned_many"] = tuned_many
     if args.flow is not None:
         out["config"]["flow"] = args.flow
     if args.vec2 is not None:

@@ -366,6 +366,20 @@ ssco_status ssco_graph_run_many(const ssco_plan* plans, int32_t n_plans, const v
                                 const int32_t* vals_dtype, const double* const* shift, const double* const* b,
                                 double* const* x, void* stream);
 
+/* ssco_autotune for the plans of one ssco_graph_run_many step: coordinate
+ * descent over each plan's dataflow choices (the bits of ssco_set_flow 0..3
+ * and the two-value-set classes of FP32 plans), every candidate timed on
+ * the multi-plan graph itself (median of `reps` replays after a warm-up;
+ * kept when 1 % faster).  A plan's best choice alone can differ from its
+ * best choice beside the others, whose work it overlaps with (Sec. 4.3's
+ * grouping decided across the patterns of a step).  Arguments as for
+ * ssco_graph_run_many; run ssco_autotune on each plan first for its other
+ * knobs.  Leaves valid results in x; *best_ms (may be NULL) receives the
+ * best step time. */
+ssco_status ssco_autotune_many(const ssco_plan* plans, int32_t n_plans, const void* const* vals,
+                               const int32_t* vals_dtype, const double* const* shift, const double* const* b,
+                               double* const* x, int32_t reps, void* stream, double* best_ms);
+
 /* End-to-end call on HOST buffers: copies vals/shift/b to the device
  * (staging areas inside the workspace), runs numeric + solve as the captured
  * graph of ssco_graph_run, copies x back and synchronizes.  Host arrays use

@@ -339,6 +339,9 @@ int launch_graph_run(Plan& P, const void* vals, int32_t vals_dtype, const double
 int launch_graph_run_many(Plan* const* plans, int32_t n, const void* const* vals, const int32_t* vals_dtype,
                           const double* const* shift, const double* const* b, double* const* x, void* stream);
 void graph_release(Plan& P);
+int autotune_many(Plan* const* plans, int32_t n, const void* const* vals, const int32_t* vals_dtype,
+                  const double* const* shift, const double* const* b, double* const* x, int32_t reps, void* stream,
+                  double* best_ms);
 int autotune(Plan& P, const void* vals, int32_t vals_dtype, const double* shift, const double* b, double* x,
              int32_t reps, void* stream, double* best_ms);
 void graph_destroy_streams(Plan& P);

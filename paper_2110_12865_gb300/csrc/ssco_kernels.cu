@@ -5186,6 +5186,75 @@ int launch_graph_run_many(Plan* const* plans, int32_t n, const void* const* vals
     return (int)cudaGraphLaunch((cudaGraphExec_t)P0.m_exec, (cudaStream_t)stream);
 }
 
+// Coordinate descent over the dataflow-related knobs of every plan of a
+// multi-plan graph, timed on that graph (ssco_graph_run_many: the plans as
+// concurrent branches), so that a plan's choice accounts for the work of the
+// others it overlaps with.  Each candidate re-captures the graph (the
+// change releases the plan's graphs); median of `reps` replays after one
+// warm-up; a candidate is kept when it is 1 % faster.
+int autotune_many(Plan* const* plans, int32_t n, const void* const* vals, const int32_t* vdt,
+                  const double* const* shift, const double* const* b, double* const* x, int32_t reps, void* stream,
+                  double* best_ms) {
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    int e = (int)cudaEventCreate(&e0);
+    if (!e) e = (int)cudaEventCreate(&e1);
+    if (e) return e;
+    auto measure = [&](double* ms_out) -> int {
+        std::vector<float> t;
+        for (int i = 0; i <= reps; ++i) {
+            int r = (int)cudaEventRecord(e0, s);
+            if (!r) r = launch_graph_run_many(plans, n, vals, vdt, shift, b, x, s);
+            if (!r) r = (int)cudaEventRecord(e1, s);
+            if (!r) r = (int)cudaEventSynchronize(e1);
+            if (r) return r;
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (i > 0) t.push_back(ms);
+        }
+        std::sort(t.begin(), t.end());
+        *ms_out = t.empty() ? 0.0 : t[t.size() / 2];
+        return 0;
+    };
+    double best = 0;
+    e = measure(&best);
+    for (int32_t i = 0; i < n && !e; ++i) {
+        Plan& P = *plans[i];
+        struct Knob {
+            int32_t* field;
+            std::vector<int32_t> cand;
+        };
+        std::vector<Knob> knobs = {{&P.tune.flow, {0, 1, 2, 3}},
+                                   {&P.tune.front_core, {0, 1}},
+                                   {&P.tune.big_fuse, {0, 1}},
+                                   {&P.tune.vec2_max_cls, P.tsize == 4 ? std::vector<int32_t>{0, 128, 160}
+                                                                       : std::vector<int32_t>{0}}};
+        for (Knob& k : knobs) {
+            if (e) break;
+            const int32_t keep = *k.field;
+            int32_t arg = keep;
+            for (int32_t c : k.cand) {
+                if (c == keep) continue;
+                *k.field = c;
+                graph_release(P);
+                double ms = 0;
+                e = measure(&ms);
+                if (e) break;
+                if (ms < best * 0.99) {
+                    best = ms;
+                    arg = c;
+                }
+            }
+            *k.field = arg;
+            graph_release(P);
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best_ms) *best_ms = best;
+    return e;
+}
+
 // Coordinate descent over the launch-shape knobs: each candidate is timed
 // (CUDA events, median of `reps` eager numeric + solve steps after one
 // warm-up) on the caller's data; the fastest setting of each knob is kept.

@@ -34,7 +34,7 @@ EXPORTED_SYMBOLS = [
     "ssco_cotan_weights", "ssco_tet_stiffness",
     "ssco_expr_compile", "ssco_expr_compile_opts", "ssco_expr_get_info", "ssco_expr_export", "ssco_expr_output_shape",
     "ssco_expr_output_pattern", "ssco_expr_bind", "ssco_expr_run", "ssco_expr_last_error", "ssco_expr_destroy",
-    "ssco_expr_save", "ssco_expr_load", "ssco_set_flow", "ssco_graph_run_many",
+    "ssco_expr_save", "ssco_expr_load", "ssco_set_flow", "ssco_graph_run_many", "ssco_autotune_many",
 ]
 KERNEL_KINDS = ["assemble", "front_small", "big_init", "big_kscatter", "big_update", "big_potrf", "big_syrk",
                 "fwd_solve", "bwd_solve", "resid", "check", "vector", "grad", "front_tiny", "big_trsm", "front_vec",
@@ -158,6 +158,7 @@ def load_library(path: str = LIB_PATH):
         "ssco_expr_destroy": (None, [vp]),
         "ssco_set_flow": (i32, [vp, i32, i64, i32]),
         "ssco_graph_run_many": (i32, [vp, i32, vp, vp, vp, vp, vp, vp]),
+        "ssco_autotune_many": (i32, [vp, i32, vp, vp, vp, vp, vp, i32, vp, C.POINTER(dbl)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -522,6 +523,28 @@ def graph_run_many(plans, vals, shifts, bs, xs, stream=None):
     if st != SSCO_OK:
         raise SscoError(st, L.ssco_last_error(plans[0]._h).decode())
     return xs
+
+
+def autotune_many(plans, vals, shifts, bs, xs, reps=3, stream=None):
+    """ssco_autotune_many: the plans' dataflow choices tuned on their
+    multi-plan graph.  Returns (best step ms, tune_flow of every plan)."""
+    L = load_library()
+    n = len(plans)
+    arr = lambda ts: (C.c_void_p * n)(*[t.data_ptr() for t in ts])
+    dts = (C.c_int32 * n)(*[VALS_F64 if v.dtype == torch.float64 else VALS_F32 for v in vals])
+    hs = (C.c_void_p * n)(*[p._h.value if isinstance(p._h, C.c_void_p) else p._h for p in plans])
+    best = C.c_double(0.0)
+    st = L.ssco_autotune_many(hs, n, arr(vals), dts, arr(shifts), arr(bs), arr(xs), int(reps), _stream_ptr(stream),
+                              C.byref(best))
+    if st != SSCO_OK:
+        raise SscoError(st, L.ssco_last_error(plans[0]._h).decode())
+    flows = []
+    for p in plans:
+        inf = Info()
+        L.ssco_plan_info(p._h, C.byref(inf))
+        p.info = inf.as_dict()
+        flows.append(int(p.info["tune_flow"]))
+    return best.value, flows
 
 
 def ssco_solve(plan: Plan, vals, shift, b):

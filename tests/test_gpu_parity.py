@@ -510,6 +510,21 @@ def test_graph_run_many_matches_single_graphs(S, prec):
     with pytest.raises(S.SscoError):
         S.graph_run_many([plans[0], plans[0]], [ins[0][0]] * 2, [ins[0][1]] * 2, [ins[0][2]] * 2,
                          [ins[0][3], ins[0][3].clone()])
+    # the dataflow choices tuned on the multi-plan graph (ssco_autotune_many):
+    # every plan keeps valid settings and the tuned graph solves every system
+    ms, flows = S.autotune_many(plans, [t[0] for t in ins], [t[1] for t in ins], [t[2] for t in ins],
+                                [t[3] for t in ins], reps=2)
+    assert ms > 0 and len(flows) == 2 and all(0 <= f < 16 for f in flows)
+    for t in ins:
+        t[3].fill_(float("nan"))
+    S.graph_run_many(plans, [t[0] for t in ins], [t[1] for t in ins], [t[2] for t in ins], [t[3] for t in ins])
+    for pl, t, (xe, it) in zip(plans, ins, ref):
+        st = pl.status()
+        assert np.all(st["status"] == 0) and np.all(st["resid"] <= RESID_TOL)
+        assert np.max(np.abs(t[3].cpu().numpy() - xe)) <= 1e-9 * np.max(np.abs(xe))
+    with pytest.raises(S.SscoError):
+        S.autotune_many(plans, [t[0] for t in ins], [t[1] for t in ins], [t[2] for t in ins],
+                        [t[3] for t in ins], reps=0)
 
 
 def test_autotune_keeps_parity_and_persists(S, tmp_path):
