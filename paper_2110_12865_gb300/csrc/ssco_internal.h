@@ -133,6 +133,8 @@ struct WsLayout {
     size_t resid, bnorm, r1, r2, sigma, sbar;
     size_t st_vals, st_shift, st_b, st_x;
     size_t tcpack;
+    size_t sys_psum, sys_pmax;     // per-system norms: chunk partial sums and maxima [S][sys_maxc]
+    int32_t sys_maxc;              // ... chunks of the longest system
     size_t diag;                   // big fronts: one factored 32x32 diagonal block per (front, value set) of a level
     size_t diag_slots;             // ... number of such slots
     size_t flow_fact, flow_solve;  // dataflow tickets (32 words) + done flags [slot][B]

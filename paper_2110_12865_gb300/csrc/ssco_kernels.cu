@@ -2882,16 +2882,75 @@ __global__ void k_from_T(const T* __restrict__ src, double* __restrict__ dst, in
 }
 
 // per-system init: ||b||_2, counters
-__global__ void k_sys_init(const double* __restrict__ bp, const int64_t* __restrict__ sys_n_off, int32_t n_pats,
-                           int64_t n, double* __restrict__ bnorm, int32_t* __restrict__ active,
+// Per-system norms in two passes: k_sys_partial reduces chunks of
+// kSysChunk rows of every system over many CTAs (one per chunk and system),
+// then k_sys_init / k_check combine a system's chunk results in chunk order
+// (a fixed order: the same sums on every run).  One CTA per whole system
+// left the GPU idle while the largest system's CTA walked its rows.
+constexpr int kSysChunk = 2048;
+
+__global__ void k_sys_partial(const double* __restrict__ v, const int64_t* __restrict__ sys_n_off, int32_t n_pats,
+                              int64_t n, int32_t maxc, const int32_t* __restrict__ active, double* __restrict__ psum,
+                              double* __restrict__ pmax) {
+    const int c = blockIdx.x, s = blockIdx.y;
+    if (active && !active[s]) return;
+    const int b = s / n_pats, k = s % n_pats;
+    const int64_t lo = sys_n_off[k] + (int64_t)c * kSysChunk;
+    const int64_t hi = min(sys_n_off[k + 1], lo + kSysChunk);
+    if (lo >= hi) return;
+    const double* vb = v + (int64_t)b * n;
+    double sum = 0.0, mx = 0.0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const double a = vb[i];
+        sum += a * a;
+        mx = fmax(mx, fabs(a));
+        if (!(fabs(a) <= 1.7976931348623157e308)) mx = INFINITY;
+    }
+    block_sum_max(sum, mx);
+    if (threadIdx.x == 0) {
+        psum[(int64_t)s * maxc + c] = sum;
+        pmax[(int64_t)s * maxc + c] = mx;
+    }
+}
+
+// Sum of squares and max magnitude of system s (valid in thread 0): from
+// its chunk results when psum is given, else directly from its rows of v
+// (one pass: plans with at least as many systems as SMs, where the systems
+// alone spread over the GPU and a second launch would cost more).
+__device__ __forceinline__ void sys_combine(const double* __restrict__ v, int64_t n,
+                                            const int64_t* __restrict__ sys_n_off, int32_t n_pats, int s,
+                                            int32_t maxc, const double* __restrict__ psum,
+                                            const double* __restrict__ pmax, double& sum, double& mx) {
+    const int b = s / n_pats, k = s % n_pats;
+    sum = 0.0;
+    mx = 0.0;
+    if (psum) {
+        const int nch = (int)((sys_n_off[k + 1] - sys_n_off[k] + kSysChunk - 1) / kSysChunk);
+        for (int c = threadIdx.x; c < nch; c += blockDim.x) {
+            sum += psum[(int64_t)s * maxc + c];
+            mx = fmax(mx, pmax[(int64_t)s * maxc + c]);
+        }
+    } else {
+        const double* vb = v + (int64_t)b * n;
+        for (int64_t i = sys_n_off[k] + threadIdx.x; i < sys_n_off[k + 1]; i += blockDim.x) {
+            const double a = vb[i];
+            sum += a * a;
+            mx = fmax(mx, fabs(a));
+            if (!(fabs(a) <= 1.7976931348623157e308)) mx = INFINITY;
+        }
+    }
+    block_sum_max(sum, mx);
+}
+
+__global__ void k_sys_init(const double* __restrict__ v, int64_t n, const int64_t* __restrict__ sys_n_off,
+                           int32_t n_pats, int32_t maxc, const double* __restrict__ psum,
+                           const double* __restrict__ pmax,
+                           double* __restrict__ bnorm, int32_t* __restrict__ active,
                            int32_t* __restrict__ sstatus, int32_t* __restrict__ iters, double* __restrict__ resid,
                            double* __restrict__ r1, double* __restrict__ r2) {
     const int s = blockIdx.x;
-    const int b = s / n_pats, k = s % n_pats;
-    const double* v = bp + (int64_t)b * n;
-    double sum = 0.0, mx = 0.0;
-    for (int64_t i = sys_n_off[k] + threadIdx.x; i < sys_n_off[k + 1]; i += blockDim.x) sum += v[i] * v[i];
-    block_sum_max(sum, mx);
+    double sum, mx;
+    sys_combine(v, n, sys_n_off, n_pats, s, maxc, psum, pmax, sum, mx);
     if (threadIdx.x == 0) {
         bnorm[s] = sqrt(sum);
         active[s] = 1;
@@ -2919,8 +2978,10 @@ __global__ void __launch_bounds__(256) k_resid(const int64_t* __restrict__ rp, c
 }
 
 // residual test and refinement decision for one system per CTA
-__global__ void k_check(const double* __restrict__ rr, const int64_t* __restrict__ sys_n_off, int32_t n_pats,
-                        int64_t n, const double* __restrict__ bnorm, int32_t* __restrict__ active,
+__global__ void k_check(const double* __restrict__ v, int64_t n, const int64_t* __restrict__ sys_n_off,
+                        int32_t n_pats, int32_t maxc, const double* __restrict__ psum,
+                        const double* __restrict__ pmax,
+                        const double* __restrict__ bnorm, int32_t* __restrict__ active,
                         int32_t* __restrict__ sstatus, int32_t* __restrict__ iters, double* __restrict__ resid,
                         double* __restrict__ r1, double* __restrict__ r2, double* __restrict__ sigma,
                         int32_t* __restrict__ any_active, int it, int maxit, double tol, int refine,
@@ -2928,16 +2989,8 @@ __global__ void k_check(const double* __restrict__ rr, const int64_t* __restrict
     const int s = blockIdx.x;
     if (!active[s]) return;
     if (it_dev) it = *it_dev;
-    const int b = s / n_pats, k = s % n_pats;
-    const double* v = rr + (int64_t)b * n;
-    double sum = 0.0, mx = 0.0;
-    for (int64_t i = sys_n_off[k] + threadIdx.x; i < sys_n_off[k + 1]; i += blockDim.x) {
-        const double a = v[i];
-        sum += a * a;
-        mx = fmax(mx, fabs(a));
-        if (!(fabs(a) <= 1.7976931348623157e308)) mx = INFINITY;
-    }
-    block_sum_max(sum, mx);
+    double sum, mx;
+    sys_combine(v, n, sys_n_off, n_pats, s, maxc, psum, pmax, sum, mx);
     if (threadIdx.x != 0) return;
     const double rn = sqrt(sum);
     const double bn = bnorm[s];
@@ -4634,6 +4687,10 @@ int run_solve(Plan& P, const double* b, double* x, cudaStream_t s, GraphLoop* gl
     double* r1 = wsp<double>(P, P.ws.r1);
     double* r2 = wsp<double>(P, P.ws.r2);
     double* sigma = wsp<double>(P, P.ws.sigma);
+    double* psum = wsp<double>(P, P.ws.sys_psum);
+    double* pmax = wsp<double>(P, P.ws.sys_pmax);
+    // per-system norms in two passes when the plan has fewer systems than SMs
+    const bool chunked = S < 152 && P.ws.sys_maxc > 1;
     const double* K = wsp<double>(P, P.ws.K);
     const dim3 gv(cdiv(n, 256), B);
     const int refine = P.prec == SSCO_FP32_REFINE;
@@ -4646,8 +4703,13 @@ int run_solve(Plan& P, const double* b, double* x, cudaStream_t s, GraphLoop* gl
     }
     {
         Prof pr(P, s, SSCO_K_CHECK);
-        k_sys_init<<<(unsigned)S, 256, 0, s>>>(bp, P.dt.sys_n_off, P.n_pats, n, bnorm, active, sst, iters, resid, r1,
-                                               r2);
+        if (chunked) {
+            k_sys_partial<<<dim3((unsigned)P.ws.sys_maxc, (unsigned)S), 256, 0, s>>>(
+                bp, P.dt.sys_n_off, P.n_pats, n, P.ws.sys_maxc, nullptr, psum, pmax);
+            P.launches++;
+        }
+        k_sys_init<<<(unsigned)S, 256, 0, s>>>(bp, n, P.dt.sys_n_off, P.n_pats, P.ws.sys_maxc, chunked ? psum : nullptr,
+                                               pmax, bnorm, active, sst, iters, resid, r1, r2);
         pr.done(2 * nB, nB * 8);
     }
     {
@@ -4674,8 +4736,14 @@ int run_solve(Plan& P, const double* b, double* x, cudaStream_t s, GraphLoop* gl
             }
             cudaMemsetAsync(anyp, 0, 4, st);
             Prof pc(P, st, SSCO_K_CHECK);
-            k_check<<<(unsigned)S, 256, 0, st>>>(rr, P.dt.sys_n_off, P.n_pats, n, bnorm, active, sst, iters, resid, r1,
-                                                 r2, sigma, anyp, 0, P.maxit, P.tol, refine, it_dev);
+            if (chunked) {
+                k_sys_partial<<<dim3((unsigned)P.ws.sys_maxc, (unsigned)S), 256, 0, st>>>(
+                    rr, P.dt.sys_n_off, P.n_pats, n, P.ws.sys_maxc, active, psum, pmax);
+                P.launches++;
+            }
+            k_check<<<(unsigned)S, 256, 0, st>>>(rr, n, P.dt.sys_n_off, P.n_pats, P.ws.sys_maxc,
+                                                 chunked ? psum : nullptr, pmax, bnorm, active, sst, iters, resid,
+                                                 r1, r2, sigma, anyp, 0, P.maxit, P.tol, refine, it_dev);
             pc.done(0, 0);
         };
         check_step(s);
@@ -4746,8 +4814,14 @@ int run_solve(Plan& P, const double* b, double* x, cudaStream_t s, GraphLoop* gl
         cudaMemsetAsync(anyp, 0, 4, s);
         {
             Prof pr(P, s, SSCO_K_CHECK);
-            k_check<<<(unsigned)S, 256, 0, s>>>(rr, P.dt.sys_n_off, P.n_pats, n, bnorm, active, sst, iters, resid, r1,
-                                                r2, sigma, anyp, it, maxit, P.tol, refine, it_dev);
+            if (chunked) {
+                k_sys_partial<<<dim3((unsigned)P.ws.sys_maxc, (unsigned)S), 256, 0, s>>>(
+                    rr, P.dt.sys_n_off, P.n_pats, n, P.ws.sys_maxc, active, psum, pmax);
+                P.launches++;
+            }
+            k_check<<<(unsigned)S, 256, 0, s>>>(rr, n, P.dt.sys_n_off, P.n_pats, P.ws.sys_maxc,
+                                                chunked ? psum : nullptr, pmax, bnorm, active, sst, iters, resid,
+                                                r1, r2, sigma, anyp, it, maxit, P.tol, refine, it_dev);
             pr.done(2 * nB, nB * 8);
         }
         if (!refine) break;

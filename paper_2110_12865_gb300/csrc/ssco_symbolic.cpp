@@ -1132,6 +1132,14 @@ void compute_ws_layout(Plan& P) {
     w.it_ctr = take(4);
     w.dev_err = take(4);
     w.resid = take(S * 8);
+    {
+        int64_t longest = 1;
+        for (size_t k = 0; k + 1 < P.sys_n_off.size(); ++k)
+            longest = std::max<int64_t>(longest, P.sys_n_off[k + 1] - P.sys_n_off[k]);
+        w.sys_maxc = (int32_t)((longest + 2047) / 2048);  // chunks of 2048 rows (kSysChunk)
+        w.sys_psum = take(S * (size_t)w.sys_maxc * 8);
+        w.sys_pmax = take(S * (size_t)w.sys_maxc * 8);
+    }
     w.bnorm = take(S * 8);
     w.r1 = take(S * 8);
     w.r2 = take(S * 8);
