@@ -1987,12 +1987,32 @@ template <class T, bool CG>
 __device__ __forceinline__ void gather_fwd(const DevTables& t, const FrontDesc& d, const T* __restrict__ vb,
                                            const T* __restrict__ pv, T* __restrict__ v, int lane) {
     const int r = d.r, w = d.w, nc = d.nchild;
+    // lane c holds child c's descriptor (fetched in parallel, handed out by
+    // shuffles), so a child costs no dependent descriptor loads in the loop
+    long long my_pv = 0, my_map = 0;
+    int my_rc = 0;
+    if (lane < nc) {
+        const FrontDesc& cd = t.fronts[t.child_ids[d.child_off + lane]];
+        my_pv = cd.pvec_off;
+        my_map = cd.relmap_off;
+        my_rc = cd.r - cd.w;
+    }
     for (int k = lane; k < r; k += 32) v[k] = k < w ? (CG ? __ldcg(vb + d.f + k) : vb[d.f + k]) : T(0);
     for (int c = 0; c < nc; ++c) {
-        const FrontDesc& cd = t.fronts[t.child_ids[d.child_off + c]];
-        const int rc = cd.r - cd.w;
-        const int32_t* map = t.relmap + cd.relmap_off;
-        const T* src = pv + cd.pvec_off;
+        int rc;
+        int64_t map_off, pv_off;
+        if (c < 32) {
+            rc = __shfl_sync(0xffffffffu, my_rc, c);
+            map_off = __shfl_sync(0xffffffffu, my_map, c);
+            pv_off = __shfl_sync(0xffffffffu, my_pv, c);
+        } else {
+            const FrontDesc& cd = t.fronts[t.child_ids[d.child_off + c]];
+            rc = cd.r - cd.w;
+            map_off = cd.relmap_off;
+            pv_off = cd.pvec_off;
+        }
+        const int32_t* map = t.relmap + map_off;
+        const T* src = pv + pv_off;
         __syncwarp();
         for (int k0 = 0; k0 < rc; k0 += 128) {
             int m[4];
@@ -2066,14 +2086,27 @@ __global__ void __launch_bounds__(512) k_fwd(const DevTables t, const int32_t* _
     T* vb = vec + (int64_t)b * n;
     const T* Pb = panel + (int64_t)b * panel_total + d.panel_off;
     T* pv = pvec + (int64_t)b * pvec_total;
+    // the children's descriptors, fetched in parallel while the vector and
+    // the first diagonal block are staged (instead of one dependent chain
+    // per child inside the loop below)
+    __shared__ ChildRef s_ch[kChildRefs];  // upd_off holds the child's passing-vector offset here
+    if (tid < min(d.nchild, kChildRefs)) {
+        const FrontDesc& cd = t.fronts[t.child_ids[d.child_off + tid]];
+        s_ch[tid] = ChildRef{cd.pvec_off, cd.relmap_off, cd.r - cd.w, 0};
+    }
     for (int k = tid; k < r; k += nth) v[k] = k < w ? vb[d.f + k] : T(0);
     stage_diag(Ld[0], dinv[0], Pb, r, 0, min(32, w), tid, nth);
     for (int c = 0; c < d.nchild; ++c) {
         __syncthreads();
-        const FrontDesc cd = t.fronts[t.child_ids[d.child_off + c]];
-        const int rc = cd.r - cd.w;
-        const int32_t* map = t.relmap + cd.relmap_off;
-        for (int k = tid; k < rc; k += nth) v[map[k]] += pv[cd.pvec_off + k];
+        ChildRef cr;
+        if (c < kChildRefs) {
+            cr = s_ch[c];
+        } else {
+            const FrontDesc& cd = t.fronts[t.child_ids[d.child_off + c]];
+            cr = ChildRef{cd.pvec_off, cd.relmap_off, cd.r - cd.w, 0};
+        }
+        const int32_t* map = t.relmap + cr.map_off;
+        for (int k = tid; k < cr.rc; k += nth) v[map[k]] += pv[cr.upd_off + k];
     }
     __syncthreads();
     int buf = 0;
@@ -2121,8 +2154,8 @@ __global__ void __launch_bounds__(512) k_bwd(const DevTables t, const int32_t* _
                                              int32_t n_pats) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* v = reinterpret_cast<T*>(smem_raw);
-    __shared__ T Ld[32][33];
-    __shared__ T dinv[32];
+    __shared__ T Ld[2][32][33];
+    __shared__ T dinv[2][32];
     __shared__ T dots[32];
     const FrontDesc d = t.fronts[list[blockIdx.x]];
     const int b = blockIdx.y;
@@ -2133,13 +2166,16 @@ __global__ void __launch_bounds__(512) k_bwd(const DevTables t, const int32_t* _
     T* vb = vec + (int64_t)b * n;
     const T* Pb = panel + (int64_t)b * panel_total + d.panel_off;
     const int32_t* rows = t.rows + d.rows_off;
+    const int nblk = (w + 31) / 32;
+    // the last diagonal block staged with the vector; each later block is
+    // staged by warps 1.. while warp 0 runs the current block's chain
+    int buf = 0;
+    if (nblk > 0) stage_diag(Ld[0], dinv[0], Pb, r, (nblk - 1) * 32, min(32, w - (nblk - 1) * 32), tid, nth);
     for (int k = tid; k < r; k += nth) v[k] = k < w ? vb[d.f + k] : vb[rows[k]];
     __syncthreads();
-    const int nblk = (w + 31) / 32;
     for (int bi = nblk - 1; bi >= 0; --bi) {
         const int jb = bi * 32;
         const int nbk = min(32, w - jb);
-        stage_diag(Ld, dinv, Pb, r, jb, nbk, tid, nth);
         for (int c = warp; c < nbk; c += nw) {
             const T* col = Pb + (int64_t)(jb + c) * r;
             T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
@@ -2159,12 +2195,15 @@ __global__ void __launch_bounds__(512) k_bwd(const DevTables t, const int32_t* _
             const int l = tid;
             T val = l < nbk ? v[jb + l] - dots[l] : T(0);
             for (int j = nbk - 1; j >= 0; --j) {
-                const T xj = __shfl_sync(0xffffffffu, val, j) * dinv[j];
+                const T xj = __shfl_sync(0xffffffffu, val, j) * dinv[buf][j];
                 if (l == j) val = xj;
-                if (l < j) val -= Ld[j][l] * xj;
+                if (l < j) val -= Ld[buf][j][l] * xj;
             }
             if (l < nbk) v[jb + l] = val;
+        } else if (bi > 0) {
+            stage_diag(Ld[buf ^ 1], dinv[buf ^ 1], Pb, r, jb - 32, 32, tid - 32, nth - 32);
         }
+        buf ^= 1;
         __syncthreads();
     }
     for (int k = tid; k < w; k += nth) vb[d.f + k] = v[k];
