@@ -2112,6 +2112,12 @@ __global__ void __launch_bounds__(512) k_fwd(const DevTables t, const int32_t* _
     int buf = 0;
     for (int jb = 0; jb < w; jb += 32) {
         const int nbk = min(32, w - jb);
+        // this thread's first row below the block: its panel entries are
+        // loaded before the block's chain, so that the loads overlap it
+        const int i0 = jb + nbk + tid;
+        T pc[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) pc[j] = (i0 < r && j < nbk) ? Pb[(int64_t)(jb + j) * r + i0] : T(0);
         if (tid < 32) {
             const int l = tid;
             T val = l < nbk ? v[jb + l] : T(0);
@@ -2120,14 +2126,24 @@ __global__ void __launch_bounds__(512) k_fwd(const DevTables t, const int32_t* _
                 if (l == j) val = yj;
                 if (l > j) val -= Ld[buf][l][j] * yj;
             }
-            if (l < nbk) {
-                v[jb + l] = val;
-                yblk[l] = val;
-            }
+            if (l < nbk) v[jb + l] = val;
+            yblk[l] = l < nbk ? val : T(0);  // zeros past the block: pc[j] * yblk[j] below must be 0 there
+        } else if (jb + 32 < w) {
+            stage_diag(Ld[buf ^ 1], dinv[buf ^ 1], Pb, r, jb + 32, min(32, w - jb - 32), tid - 32, nth - 32);
         }
         __syncthreads();
-        if (jb + 32 < w) stage_diag(Ld[buf ^ 1], dinv[buf ^ 1], Pb, r, jb + 32, min(32, w - jb - 32), tid, nth);
-        for (int i = jb + nbk + tid; i < r; i += nth) {
+        if (i0 < r) {
+            T acc[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc[u] = T(0);
+#pragma unroll
+            for (int j = 0; j < 32; j += 8) {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) acc[u] += pc[j + u] * yblk[j + u];
+            }
+            v[i0] -= ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+        }
+        for (int i = i0 + nth; i < r; i += nth) {
             const T* col = Pb + (int64_t)jb * r + i;
             T acc[8];
 #pragma unroll
