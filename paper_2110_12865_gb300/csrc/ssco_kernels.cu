@@ -2192,19 +2192,35 @@ __global__ void __launch_bounds__(512) k_bwd(const DevTables t, const int32_t* _
     for (int bi = nblk - 1; bi >= 0; --bi) {
         const int jb = bi * 32;
         const int nbk = min(32, w - jb);
-        for (int c = warp; c < nbk; c += nw) {
+        // two columns per pass (c and c + nw): eight loads in flight per lane
+        for (int c = warp; c < nbk; c += 2 * nw) {
+            const int c2 = c + nw;
             const T* col = Pb + (int64_t)(jb + c) * r;
+            const T* col2 = Pb + (int64_t)(jb + (c2 < nbk ? c2 : c)) * r;
             T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+            T t0 = T(0), t1 = T(0), t2 = T(0), t3 = T(0);
             int i = jb + nbk + lane;
             for (; i + 96 < r; i += 128) {
-                s0 += col[i] * v[i];
-                s1 += col[i + 32] * v[i + 32];
-                s2 += col[i + 64] * v[i + 64];
-                s3 += col[i + 96] * v[i + 96];
+                const T v0 = v[i], v1 = v[i + 32], v2 = v[i + 64], v3 = v[i + 96];
+                s0 += col[i] * v0;
+                s1 += col[i + 32] * v1;
+                s2 += col[i + 64] * v2;
+                s3 += col[i + 96] * v3;
+                t0 += col2[i] * v0;
+                t1 += col2[i + 32] * v1;
+                t2 += col2[i + 64] * v2;
+                t3 += col2[i + 96] * v3;
             }
-            for (; i < r; i += 32) s0 += col[i] * v[i];
-            T s = warp_sum((s0 + s1) + (s2 + s3));
-            if (lane == 0) dots[c] = s;
+            for (; i < r; i += 32) {
+                s0 += col[i] * v[i];
+                t0 += col2[i] * v[i];
+            }
+            const T s = warp_sum((s0 + s1) + (s2 + s3));
+            const T s2v = warp_sum((t0 + t1) + (t2 + t3));
+            if (lane == 0) {
+                dots[c] = s;
+                if (c2 < nbk) dots[c2] = s2v;
+            }
         }
         __syncthreads();
         if (tid < 32) {
