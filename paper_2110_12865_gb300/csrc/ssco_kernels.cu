@@ -2096,7 +2096,29 @@ __global__ void __launch_bounds__(512) k_fwd(const DevTables t, const int32_t* _
     }
     for (int k = tid; k < r; k += nth) v[k] = k < w ? vb[d.f + k] : T(0);
     stage_diag(Ld[0], dinv[0], Pb, r, 0, min(32, w), tid, nth);
-    for (int c = 0; c < d.nchild; ++c) {
+    __syncthreads();
+    // children's passing vectors: each thread's entry of the first four
+    // children loaded together (one round trip), then added child by child
+    const int nc4 = min(d.nchild, 4);
+    int cm[4];
+    T cx[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        cm[c] = -1;
+        cx[c] = T(0);
+        if (c < nc4 && tid < s_ch[c].rc) {
+            cm[c] = t.relmap[s_ch[c].map_off + tid];
+            cx[c] = pv[s_ch[c].upd_off + tid];
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        if (c >= nc4) break;
+        if (c > 0) __syncthreads();  // two children may reach the same row
+        if (cm[c] >= 0) v[cm[c]] += cx[c];
+        for (int k = tid + nth; k < s_ch[c].rc; k += nth) v[t.relmap[s_ch[c].map_off + k]] += pv[s_ch[c].upd_off + k];
+    }
+    for (int c = 4; c < d.nchild; ++c) {
         __syncthreads();
         ChildRef cr;
         if (c < kChildRefs) {
