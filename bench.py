@@ -61,9 +61,10 @@ def parse():
     ap.add_argument("--vec2", type=int, default=None,
                     help="vec2_max_cls plan option of the FP32 plans instead of the autotuner's choice "
                          "(with --no-autotune and --flow: reproduces a tuned configuration for profiling)")
-    ap.add_argument("--flow", type=int, default=None,
-                    help="ssco_set_flow value for every plan instead of the autotuner's choice (with "
-                         "--no-autotune: reproduces a tuned launch configuration for profiling)")
+    ap.add_argument("--flow", default=None,
+                    help="ssco_set_flow value of the plans instead of the autotuner's choice: one value for "
+                         "every plan or a comma list, one per plan (with --no-autotune: reproduces a tuned "
+                         "launch configuration for profiling)")
     a = ap.parse_args()
     if a.steps is None:
         a.steps = {"elast24": 20, "elast48": 5, "lll": 2000}.get(a.workload, 100)
@@ -317,8 +318,12 @@ def run_ours(args, rank, world, local_rank):
                 ms, knobs = pl.autotune(*dev_in[-1], reps=3)
                 tuned.append(knobs)
             if args.flow is not None or args.eager:
-                pl.set_flow((args.flow if args.flow is not None else pl.info["tune_flow"] & 15) |
-                            (16 if args.eager else 0))
+                if args.flow is not None:
+                    fl = [int(f) for f in str(args.flow).split(",")]
+                    base = fl[min(len(plans), len(fl) - 1)]
+                else:
+                    base = pl.info["tune_flow"] & 15
+                pl.set_flow(base | (16 if args.eager else 0))
             host_in.append((torch.tensor(v).pin_memory(), torch.tensor(s).pin_memory(), torch.tensor(b).pin_memory(),
                             torch.empty(b.shape, dtype=torch.float64).pin_memory()))
             plans.append(pl)

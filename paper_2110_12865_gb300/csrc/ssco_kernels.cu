@@ -831,6 +831,23 @@ __device__ __forceinline__ int tiny_chol_rows_unrolled(T (*F)[33], int lane, int
     return bad;
 }
 
+// A child's update matrix (rc <= RC rows, lower triangle, column-major)
+// added into the front tile through its relative map: lane i holds row i;
+// its entries are loaded together (the bound is fixed, so the loop unrolls)
+// before they are added.
+template <class T, int RC>
+__device__ __forceinline__ void tiny_child_add(T (*F)[33], const int32_t* map, const T* __restrict__ S, int rc,
+                                               int lane) {
+    if (lane >= rc) return;
+    T sv[RC];
+#pragma unroll
+    for (int kk = 0; kk < RC; ++kk) sv[kk] = kk <= lane ? S[lane + kk * rc] : T(0);
+    const int mi = map[lane];
+#pragma unroll
+    for (int kk = 0; kk < RC; ++kk)
+        if (kk <= lane) F[mi][map[kk]] += sv[kk];
+}
+
 template <class T>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2)
     k_tiny_factor(const DevTables t, int32_t n_tiny, int32_t B, int32_t prog_max, int32_t k_max,
@@ -868,7 +885,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2)
             const int rc = crec[0] - crec[1];
             const int32_t* map = prog + crec[7];
             const T* S = Ub + prog_i64(crec, 12);
-            if (lane < rc) {
+            if (rc <= 8)
+                tiny_child_add<T, 8>(F, map, S, rc, lane);
+            else if (rc <= 16)
+                tiny_child_add<T, 16>(F, map, S, rc, lane);
+            else if (lane < rc) {
                 const int mi = map[lane];
                 for (int kk = 0; kk <= lane; ++kk) F[mi][map[kk]] += S[lane + kk * rc];
             }
