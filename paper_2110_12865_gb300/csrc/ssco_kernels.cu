@@ -955,8 +955,10 @@ __device__ __forceinline__ T tiny_bwd_chain(const T* __restrict__ Pf, int lane, 
     return v;
 }
 
+// FP32 tiny solves: at most 40 registers, six CTAs (48 warps) per SM; the
+// few values kept in local memory cost less than the warps gained.
 template <class T>
-__global__ void __launch_bounds__(256) k_tiny_fwd(const DevTables t, int32_t n_tiny, int32_t B, int32_t prog_max,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 1) k_tiny_fwd(const DevTables t, int32_t n_tiny, int32_t B, int32_t prog_max,
                                                   const T* __restrict__ panel, int64_t panel_total,
                                                   T* __restrict__ vec, int64_t n, T* __restrict__ pvec,
                                                   int64_t pvec_total, const int32_t* __restrict__ active,
@@ -1002,7 +1004,7 @@ __global__ void __launch_bounds__(256) k_tiny_fwd(const DevTables t, int32_t n_t
 }
 
 template <class T>
-__global__ void __launch_bounds__(256) k_tiny_bwd(const DevTables t, int32_t n_tiny, int32_t B, int32_t prog_max,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 1) k_tiny_bwd(const DevTables t, int32_t n_tiny, int32_t B, int32_t prog_max,
                                                   const T* __restrict__ panel, int64_t panel_total,
                                                   T* __restrict__ vec, int64_t n, const int32_t* __restrict__ active,
                                                   int32_t n_pats, int32_t share) {
@@ -2403,8 +2405,10 @@ __global__ void __launch_bounds__(256) k_fwd_warp(const DevTables t, const int32
     for (int k = lane; k < r - w; k += 32) pv[d.pvec_off + k] = v[w + k];
 }
 
+// FP32: at most 64 registers, four CTAs (32 warps) per SM; the warps of a
+// level hide each other's load latency, and the dot products need no more.
 template <class T>
-__global__ void __launch_bounds__(256) k_bwd_warp(const DevTables t, const int32_t* __restrict__ list,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k_bwd_warp(const DevTables t, const int32_t* __restrict__ list,
                                                   int32_t count, int32_t B, int32_t rmax,
                                                   const T* __restrict__ panel, int64_t panel_total,
                                                   T* __restrict__ vec, int64_t n, const int32_t* __restrict__ active,
@@ -3878,9 +3882,8 @@ int run_numeric(Plan& P, const void* vals, int32_t vdt, const double* shift, cud
                 k_front_vec<T, 2><<<dim3(ll.count, (B + 1) / 2), dim3(32, nw), smem * 2, st>>>(
                     P.dt, list, B, K, P.nnzK, panel, P.panel_total, upd, P.upd_total, bad, P.n_pats);
             else
-            k_front_small<T><<<dim3(ll.count, B), dim3(32, nw), smem, st>>>(P.dt, list, K, P.nnzK, panel,
-                                                                           P.panel_total, upd, P.upd_total, bad,
-                                                                           P.n_pats);
+                k_front_small<T><<<dim3(ll.count, B), dim3(32, nw), smem, st>>>(
+                    P.dt, list, K, P.nnzK, panel, P.panel_total, upd, P.upd_total, bad, P.n_pats);
             pr.end();
             if (pr.ev >= 0) {
                 Work w = work_front_small(P, ll);
