@@ -58,9 +58,10 @@ def parse():
     ap.add_argument("--eager", action="store_true",
                     help="every kernel launched eagerly, no CUDA graphs (for profilers that do not list "
                          "kernels inside graphs; not the timed configuration)")
-    ap.add_argument("--vec2", type=int, default=None,
-                    help="vec2_max_cls plan option of the FP32 plans instead of the autotuner's choice "
-                         "(with --no-autotune and --flow: reproduces a tuned configuration for profiling)")
+    ap.add_argument("--vec2", default=None,
+                    help="vec2_max_cls plan option of the FP32 plans instead of the autotuner's choice: one "
+                         "value for every plan or a comma list, one per plan (with --no-autotune and --flow: "
+                         "reproduces a tuned configuration for profiling)")
     ap.add_argument("--flow", default=None,
                     help="ssco_set_flow value of the plans instead of the autotuner's choice: one value for "
                          "every plan or a comma list, one per plan (with --no-autotune: reproduces a tuned "
@@ -126,22 +127,24 @@ def stacked_inputs(item, B):
     return np.ascontiguousarray(vals), np.ascontiguousarray(shift), np.ascontiguousarray(b)
 
 
-def shared_plans(work, precision, rank, world, dist, S, **opts):
+def shared_plans(work, precision, rank, world, dist, S, opts=None):
     """The plans of a step, analyzed once per job: with several ranks, rank 0
     runs the host symbolic phase and writes each plan file (ssco_plan_save),
     the other ranks load it (ssco_plan_load) after a barrier.  Every rank
     solves the same patterns for its own value sets, so the plans are equal;
-    nothing of the data path is exchanged."""
+    nothing of the data path is exchanged.  opts: plan options, one dict per
+    plan (None: the defaults)."""
+    opts = opts or [{} for _ in work]
     if world == 1 or dist is None:
-        return [S.Plan(item, precision=precision, batch=Bt, **opts) for item, Bt in work]
+        return [S.Plan(item, precision=precision, batch=Bt, **o) for (item, Bt), o in zip(work, opts)]
     import tempfile
     box = [tempfile.mkdtemp(prefix="ssco_plans_") if rank == 0 else None]
     dist.broadcast_object_list(box, src=0)
     paths = [os.path.join(box[0], f"plan{k}_p{precision}.bin") for k in range(len(work))]
     plans = []
     if rank == 0:
-        for (item, Bt), path in zip(work, paths):
-            pl = S.Plan(item, precision=precision, batch=Bt, **opts)
+        for (item, Bt), path, o in zip(work, paths, opts):
+            pl = S.Plan(item, precision=precision, batch=Bt, **o)
             pl.save(path)
             plans.append(pl)
     dist.barrier()
@@ -307,8 +310,11 @@ def run_ours(args, rank, world, local_rank):
 
     def setup(precision):
         plans, dev_in, host_in = [], [], []
-        opts = {"vec2_max_cls": args.vec2} if args.vec2 is not None and precision == S.FP32_REFINE else {}
-        for (item, Bt), pl in zip(work, shared_plans(work, precision, rank, world, dist, S, **opts)):
+        opts = None
+        if args.vec2 is not None and precision == S.FP32_REFINE:
+            v2 = [int(x) for x in str(args.vec2).split(",")]
+            opts = [{"vec2_max_cls": v2[min(k, len(v2) - 1)]} for k in range(len(work))]
+        for (item, Bt), pl in zip(work, shared_plans(work, precision, rank, world, dist, S, opts)):
             pl.bind(dev)
             v, s, b = stacked_inputs(item, Bt)
             dev_in.append((torch.tensor(v, device=dev), torch.tensor(s, device=dev), torch.tensor(b, device=dev),
@@ -397,7 +403,8 @@ def run_ours(args, rank, world, local_rank):
         # the plans' dataflow choices decided together, on the step's graph
         ms_many, flows = S.autotune_many(plans32, [t[0] for t in dev32], [t[1] for t in dev32],
                                          [t[2] for t in dev32], [t[3] for t in dev32], reps=5)
-        tuned_many = {"step_ms": ms_many, "tune_flow": flows}
+        tuned_many = {"step_ms": ms_many, "tune_flow": flows,
+                      "tune_vec2_max_cls": [int(pl.info["tune_vec2_max_cls"]) for pl in plans32]}
     sampler = ClockSampler(local_rank)
     ms, launches, wall, clocks = timed(plans32, dev32, args.steps, args.warmup, sampler)
     ok32, res32, its32 = status_summary(plans32)

@@ -493,8 +493,11 @@ __global__ void __launch_bounds__(256) k_front_warp(const DevTables t, const int
 // interleaved ([packed index][V]) so that one 16-byte shared-memory access
 // serves all V and the index arithmetic is paid once per V fronts (the
 // members of a group share one template expression, Sec. 4.8).
+// Register budgets: V = 4 at 64 (four CTAs of 256 threads per SM), V = 2 at
+// 85 (three), which holds its state without local memory; the two-set
+// classes (128 and 160 rows) fit two or three CTAs per SM in shared memory.
 template <class T, int V>
-__global__ void __launch_bounds__(256) k_front_vec(const DevTables t, const int32_t* __restrict__ list, int32_t B,
+__global__ void __launch_bounds__(256, V == 2 ? 3 : 4) k_front_vec(const DevTables t, const int32_t* __restrict__ list, int32_t B,
                                                    const double* __restrict__ K, int64_t nnzK,
                                                    T* __restrict__ panel, int64_t panel_total,
                                                    T* __restrict__ upd, int64_t upd_total,

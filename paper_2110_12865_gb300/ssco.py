@@ -526,8 +526,10 @@ def graph_run_many(plans, vals, shifts, bs, xs, stream=None):
 
 
 def autotune_many(plans, vals, shifts, bs, xs, reps=3, stream=None):
-    """ssco_autotune_many: the plans' dataflow choices tuned on their
-    multi-plan graph.  Returns (best step ms, tune_flow of every plan)."""
+    """ssco_autotune_many: the plans' dataflow choices (ssco_set_flow bits
+    0..3, and the two-value-set classes of FP32 plans) tuned on their
+    multi-plan graph.  Refreshes every plan's ``info`` (``tune_flow``,
+    ``tune_vec2_max_cls``).  Returns (best step ms, tune_flow of every plan)."""
     L = load_library()
     n = len(plans)
     arr = lambda ts: (C.c_void_p * n)(*[t.data_ptr() for t in ts])
