@@ -349,6 +349,19 @@ def run_ours(args, rank, world, local_rank):
 
     launches_per_step = {}
 
+    def count_step(plans, dev_in):
+        """Kernels one step runs, counted on an eager step with the FP32
+        solve graphs off (flow bit 4): a captured graph counts its refinement
+        loop's body once, whatever number of corrections the device loop
+        runs.  The same inputs take the same corrections in every step."""
+        flows = [int(pl.info["tune_flow"]) for pl in plans]
+        for pl, f in zip(plans, flows):
+            pl.set_flow(f | 16)
+        n = eager_step(plans, dev_in)
+        for pl, f in zip(plans, flows):
+            pl.set_flow(f)
+        return n
+
     def step(plans, dev_in):
         if args.eager:
             return eager_step(plans, dev_in)
@@ -360,7 +373,7 @@ def run_ours(args, rank, world, local_rank):
         return launches_per_step.get(id(plans), 0)
 
     def timed(plans, dev_in, K, W, sampler=None):
-        launches_per_step[id(plans)] = eager_step(plans, dev_in)
+        launches_per_step[id(plans)] = count_step(plans, dev_in)
         for _ in range(W):
             step(plans, dev_in)
         torch.cuda.synchronize()
