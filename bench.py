@@ -415,7 +415,7 @@ def run_ours(args, rank, world, local_rank):
     if args.autotune and len(plans32) > 1 and args.workload != "elast48":
         # the plans' dataflow choices decided together, on the step's graph
         ms_many, flows = S.autotune_many(plans32, [t[0] for t in dev32], [t[1] for t in dev32],
-                                         [t[2] for t in dev32], [t[3] for t in dev32], reps=5)
+                                         [t[2] for t in dev32], [t[3] for t in dev32], reps=9)
         tuned_many = {"step_ms": ms_many, "tune_flow": flows,
                       "tune_vec2_max_cls": [int(pl.info["tune_vec2_max_cls"]) for pl in plans32]}
     sampler = ClockSampler(local_rank)

@@ -367,10 +367,12 @@ ssco_status ssco_graph_run_many(const ssco_plan* plans, int32_t n_plans, const v
                                 double* const* x, void* stream);
 
 /* ssco_autotune for the plans of one ssco_graph_run_many step: coordinate
- * descent over each plan's dataflow choices (the bits of ssco_set_flow 0..3
- * and the two-value-set classes of FP32 plans), every candidate timed on
- * the multi-plan graph itself (median of `reps` replays after a warm-up;
- * kept when 1 % faster).  A plan's best choice alone can differ from its
+ * descent (two sweeps over the plans) over each plan's dataflow choices
+ * (the bits of ssco_set_flow 0..3 and the two-value-set classes of FP32
+ * plans), every candidate timed on the multi-plan graph itself (median of
+ * `reps` replays after a warm-up; kept when 0.5 % faster than the current
+ * setting, re-timed beside each knob's candidates).  A plan's best choice
+ * alone can differ from its
  * best choice beside the others, whose work it overlaps with (Sec. 4.3's
  * grouping decided across the patterns of a step).  Arguments as for
  * ssco_graph_run_many; run ssco_autotune on each plan first for its other

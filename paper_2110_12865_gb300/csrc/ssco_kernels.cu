@@ -5412,8 +5412,10 @@ int autotune_many(Plan* const* plans, int32_t n, const void* const* vals, const 
     };
     double best = 0;
     e = measure(&best);
-    for (int32_t i = 0; i < n && !e; ++i) {
-        Plan& P = *plans[i];
+    // two sweeps: a plan's knob can pay off only after another plan's
+    // knob has changed (their work overlaps in the graph)
+    for (int32_t i = 0; i < 2 * n && !e; ++i) {
+        Plan& P = *plans[i % n];
         struct Knob {
             int32_t* field;
             std::vector<int32_t> cand;
@@ -5427,20 +5429,26 @@ int autotune_many(Plan* const* plans, int32_t n, const void* const* vals, const 
             if (e) break;
             const int32_t keep = *k.field;
             int32_t arg = keep;
+            // the current setting re-timed beside its candidates, so that a
+            // lucky earlier timing does not hide a real gain of ~1 %
+            double base = 0;
+            if (k.cand.size() > 1) e = measure(&base);
+            double arg_ms = base;
             for (int32_t c : k.cand) {
-                if (c == keep) continue;
+                if (e || c == keep) continue;
                 *k.field = c;
                 graph_release(P);
                 double ms = 0;
                 e = measure(&ms);
                 if (e) break;
-                if (ms < best * 0.99) {
-                    best = ms;
+                if (ms < base * 0.995 && ms < arg_ms) {
+                    arg_ms = ms;
                     arg = c;
                 }
             }
             *k.field = arg;
             graph_release(P);
+            if (k.cand.size() > 1) best = arg_ms;
         }
     }
     cudaEventDestroy(e0);
