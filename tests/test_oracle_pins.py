@@ -385,6 +385,50 @@ def test_gradient_central_differences(shift):
         assert abs(bbar[i] - fd_b) <= 1e-5 * max(abs(fd_b), 1e-3 * np.abs(bbar).max()) + floor
 
 
+def test_gradient_five_point_differences_ill_conditioned():
+    """Shift 1e-2 (kappa ~ 1e3): the fourth-order central difference
+    (8 (f(h) - f(-h)) - (f(2h) - f(-2h))) / (12 h) has a truncation error of
+    order h^4 and a rounding floor of order kappa u / h.  At h = 1e-3 for the
+    weights and right-hand side (entries of order 1) and h = 1e-3 * shift for
+    the shift (which sets the smallest eigenvalue), both are far below the
+    tolerances (2e-6 and 1e-8 relative).  So the adjoint's dloss/dw,
+    dloss/dshift and dloss/db are pinned there without the floor that the
+    two-point difference needs."""
+    p = P.grid_problem(8, 8, cfg=4, shift=1e-2)
+    _, vbar, sbar, bbar = loss_and_grad(p)
+    rng = np.random.default_rng(5)
+    h = 1e-3
+    w0, s0, b0 = p.vals[0].astype(np.float64), float(p.shift[0]), p.b[0].copy()
+
+    def five_point(solve_at, h=h):
+        return (8.0 * fd_diff(p, solve_at(h), solve_at(-h)) - fd_diff(p, solve_at(2 * h), solve_at(-2 * h))) / (12 * h)
+
+    def bump_w(e):
+        def at(t):
+            w = w0.copy()
+            w[e] += t
+            return fd_loss(p, w, s0, b0)
+        return at
+
+    def bump_b(i):
+        def at(t):
+            b = b0.copy()
+            b[i] += t
+            return fd_loss(p, w0, s0, b)
+        return at
+
+    scale_w = np.abs(vbar).max()
+    for e in rng.choice(p.m, 24, replace=False):
+        g = five_point(bump_w(e))
+        assert abs(vbar[e] - g) <= 2e-6 * max(abs(g), 1e-3 * scale_w)
+    g_s = five_point(lambda t: fd_loss(p, w0, s0 + t, b0), h=1e-3 * s0)
+    assert abs(sbar - g_s) <= 1e-8 * abs(g_s)
+    scale_b = np.abs(bbar).max()
+    for i in rng.choice(p.n, 8, replace=False):
+        g = five_point(bump_b(i))
+        assert abs(bbar[i] - g) <= 2e-6 * max(abs(g), 1e-3 * scale_b)
+
+
 def test_gradient_elasticity_central_differences():
     p = P.elasticity_problem(2, cfg=2)
     rng = np.random.default_rng(9)
