@@ -497,11 +497,10 @@ __global__ void __launch_bounds__(256) k_front_warp(const DevTables t, const int
 // 85 (three), which holds its state without local memory; the two-set
 // classes (128 and 160 rows) fit two or three CTAs per SM in shared memory.
 template <class T, int V>
-__global__ void __launch_bounds__(256, V == 2 ? 3 : 4) k_front_vec(const DevTables t, const int32_t* __restrict__ list, int32_t B,
-                                                   const double* __restrict__ K, int64_t nnzK,
-                                                   T* __restrict__ panel, int64_t panel_total,
-                                                   T* __restrict__ upd, int64_t upd_total,
-                                                   int32_t* __restrict__ bad_col, int32_t n_pats) {
+__global__ void __launch_bounds__(256, V == 2 ? 3 : 4)
+    k_front_vec(const DevTables t, const int32_t* __restrict__ list, int32_t B, const double* __restrict__ K,
+                int64_t nnzK, T* __restrict__ panel, int64_t panel_total, T* __restrict__ upd, int64_t upd_total,
+                int32_t* __restrict__ bad_col, int32_t n_pats) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* F = reinterpret_cast<T*>(smem_raw);
     const FrontDesc d = t.fronts[list[blockIdx.x]];
@@ -961,11 +960,10 @@ __device__ __forceinline__ T tiny_bwd_chain(const T* __restrict__ Pf, int lane, 
 // FP32 tiny solves: at most 40 registers, six CTAs (48 warps) per SM; the
 // few values kept in local memory cost less than the warps gained.
 template <class T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 1) k_tiny_fwd(const DevTables t, int32_t n_tiny, int32_t B, int32_t prog_max,
-                                                  const T* __restrict__ panel, int64_t panel_total,
-                                                  T* __restrict__ vec, int64_t n, T* __restrict__ pvec,
-                                                  int64_t pvec_total, const int32_t* __restrict__ active,
-                                                  int32_t n_pats, int32_t share) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 1)
+    k_tiny_fwd(const DevTables t, int32_t n_tiny, int32_t B, int32_t prog_max, const T* __restrict__ panel,
+               int64_t panel_total, T* __restrict__ vec, int64_t n, T* __restrict__ pvec, int64_t pvec_total,
+               const int32_t* __restrict__ active, int32_t n_pats, int32_t share) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t item = (int64_t)blockIdx.x * kTinyWarps + wib;
@@ -1007,10 +1005,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 1) k_tiny_fwd(const 
 }
 
 template <class T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 1) k_tiny_bwd(const DevTables t, int32_t n_tiny, int32_t B, int32_t prog_max,
-                                                  const T* __restrict__ panel, int64_t panel_total,
-                                                  T* __restrict__ vec, int64_t n, const int32_t* __restrict__ active,
-                                                  int32_t n_pats, int32_t share) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 1)
+    k_tiny_bwd(const DevTables t, int32_t n_tiny, int32_t B, int32_t prog_max, const T* __restrict__ panel,
+               int64_t panel_total, T* __restrict__ vec, int64_t n, const int32_t* __restrict__ active,
+               int32_t n_pats, int32_t share) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t item = (int64_t)blockIdx.x * kTinyWarps + wib;
@@ -2353,19 +2351,33 @@ __device__ __forceinline__ T diag_bwd_any(const T* __restrict__ Pb, int r, int j
     return diag_bwd<T, 32>(Pb, r, jb, nbk, lane, val);
 }
 
+// The same, for blocks known to be at most NBMAX columns wide (16 or 32):
+// a kernel instantiated for NBMAX = 16 holds no 32-entry diagonal row, and
+// so fits a smaller register budget.
+template <class T, int NBMAX>
+__device__ __forceinline__ T diag_fwd_upto(const T* __restrict__ Pb, int r, int jb, int nbk, int lane, T val) {
+    if (NBMAX <= 16)
+        return nbk <= 8 ? diag_fwd<T, 8>(Pb, r, jb, nbk, lane, val) : diag_fwd<T, 16>(Pb, r, jb, nbk, lane, val);
+    return diag_fwd_any<T>(Pb, r, jb, nbk, lane, val);
+}
+template <class T, int NBMAX>
+__device__ __forceinline__ T diag_bwd_upto(const T* __restrict__ Pb, int r, int jb, int nbk, int lane, T val) {
+    if (NBMAX <= 16)
+        return nbk <= 8 ? diag_bwd<T, 8>(Pb, r, jb, nbk, lane, val) : diag_bwd<T, 16>(Pb, r, jb, nbk, lane, val);
+    return diag_bwd_any<T>(Pb, r, jb, nbk, lane, val);
+}
+
 // Warp-per-(front, instance) variants of the two solves for levels that
 // supply many items (a batch of value sets): eight independent warps per
 // CTA, no block barriers; the 32x32 diagonal block is held in registers
 // (forward: lane = row, backward: lane = column) and the front's vector in
 // shared memory.  Items are front-major, so the 8 warps of a CTA read the
 // same index tables.
-template <class T>
-__global__ void __launch_bounds__(256) k_fwd_warp(const DevTables t, const int32_t* __restrict__ list,
-                                                  int32_t count, int32_t B, int32_t rmax,
-                                                  const T* __restrict__ panel, int64_t panel_total,
-                                                  T* __restrict__ vec, int64_t n, T* __restrict__ pvec,
-                                                  int64_t pvec_total, const int32_t* __restrict__ active,
-                                                  int32_t n_pats) {
+template <class T, int NBMAX>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? (NBMAX <= 16 ? 6 : 4) : 1)
+    k_fwd_warp(const DevTables t, const int32_t* __restrict__ list, int32_t count, int32_t B, int32_t rmax,
+               const T* __restrict__ panel, int64_t panel_total, T* __restrict__ vec, int64_t n,
+               T* __restrict__ pvec, int64_t pvec_total, const int32_t* __restrict__ active, int32_t n_pats) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t item = (int64_t)blockIdx.x * 8 + wib;
@@ -2383,7 +2395,7 @@ __global__ void __launch_bounds__(256) k_fwd_warp(const DevTables t, const int32
     for (int jb = 0; jb < w; jb += 32) {
         const int nbk = min(32, w - jb);
         T val = lane < nbk ? v[jb + lane] : T(0);
-        val = diag_fwd_any<T>(Pb, r, jb, nbk, lane, val);
+        val = diag_fwd_upto<T, NBMAX>(Pb, r, jb, nbk, lane, val);
         if (lane < nbk) v[jb + lane] = val;
         __syncwarp();
         for (int i0 = jb + nbk; i0 < r; i0 += 32) {
@@ -2410,12 +2422,13 @@ __global__ void __launch_bounds__(256) k_fwd_warp(const DevTables t, const int32
 
 // FP32: at most 64 registers, four CTAs (32 warps) per SM; the warps of a
 // level hide each other's load latency, and the dot products need no more.
-template <class T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k_bwd_warp(const DevTables t, const int32_t* __restrict__ list,
-                                                  int32_t count, int32_t B, int32_t rmax,
-                                                  const T* __restrict__ panel, int64_t panel_total,
-                                                  T* __restrict__ vec, int64_t n, const int32_t* __restrict__ active,
-                                                  int32_t n_pats) {
+// Levels whose fronts are all at most 16 columns wide run the NBMAX = 16
+// instantiations of both warp solves at 40 registers (six CTAs per SM).
+template <class T, int NBMAX>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? (NBMAX <= 16 ? 6 : 4) : 1)
+    k_bwd_warp(const DevTables t, const int32_t* __restrict__ list, int32_t count, int32_t B, int32_t rmax,
+               const T* __restrict__ panel, int64_t panel_total, T* __restrict__ vec, int64_t n,
+               const int32_t* __restrict__ active, int32_t n_pats) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t item = (int64_t)blockIdx.x * 8 + wib;
@@ -2449,7 +2462,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k_bwd_warp(const 
             dot += d1 + d2 + d3;
         }
         T val = lane < nbk ? v[jb + lane] - dot : T(0);
-        val = diag_bwd_any<T>(Pb, r, jb, nbk, lane, val);
+        val = diag_bwd_upto<T, NBMAX>(Pb, r, jb, nbk, lane, val);
         if (lane < nbk) v[jb + lane] = val;
         __syncwarp();
     }
@@ -4699,12 +4712,13 @@ void run_trisolve(Plan& P, const int32_t* active, cudaStream_t s) {
         const size_t smem = (size_t)ll.rmax * sizeof(T);
         if (use_warp_solve(P, ll, B)) {
             const int64_t items = (int64_t)ll.count * B;
-            k_fwd_warp<T><<<cdiv(items, 8), 256, 8 * smem, s>>>(P.dt, P.dt.flow_rest + ll.list_off, ll.count, B,
-                                                                ll.rmax, panel, P.panel_total, vecT, P.n, pvec,
-                                                                P.pvec_total, active, P.n_pats);
+            auto kf = ll.wmax <= 16 ? k_fwd_warp<T, 16> : k_fwd_warp<T, 32>;
+            kf<<<cdiv(items, 8), 256, 8 * smem, s>>>(P.dt, P.dt.flow_rest + ll.list_off, ll.count, B, ll.rmax, panel,
+                                                     P.panel_total, vecT, P.n, pvec, P.pvec_total, active, P.n_pats);
         } else
-        k_fwd<T><<<dim3(ll.count, B), solve_threads(P, ll), smem, s>>>(P.dt, P.dt.flow_rest + ll.list_off, panel, P.panel_total,
-                                                        vecT, P.n, pvec, P.pvec_total, active, P.n_pats);
+            k_fwd<T><<<dim3(ll.count, B), solve_threads(P, ll), smem, s>>>(
+                P.dt, P.dt.flow_rest + ll.list_off, panel, P.panel_total, vecT, P.n, pvec, P.pvec_total, active,
+                P.n_pats);
         pr.end();
         if (pr.ev >= 0) {
             Work w = work_solve(P, ll);
@@ -4740,12 +4754,12 @@ void run_trisolve(Plan& P, const int32_t* active, cudaStream_t s) {
         const size_t smem = (size_t)ll.rmax * sizeof(T);
         if (use_warp_solve(P, ll, B)) {
             const int64_t items = (int64_t)ll.count * B;
-            k_bwd_warp<T><<<cdiv(items, 8), 256, 8 * smem, s>>>(P.dt, P.dt.flow_rest + ll.list_off, ll.count, B,
-                                                                ll.rmax, panel, P.panel_total, vecT, P.n, active,
-                                                                P.n_pats);
+            auto kb = ll.wmax <= 16 ? k_bwd_warp<T, 16> : k_bwd_warp<T, 32>;
+            kb<<<cdiv(items, 8), 256, 8 * smem, s>>>(P.dt, P.dt.flow_rest + ll.list_off, ll.count, B, ll.rmax, panel,
+                                                     P.panel_total, vecT, P.n, active, P.n_pats);
         } else
-        k_bwd<T><<<dim3(ll.count, B), solve_threads(P, ll), smem, s>>>(P.dt, P.dt.flow_rest + ll.list_off, panel, P.panel_total,
-                                                        vecT, P.n, active, P.n_pats);
+            k_bwd<T><<<dim3(ll.count, B), solve_threads(P, ll), smem, s>>>(
+                P.dt, P.dt.flow_rest + ll.list_off, panel, P.panel_total, vecT, P.n, active, P.n_pats);
         pr.end();
         if (pr.ev >= 0) {
             Work w = work_solve(P, ll);
@@ -5089,8 +5103,10 @@ int set_attr_T() {
     if (!e) e = allow_dynamic_smem(k_tiny_factor<T>);
     if (!e) e = allow_dynamic_smem(k_tiny_fwd<T>);
     if (!e) e = allow_dynamic_smem(k_tiny_bwd<T>);
-    if (!e) e = allow_dynamic_smem(k_fwd_warp<T>);
-    if (!e) e = allow_dynamic_smem(k_bwd_warp<T>);
+    if (!e) e = allow_dynamic_smem(k_fwd_warp<T, 16>);
+    if (!e) e = allow_dynamic_smem(k_fwd_warp<T, 32>);
+    if (!e) e = allow_dynamic_smem(k_bwd_warp<T, 16>);
+    if (!e) e = allow_dynamic_smem(k_bwd_warp<T, 32>);
     if (!e) e = allow_dynamic_smem(k_fwd<T>);
     if (!e) e = allow_dynamic_smem(k_bwd<T>);
     if (!e) e = allow_dynamic_smem(k_bsplit_init<T>);
