@@ -660,7 +660,11 @@ const char* ssco_status_string(ssco_status s);
 /* Versioned binary file of the host plan (no device state): magic, version,
  * the plan's tables, then a 64-bit FNV-1a digest of everything before it.
  * Load returns SSCO_ERR_INVALID_ARG for another version, a truncated file,
- * trailing bytes or a digest mismatch; the caller owns the returned plan. */
+ * trailing bytes, a digest mismatch, or launch lists whose size fields
+ * (largest rows, width, tiles) differ from the fronts they list or that point
+ * outside the front tables; the caller owns the returned plan.  The digest
+ * detects damage, not tampering: beyond these checks the tables are trusted,
+ * so load only files that ssco_plan_save wrote. */
 ssco_status ssco_plan_save(ssco_plan plan, const char* path);
 ssco_status ssco_plan_load(const char* path, ssco_plan* out);
 void ssco_destroy(ssco_plan plan);

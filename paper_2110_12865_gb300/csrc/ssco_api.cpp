@@ -166,6 +166,41 @@ bool serialize(IO& io, Plan& P) {
     return ok;
 }
 
+// The launch lists size shared memory, register-budget instantiations and
+// big-front tiles from their rmax / wmax / tile fields: on load these must
+// equal the maxima over the listed fronts, which must exist, lie inside the
+// front list and fit their size class.  A solve list is ordered largest
+// front first (the sweeps peel off its split and cluster fronts and size the
+// rest from the next front).
+bool launch_lists_consistent(const Plan& P) {
+    const int64_t nf = (int64_t)P.fronts.size(), nl = (int64_t)P.front_lists.size();
+    auto check = [&](const std::vector<LaunchList>& lists) {
+        for (const LaunchList& ll : lists) {
+            if (ll.list_off < 0 || ll.count < 0 || ll.list_off > nl || ll.count > nl - ll.list_off) return false;
+            int32_t rmax = 0, wmax = 0, klist = 0;
+            int64_t lower = 0, syrk = 0;
+            for (int32_t i = 0; i < ll.count; ++i) {
+                const int32_t F = P.front_lists[ll.list_off + i];
+                if (F < 0 || F >= nf) return false;
+                const FrontDesc& d = P.fronts[F];
+                if (d.w < 1 || d.r < d.w || (ll.cls > 0 && d.r > ll.cls)) return false;
+                if (ll.cls == 0 && i > 0 && d.r > P.fronts[P.front_lists[ll.list_off + i - 1]].r) return false;
+                rmax = std::max(rmax, d.r);
+                wmax = std::max(wmax, d.w);
+                const int64_t t = (d.r + 63) / 64, u = (d.r - d.w + 63) / 64;
+                lower = std::max(lower, t * (t + 1) / 2);
+                syrk = std::max(syrk, u * (u + 1) / 2);
+                klist = std::max(klist, d.klist_n);
+            }
+            if (rmax != ll.rmax || wmax != ll.wmax) return false;
+            if (ll.cls == -1 && (lower != ll.max_lower_tiles || syrk != ll.max_syrk_tiles || klist != ll.max_klist))
+                return false;
+        }
+        return true;
+    };
+    return check(P.fact_launches) && check(P.solve_launches);
+}
+
 }  // namespace
 
 extern "C" {
@@ -669,6 +704,10 @@ ssco_status ssco_plan_load(const char* path, ssco_plan* out) {
     if (!ok) {
         delete h;
         return fail(nullptr, SSCO_ERR_INVALID_ARG, "truncated or corrupt plan file (checksum)");
+    }
+    if (!launch_lists_consistent(h->P)) {
+        delete h;
+        return fail(nullptr, SSCO_ERR_INVALID_ARG, "inconsistent plan file (launch lists)");
     }
     build_blob(h->P);
     compute_ws_layout(h->P);

@@ -193,6 +193,110 @@ def test_plan_save_load_roundtrip(S, tmp_path):
         assert ei.value.status == 1
 
 
+def _fnv1a64(data: bytes) -> int:
+    h = 0xcbf29ce484222325
+    for c in data:
+        h = ((h ^ c) * 0x100000001b3) & 0xFFFFFFFFFFFFFFFF
+    return h
+
+
+def _find_solve_lists(raw: bytes, n_levels: int):
+    """(offset, count) of the solve launch lists in a plan file: a u64 count N,
+    then N 56-byte records (level, class, list offset, count, largest rows,
+    width, three big-front maxima) whose level runs 0, 1, ..., whose class is
+    0 and whose list offsets never decrease, then the plan's level count (the
+    field the file writes next)."""
+    import struct
+    rec = 56
+    for o in range(0, len(raw) - 12):
+        n = struct.unpack_from("<Q", raw, o)[0]
+        if not 1 <= n <= 4096 or o + 8 + n * rec + 4 > len(raw):
+            continue
+        base = o + 8
+        recs = [struct.unpack_from("<iiqiii", raw, base + k * rec) for k in range(n)]
+        if all(r[0] == k and r[1] == 0 and r[3] >= 0 for k, r in enumerate(recs)) and \
+                all(recs[k][2] <= recs[k + 1][2] for k in range(n - 1)) and \
+                struct.unpack_from("<i", raw, base + n * rec)[0] == n_levels:
+            return base, n
+    raise AssertionError("solve launch lists not found")
+
+
+def test_plan_load_refuses_inconsistent_launch_lists(S, tmp_path):
+    """A re-digested plan file whose launch list understates its largest front
+    (which sizes shared memory), overstates its width, or reaches past the
+    front list is refused with SSCO_ERR_INVALID_ARG; the untouched file, put
+    through the same re-digest, loads."""
+    import struct
+    p = P.grid_problem(24, 24, cfg=1)
+    pl = S.Plan(p, precision=S.FP32_REFINE)
+    f = str(tmp_path / "plan.bin")
+    pl.save(f)
+    raw = open(f, "rb").read()
+    body = bytearray(raw[:-8])
+    base, n_lists = _find_solve_lists(bytes(body), int(pl.info["n_levels"]))
+    # the first list with fronts
+    k = next(k for k in range(n_lists) if struct.unpack_from("<i", body, base + k * 56 + 16)[0] > 0)
+    o = base + k * 56
+    count, rmax, wmax = struct.unpack_from("<iii", body, o + 16)
+    assert count > 0 and rmax >= wmax >= 1
+
+    def with_field(off, fmt, value):
+        b = bytearray(body)
+        struct.pack_into(fmt, b, off, value)
+        return bytes(b) + struct.pack("<Q", _fnv1a64(bytes(b)))
+
+    same = str(tmp_path / "same.bin")
+    open(same, "wb").write(bytes(body) + struct.pack("<Q", _fnv1a64(bytes(body))))
+    assert S.Plan.load(same, precision=S.FP32_REFINE).info == pl.info
+    for i, blob in enumerate([with_field(o + 20, "<i", rmax - 1),       # largest rows understated
+                              with_field(o + 24, "<i", wmax + 1),       # width overstated
+                              with_field(o + 16, "<i", 1 << 30),        # count past the front list
+                              with_field(o + 8, "<q", -1)]):            # negative list offset
+        g = str(tmp_path / f"bad{i}.bin")
+        open(g, "wb").write(blob)
+        with pytest.raises(S.SscoError) as ei:
+            S.Plan.load(g)
+        assert ei.value.status == 1
+    # a solve list out of its largest-first order: its fronts reversed in the
+    # front list.  A level whose fronts all have one size stays in order, so
+    # at least one of the reversed lists (not every one) must be refused.
+    fl_base = _find_front_lists(bytes(body), base)
+    refused = 0
+    for k in range(n_lists):
+        lo, cnt = struct.unpack_from("<qi", body, base + k * 56 + 8)
+        if cnt < 2:
+            continue
+        ids = struct.unpack_from(f"<{cnt}i", body, fl_base + 4 * lo)
+        assert len(set(ids)) == cnt and all(0 <= i < pl.info["n_fronts"] for i in ids)
+        b = bytearray(body)
+        struct.pack_into(f"<{cnt}i", b, fl_base + 4 * lo, *ids[::-1])
+        g = str(tmp_path / f"order{k}.bin")
+        open(g, "wb").write(bytes(b) + struct.pack("<Q", _fnv1a64(bytes(b))))
+        try:
+            S.Plan.load(g)
+        except S.SscoError as e:
+            assert e.status == 1
+            refused += 1
+    assert refused >= 1
+
+
+def _find_front_lists(raw: bytes, solve_base: int) -> int:
+    """Offset of the front-list entries (int32) in a plan file: the file
+    writes the front list (u64 length, entries), then the factorization
+    launch lists (u64 length, 56-byte records), then the solve lists."""
+    import struct
+    for n_fact in range(0, 1 << 16):
+        fact_len_at = solve_base - 8 - 56 * n_fact - 8
+        if fact_len_at < 8:
+            break
+        if struct.unpack_from("<Q", raw, fact_len_at)[0] != n_fact:
+            continue
+        for n_fl in range(1, (fact_len_at - 8) // 4 + 1):
+            if struct.unpack_from("<Q", raw, fact_len_at - 4 * n_fl - 8)[0] == n_fl:
+                return fact_len_at - 4 * n_fl
+    raise AssertionError("front list not found")
+
+
 def test_fixed_dofs_are_identity_rows(S):
     p = P.elasticity_problem(3, cfg=2)
     pl = S.Plan(p)
