@@ -528,24 +528,37 @@ ssco_status ssco_graph_run(ssco_plan h, const void* vals, int32_t vals_dtype, co
     return SSCO_OK;
 }
 
+// Per-plan arguments of the multi-plan calls: every plan's pointers, dtype
+// and uniqueness first (SSCO_ERR_INVALID_ARG), then their state (bound, b
+// and x distinct), so that an argument error is reported whatever the state.
+static ssco_status check_many(const ssco_plan* plans, int32_t n, const void* const* vals, const int32_t* vals_dtype,
+                              const double* const* shift, const double* const* b, double* const* x,
+                              std::vector<Plan*>& ps) {
+    for (int32_t i = 0; i < n; ++i) {
+        if (!plans[i]) return fail(nullptr, SSCO_ERR_INVALID_ARG, "NULL plan");
+        for (int32_t k = 0; k < i; ++k)
+            if (plans[k] == plans[i]) return fail(plans[i], SSCO_ERR_INVALID_ARG, "a plan appears twice");
+        if (!vals[i] || !shift[i] || !b[i] || !x[i]) return fail(plans[i], SSCO_ERR_INVALID_ARG, "NULL argument");
+        if (vals_dtype[i] != SSCO_VALS_F64 && vals_dtype[i] != SSCO_VALS_F32)
+            return fail(plans[i], SSCO_ERR_INVALID_ARG, "unknown vals dtype");
+    }
+    for (int32_t i = 0; i < n; ++i) {
+        Plan& P = plans[i]->P;
+        if (!P.bound) return fail(plans[i], SSCO_ERR_STATE, "ssco_bind has not been called");
+        if (b[i] == x[i]) return fail(plans[i], SSCO_ERR_INVALID_ARG, "b and x alias");
+        ps[i] = &P;
+    }
+    return SSCO_OK;
+}
+
 ssco_status ssco_graph_run_many(const ssco_plan* plans, int32_t n_plans, const void* const* vals,
                                 const int32_t* vals_dtype, const double* const* shift, const double* const* b,
                                 double* const* x, void* stream) {
     if (!plans || n_plans < 1 || n_plans > 1024 || !vals || !vals_dtype || !shift || !b || !x)
         return fail(nullptr, SSCO_ERR_INVALID_ARG, "NULL argument or plan count outside 1..1024");
     std::vector<Plan*> ps(n_plans);
-    for (int32_t i = 0; i < n_plans; ++i) {
-        if (!plans[i]) return fail(nullptr, SSCO_ERR_INVALID_ARG, "NULL plan");
-        for (int32_t k = 0; k < i; ++k)
-            if (plans[k] == plans[i]) return fail(plans[i], SSCO_ERR_INVALID_ARG, "a plan appears twice");
-        Plan& P = plans[i]->P;
-        if (!vals[i] || !shift[i] || !b[i] || !x[i]) return fail(plans[i], SSCO_ERR_INVALID_ARG, "NULL argument");
-        if (vals_dtype[i] != SSCO_VALS_F64 && vals_dtype[i] != SSCO_VALS_F32)
-            return fail(plans[i], SSCO_ERR_INVALID_ARG, "unknown vals dtype");
-        if (!P.bound) return fail(plans[i], SSCO_ERR_STATE, "ssco_bind has not been called");
-        if (b[i] == x[i]) return fail(plans[i], SSCO_ERR_INVALID_ARG, "b and x alias");
-        ps[i] = &P;
-    }
+    const ssco_status st = check_many(plans, n_plans, vals, vals_dtype, shift, b, x, ps);
+    if (st != SSCO_OK) return st;
     int e = launch_graph_run_many(ps.data(), n_plans, vals, vals_dtype, shift, b, x, stream);
     if (e) return cuda_fail(plans[0], e, "multi-plan graph capture or launch");
     for (Plan* P : ps) P->factored = true;
@@ -558,18 +571,8 @@ ssco_status ssco_autotune_many(const ssco_plan* plans, int32_t n_plans, const vo
     if (!plans || n_plans < 1 || n_plans > 1024 || !vals || !vals_dtype || !shift || !b || !x || reps < 1)
         return fail(nullptr, SSCO_ERR_INVALID_ARG, "NULL argument, plan count outside 1..1024 or reps < 1");
     std::vector<Plan*> ps(n_plans);
-    for (int32_t i = 0; i < n_plans; ++i) {
-        if (!plans[i]) return fail(nullptr, SSCO_ERR_INVALID_ARG, "NULL plan");
-        for (int32_t k = 0; k < i; ++k)
-            if (plans[k] == plans[i]) return fail(plans[i], SSCO_ERR_INVALID_ARG, "a plan appears twice");
-        Plan& P = plans[i]->P;
-        if (!vals[i] || !shift[i] || !b[i] || !x[i]) return fail(plans[i], SSCO_ERR_INVALID_ARG, "NULL argument");
-        if (vals_dtype[i] != SSCO_VALS_F64 && vals_dtype[i] != SSCO_VALS_F32)
-            return fail(plans[i], SSCO_ERR_INVALID_ARG, "unknown vals dtype");
-        if (!P.bound) return fail(plans[i], SSCO_ERR_STATE, "ssco_bind has not been called");
-        if (b[i] == x[i]) return fail(plans[i], SSCO_ERR_INVALID_ARG, "b and x alias");
-        ps[i] = &P;
-    }
+    const ssco_status st = check_many(plans, n_plans, vals, vals_dtype, shift, b, x, ps);
+    if (st != SSCO_OK) return st;
     int e = autotune_many(ps.data(), n_plans, vals, vals_dtype, shift, b, x, reps, stream, best_ms);
     if (e) return cuda_fail(plans[0], e, "multi-plan autotune");
     for (Plan* P : ps) P->factored = true;

@@ -297,6 +297,43 @@ def _find_front_lists(raw: bytes, solve_base: int) -> int:
     raise AssertionError("front list not found")
 
 
+def test_multi_plan_calls_refuse_bad_arguments(S):
+    """ssco_graph_run_many and ssco_autotune_many refuse on the host, before
+    any device work: no plans or more than 1024, a NULL plan array, a NULL
+    plan, a plan given twice, a NULL per-plan pointer, an unknown dtype,
+    reps < 1 (the tuner) and an unbound plan (SSCO_ERR_STATE)."""
+    import ctypes as C
+    L = S.load_library()
+    a = S.Plan(P.grid_problem(6, 6, cfg=1), precision=S.FP32_REFINE)
+    b = S.Plan(P.grid_problem(5, 7, cfg=1), precision=S.FP32_REFINE)
+
+    def h(p):
+        return p._h.value if isinstance(p._h, C.c_void_p) else p._h
+    fake = 4096   # a per-plan device pointer that is never dereferenced
+
+    def call(fn, hs, n=None, dtype=S.VALS_F32, ptr=fake, reps=3, plans_null=False):
+        k = max(len(hs), 1)
+        n = len(hs) if n is None else n
+        H = None if plans_null else (C.c_void_p * k)(*hs)
+        ptrs = (C.c_void_p * k)(*([ptr] * k))
+        dts = (C.c_int32 * k)(*([dtype] * k))
+        args = [H, n, ptrs, dts, ptrs, ptrs, ptrs]
+        if fn == "many_tune":
+            return L.ssco_autotune_many(*args, reps, None, None)
+        return L.ssco_graph_run_many(*args, None)
+
+    for fn in ("many_run", "many_tune"):
+        assert call(fn, [h(a)], n=0) == 1
+        assert call(fn, [h(a)], n=1025) == 1
+        assert call(fn, [h(a)], plans_null=True) == 1
+        assert call(fn, [h(a), None]) == 1
+        assert call(fn, [h(a), h(a)]) == 1
+        assert call(fn, [h(a), h(b)], ptr=None) == 1
+        assert call(fn, [h(a), h(b)], dtype=7) == 1
+        assert call(fn, [h(a), h(b)]) == 10          # neither plan is bound
+    assert call("many_tune", [h(a), h(b)], reps=0) == 1
+
+
 def test_fixed_dofs_are_identity_rows(S):
     p = P.elasticity_problem(3, cfg=2)
     pl = S.Plan(p)
