@@ -21,7 +21,11 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "ssco_oracle.c")
 BUILD_DIR = os.path.join(HERE, "_build")
-LIB = os.path.join(BUILD_DIR, "libssco_oracle.so")
+# A test may point the wrapper at another build of this source, one with a
+# planted mistake, to show that the pins fail on it (tests/test_oracle_mutants.py).
+_BUILT_LIB = os.path.join(BUILD_DIR, "libssco_oracle.so")
+_LIB_OVERRIDE = os.environ.get("SSCO_ORACLE_LIB")
+LIB = _LIB_OVERRIDE or _BUILT_LIB
 
 _lib = None
 KIND_ELEM_BLOCKS = 2   # K = sum_e K_e, the element blocks are the per-set values
@@ -34,18 +38,19 @@ f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (plain C, no fast-math, no FMA contraction)."""
     os.makedirs(BUILD_DIR, exist_ok=True)
-    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if force or not os.path.exists(_BUILT_LIB) or os.path.getmtime(_BUILT_LIB) < os.path.getmtime(SRC):
+        tmp = _BUILT_LIB + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
                                "-shared", "-std=c11", "-o", tmp, SRC, "-lm"])
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, _BUILT_LIB)
+    return _BUILT_LIB
 
 
 def lib():
     global _lib
     if _lib is None:
-        build()
+        if not _LIB_OVERRIDE:
+            build()
         L = C.CDLL(LIB)
         L.or_atwa_cap.restype = C.c_int64
         L.or_atwa_cap.argtypes = [C.c_int32, C.c_int32, i64p]

@@ -1,0 +1,79 @@
+"""The oracle's pins catch planted mistakes.
+
+Each case copies the oracle's C source with one plausible mistake (a dropped
+term, a flipped sign, a wrong index, a transposed operand), builds it with the
+oracle's own flags and runs the pin module against that build
+(``SSCO_ORACLE_LIB``).  The pins must fail by assertion, not by a crash, so a
+test that passed against the mutant, or a pin that never looked at the mutated
+step, would show up here.  CPU only.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "ssco_oracle.c")
+
+# (name, exact text in the oracle, planted replacement)
+MUTANTS = [
+    ("assembly drops the shift",
+     "val[colptr[u]] += shift; /* diagonal first in column */",
+     "val[colptr[u]] += 0.0 * shift; /* diagonal first in column */"),
+    ("element assembly drops the shift",
+     "if (touched[u]) val[colptr[u]] += shift;",
+     "if (touched[u]) val[colptr[u]] += 0.0 * shift;"),
+    ("Cholesky update added instead of subtracted",
+     "acc[Li[p]] -= ljk * Lval[p];",
+     "acc[Li[p]] += ljk * Lval[p];"),
+    ("pivot without the square root",
+     "double ljj = sqrt(d);",
+     "double ljj = d;"),
+    ("forward solve reads the wrong entry",
+     "y[Li[p]] -= Lval[p] * y[j];",
+     "y[Li[p]] -= Lval[p] * y[Li[p]];"),
+    ("backward solve with the transposed operand",
+     "t -= Lval[p] * y[Li[p]];",
+     "t -= Lval[p] * y[j];"),
+    ("adjoint of the weights with the wrong sign",
+     "wbar[e] = -am * ax;",
+     "wbar[e] = am * ax;"),
+    ("element adjoint takes the wrong mirrored term",
+     "if (i != j) g += k * mu[v] * x[u];",
+     "if (i != j) g += k * mu[u] * x[v];"),
+    ("elimination tree takes the largest row",
+     "s->parent[j] = len > 1 ? buf[1] : -1;",
+     "s->parent[j] = len > 1 ? buf[len - 1] : -1;"),
+]
+
+
+def run_pins_against(tmp_path, source: str):
+    """Builds `source` as the oracle library and runs the pin module on it."""
+    mut = tmp_path / "ssco_oracle_variant.c"
+    mut.write_text(source)
+    lib = tmp_path / "libssco_oracle_variant.so"
+    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=c11",
+                           "-o", str(lib), str(mut), "-lm"])
+    env = dict(os.environ, SSCO_ORACLE_LIB=str(lib))
+    return subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+                           "-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu"],
+                          cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+
+
+def test_pins_pass_on_the_unchanged_source_built_the_same_way(tmp_path):
+    """Control: the harness itself (separate build, library override) leaves
+    the pins green, so a failure below comes from the planted mistake."""
+    r = run_pins_against(tmp_path, open(SRC).read())
+    assert r.returncode == 0, r.stdout[-2000:]
+
+
+@pytest.mark.parametrize("name,orig,planted", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pins_fail_on_planted_mistake(tmp_path, name, orig, planted):
+    src = open(SRC).read()
+    assert src.count(orig) == 1, f"mutation site not unique or gone: {orig}"
+    r = run_pins_against(tmp_path, src.replace(orig, planted))
+    # exit code 1: a pin failed by assertion (a crash or an error would be
+    # another code, and 0 would mean no pin noticed the mistake)
+    assert r.returncode == 1, f"{name}: pins exit {r.returncode}\n{r.stdout[-2000:]}\n{r.stderr[-1000:]}"
+    assert "FAILED" in r.stdout
