@@ -45,6 +45,21 @@ MUTANTS = [
     ("elimination tree takes the largest row",
      "s->parent[j] = len > 1 ? buf[1] : -1;",
      "s->parent[j] = len > 1 ? buf[len - 1] : -1;"),
+    ("permutation applies perm where its inverse belongs",
+     "int32_t a = iperm[rowind[p]], b = iperm[j];",
+     "int32_t a = perm[rowind[p]], b = perm[j];"),
+    ("cotangent weight without the half",
+     "w[tri_edge[3 * t + c]] += 0.5 * dot / cross;",
+     "w[tri_edge[3 * t + c]] += dot / cross;"),
+    ("block adjoint repeats one half of the mirrored pair",
+     "-(mu[u] * x[v] + mu[v] * x[u])",
+     "-(mu[u] * x[v] + mu[u] * x[v])"),
+    ("tet stiffness with lambda replaced by mu",
+     "double lam = Ee * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));",
+     "double lam = Ee / (2.0 * (1.0 + nu));"),
+    ("tet stiffness with tensor instead of engineering shear",
+     "D[r + 3][r + 3] = mu;",
+     "D[r + 3][r + 3] = 2.0 * mu;"),
 ]
 
 
