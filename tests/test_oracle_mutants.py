@@ -92,3 +92,72 @@ def test_pins_fail_on_planted_mistake(tmp_path, name, orig, planted):
     # another code, and 0 would mean no pin noticed the mistake)
     assert r.returncode == 1, f"{name}: pins exit {r.returncode}\n{r.stdout[-2000:]}\n{r.stderr[-1000:]}"
     assert "FAILED" in r.stdout
+
+
+# ---------------------------------------------------------------------------
+# The sparse-expression evaluators are Python: each mutant is the wrapper's
+# source with one planted mistake, executed as a module of its own and put in
+# place of the oracle inside the pin module for the expression pins.
+# ---------------------------------------------------------------------------
+EXPR_MUTANTS = [
+    ("sum keeps only the second operand",
+     "d[key] = d.get(key, 0.0) + v",
+     "d[key] = v"),
+    ("product keeps only the last term",
+     "d[(i, j)] = d.get((i, j), 0.0) + a * b",
+     "d[(i, j)] = a * b"),
+    ("transpose leaves the entries in place",
+     "mats.append((ca, ra, {(j, i): v for (i, j), v in A.items()}))",
+     "mats.append((ca, ra, {(i, j): v for (i, j), v in A.items()}))"),
+    ("scaling ignores its factor",
+     "mats.append((ra, ca, {key: al * v for key, v in A.items()}))",
+     "mats.append((ra, ca, {key: v for key, v in A.items()}))"),
+    ("shared leaf values all read through the map's first entry",
+     "v = float(leaf_vals[off + (int(vm[q]) if vm is not None else q)])",
+     "v = float(leaf_vals[off + (int(vm[0]) if vm is not None else q)])"),
+    ("row of a sum keeps only the second operand",
+     "r[j] = r.get(j, 0.0) + v",
+     "r[j] = v"),
+    ("row of a product keeps only the last term",
+     "r[j] = r.get(j, 0.0) + a * b",
+     "r[j] = a * b"),
+    ("row of a scaling ignores its factor",
+     "r = {j: nd[2] * v for j, v in row(nd[1], i).items()}",
+     "r = {j: v for j, v in row(nd[1], i).items()}"),
+]
+EXPR_PINS = ["test_expr_oracle_matches_dense_evaluation", "test_expr_oracle_tridiagonal_cube_closed_form",
+             "test_expr_oracle_weighted_laplacian_of_a_path", "test_expr_row_oracle_equals_full_oracle",
+             "test_expr_oracle_shared_values_equal_expanded_values"]
+
+
+def expression_pins_failing(monkeypatch, source: str):
+    """Runs the expression pins against `source` as the oracle module; returns
+    the pins that failed by assertion (any other exception propagates)."""
+    import types
+
+    import test_oracle_pins as T
+    from oracle import oracle as real
+    mod = types.ModuleType("oracle_variant")
+    mod.__file__ = real.__file__
+    exec(compile(source, real.__file__, "exec"), mod.__dict__)
+    monkeypatch.setattr(T, "O", mod)
+    failed = []
+    for pin in EXPR_PINS:
+        try:
+            getattr(T, pin)()
+        except AssertionError:
+            failed.append(pin)
+    return failed
+
+
+def test_expression_pins_pass_on_the_unchanged_wrapper(monkeypatch):
+    from oracle import oracle as real
+    assert expression_pins_failing(monkeypatch, open(real.__file__).read()) == []
+
+
+@pytest.mark.parametrize("name,orig,planted", EXPR_MUTANTS, ids=[m[0] for m in EXPR_MUTANTS])
+def test_expression_pins_fail_on_planted_mistake(monkeypatch, name, orig, planted):
+    from oracle import oracle as real
+    src = open(real.__file__).read()
+    assert src.count(orig) == 1, f"mutation site not unique or gone: {orig}"
+    assert expression_pins_failing(monkeypatch, src.replace(orig, planted)), name
