@@ -45,6 +45,18 @@ MUTANTS = [
     ("elimination tree takes the largest row",
      "s->parent[j] = len > 1 ? buf[1] : -1;",
      "s->parent[j] = len > 1 ? buf[len - 1] : -1;"),
+    ("supernode joins a column with several children",
+     "s->parent[j - 1] == j && nchild[j] == 1 &&",
+     "s->parent[j - 1] == j && nchild[j] >= 1 &&"),
+    ("supernode joins without the column-count condition",
+     "s->colcount[j] == s->colcount[j - 1] - 1;",
+     "s->colcount[j] <= s->colcount[j - 1];"),
+    ("column level from the shortest path",
+     "if (s->col_level[c] + 1 > lv) lv = s->col_level[c] + 1;",
+     "if (lv == 0 || s->col_level[c] + 1 < lv) lv = s->col_level[c] + 1;"),
+    ("supernode parent from the supernode's first column",
+     "int32_t last = s->snode_first[k + 1] - 1;",
+     "int32_t last = s->snode_first[k];"),
     ("permutation applies perm where its inverse belongs",
      "int32_t a = iperm[rowind[p]], b = iperm[j];",
      "int32_t a = perm[rowind[p]], b = perm[j];"),
