@@ -27,6 +27,12 @@ MUTANTS = [
     ("Cholesky update added instead of subtracted",
      "acc[Li[p]] -= ljk * Lval[p];",
      "acc[Li[p]] += ljk * Lval[p];"),
+    ("factorization skips K's diagonal entry",
+     "if (s->Krowind[p] >= j) acc[s->Krowind[p]] += Kval[p];",
+     "if (s->Krowind[p] > j) acc[s->Krowind[p]] += Kval[p];"),
+    ("failing pivot recorded one column late",
+     "            bad = j;\n            break;",
+     "            bad = j + 1;\n            break;"),
     ("pivot without the square root",
      "double ljj = sqrt(d);",
      "double ljj = d;"),
