@@ -355,12 +355,13 @@ def run_ours(args, rank, world, local_rank):
         loop's body once, whatever number of corrections the device loop
         runs.  The same inputs take the same corrections in every step."""
         flows = [int(pl.info["tune_flow"]) for pl in plans]
-        for pl, f in zip(plans, flows):
-            pl.set_flow(f | 16)
-        n = eager_step(plans, dev_in)
-        for pl, f in zip(plans, flows):
-            pl.set_flow(f)
-        return n
+        try:
+            for pl, f in zip(plans, flows):
+                pl.set_flow(f | 16)
+            return eager_step(plans, dev_in)
+        finally:
+            for pl, f in zip(plans, flows):
+                pl.set_flow(f)
 
     def step(plans, dev_in):
         if args.eager:
