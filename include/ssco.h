@@ -232,13 +232,17 @@ ssco_status ssco_analyze(const ssco_pattern* const* pats, int32_t n_pats, const 
                          ssco_plan* out);
 ssco_status ssco_plan_info(ssco_plan plan, ssco_info* out);
 /* Copies one exported structure into host_buf (bytes must be >= its size,
- * else SSCO_ERR_OOM). */
+ * else SSCO_ERR_OOM).
+ * No counterpart in the paper: it exposes the host phase's structures to
+ * tests and tools. */
 ssco_status ssco_plan_export(ssco_plan plan, int32_t what, void* host_buf, size_t bytes);
 
 /* Attaches caller-allocated device memory: dev_tables (>= tables_bytes,
  * 256-byte aligned) receives the index tables (copied on `stream`);
  * dev_workspace (>= workspace_bytes, 256-byte aligned) holds K, the factor,
- * update matrices, vectors and status words.  Re-binding is allowed. */
+ * update matrices, vectors and status words.  Re-binding is allowed.
+ * The device copy of the harvested tables that every grouped launch reads
+ * (Sec. 4.4, 4.8). */
 ssco_status ssco_bind(ssco_plan plan, void* dev_tables, size_t tables_bytes, void* dev_workspace,
                       size_t workspace_bytes, void* stream);
 
@@ -293,15 +297,21 @@ ssco_status ssco_backward(ssco_plan plan, const double* x, const double* xbar, d
  * (any may be NULL): status (ssco_status codes), iters (refinement
  * iterations of the last solve), resid (||b - K x||_2 / ||b||_2 of the last
  * solve, FP64), bad_col (first non-positive pivot in permuted numbering,
- * -1 if none).  Returns SSCO_OK or the worst system status. */
+ * -1 if none).  Returns SSCO_OK or the worst system status.
+ * Per-system outcome of the repeated evaluation (Sec. 3.3); the status
+ * words have no counterpart in the paper. */
 ssco_status ssco_status_get(ssco_plan plan, void* stream, int32_t* status, int32_t* iters,
                             double* resid, int32_t* bad_col);
 
 /* Synchronizes `stream`, then writes the factor in the CSC order of
- * SSCO_EXPORT_L_ROWIND to the HOST array host_out, as double [B][nnz_L]. */
+ * SSCO_EXPORT_L_ROWIND to the HOST array host_out, as double [B][nnz_L].
+ * No counterpart in the paper: it copies a computed result out for
+ * checking. */
 ssco_status ssco_export_L(ssco_plan plan, double* host_out, void* stream);
 /* Synchronizes `stream`, then writes K~ in the CSC order of
- * SSCO_EXPORT_K_ROWIND to the HOST array host_out, double [B][nnz_K]. */
+ * SSCO_EXPORT_K_ROWIND to the HOST array host_out, double [B][nnz_K].
+ * No counterpart in the paper: it copies a computed result out for
+ * checking. */
 ssco_status ssco_export_K(ssco_plan plan, double* host_out, void* stream);
 
 /* Autotuner of the launch shapes of the level groups: for each knob (the
@@ -312,7 +322,9 @@ ssco_status ssco_export_K(ssco_plan plan, double* host_out, void* stream);
  * data (median of `reps` numeric + solve steps, CUDA events) and the fastest
  * is kept in the plan (saved by ssco_plan_save).  Synchronizes `stream`;
  * leaves a valid factor and solution (x) behind.  *best_ms (may be NULL)
- * receives the best step time. */
+ * receives the best step time.
+ * No counterpart in the paper, which fixes launch shapes when it generates
+ * code (App. F); here they are timed on the caller's data. */
 ssco_status ssco_autotune(ssco_plan plan, const void* vals, int32_t vals_dtype, const double* shift, const double* b,
                           double* x, int32_t reps, void* stream, double* best_ms);
 
@@ -348,7 +360,9 @@ ssco_status ssco_set_flow(ssco_plan plan, int32_t flow, int64_t max_polls, int32
  * iteration).  The graph is captured (on library-owned streams) on the first
  * call for this (vals, shift, b, x, workspace) tuple and replayed by later
  * calls with the same pointers; new pointers or ssco_bind re-capture.  Call
- * it outside any stream capture of your own.  Asynchronous on `stream`. */
+ * it outside any stream capture of your own.  Asynchronous on `stream`.
+ * The same evaluation replayed for every new value set (Sec. 3.3); the CUDA
+ * graph itself has no counterpart in the paper. */
 ssco_status ssco_graph_run(ssco_plan plan, const void* vals, int32_t vals_dtype, const double* shift, const double* b,
                            double* x, void* stream);
 
@@ -361,7 +375,9 @@ ssco_status ssco_graph_run(ssco_plan plan, const void* vals, int32_t vals_dtype,
  * plans[0] and re-captured when a plan, a pointer or a dtype changes, or
  * after anything that releases a plan's graphs (ssco_bind, ssco_autotune,
  * ssco_set_flow).  No plan may appear twice; call it outside any stream
- * capture of your own.  Asynchronous on `stream`. */
+ * capture of your own.  Asynchronous on `stream`.
+ * Several independent patterns' evaluations in one replay (Sec. 4.3
+ * grouping across patterns); no counterpart in the paper as a call. */
 ssco_status ssco_graph_run_many(const ssco_plan* plans, int32_t n_plans, const void* const* vals,
                                 const int32_t* vals_dtype, const double* const* shift, const double* const* b,
                                 double* const* x, void* stream);
@@ -385,7 +401,9 @@ ssco_status ssco_autotune_many(const ssco_plan* plans, int32_t n_plans, const vo
 /* End-to-end call on HOST buffers: copies vals/shift/b to the device
  * (staging areas inside the workspace), runs numeric + solve as the captured
  * graph of ssco_graph_run, copies x back and synchronizes.  Host arrays use
- * the same layouts as above. */
+ * the same layouts as above.
+ * No counterpart in the paper: the host-buffer wrapper around
+ * ssco_graph_run. */
 ssco_status ssco_refactor_solve_host(ssco_plan plan, const void* vals, int32_t vals_dtype,
                                      const double* shift, const double* b, double* x, void* stream);
 
@@ -457,7 +475,10 @@ ssco_status ssco_cotan_weights(const int32_t* tri, const int32_t* tri_edge, int6
  *          are never dereferenced; may be NULL.
  * nu must lie in (-1, 0.5).  Async on `stream`; returns
  * SSCO_ERR_INVALID_ARG for inconsistent sizes, nu or null pointers,
- * SSCO_ERR_CUDA if the launch fails. */
+ * SSCO_ERR_CUDA if the launch fails.
+ * No counterpart in the paper: it builds, from vertex positions, the per-
+ * call element blocks that SSCO_KIND_ELEM_BLOCKS patterns take (the element
+ * form of Sec. 4.2.4). */
 ssco_status ssco_tet_stiffness(const int32_t* tets, int64_t n_tet, int64_t n_node, int32_t batch, const double* xyz,
                                const double* E, double nu, double* K_e, int32_t* n_bad, void* stream);
 
@@ -543,7 +564,9 @@ enum { SSCO_EXPR_EXPORT_LEVELS = 0,   /* int64 [n_levels+1] op ranges */
  * Slot layout: slot 0 = 1, slots 1..n_leaf_vals = leaf values,
  * then the intermediates of level 1, 2, ... (op i is slot
  * 1 + n_leaf_vals + i).  Returns INVALID_ARG / PATTERN for malformed nodes
- * (message in ssco_expr_last_error(NULL)), UNSUPPORTED beyond int32 slots. */
+ * (message in ssco_expr_last_error(NULL)), UNSUPPORTED beyond int32 slots.
+ * The paper's method on sparse matrix expressions: unrolling, hashing,
+ * levels and leaf harvesting (Sec. 4.1-4.4, App. A). */
 ssco_status ssco_expr_compile(const ssco_expr_node* nodes, int32_t n_nodes, const int32_t* outputs, int32_t n_out,
                               int32_t batch, int32_t precision, int32_t inline_terms, ssco_expr* out);
 
@@ -588,27 +611,33 @@ ssco_status ssco_expr_compile_opts(const ssco_expr_node* nodes, int32_t n_nodes,
                                    int32_t n_out, const ssco_expr_opts* opts, ssco_expr* out);
 ssco_status ssco_expr_get_info(ssco_expr e, ssco_expr_info* out);
 ssco_status ssco_expr_export(ssco_expr e, int32_t what, void* host_buf, uint64_t bytes);
-/* Shape and CSR pattern of the k-th output (rowptr [rows+1], colind [nnz]). */
+/* Shape and CSR pattern of the k-th output (rowptr [rows+1], colind [nnz]).
+ * No counterpart in the paper: describes an output's pattern for the
+ * caller. */
 ssco_status ssco_expr_output_shape(ssco_expr e, int32_t k, int32_t* rows, int32_t* cols, int64_t* nnz);
 ssco_status ssco_expr_output_pattern(ssco_expr e, int32_t k, int64_t* rowptr, int32_t* colind);
 /* Caller-allocated device memory of table_bytes / workspace_bytes (256-byte
- * aligned); the tables are copied with `stream`, which is synchronized. */
+ * aligned); the tables are copied with `stream`, which is synchronized.
+ * The device copy of the harvested tables (Sec. 4.4, 4.8). */
 ssco_status ssco_expr_bind(ssco_expr e, void* dev_tables, void* dev_workspace, void* stream);
 /* Evaluates every set: leaf_vals [batch][n_leaf_vals] and out_vals
  * [batch][n_out_vals] device arrays of the program's precision.  Async;
- * launches 2 + n_levels kernels on `stream`. */
+ * launches 2 + n_levels kernels on `stream`.
+ * One launch per dependency level of grouped expressions (Sec. 4.3). */
 ssco_status ssco_expr_run(ssco_expr e, const void* leaf_vals, void* out_vals, void* stream);
 /* Versioned file of a compiled program (host tables only; digest-checked
  * like plan files).  Load refuses another version, damage, and tables that
  * index outside the program's slots; the caller owns the returned program
- * and binds it as after compile. */
+ * and binds it as after compile.
+ * No counterpart in the paper: a compiled program kept on disk. */
 ssco_status ssco_expr_save(ssco_expr e, const char* path);
 ssco_status ssco_expr_load(const char* path, ssco_expr* out);
 const char* ssco_expr_last_error(ssco_expr e);
 void ssco_expr_destroy(ssco_expr e);
 
 /* Number of kernel launches the last ssco_numeric / ssco_solve /
- * ssco_backward / ssco_refactor_solve_host call issued (host counter). */
+ * ssco_backward / ssco_refactor_solve_host call issued (host counter).
+ * No counterpart in the paper: instrumentation. */
 int64_t ssco_last_launch_count(ssco_plan plan);
 
 /* Per-kernel timing.  ssco_profile_enable(plan, max_launches) creates a pool
@@ -649,7 +678,8 @@ ssco_status ssco_profile_enable(ssco_plan plan, int32_t max_launches);
 ssco_status ssco_profile_read(ssco_plan plan, ssco_kernel_stat* out);
 /* Per-launch trace: synchronizes the device and copies up to `cap` records
  * in launch order (kind, milliseconds, flops, bytes; any array may be NULL)
- * WITHOUT clearing them; *n receives the number of records held. */
+ * WITHOUT clearing them; *n receives the number of records held.
+ * No counterpart in the paper: instrumentation. */
 ssco_status ssco_profile_trace(ssco_plan plan, int32_t* kinds, float* ms, double* flops, double* bytes,
                                int64_t cap, int64_t* n);
 const char* ssco_kernel_name(int32_t kind);
@@ -664,7 +694,9 @@ const char* ssco_status_string(ssco_status s);
  * (largest rows, width, tiles) differ from the fronts they list or that point
  * outside the front tables; the caller owns the returned plan.  The digest
  * detects damage, not tampering: beyond these checks the tables are trusted,
- * so load only files that ssco_plan_save wrote. */
+ * so load only files that ssco_plan_save wrote.
+ * No counterpart in the paper: the host phase's result kept on disk, so
+ * that it runs once per pattern (Sec. 3.3). */
 ssco_status ssco_plan_save(ssco_plan plan, const char* path);
 ssco_status ssco_plan_load(const char* path, ssco_plan* out);
 void ssco_destroy(ssco_plan plan);
